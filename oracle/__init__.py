@@ -1,0 +1,29 @@
+"""CPU oracle for fixed-radius neighbour search (arXiv 2212.07679).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import anything from this package.  The
+product path (``paper_2212_07679_gb300``) never imports, loads or runs it, and
+this package imports nothing from the product path.
+
+Contents:
+
+* ``brute_radius``        -- FP64 brute force by direct differences (C, OpenMP);
+* ``brute_radius_numpy``  -- the same definition written in numpy (second,
+                             independent implementation for small inputs);
+* ``pair_dist2``          -- the same definition for sampled (query, point) pairs;
+* ``cpu_snn``             -- Algorithms 1 and 2 in FP64 (plain CPU SNN);
+* ``dbscan``              -- DBSCAN on top of the brute-force neighbour lists.
+
+Pins (tests/test_oracle_*.py): hand cases under tests/golden/, exact
+invariants, the paper's printed return ratios (Tables 1 and 2) and the
+closed-form distance distribution of the unit square and cube, the Gaussian
+blob model of Section 5, and agreement with scipy's FP64 cdist.
+"""
+from .brute import (brute_radius, brute_radius_numpy, pair_dist2, build_oracle,
+                    oracle_threads, CSR)
+from .cpu_snn import SNNIndex, snn_index, snn_query, snn_radius
+from .dbscan import dbscan, dbscan_bfs
+
+__all__ = ["brute_radius", "brute_radius_numpy", "pair_dist2", "build_oracle",
+           "oracle_threads", "CSR", "SNNIndex", "snn_index", "snn_query", "snn_radius",
+           "dbscan", "dbscan_bfs"]

@@ -1,0 +1,160 @@
+"""FP64 brute-force oracle (test infrastructure; see the package docstring).
+
+Definition (Section 3.2 problem statement; direct form Eq. (3)): for FP32
+points p_j and query q widened exactly to FP64,
+S(j, q) = sum over ascending k of (p_jk - q_k)^2, each operation rounded to
+nearest with no fused multiply-add; j is a neighbour iff S <= fl64(R*R).
+Output: CSR with per-query ascending ids and dist2 = (float)S.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "snn_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+
+@dataclass
+class CSR:
+    offsets: np.ndarray   # int64, m+1
+    ids: np.ndarray       # int32, nnz (ascending within each row)
+    dist2: np.ndarray     # float32, nnz
+
+    @property
+    def m(self) -> int:
+        return len(self.offsets) - 1
+
+    @property
+    def nnz(self) -> int:
+        return int(self.offsets[-1])
+
+    def row(self, i: int):
+        a, b = int(self.offsets[i]), int(self.offsets[i + 1])
+        return self.ids[a:b], self.dist2[a:b]
+
+    def counts(self) -> np.ndarray:
+        return np.diff(self.offsets)
+
+
+def build_oracle(force: bool = False) -> str:
+    """Compile the C oracle (gcc, -O2 -ffp-contract=off, OpenMP)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+               "-fPIC", "-shared", "-o", tmp, _SRC]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _get():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build_oracle())
+        f32p = ctypes.POINTER(ctypes.c_float)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        f64p = ctypes.POINTER(ctypes.c_double)
+        i64, i32, f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+        lib.snn_oracle_dist2.argtypes = [f32p, f32p, i32]
+        lib.snn_oracle_dist2.restype = f64
+        lib.snn_oracle_count.argtypes = [f32p, i64, i32, i64, f32p, i64, i64, f64, i64p]
+        lib.snn_oracle_count.restype = i64
+        lib.snn_oracle_fill.argtypes = [f32p, i64, i32, i64, f32p, i64, i64, f64, i64p, i32p, f32p]
+        lib.snn_oracle_fill.restype = None
+        lib.snn_oracle_pairs.argtypes = [f32p, i32, i64, f32p, i64, i64p, i64p, i64, f64p]
+        lib.snn_oracle_pairs.restype = None
+        lib.snn_oracle_threads.argtypes = []
+        lib.snn_oracle_threads.restype = i32
+        _lib = lib
+    return _lib
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+def _as_f32(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.ndim != 2:
+        raise ValueError("expected a 2-d array")
+    return a
+
+
+def oracle_threads() -> int:
+    return int(_get().snn_oracle_threads())
+
+
+def brute_radius(P: np.ndarray, Q: np.ndarray | None, R: float) -> CSR:
+    """All j with S(j, q) <= fl64(R*R) for every row q of Q (Q=None: Q=P)."""
+    lib = _get()
+    P = _as_f32(P)
+    Q = P if Q is None else _as_f32(Q)
+    if Q.shape[1] != P.shape[1]:
+        raise ValueError("dimension mismatch")
+    n, d = P.shape
+    m = Q.shape[0]
+    R2 = float(np.float64(R) * np.float64(R))
+    counts = np.zeros(max(m, 1), dtype=np.int64)
+    if m == 0 or n == 0:
+        return CSR(np.zeros(m + 1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.float32))
+    lib.snn_oracle_count(_ptr(P, ctypes.c_float), n, d, d, _ptr(Q, ctypes.c_float), m, d, R2,
+                         _ptr(counts, ctypes.c_int64))
+    offsets = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(counts[:m], out=offsets[1:])
+    nnz = int(offsets[-1])
+    ids = np.empty(max(nnz, 1), dtype=np.int32)
+    d2 = np.empty(max(nnz, 1), dtype=np.float32)
+    lib.snn_oracle_fill(_ptr(P, ctypes.c_float), n, d, d, _ptr(Q, ctypes.c_float), m, d, R2,
+                        _ptr(offsets, ctypes.c_int64), _ptr(ids, ctypes.c_int32),
+                        _ptr(d2, ctypes.c_float))
+    return CSR(offsets, ids[:nnz], d2[:nnz])
+
+
+def brute_radius_numpy(P: np.ndarray, Q: np.ndarray | None, R: float) -> CSR:
+    """The same definition in numpy (vectorised over pairs, ascending k,
+    separate subtract / multiply / add: numpy never fuses them).  Small inputs."""
+    P = np.asarray(P, dtype=np.float32).astype(np.float64)
+    Q = P if Q is None else np.asarray(Q, dtype=np.float32).astype(np.float64)
+    m, d = Q.shape
+    R2 = np.float64(R) * np.float64(R)
+    S = np.zeros((m, P.shape[0]), dtype=np.float64)
+    for k in range(d):
+        t = P[None, :, k] - Q[:, None, k]
+        S = S + t * t
+    mask = S <= R2
+    counts = mask.sum(axis=1)
+    offsets = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(counts, out=offsets[1:])
+    qi, pj = np.nonzero(mask)          # row-major: ascending j within each i
+    return CSR(offsets, pj.astype(np.int32), S[qi, pj].astype(np.float32))
+
+
+def pair_dist2(P: np.ndarray, Q: np.ndarray | None, qi: np.ndarray, pj: np.ndarray) -> np.ndarray:
+    """S(pj[t], Q[qi[t]]) in FP64 for explicit pairs (Q=None: Q=P)."""
+    lib = _get()
+    P = _as_f32(P)
+    Q = P if Q is None else _as_f32(Q)
+    qi = np.ascontiguousarray(qi, dtype=np.int64)
+    pj = np.ascontiguousarray(pj, dtype=np.int64)
+    out = np.empty(len(qi), dtype=np.float64)
+    if len(qi):
+        lib.snn_oracle_pairs(_ptr(P, ctypes.c_float), P.shape[1], P.shape[1],
+                             _ptr(Q, ctypes.c_float), Q.shape[1],
+                             _ptr(qi, ctypes.c_int64), _ptr(pj, ctypes.c_int64), len(qi),
+                             _ptr(out, ctypes.c_double))
+    return out
+
+
+def brute_row(P: np.ndarray, q: np.ndarray, R: float):
+    """One query row against all of P: (ascending ids, dist2 float32)."""
+    csr = brute_radius(P, np.asarray(q, dtype=np.float32).reshape(1, -1), R)
+    return csr.row(0)
