@@ -1,0 +1,299 @@
+"""Benchmark of the SNN hot path on one GB300 (or N independent replicas).
+
+One step = the whole path on one synthetic batch: index build (Algorithm 1:
+mean, Gram, first direction, scores, radix sort, gather) and the exact
+self-join radius query (Algorithm 2: bands, scoring, FP64 decision, CSR).
+Workload: the 50-cluster anisotropic mixture, n = 1,000,000 points in d = 16,
+every point a query, R for ~50 neighbours per point.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+(FP64 brute force) on a bounded query sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+HBM_PEAK_FALLBACK = 6800.0
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": HBM_PEAK_FALLBACK, "bf16_tflops": 1900.0,
+                "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(args):
+    from paper_2212_07679_gb300 import workloads as wl
+    if args.workload == "gmm_aniso":
+        return wl.gmm_aniso(n=args.n) if args.n else wl.gmm_aniso()
+    if args.workload == "lowrank_img":
+        return wl.lowrank_img(n=args.n) if args.n else wl.lowrank_img()
+    if args.workload == "blobs3d":
+        return wl.blobs3d(n=args.n) if args.n else wl.blobs3d()
+    raise SystemExit(f"unknown workload {args.workload}")
+
+
+def workload_config(args, w, extra=None):
+    cfg = {"workload": f"{w.name} self-join", "n": w.n, "d": w.d, "queries": w.m,
+           "R": w.R, "precision": args.precision, "parallelism": f"replicas{args.gpus}",
+           "l2": "flushed between steps (256 MiB write)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def cpu_oracle_sample(w, budget_s=15.0, seed=7):
+    """Times the FP64 brute-force oracle on a bounded random query sample."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(w.m)
+    Qall = w.P if w.Q is None else w.Q
+    done, t_used, size = 0, 0.0, 16
+    while t_used < budget_s and done < w.m:
+        rows = order[done:done + size]
+        t0 = time.perf_counter()
+        oracle.brute_radius(w.P, Qall[rows], w.R)
+        dt = time.perf_counter() - t0
+        t_used += dt
+        done += len(rows)
+        if dt < budget_s / 8:
+            size *= 2
+    return {"value": done / t_used, "unit": "queries/s", "cores": oracle.oracle_threads(),
+            "kind": "oracle",
+            "sample": f"{done} random queries of the {w.m} against all {w.n} points "
+                      f"(FP64 brute force, {t_used:.1f} s)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = make_workload(args)
+    steps = []
+    for _ in range(args.warmup):
+        cpu_oracle_sample(w, budget_s=2.0)
+    for _ in range(args.steps):
+        steps.append(cpu_oracle_sample(w, budget_s=args.ref_budget))
+    qps = float(np.mean([s["value"] for s in steps]))
+    line = {"impl": "reference", "metric": "exact radius queries/s (self-join)", "value": qps,
+            "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * w.m / qps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args, w),
+            "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": steps[-1]["cores"],
+                             "kind": "oracle", "sample": steps[-1]["sample"]},
+            "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def count_launches(fn):
+    """Kernel launches of one call, from the CUDA activity trace."""
+    import torch
+    from torch.profiler import ProfilerActivity, profile
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        fn()
+        torch.cuda.synchronize()
+    names = [e.name for e in prof.events() if e.device_type.name == "CUDA"
+             and not e.name.startswith("Memcpy") and not e.name.startswith("Memset")]
+    ours = [n for n in names if "snn" in n]
+    return len(ours), len(names)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2212_07679_gb300 import snn
+
+    w = make_workload(args)
+    X_host = torch.from_numpy(w.P).pin_memory()
+    X = X_host.cuda()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(stats=True):
+        ix = snn.Index(X)
+        out = ix.query(None, w.R, precision=args.precision, stats=stats)
+        return ix, out
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    mine, total_k = count_launches(lambda: step(stats=True))
+
+    clocks = ClockSampler(local)
+    per_step, score_ms, stats_list = [], [], []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ix, out = step(stats=True)
+        e1.record(stream)
+        e1.synchronize()
+        per_step.append(e0.elapsed_time(e1))
+        score_ms.append(out.stats["ms_score"])
+        stats_list.append(out.stats)
+        del ix, out
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    total_ms = float(np.sum(per_step))
+    t_max = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms_step = float(t_max.item()) / args.steps
+    value = world * w.m / (ms_step / 1e3)
+
+    # end to end through host buffers: pinned X in, CSR out, every step
+    e2e_ms, h2d, d2h = [], 0, 0
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Xd = X_host.to("cuda", non_blocking=True)
+        ix = snn.Index(Xd)
+        out = ix.query(None, w.R, precision=args.precision)
+        off_h = out.offsets.cpu()
+        idx_h = out.indices.cpu()
+        d2_h = out.dist2.cpu()
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        h2d = X_host.numel() * 4
+        d2h = off_h.numel() * 8 + idx_h.numel() * 4 + d2_h.numel() * 4
+        del ix, out, Xd
+
+    st = stats_list[-1]
+    peaks, src = load_peaks()
+    sm = float(np.mean(score_ms))
+    flops = 2.0 * w.d * st["candidates"]
+    achieved = flops / (sm / 1e3) / 1e12
+    line = {
+        "metric": "exact radius queries/s (self-join, FP32 rejection + FP64 decision)",
+        "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": workload_config(args, w),
+        "pairs_scored_per_s": st["band_pairs"] / (ms_step / 1e3),
+        "candidate_pairs_per_s": st["candidates"] / (ms_step / 1e3),
+        "nnz": st["nnz"], "candidates": st["candidates"], "band_pairs": st["band_pairs"],
+        "survivors": st["survivors"],
+        "recheck_fraction": (st["survivors"] - st["nnz"]) / max(1, st["candidates"]),
+        "phase_ms": {k: st[k] for k in ("ms_prep", "ms_score", "ms_recheck", "ms_csr")},
+        "roofline": {"kernel": "k_score_fp32_single", "bound": "alu", "achieved": achieved,
+                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)",
+                     "algorithmic": "2d flop per candidate pair (Eq. (4))"},
+        "clocks": clk,
+        "gpu_launches": mine * args.steps,
+        "gpu_launches_per_step": {"snn": mine, "all": total_k},
+        "e2e": {"value": w.m / (np.median(e2e_ms) / 1e3), "unit": "queries/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+    }
+    if rank == 0:
+        if args.cpu_baseline:
+            line["cpu_baseline"] = cpu_oracle_sample(w, budget_s=args.ref_budget)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="gmm_aniso")
+    ap.add_argument("--n", type=int, default=0)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--ref-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * snn.h -- C ABI of libsnn: exact fixed-radius neighbour search by sorting
+ * (SNN, Chen & Guettel, arXiv 2212.07679) on one NVIDIA GB300 (sm_103a).
+ *
+ * Problem (Section 3, Section 3.2): given points p_1..p_n in R^d, a query q
+ * and a radius R, return every i with ||p_i - q|| <= R (inclusive), and the
+ * squared distances (Section 3: "can also return the corresponding
+ * distances").
+ *
+ * Exactness contract.  A point j is reported for query q iff the FP64 value
+ *     S(j, q) = sum_{k=0..d-1} (p_jk - q_k)^2
+ * (FP32 inputs widened exactly, ascending k, every operation rounded to
+ * nearest, no fused multiply-add) satisfies S <= fl64(R*R); the reported
+ * squared distance is (float)S.  Faster low-precision scoring only rejects
+ * pairs that a rigorous rounding bound proves to be outside the radius; every
+ * other pair is decided by S itself.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named "device" are CUDA device pointers on the current device;
+ *    "host" pointers are ordinary host memory.
+ *  - Points and queries are FP32, row-major, with a leading dimension (row
+ *    stride, in elements) >= d.  The library reads them during the call only
+ *    and never retains them.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  All device work of a call is ordered on that stream.  Calls
+ *    that must size their outputs synchronise the stream once to read a count.
+ *  - Every function returns a status and never aborts, traps or prints.  On a
+ *    non-OK status, snn_last_error() gives a message for the calling thread
+ *    and no output is owned by the caller.
+ *  - Limits: 1 <= d <= 4096, 1 <= n < 2^31, m < 2^31, total neighbour pairs
+ *    of one call < 2^31 (SNN_ENOTSUP beyond that).
+ */
+#ifndef SNN_H
+#define SNN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SNN_OK = 0,
+    SNN_EINVAL = 1,     /* invalid argument, or NaN/Inf in the data        */
+    SNN_ENOMEM = 2,     /* device or host allocation failed                */
+    SNN_ECUDA = 3,      /* a CUDA runtime call failed                      */
+    SNN_ETIMEOUT = 4,   /* a bounded device wait gave up                   */
+    SNN_EOVERFLOW = 5,  /* a device buffer stayed too small after a retry  */
+    SNN_ENOTSUP = 6     /* size or feature beyond this build's limits      */
+} snn_status;
+
+/* Arithmetic used to reject candidate pairs before the exact FP64 decision
+ * (Section 4, Eq. (4): x_j^T x_j/2 - x_j^T x_q <= (R^2 - x_q^T x_q)/2).
+ * The output is identical for every precision; only the speed differs. */
+typedef enum {
+    SNN_PREC_FP32 = 0,      /* FP32 CUDA-core dot products                  */
+    SNN_PREC_BF16 = 1,      /* BF16 tcgen05 tensor-core dot products        */
+    SNN_PREC_FP8E4M3 = 2    /* FP8 e4m3 with per-row scale (not yet built)  */
+} snn_precision;
+
+/* Opaque index (Algorithm 1 output): mean mu, first principal direction v1,
+ * points sorted by their score alpha_i = (p_i - mu)^T v1, halved squared
+ * norms of the centred points, and the sort permutation.  Library-owned;
+ * release with snn_index_free. */
+typedef struct snn_index snn_index;
+
+/* Neighbour lists in CSR form.  Row r (r = 0..m-1) holds the neighbours of
+ * query r at indices[offsets[r] .. offsets[r+1]-1], as ORIGINAL point ids
+ * (row numbers of the X given to snn_index_build) in ascending order, with
+ * dist2[] the matching (float)S.  All three arrays are DEVICE memory
+ * allocated by the library; release each with snn_free.  offsets has m+1
+ * entries; indices/dist2 are NULL when nnz == 0. */
+typedef struct {
+    int64_t m;
+    int64_t nnz;
+    int64_t *offsets;
+    int32_t *indices;
+    float *dist2;
+} snn_csr;
+
+/* Optional per-call counters (pass NULL to skip; a non-NULL pointer adds a
+ * few small kernels and one extra stream synchronisation).
+ *  candidates  sum over queries of |J_q|, the candidate range of Algorithm 2
+ *              step 4 (with the rounding-safe widening);
+ *  band_pairs  pairs actually scored (query tiles score the union of their
+ *              queries' ranges, Section 4's gemm over the union of J);
+ *  survivors   pairs the low-precision test could not reject, all of which
+ *              were decided exactly in FP64 (recheck count);
+ *  nnz         neighbour pairs returned;
+ *  ms_*        device time of the phases (CUDA events on `stream`). */
+typedef struct {
+    int64_t candidates;
+    int64_t band_pairs;
+    int64_t survivors;
+    int64_t nnz;
+    float ms_prep;
+    float ms_score;
+    float ms_recheck;
+    float ms_csr;
+} snn_query_stats;
+
+/* Algorithm 1 (Section 3.1): centre, first principal direction, scores,
+ * sort, halved norms.
+ *  X      device, n x d FP32 row-major, row stride ld (elements, >= d).
+ *  out    host pointer receiving a new index (caller frees with
+ *         snn_index_free).
+ * Errors: SNN_EINVAL for n < 1, d < 1, d > 4096, ld < d, n >= 2^31, X NULL or
+ * any NaN/Inf in X; SNN_ENOMEM / SNN_ECUDA on device failures.  Synchronises
+ * `stream` once (to check the data for NaN/Inf). */
+snn_status snn_index_build(const float *X, int64_t n, int32_t d, int64_t ld,
+                           void *stream, snn_index **out);
+
+/* Algorithm 2 (Section 3.2) for m queries at once (Section 4: one gemm over
+ * the union of candidate ranges of a tile of queries sorted by score).
+ *  Q      device, m x d FP32 row-major, stride ldq; NULL means the self-join:
+ *         the queries are the index's own points, row r of the result is
+ *         point r (m and ldq are then ignored).
+ *  R      radius, finite and >= 0 (double); the test is S <= fl64(R*R).
+ *  prec   rejection arithmetic (see snn_precision).
+ *  out    host struct receiving library-allocated device arrays.
+ *  stats  optional host struct (NULL to skip).
+ * Errors: SNN_EINVAL for a NULL index/out, m < 0, ldq < d, R < 0 or
+ * non-finite, NaN/Inf in Q; SNN_ENOTSUP for an unavailable precision or more
+ * than 2^31-1 result pairs; SNN_ENOMEM / SNN_ECUDA on device failures.
+ * m == 0 returns SNN_OK with offsets = {0}. */
+snn_status snn_query_radius(const snn_index *idx, const float *Q, int64_t m, int64_t ldq,
+                            double R, snn_precision prec, void *stream,
+                            snn_csr *out, snn_query_stats *stats);
+
+/* Many independent (index, queries, radius) problems in one call (ragged n,
+ * d and m).  Arrays of length nsets; Q[s] may be NULL (self-join of set s);
+ * ldq[s] is ignored for a self-join.  out[s] receives the CSR of set s.
+ * Errors: as snn_query_radius for each set; on error no out[s] is owned by
+ * the caller. */
+snn_status snn_query_radius_batch(int32_t nsets, const snn_index *const *idx,
+                                  const float *const *Q, const int64_t *m,
+                                  const int64_t *ldq, const double *R,
+                                  snn_precision prec, void *stream, snn_csr *out);
+
+/* DBSCAN with SNN as its neighbour search (Section 6.4).
+ *  X        device, n x d FP32, stride ld.
+ *  eps      neighbourhood radius (inclusive, S <= fl64(eps*eps)).
+ *  min_pts  a point is core iff its eps-neighbourhood, itself included,
+ *           has >= min_pts points.
+ *  labels   device, n int32 (caller-allocated): -1 for noise, otherwise the
+ *           smallest point id of the point's cluster.  Clusters are the
+ *           connected components of core points joined by neighbour pairs;
+ *           a non-core point with a core neighbour joins the cluster of its
+ *           smallest-id core neighbour.
+ *  is_core  device, n uint8 (caller-allocated): 1 for core points.
+ * Errors: as snn_index_build, plus SNN_EINVAL for eps < 0/non-finite or
+ * min_pts < 1, or NULL outputs. */
+snn_status snn_dbscan(const float *X, int64_t n, int32_t d, int64_t ld, double eps,
+                      int32_t min_pts, snn_precision prec, void *stream,
+                      int32_t *labels, uint8_t *is_core);
+
+/* Read-only view of an index's device arrays (for inspection and tests).
+ * All pointers are device memory owned by the index and valid until
+ * snn_index_free.  alpha is sorted ascending; order[r] is the original id of
+ * sorted position r. */
+typedef struct {
+    int64_t n;
+    int32_t d;
+    int32_t dp;              /* padded row stride of the sorted copies      */
+    const double *mu;        /* d, FP64 column means                        */
+    const double *v1;        /* d, FP64 unit first principal direction      */
+    const float *alpha;      /* n, sorted FP32 scores                       */
+    const int32_t *order;    /* n, original id of each sorted position      */
+    const float *points;     /* n x dp, raw points in sorted order          */
+    double alpha_err;        /* bound on |computed alpha_i - exact alpha_i| */
+} snn_index_view;
+
+snn_status snn_index_get_view(const snn_index *idx, snn_index_view *view);
+
+/* Releases a device buffer returned in an snn_csr (NULL is a no-op). */
+void snn_free(void *p);
+
+/* Releases an index and all its device memory (NULL is a no-op). */
+void snn_index_free(snn_index *idx);
+
+/* Message for the calling thread's last non-OK status ("" if none). */
+const char *snn_last_error(void);
+
+/* Library version string. */
+const char *snn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SNN_H */

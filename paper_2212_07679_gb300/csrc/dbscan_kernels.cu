@@ -1,0 +1,90 @@
+// DBSCAN on the SNN self-join (Section 6.4: the neighbour search inside
+// DBSCAN is replaced by SNN).  From the CSR of eps-neighbourhoods (self
+// included): core flags, union-find over core-core neighbour pairs (hooking
+// the larger root under the smaller with atomicCAS, path halving), border
+// points joined to the cluster of their smallest-id core neighbour, and
+// cluster labels canonicalised to the smallest member id.
+#include "dbscan_kernels.cuh"
+
+namespace snn {
+
+__global__ void k_db_core(const int64_t *__restrict__ offsets, int64_t n, int32_t min_pts,
+                          uint8_t *__restrict__ core, int32_t *__restrict__ parent) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    core[i] = (offsets[i + 1] - offsets[i]) >= min_pts ? 1 : 0;
+    parent[i] = (int32_t)i;
+}
+
+__device__ __forceinline__ int32_t uf_find(int32_t *parent, int32_t x) {
+    // path halving; every write moves a pointer to an ancestor, so concurrent
+    // finds and hooks stay consistent
+    int32_t p = parent[x];
+    while (p != x) {
+        const int32_t g = parent[p];
+        if (g != p) parent[x] = g;
+        x = p;
+        p = parent[x];
+    }
+    return x;
+}
+
+// One warp per core point i: unions i with each core neighbour j < i.
+__global__ void k_db_union(const int64_t *__restrict__ offsets, const int32_t *__restrict__ idx,
+                           int64_t n, const uint8_t *__restrict__ core,
+                           int32_t *__restrict__ parent) {
+    const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= n || !core[i]) return;
+    const int64_t o0 = offsets[i], o1 = offsets[i + 1];
+    for (int64_t o = o0 + lane; o < o1; o += 32) {
+        const int32_t j = idx[o];
+        if (j >= i || !core[j]) continue;
+        int32_t a = (int32_t)i, b = j;
+        for (;;) {
+            a = uf_find(parent, a);
+            b = uf_find(parent, b);
+            if (a == b) break;
+            const int32_t hi = max(a, b), lo = min(a, b);
+            if (atomicCAS(&parent[hi], hi, lo) == hi) break;
+            a = hi;
+            b = lo;
+        }
+    }
+}
+
+// root[i] for cores; for border points the root of the smallest-id core
+// neighbour (row ids are ascending); -1 for noise.  Also the label candidate.
+__global__ void k_db_assign(const int64_t *__restrict__ offsets, const int32_t *__restrict__ idx,
+                            int64_t n, const uint8_t *__restrict__ core,
+                            int32_t *__restrict__ parent, int32_t *__restrict__ owner,
+                            int32_t *__restrict__ minid) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t r = -1;
+    if (core[i]) {
+        r = uf_find(parent, (int32_t)i);
+    } else {
+        for (int64_t o = offsets[i]; o < offsets[i + 1]; ++o) {
+            const int32_t j = idx[o];
+            if (core[j]) { r = uf_find(parent, j); break; }
+        }
+    }
+    owner[i] = r;
+    if (r >= 0) atomicMin(&minid[r], (int32_t)i);
+}
+
+__global__ void k_db_init_minid(int32_t *__restrict__ minid, int64_t n) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) minid[i] = INT32_MAX;
+}
+
+__global__ void k_db_label(const int32_t *__restrict__ owner, const int32_t *__restrict__ minid,
+                           int64_t n, int32_t *__restrict__ labels) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t r = owner[i];
+    labels[i] = r >= 0 ? minid[r] : -1;
+}
+
+}  // namespace snn

@@ -1,0 +1,444 @@
+// Index phase kernels (Algorithm 1, Section 3.1):
+//   column means mu (FP64 accumulation, NaN/Inf check),
+//   centred Gram matrix C = (X - mu)^T (X - mu) for the first principal
+//   direction (Eq. (1): v1 is the dominant right singular vector of X, i.e.
+//   the dominant eigenvector of C),
+//   v1 by repeated squaring of C / trace(C) followed by FP64 power steps and
+//   FP64 normalisation,
+//   scores alpha_i = x_i^T v1 with a per-point rounding bound,
+//   gather of the sorted copies and halved squared norms xbar_i = x_i^T x_i/2.
+#include "index_kernels.cuh"
+
+namespace snn {
+
+// ------------------------------------------------------------ mean (K1)
+// Block b sums rows [b*rows, (b+1)*rows) of every column into part[b][c]
+// (FP64, fixed order: deterministic).  Thread (cx, ry) owns columns
+// cx, cx+TX, ... and rows ry, ry+TY, ...
+__global__ void k_colsum_partial(const float *__restrict__ X, int64_t n, int d, int64_t ld,
+                                 int64_t rows, double *__restrict__ part, int *__restrict__ bad) {
+    extern __shared__ double sh[];   // [TY][TX]
+    const int TX = d < 32 ? d : 32;
+    const int TY = blockDim.x / TX;
+    const int t = threadIdx.x;
+    const int cx = t % TX, ry = t / TX;
+    const int64_t r0 = int64_t(blockIdx.x) * rows;
+    const int64_t r1 = min(n, r0 + rows);
+    int badl = 0;
+    for (int c0 = 0; c0 < d; c0 += TX) {
+        double acc = 0.0;
+        const int c = c0 + cx;
+        if (ry < TY && c < d) {
+            for (int64_t r = r0 + ry; r < r1; r += TY) {
+                float x = X[r * ld + c];
+                badl |= !isfinite(x);
+                acc += (double)x;
+            }
+        }
+        if (ry < TY) sh[ry * TX + cx] = acc;
+        __syncthreads();
+        if (t < TX && c0 + t < d) {
+            double s = 0.0;
+            for (int y = 0; y < TY; ++y) s += sh[y * TX + t];
+            part[int64_t(blockIdx.x) * d + c0 + t] = s;
+        }
+        __syncthreads();
+    }
+    if (badl) atomicOr(bad, 1);
+}
+
+__global__ void k_mean_final(const double *__restrict__ part, int nb, int d, int64_t n,
+                             double *__restrict__ mu64, float *__restrict__ mu32) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[int64_t(b) * d + c];
+    double m = s / (double)n;
+    mu64[c] = m;
+    mu32[c] = (float)m;
+}
+
+// ------------------------------------------------------------ Gram (K2)
+// Tiles of 64 x 64 entries of C over a chunk of rows; only tiles with
+// tj >= ti are computed (C is symmetric).  part[chunk][i][j], FP32 sums of
+// FP32 products of centred values x = fl32(p - mu).
+constexpr int kGT = 64;
+constexpr int kGK = 16;
+
+__global__ void __launch_bounds__(256)
+k_gram_partial(const float *__restrict__ X, int64_t n, int d, int64_t ld,
+               const float *__restrict__ mu32, int64_t rows, int ntile,
+               float *__restrict__ part) {
+    const int ti = blockIdx.x / ntile, tj = blockIdx.x % ntile;
+    if (tj < ti) return;
+    __shared__ float A[kGK][kGT + 4];
+    __shared__ float B[kGK][kGT + 4];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t r0 = int64_t(blockIdx.y) * rows;
+    const int64_t r1 = min(n, r0 + rows);
+    float acc[4][4] = {};
+    for (int64_t rb = r0; rb < r1; rb += kGK) {
+        for (int e = threadIdx.x; e < kGK * kGT; e += 256) {
+            const int kk = e / kGT, c = e % kGT;
+            const int64_t r = rb + kk;
+            const int ci = ti * kGT + c, cj = tj * kGT + c;
+            float a = 0.f, b = 0.f;
+            if (r < r1) {
+                if (ci < d) a = X[r * ld + ci] - mu32[ci];
+                if (cj < d) b = X[r * ld + cj] - mu32[cj];
+            }
+            A[kk][c] = a;
+            B[kk][c] = b;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kGK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = A[kk][ty * 4 + u];
+                b[u] = B[kk][tx * 4 + u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int w = 0; w < 4; ++w) acc[u][w] = fmaf(a[u], b[w], acc[u][w]);
+        }
+        __syncthreads();
+    }
+    float *out = part + int64_t(blockIdx.y) * d * d;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int i = ti * kGT + ty * 4 + u, j = tj * kGT + tx * 4 + w;
+            if (i < d && j < d) out[int64_t(i) * d + j] = acc[u][w];
+        }
+}
+
+// C64[i][j] = sum over chunks (FP64), upper triangle mirrored.
+__global__ void k_gram_reduce(const float *__restrict__ part, int nchunk, int d,
+                              double *__restrict__ C) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= int64_t(d) * d) return;
+    const int i = int(e / d), j = int(e % d);
+    const int a = min(i, j), b = max(i, j);
+    double s = 0.0;
+    for (int c = 0; c < nchunk; ++c) s += (double)part[int64_t(c) * d * d + int64_t(a) * d + b];
+    C[e] = s;
+}
+
+// ------------------------------------------------- first direction (K3)
+// Small d: one CTA.  M = C / trace(C) in FP32 shared memory, squared
+// kSquarings times (M <- M*M / trace), so M tends to v1 v1^T; the column with
+// the largest diagonal entry seeds FP64 power steps v <- C v / ||C v||.
+constexpr int kSquarings = 12;
+constexpr int kPowerSteps = 4;
+
+__device__ double block_sum_d(double v, double *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += red[w];   // fixed order in every thread
+    __syncthreads();
+    return s;
+}
+
+__device__ float block_sum_f(float v, float *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    float s = 0.f;
+    for (int w = 0; w < nw; ++w) s += red[w];
+    __syncthreads();
+    return s;
+}
+
+__global__ void __launch_bounds__(1024)
+k_pc_small(const double *__restrict__ C, int d, double *__restrict__ v64, float *__restrict__ v32) {
+    extern __shared__ unsigned char smem[];
+    double *v = reinterpret_cast<double *>(smem);          // d
+    double *w = v + d;                                     // d
+    double *red = w + d;                                   // 32
+    float *redf = reinterpret_cast<float *>(red + 32);     // 32
+    float *M = redf + 32;                                  // d*d
+    float *T = M + d * d;                                  // d*d
+    const int t = threadIdx.x, nt = blockDim.x;
+    const int dd = d * d;
+
+    double tr = 0.0;
+    for (int i = 0; i < d; ++i) tr += C[int64_t(i) * d + i];
+    const bool degenerate = !(tr > 0.0) || !isfinite(tr);
+    if (!degenerate) {
+        for (int e = t; e < dd; e += nt) M[e] = (float)(C[e] / tr);
+        __syncthreads();
+        for (int it = 0; it < kSquarings; ++it) {
+            for (int e = t; e < dd; e += nt) {
+                const int i = e / d, j = e % d;
+                float s = 0.f;
+                for (int k = 0; k < d; ++k) s = fmaf(M[i * d + k], M[k * d + j], s);
+                T[e] = s;
+            }
+            __syncthreads();
+            float part = 0.f;
+            for (int i = t; i < d; i += nt) part += T[i * d + i];
+            const float trT = block_sum_f(part, redf);
+            if (!(trT > 0.f) || !isfinite(trT)) break;
+            const float inv = 1.f / trT;
+            for (int e = t; e < dd; e += nt) M[e] = T[e] * inv;
+            __syncthreads();
+        }
+        // column with the largest diagonal entry
+        int jbest = 0;
+        float best = -1.f;
+        for (int j = 0; j < d; ++j) {
+            float x = M[j * d + j];
+            if (x > best) { best = x; jbest = j; }
+        }
+        for (int i = t; i < d; i += nt) v[i] = (double)M[i * d + jbest];
+        __syncthreads();
+    } else {
+        for (int i = t; i < d; i += nt) v[i] = (i == 0) ? 1.0 : 0.0;
+        __syncthreads();
+    }
+    // FP64 power steps on C (skipped for C = 0) and FP64 normalisation
+    for (int it = 0; it < (degenerate ? 0 : kPowerSteps); ++it) {
+        for (int i = t; i < d; i += nt) {
+            double s = 0.0;
+            for (int k = 0; k < d; ++k) s += C[int64_t(i) * d + k] * v[k];
+            w[i] = s;
+        }
+        __syncthreads();
+        double part = 0.0;
+        for (int i = t; i < d; i += nt) part += w[i] * w[i];
+        const double nrm2 = block_sum_d(part, red);
+        if (!(nrm2 > 0.0) || !isfinite(nrm2)) break;
+        const double inv = 1.0 / sqrt(nrm2);
+        for (int i = t; i < d; i += nt) v[i] = w[i] * inv;
+        __syncthreads();
+    }
+    double part = 0.0;
+    for (int i = t; i < d; i += nt) part += v[i] * v[i];
+    double nrm2 = block_sum_d(part, red);
+    if (!(nrm2 > 0.0) || !isfinite(nrm2)) {
+        for (int i = t; i < d; i += nt) v[i] = (i == 0) ? 1.0 : 0.0;
+        __syncthreads();
+        nrm2 = 1.0;
+    }
+    const double inv = 1.0 / sqrt(nrm2);
+    for (int i = t; i < d; i += nt) {
+        const double x = v[i] * inv;
+        v64[i] = x;
+        v32[i] = (float)x;
+    }
+}
+
+// Large d: the same steps with grid-wide kernels.
+__global__ void k_pc_init(const double *__restrict__ C, int d, float *__restrict__ M,
+                          double *__restrict__ trace_out) {
+    // one block computes trace(C), then the grid-stride scaling happens in a
+    // second launch (k_scale_by_trace)
+    __shared__ double red[32];
+    double part = 0.0;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) part += C[int64_t(i) * d + i];
+    const double tr = block_sum_d(part, red);
+    if (threadIdx.x == 0) *trace_out = tr;
+}
+
+__global__ void k_scale_from_double(const double *__restrict__ C, int64_t count,
+                                    const double *__restrict__ tr, float *__restrict__ M) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= count) return;
+    const double t = *tr;
+    M[e] = (t > 0.0 && isfinite(t)) ? (float)(C[e] / t) : 0.f;
+}
+
+// T = M * M (d x d, FP32), 64 x 64 tiles, 4 x 4 per thread.
+__global__ void __launch_bounds__(256)
+k_square(const float *__restrict__ M, int d, float *__restrict__ T) {
+    __shared__ float As[kGK][kGT + 4];
+    __shared__ float Bs[kGK][kGT + 4];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int i0 = blockIdx.y * kGT, j0 = blockIdx.x * kGT;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < d; k0 += kGK) {
+        for (int e = threadIdx.x; e < kGK * kGT; e += 256) {
+            const int kk = e / kGT, c = e % kGT;
+            const int k = k0 + kk;
+            As[kk][c] = (k < d && i0 + c < d) ? M[int64_t(i0 + c) * d + k] : 0.f;
+            Bs[kk][c] = (k < d && j0 + c < d) ? M[int64_t(k) * d + j0 + c] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kGK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = As[kk][ty * 4 + u];
+                b[u] = Bs[kk][tx * 4 + u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int w = 0; w < 4; ++w) acc[u][w] = fmaf(a[u], b[w], acc[u][w]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int i = i0 + ty * 4 + u, j = j0 + tx * 4 + w;
+            if (i < d && j < d) T[int64_t(i) * d + j] = acc[u][w];
+        }
+}
+
+// M = T / trace(T) (one block computes the trace into *scale first).
+__global__ void k_trace_f(const float *__restrict__ T, int d, float *__restrict__ scale) {
+    __shared__ float red[32];
+    float part = 0.f;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) part += T[int64_t(i) * d + i];
+    const float tr = block_sum_f(part, red);
+    if (threadIdx.x == 0) *scale = (tr > 0.f && isfinite(tr)) ? 1.f / tr : 0.f;
+}
+
+__global__ void k_scale_f(const float *__restrict__ T, int64_t count, const float *__restrict__ scale,
+                          float *__restrict__ M) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= count) return;
+    const float s = *scale;
+    // a zero scale (vanished trace) keeps the previous M
+    if (s > 0.f) M[e] = T[e] * s;
+}
+
+__global__ void k_pick_column(const float *__restrict__ M, int d, const double *__restrict__ tr,
+                              double *__restrict__ v) {
+    __shared__ int jbest;
+    if (threadIdx.x == 0) {
+        int jb = 0;
+        float best = -1.f;
+        for (int j = 0; j < d; ++j) {
+            float x = M[int64_t(j) * d + j];
+            if (x > best) { best = x; jb = j; }
+        }
+        jbest = jb;
+    }
+    __syncthreads();
+    const bool degenerate = !(*tr > 0.0) || !isfinite(*tr);
+    for (int i = threadIdx.x; i < d; i += blockDim.x)
+        v[i] = degenerate ? (i == 0 ? 1.0 : 0.0) : (double)M[int64_t(i) * d + jbest];
+}
+
+// w = C v (FP64), one warp per row.
+__global__ void k_matvec64(const double *__restrict__ C, int d, const double *__restrict__ v,
+                           double *__restrict__ w) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= d) return;
+    double s = 0.0;
+    for (int k = lane; k < d; k += 32) s += C[int64_t(warp) * d + k] * v[k];
+    for (int o = 16; o; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) w[warp] = s;
+}
+
+// v = w / ||w|| (FP64); keeps v when w vanished.  final != 0 also writes v32.
+__global__ void k_normalise64(const double *__restrict__ w, int d, double *__restrict__ v,
+                              float *__restrict__ v32, int final_) {
+    __shared__ double red[32];
+    double part = 0.0;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) part += w[i] * w[i];
+    const double nrm2 = block_sum_d(part, red);
+    const bool ok = nrm2 > 0.0 && isfinite(nrm2);
+    const double inv = ok ? 1.0 / sqrt(nrm2) : 1.0;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) {
+        double x = ok ? w[i] * inv : v[i];
+        v[i] = x;
+        if (final_) v32[i] = (float)x;
+    }
+}
+
+// ------------------------------------------------------ projection (K4)
+// alpha_i = fl32(sum_k x_k v_k) with x_k = fl32(p_ik - mu_k) and FP32 FMA
+// accumulation.  |alpha_hat - alpha| <= (d+4) u32 sum_k |x_k||v_k| (1.01):
+// centring (u32 + 2 u64)|x_k|, v rounding u32 |v_k|, accumulation gamma_d.
+// Writes the sort key of alpha and the point id; *eps_max gets the largest
+// bound.  One thread per point (d <= 32) or one warp per point.
+__global__ void k_project(const float *__restrict__ X, int64_t n, int d, int64_t ld,
+                          const double *__restrict__ mu64, const float *__restrict__ v32,
+                          uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                          float *__restrict__ eps_max, int *__restrict__ bad) {
+    const bool warp_mode = d > 32;
+    const int64_t gt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t i = warp_mode ? gt >> 5 : gt;
+    const int lane = warp_mode ? int(threadIdx.x & 31) : 0;
+    const int step = warp_mode ? 32 : 1;
+    if (i >= n) return;   // whole warps exit together in warp mode
+    float a = 0.f, b = 0.f;
+    int badl = 0;
+    for (int k = lane; k < d; k += step) {
+        const float p = X[i * ld + k];
+        badl |= !isfinite(p);
+        const float x = (float)((double)p - mu64[k]);
+        a = fmaf(x, v32[k], a);
+        b = fmaf(fabsf(x), fabsf(v32[k]), b);
+    }
+    if (warp_mode) {
+        for (int o = 16; o; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+            badl |= __shfl_down_sync(0xffffffffu, badl, o);
+        }
+    }
+    if (lane == 0) {
+        const float eps = (float)(d + 4) * kU32 * 1.01f * b + 1e-37f;
+        keys[i] = float_to_key(a);
+        vals[i] = (uint32_t)i;
+        atomic_max_nonneg(eps_max, eps);
+        if (badl) atomicOr(bad, 1);
+    }
+}
+
+// ---------------------------------------------------------- gather (K6)
+// Sorted position r takes point order[r]: raw row (zero-padded to dp),
+// centred FP32 row, score, halved squared norm xbar = fl32(sum x_k^2)/2 and an
+// upper bound on ||x||.  Padding entries are zero in both copies.
+__global__ void k_gather(const uint32_t *__restrict__ skeys, const uint32_t *__restrict__ order,
+                         const float *__restrict__ X, int64_t n, int d, int64_t ld, int dp,
+                         const double *__restrict__ mu64, float *__restrict__ alpha,
+                         int32_t *__restrict__ order_out, float *__restrict__ praw,
+                         float *__restrict__ xc, float *__restrict__ hx,
+                         float *__restrict__ nrm) {
+    const bool warp_mode = d > 32;
+    const int64_t gt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t r = warp_mode ? gt >> 5 : gt;
+    const int lane = warp_mode ? int(threadIdx.x & 31) : 0;
+    const int step = warp_mode ? 32 : 1;
+    if (r >= n) return;
+    const int64_t i = order[r];
+    float s = 0.f;
+    for (int k = lane; k < dp; k += step) {
+        float p = 0.f, x = 0.f;
+        if (k < d) {
+            p = X[i * ld + k];
+            x = (float)((double)p - mu64[k]);
+        }
+        praw[r * dp + k] = p;
+        xc[r * dp + k] = x;
+        s = fmaf(x, x, s);
+    }
+    if (warp_mode)
+        for (int o = 16; o; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        alpha[r] = key_to_float(skeys[r]);
+        order_out[r] = (int32_t)i;
+        hx[r] = 0.5f * s;
+        // ||x|| <= sqrt(s (1 + gamma_d)) (1 + u): inflate by (d+4)u
+        nrm[r] = sqrtf(s) * (1.f + (float)(d + 4) * kU32);
+    }
+}
+
+}  // namespace snn

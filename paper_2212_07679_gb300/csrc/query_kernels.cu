@@ -1,0 +1,461 @@
+// Query-phase kernels (Algorithm 2, Section 3.2; Section 4).
+//
+// Queries are sorted by score and cut into tiles of kBQ; a tile scores the
+// union of its queries' candidate ranges (a contiguous band of the sorted
+// data, Eq. (2) and Section 4's gemm over the union of J) in chunks of kBR
+// rows.  The FP32 score is the left side of Eq. (4), xbar_j - x_j^T x_q, from
+// centred FP32 rows; a pair is rejected only when a rigorous bound proves
+// ||p_j - q|| > R for the FP64 definition; every other pair ("survivor") is
+// decided by the FP64 direct form Eq. (3) in k_recheck, which also yields the
+// reported squared distance.
+#include "query_kernels.cuh"
+
+namespace snn {
+
+// Per sorted query i, the part of the rejection threshold (halved units) that
+// does not depend on the band chunk:
+//   thrA_i >= (Rx + e_data + e_i)^2 / 2 - ||y_i||^2 / 2,
+// where Rx bounds the largest true distance the FP64 test can accept,
+// e_data / e_i bound the centring error norms of a data row / this query, and
+// hy_i = fl32(||y_i||^2)/2 underestimates ||y_i||^2/2 by at most gamma_d.
+__global__ void k_query_consts(const float *__restrict__ hy, const float *__restrict__ qn,
+                               int64_t m, int d, double Rx, double e_data,
+                               float *__restrict__ thrA) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const double ei = 1.0001 * (double)kU32 * (double)qn[i];
+    const double r = Rx + e_data + ei;
+    const double hy_low = (double)hy[i] * (1.0 - 1.05 * (d + 2) * (double)kU32);
+    const double a = 0.5 * r * r - hy_low;
+    thrA[i] = __double2float_ru(a + 4.0 * kU64 * (fabs(a) + 0.5 * r * r + (double)hy[i]));
+}
+
+__device__ __forceinline__ int64_t lower_bound_ge(const float *__restrict__ a, int64_t n, double x) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if ((double)a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+__device__ __forceinline__ int64_t upper_bound_gt(const float *__restrict__ a, int64_t n, double x) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if ((double)a[mid] <= x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Candidate band of tile t: every data row whose score is within W of the
+// score of some query of the tile (Algorithm 2 step 4 for all of them at once).
+// W = Wbase + eps_d + eps_q covers |alpha_j - alpha_q| <= ||v1|| ||p_j - q||
+// (Eq. (2)) for every pair the FP64 test can accept, plus the rounding bounds
+// of both computed scores.
+__global__ void k_tile_band(const float *__restrict__ qalpha, int64_t m,
+                            const float *__restrict__ alpha, int64_t n, double Wbase,
+                            const float *__restrict__ eps_d, const float *__restrict__ eps_q,
+                            int64_t *__restrict__ tile_lo, int64_t *__restrict__ tile_hi,
+                            int64_t *__restrict__ items, int ntiles,
+                            unsigned long long *__restrict__ band_pairs) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const double W = Wbase + (double)*eps_d + (double)*eps_q;
+    const int64_t q0 = int64_t(t) * kBQ;
+    const int64_t q1 = min(m, q0 + kBQ) - 1;
+    const double a0 = (double)qalpha[q0], a1 = (double)qalpha[q1];
+    const double lo_x = (a0 - W) - 4.0 * kU64 * (fabs(a0) + W);
+    const double hi_x = (a1 + W) + 4.0 * kU64 * (fabs(a1) + W);
+    const int64_t lo = lower_bound_ge(alpha, n, lo_x);
+    const int64_t hi = max(lo, upper_bound_gt(alpha, n, hi_x));
+    tile_lo[t] = lo;
+    tile_hi[t] = hi;
+    const int64_t chunks = cdiv(hi - lo, kBR);
+    items[t] = cdiv(chunks, kChunksPerItem);
+    if (band_pairs) atomicAdd(band_pairs, (unsigned long long)((hi - lo) * (q1 - q0 + 1)));
+}
+
+// Per-query candidate range sizes |J_q| (statistics only).
+__global__ void k_query_windows(const float *__restrict__ qalpha, int64_t m,
+                                const float *__restrict__ alpha, int64_t n, double Wbase,
+                                const float *__restrict__ eps_d, const float *__restrict__ eps_q,
+                                unsigned long long *__restrict__ cand) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const double W = Wbase + (double)*eps_d + (double)*eps_q;
+    unsigned long long c = 0;
+    if (i < m) {
+        const double a = (double)qalpha[i];
+        const double slack = 4.0 * kU64 * (fabs(a) + W);
+        const int64_t lo = lower_bound_ge(alpha, n, a - W - slack);
+        const int64_t hi = upper_bound_gt(alpha, n, a + W + slack);
+        c = hi > lo ? (unsigned long long)(hi - lo) : 0ull;
+    }
+    for (int o = 16; o; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(cand, c);
+}
+
+// ------------------------------------------------------------ FP32 score
+// 256 threads; thread (tx, ty) owns queries {ty*4+u, 64+ty*4+u} and rows
+// {tx*4+w, 64+tx*4+w}, u, w < 4.  acc starts at -xbar_j and accumulates
+// x_j . y_i with FMA, so acc = -(xbar_j - x_j^T y_i) (Eq. (4) left side).
+// Rounding: |(-acc) - (||x||^2/2 - x.y)| <= c1 (xbar_j + ||x_j|| ||y_i||).
+// A pair survives iff -acc <= thrA_i + c1 (max xbar + max||x|| ||y_i||) over
+// the chunk, i.e. unless the bound proves S > R^2.
+constexpr int kKC = 16;
+constexpr int kScoreThreads = 256;
+
+template <bool kSingle>
+__device__ __forceinline__ void score_body(const ScoreArgs &a) {
+    __shared__ __align__(16) float Qs[kKC][kBQ + 4];
+    __shared__ __align__(16) float Xs[kKC][kBR + 4];
+    __shared__ float s_thrA[kBQ], s_qn[kBQ];
+    __shared__ float s_hx[kBR];
+    __shared__ unsigned s_hxmax, s_nmax;
+    __shared__ long long s_item;
+
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int lane = tid & 31;
+    const int dp = a.x.dp;
+    const int64_t total_items = a.item_off[a.ntiles];
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_item = (long long)atomicAdd(a.work, 1ull);
+        __syncthreads();
+        const int64_t item = s_item;
+        if (item >= total_items) break;
+        // tile of this item: last t with item_off[t] <= item
+        int lo_t = 0, hi_t = a.ntiles;
+        while (hi_t - lo_t > 1) {
+            const int mid = (lo_t + hi_t) >> 1;
+            if (a.item_off[mid] <= item) lo_t = mid; else hi_t = mid;
+        }
+        const int tile = lo_t;
+        const int64_t q0 = int64_t(tile) * kBQ;
+        const int64_t band_lo = a.tile_lo[tile], band_hi = a.tile_hi[tile];
+        const int64_t c_first = (item - a.item_off[tile]) * kChunksPerItem;
+        const int64_t c_end = min(cdiv(band_hi - band_lo, kBR), c_first + kChunksPerItem);
+
+        if (tid < kBQ) {
+            const int64_t q = q0 + tid;
+            s_thrA[tid] = q < a.q.m ? a.thrA[q] : -3.0e38f;   // never survives
+            s_qn[tid] = q < a.q.m ? a.q.nrm[q] : 0.f;
+        }
+        if (kSingle) {
+            // whole query rows fit one k-chunk: stage them once per item
+            for (int e = tid; e < kBQ * (dp / 4); e += kScoreThreads) {
+                const int r = e / (dp / 4), k4 = e % (dp / 4);
+                const int64_t q = q0 + r;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (q < a.q.m) v = *reinterpret_cast<const float4 *>(a.q.xc + q * dp + k4 * 4);
+                Qs[k4 * 4 + 0][r] = v.x;
+                Qs[k4 * 4 + 1][r] = v.y;
+                Qs[k4 * 4 + 2][r] = v.z;
+                Qs[k4 * 4 + 3][r] = v.w;
+            }
+        }
+        for (int64_t c = c_first; c < c_end; ++c) {
+            const int64_t j0 = band_lo + c * kBR;
+            __syncthreads();
+            if (tid == 0) { s_hxmax = 0u; s_nmax = 0u; }
+            __syncthreads();
+            if (tid < kBR) {
+                const int64_t j = j0 + tid;
+                float h = 0.f, nr = 0.f;
+                if (j < band_hi) { h = a.x.hx[j]; nr = a.x.nrm[j]; }
+                s_hx[tid] = h;
+                // block max of non-negative floats through their bit patterns
+                unsigned hb = __float_as_uint(h), nb = __float_as_uint(nr);
+                for (int o = 16; o; o >>= 1) {
+                    hb = max(hb, __shfl_xor_sync(0xffffffffu, hb, o));
+                    nb = max(nb, __shfl_xor_sync(0xffffffffu, nb, o));
+                }
+                if (lane == 0) { atomicMax(&s_hxmax, hb); atomicMax(&s_nmax, nb); }
+            }
+            __syncthreads();
+            float acc[8][8];
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+                const float h = -s_hx[(w < 4 ? 0 : 64) + tx * 4 + (w & 3)];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc[u][w] = h;
+            }
+            for (int k0 = 0; k0 < dp; k0 += kKC) {
+                const int kc = min(kKC, dp - k0);
+                if (!kSingle) {
+                    __syncthreads();
+                    for (int e = tid; e < kBQ * (kc / 4); e += kScoreThreads) {
+                        const int r = e / (kc / 4), k4 = e % (kc / 4);
+                        const int64_t q = q0 + r;
+                        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (q < a.q.m)
+                            v = *reinterpret_cast<const float4 *>(a.q.xc + q * dp + k0 + k4 * 4);
+                        Qs[k4 * 4 + 0][r] = v.x;
+                        Qs[k4 * 4 + 1][r] = v.y;
+                        Qs[k4 * 4 + 2][r] = v.z;
+                        Qs[k4 * 4 + 3][r] = v.w;
+                    }
+                } else {
+                    __syncthreads();
+                }
+                for (int e = tid; e < kBR * (kc / 4); e += kScoreThreads) {
+                    const int r = e / (kc / 4), k4 = e % (kc / 4);
+                    const int64_t j = j0 + r;
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (j < band_hi)
+                        v = *reinterpret_cast<const float4 *>(a.x.xc + j * dp + k0 + k4 * 4);
+                    Xs[k4 * 4 + 0][r] = v.x;
+                    Xs[k4 * 4 + 1][r] = v.y;
+                    Xs[k4 * 4 + 2][r] = v.z;
+                    Xs[k4 * 4 + 3][r] = v.w;
+                }
+                __syncthreads();
+#pragma unroll 4
+                for (int kk = 0; kk < kc; ++kk) {
+                    const float4 qa = *reinterpret_cast<const float4 *>(&Qs[kk][ty * 4]);
+                    const float4 qb = *reinterpret_cast<const float4 *>(&Qs[kk][64 + ty * 4]);
+                    const float4 xa = *reinterpret_cast<const float4 *>(&Xs[kk][tx * 4]);
+                    const float4 xb = *reinterpret_cast<const float4 *>(&Xs[kk][64 + tx * 4]);
+                    const float qv[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
+                    const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+#pragma unroll
+                        for (int w = 0; w < 8; ++w) acc[u][w] = fmaf(qv[u], xv[w], acc[u][w]);
+                }
+            }
+            // epilogue: survivors
+            const float hxmax = __uint_as_float(s_hxmax), nmax = __uint_as_float(s_nmax);
+            unsigned long long mask = 0ull;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int qi = (u < 4 ? 0 : 64) + ty * 4 + (u & 3);
+                float b = a.c1 * fmaf(nmax, s_qn[qi], hxmax);
+                b = b * 1.0000010f;
+                float thr = s_thrA[qi] + b;
+                thr = thr + fabsf(thr) * 1e-6f + 1e-30f;
+                const float neg = -thr;
+#pragma unroll
+                for (int w = 0; w < 8; ++w) {
+                    const int rj = (w < 4 ? 0 : 64) + tx * 4 + (w & 3);
+                    const bool ok = (acc[u][w] >= neg) && (j0 + rj < band_hi);
+                    mask |= (unsigned long long)ok << (u * 8 + w);
+                }
+            }
+            const int cnt = __popcll(mask);
+            if (__any_sync(0xffffffffu, cnt != 0)) {
+                int incl = cnt;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int wtotal = __shfl_sync(0xffffffffu, incl, 31);
+                unsigned long long base = 0;
+                if (lane == 31) base = atomicAdd(a.count, (unsigned long long)wtotal);
+                base = __shfl_sync(0xffffffffu, base, 31);
+                unsigned long long pos = base + (unsigned long long)(incl - cnt);
+                while (mask) {
+                    const int b = __ffsll((long long)mask) - 1;
+                    mask &= mask - 1;
+                    const int u = b >> 3, w = b & 7;
+                    const int qi = (u < 4 ? 0 : 64) + ty * 4 + (u & 3);
+                    const int rj = (w < 4 ? 0 : 64) + tx * 4 + (w & 3);
+                    if (pos < (unsigned long long)a.cap)
+                        a.surv[pos] = make_uint2((unsigned)(q0 + qi), (unsigned)(j0 + rj));
+                    ++pos;
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kScoreThreads, 2) k_score_fp32_single(ScoreArgs a) {
+    score_body<true>(a);
+}
+__global__ void __launch_bounds__(kScoreThreads, 2) k_score_fp32_multi(ScoreArgs a) {
+    score_body<false>(a);
+}
+
+// ------------------------------------------------------- FP64 decision
+// Eq. (3) in the oracle's order: t = p_k - q_k, S = S + t*t, ascending k,
+// round-to-nearest intrinsics so no FMA is formed.  Keeps the pair iff
+// S <= R2 and records (original query row, original point id, (float)S).
+__global__ void k_recheck(const uint2 *__restrict__ surv, int64_t nsurv,
+                          const float *__restrict__ qraw, const int32_t *__restrict__ qorder,
+                          const float *__restrict__ praw, const int32_t *__restrict__ porder,
+                          int d, int dp, double R2, int32_t *__restrict__ rec_row,
+                          int32_t *__restrict__ rec_col, float *__restrict__ rec_d2,
+                          int32_t *__restrict__ counts) {
+    const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (s >= nsurv) return;
+    const uint2 e = surv[s];
+    const float4 *pq = reinterpret_cast<const float4 *>(qraw + int64_t(e.x) * dp);
+    const float4 *pp = reinterpret_cast<const float4 *>(praw + int64_t(e.y) * dp);
+    double S = 0.0;
+    for (int k4 = 0; k4 < dp / 4; ++k4) {
+        const float4 a = pp[k4], b = pq[k4];
+        const float av[4] = {a.x, a.y, a.z, a.w};
+        const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (k4 * 4 + c < d) {
+                const double t = __dsub_rn((double)av[c], (double)bv[c]);
+                S = __dadd_rn(S, __dmul_rn(t, t));
+            }
+        }
+    }
+    if (S <= R2) {
+        const int32_t row = qorder[e.x];
+        rec_row[s] = row;
+        rec_col[s] = porder[e.y];
+        rec_d2[s] = (float)S;
+        atomicAdd(&counts[row], 1);
+    } else {
+        rec_row[s] = -1;
+    }
+}
+
+__global__ void k_counts_to_i64(const int32_t *__restrict__ counts, int64_t m,
+                                int64_t *__restrict__ out) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < m) out[i] = counts[i];
+}
+
+__global__ void k_scatter(const int32_t *__restrict__ rec_row, const int32_t *__restrict__ rec_col,
+                          const float *__restrict__ rec_d2, int64_t nsurv,
+                          const int64_t *__restrict__ offsets, int32_t *__restrict__ cursor,
+                          int32_t *__restrict__ idx_u, float *__restrict__ d2_u) {
+    const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (s >= nsurv) return;
+    const int32_t row = rec_row[s];
+    if (row < 0) return;
+    const int64_t pos = offsets[row] + atomicAdd(&cursor[row], 1);
+    idx_u[pos] = rec_col[s];
+    d2_u[pos] = rec_d2[s];
+}
+
+// ------------------------------------------- per-row sort by column id
+__global__ void k_seg_classify(const int64_t *__restrict__ offsets, int64_t m,
+                               int32_t *__restrict__ small_list, int32_t *__restrict__ mid_list,
+                               int32_t *__restrict__ big_list, int64_t *__restrict__ big_len,
+                               unsigned *__restrict__ counters) {
+    const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (r >= m) return;
+    const int64_t len = offsets[r + 1] - offsets[r];
+    if (len == 0) return;
+    if (len <= kSegSmall) {
+        small_list[atomicAdd(&counters[0], 1u)] = (int32_t)r;
+    } else if (len <= kSegMid) {
+        mid_list[atomicAdd(&counters[1], 1u)] = (int32_t)r;
+    } else {
+        const unsigned b = atomicAdd(&counters[2], 1u);
+        big_list[b] = (int32_t)r;
+        big_len[b] = len;
+    }
+}
+
+// One warp per row of <= 32 entries: bitonic network over lanes.
+__global__ void k_seg_sort_small(const int32_t *__restrict__ list, const unsigned *__restrict__ count,
+                                 const int64_t *__restrict__ offsets,
+                                 const int32_t *__restrict__ idx_u, const float *__restrict__ d2_u,
+                                 int32_t *__restrict__ idx, float *__restrict__ d2) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
+    const unsigned total = *count;
+    for (int64_t w = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); w < total; w += nw) {
+        const int32_t r = list[w];
+        const int64_t o = offsets[r];
+        const int len = int(offsets[r + 1] - o);
+        int32_t key = lane < len ? idx_u[o + lane] : INT32_MAX;
+        float val = lane < len ? d2_u[o + lane] : 0.f;
+        for (int k = 2; k <= 32; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                const int32_t pk = __shfl_xor_sync(0xffffffffu, key, j);
+                const float pv = __shfl_xor_sync(0xffffffffu, val, j);
+                const bool up = (lane & k) == 0;
+                const bool lower = (lane & j) == 0;
+                const bool take = (lower == up) ? (pk < key) : (pk > key);
+                if (take) { key = pk; val = pv; }
+            }
+        }
+        if (lane < len) {
+            idx[o + lane] = key;
+            d2[o + lane] = val;
+        }
+    }
+}
+
+// One block per row of <= 4096 entries: bitonic sort in shared memory.
+__global__ void __launch_bounds__(256)
+k_seg_sort_mid(const int32_t *__restrict__ list, const unsigned *__restrict__ count,
+               const int64_t *__restrict__ offsets, const int32_t *__restrict__ idx_u,
+               const float *__restrict__ d2_u, int32_t *__restrict__ idx, float *__restrict__ d2) {
+    __shared__ int32_t sk[kSegMid];
+    __shared__ float sv[kSegMid];
+    const unsigned total = *count;
+    for (unsigned w = blockIdx.x; w < total; w += gridDim.x) {
+        const int32_t r = list[w];
+        const int64_t o = offsets[r];
+        const int len = int(offsets[r + 1] - o);
+        int N = 64;
+        while (N < len) N <<= 1;
+        __syncthreads();
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            sk[i] = i < len ? idx_u[o + i] : INT32_MAX;
+            sv[i] = i < len ? d2_u[o + i] : 0.f;
+        }
+        __syncthreads();
+        for (int k = 2; k <= N; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < N; i += blockDim.x) {
+                    const int ixj = i ^ j;
+                    if (ixj > i) {
+                        const bool asc = (i & k) == 0;
+                        const int32_t a = sk[i], b = sk[ixj];
+                        if ((a > b) == asc) {
+                            sk[i] = b; sk[ixj] = a;
+                            const float t = sv[i]; sv[i] = sv[ixj]; sv[ixj] = t;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int i = threadIdx.x; i < len; i += blockDim.x) {
+            idx[o + i] = sk[i];
+            d2[o + i] = sv[i];
+        }
+    }
+}
+
+// Long rows: keys (big-row rank << 32 | column), values = source position.
+__global__ void k_seg_big_gather(const int32_t *__restrict__ big_list, int nbig,
+                                 const int64_t *__restrict__ offsets, const int64_t *__restrict__ toff,
+                                 const int32_t *__restrict__ idx_u, uint64_t *__restrict__ keys,
+                                 uint32_t *__restrict__ vals) {
+    const int b = blockIdx.x;
+    if (b >= nbig) return;
+    const int32_t r = big_list[b];
+    const int64_t o = offsets[r], len = offsets[r + 1] - o, t0 = toff[b];
+    for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
+        keys[t0 + i] = (uint64_t(b) << 32) | uint64_t(uint32_t(idx_u[o + i]));
+        vals[t0 + i] = uint32_t(o + i);
+    }
+}
+
+__global__ void k_seg_big_scatter(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                                  int64_t total, const int32_t *__restrict__ big_list,
+                                  const int64_t *__restrict__ offsets, const int64_t *__restrict__ toff,
+                                  const float *__restrict__ d2_u, int32_t *__restrict__ idx,
+                                  float *__restrict__ d2) {
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const uint64_t k = keys[t];
+    const int b = int(k >> 32);
+    const int64_t pos = offsets[big_list[b]] + (t - toff[b]);
+    idx[pos] = int32_t(uint32_t(k & 0xffffffffu));
+    d2[pos] = d2_u[vals[t]];
+}
+
+}  // namespace snn

@@ -1,0 +1,88 @@
+// Query-phase kernels (Algorithm 2, Section 3.2; Section 4).
+#pragma once
+#include "common.cuh"
+
+namespace snn {
+
+// Query tile (queries sorted by score) and band chunk (sorted data rows).
+constexpr int kBQ = 128;
+constexpr int kBR = 128;
+constexpr int kChunksPerItem = 8;   // band chunks scored by one work item
+
+// Sorted query set: either the index's own points (self-join) or
+// out-of-sample queries projected, sorted and gathered like the data.
+struct QuerySet {
+    int64_t m;
+    const float *alpha;    // m, sorted scores
+    const int32_t *order;  // m, original query row of each sorted position
+    const float *raw;      // m x dp raw rows
+    const float *xc;       // m x dp centred rows
+    const float *hx;       // m, halved squared norms (FP32)
+    const float *nrm;      // m, upper bounds on norms
+};
+
+struct DataSet {
+    int64_t n;
+    int d, dp;
+    const float *alpha;
+    const int32_t *order;
+    const float *raw;
+    const float *xc;
+    const float *hx;
+    const float *nrm;
+};
+
+struct ScoreArgs {
+    QuerySet q;
+    DataSet x;
+    const float *thrA;          // m: per-query constant part of the threshold
+    const int64_t *tile_lo;     // ntiles
+    const int64_t *tile_hi;
+    const int64_t *item_off;    // ntiles + 1, exclusive scan of items per tile
+    int ntiles;
+    float c1;                   // rounding constant of the FP32 score
+    uint2 *surv;                // survivor pairs (sorted query pos, sorted row)
+    int64_t cap;
+    unsigned long long *count;  // survivors found (may exceed cap)
+    unsigned long long *work;   // work-item counter
+};
+
+__global__ void k_query_consts(const float *hy, const float *qn, int64_t m, int d, double Rx,
+                               double e_data, float *thrA);
+__global__ void k_tile_band(const float *qalpha, int64_t m, const float *alpha, int64_t n,
+                            double Wbase, const float *eps_d, const float *eps_q, int64_t *tile_lo, int64_t *tile_hi, int64_t *items,
+                            int ntiles, unsigned long long *band_pairs);
+__global__ void k_query_windows(const float *qalpha, int64_t m, const float *alpha, int64_t n,
+                                double Wbase, const float *eps_d, const float *eps_q,
+                                unsigned long long *cand);
+__global__ void k_score_fp32_single(ScoreArgs a);
+__global__ void k_score_fp32_multi(ScoreArgs a);
+__global__ void k_recheck(const uint2 *surv, int64_t nsurv, const float *qraw,
+                          const int32_t *qorder, const float *praw, const int32_t *porder,
+                          int d, int dp, double R2, int32_t *rec_row, int32_t *rec_col,
+                          float *rec_d2, int32_t *counts);
+__global__ void k_counts_to_i64(const int32_t *counts, int64_t m, int64_t *out);
+__global__ void k_scatter(const int32_t *rec_row, const int32_t *rec_col, const float *rec_d2,
+                          int64_t nsurv, const int64_t *offsets, int32_t *cursor,
+                          int32_t *idx_u, float *d2_u);
+
+// Segmented sort of CSR rows by column id.
+constexpr int kSegSmall = 32;
+constexpr int kSegMid = 4096;
+__global__ void k_seg_classify(const int64_t *offsets, int64_t m, int32_t *small_list,
+                               int32_t *mid_list, int32_t *big_list, int64_t *big_len,
+                               unsigned *counters);
+__global__ void k_seg_sort_small(const int32_t *list, const unsigned *count, const int64_t *offsets,
+                                 const int32_t *idx_u, const float *d2_u, int32_t *idx,
+                                 float *d2);
+__global__ void k_seg_sort_mid(const int32_t *list, const unsigned *count, const int64_t *offsets,
+                               const int32_t *idx_u, const float *d2_u, int32_t *idx, float *d2);
+__global__ void k_seg_big_gather(const int32_t *big_list, int nbig, const int64_t *offsets,
+                                 const int64_t *toff, const int32_t *idx_u, uint64_t *keys,
+                                 uint32_t *vals);
+__global__ void k_seg_big_scatter(const uint64_t *keys, const uint32_t *vals, int64_t total,
+                                  const int32_t *big_list, const int64_t *offsets,
+                                  const int64_t *toff, const float *d2_u, int32_t *idx,
+                                  float *d2);
+
+}  // namespace snn

@@ -1,0 +1,718 @@
+// C ABI of libsnn (include/snn.h): host orchestration of the index phase
+// (Algorithm 1), the query phase (Algorithm 2 with Section 4's blocked
+// scoring) and DBSCAN on the self-join (Section 6.4).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+#include "dbscan_kernels.cuh"
+#include "index_kernels.cuh"
+#include "query_kernels.cuh"
+#include "tc_score.cuh"
+
+struct snn_index {
+    int64_t n = 0;
+    int d = 0, dp = 0;
+    int device = 0;
+    double *mu64 = nullptr;
+    float *mu32 = nullptr;
+    double *v64 = nullptr;
+    float *v32 = nullptr;
+    float *alpha = nullptr;
+    int32_t *order = nullptr;
+    float *praw = nullptr;
+    float *xc = nullptr;
+    float *hx = nullptr;
+    float *nrm = nullptr;
+    float *dconst = nullptr;      // device: [0] alpha error bound, [1] max norm
+    uint16_t *xb = nullptr;       // BF16 centred rows (n x dpb), built on demand
+    int dpb = 0;
+    float alpha_err = 0.f;
+    float nrm_max = 0.f;
+    mutable double surv_hint = 0.0;   // survivors per query seen last time
+    mutable std::mutex mu;
+};
+
+namespace snn {
+
+namespace {
+thread_local char g_err[512] = "";
+std::once_flag g_pool_once;
+
+void pool_setup() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+}
+}  // namespace
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+void clear_error() { g_err[0] = 0; }
+
+int device_sm_count() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+static unsigned grid_for(int64_t work, int threads) {
+    return (unsigned)std::max<int64_t>(1, cdiv(work, threads));
+}
+
+template <typename T>
+static snn_status dev_alloc(T **p, size_t count) {
+    void *q = nullptr;
+    size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        return SNN_ENOMEM;
+    }
+    *p = static_cast<T *>(q);
+    return SNN_OK;
+}
+
+static void index_release(snn_index *ix) {
+    if (!ix) return;
+    void *ptrs[] = {ix->mu64, ix->mu32, ix->v64, ix->v32, ix->alpha, ix->order,
+                    ix->praw, ix->xc, ix->hx, ix->nrm, ix->dconst, ix->xb};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete ix;
+}
+
+// ---------------------------------------------------------- index build
+static snn_status project_sort_gather(const float *X, int64_t n, int d, int64_t ld, int dp,
+                                      const double *mu64, const float *v32, cudaStream_t s,
+                                      Scratch &scr, float *eps_out, int *bad, float *alpha,
+                                      int32_t *order, float *praw, float *xc, float *hx,
+                                      float *nrm) {
+    uint32_t *keys, *vals, *ka, *va;
+    SNN_TRY(scr.alloc(&keys, n));
+    SNN_TRY(scr.alloc(&vals, n));
+    SNN_TRY(scr.alloc(&ka, n));
+    SNN_TRY(scr.alloc(&va, n));
+    const int64_t pthreads = d > 32 ? n * 32 : n;
+    k_project<<<grid_for(pthreads, 256), 256, 0, s>>>(X, n, d, ld, mu64, v32, keys, vals,
+                                                      eps_out, bad);
+    SNN_LAUNCH_CHECK();
+    SNN_TRY(radix_sort_pairs<uint32_t>(keys, vals, ka, va, n, 32, s));
+    k_gather<<<grid_for(pthreads, 256), 256, 0, s>>>(keys, vals, X, n, d, ld, dp, mu64, alpha,
+                                                     order, praw, xc, hx, nrm);
+    SNN_LAUNCH_CHECK();
+    return SNN_OK;
+}
+
+__global__ void k_max_nonneg(const float *__restrict__ x, int64_t n, float *__restrict__ out) {
+    float m = 0.f;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x)
+        m = fmaxf(m, x[i]);
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
+}
+
+static snn_status first_direction(const double *C, int d, double *v64, float *v32, cudaStream_t s,
+                                  Scratch &scr) {
+    if (d <= kPcSmallMaxD) {
+        const size_t smem = (2 * d + 32) * sizeof(double) + 32 * sizeof(float) +
+                            2 * size_t(d) * d * sizeof(float);
+        k_pc_small<<<1, 1024, smem, s>>>(C, d, v64, v32);
+        SNN_LAUNCH_CHECK();
+        return SNN_OK;
+    }
+    const int64_t dd = int64_t(d) * d;
+    float *M, *T, *scale;
+    double *tr, *w;
+    SNN_TRY(scr.alloc(&M, dd));
+    SNN_TRY(scr.alloc(&T, dd));
+    SNN_TRY(scr.alloc(&scale, 1));
+    SNN_TRY(scr.alloc(&tr, 1));
+    SNN_TRY(scr.alloc(&w, d));
+    k_pc_init<<<1, 1024, 0, s>>>(C, d, M, tr);
+    SNN_LAUNCH_CHECK();
+    k_scale_from_double<<<grid_for(dd, 256), 256, 0, s>>>(C, dd, tr, M);
+    SNN_LAUNCH_CHECK();
+    const int nt = (int)cdiv(d, kGramTile);
+    for (int it = 0; it < 12; ++it) {
+        k_square<<<dim3(nt, nt), 256, 0, s>>>(M, d, T);
+        SNN_LAUNCH_CHECK();
+        k_trace_f<<<1, 1024, 0, s>>>(T, d, scale);
+        SNN_LAUNCH_CHECK();
+        k_scale_f<<<grid_for(dd, 256), 256, 0, s>>>(T, dd, scale, M);
+        SNN_LAUNCH_CHECK();
+    }
+    k_pick_column<<<1, 256, 0, s>>>(M, d, tr, v64);
+    SNN_LAUNCH_CHECK();
+    for (int it = 0; it < 4; ++it) {
+        k_matvec64<<<grid_for(int64_t(d) * 32, 256), 256, 0, s>>>(C, d, v64, w);
+        SNN_LAUNCH_CHECK();
+        k_normalise64<<<1, 1024, 0, s>>>(w, d, v64, v32, 0);
+        SNN_LAUNCH_CHECK();
+    }
+    // final FP64 normalisation (also writes the FP32 copy)
+    SNN_CUDA(cudaMemcpyAsync(w, v64, d * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    k_normalise64<<<1, 1024, 0, s>>>(w, d, v64, v32, 1);
+    SNN_LAUNCH_CHECK();
+    return SNN_OK;
+}
+
+static snn_status index_build(const float *X, int64_t n, int d, int64_t ld, cudaStream_t s,
+                              snn_index **out) {
+    std::call_once(g_pool_once, pool_setup);
+    snn_index *ix = new (std::nothrow) snn_index();
+    if (!ix) {
+        set_error("host allocation failed");
+        return SNN_ENOMEM;
+    }
+    ix->n = n;
+    ix->d = d;
+    ix->dp = (d + 3) & ~3;
+    cudaGetDevice(&ix->device);
+    const int dp = ix->dp;
+    snn_status st = SNN_OK;
+#define TRY_IX(expr)                       \
+    do {                                   \
+        st = (expr);                       \
+        if (st != SNN_OK) {                \
+            cudaStreamSynchronize(s);      \
+            index_release(ix);             \
+            return st;                     \
+        }                                  \
+    } while (0)
+    TRY_IX(dev_alloc(&ix->mu64, d));
+    TRY_IX(dev_alloc(&ix->mu32, d));
+    TRY_IX(dev_alloc(&ix->v64, d));
+    TRY_IX(dev_alloc(&ix->v32, d));
+    TRY_IX(dev_alloc(&ix->alpha, n));
+    TRY_IX(dev_alloc(&ix->order, n));
+    TRY_IX(dev_alloc(&ix->praw, size_t(n) * dp));
+    TRY_IX(dev_alloc(&ix->xc, size_t(n) * dp));
+    TRY_IX(dev_alloc(&ix->hx, n));
+    TRY_IX(dev_alloc(&ix->nrm, n));
+    TRY_IX(dev_alloc(&ix->dconst, 4));
+    {
+        Scratch scr(s);
+        int *bad;
+        TRY_IX(scr.alloc(&bad, 1));
+        if (cudaMemsetAsync(bad, 0, sizeof(int), s) != cudaSuccess ||
+            cudaMemsetAsync(ix->dconst, 0, 4 * sizeof(float), s) != cudaSuccess) {
+            set_error("cudaMemsetAsync failed");
+            TRY_IX(SNN_ECUDA);
+        }
+        // K1: column means
+        const int64_t nb = std::min<int64_t>(cdiv(n, 2048), 1024);
+        const int64_t rows = cdiv(n, nb);
+        double *part;
+        TRY_IX(scr.alloc(&part, size_t(nb) * d));
+        const int TX = d < 32 ? d : 32, TY = 256 / TX;
+        k_colsum_partial<<<(unsigned)nb, TX * TY, TX * TY * sizeof(double), s>>>(X, n, d, ld, rows,
+                                                                               part, bad);
+        if (cudaGetLastError() != cudaSuccess) { set_error("colsum launch"); TRY_IX(SNN_ECUDA); }
+        k_mean_final<<<grid_for(d, 128), 128, 0, s>>>(part, (int)nb, d, n, ix->mu64, ix->mu32);
+        // K2: centred Gram matrix
+        const int ntile = (int)cdiv(d, kGramTile);
+        const int64_t grows = std::max<int64_t>(2048, cdiv(n, 512));
+        const int64_t nchunk = cdiv(n, grows);
+        float *gpart;
+        double *C;
+        TRY_IX(scr.alloc(&gpart, size_t(nchunk) * d * d));
+        TRY_IX(scr.alloc(&C, size_t(d) * d));
+        k_gram_partial<<<dim3(ntile * ntile, (unsigned)nchunk), 256, 0, s>>>(X, n, d, ld, ix->mu32,
+                                                                             grows, ntile, gpart);
+        k_gram_reduce<<<grid_for(int64_t(d) * d, 256), 256, 0, s>>>(gpart, (int)nchunk, d, C);
+        if (cudaGetLastError() != cudaSuccess) { set_error("gram launch"); TRY_IX(SNN_ECUDA); }
+        // K3: first principal direction
+        TRY_IX(first_direction(C, d, ix->v64, ix->v32, s, scr));
+        // K4-K6: scores, sort, gather
+        TRY_IX(project_sort_gather(X, n, d, ld, dp, ix->mu64, ix->v32, s, scr, ix->dconst + 0, bad,
+                                   ix->alpha, ix->order, ix->praw, ix->xc, ix->hx, ix->nrm));
+        k_max_nonneg<<<std::min<unsigned>(grid_for(n, 256), 1024), 256, 0, s>>>(ix->nrm, n,
+                                                                                ix->dconst + 1);
+        if (cudaGetLastError() != cudaSuccess) { set_error("max launch"); TRY_IX(SNN_ECUDA); }
+        float hc[2];
+        int hbad = 0;
+        if (cudaMemcpyAsync(hc, ix->dconst, 2 * sizeof(float), cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            set_error("index build failed: %s", cudaGetErrorString(cudaGetLastError()));
+            TRY_IX(SNN_ECUDA);
+        }
+        if (hbad) {
+            set_error("X contains NaN or Inf");
+            TRY_IX(SNN_EINVAL);
+        }
+        ix->alpha_err = hc[0];
+        ix->nrm_max = hc[1];
+    }
+#undef TRY_IX
+    *out = ix;
+    return SNN_OK;
+}
+
+// ---------------------------------------------------------------- query
+struct QueryScratch {
+    float *alpha = nullptr, *raw = nullptr, *xc = nullptr, *hy = nullptr, *nrm = nullptr;
+    int32_t *order = nullptr;
+    float *eps = nullptr;
+    int *bad = nullptr;
+};
+
+// Largest true distance the FP64 test S <= fl64(R*R) can still accept:
+// S >= D^2 (1 - gamma_{d+2}) and fl64(R*R) <= R^2 (1 + u).
+static double radius_slack(double R, int d) { return R * (1.0 + (d + 8) * 0x1p-52); }
+
+static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int64_t ldq,
+                             double R, snn_precision prec, cudaStream_t s, snn_csr *out,
+                             snn_query_stats *stats) {
+    const bool self = (Q == nullptr);
+    if (self) m = ix->n;
+    const int d = ix->d, dp = ix->dp;
+    out->m = m;
+    out->nnz = 0;
+    out->offsets = nullptr;
+    out->indices = nullptr;
+    out->dist2 = nullptr;
+    SNN_TRY(dev_alloc(&out->offsets, m + 1));
+    uint2 *surv = nullptr;
+    auto fail = [&](snn_status st) {
+        if (surv) cudaFreeAsync(surv, s);
+        surv = nullptr;
+        cudaStreamSynchronize(s);
+        if (out->offsets) cudaFree(out->offsets);
+        if (out->indices) cudaFree(out->indices);
+        if (out->dist2) cudaFree(out->dist2);
+        out->offsets = nullptr;
+        out->indices = nullptr;
+        out->dist2 = nullptr;
+        return st;
+    };
+#define TRY_Q(expr)                          \
+    do {                                     \
+        snn_status _st = (expr);             \
+        if (_st != SNN_OK) return fail(_st); \
+    } while (0)
+#define CUDA_Q(call)                                                              \
+    do {                                                                          \
+        cudaError_t _e = (call);                                                  \
+        if (_e != cudaSuccess) {                                                  \
+            set_error("%s: %s", #call, cudaGetErrorString(_e));                   \
+            return fail(_e == cudaErrorMemoryAllocation ? SNN_ENOMEM : SNN_ECUDA); \
+        }                                                                         \
+    } while (0)
+
+    if (m == 0) {
+        CUDA_Q(cudaMemsetAsync(out->offsets, 0, sizeof(int64_t), s));
+        CUDA_Q(cudaStreamSynchronize(s));
+        if (stats) std::memset(stats, 0, sizeof(*stats));
+        return SNN_OK;
+    }
+    cudaEvent_t ev[5] = {};
+    if (stats) {
+        for (auto &e : ev) cudaEventCreate(&e);
+        cudaEventRecord(ev[0], s);
+    }
+    Scratch scr(s);
+    QuerySet qs;
+    qs.m = m;
+    float *eps_q = ix->dconst;   // self-join: the data's own bound
+    int *bad = nullptr;
+    TRY_Q(scr.alloc(&bad, 1));
+    CUDA_Q(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    if (self) {
+        qs.alpha = ix->alpha;
+        qs.order = ix->order;
+        qs.raw = ix->praw;
+        qs.xc = ix->xc;
+        qs.hx = ix->hx;
+        qs.nrm = ix->nrm;
+    } else {
+        float *qa, *qraw, *qxc, *qhy, *qnrm;
+        int32_t *qorder;
+        TRY_Q(scr.alloc(&qa, m));
+        TRY_Q(scr.alloc(&qorder, m));
+        TRY_Q(scr.alloc(&qraw, size_t(m) * dp));
+        TRY_Q(scr.alloc(&qxc, size_t(m) * dp));
+        TRY_Q(scr.alloc(&qhy, m));
+        TRY_Q(scr.alloc(&qnrm, m));
+        TRY_Q(scr.alloc(&eps_q, 1));
+        CUDA_Q(cudaMemsetAsync(eps_q, 0, sizeof(float), s));
+        TRY_Q(project_sort_gather(Q, m, d, ldq, dp, ix->mu64, ix->v32, s, scr, eps_q, bad, qa,
+                                  qorder, qraw, qxc, qhy, qnrm));
+        qs.alpha = qa;
+        qs.order = qorder;
+        qs.raw = qraw;
+        qs.xc = qxc;
+        qs.hx = qhy;
+        qs.nrm = qnrm;
+    }
+    DataSet ds{ix->n, d, dp, ix->alpha, ix->order, ix->praw, ix->xc, ix->hx, ix->nrm};
+
+    const double Rx = radius_slack(R, d);
+    const double e_data = 1.0001 * (double)kU32 * (double)ix->nrm_max;
+    // window half-width: |alpha_j - alpha_q| <= ||v|| D + eps_j + eps_q
+    const double Wbase = Rx * (1.0 + (d + 4) * 0x1p-52) * (1.0 + 0x1p-30);
+
+    float *thrA;
+    TRY_Q(scr.alloc(&thrA, m));
+    k_query_consts<<<grid_for(m, 256), 256, 0, s>>>(qs.hx, qs.nrm, m, d, Rx, e_data, thrA);
+    CUDA_Q(cudaGetLastError());
+
+    const int ntiles = (int)cdiv(m, kBQ);
+    int64_t *tile_lo, *tile_hi, *items, *item_off;
+    unsigned long long *ctr;   // [0] survivors, [1] work, [2] band pairs, [3] candidates
+    TRY_Q(scr.alloc(&tile_lo, ntiles));
+    TRY_Q(scr.alloc(&tile_hi, ntiles));
+    TRY_Q(scr.alloc(&items, ntiles));
+    TRY_Q(scr.alloc(&item_off, ntiles + 1));
+    TRY_Q(scr.alloc(&ctr, 4));
+    CUDA_Q(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), s));
+    k_tile_band<<<grid_for(ntiles, 128), 128, 0, s>>>(qs.alpha, m, ix->alpha, ix->n, Wbase,
+                                                      ix->dconst, eps_q, tile_lo, tile_hi, items,
+                                                      ntiles, stats ? ctr + 2 : nullptr);
+    CUDA_Q(cudaGetLastError());
+    if (stats) {
+        k_query_windows<<<grid_for(m, 256), 256, 0, s>>>(qs.alpha, m, ix->alpha, ix->n, Wbase,
+                                                         ix->dconst, eps_q, ctr + 3);
+        CUDA_Q(cudaGetLastError());
+    }
+    TRY_Q(scan_exclusive<int64_t>(items, item_off, ntiles, s));
+
+    // scoring with an adaptive survivor buffer
+    double hint;
+    {
+        std::lock_guard<std::mutex> lk(ix->mu);
+        hint = ix->surv_hint;
+    }
+    int64_t cap = std::max<int64_t>(int64_t(1) << 20,
+                                    int64_t(std::ceil((hint > 0 ? hint * 1.25 : 16.0) * m)) + 4096);
+    CUDA_Q(cudaMallocAsync(&surv, size_t(cap) * sizeof(uint2), s));
+    ScoreArgs sa;
+    sa.q = qs;
+    sa.x = ds;
+    sa.thrA = thrA;
+    sa.tile_lo = tile_lo;
+    sa.tile_hi = tile_hi;
+    sa.item_off = item_off;
+    sa.ntiles = ntiles;
+    sa.c1 = (float)((2.0 * d + 4.0) * (double)kU32 * 1.05);
+    sa.count = ctr;
+    sa.work = ctr + 1;
+    unsigned long long hctr[4] = {0, 0, 0, 0};
+    int hbad = 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        sa.surv = surv;
+        sa.cap = cap;
+        if (stats) cudaEventRecord(ev[1], s);
+        snn_status st = SNN_OK;
+        if (prec == SNN_PREC_BF16) {
+            st = tc_score_launch(ix, sa, s);
+        } else {
+            const int grid = device_sm_count() * 2;
+            if (dp <= 16)
+                k_score_fp32_single<<<grid, 256, 0, s>>>(sa);
+            else
+                k_score_fp32_multi<<<grid, 256, 0, s>>>(sa);
+            if (cudaGetLastError() != cudaSuccess) {
+                set_error("score kernel launch failed");
+                st = SNN_ECUDA;
+            }
+        }
+        if (st != SNN_OK) return fail(st);
+        if (stats) cudaEventRecord(ev[2], s);
+        cudaError_t e1 = cudaMemcpyAsync(hctr, ctr, 4 * sizeof(unsigned long long),
+                                         cudaMemcpyDeviceToHost, s);
+        cudaError_t e2 = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+        cudaError_t e3 = cudaStreamSynchronize(s);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+            set_error("scoring failed: %s", cudaGetErrorString(e3 != cudaSuccess ? e3 : e1));
+            return fail(SNN_ECUDA);
+        }
+        if (hbad) {
+            set_error("Q contains NaN or Inf");
+            return fail(SNN_EINVAL);
+        }
+        if ((int64_t)hctr[0] <= cap) break;
+        if (attempt == 1) {
+            set_error("survivor buffer overflow after retry");
+            return fail(SNN_EOVERFLOW);
+        }
+        cudaFreeAsync(surv, s);
+        surv = nullptr;
+        cap = (int64_t)hctr[0] + 1024;
+        CUDA_Q(cudaMallocAsync(&surv, size_t(cap) * sizeof(uint2), s));
+        CUDA_Q(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long), s));
+    }
+    const int64_t nsurv = (int64_t)hctr[0];
+    {
+        std::lock_guard<std::mutex> lk(ix->mu);
+        ix->surv_hint = double(nsurv) / double(m);
+    }
+
+    // exact FP64 decision for every survivor
+    int32_t *rec_row, *rec_col, *counts, *cursor;
+    float *rec_d2;
+    int64_t *counts64;
+    TRY_Q(scr.alloc(&rec_row, nsurv));
+    TRY_Q(scr.alloc(&rec_col, nsurv));
+    TRY_Q(scr.alloc(&rec_d2, nsurv));
+    TRY_Q(scr.alloc(&counts, m));
+    TRY_Q(scr.alloc(&cursor, m));
+    TRY_Q(scr.alloc(&counts64, m));
+    CUDA_Q(cudaMemsetAsync(counts, 0, m * sizeof(int32_t), s));
+    CUDA_Q(cudaMemsetAsync(cursor, 0, m * sizeof(int32_t), s));
+    const double R2 = R * R;
+    if (nsurv > 0) {
+        k_recheck<<<grid_for(nsurv, 256), 256, 0, s>>>(surv, nsurv, qs.raw, qs.order, ds.raw,
+                                                       ds.order, d, dp, R2, rec_row, rec_col,
+                                                       rec_d2, counts);
+        CUDA_Q(cudaGetLastError());
+    }
+    cudaFreeAsync(surv, s);
+    surv = nullptr;
+    if (stats) cudaEventRecord(ev[3], s);
+    k_counts_to_i64<<<grid_for(m, 256), 256, 0, s>>>(counts, m, counts64);
+    CUDA_Q(cudaGetLastError());
+    TRY_Q(scan_exclusive<int64_t>(counts64, out->offsets, m, s));
+    int64_t nnz = 0;
+    CUDA_Q(cudaMemcpyAsync(&nnz, out->offsets + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CUDA_Q(cudaStreamSynchronize(s));
+    if (nnz >= (int64_t(1) << 31)) {
+        set_error("%lld neighbour pairs exceed this build's limit of 2^31-1", (long long)nnz);
+        return fail(SNN_ENOTSUP);
+    }
+    out->nnz = nnz;
+    if (nnz > 0) {
+        TRY_Q(dev_alloc(&out->indices, nnz));
+        TRY_Q(dev_alloc(&out->dist2, nnz));
+        int32_t *idx_u;
+        float *d2_u;
+        TRY_Q(scr.alloc(&idx_u, nnz));
+        TRY_Q(scr.alloc(&d2_u, nnz));
+        k_scatter<<<grid_for(nsurv, 256), 256, 0, s>>>(rec_row, rec_col, rec_d2, nsurv,
+                                                       out->offsets, cursor, idx_u, d2_u);
+        CUDA_Q(cudaGetLastError());
+        // per-row ascending column ids
+        int32_t *lists, *big_list;
+        int64_t *big_len, *toff;
+        unsigned *cls;
+        TRY_Q(scr.alloc(&lists, 2 * m));
+        TRY_Q(scr.alloc(&big_list, m));
+        TRY_Q(scr.alloc(&big_len, m));
+        TRY_Q(scr.alloc(&toff, m + 1));
+        TRY_Q(scr.alloc(&cls, 4));
+        CUDA_Q(cudaMemsetAsync(cls, 0, 4 * sizeof(unsigned), s));
+        k_seg_classify<<<grid_for(m, 256), 256, 0, s>>>(out->offsets, m, lists, lists + m, big_list,
+                                                        big_len, cls);
+        CUDA_Q(cudaGetLastError());
+        k_seg_sort_small<<<std::min<unsigned>(grid_for(m * 32, 256), 8192), 256, 0, s>>>(
+            lists, cls, out->offsets, idx_u, d2_u, out->indices, out->dist2);
+        k_seg_sort_mid<<<std::min<unsigned>((unsigned)m, 4096), 256, 0, s>>>(
+            lists + m, cls + 1, out->offsets, idx_u, d2_u, out->indices, out->dist2);
+        CUDA_Q(cudaGetLastError());
+        unsigned hcls[4];
+        CUDA_Q(cudaMemcpyAsync(hcls, cls, sizeof(hcls), cudaMemcpyDeviceToHost, s));
+        CUDA_Q(cudaStreamSynchronize(s));
+        const int nbig = (int)hcls[2];
+        if (nbig > 0) {
+            TRY_Q(scan_exclusive<int64_t>(big_len, toff, nbig, s));
+            int64_t tot = 0;
+            CUDA_Q(cudaMemcpyAsync(&tot, toff + nbig, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            CUDA_Q(cudaStreamSynchronize(s));
+            uint64_t *bk, *bka;
+            uint32_t *bv, *bva;
+            TRY_Q(scr.alloc(&bk, tot));
+            TRY_Q(scr.alloc(&bka, tot));
+            TRY_Q(scr.alloc(&bv, tot));
+            TRY_Q(scr.alloc(&bva, tot));
+            k_seg_big_gather<<<nbig, 256, 0, s>>>(big_list, nbig, out->offsets, toff, idx_u, bk, bv);
+            CUDA_Q(cudaGetLastError());
+            int bits = 32;
+            while ((int64_t(1) << (bits - 32)) < nbig) ++bits;
+            TRY_Q(radix_sort_pairs<uint64_t>(bk, bv, bka, bva, tot, bits, s));
+            k_seg_big_scatter<<<grid_for(tot, 256), 256, 0, s>>>(bk, bv, tot, big_list, out->offsets,
+                                                                 toff, d2_u, out->indices,
+                                                                 out->dist2);
+            CUDA_Q(cudaGetLastError());
+        }
+    }
+    if (stats) {
+        cudaEventRecord(ev[4], s);
+        CUDA_Q(cudaStreamSynchronize(s));
+        stats->candidates = (int64_t)hctr[3];
+        stats->band_pairs = (int64_t)hctr[2];
+        stats->survivors = nsurv;
+        stats->nnz = nnz;
+        cudaEventElapsedTime(&stats->ms_prep, ev[0], ev[1]);
+        cudaEventElapsedTime(&stats->ms_score, ev[1], ev[2]);
+        cudaEventElapsedTime(&stats->ms_recheck, ev[2], ev[3]);
+        cudaEventElapsedTime(&stats->ms_csr, ev[3], ev[4]);
+        for (auto &e : ev) cudaEventDestroy(e);
+    }
+#undef TRY_Q
+#undef CUDA_Q
+    return SNN_OK;
+}
+
+static snn_status check_finite_r(double R, const char *what) {
+    if (!(R >= 0.0) || !std::isfinite(R)) {
+        set_error("%s must be finite and >= 0", what);
+        return SNN_EINVAL;
+    }
+    return SNN_OK;
+}
+
+static snn_status validate_points(const float *X, int64_t n, int32_t d, int64_t ld) {
+    if (!X) { set_error("X is NULL"); return SNN_EINVAL; }
+    if (n < 1 || n >= (int64_t(1) << 31)) { set_error("n must be in [1, 2^31)"); return SNN_EINVAL; }
+    if (d < 1 || d > 4096) { set_error("d must be in [1, 4096]"); return SNN_EINVAL; }
+    if (ld < d) { set_error("ld must be >= d"); return SNN_EINVAL; }
+    return SNN_OK;
+}
+
+}  // namespace snn
+
+using namespace snn;
+
+extern "C" {
+
+snn_status snn_index_build(const float *X, int64_t n, int32_t d, int64_t ld, void *stream,
+                           snn_index **out) {
+    clear_error();
+    if (!out) { set_error("out is NULL"); return SNN_EINVAL; }
+    *out = nullptr;
+    SNN_TRY(validate_points(X, n, d, ld));
+    return index_build(X, n, d, ld, static_cast<cudaStream_t>(stream), out);
+}
+
+snn_status snn_query_radius(const snn_index *idx, const float *Q, int64_t m, int64_t ldq, double R,
+                            snn_precision prec, void *stream, snn_csr *out,
+                            snn_query_stats *stats) {
+    clear_error();
+    if (!idx || !out) { set_error("index or out is NULL"); return SNN_EINVAL; }
+    std::memset(out, 0, sizeof(*out));
+    SNN_TRY(check_finite_r(R, "R"));
+    if (Q) {
+        if (m < 0 || m >= (int64_t(1) << 31)) { set_error("m must be in [0, 2^31)"); return SNN_EINVAL; }
+        if (ldq < idx->d) { set_error("ldq must be >= d"); return SNN_EINVAL; }
+    }
+    if (prec != SNN_PREC_FP32 && prec != SNN_PREC_BF16) {
+        set_error("precision %d is not available in this build", (int)prec);
+        return SNN_ENOTSUP;
+    }
+    return query_impl(idx, Q, m, ldq, R, prec, static_cast<cudaStream_t>(stream), out, stats);
+}
+
+snn_status snn_query_radius_batch(int32_t nsets, const snn_index *const *idx, const float *const *Q,
+                                  const int64_t *m, const int64_t *ldq, const double *R,
+                                  snn_precision prec, void *stream, snn_csr *out) {
+    clear_error();
+    if (nsets < 0 || (nsets > 0 && (!idx || !Q || !m || !ldq || !R || !out))) {
+        set_error("invalid batch arguments");
+        return SNN_EINVAL;
+    }
+    for (int32_t s = 0; s < nsets; ++s) {
+        snn_status st = snn_query_radius(idx[s], Q[s], m[s], ldq[s], R[s], prec, stream, &out[s],
+                                         nullptr);
+        if (st != SNN_OK) {
+            char msg[512];
+            std::snprintf(msg, sizeof(msg), "set %d: %s", (int)s, snn_last_error());
+            for (int32_t t = 0; t < s; ++t) {
+                cudaFree(out[t].offsets);
+                if (out[t].indices) cudaFree(out[t].indices);
+                if (out[t].dist2) cudaFree(out[t].dist2);
+                std::memset(&out[t], 0, sizeof(out[t]));
+            }
+            set_error("%s", msg);
+            return st;
+        }
+    }
+    return SNN_OK;
+}
+
+snn_status snn_dbscan(const float *X, int64_t n, int32_t d, int64_t ld, double eps, int32_t min_pts,
+                      snn_precision prec, void *stream, int32_t *labels, uint8_t *is_core) {
+    clear_error();
+    SNN_TRY(validate_points(X, n, d, ld));
+    SNN_TRY(check_finite_r(eps, "eps"));
+    if (min_pts < 1) { set_error("min_pts must be >= 1"); return SNN_EINVAL; }
+    if (!labels || !is_core) { set_error("labels/is_core is NULL"); return SNN_EINVAL; }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    snn_index *ix = nullptr;
+    SNN_TRY(index_build(X, n, d, ld, s, &ix));
+    snn_csr csr;
+    snn_status st = snn_query_radius(ix, nullptr, 0, 0, eps, prec, stream, &csr, nullptr);
+    if (st != SNN_OK) {
+        index_release(ix);
+        return st;
+    }
+    {
+        Scratch scr(s);
+        int32_t *parent = nullptr, *owner = nullptr, *minid = nullptr;
+        st = scr.alloc(&parent, n);
+        if (st == SNN_OK) st = scr.alloc(&owner, n);
+        if (st == SNN_OK) st = scr.alloc(&minid, n);
+        if (st == SNN_OK) {
+            k_db_core<<<grid_for(n, 256), 256, 0, s>>>(csr.offsets, n, min_pts, is_core, parent);
+            k_db_union<<<grid_for(n * 32, 256), 256, 0, s>>>(csr.offsets, csr.indices, n, is_core,
+                                                             parent);
+            k_db_init_minid<<<grid_for(n, 256), 256, 0, s>>>(minid, n);
+            k_db_assign<<<grid_for(n, 256), 256, 0, s>>>(csr.offsets, csr.indices, n, is_core,
+                                                         parent, owner, minid);
+            k_db_label<<<grid_for(n, 256), 256, 0, s>>>(owner, minid, n, labels);
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) {
+                set_error("dbscan kernels failed: %s", cudaGetErrorString(e));
+                st = SNN_ECUDA;
+            }
+        }
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(csr.offsets);
+    if (csr.indices) cudaFree(csr.indices);
+    if (csr.dist2) cudaFree(csr.dist2);
+    index_release(ix);
+    return st;
+}
+
+snn_status snn_index_get_view(const snn_index *idx, snn_index_view *view) {
+    clear_error();
+    if (!idx || !view) { set_error("index or view is NULL"); return SNN_EINVAL; }
+    view->n = idx->n;
+    view->d = idx->d;
+    view->dp = idx->dp;
+    view->mu = idx->mu64;
+    view->v1 = idx->v64;
+    view->alpha = idx->alpha;
+    view->order = idx->order;
+    view->points = idx->praw;
+    view->alpha_err = idx->alpha_err;
+    return SNN_OK;
+}
+
+void snn_free(void *p) {
+    if (p) cudaFree(p);
+}
+
+void snn_index_free(snn_index *idx) { index_release(idx); }
+
+const char *snn_last_error(void) { return g_err; }
+
+const char *snn_version(void) { return "snn-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,15 @@
+// Tensor-core (tcgen05, BF16) band scoring for the query phase.
+#pragma once
+#include "common.cuh"
+#include "query_kernels.cuh"
+
+struct snn_index;
+
+namespace snn {
+
+// Scores every band item of `a` on the tensor cores and appends survivors
+// exactly like the FP32 kernels do.  Builds the index's BF16 copy on first
+// use.  Returns SNN_ENOTSUP where the tensor-core path is not available.
+snn_status tc_score_launch(const snn_index *ix, const ScoreArgs &a, cudaStream_t s);
+
+}  // namespace snn

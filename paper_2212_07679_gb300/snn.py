@@ -1,0 +1,269 @@
+"""Thin ctypes binding of libsnn (include/snn.h).
+
+Argument marshalling only: every step of the search runs in the CUDA library.
+PyTorch supplies device memory and the current stream.  Importing this
+module loads ``_build/libsnn.so`` and raises if it is missing or cannot be
+loaded -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsnn.so")
+
+SNN_OK, SNN_EINVAL, SNN_ENOMEM, SNN_ECUDA, SNN_ETIMEOUT, SNN_EOVERFLOW, SNN_ENOTSUP = range(7)
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2}
+
+
+class SNNError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"snn status {status}: {msg}")
+        self.status = status
+
+
+class CSRStruct(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("offsets", ctypes.c_void_p), ("indices", ctypes.c_void_p),
+                ("dist2", ctypes.c_void_p)]
+
+
+class StatsStruct(ctypes.Structure):
+    _fields_ = [("candidates", ctypes.c_int64), ("band_pairs", ctypes.c_int64),
+                ("survivors", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("ms_prep", ctypes.c_float), ("ms_score", ctypes.c_float),
+                ("ms_recheck", ctypes.c_float), ("ms_csr", ctypes.c_float)]
+
+
+class ViewStruct(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32), ("dp", ctypes.c_int32),
+                ("mu", ctypes.c_void_p), ("v1", ctypes.c_void_p), ("alpha", ctypes.c_void_p),
+                ("order", ctypes.c_void_p), ("points", ctypes.c_void_p),
+                ("alpha_err", ctypes.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libsnn is not built ({LIB_PATH} missing); run "
+                          "paper_2212_07679_gb300.build.build() first")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    lib.snn_index_build.argtypes = [vp, i64, i32, i64, vp, ctypes.POINTER(vp)]
+    lib.snn_index_build.restype = ctypes.c_int
+    lib.snn_query_radius.argtypes = [vp, vp, i64, i64, f64, ctypes.c_int, vp,
+                                     ctypes.POINTER(CSRStruct), ctypes.POINTER(StatsStruct)]
+    lib.snn_query_radius.restype = ctypes.c_int
+    lib.snn_query_radius_batch.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                           ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                           ctypes.POINTER(f64), ctypes.c_int, vp,
+                                           ctypes.POINTER(CSRStruct)]
+    lib.snn_query_radius_batch.restype = ctypes.c_int
+    lib.snn_dbscan.argtypes = [vp, i64, i32, i64, f64, i32, ctypes.c_int, vp, vp, vp]
+    lib.snn_dbscan.restype = ctypes.c_int
+    lib.snn_index_get_view.argtypes = [vp, ctypes.POINTER(ViewStruct)]
+    lib.snn_index_get_view.restype = ctypes.c_int
+    lib.snn_free.argtypes = [vp]
+    lib.snn_free.restype = None
+    lib.snn_index_free.argtypes = [vp]
+    lib.snn_index_free.restype = None
+    lib.snn_last_error.argtypes = []
+    lib.snn_last_error.restype = ctypes.c_char_p
+    lib.snn_version.argtypes = []
+    lib.snn_version.restype = ctypes.c_char_p
+    return lib
+
+
+lib = _load()
+
+
+def _check(status: int):
+    if status != SNN_OK:
+        raise SNNError(status, lib.snn_last_error().decode(errors="replace"))
+
+
+def _stream_ptr(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _points(X: torch.Tensor, name: str):
+    if not isinstance(X, torch.Tensor) or not X.is_cuda or X.dtype != torch.float32 or X.dim() != 2:
+        raise TypeError(f"{name} must be a 2-d float32 CUDA tensor")
+    if X.stride(1) != 1:
+        X = X.contiguous()
+    return X, X.stride(0)
+
+
+class _DeviceBuffer:
+    """Library-allocated device memory exposed to torch; freed with snn_free."""
+
+    def __init__(self, ptr: int, count: int, typestr: str):
+        self.ptr = ptr
+        self.__cuda_array_interface__ = {"shape": (count,), "typestr": typestr,
+                                         "data": (ptr, False), "version": 3, "strides": None}
+
+    def __del__(self):
+        if self.ptr:
+            lib.snn_free(ctypes.c_void_p(self.ptr))
+            self.ptr = 0
+
+
+def _wrap(ptr: int, count: int, typestr: str, dtype, device) -> torch.Tensor:
+    if not ptr or count == 0:
+        if ptr:
+            lib.snn_free(ctypes.c_void_p(ptr))
+        return torch.empty(0, dtype=dtype, device=device)
+    return torch.as_tensor(_DeviceBuffer(ptr, count, typestr), device=device)
+
+
+@dataclass
+class CSR:
+    """Neighbour lists: row r is indices[offsets[r]:offsets[r+1]] (original
+    point ids, ascending) with dist2 the matching squared distances."""
+    offsets: torch.Tensor
+    indices: torch.Tensor
+    dist2: torch.Tensor
+    stats: dict | None = None
+
+    @property
+    def m(self) -> int:
+        return self.offsets.numel() - 1
+
+    @property
+    def nnz(self) -> int:
+        return self.indices.numel()
+
+
+def _csr_from(cs: CSRStruct, device, stats=None) -> CSR:
+    off = _wrap(cs.offsets, cs.m + 1, "<i8", torch.int64, device)
+    idx = _wrap(cs.indices, cs.nnz, "<i4", torch.int32, device)
+    d2 = _wrap(cs.dist2, cs.nnz, "<f4", torch.float32, device)
+    return CSR(off, idx, d2, stats)
+
+
+class Index:
+    """SNN index (Algorithm 1) of the rows of a float32 CUDA tensor."""
+
+    def __init__(self, X: torch.Tensor, stream=None):
+        X, ld = _points(X, "X")
+        self.device = X.device
+        self.n, self.d = X.shape
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib.snn_index_build(ctypes.c_void_p(X.data_ptr()), self.n, self.d, ld,
+                                       _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def query(self, Q: torch.Tensor | None = None, R: float = 0.0, precision: str = "fp32",
+              stats: bool = False, stream=None) -> CSR:
+        """Algorithm 2 for all rows of Q (None: self-join)."""
+        if self._h is None:
+            raise RuntimeError("index was freed")
+        cs = CSRStruct()
+        st = StatsStruct() if stats else None
+        if Q is None:
+            qptr, m, ldq = None, 0, self.d
+        else:
+            Q, ldq = _points(Q, "Q")
+            if Q.shape[1] != self.d:
+                raise ValueError("Q has the wrong number of columns")
+            qptr, m = ctypes.c_void_p(Q.data_ptr()), Q.shape[0]
+        with torch.cuda.device(self.device):
+            _check(lib.snn_query_radius(self._h, qptr, m, ldq, float(R), PRECISIONS[precision],
+                                        _stream_ptr(stream), ctypes.byref(cs),
+                                        ctypes.byref(st) if st is not None else None))
+        sd = None
+        if st is not None:
+            sd = {k: getattr(st, k) for k, _ in StatsStruct._fields_}
+        return _csr_from(cs, self.device, sd)
+
+    def view(self) -> dict:
+        """Device arrays of the index (copies), for inspection and tests."""
+        v = ViewStruct()
+        _check(lib.snn_index_get_view(self._h, ctypes.byref(v)))
+        n, d, dp = v.n, v.d, v.dp
+
+        def cp(ptr, count, typestr, dtype):
+            t = torch.as_tensor(_Borrowed(ptr, count, typestr), device=self.device)
+            return t.clone()
+        return {
+            "mu": cp(v.mu, d, "<f8", torch.float64),
+            "v1": cp(v.v1, d, "<f8", torch.float64),
+            "alpha": cp(v.alpha, n, "<f4", torch.float32),
+            "order": cp(v.order, n, "<i4", torch.int32),
+            "points": cp(v.points, n * dp, "<f4", torch.float32).view(n, dp)[:, :d],
+            "alpha_err": v.alpha_err,
+        }
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib.snn_index_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _Borrowed:
+    def __init__(self, ptr, count, typestr):
+        self.__cuda_array_interface__ = {"shape": (count,), "typestr": typestr,
+                                         "data": (ptr, True), "version": 3, "strides": None}
+
+
+def radius_search(X: torch.Tensor, Q: torch.Tensor | None, R: float, precision: str = "fp32",
+                  stats: bool = False) -> CSR:
+    """Index X and query every row of Q (None: self-join)."""
+    return Index(X).query(Q, R, precision, stats)
+
+
+def query_batch(indices: list[Index], Qs: list[torch.Tensor | None], Rs: list[float],
+                precision: str = "fp32", stream=None) -> list[CSR]:
+    """Many independent (index, queries, radius) problems in one library call."""
+    k = len(indices)
+    hs = (ctypes.c_void_p * k)(*[ix.handle.value for ix in indices])
+    qp = (ctypes.c_void_p * k)()
+    ms = (ctypes.c_int64 * k)()
+    lds = (ctypes.c_int64 * k)()
+    keep = []
+    for s, (ix, Q) in enumerate(zip(indices, Qs)):
+        if Q is None:
+            qp[s], ms[s], lds[s] = None, 0, ix.d
+        else:
+            Q, ld = _points(Q, "Q")
+            keep.append(Q)
+            qp[s], ms[s], lds[s] = Q.data_ptr(), Q.shape[0], ld
+    rs = (ctypes.c_double * k)(*[float(r) for r in Rs])
+    outs = (CSRStruct * k)()
+    dev = indices[0].device if k else torch.device("cuda")
+    with torch.cuda.device(dev):
+        _check(lib.snn_query_radius_batch(k, hs, qp, ms, lds, rs, PRECISIONS[precision],
+                                          _stream_ptr(stream), outs))
+    return [_csr_from(outs[s], dev) for s in range(k)]
+
+
+def dbscan(X: torch.Tensor, eps: float, min_pts: int, precision: str = "fp32", stream=None):
+    """DBSCAN with SNN neighbourhoods: (labels int32, is_core uint8)."""
+    X, ld = _points(X, "X")
+    n, d = X.shape
+    labels = torch.empty(n, dtype=torch.int32, device=X.device)
+    core = torch.empty(n, dtype=torch.uint8, device=X.device)
+    with torch.cuda.device(X.device):
+        _check(lib.snn_dbscan(ctypes.c_void_p(X.data_ptr()), n, d, ld, float(eps), int(min_pts),
+                              PRECISIONS[precision], _stream_ptr(stream),
+                              ctypes.c_void_p(labels.data_ptr()), ctypes.c_void_p(core.data_ptr())))
+    return labels, core
+
+
+def version() -> str:
+    return lib.snn_version().decode()

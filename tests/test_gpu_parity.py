@@ -1,0 +1,224 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Neighbour sets, their order and the squared distances must match the oracle
+bit for bit (ids ascending per row; dist2 = (float)S with S the FP64
+direct-difference sum).  Small cases span several 128-row tiles and a ragged
+tail; the full-size self-join of the 1e6-point mixture is checked on sampled
+rows and by properties that hold at any size."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2212_07679_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PRECS = ["fp32", "bf16"]
+
+
+@pytest.fixture(scope="module")
+def snn():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2212_07679_gb300 import snn as mod
+    return mod
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def assert_csr_equal(got, ref, what=""):
+    off = got.offsets.cpu().numpy()
+    idx = got.indices.cpu().numpy()
+    d2 = got.dist2.cpu().numpy()
+    assert off.shape == ref.offsets.shape, what
+    if not np.array_equal(off, ref.offsets):
+        bad = np.nonzero(np.diff(off) != np.diff(ref.offsets))[0]
+        raise AssertionError(f"{what}: row counts differ at rows {bad[:10]} "
+                             f"(got {np.diff(off)[bad[:5]]}, want {np.diff(ref.offsets)[bad[:5]]})")
+    assert np.array_equal(idx, ref.ids), what
+    assert np.array_equal(d2.view(np.uint32), ref.dist2.view(np.uint32)), what
+
+
+def _run(snn, P, Q, R, prec):
+    ix = snn.Index(_dev(P))
+    try:
+        return ix.query(None if Q is None else _dev(Q), R, precision=prec, stats=True)
+    except snn.SNNError as e:
+        if e.status == snn.SNN_ENOTSUP:
+            pytest.skip(f"{prec} not available: {e}")
+        raise
+
+
+# ------------------------------------------------------------- hand cases
+@pytest.mark.parametrize("prec", PRECS)
+def test_hand_cases(snn, golden_dir, prec):
+    import json
+    import os
+    cases = json.load(open(os.path.join(golden_dir, "hand_cases.json")))["cases"]
+    for case in cases:
+        P = np.asarray(case["P"], dtype=np.float32)
+        Q = None if case["Q"] is None else np.asarray(case["Q"], np.float32).reshape(-1, P.shape[1])
+        got = _run(snn, P, Q, case["R"], prec)
+        assert_csr_equal(got, oracle.brute_radius(P, Q, case["R"]), case["name"])
+
+
+# -------------------------------------------------- workloads, small sizes
+@pytest.mark.parametrize("prec", PRECS)
+def test_gmm_iso_full_size(snn, prec):
+    w = wl.gmm_iso()
+    got = _run(snn, w.P, w.Q, w.R, prec)
+    assert_csr_equal(got, oracle.brute_radius(w.P, w.Q, w.R), "gmm_iso")
+    st = got.stats
+    assert st["band_pairs"] >= st["candidates"] >= st["nnz"] == got.nnz
+    assert st["survivors"] >= st["nnz"]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_gmm_aniso_self_join_small(snn, prec):
+    w = wl.gmm_aniso(n=20011, sub=3000)
+    got = _run(snn, w.P, None, w.R, prec)
+    assert_csr_equal(got, oracle.brute_radius(w.P, None, w.R), "gmm_aniso")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_blobs3d_self_join_small(snn, prec):
+    w = wl.blobs3d(n=20000, blobs=16, box=20.0)
+    got = _run(snn, w.P, None, w.R, prec)
+    assert_csr_equal(got, oracle.brute_radius(w.P, None, w.R), "blobs3d")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_lowrank_img_self_join_small(snn, prec):
+    w = wl.lowrank_img(n=3001, sub=1500)
+    got = _run(snn, w.P, None, w.R, prec)
+    assert_csr_equal(got, oracle.brute_radius(w.P, None, w.R), "lowrank_img")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_out_of_sample_queries(snn, prec):
+    rng = np.random.default_rng(21)
+    P = (rng.standard_normal((7000, 12)) * 2).astype(np.float32)
+    Q = (rng.standard_normal((1500, 12)) * 2.5 + 0.3).astype(np.float32)
+    for R in [0.0, 1.5, 3.0]:
+        got = _run(snn, P, Q, R, prec)
+        assert_csr_equal(got, oracle.brute_radius(P, Q, R), f"oos R={R}")
+
+
+# ------------------------------------------------------------ edge cases
+@pytest.mark.parametrize("prec", PRECS)
+def test_edge_cases(snn, prec):
+    rng = np.random.default_rng(22)
+    cases = []
+    cases.append(("n=1", np.array([[1.0, 2.0, 3.0]], np.float32), None, 0.0))
+    cases.append(("d=1", rng.standard_normal((700, 1)).astype(np.float32), None, 0.01))
+    line = np.arange(300, dtype=np.float32)[:, None] * np.array([[3, 4]], np.float32)
+    cases.append(("line exact ties", line, None, 5.0))
+    dup = np.repeat(rng.standard_normal((20, 6)).astype(np.float32), 15, axis=0)
+    cases.append(("duplicates R=0", dup, None, 0.0))
+    cases.append(("d=17 ragged", rng.integers(-2, 3, (777, 17)).astype(np.float32), None, 2.0))
+    off = (rng.standard_normal((900, 5)) + 1e4).astype(np.float32)
+    cases.append(("large offset", off, None, 1.2))
+    grid = np.stack(np.meshgrid(np.arange(12), np.arange(12), np.arange(12)), -1).reshape(-1, 3)
+    cases.append(("integer grid exact ties", grid.astype(np.float32), None, 1.0))
+    cases.append(("all within R (long rows)", rng.random((4500, 3)).astype(np.float32), None, 2.0))
+    Q = rng.standard_normal((0, 4)).astype(np.float32)
+    cases.append(("m=0", rng.standard_normal((50, 4)).astype(np.float32), Q, 1.0))
+    for name, P, Qc, R in cases:
+        got = _run(snn, P, Qc, R, prec)
+        assert_csr_equal(got, oracle.brute_radius(P, Qc, R), name)
+
+
+def test_index_arrays(snn):
+    w = wl.gmm_aniso(n=30000, sub=2000)
+    ix = snn.Index(_dev(w.P))
+    v = ix.view()
+    alpha = v["alpha"].cpu().numpy()
+    order = v["order"].cpu().numpy()
+    assert np.all(np.diff(alpha) >= 0)
+    assert np.array_equal(np.sort(order), np.arange(w.n))
+    assert np.array_equal(v["points"].cpu().numpy(), w.P[order])
+    v1 = v["v1"].cpu().numpy()
+    assert abs(np.linalg.norm(v1) - 1.0) < 1e-12
+    ref = oracle.snn_index(w.P)
+    assert abs(abs(float(v1 @ ref.v1)) - 1.0) < 1e-3
+    assert np.allclose(v["mu"].cpu().numpy(), ref.mu, rtol=0, atol=1e-9)
+    # scores are within the recorded bound of the FP64 projection
+    a64 = (w.P[order].astype(np.float64) - v["mu"].cpu().numpy()) @ v1
+    assert np.max(np.abs(alpha - a64)) <= v["alpha_err"]
+
+
+def test_invalid_inputs(snn):
+    P = np.random.default_rng(23).standard_normal((100, 4)).astype(np.float32)
+    P[17, 2] = np.nan
+    with pytest.raises(snn.SNNError) as e:
+        snn.Index(_dev(P))
+    assert e.value.status == snn.SNN_EINVAL
+    ix = snn.Index(_dev(np.nan_to_num(P)))
+    with pytest.raises(snn.SNNError):
+        ix.query(None, -1.0)
+    with pytest.raises(snn.SNNError):
+        ix.query(None, float("inf"))
+    Q = np.ones((5, 4), np.float32)
+    Q[3, 1] = np.inf
+    with pytest.raises(snn.SNNError) as e:
+        ix.query(_dev(Q), 1.0)
+    assert e.value.status == snn.SNN_EINVAL
+
+
+def test_deterministic_repeat(snn):
+    w = wl.gmm_aniso(n=15000, sub=2000)
+    a = _run(snn, w.P, None, w.R, "fp32")
+    b = _run(snn, w.P, None, w.R, "fp32")
+    assert torch.equal(a.offsets, b.offsets) and torch.equal(a.indices, b.indices)
+    assert torch.equal(a.dist2, b.dist2)
+
+
+# ------------------------------------------------------------- DBSCAN
+def test_dbscan_small(snn):
+    w = wl.blobs3d(n=30000, blobs=20, box=25.0)
+    labels, core = snn.dbscan(_dev(w.P), 0.4, 10)
+    ref_l, ref_c = oracle.dbscan(w.P, 0.4, 10)
+    assert np.array_equal(core.cpu().numpy(), ref_c)
+    assert np.array_equal(labels.cpu().numpy(), ref_l)
+
+
+# ------------------------------------------------------------ batches
+def test_batch_matches_single_calls(snn):
+    sets = wl.ragged_batch(sets=6, n_lo=500, n_hi=5000, seed=99)
+    idx = [snn.Index(_dev(s.P)) for s in sets]
+    outs = snn.query_batch(idx, [_dev(s.Q) for s in sets], [s.R for s in sets])
+    for s, got in zip(sets, outs):
+        assert_csr_equal(got, oracle.brute_radius(s.P, s.Q, s.R), s.name)
+
+
+# ------------------------------------------------- full size (sampled)
+@pytest.mark.slow
+def test_full_size_self_join_sampled(snn):
+    w = wl.gmm_aniso()
+    ix = snn.Index(_dev(w.P))
+    got = ix.query(None, w.R, stats=True)
+    off = got.offsets.cpu().numpy()
+    idx = got.indices.cpu().numpy()
+    d2 = got.dist2.cpu().numpy()
+    rng = np.random.default_rng(24)
+    rows = rng.choice(w.n, size=64, replace=False)
+    ref = oracle.brute_radius(w.P, w.P[rows], w.R)
+    for t, r in enumerate(rows):
+        ri, rd = ref.row(t)
+        a, b = off[r], off[r + 1]
+        assert np.array_equal(idx[a:b], ri)
+        assert np.array_equal(d2[a:b].view(np.uint32), rd.view(np.uint32))
+    # properties at full size: self-inclusion with dist2 0, ascending rows,
+    # symmetry of the self-join
+    counts = np.diff(off)
+    rowid = np.repeat(np.arange(w.n), counts)
+    assert np.all(counts >= 1)
+    assert np.all((idx[1:] > idx[:-1]) | (rowid[1:] != rowid[:-1]))
+    self_hits = idx == rowid
+    assert self_hits.sum() == w.n and np.all(d2[self_hits] == 0)
+    fwd = rowid.astype(np.int64) * w.n + idx
+    bwd = idx.astype(np.int64) * w.n + rowid
+    assert np.array_equal(np.sort(fwd), np.sort(bwd))
