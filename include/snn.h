@@ -114,7 +114,8 @@ snn_status snn_index_build(const float *X, int64_t n, int32_t d, int64_t ld,
  * the union of candidate ranges of a tile of queries sorted by score).
  *  Q      device, m x d FP32 row-major, stride ldq; NULL means the self-join:
  *         the queries are the index's own points, row r of the result is
- *         point r (m and ldq are then ignored).
+ *         point r (m and ldq are then ignored).  An empty query set is m == 0
+ *         with any non-NULL Q (it is not read).
  *  R      radius, finite and >= 0 (double); the test is S <= fl64(R*R).
  *  prec   rejection arithmetic (see snn_precision).
  *  out    host struct receiving library-allocated device arrays.

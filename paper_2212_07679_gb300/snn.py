@@ -175,7 +175,13 @@ class Index:
             Q, ldq = _points(Q, "Q")
             if Q.shape[1] != self.d:
                 raise ValueError("Q has the wrong number of columns")
-            qptr, m = ctypes.c_void_p(Q.data_ptr()), Q.shape[0]
+            if Q.shape[0] == 0:
+                # an empty query set still needs a non-NULL pointer (NULL
+                # selects the self-join)
+                Q = torch.empty((1, self.d), dtype=torch.float32, device=self.device)
+                qptr, m, ldq = ctypes.c_void_p(Q.data_ptr()), 0, self.d
+            else:
+                qptr, m = ctypes.c_void_p(Q.data_ptr()), Q.shape[0]
         with torch.cuda.device(self.device):
             _check(lib.snn_query_radius(self._h, qptr, m, ldq, float(R), PRECISIONS[precision],
                                         _stream_ptr(stream), ctypes.byref(cs),
@@ -241,6 +247,11 @@ def query_batch(indices: list[Index], Qs: list[torch.Tensor | None], Rs: list[fl
             qp[s], ms[s], lds[s] = None, 0, ix.d
         else:
             Q, ld = _points(Q, "Q")
+            if Q.shape[0] == 0:
+                Q, ld = torch.empty((1, ix.d), dtype=torch.float32, device=ix.device), ix.d
+                keep.append(Q)
+                qp[s], ms[s], lds[s] = Q.data_ptr(), 0, ld
+                continue
             keep.append(Q)
             qp[s], ms[s], lds[s] = Q.data_ptr(), Q.shape[0], ld
     rs = (ctypes.c_double * k)(*[float(r) for r in Rs])
