@@ -224,7 +224,7 @@ class Index:
 class _Borrowed:
     def __init__(self, ptr, count, typestr):
         self.__cuda_array_interface__ = {"shape": (count,), "typestr": typestr,
-                                         "data": (ptr, True), "version": 3, "strides": None}
+                                         "data": (ptr, False), "version": 3, "strides": None}
 
 
 def radius_search(X: torch.Tensor, Q: torch.Tensor | None, R: float, precision: str = "fp32",
