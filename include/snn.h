@@ -85,14 +85,18 @@ typedef struct {
  *  band_pairs  pairs actually scored (query tiles score the union of their
  *              queries' ranges, Section 4's gemm over the union of J);
  *  survivors   pairs the low-precision test could not reject, all of which
- *              were decided exactly in FP64 (recheck count);
+ *              were decided exactly (recheck count; a symmetric self-join
+ *              counts each unordered pair once);
  *  nnz         neighbour pairs returned;
+ *  exact_fp64  survivors whose decision or distance needed the FP64 loop
+ *              itself (the compensated FP32 evaluation settles the rest);
  *  ms_*        device time of the phases (CUDA events on `stream`). */
 typedef struct {
     int64_t candidates;
     int64_t band_pairs;
     int64_t survivors;
     int64_t nnz;
+    int64_t exact_fp64;
     float ms_prep;
     float ms_score;
     float ms_recheck;
@@ -184,6 +188,10 @@ const char *snn_last_error(void);
 
 /* Library version string. */
 const char *snn_version(void);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (diagnostics: the difference around a call is that call's launch count). */
+uint64_t snn_launch_count(void);
 
 #ifdef __cplusplus
 }

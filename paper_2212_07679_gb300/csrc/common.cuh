@@ -128,4 +128,9 @@ snn_status radix_sort_pairs(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals
 
 int device_sm_count();
 
+// Every kernel launch of the library goes through SNN_LAUNCH, which counts
+// it (snn_launch_count() reports the total).
+void note_launch();
+#define SNN_LAUNCH(kernel, ...) ::snn::note_launch(), kernel<<<__VA_ARGS__>>>
+
 }  // namespace snn

@@ -56,7 +56,7 @@ __global__ void k_tile_band(const float *__restrict__ qalpha, int64_t m,
                             const float *__restrict__ alpha, int64_t n, double Wbase,
                             const float *__restrict__ eps_d, const float *__restrict__ eps_q,
                             int64_t *__restrict__ tile_lo, int64_t *__restrict__ tile_hi,
-                            int64_t *__restrict__ items, int ntiles,
+                            int64_t *__restrict__ items, int ntiles, int sym,
                             unsigned long long *__restrict__ band_pairs) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ntiles) return;
@@ -66,7 +66,9 @@ __global__ void k_tile_band(const float *__restrict__ qalpha, int64_t m,
     const double a0 = (double)qalpha[q0], a1 = (double)qalpha[q1];
     const double lo_x = (a0 - W) - 4.0 * kU64 * (fabs(a0) + W);
     const double hi_x = (a1 + W) + 4.0 * kU64 * (fabs(a1) + W);
-    const int64_t lo = lower_bound_ge(alpha, n, lo_x);
+    // symmetric self-join: a tile scores only rows at or after its own first
+    // query, each unordered pair once (the mirror is emitted on acceptance)
+    const int64_t lo = sym ? q0 : lower_bound_ge(alpha, n, lo_x);
     const int64_t hi = max(lo, upper_bound_gt(alpha, n, hi_x));
     tile_lo[t] = lo;
     tile_hi[t] = hi;
@@ -239,7 +241,9 @@ __device__ __forceinline__ void score_body(const ScoreArgs &a) {
 #pragma unroll
                 for (int w = 0; w < 8; ++w) {
                     const int rj = (w < 4 ? 0 : 64) + tx * 4 + (w & 3);
-                    const bool ok = (acc[u][w] >= neg) && (j0 + rj < band_hi);
+                    const int64_t jj = j0 + rj;
+                    const bool ok = (acc[u][w] >= neg) && (jj < band_hi) &&
+                                    (!a.sym || jj >= q0 + qi);
                     mask |= (unsigned long long)ok << (u * 8 + w);
                 }
             }
@@ -277,21 +281,29 @@ __global__ void __launch_bounds__(kScoreThreads, 2) k_score_fp32_multi(ScoreArgs
     score_body<false>(a);
 }
 
-// ------------------------------------------------------- FP64 decision
-// Eq. (3) in the oracle's order: t = p_k - q_k, S = S + t*t, ascending k,
-// round-to-nearest intrinsics so no FMA is formed.  Keeps the pair iff
-// S <= R2 and records (original query row, original point id, (float)S).
-__global__ void k_recheck(const uint2 *__restrict__ surv, int64_t nsurv,
-                          const float *__restrict__ qraw, const int32_t *__restrict__ qorder,
-                          const float *__restrict__ praw, const int32_t *__restrict__ porder,
-                          int d, int dp, double R2, int32_t *__restrict__ rec_row,
-                          int32_t *__restrict__ rec_col, float *__restrict__ rec_d2,
-                          int32_t *__restrict__ counts) {
-    const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (s >= nsurv) return;
-    const uint2 e = surv[s];
-    const float4 *pq = reinterpret_cast<const float4 *>(qraw + int64_t(e.x) * dp);
-    const float4 *pp = reinterpret_cast<const float4 *>(praw + int64_t(e.y) * dp);
+// ------------------------------------------------------- exact decision
+// Each survivor is decided as the FP64 definition Eq. (3) would decide it
+// (oracle order: t = p_k - q_k, S = S + t*t, ascending k, no FMA).
+//
+// Tier 1 evaluates the same sum in compensated FP32 ("double-float"):
+// TwoSum gives p_k - q_k = s + e exactly, FMA gives s^2 = ph + pl exactly,
+// c = fl(pl + 2 s e) carries the rest (error <= 4u^2 ph with e^2 dropped),
+// and (H, L) accumulates with TwoSum / FastTwoSum renormalisation (error
+// <= 7u^2 per step relative to the running sum).  So
+//   |H + L - S_true| <= (7d + 5) u^2 S,   u = 2^-24,
+// and the FP64 oracle sits within gamma_{d+2} S of S_true (the paper's bound
+// for the direct form, Section 4).  When R^2 and the nearest float rounding
+// boundary of S are both farther than the sum of the two bounds, the FP32
+// result decides membership and gives (float)S exactly; otherwise (ties,
+// near-ties, overflow or underflow) tier 2 runs the FP64 loop itself.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    const float ap = __fsub_rn(s, bp);
+    e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
+__device__ __forceinline__ double dist2_fp64(const float4 *pp, const float4 *pq, int d, int dp) {
     double S = 0.0;
     for (int k4 = 0; k4 < dp / 4; ++k4) {
         const float4 a = pp[k4], b = pq[k4];
@@ -305,16 +317,106 @@ __global__ void k_recheck(const uint2 *__restrict__ surv, int64_t nsurv,
             }
         }
     }
-    if (S <= R2) {
-        const int32_t row = qorder[e.x];
-        rec_row[s] = row;
-        rec_col[s] = porder[e.y];
-        rec_d2[s] = (float)S;
+    return S;
+}
+
+template <bool kSym>
+__device__ __forceinline__ void decide_body(
+         const uint2 *__restrict__ surv, int64_t nsurv, const float *__restrict__ qraw,
+         const int32_t *__restrict__ qorder, const float *__restrict__ praw,
+         const int32_t *__restrict__ porder, int d, int dp, double R2,
+         int32_t *__restrict__ rec_row, int32_t *__restrict__ rec_col, float *__restrict__ rec_d2,
+         int32_t *__restrict__ counts, unsigned long long *__restrict__ n_fp64) {
+    const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (s >= nsurv) return;
+    const uint2 e = surv[s];
+    const float4 *pq = reinterpret_cast<const float4 *>(qraw + int64_t(e.x) * dp);
+    const float4 *pp = reinterpret_cast<const float4 *>(praw + int64_t(e.y) * dp);
+    float H = 0.f, L = 0.f;
+    for (int k4 = 0; k4 < dp / 4; ++k4) {
+        const float4 a = pp[k4], b = pq[k4];
+        const float av[4] = {a.x, a.y, a.z, a.w};
+        const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (k4 * 4 + c < d) {
+                float sd, ed;
+                two_sum(av[c], -bv[c], sd, ed);
+                const float ph = __fmul_rn(sd, sd);
+                const float pl = __fmaf_rn(sd, sd, -ph);
+                const float cc = __fmaf_rn(__fadd_rn(sd, sd), ed, pl);
+                float s1, t1;
+                two_sum(H, ph, s1, t1);
+                const float t3 = __fadd_rn(__fadd_rn(t1, L), cc);
+                H = __fadd_rn(s1, t3);
+                L = __fsub_rn(t3, __fsub_rn(H, s1));
+            }
+        }
+    }
+    const double S_df = (double)H + (double)L;   // exact: |L| <= ulp(H)/2
+    const double rel = ((7.0 * d + 6.0) * 0x1p-48 + (d + 3.0) * 0x1p-53) * 1.01;
+    const double tol = rel * S_df + (double)d * 0x1p-140;
+    bool fallback = !(H < 0x1p100f) || !(H >= 0.f);   // overflow / NaN
+    bool accept = false;
+    float d2 = H;
+    if (!fallback) {
+        if (S_df + tol < R2) accept = true;
+        else if (S_df - tol > R2) accept = false;
+        else fallback = true;
+        if (accept && !fallback && H > 0.f) {
+            // distance of S to the rounding boundaries of H = fl32(S)
+            const float up = __uint_as_float(__float_as_uint(H) + 1u);
+            const float dn = __uint_as_float(__float_as_uint(H) - 1u);
+            const double half_up = 0.5 * ((double)up - (double)H);
+            const double half_dn = 0.5 * ((double)H - (double)dn);
+            const double room = L >= 0.f ? half_up - (double)L : half_dn + (double)L;
+            if (room <= tol) fallback = true;
+        }
+    }
+    if (fallback) {
+        const double S = dist2_fp64(pp, pq, d, dp);
+        accept = S <= R2;
+        d2 = (float)S;
+        atomicAdd(n_fp64, 1ull);
+    }
+    const int64_t slot = kSym ? 2 * s : s;
+    if (accept) {
+        const int32_t row = qorder[e.x], col = porder[e.y];
+        rec_row[slot] = row;
+        rec_col[slot] = col;
+        rec_d2[slot] = d2;
         atomicAdd(&counts[row], 1);
+        if (kSym) {
+            if (e.x != e.y) {
+                rec_row[slot + 1] = col;
+                rec_col[slot + 1] = row;
+                rec_d2[slot + 1] = d2;
+                atomicAdd(&counts[col], 1);
+            } else {
+                rec_row[slot + 1] = -1;
+            }
+        }
     } else {
-        rec_row[s] = -1;
+        rec_row[slot] = -1;
+        if (kSym) rec_row[slot + 1] = -1;
     }
 }
+
+#define SNN_DECIDE_ARGS                                                                      \
+    const uint2 *__restrict__ surv, int64_t nsurv, const float *__restrict__ qraw,             \
+        const int32_t *__restrict__ qorder, const float *__restrict__ praw,                    \
+        const int32_t *__restrict__ porder, int d, int dp, double R2,                          \
+        int32_t *__restrict__ rec_row, int32_t *__restrict__ rec_col, float *__restrict__ rec_d2, \
+        int32_t *__restrict__ counts, unsigned long long *__restrict__ n_fp64
+__global__ void __launch_bounds__(256) k_decide_sym(SNN_DECIDE_ARGS) {
+    decide_body<true>(surv, nsurv, qraw, qorder, praw, porder, d, dp, R2, rec_row, rec_col, rec_d2,
+                      counts, n_fp64);
+}
+__global__ void __launch_bounds__(256) k_decide_one(SNN_DECIDE_ARGS) {
+    decide_body<false>(surv, nsurv, qraw, qorder, praw, porder, d, dp, R2, rec_row, rec_col, rec_d2,
+                       counts, n_fp64);
+}
+#undef SNN_DECIDE_ARGS
 
 __global__ void k_counts_to_i64(const int32_t *__restrict__ counts, int64_t m,
                                 int64_t *__restrict__ out) {
@@ -336,54 +438,102 @@ __global__ void k_scatter(const int32_t *__restrict__ rec_row, const int32_t *__
 }
 
 // ------------------------------------------- per-row sort by column id
+// Rows by length: [0] <= 32, [1] <= 128 (one warp each), [2] <= 4096 (one
+// block each), [3] longer (radix sort).  lists holds 3 arrays of m entries.
 __global__ void k_seg_classify(const int64_t *__restrict__ offsets, int64_t m,
-                               int32_t *__restrict__ small_list, int32_t *__restrict__ mid_list,
-                               int32_t *__restrict__ big_list, int64_t *__restrict__ big_len,
-                               unsigned *__restrict__ counters) {
+                               int32_t *__restrict__ lists, int32_t *__restrict__ big_list,
+                               int64_t *__restrict__ big_len, unsigned *__restrict__ counters) {
     const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (r >= m) return;
     const int64_t len = offsets[r + 1] - offsets[r];
-    if (len == 0) return;
+    if (len <= 1) return;   // nothing to order (the scatter wrote it in place)
     if (len <= kSegSmall) {
-        small_list[atomicAdd(&counters[0], 1u)] = (int32_t)r;
+        lists[atomicAdd(&counters[0], 1u)] = (int32_t)r;
+    } else if (len <= 4 * kSegSmall) {
+        lists[m + atomicAdd(&counters[1], 1u)] = (int32_t)r;
     } else if (len <= kSegMid) {
-        mid_list[atomicAdd(&counters[1], 1u)] = (int32_t)r;
+        lists[2 * m + atomicAdd(&counters[2], 1u)] = (int32_t)r;
     } else {
-        const unsigned b = atomicAdd(&counters[2], 1u);
+        const unsigned b = atomicAdd(&counters[3], 1u);
         big_list[b] = (int32_t)r;
         big_len[b] = len;
     }
 }
 
-// One warp per row of <= 32 entries: bitonic network over lanes.
-__global__ void k_seg_sort_small(const int32_t *__restrict__ list, const unsigned *__restrict__ count,
-                                 const int64_t *__restrict__ offsets,
-                                 const int32_t *__restrict__ idx_u, const float *__restrict__ d2_u,
-                                 int32_t *__restrict__ idx, float *__restrict__ d2) {
+// One warp per row of <= 32*E entries: bitonic network over E registers x 32
+// lanes (element r*32 + lane lives in register r of that lane).
+template <int E>
+__device__ __forceinline__ void seg_sort_warp(const int32_t *__restrict__ list, unsigned total,
+                                              const int64_t *__restrict__ offsets,
+                                              const int32_t *__restrict__ idx_u,
+                                              const float *__restrict__ d2_u,
+                                              int32_t *__restrict__ idx, float *__restrict__ d2) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
-    const unsigned total = *count;
     for (int64_t w = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); w < total; w += nw) {
         const int32_t r = list[w];
         const int64_t o = offsets[r];
         const int len = int(offsets[r + 1] - o);
-        int32_t key = lane < len ? idx_u[o + lane] : INT32_MAX;
-        float val = lane < len ? d2_u[o + lane] : 0.f;
-        for (int k = 2; k <= 32; k <<= 1) {
+        int32_t key[E];
+        float val[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int i = e * 32 + lane;
+            key[e] = i < len ? idx_u[o + i] : INT32_MAX;
+            val[e] = i < len ? d2_u[o + i] : 0.f;
+        }
+#pragma unroll
+        for (int k = 2; k <= 32 * E; k <<= 1) {
+#pragma unroll
             for (int j = k >> 1; j > 0; j >>= 1) {
-                const int32_t pk = __shfl_xor_sync(0xffffffffu, key, j);
-                const float pv = __shfl_xor_sync(0xffffffffu, val, j);
-                const bool up = (lane & k) == 0;
-                const bool lower = (lane & j) == 0;
-                const bool take = (lower == up) ? (pk < key) : (pk > key);
-                if (take) { key = pk; val = pv; }
+                if (j >= 32) {
+                    const int jr = j >> 5;
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const int pe = e ^ jr;
+                        if (pe > e) {
+                            const bool asc = ((e * 32 + lane) & k) == 0;
+                            if ((key[e] > key[pe]) == asc) {
+                                const int32_t tk = key[e]; key[e] = key[pe]; key[pe] = tk;
+                                const float tv = val[e]; val[e] = val[pe]; val[pe] = tv;
+                            }
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const int32_t pk = __shfl_xor_sync(0xffffffffu, key[e], j);
+                        const float pv = __shfl_xor_sync(0xffffffffu, val[e], j);
+                        const bool asc = ((e * 32 + lane) & k) == 0;
+                        const bool lower = (lane & j) == 0;
+                        const bool take = (lower == asc) ? (pk < key[e]) : (pk > key[e]);
+                        if (take) { key[e] = pk; val[e] = pv; }
+                    }
+                }
             }
         }
-        if (lane < len) {
-            idx[o + lane] = key;
-            d2[o + lane] = val;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int i = e * 32 + lane;
+            if (i < len) {
+                idx[o + i] = key[e];
+                d2[o + i] = val[e];
+            }
         }
     }
+}
+
+__global__ void k_seg_sort_w1(const int32_t *__restrict__ list, const unsigned *__restrict__ count,
+                              const int64_t *__restrict__ offsets, const int32_t *__restrict__ idx_u,
+                              const float *__restrict__ d2_u, int32_t *__restrict__ idx,
+                              float *__restrict__ d2) {
+    seg_sort_warp<1>(list, *count, offsets, idx_u, d2_u, idx, d2);
+}
+__global__ void k_seg_sort_w4(const int32_t *__restrict__ list, const unsigned *__restrict__ count,
+                              const int64_t *__restrict__ offsets, const int32_t *__restrict__ idx_u,
+                              const float *__restrict__ d2_u, int32_t *__restrict__ idx,
+                              float *__restrict__ d2) {
+    seg_sort_warp<4>(list, *count, offsets, idx_u, d2_u, idx, d2);
 }
 
 // One block per row of <= 4096 entries: bitonic sort in shared memory.

@@ -40,6 +40,7 @@ struct ScoreArgs {
     const int64_t *tile_hi;
     const int64_t *item_off;    // ntiles + 1, exclusive scan of items per tile
     int ntiles;
+    int sym;                    // symmetric self-join: only pairs with row >= query
     float c1;                   // rounding constant of the FP32 score
     uint2 *surv;                // survivor pairs (sorted query pos, sorted row)
     int64_t cap;
@@ -50,17 +51,24 @@ struct ScoreArgs {
 __global__ void k_query_consts(const float *hy, const float *qn, int64_t m, int d, double Rx,
                                double e_data, float *thrA);
 __global__ void k_tile_band(const float *qalpha, int64_t m, const float *alpha, int64_t n,
-                            double Wbase, const float *eps_d, const float *eps_q, int64_t *tile_lo, int64_t *tile_hi, int64_t *items,
-                            int ntiles, unsigned long long *band_pairs);
+                            double Wbase, const float *eps_d, const float *eps_q,
+                            int64_t *tile_lo, int64_t *tile_hi, int64_t *items, int ntiles,
+                            int sym, unsigned long long *band_pairs);
 __global__ void k_query_windows(const float *qalpha, int64_t m, const float *alpha, int64_t n,
                                 double Wbase, const float *eps_d, const float *eps_q,
                                 unsigned long long *cand);
 __global__ void k_score_fp32_single(ScoreArgs a);
 __global__ void k_score_fp32_multi(ScoreArgs a);
-__global__ void k_recheck(const uint2 *surv, int64_t nsurv, const float *qraw,
-                          const int32_t *qorder, const float *praw, const int32_t *porder,
-                          int d, int dp, double R2, int32_t *rec_row, int32_t *rec_col,
-                          float *rec_d2, int32_t *counts);
+// Exact decision of survivors; _sym emits both orientations of a self-join
+// pair, _one emits the (query, point) orientation only.
+__global__ void k_decide_sym(const uint2 *surv, int64_t nsurv, const float *qraw,
+                             const int32_t *qorder, const float *praw, const int32_t *porder,
+                             int d, int dp, double R2, int32_t *rec_row, int32_t *rec_col,
+                             float *rec_d2, int32_t *counts, unsigned long long *n_fp64);
+__global__ void k_decide_one(const uint2 *surv, int64_t nsurv, const float *qraw,
+                             const int32_t *qorder, const float *praw, const int32_t *porder,
+                             int d, int dp, double R2, int32_t *rec_row, int32_t *rec_col,
+                             float *rec_d2, int32_t *counts, unsigned long long *n_fp64);
 __global__ void k_counts_to_i64(const int32_t *counts, int64_t m, int64_t *out);
 __global__ void k_scatter(const int32_t *rec_row, const int32_t *rec_col, const float *rec_d2,
                           int64_t nsurv, const int64_t *offsets, int32_t *cursor,
@@ -69,12 +77,12 @@ __global__ void k_scatter(const int32_t *rec_row, const int32_t *rec_col, const 
 // Segmented sort of CSR rows by column id.
 constexpr int kSegSmall = 32;
 constexpr int kSegMid = 4096;
-__global__ void k_seg_classify(const int64_t *offsets, int64_t m, int32_t *small_list,
-                               int32_t *mid_list, int32_t *big_list, int64_t *big_len,
-                               unsigned *counters);
-__global__ void k_seg_sort_small(const int32_t *list, const unsigned *count, const int64_t *offsets,
-                                 const int32_t *idx_u, const float *d2_u, int32_t *idx,
-                                 float *d2);
+__global__ void k_seg_classify(const int64_t *offsets, int64_t m, int32_t *lists,
+                               int32_t *big_list, int64_t *big_len, unsigned *counters);
+__global__ void k_seg_sort_w1(const int32_t *list, const unsigned *count, const int64_t *offsets,
+                              const int32_t *idx_u, const float *d2_u, int32_t *idx, float *d2);
+__global__ void k_seg_sort_w4(const int32_t *list, const unsigned *count, const int64_t *offsets,
+                              const int32_t *idx_u, const float *d2_u, int32_t *idx, float *d2);
 __global__ void k_seg_sort_mid(const int32_t *list, const unsigned *count, const int64_t *offsets,
                                const int32_t *idx_u, const float *d2_u, int32_t *idx, float *d2);
 __global__ void k_seg_big_gather(const int32_t *big_list, int nbig, const int64_t *offsets,

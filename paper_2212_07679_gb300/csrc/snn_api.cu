@@ -2,6 +2,7 @@
 // (Algorithm 1), the query phase (Algorithm 2 with Section 4's blocked
 // scoring) and DBSCAN on the self-join (Section 6.4).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -39,6 +40,8 @@ namespace snn {
 
 namespace {
 thread_local char g_err[512] = "";
+std::atomic<unsigned long long> g_launches{0};
+std::atomic<double> g_surv_hint{0.0};   // survivors per query of the last call
 std::once_flag g_pool_once;
 
 void pool_setup() {
@@ -59,6 +62,7 @@ void set_error(const char *fmt, ...) {
     va_end(ap);
 }
 void clear_error() { g_err[0] = 0; }
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 int device_sm_count() {
     int dev = 0, sms = 0;
@@ -106,11 +110,11 @@ static snn_status project_sort_gather(const float *X, int64_t n, int d, int64_t 
     SNN_TRY(scr.alloc(&ka, n));
     SNN_TRY(scr.alloc(&va, n));
     const int64_t pthreads = d > 32 ? n * 32 : n;
-    k_project<<<grid_for(pthreads, 256), 256, 0, s>>>(X, n, d, ld, mu64, v32, keys, vals,
+    SNN_LAUNCH(k_project, grid_for(pthreads, 256), 256, 0, s)(X, n, d, ld, mu64, v32, keys, vals,
                                                       eps_out, bad);
     SNN_LAUNCH_CHECK();
     SNN_TRY(radix_sort_pairs<uint32_t>(keys, vals, ka, va, n, 32, s));
-    k_gather<<<grid_for(pthreads, 256), 256, 0, s>>>(keys, vals, X, n, d, ld, dp, mu64, alpha,
+    SNN_LAUNCH(k_gather, grid_for(pthreads, 256), 256, 0, s)(keys, vals, X, n, d, ld, dp, mu64, alpha,
                                                      order, praw, xc, hx, nrm);
     SNN_LAUNCH_CHECK();
     return SNN_OK;
@@ -130,7 +134,7 @@ static snn_status first_direction(const double *C, int d, double *v64, float *v3
     if (d <= kPcSmallMaxD) {
         const size_t smem = (2 * d + 32) * sizeof(double) + 32 * sizeof(float) +
                             2 * size_t(d) * d * sizeof(float);
-        k_pc_small<<<1, 1024, smem, s>>>(C, d, v64, v32);
+        SNN_LAUNCH(k_pc_small, 1, 1024, smem, s)(C, d, v64, v32);
         SNN_LAUNCH_CHECK();
         return SNN_OK;
     }
@@ -142,30 +146,30 @@ static snn_status first_direction(const double *C, int d, double *v64, float *v3
     SNN_TRY(scr.alloc(&scale, 1));
     SNN_TRY(scr.alloc(&tr, 1));
     SNN_TRY(scr.alloc(&w, d));
-    k_pc_init<<<1, 1024, 0, s>>>(C, d, M, tr);
+    SNN_LAUNCH(k_pc_init, 1, 1024, 0, s)(C, d, M, tr);
     SNN_LAUNCH_CHECK();
-    k_scale_from_double<<<grid_for(dd, 256), 256, 0, s>>>(C, dd, tr, M);
+    SNN_LAUNCH(k_scale_from_double, grid_for(dd, 256), 256, 0, s)(C, dd, tr, M);
     SNN_LAUNCH_CHECK();
     const int nt = (int)cdiv(d, kGramTile);
     for (int it = 0; it < 12; ++it) {
-        k_square<<<dim3(nt, nt), 256, 0, s>>>(M, d, T);
+        SNN_LAUNCH(k_square, dim3(nt, nt), 256, 0, s)(M, d, T);
         SNN_LAUNCH_CHECK();
-        k_trace_f<<<1, 1024, 0, s>>>(T, d, scale);
+        SNN_LAUNCH(k_trace_f, 1, 1024, 0, s)(T, d, scale);
         SNN_LAUNCH_CHECK();
-        k_scale_f<<<grid_for(dd, 256), 256, 0, s>>>(T, dd, scale, M);
+        SNN_LAUNCH(k_scale_f, grid_for(dd, 256), 256, 0, s)(T, dd, scale, M);
         SNN_LAUNCH_CHECK();
     }
-    k_pick_column<<<1, 256, 0, s>>>(M, d, tr, v64);
+    SNN_LAUNCH(k_pick_column, 1, 256, 0, s)(M, d, tr, v64);
     SNN_LAUNCH_CHECK();
     for (int it = 0; it < 4; ++it) {
-        k_matvec64<<<grid_for(int64_t(d) * 32, 256), 256, 0, s>>>(C, d, v64, w);
+        SNN_LAUNCH(k_matvec64, grid_for(int64_t(d) * 32, 256), 256, 0, s)(C, d, v64, w);
         SNN_LAUNCH_CHECK();
-        k_normalise64<<<1, 1024, 0, s>>>(w, d, v64, v32, 0);
+        SNN_LAUNCH(k_normalise64, 1, 1024, 0, s)(w, d, v64, v32, 0);
         SNN_LAUNCH_CHECK();
     }
     // final FP64 normalisation (also writes the FP32 copy)
     SNN_CUDA(cudaMemcpyAsync(w, v64, d * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    k_normalise64<<<1, 1024, 0, s>>>(w, d, v64, v32, 1);
+    SNN_LAUNCH(k_normalise64, 1, 1024, 0, s)(w, d, v64, v32, 1);
     SNN_LAUNCH_CHECK();
     return SNN_OK;
 }
@@ -219,10 +223,10 @@ static snn_status index_build(const float *X, int64_t n, int d, int64_t ld, cuda
         double *part;
         TRY_IX(scr.alloc(&part, size_t(nb) * d));
         const int TX = d < 32 ? d : 32, TY = 256 / TX;
-        k_colsum_partial<<<(unsigned)nb, TX * TY, TX * TY * sizeof(double), s>>>(X, n, d, ld, rows,
+        SNN_LAUNCH(k_colsum_partial, (unsigned)nb, TX * TY, TX * TY * sizeof(double), s)(X, n, d, ld, rows,
                                                                                part, bad);
         if (cudaGetLastError() != cudaSuccess) { set_error("colsum launch"); TRY_IX(SNN_ECUDA); }
-        k_mean_final<<<grid_for(d, 128), 128, 0, s>>>(part, (int)nb, d, n, ix->mu64, ix->mu32);
+        SNN_LAUNCH(k_mean_final, grid_for(d, 128), 128, 0, s)(part, (int)nb, d, n, ix->mu64, ix->mu32);
         // K2: centred Gram matrix
         const int ntile = (int)cdiv(d, kGramTile);
         const int64_t grows = std::max<int64_t>(2048, cdiv(n, 512));
@@ -231,16 +235,16 @@ static snn_status index_build(const float *X, int64_t n, int d, int64_t ld, cuda
         double *C;
         TRY_IX(scr.alloc(&gpart, size_t(nchunk) * d * d));
         TRY_IX(scr.alloc(&C, size_t(d) * d));
-        k_gram_partial<<<dim3(ntile * ntile, (unsigned)nchunk), 256, 0, s>>>(X, n, d, ld, ix->mu32,
+        SNN_LAUNCH(k_gram_partial, dim3(ntile * ntile, (unsigned)nchunk), 256, 0, s)(X, n, d, ld, ix->mu32,
                                                                              grows, ntile, gpart);
-        k_gram_reduce<<<grid_for(int64_t(d) * d, 256), 256, 0, s>>>(gpart, (int)nchunk, d, C);
+        SNN_LAUNCH(k_gram_reduce, grid_for(int64_t(d) * d, 256), 256, 0, s)(gpart, (int)nchunk, d, C);
         if (cudaGetLastError() != cudaSuccess) { set_error("gram launch"); TRY_IX(SNN_ECUDA); }
         // K3: first principal direction
         TRY_IX(first_direction(C, d, ix->v64, ix->v32, s, scr));
         // K4-K6: scores, sort, gather
         TRY_IX(project_sort_gather(X, n, d, ld, dp, ix->mu64, ix->v32, s, scr, ix->dconst + 0, bad,
                                    ix->alpha, ix->order, ix->praw, ix->xc, ix->hx, ix->nrm));
-        k_max_nonneg<<<std::min<unsigned>(grid_for(n, 256), 1024), 256, 0, s>>>(ix->nrm, n,
+        SNN_LAUNCH(k_max_nonneg, std::min<unsigned>(grid_for(n, 256), 1024), 256, 0, s)(ix->nrm, n,
                                                                                 ix->dconst + 1);
         if (cudaGetLastError() != cudaSuccess) { set_error("max launch"); TRY_IX(SNN_ECUDA); }
         float hc[2];
@@ -369,24 +373,26 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
 
     float *thrA;
     TRY_Q(scr.alloc(&thrA, m));
-    k_query_consts<<<grid_for(m, 256), 256, 0, s>>>(qs.hx, qs.nrm, m, d, Rx, e_data, thrA);
+    SNN_LAUNCH(k_query_consts, grid_for(m, 256), 256, 0, s)(qs.hx, qs.nrm, m, d, Rx, e_data, thrA);
     CUDA_Q(cudaGetLastError());
 
     const int ntiles = (int)cdiv(m, kBQ);
     int64_t *tile_lo, *tile_hi, *items, *item_off;
-    unsigned long long *ctr;   // [0] survivors, [1] work, [2] band pairs, [3] candidates
+    // [0] survivors, [1] work, [2] band pairs, [3] candidates, [4] FP64 decisions
+    unsigned long long *ctr;
+    const int sym = self ? 1 : 0;
     TRY_Q(scr.alloc(&tile_lo, ntiles));
     TRY_Q(scr.alloc(&tile_hi, ntiles));
     TRY_Q(scr.alloc(&items, ntiles));
     TRY_Q(scr.alloc(&item_off, ntiles + 1));
-    TRY_Q(scr.alloc(&ctr, 4));
-    CUDA_Q(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), s));
-    k_tile_band<<<grid_for(ntiles, 128), 128, 0, s>>>(qs.alpha, m, ix->alpha, ix->n, Wbase,
+    TRY_Q(scr.alloc(&ctr, 8));
+    CUDA_Q(cudaMemsetAsync(ctr, 0, 8 * sizeof(unsigned long long), s));
+    SNN_LAUNCH(k_tile_band, grid_for(ntiles, 128), 128, 0, s)(qs.alpha, m, ix->alpha, ix->n, Wbase,
                                                       ix->dconst, eps_q, tile_lo, tile_hi, items,
-                                                      ntiles, stats ? ctr + 2 : nullptr);
+                                                      ntiles, sym, stats ? ctr + 2 : nullptr);
     CUDA_Q(cudaGetLastError());
     if (stats) {
-        k_query_windows<<<grid_for(m, 256), 256, 0, s>>>(qs.alpha, m, ix->alpha, ix->n, Wbase,
+        SNN_LAUNCH(k_query_windows, grid_for(m, 256), 256, 0, s)(qs.alpha, m, ix->alpha, ix->n, Wbase,
                                                          ix->dconst, eps_q, ctr + 3);
         CUDA_Q(cudaGetLastError());
     }
@@ -398,8 +404,11 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         std::lock_guard<std::mutex> lk(ix->mu);
         hint = ix->surv_hint;
     }
+    if (!(hint > 0)) hint = g_surv_hint.load(std::memory_order_relaxed);
+    // generous first guess (the pool keeps the memory cached); an overflow
+    // costs one re-run of the scoring with the exact count
     int64_t cap = std::max<int64_t>(int64_t(1) << 20,
-                                    int64_t(std::ceil((hint > 0 ? hint * 1.25 : 16.0) * m)) + 4096);
+                                    int64_t(std::ceil((hint > 0 ? hint * 1.25 : 96.0) * m)) + 4096);
     CUDA_Q(cudaMallocAsync(&surv, size_t(cap) * sizeof(uint2), s));
     ScoreArgs sa;
     sa.q = qs;
@@ -409,6 +418,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     sa.tile_hi = tile_hi;
     sa.item_off = item_off;
     sa.ntiles = ntiles;
+    sa.sym = sym;
     sa.c1 = (float)((2.0 * d + 4.0) * (double)kU32 * 1.05);
     sa.count = ctr;
     sa.work = ctr + 1;
@@ -424,9 +434,9 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         } else {
             const int grid = device_sm_count() * 2;
             if (dp <= 16)
-                k_score_fp32_single<<<grid, 256, 0, s>>>(sa);
+                SNN_LAUNCH(k_score_fp32_single, grid, 256, 0, s)(sa);
             else
-                k_score_fp32_multi<<<grid, 256, 0, s>>>(sa);
+                SNN_LAUNCH(k_score_fp32_multi, grid, 256, 0, s)(sa);
             if (cudaGetLastError() != cudaSuccess) {
                 set_error("score kernel launch failed");
                 st = SNN_ECUDA;
@@ -462,14 +472,16 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         std::lock_guard<std::mutex> lk(ix->mu);
         ix->surv_hint = double(nsurv) / double(m);
     }
+    g_surv_hint.store(double(nsurv) / double(m), std::memory_order_relaxed);
 
-    // exact FP64 decision for every survivor
+    // exact decision for every survivor (compensated FP32, FP64 where needed)
+    const int64_t nrec = sym ? 2 * nsurv : nsurv;
     int32_t *rec_row, *rec_col, *counts, *cursor;
     float *rec_d2;
     int64_t *counts64;
-    TRY_Q(scr.alloc(&rec_row, nsurv));
-    TRY_Q(scr.alloc(&rec_col, nsurv));
-    TRY_Q(scr.alloc(&rec_d2, nsurv));
+    TRY_Q(scr.alloc(&rec_row, nrec));
+    TRY_Q(scr.alloc(&rec_col, nrec));
+    TRY_Q(scr.alloc(&rec_d2, nrec));
     TRY_Q(scr.alloc(&counts, m));
     TRY_Q(scr.alloc(&cursor, m));
     TRY_Q(scr.alloc(&counts64, m));
@@ -477,15 +489,20 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     CUDA_Q(cudaMemsetAsync(cursor, 0, m * sizeof(int32_t), s));
     const double R2 = R * R;
     if (nsurv > 0) {
-        k_recheck<<<grid_for(nsurv, 256), 256, 0, s>>>(surv, nsurv, qs.raw, qs.order, ds.raw,
-                                                       ds.order, d, dp, R2, rec_row, rec_col,
-                                                       rec_d2, counts);
+        if (sym)
+            SNN_LAUNCH(k_decide_sym, grid_for(nsurv, 256), 256, 0, s)(surv, nsurv, qs.raw, qs.order, ds.raw,
+                                                                ds.order, d, dp, R2, rec_row, rec_col,
+                                                                rec_d2, counts, ctr + 4);
+        else
+            SNN_LAUNCH(k_decide_one, grid_for(nsurv, 256), 256, 0, s)(surv, nsurv, qs.raw, qs.order,
+                                                                 ds.raw, ds.order, d, dp, R2, rec_row,
+                                                                 rec_col, rec_d2, counts, ctr + 4);
         CUDA_Q(cudaGetLastError());
     }
     cudaFreeAsync(surv, s);
     surv = nullptr;
     if (stats) cudaEventRecord(ev[3], s);
-    k_counts_to_i64<<<grid_for(m, 256), 256, 0, s>>>(counts, m, counts64);
+    SNN_LAUNCH(k_counts_to_i64, grid_for(m, 256), 256, 0, s)(counts, m, counts64);
     CUDA_Q(cudaGetLastError());
     TRY_Q(scan_exclusive<int64_t>(counts64, out->offsets, m, s));
     int64_t nnz = 0;
@@ -503,31 +520,36 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         float *d2_u;
         TRY_Q(scr.alloc(&idx_u, nnz));
         TRY_Q(scr.alloc(&d2_u, nnz));
-        k_scatter<<<grid_for(nsurv, 256), 256, 0, s>>>(rec_row, rec_col, rec_d2, nsurv,
-                                                       out->offsets, cursor, idx_u, d2_u);
+        SNN_LAUNCH(k_scatter, grid_for(nrec, 256), 256, 0, s)(rec_row, rec_col, rec_d2, nrec,
+                                                      out->offsets, cursor, idx_u, d2_u);
         CUDA_Q(cudaGetLastError());
         // per-row ascending column ids
         int32_t *lists, *big_list;
         int64_t *big_len, *toff;
         unsigned *cls;
-        TRY_Q(scr.alloc(&lists, 2 * m));
+        TRY_Q(scr.alloc(&lists, 3 * m));
         TRY_Q(scr.alloc(&big_list, m));
         TRY_Q(scr.alloc(&big_len, m));
         TRY_Q(scr.alloc(&toff, m + 1));
         TRY_Q(scr.alloc(&cls, 4));
         CUDA_Q(cudaMemsetAsync(cls, 0, 4 * sizeof(unsigned), s));
-        k_seg_classify<<<grid_for(m, 256), 256, 0, s>>>(out->offsets, m, lists, lists + m, big_list,
-                                                        big_len, cls);
-        CUDA_Q(cudaGetLastError());
-        k_seg_sort_small<<<std::min<unsigned>(grid_for(m * 32, 256), 8192), 256, 0, s>>>(
-            lists, cls, out->offsets, idx_u, d2_u, out->indices, out->dist2);
-        k_seg_sort_mid<<<std::min<unsigned>((unsigned)m, 4096), 256, 0, s>>>(
-            lists + m, cls + 1, out->offsets, idx_u, d2_u, out->indices, out->dist2);
+        SNN_LAUNCH(k_seg_classify, grid_for(m, 256), 256, 0, s)(out->offsets, m, lists, big_list,
+                                                                big_len, cls);
+        // rows of 0 or 1 entries are already in place
+        CUDA_Q(cudaMemcpyAsync(out->indices, idx_u, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        CUDA_Q(cudaMemcpyAsync(out->dist2, d2_u, nnz * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        const unsigned wgrid = std::min<unsigned>(grid_for(m * 32, 256), 16384);
+        SNN_LAUNCH(k_seg_sort_w1, wgrid, 256, 0, s)(lists, cls, out->offsets, idx_u, d2_u,
+                                                     out->indices, out->dist2);
+        SNN_LAUNCH(k_seg_sort_w4, wgrid, 256, 0, s)(lists + m, cls + 1, out->offsets, idx_u, d2_u,
+                                                     out->indices, out->dist2);
+        SNN_LAUNCH(k_seg_sort_mid, std::min<unsigned>((unsigned)m, 4096), 256, 0, s)(
+            lists + 2 * m, cls + 2, out->offsets, idx_u, d2_u, out->indices, out->dist2);
         CUDA_Q(cudaGetLastError());
         unsigned hcls[4];
         CUDA_Q(cudaMemcpyAsync(hcls, cls, sizeof(hcls), cudaMemcpyDeviceToHost, s));
         CUDA_Q(cudaStreamSynchronize(s));
-        const int nbig = (int)hcls[2];
+        const int nbig = (int)hcls[3];
         if (nbig > 0) {
             TRY_Q(scan_exclusive<int64_t>(big_len, toff, nbig, s));
             int64_t tot = 0;
@@ -539,12 +561,12 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
             TRY_Q(scr.alloc(&bka, tot));
             TRY_Q(scr.alloc(&bv, tot));
             TRY_Q(scr.alloc(&bva, tot));
-            k_seg_big_gather<<<nbig, 256, 0, s>>>(big_list, nbig, out->offsets, toff, idx_u, bk, bv);
+            SNN_LAUNCH(k_seg_big_gather, nbig, 256, 0, s)(big_list, nbig, out->offsets, toff, idx_u, bk, bv);
             CUDA_Q(cudaGetLastError());
             int bits = 32;
             while ((int64_t(1) << (bits - 32)) < nbig) ++bits;
             TRY_Q(radix_sort_pairs<uint64_t>(bk, bv, bka, bva, tot, bits, s));
-            k_seg_big_scatter<<<grid_for(tot, 256), 256, 0, s>>>(bk, bv, tot, big_list, out->offsets,
+            SNN_LAUNCH(k_seg_big_scatter, grid_for(tot, 256), 256, 0, s)(bk, bv, tot, big_list, out->offsets,
                                                                  toff, d2_u, out->indices,
                                                                  out->dist2);
             CUDA_Q(cudaGetLastError());
@@ -552,7 +574,10 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     }
     if (stats) {
         cudaEventRecord(ev[4], s);
+        unsigned long long nf = 0;
+        CUDA_Q(cudaMemcpyAsync(&nf, ctr + 4, sizeof(nf), cudaMemcpyDeviceToHost, s));
         CUDA_Q(cudaStreamSynchronize(s));
+        stats->exact_fp64 = (int64_t)nf;
         stats->candidates = (int64_t)hctr[3];
         stats->band_pairs = (int64_t)hctr[2];
         stats->survivors = nsurv;
@@ -667,13 +692,13 @@ snn_status snn_dbscan(const float *X, int64_t n, int32_t d, int64_t ld, double e
         if (st == SNN_OK) st = scr.alloc(&owner, n);
         if (st == SNN_OK) st = scr.alloc(&minid, n);
         if (st == SNN_OK) {
-            k_db_core<<<grid_for(n, 256), 256, 0, s>>>(csr.offsets, n, min_pts, is_core, parent);
-            k_db_union<<<grid_for(n * 32, 256), 256, 0, s>>>(csr.offsets, csr.indices, n, is_core,
+            SNN_LAUNCH(k_db_core, grid_for(n, 256), 256, 0, s)(csr.offsets, n, min_pts, is_core, parent);
+            SNN_LAUNCH(k_db_union, grid_for(n * 32, 256), 256, 0, s)(csr.offsets, csr.indices, n, is_core,
                                                              parent);
-            k_db_init_minid<<<grid_for(n, 256), 256, 0, s>>>(minid, n);
-            k_db_assign<<<grid_for(n, 256), 256, 0, s>>>(csr.offsets, csr.indices, n, is_core,
+            SNN_LAUNCH(k_db_init_minid, grid_for(n, 256), 256, 0, s)(minid, n);
+            SNN_LAUNCH(k_db_assign, grid_for(n, 256), 256, 0, s)(csr.offsets, csr.indices, n, is_core,
                                                          parent, owner, minid);
-            k_db_label<<<grid_for(n, 256), 256, 0, s>>>(owner, minid, n, labels);
+            SNN_LAUNCH(k_db_label, grid_for(n, 256), 256, 0, s)(owner, minid, n, labels);
             cudaError_t e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) {
@@ -714,5 +739,7 @@ void snn_index_free(snn_index *idx) { index_release(idx); }
 const char *snn_last_error(void) { return g_err; }
 
 const char *snn_version(void) { return "snn-gb300 0.1 (sm_103a)"; }
+
+uint64_t snn_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 }  // extern "C"

@@ -111,7 +111,7 @@ snn_status scan_exclusive(const T *in, T *out, int64_t n, cudaStream_t s) {
     }
     const int64_t nb = cdiv(n, kScanTile);
     if (nb <= 8) {
-        k_scan_single<T><<<1, kScanThreads, 0, s>>>(in, out, n);
+        SNN_LAUNCH(k_scan_single<T>, 1, kScanThreads, 0, s)(in, out, n);
         SNN_LAUNCH_CHECK();
         return SNN_OK;
     }
@@ -119,10 +119,10 @@ snn_status scan_exclusive(const T *in, T *out, int64_t n, cudaStream_t s) {
     T *sums, *offs;
     SNN_TRY(scr.alloc(&sums, nb));
     SNN_TRY(scr.alloc(&offs, nb + 1));
-    k_scan_reduce<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums);
+    SNN_LAUNCH(k_scan_reduce<T>, (unsigned)nb, kScanThreads, 0, s)(in, n, sums);
     SNN_LAUNCH_CHECK();
     SNN_TRY(scan_exclusive<T>(sums, offs, nb, s));
-    k_scan_down<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, offs);
+    SNN_LAUNCH(k_scan_down<T>, (unsigned)nb, kScanThreads, 0, s)(in, out, n, offs);
     SNN_LAUNCH_CHECK();
     return SNN_OK;
 }
@@ -233,10 +233,10 @@ snn_status radix_sort_pairs(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals
     uint32_t *va = vals, *vb = vals_alt;
     int passes = 0;
     for (int shift = 0; shift < end_bit; shift += 8, ++passes) {
-        k_radix_upsweep<K><<<(unsigned)nb, kRadixThreads, 0, s>>>(ka, n, shift, hist);
+        SNN_LAUNCH(k_radix_upsweep<K>, (unsigned)nb, kRadixThreads, 0, s)(ka, n, shift, hist);
         SNN_LAUNCH_CHECK();
         SNN_TRY(scan_exclusive<uint32_t>(hist, offs, hn, s));
-        k_radix_downsweep<K><<<(unsigned)nb, kRadixThreads, 0, s>>>(ka, va, kb, vb, n, shift, offs);
+        SNN_LAUNCH(k_radix_downsweep<K>, (unsigned)nb, kRadixThreads, 0, s)(ka, va, kb, vb, n, shift, offs);
         SNN_LAUNCH_CHECK();
         K *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;

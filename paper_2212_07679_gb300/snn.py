@@ -35,7 +35,7 @@ class CSRStruct(ctypes.Structure):
 class StatsStruct(ctypes.Structure):
     _fields_ = [("candidates", ctypes.c_int64), ("band_pairs", ctypes.c_int64),
                 ("survivors", ctypes.c_int64), ("nnz", ctypes.c_int64),
-                ("ms_prep", ctypes.c_float), ("ms_score", ctypes.c_float),
+                ("exact_fp64", ctypes.c_int64), ("ms_prep", ctypes.c_float), ("ms_score", ctypes.c_float),
                 ("ms_recheck", ctypes.c_float), ("ms_csr", ctypes.c_float)]
 
 
@@ -74,6 +74,8 @@ def _load():
     lib.snn_last_error.restype = ctypes.c_char_p
     lib.snn_version.argtypes = []
     lib.snn_version.restype = ctypes.c_char_p
+    lib.snn_launch_count.argtypes = []
+    lib.snn_launch_count.restype = ctypes.c_uint64
     return lib
 
 
@@ -278,3 +280,8 @@ def dbscan(X: torch.Tensor, eps: float, min_pts: int, precision: str = "fp32", s
 
 def version() -> str:
     return lib.snn_version().decode()
+
+
+def launch_count() -> int:
+    """Kernels launched by libsnn in this process so far."""
+    return int(lib.snn_launch_count())

@@ -222,3 +222,24 @@ def test_full_size_self_join_sampled(snn):
     fwd = rowid.astype(np.int64) * w.n + idx
     bwd = idx.astype(np.int64) * w.n + rowid
     assert np.array_equal(np.sort(fwd), np.sort(bwd))
+
+
+def test_exact_ties_take_the_fp64_path(snn):
+    # integer grid with R = 2: many pairs sit exactly on the boundary S == R^2,
+    # which the compensated FP32 tier cannot settle; they must be decided by
+    # the FP64 loop and included (inclusive radius)
+    g = np.stack(np.meshgrid(np.arange(9), np.arange(9), np.arange(9)), -1).reshape(-1, 3)
+    P = g.astype(np.float32) * np.float32(0.5)
+    got = _run(snn, P, None, 1.0, "fp32")
+    assert_csr_equal(got, oracle.brute_radius(P, None, 1.0), "half-integer grid")
+    assert got.stats["exact_fp64"] > 0
+    # random data: the FP64 loop is (almost) never needed
+    w = wl.gmm_aniso(n=20000, sub=2000)
+    got = _run(snn, w.P, None, w.R, "fp32")
+    assert got.stats["exact_fp64"] <= max(2, got.stats["survivors"] // 10000)
+
+
+def test_launch_counter_moves(snn):
+    before = snn.launch_count()
+    _run(snn, np.random.default_rng(1).standard_normal((500, 3)).astype(np.float32), None, 0.5, "fp32")
+    assert snn.launch_count() > before
