@@ -1,0 +1,33 @@
+// Definition of the opaque index (Algorithm 1 output) shared by the host
+// modules of libsnn.
+#pragma once
+#include <mutex>
+#include "common.cuh"
+
+struct snn_index {
+    int64_t n = 0;
+    int d = 0, dp = 0;
+    int device = 0;
+    double *mu64 = nullptr;
+    float *mu32 = nullptr;
+    double *v64 = nullptr;
+    float *v32 = nullptr;
+    float *alpha = nullptr;
+    int32_t *order = nullptr;
+    float *praw = nullptr;
+    float *xc = nullptr;
+    float *hx = nullptr;
+    float *nrm = nullptr;
+    float *dconst = nullptr;      // device: [0] alpha error bound, [1] max norm
+    // BF16 split operands of the tensor-core path (built on first use):
+    // tc_part[p] is n x tc_k2 bf16, part p of the split of each centred row
+    // plus the folded threshold columns.
+    uint16_t *tc_part[3] = {nullptr, nullptr, nullptr};
+    int tc_nsplit = 0;
+    int tc_k2 = 0;
+    float alpha_err = 0.f;
+    float nrm_max = 0.f;
+    mutable double surv_hint = 0.0;   // survivors per query seen last time
+    mutable std::mutex mu;
+};
+

@@ -12,29 +12,7 @@
 #include "index_kernels.cuh"
 #include "query_kernels.cuh"
 #include "tc_score.cuh"
-
-struct snn_index {
-    int64_t n = 0;
-    int d = 0, dp = 0;
-    int device = 0;
-    double *mu64 = nullptr;
-    float *mu32 = nullptr;
-    double *v64 = nullptr;
-    float *v32 = nullptr;
-    float *alpha = nullptr;
-    int32_t *order = nullptr;
-    float *praw = nullptr;
-    float *xc = nullptr;
-    float *hx = nullptr;
-    float *nrm = nullptr;
-    float *dconst = nullptr;      // device: [0] alpha error bound, [1] max norm
-    uint16_t *xb = nullptr;       // BF16 centred rows (n x dpb), built on demand
-    int dpb = 0;
-    float alpha_err = 0.f;
-    float nrm_max = 0.f;
-    mutable double surv_hint = 0.0;   // survivors per query seen last time
-    mutable std::mutex mu;
-};
+#include "index_struct.cuh"
 
 namespace snn {
 
@@ -91,8 +69,9 @@ static snn_status dev_alloc(T **p, size_t count) {
 
 static void index_release(snn_index *ix) {
     if (!ix) return;
-    void *ptrs[] = {ix->mu64, ix->mu32, ix->v64, ix->v32, ix->alpha, ix->order,
-                    ix->praw, ix->xc, ix->hx, ix->nrm, ix->dconst, ix->xb};
+    void *ptrs[] = {ix->mu64, ix->mu32, ix->v64,   ix->v32,        ix->alpha,      ix->order,
+                    ix->praw, ix->xc,   ix->hx,    ix->nrm,        ix->dconst,     ix->tc_part[0],
+                    ix->tc_part[1], ix->tc_part[2]};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete ix;
