@@ -326,7 +326,8 @@ __device__ __forceinline__ void decide_body(
          const int32_t *__restrict__ qorder, const float *__restrict__ praw,
          const int32_t *__restrict__ porder, int d, int dp, double R2,
          int32_t *__restrict__ rec_row, int32_t *__restrict__ rec_col, float *__restrict__ rec_d2,
-         int32_t *__restrict__ counts, unsigned long long *__restrict__ n_fp64) {
+         int32_t *__restrict__ rec_pos, int32_t *__restrict__ counts,
+         unsigned long long *__restrict__ n_fp64) {
     const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (s >= nsurv) return;
     const uint2 e = surv[s];
@@ -379,19 +380,21 @@ __device__ __forceinline__ void decide_body(
         d2 = (float)S;
         atomicAdd(n_fp64, 1ull);
     }
+    // records: (row, column, dist2, position within the row); the position
+    // comes from the counting atomic, so the scatter needs no atomics
     const int64_t slot = kSym ? 2 * s : s;
     if (accept) {
         const int32_t row = qorder[e.x], col = porder[e.y];
         rec_row[slot] = row;
         rec_col[slot] = col;
         rec_d2[slot] = d2;
-        atomicAdd(&counts[row], 1);
+        rec_pos[slot] = atomicAdd(&counts[row], 1);
         if (kSym) {
             if (e.x != e.y) {
                 rec_row[slot + 1] = col;
                 rec_col[slot + 1] = row;
                 rec_d2[slot + 1] = d2;
-                atomicAdd(&counts[col], 1);
+                rec_pos[slot + 1] = atomicAdd(&counts[col], 1);
             } else {
                 rec_row[slot + 1] = -1;
             }
@@ -407,14 +410,15 @@ __device__ __forceinline__ void decide_body(
         const int32_t *__restrict__ qorder, const float *__restrict__ praw,                    \
         const int32_t *__restrict__ porder, int d, int dp, double R2,                          \
         int32_t *__restrict__ rec_row, int32_t *__restrict__ rec_col, float *__restrict__ rec_d2, \
-        int32_t *__restrict__ counts, unsigned long long *__restrict__ n_fp64
+        int32_t *__restrict__ rec_pos, int32_t *__restrict__ counts,                          \
+        unsigned long long *__restrict__ n_fp64
 __global__ void __launch_bounds__(256) k_decide_sym(SNN_DECIDE_ARGS) {
     decide_body<true>(surv, nsurv, qraw, qorder, praw, porder, d, dp, R2, rec_row, rec_col, rec_d2,
-                      counts, n_fp64);
+                      rec_pos, counts, n_fp64);
 }
 __global__ void __launch_bounds__(256) k_decide_one(SNN_DECIDE_ARGS) {
     decide_body<false>(surv, nsurv, qraw, qorder, praw, porder, d, dp, R2, rec_row, rec_col, rec_d2,
-                       counts, n_fp64);
+                       rec_pos, counts, n_fp64);
 }
 #undef SNN_DECIDE_ARGS
 
@@ -425,21 +429,22 @@ __global__ void k_counts_to_i64(const int32_t *__restrict__ counts, int64_t m,
 }
 
 __global__ void k_scatter(const int32_t *__restrict__ rec_row, const int32_t *__restrict__ rec_col,
-                          const float *__restrict__ rec_d2, int64_t nsurv,
-                          const int64_t *__restrict__ offsets, int32_t *__restrict__ cursor,
+                          const float *__restrict__ rec_d2, const int32_t *__restrict__ rec_pos,
+                          int64_t nsurv, const int64_t *__restrict__ offsets,
                           int32_t *__restrict__ idx_u, float *__restrict__ d2_u) {
     const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (s >= nsurv) return;
     const int32_t row = rec_row[s];
     if (row < 0) return;
-    const int64_t pos = offsets[row] + atomicAdd(&cursor[row], 1);
+    const int64_t pos = offsets[row] + rec_pos[s];
     idx_u[pos] = rec_col[s];
     d2_u[pos] = rec_d2[s];
 }
 
 // ------------------------------------------- per-row sort by column id
-// Rows by length: [0] <= 32, [1] <= 128 (one warp each), [2] <= 4096 (one
-// block each), [3] longer (radix sort).  lists holds 3 arrays of m entries.
+// Rows by length: [0] <= 32, [1] <= 128, [2] <= 512 (one warp each),
+// [3] <= 4096 (one block each), [4] longer (radix sort).  lists holds 4
+// arrays of m entries.
 __global__ void k_seg_classify(const int64_t *__restrict__ offsets, int64_t m,
                                int32_t *__restrict__ lists, int32_t *__restrict__ big_list,
                                int64_t *__restrict__ big_len, unsigned *__restrict__ counters) {
@@ -451,10 +456,12 @@ __global__ void k_seg_classify(const int64_t *__restrict__ offsets, int64_t m,
         lists[atomicAdd(&counters[0], 1u)] = (int32_t)r;
     } else if (len <= 4 * kSegSmall) {
         lists[m + atomicAdd(&counters[1], 1u)] = (int32_t)r;
-    } else if (len <= kSegMid) {
+    } else if (len <= 16 * kSegSmall) {
         lists[2 * m + atomicAdd(&counters[2], 1u)] = (int32_t)r;
+    } else if (len <= kSegMid) {
+        lists[3 * m + atomicAdd(&counters[3], 1u)] = (int32_t)r;
     } else {
-        const unsigned b = atomicAdd(&counters[3], 1u);
+        const unsigned b = atomicAdd(&counters[4], 1u);
         big_list[b] = (int32_t)r;
         big_len[b] = len;
     }
@@ -528,6 +535,12 @@ __global__ void k_seg_sort_w1(const int32_t *__restrict__ list, const unsigned *
                               const float *__restrict__ d2_u, int32_t *__restrict__ idx,
                               float *__restrict__ d2) {
     seg_sort_warp<1>(list, *count, offsets, idx_u, d2_u, idx, d2);
+}
+__global__ void k_seg_sort_w16(const int32_t *__restrict__ list, const unsigned *__restrict__ count,
+                               const int64_t *__restrict__ offsets, const int32_t *__restrict__ idx_u,
+                               const float *__restrict__ d2_u, int32_t *__restrict__ idx,
+                               float *__restrict__ d2) {
+    seg_sort_warp<16>(list, *count, offsets, idx_u, d2_u, idx, d2);
 }
 __global__ void k_seg_sort_w4(const int32_t *__restrict__ list, const unsigned *__restrict__ count,
                               const int64_t *__restrict__ offsets, const int32_t *__restrict__ idx_u,

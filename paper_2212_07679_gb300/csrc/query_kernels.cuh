@@ -46,6 +46,7 @@ struct ScoreArgs {
     int64_t cap;
     unsigned long long *count;  // survivors found (may exceed cap)
     unsigned long long *work;   // work-item counter
+    int *err;                   // device error flag (bounded waits that gave up)
 };
 
 __global__ void k_query_consts(const float *hy, const float *qn, int64_t m, int d, double Rx,
@@ -64,14 +65,16 @@ __global__ void k_score_fp32_multi(ScoreArgs a);
 __global__ void k_decide_sym(const uint2 *surv, int64_t nsurv, const float *qraw,
                              const int32_t *qorder, const float *praw, const int32_t *porder,
                              int d, int dp, double R2, int32_t *rec_row, int32_t *rec_col,
-                             float *rec_d2, int32_t *counts, unsigned long long *n_fp64);
+                             float *rec_d2, int32_t *rec_pos, int32_t *counts,
+                             unsigned long long *n_fp64);
 __global__ void k_decide_one(const uint2 *surv, int64_t nsurv, const float *qraw,
                              const int32_t *qorder, const float *praw, const int32_t *porder,
                              int d, int dp, double R2, int32_t *rec_row, int32_t *rec_col,
-                             float *rec_d2, int32_t *counts, unsigned long long *n_fp64);
+                             float *rec_d2, int32_t *rec_pos, int32_t *counts,
+                             unsigned long long *n_fp64);
 __global__ void k_counts_to_i64(const int32_t *counts, int64_t m, int64_t *out);
 __global__ void k_scatter(const int32_t *rec_row, const int32_t *rec_col, const float *rec_d2,
-                          int64_t nsurv, const int64_t *offsets, int32_t *cursor,
+                          const int32_t *rec_pos, int64_t nsurv, const int64_t *offsets,
                           int32_t *idx_u, float *d2_u);
 
 // Segmented sort of CSR rows by column id.
@@ -81,6 +84,8 @@ __global__ void k_seg_classify(const int64_t *offsets, int64_t m, int32_t *lists
                                int32_t *big_list, int64_t *big_len, unsigned *counters);
 __global__ void k_seg_sort_w1(const int32_t *list, const unsigned *count, const int64_t *offsets,
                               const int32_t *idx_u, const float *d2_u, int32_t *idx, float *d2);
+__global__ void k_seg_sort_w16(const int32_t *list, const unsigned *count, const int64_t *offsets,
+                               const int32_t *idx_u, const float *d2_u, int32_t *idx, float *d2);
 __global__ void k_seg_sort_w4(const int32_t *list, const unsigned *count, const int64_t *offsets,
                               const int32_t *idx_u, const float *d2_u, int32_t *idx, float *d2);
 __global__ void k_seg_sort_mid(const int32_t *list, const unsigned *count, const int64_t *offsets,

@@ -401,6 +401,11 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     sa.c1 = (float)((2.0 * d + 4.0) * (double)kU32 * 1.05);
     sa.count = ctr;
     sa.work = ctr + 1;
+    int *dev_err;
+    TRY_Q(scr.alloc(&dev_err, 1));
+    CUDA_Q(cudaMemsetAsync(dev_err, 0, sizeof(int), s));
+    sa.err = dev_err;
+    int herr = 0;
     unsigned long long hctr[4] = {0, 0, 0, 0};
     int hbad = 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
@@ -409,7 +414,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         if (stats) cudaEventRecord(ev[1], s);
         snn_status st = SNN_OK;
         if (prec == SNN_PREC_BF16) {
-            st = tc_score_launch(ix, sa, s);
+            st = tc_score_launch(ix, sa, s, Rx, e_data, scr);
         } else {
             const int grid = device_sm_count() * 2;
             if (dp <= 16)
@@ -426,7 +431,9 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         cudaError_t e1 = cudaMemcpyAsync(hctr, ctr, 4 * sizeof(unsigned long long),
                                          cudaMemcpyDeviceToHost, s);
         cudaError_t e2 = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+        cudaError_t e4 = cudaMemcpyAsync(&herr, dev_err, sizeof(int), cudaMemcpyDeviceToHost, s);
         cudaError_t e3 = cudaStreamSynchronize(s);
+        if (e4 != cudaSuccess) e2 = e4;
         if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
             set_error("scoring failed: %s", cudaGetErrorString(e3 != cudaSuccess ? e3 : e1));
             return fail(SNN_ECUDA);
@@ -434,6 +441,10 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         if (hbad) {
             set_error("Q contains NaN or Inf");
             return fail(SNN_EINVAL);
+        }
+        if (herr) {
+            set_error("tensor-core scoring: a bounded wait gave up (pipeline stalled)");
+            return fail(SNN_ETIMEOUT);
         }
         if ((int64_t)hctr[0] <= cap) break;
         if (attempt == 1) {
@@ -455,27 +466,27 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
 
     // exact decision for every survivor (compensated FP32, FP64 where needed)
     const int64_t nrec = sym ? 2 * nsurv : nsurv;
-    int32_t *rec_row, *rec_col, *counts, *cursor;
+    int32_t *rec_row, *rec_col, *rec_pos, *counts;
     float *rec_d2;
     int64_t *counts64;
     TRY_Q(scr.alloc(&rec_row, nrec));
     TRY_Q(scr.alloc(&rec_col, nrec));
     TRY_Q(scr.alloc(&rec_d2, nrec));
+    TRY_Q(scr.alloc(&rec_pos, nrec));
     TRY_Q(scr.alloc(&counts, m));
-    TRY_Q(scr.alloc(&cursor, m));
     TRY_Q(scr.alloc(&counts64, m));
     CUDA_Q(cudaMemsetAsync(counts, 0, m * sizeof(int32_t), s));
-    CUDA_Q(cudaMemsetAsync(cursor, 0, m * sizeof(int32_t), s));
     const double R2 = R * R;
     if (nsurv > 0) {
         if (sym)
             SNN_LAUNCH(k_decide_sym, grid_for(nsurv, 256), 256, 0, s)(surv, nsurv, qs.raw, qs.order, ds.raw,
                                                                 ds.order, d, dp, R2, rec_row, rec_col,
-                                                                rec_d2, counts, ctr + 4);
+                                                                rec_d2, rec_pos, counts, ctr + 4);
         else
             SNN_LAUNCH(k_decide_one, grid_for(nsurv, 256), 256, 0, s)(surv, nsurv, qs.raw, qs.order,
                                                                  ds.raw, ds.order, d, dp, R2, rec_row,
-                                                                 rec_col, rec_d2, counts, ctr + 4);
+                                                                 rec_col, rec_d2, rec_pos, counts,
+                                                                 ctr + 4);
         CUDA_Q(cudaGetLastError());
     }
     cudaFreeAsync(surv, s);
@@ -499,19 +510,19 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         float *d2_u;
         TRY_Q(scr.alloc(&idx_u, nnz));
         TRY_Q(scr.alloc(&d2_u, nnz));
-        SNN_LAUNCH(k_scatter, grid_for(nrec, 256), 256, 0, s)(rec_row, rec_col, rec_d2, nrec,
-                                                      out->offsets, cursor, idx_u, d2_u);
+        SNN_LAUNCH(k_scatter, grid_for(nrec, 256), 256, 0, s)(rec_row, rec_col, rec_d2, rec_pos, nrec,
+                                                      out->offsets, idx_u, d2_u);
         CUDA_Q(cudaGetLastError());
         // per-row ascending column ids
         int32_t *lists, *big_list;
         int64_t *big_len, *toff;
         unsigned *cls;
-        TRY_Q(scr.alloc(&lists, 3 * m));
+        TRY_Q(scr.alloc(&lists, 4 * m));
         TRY_Q(scr.alloc(&big_list, m));
         TRY_Q(scr.alloc(&big_len, m));
         TRY_Q(scr.alloc(&toff, m + 1));
-        TRY_Q(scr.alloc(&cls, 4));
-        CUDA_Q(cudaMemsetAsync(cls, 0, 4 * sizeof(unsigned), s));
+        TRY_Q(scr.alloc(&cls, 8));
+        CUDA_Q(cudaMemsetAsync(cls, 0, 8 * sizeof(unsigned), s));
         SNN_LAUNCH(k_seg_classify, grid_for(m, 256), 256, 0, s)(out->offsets, m, lists, big_list,
                                                                 big_len, cls);
         // rows of 0 or 1 entries are already in place
@@ -522,13 +533,15 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
                                                      out->indices, out->dist2);
         SNN_LAUNCH(k_seg_sort_w4, wgrid, 256, 0, s)(lists + m, cls + 1, out->offsets, idx_u, d2_u,
                                                      out->indices, out->dist2);
+        SNN_LAUNCH(k_seg_sort_w16, wgrid, 256, 0, s)(lists + 2 * m, cls + 2, out->offsets, idx_u,
+                                                      d2_u, out->indices, out->dist2);
         SNN_LAUNCH(k_seg_sort_mid, std::min<unsigned>((unsigned)m, 4096), 256, 0, s)(
-            lists + 2 * m, cls + 2, out->offsets, idx_u, d2_u, out->indices, out->dist2);
+            lists + 3 * m, cls + 3, out->offsets, idx_u, d2_u, out->indices, out->dist2);
         CUDA_Q(cudaGetLastError());
-        unsigned hcls[4];
+        unsigned hcls[8];
         CUDA_Q(cudaMemcpyAsync(hcls, cls, sizeof(hcls), cudaMemcpyDeviceToHost, s));
         CUDA_Q(cudaStreamSynchronize(s));
-        const int nbig = (int)hcls[3];
+        const int nbig = (int)hcls[4];
         if (nbig > 0) {
             TRY_Q(scan_exclusive<int64_t>(big_len, toff, nbig, s));
             int64_t tot = 0;

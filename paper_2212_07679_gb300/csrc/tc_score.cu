@@ -1,11 +1,621 @@
-// Tensor-core (tcgen05, BF16) band scoring.  Not built yet.
+// Tensor-core band scoring on sm_103a: TMA-staged BF16 operands, tcgen05.mma
+// into TMEM (FP32 accumulation), sign test in the epilogue.
+//
+// The left side of Eq. (4), x_j^T x_j/2 - x_j^T x_q, is scored for a tile of
+// 128 queries (sorted by score) against 128-row chunks of the union band
+// (Section 4: one gemm over the union of the candidate ranges).  Every
+// centred FP32 row is split into BF16 parts, x = x1 + x2 (+ x3), and the
+// products x1.y1 + x1.y2 + x2.y1 (+ x1.y3 + x2.y2 + x3.y1) are accumulated
+// in FP32.  The rejection threshold is folded into the contraction as
+// rank-one columns, so the accumulator itself is
+//     acc_ij = x_j.y_i - (1 - c) xbar_j + c ||y_i|| ||x_j|| + A_i,
+// where A_i bounds (R + slack)^2/2 - ||y_i||^2/2 and c bounds every rounding
+// (split, FP32 accumulation, norms) relative to xbar_j + ||x_j|| ||y_i||.
+// A pair the FP64 definition could accept has acc_ij > 0, so a pair is
+// rejected exactly when the sign bit of acc_ij is set; all other pairs go to
+// the exact decision like the FP32 path's survivors.
+//
+// Warp roles (192 threads): warp 0 issues TMA loads, warp 1 owns TMEM and
+// issues the MMAs, warps 2-5 drain the accumulators.  Stages are guarded by
+// mbarriers; every wait is bounded and a timeout sets an error flag.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "index_struct.cuh"
 #include "tc_score.cuh"
 
 namespace snn {
 
-snn_status tc_score_launch(const snn_index *, const ScoreArgs &, cudaStream_t) {
-    set_error("BF16 tensor-core scoring is not available in this build");
-    return SNN_ENOTSUP;
+namespace {
+
+constexpr int kTM = 128;            // queries per tile (MMA M)
+constexpr int kTN = 128;            // band rows per chunk (MMA N)
+constexpr int kTK = 64;             // columns per k-block (128 B rows, 128B swizzle)
+constexpr int kTileBytes = kTM * kTK * 2;   // 16 KiB per operand part per stage
+constexpr int kTcThreads = 192;
+constexpr int kExtra = 9;           // folded columns
+constexpr long long kTimeoutCycles = 4000000000LL;   // ~2 s
+
+__host__ __device__ constexpr int tc_stages(int nsplit) { return nsplit == 2 ? 3 : 2; }
+__host__ __device__ constexpr int tc_npairs(int nsplit) { return nsplit == 2 ? 3 : 6; }
+__host__ __device__ constexpr size_t tc_smem_bytes(int nsplit) {
+    return size_t(tc_stages(nsplit)) * nsplit * 2 * kTileBytes + 1024 /*align*/ + 256 /*bars*/;
+}
+
+// ------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; on timeout (or when another role already gave up) sets the
+// abort flags and returns false.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                          int *err) {
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kTimeoutCycles) {
+            *abort_flag = 1;
+            atomicOr(err, 1);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile, 128-byte rows, 128B swizzle,
+// 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= uint64_t((saddr & 0x3FFFFu) >> 4);
+    d |= uint64_t(1) << 16;                 // leading byte offset (unused here)
+    d |= uint64_t(1024 >> 4) << 32;         // stride byte offset
+    d |= uint64_t(1) << 46;                 // descriptor version
+    d |= uint64_t(2) << 61;                 // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor of kind::f16: BF16 A and B, FP32 D, both K-major.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kTN >> 3) << 17) |
+                            (uint32_t(kTM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct TcArgs {
+    int64_t m;
+    int64_t n;
+    int ksteps;                 // 16-wide k steps that hold data or folded columns
+    int nkb;                    // 64-wide k blocks loaded per chunk
+    const int64_t *tile_lo;
+    const int64_t *tile_hi;
+    const int64_t *item_off;
+    int ntiles;
+    int sym;
+    uint2 *surv;
+    int64_t cap;
+    unsigned long long *count;
+    int *err;
+};
+
+struct ItemInfo {
+    int64_t q0, band_lo, band_hi, c_first, c_end;
+};
+
+__device__ __forceinline__ ItemInfo item_info(const TcArgs &a, int64_t item) {
+    int lo = 0, hi = a.ntiles;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (a.item_off[mid] <= item) lo = mid; else hi = mid;
+    }
+    ItemInfo f;
+    f.q0 = int64_t(lo) * kTM;
+    f.band_lo = a.tile_lo[lo];
+    f.band_hi = a.tile_hi[lo];
+    f.c_first = (item - a.item_off[lo]) * kChunksPerItem;
+    f.c_end = min(cdiv(f.band_hi - f.band_lo, kTN), f.c_first + kChunksPerItem);
+    return f;
+}
+
+template <int NSPLIT>
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUtensorMap qa1,
+           const __grid_constant__ CUtensorMap qa2, const __grid_constant__ CUtensorMap xb0,
+           const __grid_constant__ CUtensorMap xb1, const __grid_constant__ CUtensorMap xb2,
+           TcArgs a) {
+    constexpr int S = tc_stages(NSPLIT);
+    constexpr int NP = tc_npairs(NSPLIT);
+    constexpr uint32_t kStageBytes = uint32_t(NSPLIT) * 2 * kTileBytes;
+    // (A part, B part) products kept by the split: all with pa + pb <= NSPLIT-1
+    constexpr int kPa[6] = {0, 0, 1, 0, 1, 2};
+    constexpr int kPb[6] = {0, 1, 0, 2, 1, 0};
+
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char *gbase = smem_raw + (base - raw);
+    // stage s, part p: A at base + (s*NSPLIT*2 + p)*tile, B after the A parts
+    auto a_tile = [&](int s, int p) { return base + uint32_t((s * NSPLIT * 2 + p) * kTileBytes); };
+    auto b_tile = [&](int s, int p) {
+        return base + uint32_t((s * NSPLIT * 2 + NSPLIT + p) * kTileBytes);
+    };
+    const uint32_t bar0 = base + uint32_t(S * kStageBytes);
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (S + s); };
+    auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * S + b); };
+    auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * S + 2 + b); };
+    const uint32_t done_bar = bar0 + 8u * (2 * S + 4);
+    unsigned char *gmisc = gbase + S * kStageBytes + 8 * (2 * S + 5);
+    volatile uint32_t *s_tmem = reinterpret_cast<volatile uint32_t *>(gmisc);
+    volatile int *s_abort = reinterpret_cast<volatile int *>(gmisc + 4);
+    volatile int *s_consumed = reinterpret_cast<volatile int *>(gmisc + 8);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const CUtensorMap *qa[3] = {&qa0, &qa1, &qa2};
+    const CUtensorMap *xb[3] = {&xb0, &xb1, &xb2};
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull_bar(b), 1);
+            mbar_init(tempty_bar(b), 128);
+        }
+        mbar_init(done_bar, 1);
+        *s_abort = 0;
+        *s_consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        // 2 accumulators x 128 FP32 columns
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
+                         smem_u32((const void *)s_tmem))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    const uint32_t tmem = *s_tmem;
+    const int64_t total = a.item_off[a.ntiles];
+
+    int issued = 0;
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int it = 0;
+            for (int64_t item = blockIdx.x; item < total && !*s_abort; item += gridDim.x) {
+                const ItemInfo f = item_info(a, item);
+                for (int64_t c = f.c_first; c < f.c_end && !*s_abort; ++c) {
+                    const int64_t j0 = f.band_lo + c * kTN;
+                    for (int kb = 0; kb < a.nkb; ++kb, ++it) {
+                        const int s = it % S;
+                        const uint32_t round = uint32_t(it / S);
+                        if (!mbar_wait(empty_bar(s), (round & 1u) ^ 1u, s_abort, a.err)) break;
+                        mbar_expect_tx(full_bar(s), kStageBytes);
+                        for (int p = 0; p < NSPLIT; ++p) {
+                            tma_load_2d(a_tile(s, p), qa[p], kb * kTK, int(f.q0), full_bar(s));
+                            tma_load_2d(b_tile(s, p), xb[p], kb * kTK, int(j0), full_bar(s));
+                        }
+                        issued = it + 1;
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            int it = 0, chunk = 0;
+            bool ok = true;
+            for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
+                const ItemInfo f = item_info(a, item);
+                for (int64_t c = f.c_first; c < f.c_end && ok; ++c, ++chunk) {
+                    const int b = chunk & 1;
+                    const uint32_t use = uint32_t(chunk >> 1);
+                    if (!(ok = mbar_wait(tempty_bar(b), (use & 1u) ^ 1u, s_abort, a.err))) break;
+                    tmem_fence_after();
+                    const uint32_t dt = tmem + uint32_t(b * kTN);
+                    for (int kb = 0; kb < a.nkb; ++kb, ++it) {
+                        const int s = it % S;
+                        const uint32_t round = uint32_t(it / S);
+                        if (!(ok = mbar_wait(full_bar(s), round & 1u, s_abort, a.err))) break;
+                        tmem_fence_after();
+                        for (int ks = 0; ks < 4; ++ks) {
+                            if (kb * 4 + ks >= a.ksteps) break;
+#pragma unroll
+                            for (int pr = 0; pr < NP; ++pr) {
+                                const uint64_t ad = smem_desc(a_tile(s, kPa[pr]) + 32u * ks);
+                                const uint64_t bd = smem_desc(b_tile(s, kPb[pr]) + 32u * ks);
+                                mma_bf16(dt, ad, bd, (kb | ks | pr) != 0 ? 1u : 0u);
+                            }
+                        }
+                        mma_commit(empty_bar(s));
+                        *s_consumed = it + 1;
+                    }
+                    if (ok) mma_commit(tfull_bar(b));
+                }
+            }
+            // every MMA issued by this thread has completed before TMEM is freed
+            mma_commit(done_bar);
+            mbar_wait(done_bar, 0u, s_abort, a.err);
+        }
+    } else {
+        // ---------------------------------------------------- epilogue
+        const int quad = warp & 3;                 // TMEM lanes 32*quad .. +31
+        const int qi = quad * 32 + lane;           // query row within the tile
+        int chunk = 0;
+        bool ok = true;
+        for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
+            const ItemInfo f = item_info(a, item);
+            const int64_t q = f.q0 + qi;
+            for (int64_t c = f.c_first; c < f.c_end && ok; ++c, ++chunk) {
+                const int64_t j0 = f.band_lo + c * kTN;
+                const int b = chunk & 1;
+                const uint32_t use = uint32_t(chunk >> 1);
+                ok = mbar_wait(tfull_bar(b), use & 1u, s_abort, a.err);
+                if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+                tmem_fence_after();
+#pragma unroll 1
+                for (int cb = 0; cb < kTN / 32; ++cb) {
+                    uint32_t r[32];
+                    tmem_ld32(tmem + (uint32_t(quad * 32) << 16) + uint32_t(b * kTN + cb * 32), r);
+                    uint32_t all = 0xffffffffu;
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) all &= r[i];
+                    // sign bit clear somewhere: a possible neighbour in this group
+                    // a clear sign bit somewhere: a possible neighbour in this group
+                    uint32_t mask = 0;
+                    if (!(all >> 31)) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) mask |= ((r[i] >> 31) ^ 1u) << i;
+                        // validity: query inside the set, row inside the band,
+                        // symmetric self-join keeps rows at or after the query
+                        const int64_t jb = j0 + cb * 32;
+                        const int64_t lim = f.band_hi - jb;
+                        if (q >= a.m || lim <= 0) mask = 0;
+                        else if (lim < 32) mask &= (1u << lim) - 1u;
+                        if (a.sym) {
+                            const int64_t first = q - jb;
+                            if (first >= 32) mask = 0;
+                            else if (first > 0) mask &= ~((1u << first) - 1u);
+                        }
+                    }
+                    const int cnt = __popc(mask);
+                    if (__any_sync(0xffffffffu, cnt != 0)) {
+                        int incl = cnt;
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                            if (lane >= o) incl += y;
+                        }
+                        const int wtot = __shfl_sync(0xffffffffu, incl, 31);
+                        unsigned long long pos = 0;
+                        if (lane == 31) pos = atomicAdd(a.count, (unsigned long long)wtot);
+                        pos = __shfl_sync(0xffffffffu, pos, 31) + (unsigned long long)(incl - cnt);
+                        while (mask) {
+                            const int i = __ffs(mask) - 1;
+                            mask &= mask - 1;
+                            if (pos < (unsigned long long)a.cap)
+                                a.surv[pos] = make_uint2(unsigned(q), unsigned(j0 + cb * 32 + i));
+                            ++pos;
+                        }
+                    }
+                }
+                tmem_fence_before();
+                mbar_arrive(tempty_bar(b));
+            }
+        }
+    }
+    __syncthreads();
+    // drain TMA copies still in flight (only after an abort)
+    if (warp == 0 && lane == 0) {
+        for (int it = *s_consumed; it < issued; ++it)
+            mbar_wait(full_bar(it % S), uint32_t(it / S) & 1u, s_abort, a.err);
+    }
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+}
+
+// ------------------------------------------------ operand packing
+__device__ __forceinline__ uint16_t bf16_bits(__nv_bfloat16 v) {
+    return __bfloat16_as_ushort(v);
+}
+
+// Three BF16 parts of an FP64 value, |w - w1 - w2 - w3| <= 2^-23 |w|.
+__device__ __forceinline__ void split3(double w, uint16_t (&o)[3]) {
+    double r = w;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const __nv_bfloat16 b = __float2bfloat16_rn((float)r);
+        o[i] = bf16_bits(b);
+        r = r - (double)__bfloat162float(b);
+    }
+}
+
+// Row r of an operand: split parts of the centred row, then the folded
+// columns (data side: -(1-c) xbar_j split, ||x_j|| rounded up three times,
+// ones; query side: ones, c ||y_i|| split, A'_i split).
+template <int NSPLIT>
+__global__ void k_tc_pack(const float *__restrict__ xc, int dp, const float *__restrict__ hx,
+                          const float *__restrict__ nrm, const double *__restrict__ Aq,
+                          int64_t rows, int d, int K2, double c, int query_side,
+                          uint16_t *__restrict__ p0, uint16_t *__restrict__ p1,
+                          uint16_t *__restrict__ p2) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= rows * K2) return;
+    const int64_t r = e / K2;
+    const int k = int(e % K2);
+    uint16_t v0 = 0, v1 = 0, v2 = 0;
+    if (k < d) {
+        const float x = xc[r * dp + k];
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        const float xr = x - __bfloat162float(h);               // exact
+        const __nv_bfloat16 l = __float2bfloat16_rn(xr);
+        v0 = bf16_bits(h);
+        v1 = bf16_bits(l);
+        if (NSPLIT == 3) v2 = bf16_bits(__float2bfloat16_rn(xr - __bfloat162float(l)));
+    } else if (k < d + kExtra) {
+        const int t = k - d;
+        uint16_t sp[3];
+        if (!query_side) {
+            if (t < 3) {
+                split3(-(1.0 - c) * (double)hx[r], sp);
+                v0 = sp[t];
+            } else if (t < 6) {
+                v0 = bf16_bits(__float2bfloat16_ru(nrm[r]));
+            } else {
+                v0 = bf16_bits(__float2bfloat16_rn(1.0f));
+            }
+        } else {
+            if (t < 3) {
+                v0 = bf16_bits(__float2bfloat16_rn(1.0f));
+            } else if (t < 6) {
+                split3(c * (double)nrm[r], sp);
+                v0 = sp[t - 3];
+            } else {
+                split3(Aq[r], sp);
+                v0 = sp[t - 6];
+            }
+        }
+    }
+    p0[e] = v0;
+    if (NSPLIT >= 2) p1[e] = v1;
+    if (NSPLIT >= 3) p2[e] = v2;
+}
+
+// A'_i >= (Rx + e_data + e_i)^2/2 - ||y_i||^2/2, inflated so that its split
+// representation and the accumulation rounding (delta) keep the sign test
+// conservative, plus a margin that makes an acceptable pair's acc positive.
+__global__ void k_tc_query_consts(const float *__restrict__ hy, const float *__restrict__ qn,
+                                  int64_t m, int d, double Rx, double e_data, double delta,
+                                  double *__restrict__ Aq) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const double ei = 1.0001 * (double)kU32 * (double)qn[i];
+    const double r = Rx + e_data + ei;
+    const double hy_low = (double)hy[i] * (1.0 - 1.05 * (d + 2) * (double)kU32);
+    double A = 0.5 * r * r - hy_low;
+    A += 4.0 * kU64 * (fabs(A) + 0.5 * r * r + (double)hy[i]);
+    A = A >= 0.0 ? A / (1.0 - delta) : A / (1.0 + delta);
+    A += 0x1p-22 * fabs(A) + 0x1p-100;
+    Aq[i] = A;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+snn_status make_map(CUtensorMap *map, const uint16_t *ptr, int64_t rows, int K2) {
+    EncodeTiledFn enc = get_encode();
+    if (!enc) {
+        set_error("cuTensorMapEncodeTiled is unavailable");
+        return SNN_ENOTSUP;
+    }
+    cuuint64_t dims[2] = {cuuint64_t(K2), cuuint64_t(rows)};
+    cuuint64_t strides[1] = {cuuint64_t(K2) * 2};
+    cuuint32_t box[2] = {cuuint32_t(kTK), cuuint32_t(kTM)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(ptr), dims,
+                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d)", int(r));
+        return SNN_ECUDA;
+    }
+    return SNN_OK;
+}
+
+// Rounding constant c of the folded test for a split and a dimension.
+double tc_constant(int nsplit, int d, double *u_k_out) {
+    const int ksteps = int(cdiv(d + kExtra, 16));
+    const int ninstr = tc_npairs(nsplit) * ksteps;
+    // FP32 accumulation: each MMA instruction is charged 2^-22 of (|C_in| +
+    // sum of its |products|), i.e. (ninstr + 1) 2^-22 of all |products|
+    const double u_k = 0x1p-22 * (ninstr + 1);
+    const double quant = nsplit == 2 ? 3.1 * 0x1p-16 : 4.2 * 0x1p-24;
+    const double c_mn = (quant + 1.01 * u_k) / (1.0 - 0x1p-23 - u_k);
+    const double c_hx = 0x1p-23 + 1.05 * (d + 2) * 0x1p-24 + u_k;
+    if (u_k_out) *u_k_out = u_k;
+    return 1.02 * (c_mn > c_hx ? c_mn : c_hx);
+}
+
+template <int NSPLIT>
+snn_status launch_tc(const snn_index *ix, const ScoreArgs &sa, const uint16_t *const *qp,
+                     int K2, cudaStream_t s) {
+    CUtensorMap maps[6];
+    for (int p = 0; p < 3; ++p) {
+        const int pp = p < NSPLIT ? p : 0;
+        SNN_TRY(make_map(&maps[p], qp[pp], sa.q.m, K2));
+        SNN_TRY(make_map(&maps[3 + p], ix->tc_part[pp], ix->n, K2));
+    }
+    const size_t smem = tc_smem_bytes(NSPLIT);
+    SNN_CUDA(cudaFuncSetAttribute(k_score_tc<NSPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  int(smem)));
+    TcArgs a;
+    a.m = sa.q.m;
+    a.n = ix->n;
+    a.ksteps = int(cdiv(ix->d + kExtra, 16));
+    a.nkb = K2 / kTK;
+    a.tile_lo = sa.tile_lo;
+    a.tile_hi = sa.tile_hi;
+    a.item_off = sa.item_off;
+    a.ntiles = sa.ntiles;
+    a.sym = sa.sym;
+    a.surv = sa.surv;
+    a.cap = sa.cap;
+    a.count = sa.count;
+    a.err = sa.err;
+    SNN_LAUNCH(k_score_tc<NSPLIT>, device_sm_count(), kTcThreads, smem, s)(
+        maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], a);
+    SNN_LAUNCH_CHECK();
+    return SNN_OK;
+}
+
+}  // namespace
+
+snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream_t s,
+                           double Rx, double e_data, Scratch &scr) {
+    snn_index *ix = const_cast<snn_index *>(ixc);
+    const int d = ix->d;
+    const double R2h = 0.5 * Rx * Rx;
+    // the two-part split suffices when its slack stays a small fraction of
+    // R^2/2 for the largest norms; otherwise use three parts
+    const double N = (double)ix->nrm_max;
+    const double c2 = tc_constant(2, d, nullptr);
+    const int nsplit = (c2 * 1.5 * N * N <= 0.02 * R2h) ? 2 : 3;
+    double u_k = 0.0;
+    const double c = tc_constant(nsplit, d, &u_k);
+    const int K2 = int(cdiv(d + kExtra, kTK) * kTK);
+    {
+        std::lock_guard<std::mutex> lk(ix->mu);
+        if (ix->tc_nsplit != nsplit) {
+            for (int p = 0; p < 3; ++p) {
+                if (ix->tc_part[p]) cudaFree(ix->tc_part[p]);
+                ix->tc_part[p] = nullptr;
+            }
+            ix->tc_nsplit = 0;
+            for (int p = 0; p < nsplit; ++p) {
+                cudaError_t e = cudaMalloc(&ix->tc_part[p], size_t(ix->n) * K2 * sizeof(uint16_t));
+                if (e != cudaSuccess) {
+                    set_error("BF16 operand allocation failed: %s", cudaGetErrorString(e));
+                    return SNN_ENOMEM;
+                }
+            }
+            const int64_t tot = ix->n * K2;
+            auto packer = nsplit == 2 ? k_tc_pack<2> : k_tc_pack<3>;
+            SNN_LAUNCH(packer, unsigned(cdiv(tot, 256)), 256, 0, s)(
+                ix->xc, ix->dp, ix->hx, ix->nrm, nullptr, ix->n, d, K2, c, 0, ix->tc_part[0],
+                ix->tc_part[1], ix->tc_part[2]);
+            SNN_LAUNCH_CHECK();
+            ix->tc_nsplit = nsplit;
+            ix->tc_k2 = K2;
+        }
+    }
+    // query operands (per call): same split, query-side folded columns
+    const int64_t m = sa.q.m;
+    double *Aq;
+    uint16_t *qp[3] = {nullptr, nullptr, nullptr};
+    SNN_TRY(scr.alloc(&Aq, m));
+    for (int p = 0; p < nsplit; ++p) SNN_TRY(scr.alloc(&qp[p], size_t(m) * K2));
+    SNN_LAUNCH(k_tc_query_consts, unsigned(cdiv(m, 256)), 256, 0, s)(
+        sa.q.hx, sa.q.nrm, m, d, Rx, e_data, 0x1p-23 + u_k, Aq);
+    SNN_LAUNCH_CHECK();
+    const int64_t tot = m * K2;
+    auto packer = nsplit == 2 ? k_tc_pack<2> : k_tc_pack<3>;
+    SNN_LAUNCH(packer, unsigned(cdiv(tot, 256)), 256, 0, s)(sa.q.xc, ix->dp, sa.q.hx, sa.q.nrm, Aq,
+                                                            m, d, K2, c, 1, qp[0], qp[1], qp[2]);
+    SNN_LAUNCH_CHECK();
+    return nsplit == 2 ? launch_tc<2>(ix, sa, qp, K2, s) : launch_tc<3>(ix, sa, qp, K2, s);
 }
 
 }  // namespace snn

@@ -10,6 +10,9 @@ namespace snn {
 // Scores every band item of `a` on the tensor cores and appends survivors
 // exactly like the FP32 kernels do.  Builds the index's BF16 copy on first
 // use.  Returns SNN_ENOTSUP where the tensor-core path is not available.
-snn_status tc_score_launch(const snn_index *ix, const ScoreArgs &a, cudaStream_t s);
+// Rx: largest true distance the FP64 test can accept; e_data: bound on the
+// centring error norm of a data row.  Query operands live in `scr`.
+snn_status tc_score_launch(const snn_index *ix, const ScoreArgs &a, cudaStream_t s, double Rx,
+                           double e_data, Scratch &scr);
 
 }  // namespace snn
