@@ -29,18 +29,32 @@ namespace snn {
 namespace {
 
 constexpr int kTM = 128;            // queries per tile (MMA M)
-constexpr int kTN = 128;            // band rows per chunk (MMA N)
-constexpr int kTK = 64;             // columns per k-block (128 B rows, 128B swizzle)
-constexpr int kTileBytes = kTM * kTK * 2;   // 16 KiB per operand part per stage
 constexpr int kTcThreads = 192;
 constexpr int kExtra = 9;           // folded columns
 constexpr long long kTimeoutCycles = 4000000000LL;   // ~2 s
+constexpr int kSmemBudget = 232448 - 1024 - 256;     // dynamic smem minus alignment and barriers
 
-__host__ __device__ constexpr int tc_stages(int nsplit) { return nsplit == 2 ? 3 : 2; }
+// Shape of one kernel instance: NSPLIT BF16 parts, BK columns per k-block
+// (64: 128-byte rows, 128B swizzle; 32: 64-byte rows, 64B swizzle), BN band
+// rows per chunk (MMA N), ARES: the query tile stays in shared memory for a
+// whole work item (only when one k-block holds all columns).
+template <int NSPLIT, int BK, int BN, bool ARES>
+struct TcShape {
+    static constexpr int kTA = kTM * BK * 2;            // bytes of one A part tile
+    static constexpr int kTB = BN * BK * 2;             // bytes of one B part tile
+    static constexpr int kAResBytes = ARES ? NSPLIT * kTA : 0;
+    static constexpr int kStageBytes = ARES ? NSPLIT * kTB : NSPLIT * (kTA + kTB);
+    static constexpr int kStagesRaw = (kSmemBudget - kAResBytes) / kStageBytes;
+    static constexpr int kStages = kStagesRaw > 8 ? 8 : kStagesRaw;
+    static constexpr int kNP = NSPLIT == 2 ? 3 : 6;     // MMAs per k-step
+    static constexpr int kKSteps = BK / 16;             // k-steps per k-block
+    static constexpr int kRowBytes = BK * 2;
+    static constexpr uint32_t kTmemCols = 2 * BN;
+    static constexpr size_t kSmem = size_t(kAResBytes) + size_t(kStages) * kStageBytes + 1024 + 256;
+    static_assert(kStagesRaw >= 2, "shape does not fit shared memory");
+};
+
 __host__ __device__ constexpr int tc_npairs(int nsplit) { return nsplit == 2 ? 3 : 6; }
-__host__ __device__ constexpr size_t tc_smem_bytes(int nsplit) {
-    return size_t(tc_stages(nsplit)) * nsplit * 2 * kTileBytes + 1024 /*align*/ + 256 /*bars*/;
-}
 
 // ------------------------------------------------------- PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -97,29 +111,34 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major tile, 128-byte rows, 128B swizzle,
-// 8-row groups 1024 bytes apart.
+// Shared-memory matrix descriptor of a K-major tile whose rows are ROWB
+// bytes (128: 128B swizzle, 64: 64B swizzle); 8-row groups are 8*ROWB apart.
+template <int ROWB>
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= uint64_t((saddr & 0x3FFFFu) >> 4);
-    d |= uint64_t(1) << 16;                 // leading byte offset (unused here)
-    d |= uint64_t(1024 >> 4) << 32;         // stride byte offset
-    d |= uint64_t(1) << 46;                 // descriptor version
-    d |= uint64_t(2) << 61;                 // 128-byte swizzle
+    d |= uint64_t(1) << 16;                         // leading byte offset (unused)
+    d |= uint64_t((8 * ROWB) >> 4) << 32;           // stride byte offset
+    d |= uint64_t(1) << 46;                         // descriptor version
+    d |= uint64_t(ROWB == 128 ? 2 : 4) << 61;       // 128B or 64B swizzle
     return d;
 }
 
-// Instruction descriptor of kind::f16: BF16 A and B, FP32 D, both K-major.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kTN >> 3) << 17) |
-                            (uint32_t(kTM >> 4) << 24);
+// Instruction descriptor of kind::f16: BF16 A and B, FP32 D, both K-major,
+// M = 128, N = BN.
+template <int BN>
+__host__ __device__ constexpr uint32_t idesc_bf16() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) |
+           (uint32_t(kTM >> 4) << 24);
+}
 
 __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t accumulate) {
+                                         uint32_t idesc, uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
@@ -155,7 +174,7 @@ struct TcArgs {
     int64_t m;
     int64_t n;
     int ksteps;                 // 16-wide k steps that hold data or folded columns
-    int nkb;                    // 64-wide k blocks loaded per chunk
+    int nkb;                    // k blocks loaded per chunk
     const int64_t *tile_lo;
     const int64_t *tile_hi;
     const int64_t *item_off;
@@ -168,7 +187,7 @@ struct TcArgs {
 };
 
 struct ItemInfo {
-    int64_t q0, band_lo, band_hi, c_first, c_end;
+    int64_t q0, band_lo, band_hi, c_first, c_end;   // chunks of kBR rows
 };
 
 __device__ __forceinline__ ItemInfo item_info(const TcArgs &a, int64_t item) {
@@ -182,19 +201,21 @@ __device__ __forceinline__ ItemInfo item_info(const TcArgs &a, int64_t item) {
     f.band_lo = a.tile_lo[lo];
     f.band_hi = a.tile_hi[lo];
     f.c_first = (item - a.item_off[lo]) * kChunksPerItem;
-    f.c_end = min(cdiv(f.band_hi - f.band_lo, kTN), f.c_first + kChunksPerItem);
+    f.c_end = min(cdiv(f.band_hi - f.band_lo, kBR), f.c_first + kChunksPerItem);
     return f;
 }
 
-template <int NSPLIT>
+template <int NSPLIT, int BK, int BN, bool ARES>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUtensorMap qa1,
            const __grid_constant__ CUtensorMap qa2, const __grid_constant__ CUtensorMap xb0,
            const __grid_constant__ CUtensorMap xb1, const __grid_constant__ CUtensorMap xb2,
            TcArgs a) {
-    constexpr int S = tc_stages(NSPLIT);
-    constexpr int NP = tc_npairs(NSPLIT);
-    constexpr uint32_t kStageBytes = uint32_t(NSPLIT) * 2 * kTileBytes;
+    using Sh = TcShape<NSPLIT, BK, BN, ARES>;
+    constexpr int S = Sh::kStages;
+    constexpr int NP = Sh::kNP;
+    constexpr int CSTEP = BN / kBR;              // kBR-row chunks per MMA chunk
+    constexpr uint32_t kIdesc = idesc_bf16<BN>();
     // (A part, B part) products kept by the split: all with pa + pb <= NSPLIT-1
     constexpr int kPa[6] = {0, 0, 1, 0, 1, 2};
     constexpr int kPb[6] = {0, 1, 0, 2, 1, 0};
@@ -203,21 +224,28 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     unsigned char *gbase = smem_raw + (base - raw);
-    // stage s, part p: A at base + (s*NSPLIT*2 + p)*tile, B after the A parts
-    auto a_tile = [&](int s, int p) { return base + uint32_t((s * NSPLIT * 2 + p) * kTileBytes); };
-    auto b_tile = [&](int s, int p) {
-        return base + uint32_t((s * NSPLIT * 2 + NSPLIT + p) * kTileBytes);
+    // resident A parts first (ARES), then the stages
+    const uint32_t stage0 = base + uint32_t(Sh::kAResBytes);
+    auto a_tile = [&](int s, int p) -> uint32_t {
+        if (ARES) return base + uint32_t(p * Sh::kTA);
+        return stage0 + uint32_t(s * Sh::kStageBytes + p * Sh::kTA);
     };
-    const uint32_t bar0 = base + uint32_t(S * kStageBytes);
+    auto b_tile = [&](int s, int p) -> uint32_t {
+        return stage0 + uint32_t(s * Sh::kStageBytes + (ARES ? 0 : NSPLIT * Sh::kTA) + p * Sh::kTB);
+    };
+    const uint32_t bar0 = stage0 + uint32_t(S * Sh::kStageBytes);
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
     auto empty_bar = [&](int s) { return bar0 + 8u * (S + s); };
     auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * S + b); };
     auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * S + 2 + b); };
     const uint32_t done_bar = bar0 + 8u * (2 * S + 4);
-    unsigned char *gmisc = gbase + S * kStageBytes + 8 * (2 * S + 5);
+    const uint32_t afull_bar = bar0 + 8u * (2 * S + 5);
+    const uint32_t aempty_bar = bar0 + 8u * (2 * S + 6);
+    unsigned char *gmisc = gbase + (bar0 - base) + 8 * (2 * S + 7);
     volatile uint32_t *s_tmem = reinterpret_cast<volatile uint32_t *>(gmisc);
     volatile int *s_abort = reinterpret_cast<volatile int *>(gmisc + 4);
     volatile int *s_consumed = reinterpret_cast<volatile int *>(gmisc + 8);
+    volatile int *s_aconsumed = reinterpret_cast<volatile int *>(gmisc + 12);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const CUtensorMap *qa[3] = {&qa0, &qa1, &qa2};
@@ -233,15 +261,19 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
             mbar_init(tempty_bar(b), 128);
         }
         mbar_init(done_bar, 1);
+        mbar_init(afull_bar, 1);
+        mbar_init(aempty_bar, 1);
         *s_abort = 0;
         *s_consumed = 0;
+        *s_aconsumed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) {
-        // 2 accumulators x 128 FP32 columns
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
-                         smem_u32((const void *)s_tmem))
+        // two accumulators of BN FP32 columns
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32((const void *)s_tmem)),
+                     "n"(Sh::kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -251,23 +283,31 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
     const uint32_t tmem = *s_tmem;
     const int64_t total = a.item_off[a.ntiles];
 
-    int issued = 0;
+    int issued = 0, a_issued = 0;
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
-            int it = 0;
-            for (int64_t item = blockIdx.x; item < total && !*s_abort; item += gridDim.x) {
+            int it = 0, itm = 0;
+            for (int64_t item = blockIdx.x; item < total && !*s_abort; item += gridDim.x, ++itm) {
                 const ItemInfo f = item_info(a, item);
-                for (int64_t c = f.c_first; c < f.c_end && !*s_abort; ++c) {
-                    const int64_t j0 = f.band_lo + c * kTN;
+                if (ARES) {
+                    // the query tile of this item, once
+                    if (!mbar_wait(aempty_bar, (uint32_t(itm) & 1u) ^ 1u, s_abort, a.err)) break;
+                    mbar_expect_tx(afull_bar, uint32_t(NSPLIT * Sh::kTA));
+                    for (int p = 0; p < NSPLIT; ++p)
+                        tma_load_2d(a_tile(0, p), qa[p], 0, int(f.q0), afull_bar);
+                    a_issued = itm + 1;
+                }
+                for (int64_t c = f.c_first; c < f.c_end && !*s_abort; c += CSTEP) {
+                    const int64_t j0 = f.band_lo + c * kBR;
                     for (int kb = 0; kb < a.nkb; ++kb, ++it) {
                         const int s = it % S;
                         const uint32_t round = uint32_t(it / S);
                         if (!mbar_wait(empty_bar(s), (round & 1u) ^ 1u, s_abort, a.err)) break;
-                        mbar_expect_tx(full_bar(s), kStageBytes);
+                        mbar_expect_tx(full_bar(s), uint32_t(Sh::kStageBytes));
                         for (int p = 0; p < NSPLIT; ++p) {
-                            tma_load_2d(a_tile(s, p), qa[p], kb * kTK, int(f.q0), full_bar(s));
-                            tma_load_2d(b_tile(s, p), xb[p], kb * kTK, int(j0), full_bar(s));
+                            if (!ARES) tma_load_2d(a_tile(s, p), qa[p], kb * BK, int(f.q0), full_bar(s));
+                            tma_load_2d(b_tile(s, p), xb[p], kb * BK, int(j0), full_bar(s));
                         }
                         issued = it + 1;
                     }
@@ -277,28 +317,36 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
     } else if (warp == 1) {
         // ------------------------------------------------- MMA issuer
         if (lane == 0) {
-            int it = 0, chunk = 0;
+            int it = 0, chunk = 0, itm = 0;
             bool ok = true;
-            for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
+            for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x, ++itm) {
                 const ItemInfo f = item_info(a, item);
-                for (int64_t c = f.c_first; c < f.c_end && ok; ++c, ++chunk) {
+                if (ARES) {
+                    if (!(ok = mbar_wait(afull_bar, uint32_t(itm) & 1u, s_abort, a.err))) break;
+                    *s_aconsumed = itm + 1;
+                    tmem_fence_after();
+                }
+                for (int64_t c = f.c_first; c < f.c_end && ok; c += CSTEP, ++chunk) {
                     const int b = chunk & 1;
                     const uint32_t use = uint32_t(chunk >> 1);
                     if (!(ok = mbar_wait(tempty_bar(b), (use & 1u) ^ 1u, s_abort, a.err))) break;
                     tmem_fence_after();
-                    const uint32_t dt = tmem + uint32_t(b * kTN);
+                    const uint32_t dt = tmem + uint32_t(b * BN);
                     for (int kb = 0; kb < a.nkb; ++kb, ++it) {
                         const int s = it % S;
                         const uint32_t round = uint32_t(it / S);
                         if (!(ok = mbar_wait(full_bar(s), round & 1u, s_abort, a.err))) break;
                         tmem_fence_after();
-                        for (int ks = 0; ks < 4; ++ks) {
-                            if (kb * 4 + ks >= a.ksteps) break;
+#pragma unroll
+                        for (int ks = 0; ks < Sh::kKSteps; ++ks) {
+                            if (kb * Sh::kKSteps + ks >= a.ksteps) break;
 #pragma unroll
                             for (int pr = 0; pr < NP; ++pr) {
-                                const uint64_t ad = smem_desc(a_tile(s, kPa[pr]) + 32u * ks);
-                                const uint64_t bd = smem_desc(b_tile(s, kPb[pr]) + 32u * ks);
-                                mma_bf16(dt, ad, bd, (kb | ks | pr) != 0 ? 1u : 0u);
+                                const uint64_t ad =
+                                    smem_desc<Sh::kRowBytes>(a_tile(s, kPa[pr]) + 32u * ks);
+                                const uint64_t bd =
+                                    smem_desc<Sh::kRowBytes>(b_tile(s, kPb[pr]) + 32u * ks);
+                                mma_bf16(dt, ad, bd, kIdesc, (kb | ks | pr) != 0 ? 1u : 0u);
                             }
                         }
                         mma_commit(empty_bar(s));
@@ -306,6 +354,7 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                     }
                     if (ok) mma_commit(tfull_bar(b));
                 }
+                if (ARES && ok) mma_commit(aempty_bar);   // the query tile may be replaced
             }
             // every MMA issued by this thread has completed before TMEM is freed
             mma_commit(done_bar);
@@ -320,21 +369,20 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
         for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
             const ItemInfo f = item_info(a, item);
             const int64_t q = f.q0 + qi;
-            for (int64_t c = f.c_first; c < f.c_end && ok; ++c, ++chunk) {
-                const int64_t j0 = f.band_lo + c * kTN;
+            for (int64_t c = f.c_first; c < f.c_end && ok; c += CSTEP, ++chunk) {
+                const int64_t j0 = f.band_lo + c * kBR;
                 const int b = chunk & 1;
                 const uint32_t use = uint32_t(chunk >> 1);
                 ok = mbar_wait(tfull_bar(b), use & 1u, s_abort, a.err);
                 if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
                 tmem_fence_after();
 #pragma unroll 1
-                for (int cb = 0; cb < kTN / 32; ++cb) {
+                for (int cb = 0; cb < BN / 32; ++cb) {
                     uint32_t r[32];
-                    tmem_ld32(tmem + (uint32_t(quad * 32) << 16) + uint32_t(b * kTN + cb * 32), r);
+                    tmem_ld32(tmem + (uint32_t(quad * 32) << 16) + uint32_t(b * BN + cb * 32), r);
                     uint32_t all = 0xffffffffu;
 #pragma unroll
                     for (int i = 0; i < 32; ++i) all &= r[i];
-                    // sign bit clear somewhere: a possible neighbour in this group
                     // a clear sign bit somewhere: a possible neighbour in this group
                     uint32_t mask = 0;
                     if (!(all >> 31)) {
@@ -382,12 +430,16 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
     if (warp == 0 && lane == 0) {
         for (int it = *s_consumed; it < issued; ++it)
             mbar_wait(full_bar(it % S), uint32_t(it / S) & 1u, s_abort, a.err);
+        for (int itm = *s_aconsumed; itm < a_issued; ++itm)
+            mbar_wait(afull_bar, uint32_t(itm) & 1u, s_abort, a.err);
     }
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();
     if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "n"(Sh::kTmemCols)
+                     : "memory");
 }
 
 // ------------------------------------------------ operand packing
@@ -495,7 +547,8 @@ EncodeTiledFn get_encode() {
     return fn;
 }
 
-snn_status make_map(CUtensorMap *map, const uint16_t *ptr, int64_t rows, int K2) {
+snn_status make_map(CUtensorMap *map, const uint16_t *ptr, int64_t rows, int K2, int bk,
+                    int box_rows) {
     EncodeTiledFn enc = get_encode();
     if (!enc) {
         set_error("cuTensorMapEncodeTiled is unavailable");
@@ -503,10 +556,11 @@ snn_status make_map(CUtensorMap *map, const uint16_t *ptr, int64_t rows, int K2)
     }
     cuuint64_t dims[2] = {cuuint64_t(K2), cuuint64_t(rows)};
     cuuint64_t strides[1] = {cuuint64_t(K2) * 2};
-    cuuint32_t box[2] = {cuuint32_t(kTK), cuuint32_t(kTM)};
+    cuuint32_t box[2] = {cuuint32_t(bk), cuuint32_t(box_rows)};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(ptr), dims,
-                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed (%d)", int(r));
@@ -529,23 +583,23 @@ double tc_constant(int nsplit, int d, double *u_k_out) {
     return 1.02 * (c_mn > c_hx ? c_mn : c_hx);
 }
 
-template <int NSPLIT>
+template <int NSPLIT, int BK, int BN, bool ARES>
 snn_status launch_tc(const snn_index *ix, const ScoreArgs &sa, const uint16_t *const *qp,
                      int K2, cudaStream_t s) {
+    using Sh = TcShape<NSPLIT, BK, BN, ARES>;
     CUtensorMap maps[6];
     for (int p = 0; p < 3; ++p) {
         const int pp = p < NSPLIT ? p : 0;
-        SNN_TRY(make_map(&maps[p], qp[pp], sa.q.m, K2));
-        SNN_TRY(make_map(&maps[3 + p], ix->tc_part[pp], ix->n, K2));
+        SNN_TRY(make_map(&maps[p], qp[pp], sa.q.m, K2, BK, kTM));
+        SNN_TRY(make_map(&maps[3 + p], ix->tc_part[pp], ix->n, K2, BK, BN));
     }
-    const size_t smem = tc_smem_bytes(NSPLIT);
-    SNN_CUDA(cudaFuncSetAttribute(k_score_tc<NSPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  int(smem)));
+    auto kern = k_score_tc<NSPLIT, BK, BN, ARES>;
+    SNN_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::kSmem)));
     TcArgs a;
     a.m = sa.q.m;
     a.n = ix->n;
     a.ksteps = int(cdiv(ix->d + kExtra, 16));
-    a.nkb = K2 / kTK;
+    a.nkb = K2 / BK;
     a.tile_lo = sa.tile_lo;
     a.tile_hi = sa.tile_hi;
     a.item_off = sa.item_off;
@@ -555,8 +609,8 @@ snn_status launch_tc(const snn_index *ix, const ScoreArgs &sa, const uint16_t *c
     a.cap = sa.cap;
     a.count = sa.count;
     a.err = sa.err;
-    SNN_LAUNCH(k_score_tc<NSPLIT>, device_sm_count(), kTcThreads, smem, s)(
-        maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], a);
+    SNN_LAUNCH(kern, device_sm_count(), kTcThreads, Sh::kSmem, s)(maps[0], maps[1], maps[2],
+                                                                 maps[3], maps[4], maps[5], a);
     SNN_LAUNCH_CHECK();
     return SNN_OK;
 }
@@ -575,10 +629,14 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
     const int nsplit = (c2 * 1.5 * N * N <= 0.02 * R2h) ? 2 : 3;
     double u_k = 0.0;
     const double c = tc_constant(nsplit, d, &u_k);
-    const int K2 = int(cdiv(d + kExtra, kTK) * kTK);
+    // shape: one 32- or 64-column k-block holds everything for low d (query
+    // tile resident for a whole item); 64-column k-blocks streamed otherwise
+    const int kp = d + kExtra;
+    const int bk = kp <= 32 ? 32 : 64;
+    const int K2 = int(cdiv(kp, bk) * bk);
     {
         std::lock_guard<std::mutex> lk(ix->mu);
-        if (ix->tc_nsplit != nsplit) {
+        if (ix->tc_nsplit != nsplit || ix->tc_k2 != K2) {
             for (int p = 0; p < 3; ++p) {
                 if (ix->tc_part[p]) cudaFree(ix->tc_part[p]);
                 ix->tc_part[p] = nullptr;
@@ -615,7 +673,14 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
     SNN_LAUNCH(packer, unsigned(cdiv(tot, 256)), 256, 0, s)(sa.q.xc, ix->dp, sa.q.hx, sa.q.nrm, Aq,
                                                             m, d, K2, c, 1, qp[0], qp[1], qp[2]);
     SNN_LAUNCH_CHECK();
-    return nsplit == 2 ? launch_tc<2>(ix, sa, qp, K2, s) : launch_tc<3>(ix, sa, qp, K2, s);
+    if (kp <= 32)
+        return nsplit == 2 ? launch_tc<2, 32, 256, true>(ix, sa, qp, K2, s)
+                           : launch_tc<3, 32, 256, true>(ix, sa, qp, K2, s);
+    if (kp <= 64)
+        return nsplit == 2 ? launch_tc<2, 64, 128, true>(ix, sa, qp, K2, s)
+                           : launch_tc<3, 64, 128, true>(ix, sa, qp, K2, s);
+    return nsplit == 2 ? launch_tc<2, 64, 128, false>(ix, sa, qp, K2, s)
+                       : launch_tc<3, 64, 128, false>(ix, sa, qp, K2, s);
 }
 
 }  // namespace snn

@@ -243,3 +243,21 @@ def test_launch_counter_moves(snn):
     before = snn.launch_count()
     _run(snn, np.random.default_rng(1).standard_normal((500, 3)).astype(np.float32), None, 0.5, "fp32")
     assert snn.launch_count() > before
+
+
+@pytest.mark.parametrize("d", [5, 23, 40, 55, 100, 300])
+@pytest.mark.parametrize("spread", [1.0, 30.0])
+def test_tensor_core_shapes(snn, d, spread):
+    # covers every tensor-core kernel shape: one 32- or 64-column k-block with
+    # the query tile resident (d + 9 <= 64) or streamed 64-column k-blocks,
+    # and both the two- and three-part BF16 splits (cluster spread relative to
+    # R decides the split)
+    rng = np.random.default_rng(100 + d)
+    centres = rng.uniform(-spread, spread, size=(6, d))
+    lab = rng.integers(0, 6, size=5000)
+    P = (centres[lab] + rng.standard_normal((5000, d))).astype(np.float32)
+    Q = (centres[rng.integers(0, 6, size=700)] + rng.standard_normal((700, d))).astype(np.float32)
+    R = float(np.sqrt(2.0 * d) * 0.8)
+    for q in (None, Q):
+        got = _run(snn, P, q, R, "bf16")
+        assert_csr_equal(got, oracle.brute_radius(P, q, R), f"d={d} spread={spread}")
