@@ -189,6 +189,35 @@ const char *snn_last_error(void);
 /* Library version string. */
 const char *snn_version(void);
 
+/* Largest n accepted by snn_sort_scores_noalloc. */
+#define SNN_NOALLOC_SORT_MAX_N (1 << 20)
+
+/* Allocation-free sort of scores (the paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory).  Some
+ * callers cannot call cudaMalloc or use a memory pool: code that runs while a
+ * stream is being captured into a CUDA graph under an allocation ban, a
+ * process whose device memory budget is fixed by someone else, or a latency-
+ * critical loop that must never enter the allocator.  This call sorts n FP32
+ * values ascending with a stable LSD radix sort -- the same sort and the same
+ * result as the index build's sort of alpha (Algorithm 1, step 6) -- using
+ * only a static device array compiled into the library (about 9 MB, held by
+ * every GPU that loads the library until the process exits).
+ *  alpha         device, n FP32 values (NaN/Inf rejected); may equal
+ *                alpha_sorted (in place).
+ *  n             0 <= n <= SNN_NOALLOC_SORT_MAX_N; larger n returns
+ *                SNN_EINVAL with a message naming the limit.
+ *  alpha_sorted  device, n FP32 outputs, ascending (caller-allocated).
+ *  order         device, n int32 outputs: order[r] is the input position of
+ *                alpha_sorted[r]; equal values keep their input order.
+ * The call allocates nothing and synchronises `stream` once (to check the
+ * input for NaN/Inf).  The first call on a device looks up the device address
+ * of the static array (make that first call before any stream capture).  All
+ * calls share the one array and it keeps the last call's contents, so calls
+ * whose device work overlaps (different streams, or different host threads on
+ * one device) race: serialise them. */
+snn_status snn_sort_scores_noalloc(const float *alpha, int64_t n, float *alpha_sorted,
+                                   int32_t *order, void *stream);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (diagnostics: the difference around a call is that call's launch count). */
 uint64_t snn_launch_count(void);

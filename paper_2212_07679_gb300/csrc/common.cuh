@@ -128,6 +128,10 @@ snn_status radix_sort_pairs(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals
 
 int device_sm_count();
 
+// Allocation-free stable sort of FP32 scores (noalloc_sort.cu).
+snn_status sort_scores_noalloc(const float *alpha, int64_t n, float *alpha_sorted, int32_t *order,
+                               cudaStream_t s);
+
 // Every kernel launch of the library goes through SNN_LAUNCH, which counts
 // it (snn_launch_count() reports the total).
 void note_launch();

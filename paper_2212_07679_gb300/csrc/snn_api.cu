@@ -734,4 +734,10 @@ const char *snn_version(void) { return "snn-gb300 0.1 (sm_103a)"; }
 
 uint64_t snn_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
+snn_status snn_sort_scores_noalloc(const float *alpha, int64_t n, float *alpha_sorted,
+                                   int32_t *order, void *stream) {
+    clear_error();
+    return sort_scores_noalloc(alpha, n, alpha_sorted, order, static_cast<cudaStream_t>(stream));
+}
+
 }  // extern "C"
