@@ -90,6 +90,8 @@ typedef struct {
  *  nnz         neighbour pairs returned;
  *  exact_fp64  survivors whose decision or distance needed the FP64 loop
  *              itself (the compensated FP32 evaluation settles the rest);
+ *  mma_flops_per_pair  tensor-core flops executed per scored pair (BF16
+ *              split products and folded threshold columns; 0 for FP32);
  *  ms_*        device time of the phases (CUDA events on `stream`). */
 typedef struct {
     int64_t candidates;
@@ -97,6 +99,7 @@ typedef struct {
     int64_t survivors;
     int64_t nnz;
     int64_t exact_fp64;
+    int64_t mma_flops_per_pair;
     float ms_prep;
     float ms_score;
     float ms_recheck;

@@ -77,6 +77,14 @@ __global__ void k_tile_band(const float *__restrict__ qalpha, int64_t m,
     if (band_pairs) atomicAdd(band_pairs, (unsigned long long)((hi - lo) * (q1 - q0 + 1)));
 }
 
+// item_tile[i] = the tile whose band chunk group i is (one thread per tile).
+__global__ void k_item_tiles(const int64_t *__restrict__ item_off, int ntiles,
+                             int32_t *__restrict__ item_tile) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    for (int64_t i = item_off[t]; i < item_off[t + 1]; ++i) item_tile[i] = t;
+}
+
 // Per-query candidate range sizes |J_q| (statistics only).
 __global__ void k_query_windows(const float *__restrict__ qalpha, int64_t m,
                                 const float *__restrict__ alpha, int64_t n, double Wbase,
@@ -127,13 +135,7 @@ __device__ __forceinline__ void score_body(const ScoreArgs &a) {
         __syncthreads();
         const int64_t item = s_item;
         if (item >= total_items) break;
-        // tile of this item: last t with item_off[t] <= item
-        int lo_t = 0, hi_t = a.ntiles;
-        while (hi_t - lo_t > 1) {
-            const int mid = (lo_t + hi_t) >> 1;
-            if (a.item_off[mid] <= item) lo_t = mid; else hi_t = mid;
-        }
-        const int tile = lo_t;
+        const int tile = a.item_tile[item];
         const int64_t q0 = int64_t(tile) * kBQ;
         const int64_t band_lo = a.tile_lo[tile], band_hi = a.tile_hi[tile];
         const int64_t c_first = (item - a.item_off[tile]) * kChunksPerItem;

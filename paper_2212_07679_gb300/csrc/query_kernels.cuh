@@ -7,7 +7,7 @@ namespace snn {
 // Query tile (queries sorted by score) and band chunk (sorted data rows).
 constexpr int kBQ = 128;
 constexpr int kBR = 128;
-constexpr int kChunksPerItem = 8;   // band chunks scored by one work item
+constexpr int kChunksPerItem = 16;  // band chunks scored by one work item
 
 // Sorted query set: either the index's own points (self-join) or
 // out-of-sample queries projected, sorted and gathered like the data.
@@ -39,6 +39,7 @@ struct ScoreArgs {
     const int64_t *tile_lo;     // ntiles
     const int64_t *tile_hi;
     const int64_t *item_off;    // ntiles + 1, exclusive scan of items per tile
+    const int32_t *item_tile;   // tile of each work item
     int ntiles;
     int sym;                    // symmetric self-join: only pairs with row >= query
     float c1;                   // rounding constant of the FP32 score
@@ -49,6 +50,7 @@ struct ScoreArgs {
     int *err;                   // device error flag (bounded waits that gave up)
 };
 
+__global__ void k_item_tiles(const int64_t *item_off, int ntiles, int32_t *item_tile);
 __global__ void k_query_consts(const float *hy, const float *qn, int64_t m, int d, double Rx,
                                double e_data, float *thrA);
 __global__ void k_tile_band(const float *qalpha, int64_t m, const float *alpha, int64_t n,

@@ -376,6 +376,13 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         CUDA_Q(cudaGetLastError());
     }
     TRY_Q(scan_exclusive<int64_t>(items, item_off, ntiles, s));
+    // work item -> tile (upper bound on the item count: every tile's band is
+    // at most the whole data set)
+    const int64_t max_items = int64_t(ntiles) * (cdiv(ix->n, int64_t(kBR) * kChunksPerItem) + 1);
+    int32_t *item_tile;
+    TRY_Q(scr.alloc(&item_tile, max_items));
+    SNN_LAUNCH(k_item_tiles, grid_for(ntiles, 128), 128, 0, s)(item_off, ntiles, item_tile);
+    CUDA_Q(cudaGetLastError());
 
     // scoring with an adaptive survivor buffer
     double hint;
@@ -396,6 +403,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     sa.tile_lo = tile_lo;
     sa.tile_hi = tile_hi;
     sa.item_off = item_off;
+    sa.item_tile = item_tile;
     sa.ntiles = ntiles;
     sa.sym = sym;
     sa.c1 = (float)((2.0 * d + 4.0) * (double)kU32 * 1.05);
@@ -407,6 +415,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     sa.err = dev_err;
     int herr = 0;
     unsigned long long hctr[4] = {0, 0, 0, 0};
+    int64_t mma_fpp = 0;
     int hbad = 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
         sa.surv = surv;
@@ -414,7 +423,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         if (stats) cudaEventRecord(ev[1], s);
         snn_status st = SNN_OK;
         if (prec == SNN_PREC_BF16) {
-            st = tc_score_launch(ix, sa, s, Rx, e_data, scr);
+            st = tc_score_launch(ix, sa, s, Rx, e_data, scr, &mma_fpp);
         } else {
             const int grid = device_sm_count() * 2;
             if (dp <= 16)
@@ -570,6 +579,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         CUDA_Q(cudaMemcpyAsync(&nf, ctr + 4, sizeof(nf), cudaMemcpyDeviceToHost, s));
         CUDA_Q(cudaStreamSynchronize(s));
         stats->exact_fp64 = (int64_t)nf;
+        stats->mma_flops_per_pair = mma_fpp;
         stats->candidates = (int64_t)hctr[3];
         stats->band_pairs = (int64_t)hctr[2];
         stats->survivors = nsurv;

@@ -29,7 +29,8 @@ namespace snn {
 namespace {
 
 constexpr int kTM = 128;            // queries per tile (MMA M)
-constexpr int kTcThreads = 192;
+constexpr int kEpiWarps = 8;        // two warps per TMEM lane quadrant, half the columns each
+constexpr int kTcThreads = 64 + 32 * kEpiWarps;
 constexpr int kExtra = 9;           // folded columns
 constexpr long long kTimeoutCycles = 4000000000LL;   // ~2 s
 constexpr int kSmemBudget = 232448 - 1024 - 256;     // dynamic smem minus alignment and barriers
@@ -37,12 +38,13 @@ constexpr int kSmemBudget = 232448 - 1024 - 256;     // dynamic smem minus align
 // Shape of one kernel instance: NSPLIT BF16 parts, BK columns per k-block
 // (64: 128-byte rows, 128B swizzle; 32: 64-byte rows, 64B swizzle), BN band
 // rows per chunk (MMA N), ARES: the query tile stays in shared memory for a
-// whole work item (only when one k-block holds all columns).
+// whole work item (only when one k-block holds all columns), in two slots so
+// that the next item's tile loads while the current one is in use.
 template <int NSPLIT, int BK, int BN, bool ARES>
 struct TcShape {
     static constexpr int kTA = kTM * BK * 2;            // bytes of one A part tile
     static constexpr int kTB = BN * BK * 2;             // bytes of one B part tile
-    static constexpr int kAResBytes = ARES ? NSPLIT * kTA : 0;
+    static constexpr int kAResBytes = ARES ? 2 * NSPLIT * kTA : 0;
     static constexpr int kStageBytes = ARES ? NSPLIT * kTB : NSPLIT * (kTA + kTB);
     static constexpr int kStagesRaw = (kSmemBudget - kAResBytes) / kStageBytes;
     static constexpr int kStages = kStagesRaw > 8 ? 8 : kStagesRaw;
@@ -155,20 +157,26 @@ __device__ __forceinline__ void tmem_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+// Loads 64 consecutive FP32 accumulator columns of this warp's 32 TMEM lanes
+// (32x32b shape, 64 repetitions) and waits for them in the same statement,
+// so no use of the registers can be scheduled before the wait.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[64]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-          "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+          "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+          "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+          "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+          "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(taddr)
+        : "memory");
 }
+
 
 struct TcArgs {
     int64_t m;
@@ -178,6 +186,7 @@ struct TcArgs {
     const int64_t *tile_lo;
     const int64_t *tile_hi;
     const int64_t *item_off;
+    const int32_t *item_tile;
     int ntiles;
     int sym;
     uint2 *surv;
@@ -191,11 +200,7 @@ struct ItemInfo {
 };
 
 __device__ __forceinline__ ItemInfo item_info(const TcArgs &a, int64_t item) {
-    int lo = 0, hi = a.ntiles;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (a.item_off[mid] <= item) lo = mid; else hi = mid;
-    }
+    const int lo = a.item_tile[item];
     ItemInfo f;
     f.q0 = int64_t(lo) * kTM;
     f.band_lo = a.tile_lo[lo];
@@ -226,8 +231,9 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
     unsigned char *gbase = smem_raw + (base - raw);
     // resident A parts first (ARES), then the stages
     const uint32_t stage0 = base + uint32_t(Sh::kAResBytes);
+    // ARES: s is the A slot (item parity); otherwise the stage
     auto a_tile = [&](int s, int p) -> uint32_t {
-        if (ARES) return base + uint32_t(p * Sh::kTA);
+        if (ARES) return base + uint32_t((s * NSPLIT + p) * Sh::kTA);
         return stage0 + uint32_t(s * Sh::kStageBytes + p * Sh::kTA);
     };
     auto b_tile = [&](int s, int p) -> uint32_t {
@@ -239,9 +245,9 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
     auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * S + b); };
     auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * S + 2 + b); };
     const uint32_t done_bar = bar0 + 8u * (2 * S + 4);
-    const uint32_t afull_bar = bar0 + 8u * (2 * S + 5);
-    const uint32_t aempty_bar = bar0 + 8u * (2 * S + 6);
-    unsigned char *gmisc = gbase + (bar0 - base) + 8 * (2 * S + 7);
+    auto afull_bar = [&](int k) { return bar0 + 8u * (2 * S + 5 + k); };
+    auto aempty_bar = [&](int k) { return bar0 + 8u * (2 * S + 7 + k); };
+    unsigned char *gmisc = gbase + (bar0 - base) + 8 * (2 * S + 9);
     volatile uint32_t *s_tmem = reinterpret_cast<volatile uint32_t *>(gmisc);
     volatile int *s_abort = reinterpret_cast<volatile int *>(gmisc + 4);
     volatile int *s_consumed = reinterpret_cast<volatile int *>(gmisc + 8);
@@ -258,11 +264,11 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(tfull_bar(b), 1);
-            mbar_init(tempty_bar(b), 128);
+            mbar_init(tempty_bar(b), 32 * kEpiWarps);
+            mbar_init(afull_bar(b), 1);
+            mbar_init(aempty_bar(b), 1);
         }
         mbar_init(done_bar, 1);
-        mbar_init(afull_bar, 1);
-        mbar_init(aempty_bar, 1);
         *s_abort = 0;
         *s_consumed = 0;
         *s_aconsumed = 0;
@@ -291,11 +297,13 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
             for (int64_t item = blockIdx.x; item < total && !*s_abort; item += gridDim.x, ++itm) {
                 const ItemInfo f = item_info(a, item);
                 if (ARES) {
-                    // the query tile of this item, once
-                    if (!mbar_wait(aempty_bar, (uint32_t(itm) & 1u) ^ 1u, s_abort, a.err)) break;
-                    mbar_expect_tx(afull_bar, uint32_t(NSPLIT * Sh::kTA));
+                    // the query tile of this item, once, into slot itm & 1
+                    const int k = itm & 1;
+                    const uint32_t use = uint32_t(itm >> 1);
+                    if (!mbar_wait(aempty_bar(k), (use & 1u) ^ 1u, s_abort, a.err)) break;
+                    mbar_expect_tx(afull_bar(k), uint32_t(NSPLIT * Sh::kTA));
                     for (int p = 0; p < NSPLIT; ++p)
-                        tma_load_2d(a_tile(0, p), qa[p], 0, int(f.q0), afull_bar);
+                        tma_load_2d(a_tile(k, p), qa[p], 0, int(f.q0), afull_bar(k));
                     a_issued = itm + 1;
                 }
                 for (int64_t c = f.c_first; c < f.c_end && !*s_abort; c += CSTEP) {
@@ -321,8 +329,10 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
             bool ok = true;
             for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x, ++itm) {
                 const ItemInfo f = item_info(a, item);
+                const int aslot = itm & 1;
                 if (ARES) {
-                    if (!(ok = mbar_wait(afull_bar, uint32_t(itm) & 1u, s_abort, a.err))) break;
+                    if (!(ok = mbar_wait(afull_bar(aslot), uint32_t(itm >> 1) & 1u, s_abort, a.err)))
+                        break;
                     *s_aconsumed = itm + 1;
                     tmem_fence_after();
                 }
@@ -342,8 +352,8 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                             if (kb * Sh::kKSteps + ks >= a.ksteps) break;
 #pragma unroll
                             for (int pr = 0; pr < NP; ++pr) {
-                                const uint64_t ad =
-                                    smem_desc<Sh::kRowBytes>(a_tile(s, kPa[pr]) + 32u * ks);
+                                const uint64_t ad = smem_desc<Sh::kRowBytes>(
+                                    a_tile(ARES ? aslot : s, kPa[pr]) + 32u * ks);
                                 const uint64_t bd =
                                     smem_desc<Sh::kRowBytes>(b_tile(s, kPb[pr]) + 32u * ks);
                                 mma_bf16(dt, ad, bd, kIdesc, (kb | ks | pr) != 0 ? 1u : 0u);
@@ -354,7 +364,7 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                     }
                     if (ok) mma_commit(tfull_bar(b));
                 }
-                if (ARES && ok) mma_commit(aempty_bar);   // the query tile may be replaced
+                if (ARES && ok) mma_commit(aempty_bar(aslot));   // this slot may be refilled
             }
             // every MMA issued by this thread has completed before TMEM is freed
             mma_commit(done_bar);
@@ -362,8 +372,11 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
         }
     } else {
         // ---------------------------------------------------- epilogue
+        const int ew = warp - 2;                   // 0 .. kEpiWarps-1
         const int quad = warp & 3;                 // TMEM lanes 32*quad .. +31
+        const int half = ew >> 2;                  // which half of the columns
         const int qi = quad * 32 + lane;           // query row within the tile
+        constexpr int kGroups = BN / 32 / 2;       // 32-column groups per warp
         int chunk = 0;
         bool ok = true;
         for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
@@ -376,47 +389,54 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                 ok = mbar_wait(tfull_bar(b), use & 1u, s_abort, a.err);
                 if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
                 tmem_fence_after();
+                const uint32_t tbase = tmem + (uint32_t(quad * 32) << 16) + uint32_t(b * BN);
 #pragma unroll 1
-                for (int cb = 0; cb < BN / 32; ++cb) {
-                    uint32_t r[32];
-                    tmem_ld32(tmem + (uint32_t(quad * 32) << 16) + uint32_t(b * BN + cb * 32), r);
-                    uint32_t all = 0xffffffffu;
+                for (int g2 = 0; g2 < kGroups; g2 += 2) {
+                    uint32_t rr[64];
+                    const int cb0 = half * kGroups + g2;
+                    tmem_ld64(tbase + uint32_t(cb0 * 32), rr);
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) all &= r[i];
-                    // a clear sign bit somewhere: a possible neighbour in this group
-                    uint32_t mask = 0;
-                    if (!(all >> 31)) {
+                    for (int h = 0; h < 2; ++h) {
+                        const int cb = cb0 + h;
+                        const uint32_t *rh = rr + 32 * h;
+                        uint32_t all = 0xffffffffu;
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) mask |= ((r[i] >> 31) ^ 1u) << i;
-                        // validity: query inside the set, row inside the band,
-                        // symmetric self-join keeps rows at or after the query
-                        const int64_t jb = j0 + cb * 32;
-                        const int64_t lim = f.band_hi - jb;
-                        if (q >= a.m || lim <= 0) mask = 0;
-                        else if (lim < 32) mask &= (1u << lim) - 1u;
-                        if (a.sym) {
-                            const int64_t first = q - jb;
-                            if (first >= 32) mask = 0;
-                            else if (first > 0) mask &= ~((1u << first) - 1u);
+                        for (int i = 0; i < 32; ++i) all &= rh[i];
+                        // a clear sign bit somewhere: a possible neighbour
+                        uint32_t mask = 0;
+                        if (!(all >> 31)) {
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) mask |= ((rh[i] >> 31) ^ 1u) << i;
+                            // validity: query inside the set, row inside the
+                            // band, symmetric self-join keeps rows >= query
+                            const int64_t jb = j0 + cb * 32;
+                            const int64_t lim = f.band_hi - jb;
+                            if (q >= a.m || lim <= 0) mask = 0;
+                            else if (lim < 32) mask &= (1u << lim) - 1u;
+                            if (a.sym) {
+                                const int64_t first = q - jb;
+                                if (first >= 32) mask = 0;
+                                else if (first > 0) mask &= ~((1u << first) - 1u);
+                            }
                         }
-                    }
-                    const int cnt = __popc(mask);
-                    if (__any_sync(0xffffffffu, cnt != 0)) {
-                        int incl = cnt;
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                            if (lane >= o) incl += y;
-                        }
-                        const int wtot = __shfl_sync(0xffffffffu, incl, 31);
-                        unsigned long long pos = 0;
-                        if (lane == 31) pos = atomicAdd(a.count, (unsigned long long)wtot);
-                        pos = __shfl_sync(0xffffffffu, pos, 31) + (unsigned long long)(incl - cnt);
-                        while (mask) {
-                            const int i = __ffs(mask) - 1;
-                            mask &= mask - 1;
-                            if (pos < (unsigned long long)a.cap)
-                                a.surv[pos] = make_uint2(unsigned(q), unsigned(j0 + cb * 32 + i));
-                            ++pos;
+                        const int cnt = __popc(mask);
+                        if (__any_sync(0xffffffffu, cnt != 0)) {
+                            int incl = cnt;
+                            for (int o = 1; o < 32; o <<= 1) {
+                                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                                if (lane >= o) incl += y;
+                            }
+                            const int wtot = __shfl_sync(0xffffffffu, incl, 31);
+                            unsigned long long pos = 0;
+                            if (lane == 31) pos = atomicAdd(a.count, (unsigned long long)wtot);
+                            pos = __shfl_sync(0xffffffffu, pos, 31) + (unsigned long long)(incl - cnt);
+                            while (mask) {
+                                const int i = __ffs(mask) - 1;
+                                mask &= mask - 1;
+                                if (pos < (unsigned long long)a.cap)
+                                    a.surv[pos] = make_uint2(unsigned(q), unsigned(j0 + cb * 32 + i));
+                                ++pos;
+                            }
                         }
                     }
                 }
@@ -431,7 +451,7 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
         for (int it = *s_consumed; it < issued; ++it)
             mbar_wait(full_bar(it % S), uint32_t(it / S) & 1u, s_abort, a.err);
         for (int itm = *s_aconsumed; itm < a_issued; ++itm)
-            mbar_wait(afull_bar, uint32_t(itm) & 1u, s_abort, a.err);
+            mbar_wait(afull_bar(itm & 1), uint32_t(itm >> 1) & 1u, s_abort, a.err);
     }
     tmem_fence_before();
     __syncthreads();
@@ -603,6 +623,7 @@ snn_status launch_tc(const snn_index *ix, const ScoreArgs &sa, const uint16_t *c
     a.tile_lo = sa.tile_lo;
     a.tile_hi = sa.tile_hi;
     a.item_off = sa.item_off;
+    a.item_tile = sa.item_tile;
     a.ntiles = sa.ntiles;
     a.sym = sa.sym;
     a.surv = sa.surv;
@@ -618,7 +639,7 @@ snn_status launch_tc(const snn_index *ix, const ScoreArgs &sa, const uint16_t *c
 }  // namespace
 
 snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream_t s,
-                           double Rx, double e_data, Scratch &scr) {
+                           double Rx, double e_data, Scratch &scr, int64_t *mma_flops_per_pair) {
     snn_index *ix = const_cast<snn_index *>(ixc);
     const int d = ix->d;
     const double R2h = 0.5 * Rx * Rx;
@@ -659,6 +680,8 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
             ix->tc_k2 = K2;
         }
     }
+    if (mma_flops_per_pair)
+        *mma_flops_per_pair = int64_t(2) * 16 * cdiv(d + kExtra, 16) * tc_npairs(nsplit);
     // query operands (per call): same split, query-side folded columns
     const int64_t m = sa.q.m;
     double *Aq;

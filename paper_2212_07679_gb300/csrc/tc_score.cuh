@@ -12,7 +12,9 @@ namespace snn {
 // use.  Returns SNN_ENOTSUP where the tensor-core path is not available.
 // Rx: largest true distance the FP64 test can accept; e_data: bound on the
 // centring error norm of a data row.  Query operands live in `scr`.
+// *mma_flops_per_pair receives the tensor-core flops executed per scored
+// pair (2 x 16 x k-steps x MMAs per k-step).
 snn_status tc_score_launch(const snn_index *ix, const ScoreArgs &a, cudaStream_t s, double Rx,
-                           double e_data, Scratch &scr);
+                           double e_data, Scratch &scr, int64_t *mma_flops_per_pair);
 
 }  // namespace snn

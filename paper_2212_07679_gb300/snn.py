@@ -35,7 +35,8 @@ class CSRStruct(ctypes.Structure):
 class StatsStruct(ctypes.Structure):
     _fields_ = [("candidates", ctypes.c_int64), ("band_pairs", ctypes.c_int64),
                 ("survivors", ctypes.c_int64), ("nnz", ctypes.c_int64),
-                ("exact_fp64", ctypes.c_int64), ("ms_prep", ctypes.c_float), ("ms_score", ctypes.c_float),
+                ("exact_fp64", ctypes.c_int64), ("mma_flops_per_pair", ctypes.c_int64),
+                ("ms_prep", ctypes.c_float), ("ms_score", ctypes.c_float),
                 ("ms_recheck", ctypes.c_float), ("ms_csr", ctypes.c_float)]
 
 
