@@ -327,8 +327,7 @@ __device__ __forceinline__ void decide_body(
          const uint2 *__restrict__ surv, int64_t nsurv, const float *__restrict__ qraw,
          const int32_t *__restrict__ qorder, const float *__restrict__ praw,
          const int32_t *__restrict__ porder, int d, int dp, double R2,
-         int32_t *__restrict__ rec_row, int32_t *__restrict__ rec_col, float *__restrict__ rec_d2,
-         int32_t *__restrict__ rec_pos, int32_t *__restrict__ counts,
+         float *__restrict__ rec_d2, int32_t *__restrict__ rec_pos, int32_t *__restrict__ counts,
          unsigned long long *__restrict__ n_fp64) {
     const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (s >= nsurv) return;
@@ -382,45 +381,33 @@ __device__ __forceinline__ void decide_body(
         d2 = (float)S;
         atomicAdd(n_fp64, 1ull);
     }
-    // records: (row, column, dist2, position within the row); the position
-    // comes from the counting atomic, so the scatter needs no atomics
-    const int64_t slot = kSym ? 2 * s : s;
+    // record: dist2 and the slot of the pair within its row (from the
+    // counting atomic, so the scatter needs no atomics); -1 = not a neighbour.
+    // A symmetric self-join pair also takes a slot in the mirrored row.
+    int32_t p0 = -1, p1 = -1;
     if (accept) {
         const int32_t row = qorder[e.x], col = porder[e.y];
-        rec_row[slot] = row;
-        rec_col[slot] = col;
-        rec_d2[slot] = d2;
-        rec_pos[slot] = atomicAdd(&counts[row], 1);
-        if (kSym) {
-            if (e.x != e.y) {
-                rec_row[slot + 1] = col;
-                rec_col[slot + 1] = row;
-                rec_d2[slot + 1] = d2;
-                rec_pos[slot + 1] = atomicAdd(&counts[col], 1);
-            } else {
-                rec_row[slot + 1] = -1;
-            }
-        }
-    } else {
-        rec_row[slot] = -1;
-        if (kSym) rec_row[slot + 1] = -1;
+        p0 = atomicAdd(&counts[row], 1);
+        if (kSym && e.x != e.y) p1 = atomicAdd(&counts[col], 1);
     }
+    rec_d2[s] = d2;
+    rec_pos[s] = p0;
+    if (kSym) rec_pos[nsurv + s] = p1;
 }
 
 #define SNN_DECIDE_ARGS                                                                      \
     const uint2 *__restrict__ surv, int64_t nsurv, const float *__restrict__ qraw,             \
         const int32_t *__restrict__ qorder, const float *__restrict__ praw,                    \
         const int32_t *__restrict__ porder, int d, int dp, double R2,                          \
-        int32_t *__restrict__ rec_row, int32_t *__restrict__ rec_col, float *__restrict__ rec_d2, \
-        int32_t *__restrict__ rec_pos, int32_t *__restrict__ counts,                          \
+        float *__restrict__ rec_d2, int32_t *__restrict__ rec_pos, int32_t *__restrict__ counts, \
         unsigned long long *__restrict__ n_fp64
 __global__ void __launch_bounds__(256) k_decide_sym(SNN_DECIDE_ARGS) {
-    decide_body<true>(surv, nsurv, qraw, qorder, praw, porder, d, dp, R2, rec_row, rec_col, rec_d2,
-                      rec_pos, counts, n_fp64);
+    decide_body<true>(surv, nsurv, qraw, qorder, praw, porder, d, dp, R2, rec_d2, rec_pos, counts,
+                      n_fp64);
 }
 __global__ void __launch_bounds__(256) k_decide_one(SNN_DECIDE_ARGS) {
-    decide_body<false>(surv, nsurv, qraw, qorder, praw, porder, d, dp, R2, rec_row, rec_col, rec_d2,
-                       rec_pos, counts, n_fp64);
+    decide_body<false>(surv, nsurv, qraw, qorder, praw, porder, d, dp, R2, rec_d2, rec_pos, counts,
+                       n_fp64);
 }
 #undef SNN_DECIDE_ARGS
 
@@ -430,17 +417,29 @@ __global__ void k_counts_to_i64(const int32_t *__restrict__ counts, int64_t m,
     if (i < m) out[i] = counts[i];
 }
 
-__global__ void k_scatter(const int32_t *__restrict__ rec_row, const int32_t *__restrict__ rec_col,
+// Writes each accepted pair at its row slot (and the mirrored pair of a
+// symmetric self-join), straight into the output CSR arrays.
+__global__ void k_scatter(const uint2 *__restrict__ surv, int64_t nsurv,
+                          const int32_t *__restrict__ qorder, const int32_t *__restrict__ porder,
                           const float *__restrict__ rec_d2, const int32_t *__restrict__ rec_pos,
-                          int64_t nsurv, const int64_t *__restrict__ offsets,
-                          int32_t *__restrict__ idx_u, float *__restrict__ d2_u) {
+                          int sym, const int64_t *__restrict__ offsets, int32_t *__restrict__ idx,
+                          float *__restrict__ d2) {
     const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (s >= nsurv) return;
-    const int32_t row = rec_row[s];
-    if (row < 0) return;
-    const int64_t pos = offsets[row] + rec_pos[s];
-    idx_u[pos] = rec_col[s];
-    d2_u[pos] = rec_d2[s];
+    const int32_t p0 = rec_pos[s];
+    if (p0 < 0) return;
+    const uint2 e = surv[s];
+    const int32_t row = qorder[e.x], col = porder[e.y];
+    const float v = rec_d2[s];
+    idx[offsets[row] + p0] = col;
+    d2[offsets[row] + p0] = v;
+    if (sym) {
+        const int32_t p1 = rec_pos[nsurv + s];
+        if (p1 >= 0) {
+            idx[offsets[col] + p1] = row;
+            d2[offsets[col] + p1] = v;
+        }
+    }
 }
 
 // ------------------------------------------- per-row sort by column id
@@ -474,9 +473,7 @@ __global__ void k_seg_classify(const int64_t *__restrict__ offsets, int64_t m,
 template <int E>
 __device__ __forceinline__ void seg_sort_warp(const int32_t *__restrict__ list, unsigned total,
                                               const int64_t *__restrict__ offsets,
-                                              const int32_t *__restrict__ idx_u,
-                                              const float *__restrict__ d2_u,
-                                              int32_t *__restrict__ idx, float *__restrict__ d2) {
+                                              int32_t *idx, float *d2) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
     for (int64_t w = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); w < total; w += nw) {
@@ -488,8 +485,8 @@ __device__ __forceinline__ void seg_sort_warp(const int32_t *__restrict__ list, 
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int i = e * 32 + lane;
-            key[e] = i < len ? idx_u[o + i] : INT32_MAX;
-            val[e] = i < len ? d2_u[o + i] : 0.f;
+            key[e] = i < len ? idx[o + i] : INT32_MAX;
+            val[e] = i < len ? d2[o + i] : 0.f;
         }
 #pragma unroll
         for (int k = 2; k <= 32 * E; k <<= 1) {
@@ -533,29 +530,22 @@ __device__ __forceinline__ void seg_sort_warp(const int32_t *__restrict__ list, 
 }
 
 __global__ void k_seg_sort_w1(const int32_t *__restrict__ list, const unsigned *__restrict__ count,
-                              const int64_t *__restrict__ offsets, const int32_t *__restrict__ idx_u,
-                              const float *__restrict__ d2_u, int32_t *__restrict__ idx,
-                              float *__restrict__ d2) {
-    seg_sort_warp<1>(list, *count, offsets, idx_u, d2_u, idx, d2);
+                              const int64_t *__restrict__ offsets, int32_t *idx, float *d2) {
+    seg_sort_warp<1>(list, *count, offsets, idx, d2);
 }
 __global__ void k_seg_sort_w16(const int32_t *__restrict__ list, const unsigned *__restrict__ count,
-                               const int64_t *__restrict__ offsets, const int32_t *__restrict__ idx_u,
-                               const float *__restrict__ d2_u, int32_t *__restrict__ idx,
-                               float *__restrict__ d2) {
-    seg_sort_warp<16>(list, *count, offsets, idx_u, d2_u, idx, d2);
+                              const int64_t *__restrict__ offsets, int32_t *idx, float *d2) {
+    seg_sort_warp<16>(list, *count, offsets, idx, d2);
 }
 __global__ void k_seg_sort_w4(const int32_t *__restrict__ list, const unsigned *__restrict__ count,
-                              const int64_t *__restrict__ offsets, const int32_t *__restrict__ idx_u,
-                              const float *__restrict__ d2_u, int32_t *__restrict__ idx,
-                              float *__restrict__ d2) {
-    seg_sort_warp<4>(list, *count, offsets, idx_u, d2_u, idx, d2);
+                              const int64_t *__restrict__ offsets, int32_t *idx, float *d2) {
+    seg_sort_warp<4>(list, *count, offsets, idx, d2);
 }
 
 // One block per row of <= 4096 entries: bitonic sort in shared memory.
 __global__ void __launch_bounds__(256)
 k_seg_sort_mid(const int32_t *__restrict__ list, const unsigned *__restrict__ count,
-               const int64_t *__restrict__ offsets, const int32_t *__restrict__ idx_u,
-               const float *__restrict__ d2_u, int32_t *__restrict__ idx, float *__restrict__ d2) {
+               const int64_t *__restrict__ offsets, int32_t *idx, float *d2) {
     __shared__ int32_t sk[kSegMid];
     __shared__ float sv[kSegMid];
     const unsigned total = *count;
@@ -567,8 +557,8 @@ k_seg_sort_mid(const int32_t *__restrict__ list, const unsigned *__restrict__ co
         while (N < len) N <<= 1;
         __syncthreads();
         for (int i = threadIdx.x; i < N; i += blockDim.x) {
-            sk[i] = i < len ? idx_u[o + i] : INT32_MAX;
-            sv[i] = i < len ? d2_u[o + i] : 0.f;
+            sk[i] = i < len ? idx[o + i] : INT32_MAX;
+            sv[i] = i < len ? d2[o + i] : 0.f;
         }
         __syncthreads();
         for (int k = 2; k <= N; k <<= 1) {
@@ -597,22 +587,24 @@ k_seg_sort_mid(const int32_t *__restrict__ list, const unsigned *__restrict__ co
 // Long rows: keys (big-row rank << 32 | column), values = source position.
 __global__ void k_seg_big_gather(const int32_t *__restrict__ big_list, int nbig,
                                  const int64_t *__restrict__ offsets, const int64_t *__restrict__ toff,
-                                 const int32_t *__restrict__ idx_u, uint64_t *__restrict__ keys,
-                                 uint32_t *__restrict__ vals) {
+                                 const int32_t *__restrict__ idx, const float *__restrict__ d2,
+                                 uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                                 float *__restrict__ gd2) {
     const int b = blockIdx.x;
     if (b >= nbig) return;
     const int32_t r = big_list[b];
     const int64_t o = offsets[r], len = offsets[r + 1] - o, t0 = toff[b];
     for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
-        keys[t0 + i] = (uint64_t(b) << 32) | uint64_t(uint32_t(idx_u[o + i]));
-        vals[t0 + i] = uint32_t(o + i);
+        keys[t0 + i] = (uint64_t(b) << 32) | uint64_t(uint32_t(idx[o + i]));
+        vals[t0 + i] = uint32_t(t0 + i);
+        gd2[t0 + i] = d2[o + i];
     }
 }
 
 __global__ void k_seg_big_scatter(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
                                   int64_t total, const int32_t *__restrict__ big_list,
                                   const int64_t *__restrict__ offsets, const int64_t *__restrict__ toff,
-                                  const float *__restrict__ d2_u, int32_t *__restrict__ idx,
+                                  const float *__restrict__ gd2, int32_t *__restrict__ idx,
                                   float *__restrict__ d2) {
     const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (t >= total) return;
@@ -620,7 +612,7 @@ __global__ void k_seg_big_scatter(const uint64_t *__restrict__ keys, const uint3
     const int b = int(k >> 32);
     const int64_t pos = offsets[big_list[b]] + (t - toff[b]);
     idx[pos] = int32_t(uint32_t(k & 0xffffffffu));
-    d2[pos] = d2_u[vals[t]];
+    d2[pos] = gd2[vals[t]];
 }
 
 }  // namespace snn

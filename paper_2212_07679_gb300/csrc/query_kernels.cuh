@@ -66,18 +66,16 @@ __global__ void k_score_fp32_multi(ScoreArgs a);
 // pair, _one emits the (query, point) orientation only.
 __global__ void k_decide_sym(const uint2 *surv, int64_t nsurv, const float *qraw,
                              const int32_t *qorder, const float *praw, const int32_t *porder,
-                             int d, int dp, double R2, int32_t *rec_row, int32_t *rec_col,
-                             float *rec_d2, int32_t *rec_pos, int32_t *counts,
-                             unsigned long long *n_fp64);
+                             int d, int dp, double R2, float *rec_d2, int32_t *rec_pos,
+                             int32_t *counts, unsigned long long *n_fp64);
 __global__ void k_decide_one(const uint2 *surv, int64_t nsurv, const float *qraw,
                              const int32_t *qorder, const float *praw, const int32_t *porder,
-                             int d, int dp, double R2, int32_t *rec_row, int32_t *rec_col,
-                             float *rec_d2, int32_t *rec_pos, int32_t *counts,
-                             unsigned long long *n_fp64);
+                             int d, int dp, double R2, float *rec_d2, int32_t *rec_pos,
+                             int32_t *counts, unsigned long long *n_fp64);
 __global__ void k_counts_to_i64(const int32_t *counts, int64_t m, int64_t *out);
-__global__ void k_scatter(const int32_t *rec_row, const int32_t *rec_col, const float *rec_d2,
-                          const int32_t *rec_pos, int64_t nsurv, const int64_t *offsets,
-                          int32_t *idx_u, float *d2_u);
+__global__ void k_scatter(const uint2 *surv, int64_t nsurv, const int32_t *qorder,
+                          const int32_t *porder, const float *rec_d2, const int32_t *rec_pos, int sym,
+                          const int64_t *offsets, int32_t *idx, float *d2);
 
 // Segmented sort of CSR rows by column id.
 constexpr int kSegSmall = 32;
@@ -85,19 +83,18 @@ constexpr int kSegMid = 4096;
 __global__ void k_seg_classify(const int64_t *offsets, int64_t m, int32_t *lists,
                                int32_t *big_list, int64_t *big_len, unsigned *counters);
 __global__ void k_seg_sort_w1(const int32_t *list, const unsigned *count, const int64_t *offsets,
-                              const int32_t *idx_u, const float *d2_u, int32_t *idx, float *d2);
+                              int32_t *idx, float *d2);
 __global__ void k_seg_sort_w16(const int32_t *list, const unsigned *count, const int64_t *offsets,
-                               const int32_t *idx_u, const float *d2_u, int32_t *idx, float *d2);
+                              int32_t *idx, float *d2);
 __global__ void k_seg_sort_w4(const int32_t *list, const unsigned *count, const int64_t *offsets,
-                              const int32_t *idx_u, const float *d2_u, int32_t *idx, float *d2);
+                              int32_t *idx, float *d2);
 __global__ void k_seg_sort_mid(const int32_t *list, const unsigned *count, const int64_t *offsets,
-                               const int32_t *idx_u, const float *d2_u, int32_t *idx, float *d2);
+                               int32_t *idx, float *d2);
 __global__ void k_seg_big_gather(const int32_t *big_list, int nbig, const int64_t *offsets,
-                                 const int64_t *toff, const int32_t *idx_u, uint64_t *keys,
-                                 uint32_t *vals);
+                                 const int64_t *toff, const int32_t *idx, const float *d2,
+                                 uint64_t *keys, uint32_t *vals, float *gd2);
 __global__ void k_seg_big_scatter(const uint64_t *keys, const uint32_t *vals, int64_t total,
                                   const int32_t *big_list, const int64_t *offsets,
-                                  const int64_t *toff, const float *d2_u, int32_t *idx,
-                                  float *d2);
+                                  const int64_t *toff, const float *gd2, int32_t *idx, float *d2);
 
 }  // namespace snn

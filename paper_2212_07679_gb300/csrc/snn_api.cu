@@ -474,32 +474,26 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     g_surv_hint.store(double(nsurv) / double(m), std::memory_order_relaxed);
 
     // exact decision for every survivor (compensated FP32, FP64 where needed)
-    const int64_t nrec = sym ? 2 * nsurv : nsurv;
-    int32_t *rec_row, *rec_col, *rec_pos, *counts;
+    int32_t *rec_pos, *counts;
     float *rec_d2;
     int64_t *counts64;
-    TRY_Q(scr.alloc(&rec_row, nrec));
-    TRY_Q(scr.alloc(&rec_col, nrec));
-    TRY_Q(scr.alloc(&rec_d2, nrec));
-    TRY_Q(scr.alloc(&rec_pos, nrec));
+    TRY_Q(scr.alloc(&rec_d2, nsurv));
+    TRY_Q(scr.alloc(&rec_pos, sym ? 2 * nsurv : nsurv));
     TRY_Q(scr.alloc(&counts, m));
     TRY_Q(scr.alloc(&counts64, m));
     CUDA_Q(cudaMemsetAsync(counts, 0, m * sizeof(int32_t), s));
     const double R2 = R * R;
     if (nsurv > 0) {
         if (sym)
-            SNN_LAUNCH(k_decide_sym, grid_for(nsurv, 256), 256, 0, s)(surv, nsurv, qs.raw, qs.order, ds.raw,
-                                                                ds.order, d, dp, R2, rec_row, rec_col,
-                                                                rec_d2, rec_pos, counts, ctr + 4);
+            SNN_LAUNCH(k_decide_sym, grid_for(nsurv, 256), 256, 0, s)(
+                surv, nsurv, qs.raw, qs.order, ds.raw, ds.order, d, dp, R2, rec_d2, rec_pos, counts,
+                ctr + 4);
         else
-            SNN_LAUNCH(k_decide_one, grid_for(nsurv, 256), 256, 0, s)(surv, nsurv, qs.raw, qs.order,
-                                                                 ds.raw, ds.order, d, dp, R2, rec_row,
-                                                                 rec_col, rec_d2, rec_pos, counts,
-                                                                 ctr + 4);
+            SNN_LAUNCH(k_decide_one, grid_for(nsurv, 256), 256, 0, s)(
+                surv, nsurv, qs.raw, qs.order, ds.raw, ds.order, d, dp, R2, rec_d2, rec_pos, counts,
+                ctr + 4);
         CUDA_Q(cudaGetLastError());
     }
-    cudaFreeAsync(surv, s);
-    surv = nullptr;
     if (stats) cudaEventRecord(ev[3], s);
     SNN_LAUNCH(k_counts_to_i64, grid_for(m, 256), 256, 0, s)(counts, m, counts64);
     CUDA_Q(cudaGetLastError());
@@ -515,14 +509,11 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     if (nnz > 0) {
         TRY_Q(dev_alloc(&out->indices, nnz));
         TRY_Q(dev_alloc(&out->dist2, nnz));
-        int32_t *idx_u;
-        float *d2_u;
-        TRY_Q(scr.alloc(&idx_u, nnz));
-        TRY_Q(scr.alloc(&d2_u, nnz));
-        SNN_LAUNCH(k_scatter, grid_for(nrec, 256), 256, 0, s)(rec_row, rec_col, rec_d2, rec_pos, nrec,
-                                                      out->offsets, idx_u, d2_u);
+        SNN_LAUNCH(k_scatter, grid_for(nsurv, 256), 256, 0, s)(surv, nsurv, qs.order, ds.order,
+                                                               rec_d2, rec_pos, sym, out->offsets,
+                                                               out->indices, out->dist2);
         CUDA_Q(cudaGetLastError());
-        // per-row ascending column ids
+        // per-row ascending column ids, in place
         int32_t *lists, *big_list;
         int64_t *big_len, *toff;
         unsigned *cls;
@@ -534,18 +525,15 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         CUDA_Q(cudaMemsetAsync(cls, 0, 8 * sizeof(unsigned), s));
         SNN_LAUNCH(k_seg_classify, grid_for(m, 256), 256, 0, s)(out->offsets, m, lists, big_list,
                                                                 big_len, cls);
-        // rows of 0 or 1 entries are already in place
-        CUDA_Q(cudaMemcpyAsync(out->indices, idx_u, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-        CUDA_Q(cudaMemcpyAsync(out->dist2, d2_u, nnz * sizeof(float), cudaMemcpyDeviceToDevice, s));
         const unsigned wgrid = std::min<unsigned>(grid_for(m * 32, 256), 16384);
-        SNN_LAUNCH(k_seg_sort_w1, wgrid, 256, 0, s)(lists, cls, out->offsets, idx_u, d2_u,
-                                                     out->indices, out->dist2);
-        SNN_LAUNCH(k_seg_sort_w4, wgrid, 256, 0, s)(lists + m, cls + 1, out->offsets, idx_u, d2_u,
-                                                     out->indices, out->dist2);
-        SNN_LAUNCH(k_seg_sort_w16, wgrid, 256, 0, s)(lists + 2 * m, cls + 2, out->offsets, idx_u,
-                                                      d2_u, out->indices, out->dist2);
+        SNN_LAUNCH(k_seg_sort_w1, wgrid, 256, 0, s)(lists, cls, out->offsets, out->indices,
+                                                     out->dist2);
+        SNN_LAUNCH(k_seg_sort_w4, wgrid, 256, 0, s)(lists + m, cls + 1, out->offsets, out->indices,
+                                                     out->dist2);
+        SNN_LAUNCH(k_seg_sort_w16, wgrid, 256, 0, s)(lists + 2 * m, cls + 2, out->offsets,
+                                                      out->indices, out->dist2);
         SNN_LAUNCH(k_seg_sort_mid, std::min<unsigned>((unsigned)m, 4096), 256, 0, s)(
-            lists + 3 * m, cls + 3, out->offsets, idx_u, d2_u, out->indices, out->dist2);
+            lists + 3 * m, cls + 3, out->offsets, out->indices, out->dist2);
         CUDA_Q(cudaGetLastError());
         unsigned hcls[8];
         CUDA_Q(cudaMemcpyAsync(hcls, cls, sizeof(hcls), cudaMemcpyDeviceToHost, s));
@@ -558,21 +546,25 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
             CUDA_Q(cudaStreamSynchronize(s));
             uint64_t *bk, *bka;
             uint32_t *bv, *bva;
+            float *gd2;
             TRY_Q(scr.alloc(&bk, tot));
             TRY_Q(scr.alloc(&bka, tot));
             TRY_Q(scr.alloc(&bv, tot));
             TRY_Q(scr.alloc(&bva, tot));
-            SNN_LAUNCH(k_seg_big_gather, nbig, 256, 0, s)(big_list, nbig, out->offsets, toff, idx_u, bk, bv);
+            TRY_Q(scr.alloc(&gd2, tot));
+            SNN_LAUNCH(k_seg_big_gather, nbig, 256, 0, s)(big_list, nbig, out->offsets, toff,
+                                                          out->indices, out->dist2, bk, bv, gd2);
             CUDA_Q(cudaGetLastError());
             int bits = 32;
             while ((int64_t(1) << (bits - 32)) < nbig) ++bits;
             TRY_Q(radix_sort_pairs<uint64_t>(bk, bv, bka, bva, tot, bits, s));
-            SNN_LAUNCH(k_seg_big_scatter, grid_for(tot, 256), 256, 0, s)(bk, bv, tot, big_list, out->offsets,
-                                                                 toff, d2_u, out->indices,
-                                                                 out->dist2);
+            SNN_LAUNCH(k_seg_big_scatter, grid_for(tot, 256), 256, 0, s)(
+                bk, bv, tot, big_list, out->offsets, toff, gd2, out->indices, out->dist2);
             CUDA_Q(cudaGetLastError());
         }
     }
+    cudaFreeAsync(surv, s);
+    surv = nullptr;
     if (stats) {
         cudaEventRecord(ev[4], s);
         unsigned long long nf = 0;

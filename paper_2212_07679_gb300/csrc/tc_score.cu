@@ -182,6 +182,7 @@ struct TcArgs {
     int64_t m;
     int64_t n;
     int ksteps;                 // 16-wide k steps that hold data or folded columns
+    int ksteps_data;            // k steps that hold data columns (the rest: folded only)
     int nkb;                    // k blocks loaded per chunk
     const int64_t *tile_lo;
     const int64_t *tile_hi;
@@ -349,9 +350,14 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                         tmem_fence_after();
 #pragma unroll
                         for (int ks = 0; ks < Sh::kKSteps; ++ks) {
-                            if (kb * Sh::kKSteps + ks >= a.ksteps) break;
+                            const int kg = kb * Sh::kKSteps + ks;
+                            if (kg >= a.ksteps) break;
+                            // the folded columns live in part 0 only: a k step
+                            // without data columns needs the (0,0) product alone
+                            const int np = kg < a.ksteps_data ? NP : 1;
 #pragma unroll
                             for (int pr = 0; pr < NP; ++pr) {
+                                if (pr >= np) break;
                                 const uint64_t ad = smem_desc<Sh::kRowBytes>(
                                     a_tile(ARES ? aslot : s, kPa[pr]) + 32u * ks);
                                 const uint64_t bd =
@@ -592,7 +598,8 @@ snn_status make_map(CUtensorMap *map, const uint16_t *ptr, int64_t rows, int K2,
 // Rounding constant c of the folded test for a split and a dimension.
 double tc_constant(int nsplit, int d, double *u_k_out) {
     const int ksteps = int(cdiv(d + kExtra, 16));
-    const int ninstr = tc_npairs(nsplit) * ksteps;
+    const int ksteps_data = int(cdiv(d, 16));
+    const int ninstr = tc_npairs(nsplit) * ksteps_data + (ksteps - ksteps_data);
     // FP32 accumulation: each MMA instruction is charged 2^-22 of (|C_in| +
     // sum of its |products|), i.e. (ninstr + 1) 2^-22 of all |products|
     const double u_k = 0x1p-22 * (ninstr + 1);
@@ -619,6 +626,7 @@ snn_status launch_tc(const snn_index *ix, const ScoreArgs &sa, const uint16_t *c
     a.m = sa.q.m;
     a.n = ix->n;
     a.ksteps = int(cdiv(ix->d + kExtra, 16));
+    a.ksteps_data = int(cdiv(ix->d, 16));
     a.nkb = K2 / BK;
     a.tile_lo = sa.tile_lo;
     a.tile_hi = sa.tile_hi;
@@ -680,8 +688,10 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
             ix->tc_k2 = K2;
         }
     }
-    if (mma_flops_per_pair)
-        *mma_flops_per_pair = int64_t(2) * 16 * cdiv(d + kExtra, 16) * tc_npairs(nsplit);
+    if (mma_flops_per_pair) {
+        const int64_t ks_all = cdiv(d + kExtra, 16), ks_data = cdiv(d, 16);
+        *mma_flops_per_pair = int64_t(2) * 16 * (ks_data * tc_npairs(nsplit) + (ks_all - ks_data));
+    }
     // query operands (per call): same split, query-side folded columns
     const int64_t m = sa.q.m;
     double *Aq;
