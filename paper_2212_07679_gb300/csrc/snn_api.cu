@@ -517,7 +517,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         int32_t *lists, *big_list;
         int64_t *big_len, *toff;
         unsigned *cls;
-        TRY_Q(scr.alloc(&lists, 4 * m));
+        TRY_Q(scr.alloc(&lists, 5 * m));
         TRY_Q(scr.alloc(&big_list, m));
         TRY_Q(scr.alloc(&big_len, m));
         TRY_Q(scr.alloc(&toff, m + 1));
@@ -530,6 +530,8 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
                                                      out->dist2);
         SNN_LAUNCH(k_seg_sort_w4, wgrid, 256, 0, s)(lists + m, cls + 1, out->offsets, out->indices,
                                                      out->dist2);
+        SNN_LAUNCH(k_seg_sort_w8, wgrid, 256, 0, s)(lists + 4 * m, cls + 5, out->offsets,
+                                                     out->indices, out->dist2);
         SNN_LAUNCH(k_seg_sort_w16, wgrid, 256, 0, s)(lists + 2 * m, cls + 2, out->offsets,
                                                       out->indices, out->dist2);
         SNN_LAUNCH(k_seg_sort_mid, std::min<unsigned>((unsigned)m, 4096), 256, 0, s)(

@@ -33,15 +33,20 @@ constexpr int kEpiWarps = 8;        // two warps per TMEM lane quadrant, half th
 constexpr int kTcThreads = 64 + 32 * kEpiWarps;
 constexpr int kExtra = 9;           // folded columns
 constexpr long long kTimeoutCycles = 4000000000LL;   // ~2 s
-constexpr int kSmemBudget = 232448 - 1024 - 256;     // dynamic smem minus alignment and barriers
+// dynamic shared memory per CTA (minus alignment and barriers) for 1 or 2
+// resident CTAs per SM
+__host__ __device__ constexpr int smem_budget(int cps) {
+    return cps == 1 ? 232448 - 1024 - 256 : 233472 / 2 - 1024 - 1024 - 256;
+}
 
 // Shape of one kernel instance: NSPLIT BF16 parts, BK columns per k-block
 // (64: 128-byte rows, 128B swizzle; 32: 64-byte rows, 64B swizzle), BN band
 // rows per chunk (MMA N), ARES: the query tile stays in shared memory for a
 // whole work item (only when one k-block holds all columns), in two slots so
 // that the next item's tile loads while the current one is in use.
-template <int NSPLIT, int BK, int BN, bool ARES>
+template <int NSPLIT, int BK, int BN, bool ARES, int CPS = 1>
 struct TcShape {
+    static constexpr int kSmemBudget = smem_budget(CPS);
     static constexpr int kTA = kTM * BK * 2;            // bytes of one A part tile
     static constexpr int kTB = BN * BK * 2;             // bytes of one B part tile
     static constexpr int kAResBytes = ARES ? 2 * NSPLIT * kTA : 0;
@@ -211,13 +216,13 @@ __device__ __forceinline__ ItemInfo item_info(const TcArgs &a, int64_t item) {
     return f;
 }
 
-template <int NSPLIT, int BK, int BN, bool ARES>
-__global__ void __launch_bounds__(kTcThreads, 1)
+template <int NSPLIT, int BK, int BN, bool ARES, int CPS>
+__global__ void __launch_bounds__(kTcThreads, CPS)
 k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUtensorMap qa1,
            const __grid_constant__ CUtensorMap qa2, const __grid_constant__ CUtensorMap xb0,
            const __grid_constant__ CUtensorMap xb1, const __grid_constant__ CUtensorMap xb2,
            TcArgs a) {
-    using Sh = TcShape<NSPLIT, BK, BN, ARES>;
+    using Sh = TcShape<NSPLIT, BK, BN, ARES, CPS>;
     constexpr int S = Sh::kStages;
     constexpr int NP = Sh::kNP;
     constexpr int CSTEP = BN / kBR;              // kBR-row chunks per MMA chunk
@@ -486,53 +491,57 @@ __device__ __forceinline__ void split3(double w, uint16_t (&o)[3]) {
 
 // Row r of an operand: split parts of the centred row, then the folded
 // columns (data side: -(1-c) xbar_j split, ||x_j|| rounded up three times,
-// ones; query side: ones, c ||y_i|| split, A'_i split).
+// ones; query side: ones, c ||y_i|| split, A'_i split).  One warp per row,
+// lanes over columns (coalesced 2-byte stores).
 template <int NSPLIT>
 __global__ void k_tc_pack(const float *__restrict__ xc, int dp, const float *__restrict__ hx,
                           const float *__restrict__ nrm, const double *__restrict__ Aq,
                           int64_t rows, int d, int K2, double c, int query_side,
                           uint16_t *__restrict__ p0, uint16_t *__restrict__ p1,
                           uint16_t *__restrict__ p2) {
-    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (e >= rows * K2) return;
-    const int64_t r = e / K2;
-    const int k = int(e % K2);
-    uint16_t v0 = 0, v1 = 0, v2 = 0;
-    if (k < d) {
-        const float x = xc[r * dp + k];
-        const __nv_bfloat16 h = __float2bfloat16_rn(x);
-        const float xr = x - __bfloat162float(h);               // exact
-        const __nv_bfloat16 l = __float2bfloat16_rn(xr);
-        v0 = bf16_bits(h);
-        v1 = bf16_bits(l);
-        if (NSPLIT == 3) v2 = bf16_bits(__float2bfloat16_rn(xr - __bfloat162float(l)));
-    } else if (k < d + kExtra) {
-        const int t = k - d;
-        uint16_t sp[3];
-        if (!query_side) {
-            if (t < 3) {
-                split3(-(1.0 - c) * (double)hx[r], sp);
-                v0 = sp[t];
-            } else if (t < 6) {
-                v0 = bf16_bits(__float2bfloat16_ru(nrm[r]));
+    const int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    const float *xr = xc + r * dp;
+    const int64_t ro = r * K2;
+    for (int k = lane; k < K2; k += 32) {
+        uint16_t v0 = 0, v1 = 0, v2 = 0;
+        if (k < d) {
+            const float x = xr[k];
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            const float xr1 = x - __bfloat162float(h);               // exact
+            const __nv_bfloat16 l = __float2bfloat16_rn(xr1);
+            v0 = bf16_bits(h);
+            v1 = bf16_bits(l);
+            if (NSPLIT == 3) v2 = bf16_bits(__float2bfloat16_rn(xr1 - __bfloat162float(l)));
+        } else if (k < d + kExtra) {
+            const int t = k - d;
+            uint16_t sp[3];
+            if (!query_side) {
+                if (t < 3) {
+                    split3(-(1.0 - c) * (double)hx[r], sp);
+                    v0 = sp[t];
+                } else if (t < 6) {
+                    v0 = bf16_bits(__float2bfloat16_ru(nrm[r]));
+                } else {
+                    v0 = bf16_bits(__float2bfloat16_rn(1.0f));
+                }
             } else {
-                v0 = bf16_bits(__float2bfloat16_rn(1.0f));
-            }
-        } else {
-            if (t < 3) {
-                v0 = bf16_bits(__float2bfloat16_rn(1.0f));
-            } else if (t < 6) {
-                split3(c * (double)nrm[r], sp);
-                v0 = sp[t - 3];
-            } else {
-                split3(Aq[r], sp);
-                v0 = sp[t - 6];
+                if (t < 3) {
+                    v0 = bf16_bits(__float2bfloat16_rn(1.0f));
+                } else if (t < 6) {
+                    split3(c * (double)nrm[r], sp);
+                    v0 = sp[t - 3];
+                } else {
+                    split3(Aq[r], sp);
+                    v0 = sp[t - 6];
+                }
             }
         }
+        p0[ro + k] = v0;
+        if (NSPLIT >= 2) p1[ro + k] = v1;
+        if (NSPLIT >= 3) p2[ro + k] = v2;
     }
-    p0[e] = v0;
-    if (NSPLIT >= 2) p1[e] = v1;
-    if (NSPLIT >= 3) p2[e] = v2;
 }
 
 // A'_i >= (Rx + e_data + e_i)^2/2 - ||y_i||^2/2, inflated so that its split
@@ -610,17 +619,17 @@ double tc_constant(int nsplit, int d, double *u_k_out) {
     return 1.02 * (c_mn > c_hx ? c_mn : c_hx);
 }
 
-template <int NSPLIT, int BK, int BN, bool ARES>
+template <int NSPLIT, int BK, int BN, bool ARES, int CPS>
 snn_status launch_tc(const snn_index *ix, const ScoreArgs &sa, const uint16_t *const *qp,
                      int K2, cudaStream_t s) {
-    using Sh = TcShape<NSPLIT, BK, BN, ARES>;
+    using Sh = TcShape<NSPLIT, BK, BN, ARES, CPS>;
     CUtensorMap maps[6];
     for (int p = 0; p < 3; ++p) {
         const int pp = p < NSPLIT ? p : 0;
         SNN_TRY(make_map(&maps[p], qp[pp], sa.q.m, K2, BK, kTM));
         SNN_TRY(make_map(&maps[3 + p], ix->tc_part[pp], ix->n, K2, BK, BN));
     }
-    auto kern = k_score_tc<NSPLIT, BK, BN, ARES>;
+    auto kern = k_score_tc<NSPLIT, BK, BN, ARES, CPS>;
     SNN_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::kSmem)));
     TcArgs a;
     a.m = sa.q.m;
@@ -638,7 +647,7 @@ snn_status launch_tc(const snn_index *ix, const ScoreArgs &sa, const uint16_t *c
     a.cap = sa.cap;
     a.count = sa.count;
     a.err = sa.err;
-    SNN_LAUNCH(kern, device_sm_count(), kTcThreads, Sh::kSmem, s)(maps[0], maps[1], maps[2],
+    SNN_LAUNCH(kern, device_sm_count() * CPS, kTcThreads, Sh::kSmem, s)(maps[0], maps[1], maps[2],
                                                                  maps[3], maps[4], maps[5], a);
     SNN_LAUNCH_CHECK();
     return SNN_OK;
@@ -678,9 +687,8 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
                     return SNN_ENOMEM;
                 }
             }
-            const int64_t tot = ix->n * K2;
             auto packer = nsplit == 2 ? k_tc_pack<2> : k_tc_pack<3>;
-            SNN_LAUNCH(packer, unsigned(cdiv(tot, 256)), 256, 0, s)(
+            SNN_LAUNCH(packer, unsigned(cdiv(ix->n * 32, 256)), 256, 0, s)(
                 ix->xc, ix->dp, ix->hx, ix->nrm, nullptr, ix->n, d, K2, c, 0, ix->tc_part[0],
                 ix->tc_part[1], ix->tc_part[2]);
             SNN_LAUNCH_CHECK();
@@ -701,19 +709,21 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
     SNN_LAUNCH(k_tc_query_consts, unsigned(cdiv(m, 256)), 256, 0, s)(
         sa.q.hx, sa.q.nrm, m, d, Rx, e_data, 0x1p-23 + u_k, Aq);
     SNN_LAUNCH_CHECK();
-    const int64_t tot = m * K2;
     auto packer = nsplit == 2 ? k_tc_pack<2> : k_tc_pack<3>;
-    SNN_LAUNCH(packer, unsigned(cdiv(tot, 256)), 256, 0, s)(sa.q.xc, ix->dp, sa.q.hx, sa.q.nrm, Aq,
+    SNN_LAUNCH(packer, unsigned(cdiv(m * 32, 256)), 256, 0, s)(sa.q.xc, ix->dp, sa.q.hx, sa.q.nrm, Aq,
                                                             m, d, K2, c, 1, qp[0], qp[1], qp[2]);
     SNN_LAUNCH_CHECK();
+    // low d: two CTAs per SM, each with a resident query tile, so that one
+    // CTA's pipeline bubbles (accumulator hand-off, item changes) overlap the
+    // other's MMAs
     if (kp <= 32)
-        return nsplit == 2 ? launch_tc<2, 32, 256, true>(ix, sa, qp, K2, s)
-                           : launch_tc<3, 32, 256, true>(ix, sa, qp, K2, s);
+        return nsplit == 2 ? launch_tc<2, 32, 128, true, 2>(ix, sa, qp, K2, s)
+                           : launch_tc<3, 32, 128, true, 2>(ix, sa, qp, K2, s);
     if (kp <= 64)
-        return nsplit == 2 ? launch_tc<2, 64, 128, true>(ix, sa, qp, K2, s)
-                           : launch_tc<3, 64, 128, true>(ix, sa, qp, K2, s);
-    return nsplit == 2 ? launch_tc<2, 64, 128, false>(ix, sa, qp, K2, s)
-                       : launch_tc<3, 64, 128, false>(ix, sa, qp, K2, s);
+        return nsplit == 2 ? launch_tc<2, 64, 128, true, 1>(ix, sa, qp, K2, s)
+                           : launch_tc<3, 64, 128, true, 1>(ix, sa, qp, K2, s);
+    return nsplit == 2 ? launch_tc<2, 64, 128, false, 1>(ix, sa, qp, K2, s)
+                       : launch_tc<3, 64, 128, false, 1>(ix, sa, qp, K2, s);
 }
 
 }  // namespace snn
