@@ -212,6 +212,31 @@ def run_ours(args):
     ms_step = float(t_max.item()) / args.steps
     value = world * w.m / (ms_step / 1e3)
 
+    # the other scoring precision on the same workload, same timing rules
+    compare = None
+    if args.compare:
+        other = "fp32" if args.precision == "bf16" else "bf16"
+        for _ in range(2):
+            ix = snn.Index(X)
+            ix.query(None, w.R, precision=other)
+            del ix
+        times = []
+        for _ in range(max(3, min(args.steps, 5))):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ix = snn.Index(X)
+            out = ix.query(None, w.R, precision=other, stats=True)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            ost = out.stats
+            del ix, out
+        oms = float(np.mean(times))
+        compare = {"precision": other, "value": w.m / (oms / 1e3), "unit": "queries/s",
+                   "ms_per_step": oms, "score_ms": ost["ms_score"], "survivors": ost["survivors"]}
+
     # end to end through host buffers: pinned X in, CSR out, every step
     e2e_ms, h2d, d2h = [], 0, 0
     for _ in range(max(1, min(args.steps, 3))):
@@ -260,10 +285,10 @@ def run_ours(args):
                                    "scores each unordered pair once",
                     "effective_tflops": effective, "score_ms": sm}
     line = {
-        "metric": "exact radius queries/s (self-join, FP32 rejection + FP64 decision)",
+        "metric": "exact radius queries/s (self-join; BF16 tensor-core or FP32 rejection, exact decision)",
         "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32+f64" if args.precision == "bf16" else "f32+f64", "data": "synthetic",
         "config": workload_config(args, w),
         "pairs_scored_per_s": st["band_pairs"] / (ms_step / 1e3),
         "candidate_pairs_per_s": st["candidates"] / (ms_step / 1e3),
@@ -273,6 +298,7 @@ def run_ours(args):
         "phase_ms": {k: st[k] for k in ("ms_prep", "ms_score", "ms_recheck", "ms_csr")},
         "roofline": roofline,
         "clocks": clk,
+        "other_precision": compare,
         "gpu_launches": launches,
         "gpu_launches_per_step": launches / args.steps,
         "e2e": {"value": w.m / (np.median(e2e_ms) / 1e3), "unit": "queries/s",
@@ -294,7 +320,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="gmm_aniso")
     ap.add_argument("--n", type=int, default=0)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
+    ap.add_argument("--no-compare", dest="compare", action="store_false",
+                    help="skip timing the other precision beside the headline one")
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     args = ap.parse_args()

@@ -443,9 +443,9 @@ __global__ void k_scatter(const uint2 *__restrict__ surv, int64_t nsurv,
 }
 
 // ------------------------------------------- per-row sort by column id
-// Rows by length: [0] <= 32, [1] <= 128, [2] <= 512, [5] <= 256 (one warp
-// each), [3] <= 4096 (one block each), [4] longer (radix sort).  lists holds
-// 5 arrays of m entries ([5] in the last).
+// Rows by length: [0] <= 32, [6] <= 64, [1] <= 128, [5] <= 256, [2] <= 512
+// (one warp each), [3] <= 4096 (one block each), [4] longer (radix sort).
+// lists holds 6 arrays of m entries (class 5 in slot 4, class 6 in slot 5).
 __global__ void k_seg_classify(const int64_t *__restrict__ offsets, int64_t m,
                                int32_t *__restrict__ lists, int32_t *__restrict__ big_list,
                                int64_t *__restrict__ big_len, unsigned *__restrict__ counters) {
@@ -455,6 +455,8 @@ __global__ void k_seg_classify(const int64_t *__restrict__ offsets, int64_t m,
     if (len <= 1) return;   // nothing to order (the scatter wrote it in place)
     if (len <= kSegSmall) {
         lists[atomicAdd(&counters[0], 1u)] = (int32_t)r;
+    } else if (len <= 2 * kSegSmall) {
+        lists[5 * m + atomicAdd(&counters[6], 1u)] = (int32_t)r;
     } else if (len <= 4 * kSegSmall) {
         lists[m + atomicAdd(&counters[1], 1u)] = (int32_t)r;
     } else if (len <= 8 * kSegSmall) {
@@ -542,6 +544,10 @@ __global__ void k_seg_sort_w16(const int32_t *__restrict__ list, const unsigned 
 __global__ void k_seg_sort_w8(const int32_t *__restrict__ list, const unsigned *__restrict__ count,
                               const int64_t *__restrict__ offsets, int32_t *idx, float *d2) {
     seg_sort_warp<8>(list, *count, offsets, idx, d2);
+}
+__global__ void k_seg_sort_w2(const int32_t *__restrict__ list, const unsigned *__restrict__ count,
+                              const int64_t *__restrict__ offsets, int32_t *idx, float *d2) {
+    seg_sort_warp<2>(list, *count, offsets, idx, d2);
 }
 __global__ void k_seg_sort_w4(const int32_t *__restrict__ list, const unsigned *__restrict__ count,
                               const int64_t *__restrict__ offsets, int32_t *idx, float *d2) {

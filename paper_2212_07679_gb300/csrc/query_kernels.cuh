@@ -88,6 +88,8 @@ __global__ void k_seg_sort_w16(const int32_t *list, const unsigned *count, const
                               int32_t *idx, float *d2);
 __global__ void k_seg_sort_w8(const int32_t *list, const unsigned *count, const int64_t *offsets,
                               int32_t *idx, float *d2);
+__global__ void k_seg_sort_w2(const int32_t *list, const unsigned *count, const int64_t *offsets,
+                              int32_t *idx, float *d2);
 __global__ void k_seg_sort_w4(const int32_t *list, const unsigned *count, const int64_t *offsets,
                               int32_t *idx, float *d2);
 __global__ void k_seg_sort_mid(const int32_t *list, const unsigned *count, const int64_t *offsets,

@@ -517,7 +517,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         int32_t *lists, *big_list;
         int64_t *big_len, *toff;
         unsigned *cls;
-        TRY_Q(scr.alloc(&lists, 5 * m));
+        TRY_Q(scr.alloc(&lists, 6 * m));
         TRY_Q(scr.alloc(&big_list, m));
         TRY_Q(scr.alloc(&big_len, m));
         TRY_Q(scr.alloc(&toff, m + 1));
@@ -528,6 +528,8 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         const unsigned wgrid = std::min<unsigned>(grid_for(m * 32, 256), 16384);
         SNN_LAUNCH(k_seg_sort_w1, wgrid, 256, 0, s)(lists, cls, out->offsets, out->indices,
                                                      out->dist2);
+        SNN_LAUNCH(k_seg_sort_w2, wgrid, 256, 0, s)(lists + 5 * m, cls + 6, out->offsets,
+                                                     out->indices, out->dist2);
         SNN_LAUNCH(k_seg_sort_w4, wgrid, 256, 0, s)(lists + m, cls + 1, out->offsets, out->indices,
                                                      out->dist2);
         SNN_LAUNCH(k_seg_sort_w8, wgrid, 256, 0, s)(lists + 4 * m, cls + 5, out->offsets,

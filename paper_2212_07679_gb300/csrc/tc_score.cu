@@ -478,14 +478,16 @@ __device__ __forceinline__ uint16_t bf16_bits(__nv_bfloat16 v) {
     return __bfloat16_as_ushort(v);
 }
 
-// Three BF16 parts of an FP64 value, |w - w1 - w2 - w3| <= 2^-23 |w|.
+// Three BF16 parts of a value w given in FP64: w is rounded once to FP32
+// (error <= 2^-24 |w|), then split exactly in FP32 (each remainder is exact,
+// the last part leaves <= 2^-24 |w|): |w - w1 - w2 - w3| <= 2^-23 |w|.
 __device__ __forceinline__ void split3(double w, uint16_t (&o)[3]) {
-    double r = w;
+    float r = (float)w;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        const __nv_bfloat16 b = __float2bfloat16_rn((float)r);
+        const __nv_bfloat16 b = __float2bfloat16_rn(r);
         o[i] = bf16_bits(b);
-        r = r - (double)__bfloat162float(b);
+        r = r - __bfloat162float(b);
     }
 }
 
