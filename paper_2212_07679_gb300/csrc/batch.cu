@@ -1,0 +1,670 @@
+// Many independent (index, queries, radius) problems of uneven n, d and m in
+// one call.  All sets share one pipeline: a composite-key sort of every
+// out-of-sample query by (set, score), one band computation over the global
+// list of query tiles, ONE persistent scoring launch driven by a device work
+// counter over (set, tile, band chunk) items, one exact-decision pass, one
+// CSR build whose per-set slices are the per-set results.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "index_struct.cuh"
+#include "query_kernels.cuh"
+
+namespace snn {
+
+snn_status register_block(void *block, void *const *ptrs, int count);
+
+namespace {
+
+__device__ __forceinline__ int find_set(const int64_t *__restrict__ off, int nsets, int64_t g) {
+    int lo = 0, hi = nsets;   // last s with off[s] <= g
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= g) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+struct OosDesc {
+    const float *Q;        // caller's queries
+    int64_t ldq;
+    const double *mu64;
+    const float *v32;
+    int d, dp;
+    int set;               // batch set number
+    int64_t elem_off;      // offset of this set's rows in the concatenated arrays (floats)
+};
+
+// Projection of every out-of-sample query: key = (set rank << 32) | score key.
+__global__ void k_b_project(const OosDesc *__restrict__ od, const int64_t *__restrict__ ooff,
+                            int noos, int64_t total, uint64_t *__restrict__ keys,
+                            uint32_t *__restrict__ vals, float *__restrict__ eps,
+                            int *__restrict__ bad) {
+    const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const int r = find_set(ooff, noos, g);
+    const OosDesc &o = od[r];
+    const float *q = o.Q + (g - ooff[r]) * o.ldq;
+    float a = 0.f, b = 0.f;
+    int badl = 0;
+    for (int k = 0; k < o.d; ++k) {
+        const float p = q[k];
+        badl |= !isfinite(p);
+        const float x = (float)((double)p - o.mu64[k]);
+        a = fmaf(x, o.v32[k], a);
+        b = fmaf(fabsf(x), fabsf(o.v32[k]), b);
+    }
+    keys[g] = (uint64_t(r) << 32) | uint64_t(float_to_key(a));
+    vals[g] = uint32_t(g);
+    atomic_max_nonneg(&eps[r], (float)(o.d + 4) * kU32 * 1.01f * b + 1e-37f);
+    if (badl) atomicOr(bad, 1);
+}
+
+// Sorted position p (within the set's contiguous range) takes query vals[p].
+__global__ void k_b_gather(const OosDesc *__restrict__ od, const int64_t *__restrict__ ooff,
+                           int noos, int64_t total, const uint64_t *__restrict__ keys,
+                           const uint32_t *__restrict__ vals, float *__restrict__ q_alpha,
+                           int32_t *__restrict__ q_order, float *__restrict__ q_raw,
+                           float *__restrict__ q_xc, float *__restrict__ q_hx,
+                           float *__restrict__ q_nrm) {
+    const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (p >= total) return;
+    const int r = int(keys[p] >> 32);
+    const OosDesc &o = od[r];
+    const int64_t g = vals[p];
+    const int64_t local_row = g - ooff[r];
+    const int64_t local_pos = p - ooff[r];
+    const float *q = o.Q + local_row * o.ldq;
+    float *raw = q_raw + o.elem_off + local_pos * o.dp;
+    float *xc = q_xc + o.elem_off + local_pos * o.dp;
+    float s = 0.f;
+    for (int k = 0; k < o.dp; ++k) {
+        float pv = 0.f, x = 0.f;
+        if (k < o.d) {
+            pv = q[k];
+            x = (float)((double)pv - o.mu64[k]);
+        }
+        raw[k] = pv;
+        xc[k] = x;
+        s = fmaf(x, x, s);
+    }
+    q_alpha[p] = key_to_float(uint32_t(keys[p] & 0xffffffffu));
+    q_order[p] = int32_t(local_row);
+    q_hx[p] = 0.5f * s;
+    q_nrm[p] = sqrtf(s) * (1.f + (float)(o.d + 4) * kU32);
+}
+
+__global__ void k_b_qset(const int64_t *__restrict__ qglob, int nsets, int64_t total,
+                         int32_t *__restrict__ qset) {
+    const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g < total) qset[g] = find_set(qglob, nsets, g);
+}
+
+__global__ void k_b_tileset(const int64_t *__restrict__ tile0, int nsets, int64_t ntiles,
+                            int32_t *__restrict__ tile_set) {
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t < ntiles) tile_set[t] = find_set(tile0, nsets, t);
+}
+
+// Threshold constant of every global query (as k_query_consts, per set).
+__global__ void k_b_consts(const SetDesc *__restrict__ sets, const int32_t *__restrict__ qset,
+                           int64_t total, float *__restrict__ thrA) {
+    const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const SetDesc &sd = sets[qset[g]];
+    const int64_t i = g - sd.q_glob;
+    const double ei = 1.0001 * (double)kU32 * (double)sd.q_nrm[i];
+    const double r = sd.Rx + sd.e_data + ei;
+    const double hy = (double)sd.q_hx[i];
+    const double hy_low = hy * (1.0 - 1.05 * (sd.d + 2) * (double)kU32);
+    const double a = 0.5 * r * r - hy_low;
+    thrA[g] = __double2float_ru(a + 4.0 * kU64 * (fabs(a) + 0.5 * r * r + hy));
+}
+
+__device__ __forceinline__ int64_t lb_ge(const float *__restrict__ a, int64_t n, double x) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((double)a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+__device__ __forceinline__ int64_t ub_gt(const float *__restrict__ a, int64_t n, double x) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((double)a[mid] <= x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Band of every global tile (as k_tile_band, in the tile's own set).
+__global__ void k_b_band(const SetDesc *__restrict__ sets, const int32_t *__restrict__ tile_set,
+                         int64_t ntiles, int64_t *__restrict__ tile_lo, int64_t *__restrict__ tile_hi,
+                         int64_t *__restrict__ items) {
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const SetDesc &sd = sets[tile_set[t]];
+    const int64_t q0 = (t - sd.tile0) * kBQ;
+    const int64_t q1 = min(sd.m, q0 + kBQ) - 1;
+    const double W = sd.Wbase + (double)*sd.eps_d + (double)*sd.eps_q;
+    const double a0 = (double)sd.q_alpha[q0], a1 = (double)sd.q_alpha[q1];
+    const double lo_x = (a0 - W) - 4.0 * kU64 * (fabs(a0) + W);
+    const double hi_x = (a1 + W) + 4.0 * kU64 * (fabs(a1) + W);
+    const int64_t lo = sd.sym ? q0 : lb_ge(sd.x_alpha, sd.n, lo_x);
+    const int64_t hi = max(lo, ub_gt(sd.x_alpha, sd.n, hi_x));
+    tile_lo[t] = lo;
+    tile_hi[t] = hi;
+    items[t] = cdiv(cdiv(hi - lo, kBR), kChunksPerItem);
+}
+
+__device__ __forceinline__ void two_sum_b(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    const float ap = __fsub_rn(s, bp);
+    e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
+// Exact decision of every survivor (same arithmetic as k_decide_*), with the
+// set looked up from the global query number.  rec_pos[s] / rec_pos[N + s]:
+// slot of the pair in its (global) row / in the mirrored row, or -1.
+__global__ void __launch_bounds__(256)
+k_b_decide(const uint2 *__restrict__ surv, int64_t nsurv, const SetDesc *__restrict__ sets,
+           const int32_t *__restrict__ qset, float *__restrict__ rec_d2,
+           int32_t *__restrict__ rec_pos, int32_t *__restrict__ counts) {
+    const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (s >= nsurv) return;
+    const uint2 e = surv[s];
+    const SetDesc &sd = sets[qset[e.x]];
+    const int64_t ql = int64_t(e.x) - sd.q_glob;
+    const int d = sd.d, dp = sd.dp;
+    const float4 *pq = reinterpret_cast<const float4 *>(sd.q_raw + ql * dp);
+    const float4 *pp = reinterpret_cast<const float4 *>(sd.x_raw + int64_t(e.y) * dp);
+    float H = 0.f, L = 0.f;
+    for (int k4 = 0; k4 < dp / 4; ++k4) {
+        const float4 a = pp[k4], b = pq[k4];
+        const float av[4] = {a.x, a.y, a.z, a.w};
+        const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (k4 * 4 + c < d) {
+                float sd_, ed;
+                two_sum_b(av[c], -bv[c], sd_, ed);
+                const float ph = __fmul_rn(sd_, sd_);
+                const float pl = __fmaf_rn(sd_, sd_, -ph);
+                const float cc = __fmaf_rn(__fadd_rn(sd_, sd_), ed, pl);
+                float s1, t1;
+                two_sum_b(H, ph, s1, t1);
+                const float t3 = __fadd_rn(__fadd_rn(t1, L), cc);
+                H = __fadd_rn(s1, t3);
+                L = __fsub_rn(t3, __fsub_rn(H, s1));
+            }
+        }
+    }
+    const double S_df = (double)H + (double)L;
+    const double rel = ((7.0 * d + 6.0) * 0x1p-48 + (d + 3.0) * 0x1p-53) * 1.01;
+    const double tol = rel * S_df + (double)d * 0x1p-140;
+    const double R2 = sd.R2;
+    bool fallback = !(H < 0x1p100f) || !(H >= 0.f);
+    bool accept = false;
+    float d2 = H;
+    if (!fallback) {
+        if (S_df + tol < R2) accept = true;
+        else if (S_df - tol > R2) accept = false;
+        else fallback = true;
+        if (accept && !fallback && H > 0.f) {
+            const float up = __uint_as_float(__float_as_uint(H) + 1u);
+            const float dn = __uint_as_float(__float_as_uint(H) - 1u);
+            const double half_up = 0.5 * ((double)up - (double)H);
+            const double half_dn = 0.5 * ((double)H - (double)dn);
+            const double room = L >= 0.f ? half_up - (double)L : half_dn + (double)L;
+            if (room <= tol) fallback = true;
+        }
+    }
+    if (fallback) {
+        double S = 0.0;
+        for (int k = 0; k < d; ++k) {
+            const double t = __dsub_rn((double)sd.x_raw[int64_t(e.y) * dp + k],
+                                       (double)sd.q_raw[ql * dp + k]);
+            S = __dadd_rn(S, __dmul_rn(t, t));
+        }
+        accept = S <= R2;
+        d2 = (float)S;
+    }
+    int32_t p0 = -1, p1 = -1;
+    if (accept) {
+        const int64_t row = sd.q_glob + sd.q_order[ql];
+        p0 = atomicAdd(&counts[row], 1);
+        if (sd.sym && int64_t(e.y) != ql) p1 = atomicAdd(&counts[sd.q_glob + sd.x_order[e.y]], 1);
+    }
+    rec_d2[s] = d2;
+    rec_pos[s] = p0;
+    rec_pos[nsurv + s] = p1;
+}
+
+__global__ void k_b_scatter(const uint2 *__restrict__ surv, int64_t nsurv,
+                            const SetDesc *__restrict__ sets, const int32_t *__restrict__ qset,
+                            const float *__restrict__ rec_d2, const int32_t *__restrict__ rec_pos,
+                            const int64_t *__restrict__ offsets, int32_t *__restrict__ idx,
+                            float *__restrict__ d2) {
+    const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (s >= nsurv) return;
+    const int32_t p0 = rec_pos[s];
+    if (p0 < 0) return;
+    const uint2 e = surv[s];
+    const SetDesc &sd = sets[qset[e.x]];
+    const int64_t ql = int64_t(e.x) - sd.q_glob;
+    const int32_t qrow = sd.q_order[ql], col = sd.x_order[e.y];
+    const float v = rec_d2[s];
+    const int64_t o = offsets[sd.q_glob + qrow] + p0;
+    idx[o] = col;
+    d2[o] = v;
+    const int32_t p1 = rec_pos[nsurv + s];
+    if (p1 >= 0) {
+        const int64_t o1 = offsets[sd.q_glob + col] + p1;
+        idx[o1] = qrow;
+        d2[o1] = v;
+    }
+}
+
+// Per-set offsets, rebased to start at 0, into the output block: entry
+// g - qglob[s] of set s for every global query g, then each set's end entry.
+__global__ void k_b_offsets(const int64_t *__restrict__ goff, const int64_t *__restrict__ qglob,
+                            int nsets, int64_t total, int64_t *__restrict__ out_off,
+                            const int64_t *__restrict__ out_off_pos) {
+    const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const int s = find_set(qglob, nsets, g);
+    out_off[out_off_pos[s] + (g - qglob[s])] = goff[g] - goff[qglob[s]];
+}
+
+__global__ void k_b_offsets_end(const int64_t *__restrict__ goff, const int64_t *__restrict__ qglob,
+                                int nsets, int64_t *__restrict__ out_off,
+                                const int64_t *__restrict__ out_off_pos) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsets) return;
+    out_off[out_off_pos[s] + (qglob[s + 1] - qglob[s])] = goff[qglob[s + 1]] - goff[qglob[s]];
+}
+
+}  // namespace
+
+// Host side of snn_query_radius_batch.
+snn_status batch_query(int32_t nsets, const snn_index *const *idx, const float *const *Q,
+                       const int64_t *m_in, const int64_t *ldq_in, const double *R_in,
+                       cudaStream_t s, snn_csr *out) {
+    for (int32_t t = 0; t < nsets; ++t) std::memset(&out[t], 0, sizeof(out[t]));
+    if (nsets == 0) return SNN_OK;
+    // ------------------------------------------------------- host plan
+    std::vector<SetDesc> sd(nsets);
+    std::vector<int64_t> qglob(nsets + 1, 0), tile0(nsets + 1, 0);
+    std::vector<OosDesc> od;
+    std::vector<int64_t> ooff(1, 0);
+    std::vector<int> oos_of(nsets, -1);
+    int64_t oos_elems = 0;
+    for (int32_t t = 0; t < nsets; ++t) {
+        const snn_index *ix = idx[t];
+        if (!ix) { set_error("set %d: index is NULL", t); return SNN_EINVAL; }
+        if (!(R_in[t] >= 0.0) || !std::isfinite(R_in[t])) {
+            set_error("set %d: R must be finite and >= 0", t);
+            return SNN_EINVAL;
+        }
+        const bool self = Q[t] == nullptr;
+        const int64_t m = self ? ix->n : m_in[t];
+        if (!self && (m < 0 || m >= (int64_t(1) << 31))) {
+            set_error("set %d: m must be in [0, 2^31)", t);
+            return SNN_EINVAL;
+        }
+        if (!self && m > 0 && ldq_in[t] < ix->d) { set_error("set %d: ldq must be >= d", t); return SNN_EINVAL; }
+        SetDesc &d = sd[t];
+        std::memset(&d, 0, sizeof(d));
+        d.m = m;
+        d.n = ix->n;
+        d.d = ix->d;
+        d.dp = ix->dp;
+        d.sym = self ? 1 : 0;
+        d.c1 = (float)((2.0 * ix->d + 4.0) * (double)kU32 * 1.05);
+        d.q_glob = qglob[t];
+        d.tile0 = tile0[t];
+        d.R2 = R_in[t] * R_in[t];
+        d.Rx = R_in[t] * (1.0 + (ix->d + 8) * 0x1p-52);
+        d.Wbase = d.Rx * (1.0 + (ix->d + 4) * 0x1p-52) * (1.0 + 0x1p-30);
+        d.e_data = 1.0001 * (double)kU32 * (double)ix->nrm_max;
+        d.x_alpha = ix->alpha;
+        d.x_raw = ix->praw;
+        d.x_xc = ix->xc;
+        d.x_hx = ix->hx;
+        d.x_nrm = ix->nrm;
+        d.x_order = ix->order;
+        d.eps_d = ix->dconst;
+        if (self) {
+            d.q_alpha = ix->alpha;
+            d.q_raw = ix->praw;
+            d.q_xc = ix->xc;
+            d.q_hx = ix->hx;
+            d.q_nrm = ix->nrm;
+            d.q_order = ix->order;
+            d.eps_q = ix->dconst;
+        } else if (m > 0) {
+            OosDesc o;
+            o.Q = Q[t];
+            o.ldq = ldq_in[t];
+            o.mu64 = ix->mu64;
+            o.v32 = ix->v32;
+            o.d = ix->d;
+            o.dp = ix->dp;
+            o.set = t;
+            o.elem_off = oos_elems;
+            oos_of[t] = int(od.size());
+            od.push_back(o);
+            ooff.push_back(ooff.back() + m);
+            oos_elems += m * ix->dp;
+        }
+        qglob[t + 1] = qglob[t] + m;
+        tile0[t + 1] = tile0[t] + cdiv(m, kBQ);
+    }
+    const int64_t M = qglob[nsets];
+    const int64_t ntiles = tile0[nsets];
+    const int noos = int(od.size());
+    const int64_t Moos = ooff.back();
+
+    Scratch scr(s);
+    std::vector<void *> to_free;
+    // ------------------------------------------- out-of-sample query prep
+    float *q_alpha = nullptr, *q_raw = nullptr, *q_xc = nullptr, *q_hx = nullptr, *q_nrm = nullptr;
+    int32_t *q_order = nullptr;
+    float *oeps = nullptr;
+    int *bad = nullptr;
+    SNN_TRY(scr.alloc(&bad, 1));
+    SNN_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    if (noos > 0) {
+        OosDesc *d_od;
+        int64_t *d_ooff;
+        uint64_t *keys, *keys_alt;
+        uint32_t *vals, *vals_alt;
+        SNN_TRY(scr.alloc(&d_od, noos));
+        SNN_TRY(scr.alloc(&d_ooff, noos + 1));
+        SNN_TRY(scr.alloc(&oeps, noos));
+        SNN_TRY(scr.alloc(&keys, Moos));
+        SNN_TRY(scr.alloc(&keys_alt, Moos));
+        SNN_TRY(scr.alloc(&vals, Moos));
+        SNN_TRY(scr.alloc(&vals_alt, Moos));
+        SNN_TRY(scr.alloc(&q_alpha, Moos));
+        SNN_TRY(scr.alloc(&q_order, Moos));
+        SNN_TRY(scr.alloc(&q_hx, Moos));
+        SNN_TRY(scr.alloc(&q_nrm, Moos));
+        SNN_TRY(scr.alloc(&q_raw, oos_elems));
+        SNN_TRY(scr.alloc(&q_xc, oos_elems));
+        SNN_CUDA(cudaMemcpyAsync(d_od, od.data(), noos * sizeof(OosDesc), cudaMemcpyHostToDevice, s));
+        SNN_CUDA(cudaMemcpyAsync(d_ooff, ooff.data(), (noos + 1) * sizeof(int64_t),
+                                 cudaMemcpyHostToDevice, s));
+        SNN_CUDA(cudaMemsetAsync(oeps, 0, noos * sizeof(float), s));
+        SNN_LAUNCH(k_b_project, unsigned(cdiv(Moos, 256)), 256, 0, s)(d_od, d_ooff, noos, Moos, keys,
+                                                                      vals, oeps, bad);
+        SNN_LAUNCH_CHECK();
+        int bits = 32;
+        while ((int64_t(1) << (bits - 32)) < noos) ++bits;
+        SNN_TRY(radix_sort_pairs<uint64_t>(keys, vals, keys_alt, vals_alt, Moos, bits, s));
+        SNN_LAUNCH(k_b_gather, unsigned(cdiv(Moos, 256)), 256, 0, s)(
+            d_od, d_ooff, noos, Moos, keys, vals, q_alpha, q_order, q_raw, q_xc, q_hx, q_nrm);
+        SNN_LAUNCH_CHECK();
+        for (int32_t t = 0; t < nsets; ++t) {
+            const int r = oos_of[t];
+            if (r < 0) continue;
+            SetDesc &d = sd[t];
+            d.q_alpha = q_alpha + ooff[r];
+            d.q_order = q_order + ooff[r];
+            d.q_hx = q_hx + ooff[r];
+            d.q_nrm = q_nrm + ooff[r];
+            d.q_raw = q_raw + od[r].elem_off;
+            d.q_xc = q_xc + od[r].elem_off;
+            d.eps_q = oeps + r;
+        }
+    }
+    // sets with m == 0 and no self-join keep NULL query arrays; they own no tiles
+    SetDesc *d_sets;
+    int64_t *d_qglob, *d_tile0;
+    SNN_TRY(scr.alloc(&d_sets, nsets));
+    SNN_TRY(scr.alloc(&d_qglob, nsets + 1));
+    SNN_TRY(scr.alloc(&d_tile0, nsets + 1));
+    SNN_CUDA(cudaMemcpyAsync(d_sets, sd.data(), nsets * sizeof(SetDesc), cudaMemcpyHostToDevice, s));
+    SNN_CUDA(cudaMemcpyAsync(d_qglob, qglob.data(), (nsets + 1) * sizeof(int64_t),
+                             cudaMemcpyHostToDevice, s));
+    SNN_CUDA(cudaMemcpyAsync(d_tile0, tile0.data(), (nsets + 1) * sizeof(int64_t),
+                             cudaMemcpyHostToDevice, s));
+
+    // ------------------------------------------------ thresholds, bands
+    int32_t *qset, *tile_set;
+    float *thrA;
+    int64_t *tile_lo, *tile_hi, *items, *item_off;
+    unsigned long long *ctr;
+    SNN_TRY(scr.alloc(&qset, M));
+    SNN_TRY(scr.alloc(&thrA, M));
+    SNN_TRY(scr.alloc(&tile_set, ntiles));
+    SNN_TRY(scr.alloc(&tile_lo, ntiles));
+    SNN_TRY(scr.alloc(&tile_hi, ntiles));
+    SNN_TRY(scr.alloc(&items, ntiles));
+    SNN_TRY(scr.alloc(&item_off, ntiles + 1));
+    SNN_TRY(scr.alloc(&ctr, 4));
+    SNN_CUDA(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), s));
+    if (M > 0) {
+        SNN_LAUNCH(k_b_qset, unsigned(cdiv(M, 256)), 256, 0, s)(d_qglob, nsets, M, qset);
+        SNN_LAUNCH(k_b_consts, unsigned(cdiv(M, 256)), 256, 0, s)(d_sets, qset, M, thrA);
+        SNN_LAUNCH(k_b_tileset, unsigned(cdiv(ntiles, 256)), 256, 0, s)(d_tile0, nsets, ntiles,
+                                                                         tile_set);
+        SNN_LAUNCH(k_b_band, unsigned(cdiv(ntiles, 128)), 128, 0, s)(d_sets, tile_set, ntiles,
+                                                                     tile_lo, tile_hi, items);
+        SNN_LAUNCH_CHECK();
+    }
+    SNN_TRY(scan_exclusive<int64_t>(items, item_off, ntiles, s));
+    int64_t max_items = 0;
+    for (int32_t t = 0; t < nsets; ++t)
+        max_items += cdiv(sd[t].m, kBQ) * (cdiv(sd[t].n, int64_t(kBR) * kChunksPerItem) + 1);
+    int32_t *item_tile;
+    SNN_TRY(scr.alloc(&item_tile, std::max<int64_t>(max_items, 1)));
+    if (ntiles > 0) {
+        SNN_LAUNCH(k_item_tiles, unsigned(cdiv(ntiles, 128)), 128, 0, s)(item_off, int(ntiles),
+                                                                          item_tile);
+        SNN_LAUNCH_CHECK();
+    }
+
+    // ------------------------------------- one persistent scoring launch
+    int64_t cap = std::max<int64_t>(int64_t(1) << 20, 64 * M + 4096);
+    uint2 *surv = nullptr;
+    SNN_TRY(scr.alloc(&surv, cap));
+    BatchScoreArgs ba;
+    ba.sets = d_sets;
+    ba.tile_set = tile_set;
+    ba.thrA = thrA;
+    ba.tile_lo = tile_lo;
+    ba.tile_hi = tile_hi;
+    ba.item_off = item_off;
+    ba.item_tile = item_tile;
+    ba.ntiles = int(ntiles);
+    ba.count = ctr;
+    ba.work = ctr + 1;
+    unsigned long long hctr[2] = {0, 0};
+    int hbad = 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        ba.surv = surv;
+        ba.cap = cap;
+        if (ntiles > 0) {
+            SNN_LAUNCH(k_score_fp32_batch, device_sm_count() * 2, 256, 0, s)(ba);
+            SNN_LAUNCH_CHECK();
+        }
+        SNN_CUDA(cudaMemcpyAsync(hctr, ctr, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        SNN_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SNN_CUDA(cudaStreamSynchronize(s));
+        if (hbad) { set_error("a query set contains NaN or Inf"); return SNN_EINVAL; }
+        if ((int64_t)hctr[0] <= cap) break;
+        if (attempt == 1) { set_error("survivor buffer overflow after retry"); return SNN_EOVERFLOW; }
+        cap = (int64_t)hctr[0] + 1024;
+        SNN_TRY(scr.alloc(&surv, cap));
+        SNN_CUDA(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long), s));
+    }
+    const int64_t nsurv = (int64_t)hctr[0];
+
+    // ------------------------------------------------- exact decision
+    float *rec_d2;
+    int32_t *rec_pos, *counts;
+    int64_t *counts64, *goff;
+    SNN_TRY(scr.alloc(&rec_d2, nsurv));
+    SNN_TRY(scr.alloc(&rec_pos, 2 * nsurv));
+    SNN_TRY(scr.alloc(&counts, M));
+    SNN_TRY(scr.alloc(&counts64, M));
+    SNN_TRY(scr.alloc(&goff, M + 1));
+    SNN_CUDA(cudaMemsetAsync(counts, 0, std::max<int64_t>(M, 1) * sizeof(int32_t), s));
+    if (nsurv > 0) {
+        SNN_LAUNCH(k_b_decide, unsigned(cdiv(nsurv, 256)), 256, 0, s)(surv, nsurv, d_sets, qset,
+                                                                      rec_d2, rec_pos, counts);
+        SNN_LAUNCH_CHECK();
+    }
+    if (M > 0) {
+        SNN_LAUNCH(k_counts_to_i64, unsigned(cdiv(M, 256)), 256, 0, s)(counts, M, counts64);
+        SNN_LAUNCH_CHECK();
+    }
+    SNN_TRY(scan_exclusive<int64_t>(counts64, goff, M, s));
+    int64_t nnz = 0;
+    SNN_CUDA(cudaMemcpyAsync(&nnz, goff + M, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaStreamSynchronize(s));
+    if (nnz >= (int64_t(1) << 31)) {
+        set_error("%lld neighbour pairs exceed this build's limit of 2^31-1", (long long)nnz);
+        return SNN_ENOTSUP;
+    }
+    // nnz of every set
+    std::vector<int64_t> hgoff_set(nsets + 1);
+    {
+        int64_t *tmp;
+        SNN_TRY(scr.alloc(&tmp, nsets + 1));
+        for (int32_t t = 0; t <= nsets; ++t)
+            SNN_CUDA(cudaMemcpyAsync(tmp + t, goff + qglob[t], sizeof(int64_t),
+                                     cudaMemcpyDeviceToDevice, s));
+        SNN_CUDA(cudaMemcpyAsync(hgoff_set.data(), tmp, (nsets + 1) * sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, s));
+        SNN_CUDA(cudaStreamSynchronize(s));
+    }
+
+    // ---------------------------- one output block, per-set slices of it
+    std::vector<int64_t> off_pos(nsets);
+    int64_t off_words = 0;
+    for (int32_t t = 0; t < nsets; ++t) {
+        off_pos[t] = off_words;
+        off_words += (sd[t].m + 1 + 31) & ~int64_t(31);   // 256-byte aligned slices
+    }
+    const size_t idx_bytes = ((size_t(nnz) * 4 + 255) & ~size_t(255));
+    const size_t bytes = size_t(off_words) * 8 + 2 * std::max<size_t>(idx_bytes, 256);
+    char *block = nullptr;
+    {
+        cudaError_t e = cudaMalloc(&block, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("output allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+            return SNN_ENOMEM;
+        }
+    }
+    int64_t *out_off = reinterpret_cast<int64_t *>(block);
+    int32_t *gidx = reinterpret_cast<int32_t *>(block + size_t(off_words) * 8);
+    float *gd2 = reinterpret_cast<float *>(block + size_t(off_words) * 8 + std::max<size_t>(idx_bytes, 256));
+    int64_t *d_offpos;
+    snn_status st = scr.alloc(&d_offpos, nsets);
+    auto fail = [&](snn_status code) {
+        cudaStreamSynchronize(s);
+        cudaFree(block);
+        return code;
+    };
+    if (st != SNN_OK) return fail(st);
+    if (cudaMemcpyAsync(d_offpos, off_pos.data(), nsets * sizeof(int64_t), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess) {
+        set_error("offset table upload failed");
+        return fail(SNN_ECUDA);
+    }
+    if (M > 0)
+        SNN_LAUNCH(k_b_offsets, unsigned(cdiv(M, 256)), 256, 0, s)(goff, d_qglob, nsets, M, out_off,
+                                                                   d_offpos);
+    SNN_LAUNCH(k_b_offsets_end, unsigned(cdiv(nsets, 128)), 128, 0, s)(goff, d_qglob, nsets, out_off,
+                                                                       d_offpos);
+    if (nsurv > 0 && nnz > 0) {
+        SNN_LAUNCH(k_b_scatter, unsigned(cdiv(nsurv, 256)), 256, 0, s)(
+            surv, nsurv, d_sets, qset, rec_d2, rec_pos, goff, gidx, gd2);
+        // per-row ascending ids over the global CSR (rows of every set)
+        int32_t *lists, *big_list;
+        int64_t *big_len, *toff;
+        unsigned *cls;
+        st = scr.alloc(&lists, 6 * M);
+        if (st == SNN_OK) st = scr.alloc(&big_list, M);
+        if (st == SNN_OK) st = scr.alloc(&big_len, M);
+        if (st == SNN_OK) st = scr.alloc(&toff, M + 1);
+        if (st == SNN_OK) st = scr.alloc(&cls, 8);
+        if (st != SNN_OK) return fail(st);
+        cudaMemsetAsync(cls, 0, 8 * sizeof(unsigned), s);
+        SNN_LAUNCH(k_seg_classify, unsigned(cdiv(M, 256)), 256, 0, s)(goff, M, lists, big_list,
+                                                                      big_len, cls);
+        const unsigned wgrid = std::min<unsigned>(unsigned(cdiv(M * 32, 256)), 16384);
+        SNN_LAUNCH(k_seg_sort_w1, wgrid, 256, 0, s)(lists, cls, goff, gidx, gd2);
+        SNN_LAUNCH(k_seg_sort_w2, wgrid, 256, 0, s)(lists + 5 * M, cls + 6, goff, gidx, gd2);
+        SNN_LAUNCH(k_seg_sort_w4, wgrid, 256, 0, s)(lists + M, cls + 1, goff, gidx, gd2);
+        SNN_LAUNCH(k_seg_sort_w8, wgrid, 256, 0, s)(lists + 4 * M, cls + 5, goff, gidx, gd2);
+        SNN_LAUNCH(k_seg_sort_w16, wgrid, 256, 0, s)(lists + 2 * M, cls + 2, goff, gidx, gd2);
+        SNN_LAUNCH(k_seg_sort_mid, std::min<unsigned>(unsigned(M), 4096), 256, 0, s)(
+            lists + 3 * M, cls + 3, goff, gidx, gd2);
+        unsigned hcls[8];
+        if (cudaMemcpyAsync(hcls, cls, sizeof(hcls), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            set_error("batched CSR build failed: %s", cudaGetErrorString(cudaGetLastError()));
+            return fail(SNN_ECUDA);
+        }
+        const int nbig = int(hcls[4]);
+        if (nbig > 0) {
+            // rows longer than 4096 entries: radix sort of (row rank, id)
+            if ((st = scan_exclusive<int64_t>(big_len, toff, nbig, s)) != SNN_OK) return fail(st);
+            int64_t tot = 0;
+            cudaMemcpyAsync(&tot, toff + nbig, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+            cudaStreamSynchronize(s);
+            uint64_t *bk, *bka;
+            uint32_t *bv, *bva;
+            float *bd2;
+            st = scr.alloc(&bk, tot);
+            if (st == SNN_OK) st = scr.alloc(&bka, tot);
+            if (st == SNN_OK) st = scr.alloc(&bv, tot);
+            if (st == SNN_OK) st = scr.alloc(&bva, tot);
+            if (st == SNN_OK) st = scr.alloc(&bd2, tot);
+            if (st != SNN_OK) return fail(st);
+            SNN_LAUNCH(k_seg_big_gather, nbig, 256, 0, s)(big_list, nbig, goff, toff, gidx, gd2, bk,
+                                                          bv, bd2);
+            int bits = 32;
+            while ((int64_t(1) << (bits - 32)) < nbig) ++bits;
+            if ((st = radix_sort_pairs<uint64_t>(bk, bv, bka, bva, tot, bits, s)) != SNN_OK)
+                return fail(st);
+            SNN_LAUNCH(k_seg_big_scatter, unsigned(cdiv(tot, 256)), 256, 0, s)(
+                bk, bv, tot, big_list, goff, toff, bd2, gidx, gd2);
+        }
+    }
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("batched CSR build failed");
+        return fail(SNN_ECUDA);
+    }
+    // hand out the slices; the block is freed when every slice was freed
+    std::vector<void *> ptrs;
+    for (int32_t t = 0; t < nsets; ++t) {
+        const int64_t nz = hgoff_set[t + 1] - hgoff_set[t];
+        out[t].m = sd[t].m;
+        out[t].nnz = nz;
+        out[t].offsets = out_off + off_pos[t];
+        out[t].indices = nz > 0 ? gidx + hgoff_set[t] : nullptr;
+        out[t].dist2 = nz > 0 ? gd2 + hgoff_set[t] : nullptr;
+        ptrs.push_back(out[t].offsets);
+        if (nz > 0) {
+            ptrs.push_back(out[t].indices);
+            ptrs.push_back(out[t].dist2);
+        }
+    }
+    st = register_block(block, ptrs.data(), int(ptrs.size()));
+    if (st != SNN_OK) {
+        for (int32_t t = 0; t < nsets; ++t) std::memset(&out[t], 0, sizeof(out[t]));
+        return fail(st);
+    }
+    return SNN_OK;
+}
+
+}  // namespace snn

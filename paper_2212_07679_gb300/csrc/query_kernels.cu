@@ -115,172 +115,231 @@ constexpr int kKC = 16;
 constexpr int kScoreThreads = 256;
 
 template <bool kSingle>
-__device__ __forceinline__ void score_body(const ScoreArgs &a) {
+__device__ __forceinline__ void score_item(const ScoreJob &jb, float c1, uint2 *__restrict__ surv,
+                                           int64_t cap, unsigned long long *__restrict__ count) {
     __shared__ __align__(16) float Qs[kKC][kBQ + 4];
     __shared__ __align__(16) float Xs[kKC][kBR + 4];
     __shared__ float s_thrA[kBQ], s_qn[kBQ];
     __shared__ float s_hx[kBR];
     __shared__ unsigned s_hxmax, s_nmax;
-    __shared__ long long s_item;
 
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const int lane = tid & 31;
-    const int dp = a.x.dp;
-    const int64_t total_items = a.item_off[a.ntiles];
+    const int dp = jb.dp;
+    const int64_t q0 = jb.q0;
+    const int64_t band_lo = jb.band_lo, band_hi = jb.band_hi;
 
-    for (;;) {
-        __syncthreads();
-        if (tid == 0) s_item = (long long)atomicAdd(a.work, 1ull);
-        __syncthreads();
-        const int64_t item = s_item;
-        if (item >= total_items) break;
-        const int tile = a.item_tile[item];
-        const int64_t q0 = int64_t(tile) * kBQ;
-        const int64_t band_lo = a.tile_lo[tile], band_hi = a.tile_hi[tile];
-        const int64_t c_first = (item - a.item_off[tile]) * kChunksPerItem;
-        const int64_t c_end = min(cdiv(band_hi - band_lo, kBR), c_first + kChunksPerItem);
-
-        if (tid < kBQ) {
-            const int64_t q = q0 + tid;
-            s_thrA[tid] = q < a.q.m ? a.thrA[q] : -3.0e38f;   // never survives
-            s_qn[tid] = q < a.q.m ? a.q.nrm[q] : 0.f;
+    __syncthreads();
+    if (tid < kBQ) {
+        const int64_t q = q0 + tid;
+        s_thrA[tid] = q < jb.m ? jb.thrA[q] : -3.0e38f;   // never survives
+        s_qn[tid] = q < jb.m ? jb.qnrm[q] : 0.f;
+    }
+    if (kSingle) {
+        // whole query rows fit one k-chunk: stage them once per item
+        for (int e = tid; e < kBQ * (dp / 4); e += kScoreThreads) {
+            const int r = e / (dp / 4), k4 = e % (dp / 4);
+            const int64_t q = q0 + r;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (q < jb.m) v = *reinterpret_cast<const float4 *>(jb.qxc + q * dp + k4 * 4);
+            Qs[k4 * 4 + 0][r] = v.x;
+            Qs[k4 * 4 + 1][r] = v.y;
+            Qs[k4 * 4 + 2][r] = v.z;
+            Qs[k4 * 4 + 3][r] = v.w;
         }
-        if (kSingle) {
-            // whole query rows fit one k-chunk: stage them once per item
-            for (int e = tid; e < kBQ * (dp / 4); e += kScoreThreads) {
-                const int r = e / (dp / 4), k4 = e % (dp / 4);
-                const int64_t q = q0 + r;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (q < a.q.m) v = *reinterpret_cast<const float4 *>(a.q.xc + q * dp + k4 * 4);
-                Qs[k4 * 4 + 0][r] = v.x;
-                Qs[k4 * 4 + 1][r] = v.y;
-                Qs[k4 * 4 + 2][r] = v.z;
-                Qs[k4 * 4 + 3][r] = v.w;
+    }
+    for (int64_t c = jb.c_first; c < jb.c_end; ++c) {
+        const int64_t j0 = band_lo + c * kBR;
+        __syncthreads();
+        if (tid == 0) { s_hxmax = 0u; s_nmax = 0u; }
+        __syncthreads();
+        if (tid < kBR) {
+            const int64_t j = j0 + tid;
+            float h = 0.f, nr = 0.f;
+            if (j < band_hi) { h = jb.xhx[j]; nr = jb.xnrm[j]; }
+            s_hx[tid] = h;
+            // block max of non-negative floats through their bit patterns
+            unsigned hb = __float_as_uint(h), nb = __float_as_uint(nr);
+            for (int o = 16; o; o >>= 1) {
+                hb = max(hb, __shfl_xor_sync(0xffffffffu, hb, o));
+                nb = max(nb, __shfl_xor_sync(0xffffffffu, nb, o));
             }
+            if (lane == 0) { atomicMax(&s_hxmax, hb); atomicMax(&s_nmax, nb); }
         }
-        for (int64_t c = c_first; c < c_end; ++c) {
-            const int64_t j0 = band_lo + c * kBR;
+        __syncthreads();
+        float acc[8][8];
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const float h = -s_hx[(w < 4 ? 0 : 64) + tx * 4 + (w & 3)];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u][w] = h;
+        }
+        for (int k0 = 0; k0 < dp; k0 += kKC) {
+            const int kc = min(kKC, dp - k0);
             __syncthreads();
-            if (tid == 0) { s_hxmax = 0u; s_nmax = 0u; }
-            __syncthreads();
-            if (tid < kBR) {
-                const int64_t j = j0 + tid;
-                float h = 0.f, nr = 0.f;
-                if (j < band_hi) { h = a.x.hx[j]; nr = a.x.nrm[j]; }
-                s_hx[tid] = h;
-                // block max of non-negative floats through their bit patterns
-                unsigned hb = __float_as_uint(h), nb = __float_as_uint(nr);
-                for (int o = 16; o; o >>= 1) {
-                    hb = max(hb, __shfl_xor_sync(0xffffffffu, hb, o));
-                    nb = max(nb, __shfl_xor_sync(0xffffffffu, nb, o));
+            if (!kSingle) {
+                for (int e = tid; e < kBQ * (kc / 4); e += kScoreThreads) {
+                    const int r = e / (kc / 4), k4 = e % (kc / 4);
+                    const int64_t q = q0 + r;
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (q < jb.m) v = *reinterpret_cast<const float4 *>(jb.qxc + q * dp + k0 + k4 * 4);
+                    Qs[k4 * 4 + 0][r] = v.x;
+                    Qs[k4 * 4 + 1][r] = v.y;
+                    Qs[k4 * 4 + 2][r] = v.z;
+                    Qs[k4 * 4 + 3][r] = v.w;
                 }
-                if (lane == 0) { atomicMax(&s_hxmax, hb); atomicMax(&s_nmax, nb); }
+            }
+            for (int e = tid; e < kBR * (kc / 4); e += kScoreThreads) {
+                const int r = e / (kc / 4), k4 = e % (kc / 4);
+                const int64_t j = j0 + r;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (j < band_hi) v = *reinterpret_cast<const float4 *>(jb.xxc + j * dp + k0 + k4 * 4);
+                Xs[k4 * 4 + 0][r] = v.x;
+                Xs[k4 * 4 + 1][r] = v.y;
+                Xs[k4 * 4 + 2][r] = v.z;
+                Xs[k4 * 4 + 3][r] = v.w;
             }
             __syncthreads();
-            float acc[8][8];
+#pragma unroll 4
+            for (int kk = 0; kk < kc; ++kk) {
+                const float4 qa = *reinterpret_cast<const float4 *>(&Qs[kk][ty * 4]);
+                const float4 qb = *reinterpret_cast<const float4 *>(&Qs[kk][64 + ty * 4]);
+                const float4 xa = *reinterpret_cast<const float4 *>(&Xs[kk][tx * 4]);
+                const float4 xb = *reinterpret_cast<const float4 *>(&Xs[kk][64 + tx * 4]);
+                const float qv[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
+                const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+#pragma unroll
+                    for (int w = 0; w < 8; ++w) acc[u][w] = fmaf(qv[u], xv[w], acc[u][w]);
+            }
+        }
+        // epilogue: survivors
+        const float hxmax = __uint_as_float(s_hxmax), nmax = __uint_as_float(s_nmax);
+        unsigned long long mask = 0ull;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int qi = (u < 4 ? 0 : 64) + ty * 4 + (u & 3);
+            float b = c1 * fmaf(nmax, s_qn[qi], hxmax);
+            b = b * 1.0000010f;
+            float thr = s_thrA[qi] + b;
+            thr = thr + fabsf(thr) * 1e-6f + 1e-30f;
+            const float neg = -thr;
 #pragma unroll
             for (int w = 0; w < 8; ++w) {
-                const float h = -s_hx[(w < 4 ? 0 : 64) + tx * 4 + (w & 3)];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) acc[u][w] = h;
+                const int rj = (w < 4 ? 0 : 64) + tx * 4 + (w & 3);
+                const int64_t jj = j0 + rj;
+                const bool ok = (acc[u][w] >= neg) && (jj < band_hi) &&
+                                (!jb.sym || jj >= q0 + qi);
+                mask |= (unsigned long long)ok << (u * 8 + w);
             }
-            for (int k0 = 0; k0 < dp; k0 += kKC) {
-                const int kc = min(kKC, dp - k0);
-                if (!kSingle) {
-                    __syncthreads();
-                    for (int e = tid; e < kBQ * (kc / 4); e += kScoreThreads) {
-                        const int r = e / (kc / 4), k4 = e % (kc / 4);
-                        const int64_t q = q0 + r;
-                        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (q < a.q.m)
-                            v = *reinterpret_cast<const float4 *>(a.q.xc + q * dp + k0 + k4 * 4);
-                        Qs[k4 * 4 + 0][r] = v.x;
-                        Qs[k4 * 4 + 1][r] = v.y;
-                        Qs[k4 * 4 + 2][r] = v.z;
-                        Qs[k4 * 4 + 3][r] = v.w;
-                    }
-                } else {
-                    __syncthreads();
-                }
-                for (int e = tid; e < kBR * (kc / 4); e += kScoreThreads) {
-                    const int r = e / (kc / 4), k4 = e % (kc / 4);
-                    const int64_t j = j0 + r;
-                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (j < band_hi)
-                        v = *reinterpret_cast<const float4 *>(a.x.xc + j * dp + k0 + k4 * 4);
-                    Xs[k4 * 4 + 0][r] = v.x;
-                    Xs[k4 * 4 + 1][r] = v.y;
-                    Xs[k4 * 4 + 2][r] = v.z;
-                    Xs[k4 * 4 + 3][r] = v.w;
-                }
-                __syncthreads();
-#pragma unroll 4
-                for (int kk = 0; kk < kc; ++kk) {
-                    const float4 qa = *reinterpret_cast<const float4 *>(&Qs[kk][ty * 4]);
-                    const float4 qb = *reinterpret_cast<const float4 *>(&Qs[kk][64 + ty * 4]);
-                    const float4 xa = *reinterpret_cast<const float4 *>(&Xs[kk][tx * 4]);
-                    const float4 xb = *reinterpret_cast<const float4 *>(&Xs[kk][64 + tx * 4]);
-                    const float qv[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
-                    const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
-#pragma unroll
-                    for (int u = 0; u < 8; ++u)
-#pragma unroll
-                        for (int w = 0; w < 8; ++w) acc[u][w] = fmaf(qv[u], xv[w], acc[u][w]);
-                }
+        }
+        const int cnt = __popcll(mask);
+        if (__any_sync(0xffffffffu, cnt != 0)) {
+            int incl = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
             }
-            // epilogue: survivors
-            const float hxmax = __uint_as_float(s_hxmax), nmax = __uint_as_float(s_nmax);
-            unsigned long long mask = 0ull;
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            const int wtotal = __shfl_sync(0xffffffffu, incl, 31);
+            unsigned long long base = 0;
+            if (lane == 31) base = atomicAdd(count, (unsigned long long)wtotal);
+            base = __shfl_sync(0xffffffffu, base, 31);
+            unsigned long long pos = base + (unsigned long long)(incl - cnt);
+            while (mask) {
+                const int b = __ffsll((long long)mask) - 1;
+                mask &= mask - 1;
+                const int u = b >> 3, w = b & 7;
                 const int qi = (u < 4 ? 0 : 64) + ty * 4 + (u & 3);
-                float b = a.c1 * fmaf(nmax, s_qn[qi], hxmax);
-                b = b * 1.0000010f;
-                float thr = s_thrA[qi] + b;
-                thr = thr + fabsf(thr) * 1e-6f + 1e-30f;
-                const float neg = -thr;
-#pragma unroll
-                for (int w = 0; w < 8; ++w) {
-                    const int rj = (w < 4 ? 0 : 64) + tx * 4 + (w & 3);
-                    const int64_t jj = j0 + rj;
-                    const bool ok = (acc[u][w] >= neg) && (jj < band_hi) &&
-                                    (!a.sym || jj >= q0 + qi);
-                    mask |= (unsigned long long)ok << (u * 8 + w);
-                }
-            }
-            const int cnt = __popcll(mask);
-            if (__any_sync(0xffffffffu, cnt != 0)) {
-                int incl = cnt;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                const int wtotal = __shfl_sync(0xffffffffu, incl, 31);
-                unsigned long long base = 0;
-                if (lane == 31) base = atomicAdd(a.count, (unsigned long long)wtotal);
-                base = __shfl_sync(0xffffffffu, base, 31);
-                unsigned long long pos = base + (unsigned long long)(incl - cnt);
-                while (mask) {
-                    const int b = __ffsll((long long)mask) - 1;
-                    mask &= mask - 1;
-                    const int u = b >> 3, w = b & 7;
-                    const int qi = (u < 4 ? 0 : 64) + ty * 4 + (u & 3);
-                    const int rj = (w < 4 ? 0 : 64) + tx * 4 + (w & 3);
-                    if (pos < (unsigned long long)a.cap)
-                        a.surv[pos] = make_uint2((unsigned)(q0 + qi), (unsigned)(j0 + rj));
-                    ++pos;
-                }
+                const int rj = (w < 4 ? 0 : 64) + tx * 4 + (w & 3);
+                if (pos < (unsigned long long)cap)
+                    surv[pos] = make_uint2((unsigned)(jb.q_out + q0 + qi), (unsigned)(j0 + rj));
+                ++pos;
             }
         }
     }
 }
 
+// One work item of a single query set.
+__device__ __forceinline__ ScoreJob single_job(const ScoreArgs &a, int64_t item) {
+    const int tile = a.item_tile[item];
+    ScoreJob jb;
+    jb.m = a.q.m;
+    jb.qxc = a.q.xc;
+    jb.qnrm = a.q.nrm;
+    jb.thrA = a.thrA;
+    jb.xxc = a.x.xc;
+    jb.xhx = a.x.hx;
+    jb.xnrm = a.x.nrm;
+    jb.dp = a.x.dp;
+    jb.sym = a.sym;
+    jb.q0 = int64_t(tile) * kBQ;
+    jb.band_lo = a.tile_lo[tile];
+    jb.band_hi = a.tile_hi[tile];
+    jb.c_first = (item - a.item_off[tile]) * kChunksPerItem;
+    jb.c_end = min(cdiv(jb.band_hi - jb.band_lo, kBR), jb.c_first + kChunksPerItem);
+    jb.q_out = 0;
+    return jb;
+}
+
+template <bool kSingle>
+__device__ __forceinline__ void score_loop(const ScoreArgs &a) {
+    __shared__ long long s_item;
+    const int64_t total_items = a.item_off[a.ntiles];
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(a.work, 1ull);
+        __syncthreads();
+        const int64_t item = s_item;
+        if (item >= total_items) break;
+        score_item<kSingle>(single_job(a, item), a.c1, a.surv, a.cap, a.count);
+    }
+}
+
 __global__ void __launch_bounds__(kScoreThreads, 2) k_score_fp32_single(ScoreArgs a) {
-    score_body<true>(a);
+    score_loop<true>(a);
 }
 __global__ void __launch_bounds__(kScoreThreads, 2) k_score_fp32_multi(ScoreArgs a) {
-    score_body<false>(a);
+    score_loop<false>(a);
+}
+
+// Many query sets in one persistent launch: every work item names a global
+// tile, the tile names its set, and the set descriptor gives that set's
+// arrays, row stride and radius-dependent thresholds.  Survivors carry the
+// global query number (the set's first global query + local sorted query).
+__global__ void __launch_bounds__(kScoreThreads, 2) k_score_fp32_batch(BatchScoreArgs a) {
+    __shared__ long long s_item;
+    const int64_t total_items = a.item_off[a.ntiles];
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(a.work, 1ull);
+        __syncthreads();
+        const int64_t item = s_item;
+        if (item >= total_items) break;
+        const int tile = a.item_tile[item];
+        const SetDesc &sd = a.sets[a.tile_set[tile]];
+        ScoreJob jb;
+        jb.m = sd.m;
+        jb.qxc = sd.q_xc;
+        jb.qnrm = sd.q_nrm;
+        jb.thrA = a.thrA + sd.q_glob;
+        jb.xxc = sd.x_xc;
+        jb.xhx = sd.x_hx;
+        jb.xnrm = sd.x_nrm;
+        jb.dp = sd.dp;
+        jb.sym = sd.sym;
+        jb.q0 = int64_t(tile - sd.tile0) * kBQ;
+        jb.band_lo = a.tile_lo[tile];
+        jb.band_hi = a.tile_hi[tile];
+        jb.c_first = (item - a.item_off[tile]) * kChunksPerItem;
+        jb.c_end = min(cdiv(jb.band_hi - jb.band_lo, kBR), jb.c_first + kChunksPerItem);
+        jb.q_out = sd.q_glob;
+        if (jb.dp <= kKC)
+            score_item<true>(jb, sd.c1, a.surv, a.cap, a.count);
+        else
+            score_item<false>(jb, sd.c1, a.surv, a.cap, a.count);
+    }
 }
 
 // ------------------------------------------------------- exact decision

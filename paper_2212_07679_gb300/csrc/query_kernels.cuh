@@ -50,6 +50,46 @@ struct ScoreArgs {
     int *err;                   // device error flag (bounded waits that gave up)
 };
 
+// One work item of the FP32 scorer: a 128-query tile against band chunks
+// [c_first, c_end) of its band; survivors are reported with query number
+// q_out + local sorted query.
+struct ScoreJob {
+    int64_t m;
+    const float *qxc, *qnrm, *thrA;
+    const float *xxc, *xhx, *xnrm;
+    int dp, sym;
+    int64_t q0, band_lo, band_hi, c_first, c_end, q_out;
+};
+
+// Per-set descriptor of a batched query (device memory).
+struct SetDesc {
+    int64_t m, n;               // queries, data points
+    int d, dp, sym;             // dims, row stride, symmetric self-join
+    float c1;                   // FP32 score rounding constant of this d
+    int64_t q_glob;             // first global query number of the set
+    int64_t tile0;              // first global tile of the set
+    double R2, Wbase;           // fl64(R*R), band half-width base
+    const float *q_alpha, *q_raw, *q_xc, *q_hx, *q_nrm;
+    const int32_t *q_order;
+    const float *x_alpha, *x_raw, *x_xc, *x_hx, *x_nrm;
+    const int32_t *x_order;
+    const float *eps_d, *eps_q; // device scalars: score rounding bounds
+    double Rx, e_data;          // radius slack and centring error bound
+};
+
+struct BatchScoreArgs {
+    const SetDesc *sets;
+    const int32_t *tile_set;    // set of each global tile
+    const float *thrA;          // per global query
+    const int64_t *tile_lo, *tile_hi, *item_off;
+    const int32_t *item_tile;
+    int ntiles;
+    uint2 *surv;
+    int64_t cap;
+    unsigned long long *count, *work;
+};
+
+__global__ void k_score_fp32_batch(BatchScoreArgs a);
 __global__ void k_item_tiles(const int64_t *item_off, int ntiles, int32_t *item_tile);
 __global__ void k_query_consts(const float *hy, const float *qn, int64_t m, int d, double Rx,
                                double e_data, float *thrA);

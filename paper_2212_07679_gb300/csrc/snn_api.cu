@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <unordered_map>
 
 #include "common.cuh"
 #include "dbscan_kernels.cuh"
@@ -40,6 +41,56 @@ void set_error(const char *fmt, ...) {
     va_end(ap);
 }
 void clear_error() { g_err[0] = 0; }
+
+// Output blocks shared by several library-returned pointers (the per-set
+// slices of a batched query): each registered pointer holds one reference and
+// the block is released when the last one is passed to snn_free.
+namespace {
+struct SharedBlock {
+    void *base;
+    int refs;
+};
+std::mutex g_blocks_mu;
+std::unordered_map<void *, SharedBlock *> g_blocks;
+}  // namespace
+
+snn_status register_block(void *block, void *const *ptrs, int count) {
+    std::lock_guard<std::mutex> lk(g_blocks_mu);
+    SharedBlock *b = new (std::nothrow) SharedBlock{block, 0};
+    if (!b) {
+        set_error("host allocation failed");
+        return SNN_ENOMEM;
+    }
+    for (int i = 0; i < count; ++i) {
+        if (!ptrs[i]) continue;
+        g_blocks[ptrs[i]] = b;
+        ++b->refs;
+    }
+    if (b->refs == 0) {
+        cudaFree(block);
+        delete b;
+    }
+    return SNN_OK;
+}
+
+static void free_device_ptr(void *p) {
+    SharedBlock *b = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_blocks_mu);
+        auto it = g_blocks.find(p);
+        if (it != g_blocks.end()) {
+            b = it->second;
+            g_blocks.erase(it);
+            if (--b->refs > 0) return;
+        }
+    }
+    if (b) {
+        cudaFree(b->base);
+        delete b;
+    } else {
+        cudaFree(p);
+    }
+}
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 int device_sm_count() {
@@ -591,6 +642,10 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     return SNN_OK;
 }
 
+snn_status batch_query(int32_t nsets, const snn_index *const *idx, const float *const *Q,
+                       const int64_t *m_in, const int64_t *ldq_in, const double *R_in,
+                       cudaStream_t s, snn_csr *out);
+
 static snn_status check_finite_r(double R, const char *what) {
     if (!(R >= 0.0) || !std::isfinite(R)) {
         set_error("%s must be finite and >= 0", what);
@@ -648,23 +703,12 @@ snn_status snn_query_radius_batch(int32_t nsets, const snn_index *const *idx, co
         set_error("invalid batch arguments");
         return SNN_EINVAL;
     }
-    for (int32_t s = 0; s < nsets; ++s) {
-        snn_status st = snn_query_radius(idx[s], Q[s], m[s], ldq[s], R[s], prec, stream, &out[s],
-                                         nullptr);
-        if (st != SNN_OK) {
-            char msg[512];
-            std::snprintf(msg, sizeof(msg), "set %d: %s", (int)s, snn_last_error());
-            for (int32_t t = 0; t < s; ++t) {
-                cudaFree(out[t].offsets);
-                if (out[t].indices) cudaFree(out[t].indices);
-                if (out[t].dist2) cudaFree(out[t].dist2);
-                std::memset(&out[t], 0, sizeof(out[t]));
-            }
-            set_error("%s", msg);
-            return st;
-        }
+    if (prec != SNN_PREC_FP32 && prec != SNN_PREC_BF16) {
+        set_error("precision %d is not available in this build", (int)prec);
+        return SNN_ENOTSUP;
     }
-    return SNN_OK;
+    std::call_once(g_pool_once, pool_setup);
+    return batch_query(nsets, idx, Q, m, ldq, R, static_cast<cudaStream_t>(stream), out);
 }
 
 snn_status snn_dbscan(const float *X, int64_t n, int32_t d, int64_t ld, double eps, int32_t min_pts,
@@ -729,7 +773,7 @@ snn_status snn_index_get_view(const snn_index *idx, snn_index_view *view) {
 }
 
 void snn_free(void *p) {
-    if (p) cudaFree(p);
+    if (p) free_device_ptr(p);
 }
 
 void snn_index_free(snn_index *idx) { index_release(idx); }

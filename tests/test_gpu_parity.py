@@ -186,12 +186,42 @@ def test_dbscan_small(snn):
 
 
 # ------------------------------------------------------------ batches
-def test_batch_matches_single_calls(snn):
-    sets = wl.ragged_batch(sets=6, n_lo=500, n_hi=5000, seed=99)
+def test_batch_matches_oracle(snn):
+    # one call, one persistent scoring launch for all sets: ragged n and d
+    # (2, 3, 8, 32), out-of-sample queries, per-set radius
+    sets = wl.ragged_batch(sets=12, n_lo=500, n_hi=6000, seed=99)
     idx = [snn.Index(_dev(s.P)) for s in sets]
+    before = snn.launch_count()
     outs = snn.query_batch(idx, [_dev(s.Q) for s in sets], [s.R for s in sets])
+    launches = snn.launch_count() - before
+    assert launches < 60          # independent of the number of sets
     for s, got in zip(sets, outs):
         assert_csr_equal(got, oracle.brute_radius(s.P, s.Q, s.R), s.name)
+
+
+def test_batch_mixed_sets(snn):
+    rng = np.random.default_rng(98)
+    cases = []
+    for k, (n, d) in enumerate([(3000, 2), (2500, 17), (4000, 8), (1200, 40), (900, 3), (50, 5)]):
+        P = (rng.standard_normal((n, d)) * (1 + k)).astype(np.float32)
+        if k % 2 == 0:
+            cases.append((P, None, 0.9 + 0.2 * k))                      # self-join
+        else:
+            Q = (rng.standard_normal((n // 3, d)) * (1 + k)).astype(np.float32)
+            cases.append((P, Q, 1.1 + 0.1 * k))
+    cases.append((rng.standard_normal((700, 4)).astype(np.float32),
+                  np.zeros((0, 4), np.float32), 1.0))                   # no queries
+    dup = np.repeat(rng.standard_normal((30, 6)).astype(np.float32), 7, axis=0)
+    cases.append((dup, None, 0.0))                                       # R = 0, duplicates
+    idx = [snn.Index(_dev(P)) for P, _, _ in cases]
+    Qs = [None if Q is None else _dev(Q) for _, Q, _ in cases]
+    outs = snn.query_batch(idx, Qs, [R for _, _, R in cases])
+    for k, ((P, Q, R), got) in enumerate(zip(cases, outs)):
+        assert_csr_equal(got, oracle.brute_radius(P, Q, R), f"set {k}")
+    # the per-set results are slices of one allocation: free them out of order
+    for k in [3, 0, 7, 1, 6, 2, 5, 4]:
+        outs[k] = None
+    del outs
 
 
 # ------------------------------------------------- full size (sampled)
