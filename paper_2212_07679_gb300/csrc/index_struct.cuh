@@ -24,7 +24,8 @@ struct snn_index {
     // plus the folded threshold columns.
     uint16_t *tc_part[3] = {nullptr, nullptr, nullptr};
     int tc_nsplit = 0;
-    int tc_k2 = 0;
+    int tc_k2 = 0;                // row width of part 1 (columns)
+    int tc_k2n = 0;               // row width of parts 2 and 3
     float alpha_err = 0.f;
     float nrm_max = 0.f;
     mutable double surv_hint = 0.0;   // survivors per query seen last time

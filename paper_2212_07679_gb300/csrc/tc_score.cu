@@ -33,32 +33,43 @@ constexpr int kEpiWarps = 8;        // two warps per TMEM lane quadrant, half th
 constexpr int kTcThreads = 64 + 32 * kEpiWarps;
 constexpr int kExtra = 9;           // folded columns
 constexpr long long kTimeoutCycles = 4000000000LL;   // ~2 s
-// dynamic shared memory per CTA (minus alignment and barriers) for 1 or 2
-// resident CTAs per SM
-__host__ __device__ constexpr int smem_budget(int cps) {
-    return cps == 1 ? 232448 - 1024 - 256 : 233472 / 2 - 1024 - 1024 - 256;
+// dynamic shared memory per CTA (minus base alignment and barriers) for 1
+// or 2 resident CTAs per SM
+__host__ __device__ constexpr int smem_budget(int cps, int align) {
+    return (cps == 1 ? 232448 : 115712) - align - 256;
 }
 
 // Shape of one kernel instance: NSPLIT BF16 parts, BK columns per k-block
-// (64: 128-byte rows, 128B swizzle; 32: 64-byte rows, 64B swizzle), BN band
-// rows per chunk (MMA N), ARES: the query tile stays in shared memory for a
-// whole work item (only when one k-block holds all columns), in two slots so
-// that the next item's tile loads while the current one is in use.
-template <int NSPLIT, int BK, int BN, bool ARES, int CPS = 1>
+// for part 1 (64: 128-byte rows, 128B swizzle; 32: 64-byte rows, 64B swizzle),
+// NW columns for parts 2 and 3 (NW < BK when all data columns fit NW: those
+// parts carry no folded columns, so their tiles are narrower), BN band rows
+// per chunk (MMA N), ARES: the query tile stays in shared memory for a whole
+// work item (only when one k-block holds all columns), in two slots so that
+// the next item's tile loads while the current one is in use; CPS resident
+// CTAs per SM.
+template <int NSPLIT, int BK, int BN, bool ARES, int CPS = 1, int NW = BK>
 struct TcShape {
-    static constexpr int kSmemBudget = smem_budget(CPS);
-    static constexpr int kTA = kTM * BK * 2;            // bytes of one A part tile
-    static constexpr int kTB = BN * BK * 2;             // bytes of one B part tile
-    static constexpr int kAResBytes = ARES ? 2 * NSPLIT * kTA : 0;
-    static constexpr int kStageBytes = ARES ? NSPLIT * kTB : NSPLIT * (kTA + kTB);
+    static constexpr int kAlign = BK == 64 ? 1024 : 512;
+    static constexpr int kSmemBudget = smem_budget(CPS, kAlign);
+    static constexpr int kTA0 = kTM * BK * 2;           // A part 1 tile
+    static constexpr int kTA1 = kTM * NW * 2;           // A parts 2, 3
+    static constexpr int kTB0 = BN * BK * 2;            // B part 1 tile
+    static constexpr int kTB1 = BN * NW * 2;            // B parts 2, 3
+    static constexpr int kASlot = kTA0 + (NSPLIT - 1) * kTA1;
+    static constexpr int kBStage = kTB0 + (NSPLIT - 1) * kTB1;
+    static constexpr int kAResBytes = ARES ? 2 * kASlot : 0;
+    static constexpr int kStageBytes = ARES ? kBStage : kASlot + kBStage;
     static constexpr int kStagesRaw = (kSmemBudget - kAResBytes) / kStageBytes;
     static constexpr int kStages = kStagesRaw > 8 ? 8 : kStagesRaw;
     static constexpr int kNP = NSPLIT == 2 ? 3 : 6;     // MMAs per k-step
     static constexpr int kKSteps = BK / 16;             // k-steps per k-block
     static constexpr int kRowBytes = BK * 2;
+    static constexpr int kRowBytesN = NW * 2;
     static constexpr uint32_t kTmemCols = 2 * BN;
-    static constexpr size_t kSmem = size_t(kAResBytes) + size_t(kStages) * kStageBytes + 1024 + 256;
+    static constexpr size_t kSmem = size_t(kAResBytes) + size_t(kStages) * kStageBytes + kAlign + 256;
     static_assert(kStagesRaw >= 2, "shape does not fit shared memory");
+    static_assert(ARES || NW == BK, "narrow parts need a resident query tile");
+    static_assert(NW == 16 || NW == 32 || NW == 64, "unsupported part width");
 };
 
 __host__ __device__ constexpr int tc_npairs(int nsplit) { return nsplit == 2 ? 3 : 6; }
@@ -119,7 +130,8 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
 }
 
 // Shared-memory matrix descriptor of a K-major tile whose rows are ROWB
-// bytes (128: 128B swizzle, 64: 64B swizzle); 8-row groups are 8*ROWB apart.
+// bytes (128, 64 or 32, with the swizzle of that width); 8-row groups are
+// 8*ROWB apart.
 template <int ROWB>
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     uint64_t d = 0;
@@ -127,7 +139,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     d |= uint64_t(1) << 16;                         // leading byte offset (unused)
     d |= uint64_t((8 * ROWB) >> 4) << 32;           // stride byte offset
     d |= uint64_t(1) << 46;                         // descriptor version
-    d |= uint64_t(ROWB == 128 ? 2 : 4) << 61;       // 128B or 64B swizzle
+    d |= uint64_t(ROWB == 128 ? 2 : (ROWB == 64 ? 4 : 6)) << 61;   // 128B / 64B / 32B swizzle
     return d;
 }
 
@@ -216,13 +228,13 @@ __device__ __forceinline__ ItemInfo item_info(const TcArgs &a, int64_t item) {
     return f;
 }
 
-template <int NSPLIT, int BK, int BN, bool ARES, int CPS>
+template <int NSPLIT, int BK, int BN, bool ARES, int CPS, int NW>
 __global__ void __launch_bounds__(kTcThreads, CPS)
 k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUtensorMap qa1,
            const __grid_constant__ CUtensorMap qa2, const __grid_constant__ CUtensorMap xb0,
            const __grid_constant__ CUtensorMap xb1, const __grid_constant__ CUtensorMap xb2,
            TcArgs a) {
-    using Sh = TcShape<NSPLIT, BK, BN, ARES, CPS>;
+    using Sh = TcShape<NSPLIT, BK, BN, ARES, CPS, NW>;
     constexpr int S = Sh::kStages;
     constexpr int NP = Sh::kNP;
     constexpr int CSTEP = BN / kBR;              // kBR-row chunks per MMA chunk
@@ -233,17 +245,19 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
 
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
-    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t base = (raw + uint32_t(Sh::kAlign - 1)) & ~uint32_t(Sh::kAlign - 1);
     unsigned char *gbase = smem_raw + (base - raw);
     // resident A parts first (ARES), then the stages
     const uint32_t stage0 = base + uint32_t(Sh::kAResBytes);
     // ARES: s is the A slot (item parity); otherwise the stage
     auto a_tile = [&](int s, int p) -> uint32_t {
-        if (ARES) return base + uint32_t((s * NSPLIT + p) * Sh::kTA);
-        return stage0 + uint32_t(s * Sh::kStageBytes + p * Sh::kTA);
+        const uint32_t po = p == 0 ? 0u : uint32_t(Sh::kTA0 + (p - 1) * Sh::kTA1);
+        if (ARES) return base + uint32_t(s * Sh::kASlot) + po;
+        return stage0 + uint32_t(s * Sh::kStageBytes) + po;
     };
     auto b_tile = [&](int s, int p) -> uint32_t {
-        return stage0 + uint32_t(s * Sh::kStageBytes + (ARES ? 0 : NSPLIT * Sh::kTA) + p * Sh::kTB);
+        const uint32_t po = p == 0 ? 0u : uint32_t(Sh::kTB0 + (p - 1) * Sh::kTB1);
+        return stage0 + uint32_t(s * Sh::kStageBytes + (ARES ? 0 : Sh::kASlot)) + po;
     };
     const uint32_t bar0 = stage0 + uint32_t(S * Sh::kStageBytes);
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
@@ -307,7 +321,7 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                     const int k = itm & 1;
                     const uint32_t use = uint32_t(itm >> 1);
                     if (!mbar_wait(aempty_bar(k), (use & 1u) ^ 1u, s_abort, a.err)) break;
-                    mbar_expect_tx(afull_bar(k), uint32_t(NSPLIT * Sh::kTA));
+                    mbar_expect_tx(afull_bar(k), uint32_t(Sh::kASlot));
                     for (int p = 0; p < NSPLIT; ++p)
                         tma_load_2d(a_tile(k, p), qa[p], 0, int(f.q0), afull_bar(k));
                     a_issued = itm + 1;
@@ -320,8 +334,9 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                         if (!mbar_wait(empty_bar(s), (round & 1u) ^ 1u, s_abort, a.err)) break;
                         mbar_expect_tx(full_bar(s), uint32_t(Sh::kStageBytes));
                         for (int p = 0; p < NSPLIT; ++p) {
-                            if (!ARES) tma_load_2d(a_tile(s, p), qa[p], kb * BK, int(f.q0), full_bar(s));
-                            tma_load_2d(b_tile(s, p), xb[p], kb * BK, int(j0), full_bar(s));
+                            const int kx = kb * (p == 0 ? BK : NW);
+                            if (!ARES) tma_load_2d(a_tile(s, p), qa[p], kx, int(f.q0), full_bar(s));
+                            tma_load_2d(b_tile(s, p), xb[p], kx, int(j0), full_bar(s));
                         }
                         issued = it + 1;
                     }
@@ -363,10 +378,12 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
 #pragma unroll
                             for (int pr = 0; pr < NP; ++pr) {
                                 if (pr >= np) break;
-                                const uint64_t ad = smem_desc<Sh::kRowBytes>(
-                                    a_tile(ARES ? aslot : s, kPa[pr]) + 32u * ks);
-                                const uint64_t bd =
-                                    smem_desc<Sh::kRowBytes>(b_tile(s, kPb[pr]) + 32u * ks);
+                                const uint32_t aa = a_tile(ARES ? aslot : s, kPa[pr]) + 32u * ks;
+                                const uint32_t bb = b_tile(s, kPb[pr]) + 32u * ks;
+                                const uint64_t ad = kPa[pr] == 0 ? smem_desc<Sh::kRowBytes>(aa)
+                                                                 : smem_desc<Sh::kRowBytesN>(aa);
+                                const uint64_t bd = kPb[pr] == 0 ? smem_desc<Sh::kRowBytes>(bb)
+                                                                 : smem_desc<Sh::kRowBytesN>(bb);
                                 mma_bf16(dt, ad, bd, kIdesc, (kb | ks | pr) != 0 ? 1u : 0u);
                             }
                         }
@@ -498,7 +515,7 @@ __device__ __forceinline__ void split3(double w, uint16_t (&o)[3]) {
 template <int NSPLIT>
 __global__ void k_tc_pack(const float *__restrict__ xc, int dp, const float *__restrict__ hx,
                           const float *__restrict__ nrm, const double *__restrict__ Aq,
-                          int64_t rows, int d, int K2, double c, int query_side,
+                          int64_t rows, int d, int K2, int K2n, double c, int query_side,
                           uint16_t *__restrict__ p0, uint16_t *__restrict__ p1,
                           uint16_t *__restrict__ p2) {
     const int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -541,8 +558,11 @@ __global__ void k_tc_pack(const float *__restrict__ xc, int dp, const float *__r
             }
         }
         p0[ro + k] = v0;
-        if (NSPLIT >= 2) p1[ro + k] = v1;
-        if (NSPLIT >= 3) p2[ro + k] = v2;
+        // parts 2 and 3 hold data columns only, rows of K2n columns
+        if (k < K2n) {
+            if (NSPLIT >= 2) p1[r * K2n + k] = v1;
+            if (NSPLIT >= 3) p2[r * K2n + k] = v2;
+        }
     }
 }
 
@@ -597,7 +617,8 @@ snn_status make_map(CUtensorMap *map, const uint16_t *ptr, int64_t rows, int K2,
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(ptr), dims,
                      strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                     bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
+                              : (bk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B),
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed (%d)", int(r));
@@ -621,17 +642,18 @@ double tc_constant(int nsplit, int d, double *u_k_out) {
     return 1.02 * (c_mn > c_hx ? c_mn : c_hx);
 }
 
-template <int NSPLIT, int BK, int BN, bool ARES, int CPS>
+template <int NSPLIT, int BK, int BN, bool ARES, int CPS, int NW>
 snn_status launch_tc(const snn_index *ix, const ScoreArgs &sa, const uint16_t *const *qp,
-                     int K2, cudaStream_t s) {
-    using Sh = TcShape<NSPLIT, BK, BN, ARES, CPS>;
+                     int K2, int K2n, cudaStream_t s) {
+    using Sh = TcShape<NSPLIT, BK, BN, ARES, CPS, NW>;
     CUtensorMap maps[6];
     for (int p = 0; p < 3; ++p) {
         const int pp = p < NSPLIT ? p : 0;
-        SNN_TRY(make_map(&maps[p], qp[pp], sa.q.m, K2, BK, kTM));
-        SNN_TRY(make_map(&maps[3 + p], ix->tc_part[pp], ix->n, K2, BK, BN));
+        const int k2 = pp == 0 ? K2 : K2n, box = pp == 0 ? BK : NW;
+        SNN_TRY(make_map(&maps[p], qp[pp], sa.q.m, k2, box, kTM));
+        SNN_TRY(make_map(&maps[3 + p], ix->tc_part[pp], ix->n, k2, box, BN));
     }
-    auto kern = k_score_tc<NSPLIT, BK, BN, ARES, CPS>;
+    auto kern = k_score_tc<NSPLIT, BK, BN, ARES, CPS, NW>;
     SNN_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::kSmem)));
     TcArgs a;
     a.m = sa.q.m;
@@ -674,16 +696,20 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
     const int kp = d + kExtra;
     const int bk = kp <= 32 ? 32 : 64;
     const int K2 = int(cdiv(kp, bk) * bk);
+    // parts 2 and 3 carry no folded columns: with every data column inside
+    // the first 16, their rows are 16 columns wide (low-d shape only)
+    const int K2n = (kp <= 32 && d <= 16) ? 16 : K2;
     {
         std::lock_guard<std::mutex> lk(ix->mu);
-        if (ix->tc_nsplit != nsplit || ix->tc_k2 != K2) {
+        if (ix->tc_nsplit != nsplit || ix->tc_k2 != K2 || ix->tc_k2n != K2n) {
             for (int p = 0; p < 3; ++p) {
                 if (ix->tc_part[p]) cudaFree(ix->tc_part[p]);
                 ix->tc_part[p] = nullptr;
             }
             ix->tc_nsplit = 0;
             for (int p = 0; p < nsplit; ++p) {
-                cudaError_t e = cudaMalloc(&ix->tc_part[p], size_t(ix->n) * K2 * sizeof(uint16_t));
+                const int w = p == 0 ? K2 : K2n;
+                cudaError_t e = cudaMalloc(&ix->tc_part[p], size_t(ix->n) * w * sizeof(uint16_t));
                 if (e != cudaSuccess) {
                     set_error("BF16 operand allocation failed: %s", cudaGetErrorString(e));
                     return SNN_ENOMEM;
@@ -691,11 +717,12 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
             }
             auto packer = nsplit == 2 ? k_tc_pack<2> : k_tc_pack<3>;
             SNN_LAUNCH(packer, unsigned(cdiv(ix->n * 32, 256)), 256, 0, s)(
-                ix->xc, ix->dp, ix->hx, ix->nrm, nullptr, ix->n, d, K2, c, 0, ix->tc_part[0],
+                ix->xc, ix->dp, ix->hx, ix->nrm, nullptr, ix->n, d, K2, K2n, c, 0, ix->tc_part[0],
                 ix->tc_part[1], ix->tc_part[2]);
             SNN_LAUNCH_CHECK();
             ix->tc_nsplit = nsplit;
             ix->tc_k2 = K2;
+            ix->tc_k2n = K2n;
         }
     }
     if (mma_flops_per_pair) {
@@ -707,25 +734,28 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
     double *Aq;
     uint16_t *qp[3] = {nullptr, nullptr, nullptr};
     SNN_TRY(scr.alloc(&Aq, m));
-    for (int p = 0; p < nsplit; ++p) SNN_TRY(scr.alloc(&qp[p], size_t(m) * K2));
+    for (int p = 0; p < nsplit; ++p) SNN_TRY(scr.alloc(&qp[p], size_t(m) * (p == 0 ? K2 : K2n)));
     SNN_LAUNCH(k_tc_query_consts, unsigned(cdiv(m, 256)), 256, 0, s)(
         sa.q.hx, sa.q.nrm, m, d, Rx, e_data, 0x1p-23 + u_k, Aq);
     SNN_LAUNCH_CHECK();
     auto packer = nsplit == 2 ? k_tc_pack<2> : k_tc_pack<3>;
     SNN_LAUNCH(packer, unsigned(cdiv(m * 32, 256)), 256, 0, s)(sa.q.xc, ix->dp, sa.q.hx, sa.q.nrm, Aq,
-                                                            m, d, K2, c, 1, qp[0], qp[1], qp[2]);
+                                                            m, d, K2, K2n, c, 1, qp[0], qp[1], qp[2]);
     SNN_LAUNCH_CHECK();
     // low d: two CTAs per SM, each with a resident query tile, so that one
     // CTA's pipeline bubbles (accumulator hand-off, item changes) overlap the
     // other's MMAs
+    if (kp <= 32 && K2n == 16)
+        return nsplit == 2 ? launch_tc<2, 32, 128, true, 2, 16>(ix, sa, qp, K2, K2n, s)
+                           : launch_tc<3, 32, 128, true, 2, 16>(ix, sa, qp, K2, K2n, s);
     if (kp <= 32)
-        return nsplit == 2 ? launch_tc<2, 32, 128, true, 2>(ix, sa, qp, K2, s)
-                           : launch_tc<3, 32, 128, true, 2>(ix, sa, qp, K2, s);
+        return nsplit == 2 ? launch_tc<2, 32, 128, true, 2, 32>(ix, sa, qp, K2, K2n, s)
+                           : launch_tc<3, 32, 128, true, 2, 32>(ix, sa, qp, K2, K2n, s);
     if (kp <= 64)
-        return nsplit == 2 ? launch_tc<2, 64, 128, true, 1>(ix, sa, qp, K2, s)
-                           : launch_tc<3, 64, 128, true, 1>(ix, sa, qp, K2, s);
-    return nsplit == 2 ? launch_tc<2, 64, 128, false, 1>(ix, sa, qp, K2, s)
-                       : launch_tc<3, 64, 128, false, 1>(ix, sa, qp, K2, s);
+        return nsplit == 2 ? launch_tc<2, 64, 128, true, 1, 64>(ix, sa, qp, K2, K2n, s)
+                           : launch_tc<3, 64, 128, true, 1, 64>(ix, sa, qp, K2, K2n, s);
+    return nsplit == 2 ? launch_tc<2, 64, 128, false, 1, 64>(ix, sa, qp, K2, K2n, s)
+                       : launch_tc<3, 64, 128, false, 1, 64>(ix, sa, qp, K2, K2n, s);
 }
 
 }  // namespace snn
