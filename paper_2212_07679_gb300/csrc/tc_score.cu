@@ -29,8 +29,10 @@ namespace snn {
 namespace {
 
 constexpr int kTM = 128;            // queries per tile (MMA M)
-constexpr int kEpiWarps = 8;        // two warps per TMEM lane quadrant, half the columns each
-constexpr int kTcThreads = 64 + 32 * kEpiWarps;
+// epilogue: two warps per TMEM lane quadrant and query sub-tile (half the
+// columns each); producer and MMA warps in front
+__host__ __device__ constexpr int tc_epi_warps(int mt) { return 8 * mt; }
+__host__ __device__ constexpr int tc_threads(int mt) { return 64 + 32 * tc_epi_warps(mt); }
 constexpr int kExtra = 9;           // folded columns
 constexpr long long kTimeoutCycles = 4000000000LL;   // ~2 s
 // dynamic shared memory per CTA (minus base alignment and barriers) for 1
@@ -46,13 +48,14 @@ __host__ __device__ constexpr int smem_budget(int cps, int align) {
 // per chunk (MMA N), ARES: the query tile stays in shared memory for a whole
 // work item (only when one k-block holds all columns), in two slots so that
 // the next item's tile loads while the current one is in use; CPS resident
-// CTAs per SM.
-template <int NSPLIT, int BK, int BN, bool ARES, int CPS = 1, int NW = BK>
+// CTAs per SM; MT query tiles of 128 per work item (each band chunk is loaded
+// once and multiplied with all MT tiles, M = 128 per MMA).
+template <int NSPLIT, int BK, int BN, bool ARES, int CPS = 1, int NW = BK, int MT = 1>
 struct TcShape {
     static constexpr int kAlign = BK == 64 ? 1024 : 512;
     static constexpr int kSmemBudget = smem_budget(CPS, kAlign);
-    static constexpr int kTA0 = kTM * BK * 2;           // A part 1 tile
-    static constexpr int kTA1 = kTM * NW * 2;           // A parts 2, 3
+    static constexpr int kTA0 = MT * kTM * BK * 2;      // A part 1 tile
+    static constexpr int kTA1 = MT * kTM * NW * 2;      // A parts 2, 3
     static constexpr int kTB0 = BN * BK * 2;            // B part 1 tile
     static constexpr int kTB1 = BN * NW * 2;            // B parts 2, 3
     static constexpr int kASlot = kTA0 + (NSPLIT - 1) * kTA1;
@@ -65,10 +68,14 @@ struct TcShape {
     static constexpr int kKSteps = BK / 16;             // k-steps per k-block
     static constexpr int kRowBytes = BK * 2;
     static constexpr int kRowBytesN = NW * 2;
-    static constexpr uint32_t kTmemCols = 2 * BN;
+    static constexpr uint32_t kTmemCols = 2 * MT * BN;
+    static constexpr int kEpiWarps = tc_epi_warps(MT);
+    static constexpr int kThreads = tc_threads(MT);
     static constexpr size_t kSmem = size_t(kAResBytes) + size_t(kStages) * kStageBytes + kAlign + 256;
     static_assert(kStagesRaw >= 2, "shape does not fit shared memory");
     static_assert(ARES || NW == BK, "narrow parts need a resident query tile");
+    static_assert(MT == 1 || ARES, "several query tiles per item need a resident query tile");
+    static_assert(kTmemCols <= 512, "accumulators exceed TMEM");
     static_assert(NW == 16 || NW == 32 || NW == 64, "unsupported part width");
 };
 
@@ -217,10 +224,12 @@ struct ItemInfo {
     int64_t q0, band_lo, band_hi, c_first, c_end;   // chunks of kBR rows
 };
 
+// tiles here are groups of MT consecutive 128-query tiles
+template <int MT>
 __device__ __forceinline__ ItemInfo item_info(const TcArgs &a, int64_t item) {
     const int lo = a.item_tile[item];
     ItemInfo f;
-    f.q0 = int64_t(lo) * kTM;
+    f.q0 = int64_t(lo) * kTM * MT;
     f.band_lo = a.tile_lo[lo];
     f.band_hi = a.tile_hi[lo];
     f.c_first = (item - a.item_off[lo]) * kChunksPerItem;
@@ -228,13 +237,13 @@ __device__ __forceinline__ ItemInfo item_info(const TcArgs &a, int64_t item) {
     return f;
 }
 
-template <int NSPLIT, int BK, int BN, bool ARES, int CPS, int NW>
-__global__ void __launch_bounds__(kTcThreads, CPS)
+template <int NSPLIT, int BK, int BN, bool ARES, int CPS, int NW, int MT>
+__global__ void __launch_bounds__(tc_threads(MT), CPS)
 k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUtensorMap qa1,
            const __grid_constant__ CUtensorMap qa2, const __grid_constant__ CUtensorMap xb0,
            const __grid_constant__ CUtensorMap xb1, const __grid_constant__ CUtensorMap xb2,
            TcArgs a) {
-    using Sh = TcShape<NSPLIT, BK, BN, ARES, CPS, NW>;
+    using Sh = TcShape<NSPLIT, BK, BN, ARES, CPS, NW, MT>;
     constexpr int S = Sh::kStages;
     constexpr int NP = Sh::kNP;
     constexpr int CSTEP = BN / kBR;              // kBR-row chunks per MMA chunk
@@ -284,7 +293,7 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(tfull_bar(b), 1);
-            mbar_init(tempty_bar(b), 32 * kEpiWarps);
+            mbar_init(tempty_bar(b), 32 * Sh::kEpiWarps);
             mbar_init(afull_bar(b), 1);
             mbar_init(aempty_bar(b), 1);
         }
@@ -297,6 +306,7 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
     }
     if (warp == 1) {
         // two accumulators of BN FP32 columns
+        // two accumulator sets of MT x BN FP32 columns
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32((const void *)s_tmem)),
                      "n"(Sh::kTmemCols)
@@ -315,7 +325,7 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
         if (lane == 0) {
             int it = 0, itm = 0;
             for (int64_t item = blockIdx.x; item < total && !*s_abort; item += gridDim.x, ++itm) {
-                const ItemInfo f = item_info(a, item);
+                const ItemInfo f = item_info<MT>(a, item);
                 if (ARES) {
                     // the query tile of this item, once, into slot itm & 1
                     const int k = itm & 1;
@@ -349,7 +359,7 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
             int it = 0, chunk = 0, itm = 0;
             bool ok = true;
             for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x, ++itm) {
-                const ItemInfo f = item_info(a, item);
+                const ItemInfo f = item_info<MT>(a, item);
                 const int aslot = itm & 1;
                 if (ARES) {
                     if (!(ok = mbar_wait(afull_bar(aslot), uint32_t(itm >> 1) & 1u, s_abort, a.err)))
@@ -362,7 +372,7 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                     const uint32_t use = uint32_t(chunk >> 1);
                     if (!(ok = mbar_wait(tempty_bar(b), (use & 1u) ^ 1u, s_abort, a.err))) break;
                     tmem_fence_after();
-                    const uint32_t dt = tmem + uint32_t(b * BN);
+                    const uint32_t dt0 = tmem + uint32_t(b * MT * BN);
                     for (int kb = 0; kb < a.nkb; ++kb, ++it) {
                         const int s = it % S;
                         const uint32_t round = uint32_t(it / S);
@@ -378,13 +388,20 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
 #pragma unroll
                             for (int pr = 0; pr < NP; ++pr) {
                                 if (pr >= np) break;
-                                const uint32_t aa = a_tile(ARES ? aslot : s, kPa[pr]) + 32u * ks;
                                 const uint32_t bb = b_tile(s, kPb[pr]) + 32u * ks;
-                                const uint64_t ad = kPa[pr] == 0 ? smem_desc<Sh::kRowBytes>(aa)
-                                                                 : smem_desc<Sh::kRowBytesN>(aa);
                                 const uint64_t bd = kPb[pr] == 0 ? smem_desc<Sh::kRowBytes>(bb)
                                                                  : smem_desc<Sh::kRowBytesN>(bb);
-                                mma_bf16(dt, ad, bd, kIdesc, (kb | ks | pr) != 0 ? 1u : 0u);
+#pragma unroll
+                                for (int h = 0; h < MT; ++h) {
+                                    // query sub-tile h: 128 rows further into the A tile
+                                    const uint32_t arow = kPa[pr] == 0 ? Sh::kRowBytes : Sh::kRowBytesN;
+                                    const uint32_t aa = a_tile(ARES ? aslot : s, kPa[pr]) +
+                                                        uint32_t(h * kTM) * arow + 32u * ks;
+                                    const uint64_t ad = kPa[pr] == 0 ? smem_desc<Sh::kRowBytes>(aa)
+                                                                     : smem_desc<Sh::kRowBytesN>(aa);
+                                    mma_bf16(dt0 + uint32_t(h * BN), ad, bd, kIdesc,
+                                             (kb | ks | pr) != 0 ? 1u : 0u);
+                                }
                             }
                         }
                         mma_commit(empty_bar(s));
@@ -402,13 +419,15 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
         // ---------------------------------------------------- epilogue
         const int ew = warp - 2;                   // 0 .. kEpiWarps-1
         const int quad = warp & 3;                 // TMEM lanes 32*quad .. +31
-        const int half = ew >> 2;                  // which half of the columns
-        const int qi = quad * 32 + lane;           // query row within the tile
+        const int sub = ew >> 2;
+        const int half = sub & 1;                  // which half of the columns
+        const int ht = sub >> 1;                   // which query sub-tile
+        const int qi = ht * kTM + quad * 32 + lane;   // query row within the item's tiles
         constexpr int kGroups = BN / 32 / 2;       // 32-column groups per warp
         int chunk = 0;
         bool ok = true;
         for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
-            const ItemInfo f = item_info(a, item);
+            const ItemInfo f = item_info<MT>(a, item);
             const int64_t q = f.q0 + qi;
             for (int64_t c = f.c_first; c < f.c_end && ok; c += CSTEP, ++chunk) {
                 const int64_t j0 = f.band_lo + c * kBR;
@@ -417,7 +436,8 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                 ok = mbar_wait(tfull_bar(b), use & 1u, s_abort, a.err);
                 if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
                 tmem_fence_after();
-                const uint32_t tbase = tmem + (uint32_t(quad * 32) << 16) + uint32_t(b * BN);
+                const uint32_t tbase =
+                    tmem + (uint32_t(quad * 32) << 16) + uint32_t(b * MT * BN + ht * BN);
 #pragma unroll 1
                 for (int g2 = 0; g2 < kGroups; g2 += 2) {
                     uint32_t rr[64];
@@ -488,6 +508,30 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "n"(Sh::kTmemCols)
                      : "memory");
+}
+
+// Work list of the tensor-core scorer over tiles of MT x 128 queries.
+struct TileSet {
+    const int64_t *lo, *hi, *item_off;
+    const int32_t *item_tile;
+    int ntiles;
+};
+
+// Band of a group of mt consecutive 128-query tiles: the union of their bands.
+__global__ void k_group_band(const int64_t *__restrict__ tile_lo, const int64_t *__restrict__ tile_hi,
+                             int ntiles, int mt, int64_t *__restrict__ lo2, int64_t *__restrict__ hi2,
+                             int64_t *__restrict__ items2, int ngroups) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ngroups) return;
+    const int t0 = g * mt, t1 = min(ntiles, t0 + mt);
+    int64_t lo = tile_lo[t0], hi = tile_hi[t0];
+    for (int t = t0 + 1; t < t1; ++t) {
+        lo = min(lo, tile_lo[t]);
+        hi = max(hi, tile_hi[t]);
+    }
+    lo2[g] = lo;
+    hi2[g] = hi;
+    items2[g] = cdiv(cdiv(hi - lo, kBR), kChunksPerItem);
 }
 
 // ------------------------------------------------ operand packing
@@ -642,18 +686,18 @@ double tc_constant(int nsplit, int d, double *u_k_out) {
     return 1.02 * (c_mn > c_hx ? c_mn : c_hx);
 }
 
-template <int NSPLIT, int BK, int BN, bool ARES, int CPS, int NW>
+template <int NSPLIT, int BK, int BN, bool ARES, int CPS, int NW, int MT>
 snn_status launch_tc(const snn_index *ix, const ScoreArgs &sa, const uint16_t *const *qp,
-                     int K2, int K2n, cudaStream_t s) {
-    using Sh = TcShape<NSPLIT, BK, BN, ARES, CPS, NW>;
+                     int K2, int K2n, const TileSet &ts, cudaStream_t s) {
+    using Sh = TcShape<NSPLIT, BK, BN, ARES, CPS, NW, MT>;
     CUtensorMap maps[6];
     for (int p = 0; p < 3; ++p) {
         const int pp = p < NSPLIT ? p : 0;
         const int k2 = pp == 0 ? K2 : K2n, box = pp == 0 ? BK : NW;
-        SNN_TRY(make_map(&maps[p], qp[pp], sa.q.m, k2, box, kTM));
+        SNN_TRY(make_map(&maps[p], qp[pp], sa.q.m, k2, box, kTM * MT));
         SNN_TRY(make_map(&maps[3 + p], ix->tc_part[pp], ix->n, k2, box, BN));
     }
-    auto kern = k_score_tc<NSPLIT, BK, BN, ARES, CPS, NW>;
+    auto kern = k_score_tc<NSPLIT, BK, BN, ARES, CPS, NW, MT>;
     SNN_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::kSmem)));
     TcArgs a;
     a.m = sa.q.m;
@@ -661,17 +705,17 @@ snn_status launch_tc(const snn_index *ix, const ScoreArgs &sa, const uint16_t *c
     a.ksteps = int(cdiv(ix->d + kExtra, 16));
     a.ksteps_data = int(cdiv(ix->d, 16));
     a.nkb = K2 / BK;
-    a.tile_lo = sa.tile_lo;
-    a.tile_hi = sa.tile_hi;
-    a.item_off = sa.item_off;
-    a.item_tile = sa.item_tile;
-    a.ntiles = sa.ntiles;
+    a.tile_lo = ts.lo;
+    a.tile_hi = ts.hi;
+    a.item_off = ts.item_off;
+    a.item_tile = ts.item_tile;
+    a.ntiles = ts.ntiles;
     a.sym = sa.sym;
     a.surv = sa.surv;
     a.cap = sa.cap;
     a.count = sa.count;
     a.err = sa.err;
-    SNN_LAUNCH(kern, device_sm_count() * CPS, kTcThreads, Sh::kSmem, s)(maps[0], maps[1], maps[2],
+    SNN_LAUNCH(kern, device_sm_count() * CPS, Sh::kThreads, Sh::kSmem, s)(maps[0], maps[1], maps[2],
                                                                  maps[3], maps[4], maps[5], a);
     SNN_LAUNCH_CHECK();
     return SNN_OK;
@@ -742,20 +786,40 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
     SNN_LAUNCH(packer, unsigned(cdiv(m * 32, 256)), 256, 0, s)(sa.q.xc, ix->dp, sa.q.hx, sa.q.nrm, Aq,
                                                             m, d, K2, K2n, c, 1, qp[0], qp[1], qp[2]);
     SNN_LAUNCH_CHECK();
-    // low d: two CTAs per SM, each with a resident query tile, so that one
-    // CTA's pipeline bubbles (accumulator hand-off, item changes) overlap the
-    // other's MMAs
-    if (kp <= 32 && K2n == 16)
-        return nsplit == 2 ? launch_tc<2, 32, 128, true, 2, 16>(ix, sa, qp, K2, K2n, s)
-                           : launch_tc<3, 32, 128, true, 2, 16>(ix, sa, qp, K2, K2n, s);
+    TileSet ts1{sa.tile_lo, sa.tile_hi, sa.item_off, sa.item_tile, sa.ntiles};
+    if (kp <= 32 && K2n == 16) {
+        // low d: the band traffic per pair dominates, so every band chunk is
+        // multiplied with two query tiles (256 queries) sharing its load
+        constexpr int MT = 2;
+        const int ng = int(cdiv(sa.ntiles, MT));
+        int64_t *lo2, *hi2, *items2, *off2;
+        int32_t *it2;
+        SNN_TRY(scr.alloc(&lo2, ng));
+        SNN_TRY(scr.alloc(&hi2, ng));
+        SNN_TRY(scr.alloc(&items2, ng));
+        SNN_TRY(scr.alloc(&off2, ng + 1));
+        SNN_LAUNCH(k_group_band, unsigned(cdiv(ng, 128)), 128, 0, s)(sa.tile_lo, sa.tile_hi, sa.ntiles,
+                                                                     MT, lo2, hi2, items2, ng);
+        SNN_LAUNCH_CHECK();
+        SNN_TRY(scan_exclusive<int64_t>(items2, off2, ng, s));
+        const int64_t max_items = int64_t(ng) * (cdiv(ix->n, int64_t(kBR) * kChunksPerItem) + 1);
+        SNN_TRY(scr.alloc(&it2, max_items));
+        SNN_LAUNCH(k_item_tiles, unsigned(cdiv(ng, 128)), 128, 0, s)(off2, ng, it2);
+        SNN_LAUNCH_CHECK();
+        TileSet ts2{lo2, hi2, off2, it2, ng};
+        return nsplit == 2 ? launch_tc<2, 32, 128, true, 1, 16, MT>(ix, sa, qp, K2, K2n, ts2, s)
+                           : launch_tc<3, 32, 128, true, 1, 16, MT>(ix, sa, qp, K2, K2n, ts2, s);
+    }
+    // other low-d shapes: two CTAs per SM with a resident query tile, so that
+    // one CTA's pipeline bubbles overlap the other's MMAs
     if (kp <= 32)
-        return nsplit == 2 ? launch_tc<2, 32, 128, true, 2, 32>(ix, sa, qp, K2, K2n, s)
-                           : launch_tc<3, 32, 128, true, 2, 32>(ix, sa, qp, K2, K2n, s);
+        return nsplit == 2 ? launch_tc<2, 32, 128, true, 2, 32, 1>(ix, sa, qp, K2, K2n, ts1, s)
+                           : launch_tc<3, 32, 128, true, 2, 32, 1>(ix, sa, qp, K2, K2n, ts1, s);
     if (kp <= 64)
-        return nsplit == 2 ? launch_tc<2, 64, 128, true, 1, 64>(ix, sa, qp, K2, K2n, s)
-                           : launch_tc<3, 64, 128, true, 1, 64>(ix, sa, qp, K2, K2n, s);
-    return nsplit == 2 ? launch_tc<2, 64, 128, false, 1, 64>(ix, sa, qp, K2, K2n, s)
-                       : launch_tc<3, 64, 128, false, 1, 64>(ix, sa, qp, K2, K2n, s);
+        return nsplit == 2 ? launch_tc<2, 64, 128, true, 1, 64, 1>(ix, sa, qp, K2, K2n, ts1, s)
+                           : launch_tc<3, 64, 128, true, 1, 64, 1>(ix, sa, qp, K2, K2n, ts1, s);
+    return nsplit == 2 ? launch_tc<2, 64, 128, false, 1, 64, 1>(ix, sa, qp, K2, K2n, ts1, s)
+                       : launch_tc<3, 64, 128, false, 1, 64, 1>(ix, sa, qp, K2, K2n, ts1, s);
 }
 
 }  // namespace snn
