@@ -182,12 +182,13 @@ __device__ __forceinline__ void tmem_fence_after() {
 }
 
 // Loads 64 consecutive FP32 accumulator columns of this warp's 32 TMEM lanes
-// (32x32b shape, 64 repetitions) and waits for them in the same statement,
-// so no use of the registers can be scheduled before the wait.
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[64]) {
+// (32x32b shape, 64 repetitions) together with their maximum (the load's max
+// reduction over the 64 columns of each lane), and waits for them in the same
+// statement, so no use of the registers can be scheduled before the wait.
+__device__ __forceinline__ void tmem_ld64_max(uint32_t taddr, uint32_t (&r)[64], float &mx) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];\n\t"
+        "tcgen05.ld.red.sync.aligned.32x32b.x64.max.f32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, %64, [%65];\n\t"
         "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
@@ -196,7 +197,8 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[64]) {
           "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
           "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
           "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
-          "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+          "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63]),
+          "=f"(mx)
         : "r"(taddr)
         : "memory");
 }
@@ -441,18 +443,19 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
 #pragma unroll 1
                 for (int g2 = 0; g2 < kGroups; g2 += 2) {
                     uint32_t rr[64];
+                    float mx;
                     const int cb0 = half * kGroups + g2;
-                    tmem_ld64(tbase + uint32_t(cb0 * 32), rr);
+                    tmem_ld64_max(tbase + uint32_t(cb0 * 32), rr, mx);
+                    // every accumulator of the 64 columns negative: all rejected
+                    // (an acceptable pair's accumulator is strictly positive)
+                    const bool any = !(mx < 0.f);
+                    if (!__any_sync(0xffffffffu, any)) continue;
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int cb = cb0 + h;
                         const uint32_t *rh = rr + 32 * h;
-                        uint32_t all = 0xffffffffu;
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) all &= rh[i];
-                        // a clear sign bit somewhere: a possible neighbour
                         uint32_t mask = 0;
-                        if (!(all >> 31)) {
+                        if (any) {
 #pragma unroll
                             for (int i = 0; i < 32; ++i) mask |= ((rh[i] >> 31) ^ 1u) << i;
                             // validity: query inside the set, row inside the
