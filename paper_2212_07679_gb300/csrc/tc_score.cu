@@ -456,8 +456,12 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                         const uint32_t *rh = rr + 32 * h;
                         uint32_t mask = 0;
                         if (any) {
+                            // bit i = sign of column i: (mask << 1) | (x >> 31) per
+                            // column, one funnel shift each, highest column first
+                            uint32_t neg = 0;
 #pragma unroll
-                            for (int i = 0; i < 32; ++i) mask |= ((rh[i] >> 31) ^ 1u) << i;
+                            for (int i = 31; i >= 0; --i) neg = __funnelshift_l(rh[i], neg, 1);
+                            mask = ~neg;
                             // validity: query inside the set, row inside the
                             // band, symmetric self-join keeps rows >= query
                             const int64_t jb = j0 + cb * 32;
