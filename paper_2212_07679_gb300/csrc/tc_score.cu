@@ -182,15 +182,13 @@ __device__ __forceinline__ void tmem_fence_after() {
 }
 
 // Loads 64 consecutive FP32 accumulator columns of this warp's 32 TMEM lanes
-// as four 16-column loads (32x32b shape), each with its maximum (the load's
-// max reduction over those 16 columns of each lane), and waits for them in the
-// same statement, so no use of the registers is scheduled before the wait.
-__device__ __forceinline__ void tmem_ld64_max4(uint32_t taddr, uint32_t (&r)[64], float (&mx)[4]) {
+// (32x32b shape, 64 repetitions) together with their maximum (the load's max
+// reduction over the 64 columns of each lane), and waits for them in the same
+// statement, so no use of the registers can be scheduled before the wait.
+__device__ __forceinline__ void tmem_ld64_max(uint32_t taddr, uint32_t (&r)[64], float &mx) {
     asm volatile(
-        "tcgen05.ld.red.sync.aligned.32x32b.x16.max.f32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, %64, [%68];\n\t"
-        "tcgen05.ld.red.sync.aligned.32x32b.x16.max.f32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, %65, [%69];\n\t"
-        "tcgen05.ld.red.sync.aligned.32x32b.x16.max.f32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47}, %66, [%70];\n\t"
-        "tcgen05.ld.red.sync.aligned.32x32b.x16.max.f32 {%48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, %67, [%71];\n\t"
+        "tcgen05.ld.red.sync.aligned.32x32b.x64.max.f32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, %64, [%65];\n\t"
         "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
@@ -200,8 +198,8 @@ __device__ __forceinline__ void tmem_ld64_max4(uint32_t taddr, uint32_t (&r)[64]
           "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
           "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
           "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63]),
-          "=f"(mx[0]), "=f"(mx[1]), "=f"(mx[2]), "=f"(mx[3])
-        : "r"(taddr), "r"(taddr + 16u), "r"(taddr + 32u), "r"(taddr + 48u)
+          "=f"(mx)
+        : "r"(taddr)
         : "memory");
 }
 
@@ -445,36 +443,34 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
 #pragma unroll 1
                 for (int g2 = 0; g2 < kGroups; g2 += 2) {
                     uint32_t rr[64];
-                    float mx[4];
+                    float mx;
                     const int cb0 = half * kGroups + g2;
-                    tmem_ld64_max4(tbase + uint32_t(cb0 * 32), rr, mx);
-                    // a 16-column group whose maximum is negative is rejected
-                    // whole (an acceptable pair's accumulator is strictly positive)
-                    uint32_t gbits = 0;
+                    tmem_ld64_max(tbase + uint32_t(cb0 * 32), rr, mx);
+                    // every accumulator of the 64 columns negative: all rejected
+                    // (an acceptable pair's accumulator is strictly positive)
+                    const bool any = !(mx < 0.f);
+                    if (!__any_sync(0xffffffffu, any)) continue;
 #pragma unroll
-                    for (int g = 0; g < 4; ++g) gbits |= uint32_t(!(mx[g] < 0.f)) << g;
-                    if (!__any_sync(0xffffffffu, gbits != 0)) continue;
-                    const int64_t jg0 = j0 + int64_t(cb0) * 32;
-#pragma unroll
-                    for (int g = 0; g < 4; ++g) {
-                        if (!__any_sync(0xffffffffu, (gbits >> g) & 1u)) continue;
+                    for (int h = 0; h < 2; ++h) {
+                        const int cb = cb0 + h;
+                        const uint32_t *rh = rr + 32 * h;
                         uint32_t mask = 0;
-                        if ((gbits >> g) & 1u) {
-                            // bit i = sign of column i: (neg << 1) | (x >> 31),
-                            // one funnel shift per column, highest column first
+                        if (any) {
+                            // bit i = sign of column i: (mask << 1) | (x >> 31) per
+                            // column, one funnel shift each, highest column first
                             uint32_t neg = 0;
 #pragma unroll
-                            for (int i = 15; i >= 0; --i) neg = __funnelshift_l(rr[16 * g + i], neg, 1);
-                            mask = ~neg & 0xffffu;
+                            for (int i = 31; i >= 0; --i) neg = __funnelshift_l(rh[i], neg, 1);
+                            mask = ~neg;
                             // validity: query inside the set, row inside the
                             // band, symmetric self-join keeps rows >= query
-                            const int64_t jb = jg0 + 16 * g;
+                            const int64_t jb = j0 + cb * 32;
                             const int64_t lim = f.band_hi - jb;
                             if (q >= a.m || lim <= 0) mask = 0;
-                            else if (lim < 16) mask &= (1u << lim) - 1u;
+                            else if (lim < 32) mask &= (1u << lim) - 1u;
                             if (a.sym) {
                                 const int64_t first = q - jb;
-                                if (first >= 16) mask = 0;
+                                if (first >= 32) mask = 0;
                                 else if (first > 0) mask &= ~((1u << first) - 1u);
                             }
                         }
@@ -493,7 +489,7 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                                 const int i = __ffs(mask) - 1;
                                 mask &= mask - 1;
                                 if (pos < (unsigned long long)a.cap)
-                                    a.surv[pos] = make_uint2(unsigned(q), unsigned(jg0 + 16 * g + i));
+                                    a.surv[pos] = make_uint2(unsigned(q), unsigned(j0 + cb * 32 + i));
                                 ++pos;
                             }
                         }
