@@ -440,6 +440,10 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                 tmem_fence_after();
                 const uint32_t tbase =
                     tmem + (uint32_t(quad * 32) << 16) + uint32_t(b * MT * BN + ht * BN);
+                // chunks away from the band end and from the queries' own rows
+                // need no per-column validity checks
+                const bool edge = (j0 + BN > f.band_hi) || (a.sym && j0 < f.q0 + int64_t(MT) * kTM);
+                const bool qvalid = q < a.m;
 #pragma unroll 1
                 for (int g2 = 0; g2 < kGroups; g2 += 2) {
                     uint32_t rr[64];
@@ -461,17 +465,19 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                             uint32_t neg = 0;
 #pragma unroll
                             for (int i = 31; i >= 0; --i) neg = __funnelshift_l(rh[i], neg, 1);
-                            mask = ~neg;
-                            // validity: query inside the set, row inside the
-                            // band, symmetric self-join keeps rows >= query
-                            const int64_t jb = j0 + cb * 32;
-                            const int64_t lim = f.band_hi - jb;
-                            if (q >= a.m || lim <= 0) mask = 0;
-                            else if (lim < 32) mask &= (1u << lim) - 1u;
-                            if (a.sym) {
-                                const int64_t first = q - jb;
-                                if (first >= 32) mask = 0;
-                                else if (first > 0) mask &= ~((1u << first) - 1u);
+                            mask = qvalid ? ~neg : 0u;
+                            if (edge) {
+                                // validity near the band end and on the diagonal of
+                                // a symmetric self-join (rows >= query only)
+                                const int64_t jb = j0 + cb * 32;
+                                const int64_t lim = f.band_hi - jb;
+                                if (lim <= 0) mask = 0;
+                                else if (lim < 32) mask &= (1u << lim) - 1u;
+                                if (a.sym) {
+                                    const int64_t first = q - jb;
+                                    if (first >= 32) mask = 0;
+                                    else if (first > 0) mask &= ~((1u << first) - 1u);
+                                }
                             }
                         }
                         const int cnt = __popc(mask);
