@@ -221,6 +221,16 @@ const char *snn_version(void);
 snn_status snn_sort_scores_noalloc(const float *alpha, int64_t n, float *alpha_sorted,
                                    int32_t *order, void *stream);
 
+/* Test-only fault injection (the paper has no counterpart): arms a one-shot
+ * fault for the next call that reaches it, to exercise failure detection
+ * without faulting the GPU.  SNN_FAULT_STALL_TC_PRODUCER makes the next
+ * tensor-core scoring launch issue no TMA loads; its consumers' bounded waits
+ * (about 2 s of SM clock) expire, the kernel frees its TMEM and exits, and the
+ * query returns SNN_ETIMEOUT with the CUDA context still usable.  0 disarms.
+ * Returns SNN_EINVAL for an unknown fault. */
+#define SNN_FAULT_STALL_TC_PRODUCER 1
+snn_status snn_test_inject(int32_t fault);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (diagnostics: the difference around a call is that call's launch count). */
 uint64_t snn_launch_count(void);

@@ -409,6 +409,23 @@ snn_status batch_query(int32_t nsets, const snn_index *const *idx, const float *
         SNN_LAUNCH(k_b_gather, unsigned(cdiv(Moos, 256)), 256, 0, s)(
             d_od, d_ooff, noos, Moos, keys, vals, q_alpha, q_order, q_raw, q_xc, q_hx, q_nrm);
         SNN_LAUNCH_CHECK();
+        // NaN/Inf and norm range of the queries, checked before any scoring
+        float *qnmax;
+        SNN_TRY(scr.alloc(&qnmax, 1));
+        SNN_CUDA(cudaMemsetAsync(qnmax, 0, sizeof(float), s));
+        SNN_LAUNCH(k_max_nonneg, std::min<unsigned>(unsigned(cdiv(Moos, 256)), 1024u), 256, 0, s)(
+            q_nrm, Moos, qnmax);
+        SNN_LAUNCH_CHECK();
+        float hq = 0.f;
+        int hb = 0;
+        SNN_CUDA(cudaMemcpyAsync(&hq, qnmax, sizeof(float), cudaMemcpyDeviceToHost, s));
+        SNN_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SNN_CUDA(cudaStreamSynchronize(s));
+        if (hb) { set_error("a query set contains NaN or Inf"); return SNN_EINVAL; }
+        if (!(hq <= kMaxCentredNorm)) {
+            set_error("a centred query norm of %g exceeds %g", (double)hq, kMaxCentredNorm);
+            return SNN_ENOTSUP;
+        }
         for (int32_t t = 0; t < nsets; ++t) {
             const int r = oos_of[t];
             if (r < 0) continue;

@@ -113,6 +113,9 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 
 constexpr float kU32 = 5.9604644775390625e-8f;   // 2^-24, FP32 unit roundoff
+// Largest centred norm accepted: products of two such norms stay far below
+// the FP32 range, so no score can overflow.
+constexpr double kMaxCentredNorm = 1e18;
 constexpr double kU64 = 1.1102230246251565e-16;  // 2^-53
 
 // ------------------------------------------------- library-wide primitives
@@ -127,6 +130,12 @@ snn_status radix_sort_pairs(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals
                             int64_t n, int end_bit, cudaStream_t s);
 
 int device_sm_count();
+
+// out = max(out, max_i x[i]) for non-negative x (snn_api.cu).
+__global__ void k_max_nonneg(const float *x, int64_t n, float *out);
+
+// One-shot fault armed by snn_test_inject (0 = none); reading clears it.
+int take_injected_fault();
 
 // Allocation-free stable sort of FP32 scores (noalloc_sort.cu).
 snn_status sort_scores_noalloc(const float *alpha, int64_t n, float *alpha_sorted, int32_t *order,

@@ -93,6 +93,11 @@ static void free_device_ptr(void *p) {
 }
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+namespace {
+std::atomic<int> g_inject{0};
+}
+int take_injected_fault() { return g_inject.exchange(0); }
+
 int device_sm_count() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -292,6 +297,11 @@ static snn_status index_build(const float *X, int64_t n, int d, int64_t ld, cuda
         }
         ix->alpha_err = hc[0];
         ix->nrm_max = hc[1];
+        if (!(hc[1] <= kMaxCentredNorm)) {
+            set_error("a centred point norm of %g exceeds %g: the FP32 and BF16 scores would "
+                      "overflow", (double)hc[1], kMaxCentredNorm);
+            TRY_IX(SNN_ENOTSUP);
+        }
     }
 #undef TRY_IX
     *out = ix;
@@ -387,6 +397,26 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         CUDA_Q(cudaMemsetAsync(eps_q, 0, sizeof(float), s));
         TRY_Q(project_sort_gather(Q, m, d, ldq, dp, ix->mu64, ix->v32, s, scr, eps_q, bad, qa,
                                   qorder, qraw, qxc, qhy, qnrm));
+        // NaN/Inf and norm range of the queries, checked before any scoring
+        float *qnmax;
+        TRY_Q(scr.alloc(&qnmax, 1));
+        CUDA_Q(cudaMemsetAsync(qnmax, 0, sizeof(float), s));
+        SNN_LAUNCH(k_max_nonneg, std::min<unsigned>(grid_for(m, 256), 1024), 256, 0, s)(qnrm, m, qnmax);
+        CUDA_Q(cudaGetLastError());
+        float hq = 0.f;
+        int hb = 0;
+        CUDA_Q(cudaMemcpyAsync(&hq, qnmax, sizeof(float), cudaMemcpyDeviceToHost, s));
+        CUDA_Q(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CUDA_Q(cudaStreamSynchronize(s));
+        if (hb) {
+            set_error("Q contains NaN or Inf");
+            return fail(SNN_EINVAL);
+        }
+        if (!(hq <= kMaxCentredNorm)) {
+            set_error("a centred query norm of %g exceeds %g: the FP32 and BF16 scores would "
+                      "overflow", (double)hq, kMaxCentredNorm);
+            return fail(SNN_ENOTSUP);
+        }
         qs.alpha = qa;
         qs.order = qorder;
         qs.raw = qraw;
@@ -783,6 +813,16 @@ const char *snn_last_error(void) { return g_err; }
 const char *snn_version(void) { return "snn-gb300 0.1 (sm_103a)"; }
 
 uint64_t snn_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+snn_status snn_test_inject(int32_t fault) {
+    clear_error();
+    if (fault != 0 && fault != SNN_FAULT_STALL_TC_PRODUCER) {
+        set_error("unknown fault %d", (int)fault);
+        return SNN_EINVAL;
+    }
+    g_inject.store(fault);
+    return SNN_OK;
+}
 
 snn_status snn_sort_scores_noalloc(const float *alpha, int64_t n, float *alpha_sorted,
                                    int32_t *order, void *stream) {

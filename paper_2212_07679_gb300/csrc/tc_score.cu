@@ -220,6 +220,7 @@ struct TcArgs {
     int64_t cap;
     unsigned long long *count;
     int *err;
+    int stall;                  // test fault: the producer issues no loads
 };
 
 struct ItemInfo {
@@ -324,7 +325,9 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
     int issued = 0, a_issued = 0;
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
-        if (lane == 0) {
+        // (a test fault withholds every load, so the consumers' bounded waits
+        // expire and the call reports SNN_ETIMEOUT)
+        if (lane == 0 && !a.stall) {
             int it = 0, itm = 0;
             for (int64_t item = blockIdx.x; item < total && !*s_abort; item += gridDim.x, ++itm) {
                 const ItemInfo f = item_info<MT>(a, item);
@@ -728,6 +731,7 @@ snn_status launch_tc(const snn_index *ix, const ScoreArgs &sa, const uint16_t *c
     a.cap = sa.cap;
     a.count = sa.count;
     a.err = sa.err;
+    a.stall = take_injected_fault() == SNN_FAULT_STALL_TC_PRODUCER ? 1 : 0;
     SNN_LAUNCH(kern, device_sm_count() * CPS, Sh::kThreads, Sh::kSmem, s)(maps[0], maps[1], maps[2],
                                                                  maps[3], maps[4], maps[5], a);
     SNN_LAUNCH_CHECK();

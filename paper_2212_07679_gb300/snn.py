@@ -75,6 +75,8 @@ def _load():
     lib.snn_last_error.restype = ctypes.c_char_p
     lib.snn_version.argtypes = []
     lib.snn_version.restype = ctypes.c_char_p
+    lib.snn_test_inject.argtypes = [ctypes.c_int32]
+    lib.snn_test_inject.restype = ctypes.c_int
     lib.snn_launch_count.argtypes = []
     lib.snn_launch_count.restype = ctypes.c_uint64
     return lib
@@ -281,6 +283,14 @@ def dbscan(X: torch.Tensor, eps: float, min_pts: int, precision: str = "fp32", s
 
 def version() -> str:
     return lib.snn_version().decode()
+
+
+SNN_FAULT_STALL_TC_PRODUCER = 1
+
+
+def test_inject(fault: int) -> None:
+    """Arms a one-shot test fault (see snn_test_inject in include/snn.h)."""
+    _check(lib.snn_test_inject(int(fault)))
 
 
 def launch_count() -> int:

@@ -73,3 +73,10 @@ def test_argument_validation_needs_no_gpu(libpath):
                           ctypes.c_void_p(16), ctypes.c_void_p(16)) == 1
     lib.snn_free(None)
     lib.snn_index_free(None)
+
+
+def test_fault_injection_arguments_need_no_gpu(libpath):
+    lib = ctypes.CDLL(libpath)
+    lib.snn_test_inject.argtypes = [ctypes.c_int32]
+    assert lib.snn_test_inject(99) == 1
+    assert lib.snn_test_inject(0) == 0
