@@ -291,3 +291,79 @@ def test_tensor_core_shapes(snn, d, spread):
     for q in (None, Q):
         got = _run(snn, P, q, R, "bf16")
         assert_csr_equal(got, oracle.brute_radius(P, q, R), f"d={d} spread={spread}")
+
+
+def _check_sampled_rows(got, P, Q, R, rows):
+    off = got.offsets.cpu().numpy()
+    idx = got.indices.cpu().numpy()
+    d2 = got.dist2.cpu().numpy()
+    Qs = P[rows] if Q is None else Q[rows]
+    ref = oracle.brute_radius(P, Qs, R)
+    for t, r in enumerate(rows):
+        ri, rd = ref.row(t)
+        a, b = off[r], off[r + 1]
+        assert np.array_equal(idx[a:b], ri), r
+        assert np.array_equal(d2[a:b].view(np.uint32), rd.view(np.uint32)), r
+
+
+@pytest.mark.slow
+def test_full_size_self_join_sampled_bf16(snn):
+    w = wl.gmm_aniso()
+    got = snn.Index(_dev(w.P)).query(None, w.R, precision="bf16")
+    rows = np.random.default_rng(25).choice(w.n, size=48, replace=False)
+    _check_sampled_rows(got, w.P, None, w.R, rows)
+    assert got.nnz == int(got.offsets[-1])
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", PRECS)
+def test_full_size_lowrank_img_sampled(snn, prec):
+    w = wl.lowrank_img()
+    got = snn.Index(_dev(w.P)).query(None, w.R, precision=prec, stats=True)
+    rows = np.random.default_rng(26).choice(w.n, size=24, replace=False)
+    _check_sampled_rows(got, w.P, None, w.R, rows)
+    # symmetry of the whole self-join
+    off = got.offsets.cpu().numpy()
+    idx = got.indices.cpu().numpy().astype(np.int64)
+    rowid = np.repeat(np.arange(w.n, dtype=np.int64), np.diff(off))
+    assert np.array_equal(np.sort(rowid * w.n + idx), np.sort(idx * w.n + rowid))
+
+
+@pytest.mark.slow
+def test_full_size_dbscan_sampled(snn):
+    w = wl.blobs3d()
+    eps, min_pts = w.R, w.extra["min_pts"]
+    labels, core = snn.dbscan(_dev(w.P), eps, min_pts)
+    labels = labels.cpu().numpy()
+    core = core.cpu().numpy().astype(bool)
+    n = w.n
+    # canonical labels: a cluster's label is one of its members, its smallest
+    lab = labels[labels >= 0]
+    assert np.all(labels[np.unique(lab)] == np.unique(lab))
+    assert np.all((labels < 0) | (labels <= np.arange(n)))
+    assert np.all(labels[core] >= 0)
+    rows = np.random.default_rng(27).choice(n, size=300, replace=False)
+    ref = oracle.brute_radius(w.P, w.P[rows], eps)
+    for t, r in enumerate(rows):
+        nb = ref.row(t)[0]
+        assert core[r] == (len(nb) >= min_pts), r
+        core_nb = nb[core[nb]]
+        if core[r]:
+            # every core neighbour is in the same cluster
+            assert np.all(labels[core_nb] == labels[r]), r
+        elif len(core_nb):
+            assert labels[r] == labels[core_nb.min()], r
+        else:
+            assert labels[r] == -1, r
+
+
+@pytest.mark.slow
+def test_full_size_ragged_batch_sampled(snn):
+    sets = wl.ragged_batch()
+    idx = [snn.Index(_dev(s.P)) for s in sets]
+    outs = snn.query_batch(idx, [_dev(s.Q) for s in sets], [s.R for s in sets])
+    rng = np.random.default_rng(28)
+    for s, got in zip(sets, outs):
+        rows = rng.choice(s.m, size=min(2, s.m), replace=False)
+        _check_sampled_rows(got, s.P, s.Q, s.R, rows)
+        assert got.m == s.m
