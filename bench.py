@@ -259,7 +259,7 @@ def run_ours(args):
     sm = float(np.mean(score_ms))
     # executed: pairs the kernel actually scored (the symmetric self-join
     # scores each unordered pair once); effective: the candidate pairs of
-    # Algorithm 2 step 4 that this replaces
+    # the per-query candidate ranges of Algorithm 2 that this replaces
     flops = 2.0 * w.d * st["band_pairs"]
     achieved = flops / (sm / 1e3) / 1e12
     effective = 2.0 * w.d * st["candidates"] / (sm / 1e3) / 1e12

@@ -81,7 +81,7 @@ typedef struct {
 /* Optional per-call counters (pass NULL to skip; a non-NULL pointer adds a
  * few small kernels and one extra stream synchronisation).
  *  candidates  sum over queries of |J_q|, the candidate range of Algorithm 2
- *              step 4 (with the rounding-safe widening);
+ *              (with the rounding-safe widening);
  *  band_pairs  pairs actually scored (query tiles score the union of their
  *              queries' ranges, Section 4's gemm over the union of J);
  *  survivors   pairs the low-precision test could not reject, all of which
@@ -202,7 +202,7 @@ const char *snn_version(void);
  * process whose device memory budget is fixed by someone else, or a latency-
  * critical loop that must never enter the allocator.  This call sorts n FP32
  * values ascending with a stable LSD radix sort -- the same sort and the same
- * result as the index build's sort of alpha (Algorithm 1, step 6) -- using
+ * result as the index build's sort of alpha (Algorithm 1) -- using
  * only a static device array compiled into the library (about 9 MB, held by
  * every GPU that loads the library until the process exits).
  *  alpha         device, n FP32 values (NaN/Inf rejected); may equal

@@ -13,7 +13,7 @@
  * k, each subtraction, product and addition rounded to nearest on its own
  * (built with -ffp-contract=off so no FMA is formed).  A point j is a
  * neighbour of q iff S(j, q) <= R2 (inclusive, as "||p_i - q|| <= R" in
- * Section 3.2 and step 6 of Algorithm 2), where R2 = fl64(R * R) is passed in.
+ * Section 3.2 and the final test of Algorithm 2), where R2 = fl64(R * R) is passed in.
  * Neighbour ids are reported in ascending order and the squared distance is
  * reported as (float)S.  The raw, uncentred points are used: centring
  * preserves distances only in exact arithmetic (Section 3.1).

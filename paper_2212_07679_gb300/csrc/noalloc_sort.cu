@@ -1,5 +1,5 @@
-// Allocation-free variant of the score sort (the radix sort of Algorithm 1,
-// step 6) for callers that cannot allocate device memory: code running while
+// Allocation-free variant of the score sort (the radix sort of the scores
+// in Algorithm 1) for callers that cannot allocate device memory: code running while
 // a CUDA graph is being captured with allocation disallowed, processes that
 // run under a fixed device-memory budget set by someone else, or real-time
 // loops that must not enter the allocator.  Its scratch lives in one

@@ -48,7 +48,7 @@ __device__ __forceinline__ int64_t upper_bound_gt(const float *__restrict__ a, i
 }
 
 // Candidate band of tile t: every data row whose score is within W of the
-// score of some query of the tile (Algorithm 2 step 4 for all of them at once).
+// score of some query of the tile (the candidate range of Algorithm 2 for all of them at once).
 // W = Wbase + eps_d + eps_q covers |alpha_j - alpha_q| <= ||v1|| ||p_j - q||
 // (Eq. (2)) for every pair the FP64 test can accept, plus the rounding bounds
 // of both computed scores.

@@ -1,10 +1,10 @@
 // Device-wide exclusive scan and stable LSD radix sort of (key, value) pairs.
 //
-// The radix sort orders the projection scores alpha_i (Algorithm 1, step 6:
-// "Sort data points X such that alpha_1 <= ... <= alpha_n"), the query
-// scores, and long neighbour rows.  8-bit digits, one upsweep (per-tile digit
-// histogram), one scan of the digit-major histogram, one downsweep that
-// ranks keys stably inside each tile with warp match/ballot and scatters.
+// The radix sort orders the projection scores alpha_i ascending (the sort
+// of the index phase, Algorithm 1), the query scores, and long neighbour
+// rows.  8-bit digits, one upsweep (per-tile digit histogram), one scan of
+// the digit-major histogram, one downsweep that ranks keys stably inside
+// each tile with warp match/ballot and scatters.
 #include "common.cuh"
 
 namespace snn {

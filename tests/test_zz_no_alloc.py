@@ -4,7 +4,7 @@ snn_sort_scores_noalloc serves callers that may not allocate device memory
 (for example code running under a stream capture that forbids allocation, or
 a process whose device memory budget is fixed elsewhere): it sorts with a
 static scratch array compiled into the library.  Its result must equal the
-sort the index build performs (Algorithm 1, step 6) on the same scores: same
+sort the index build performs (the score sort of Algorithm 1) on the same scores: same
 sorted values and the same stable permutation, bit for bit.  The file is
 collected last so that a failure here leaves every other test already run;
 it also passes on its own in a fresh process."""
