@@ -109,26 +109,50 @@ def workload_config(args, w, extra=None):
     return cfg
 
 
-def cpu_oracle_sample(w, budget_s=15.0, seed=7):
-    """Times the FP64 brute-force oracle on a bounded random query sample."""
+def cpu_oracle_sample(w, budget_s=15.0, seed=7, gpu_csr=None):
+    """Times the FP64 brute-force oracle on a bounded random query sample.
+
+    With ``gpu_csr`` = (offsets, indices, dist2) host arrays of the GPU
+    result, the sampled rows are also compared with the oracle's: neighbour
+    sets (must be identical) and the largest relative dist2 error."""
     import oracle
     rng = np.random.default_rng(seed)
     order = rng.permutation(w.m)
     Qall = w.P if w.Q is None else w.Q
     done, t_used, size = 0, 0.0, 16
+    mism, max_rel, checked_pairs = 0, 0.0, 0
     while t_used < budget_s and done < w.m:
         rows = order[done:done + size]
         t0 = time.perf_counter()
-        oracle.brute_radius(w.P, Qall[rows], w.R)
+        ref = oracle.brute_radius(w.P, Qall[rows], w.R)
         dt = time.perf_counter() - t0
         t_used += dt
         done += len(rows)
+        if gpu_csr is not None:
+            off, ids, d2 = gpu_csr
+            for k, r in enumerate(rows):
+                a, b = ref.offsets[k], ref.offsets[k + 1]
+                ga, gb = off[r], off[r + 1]
+                if gb - ga != b - a or not np.array_equal(ids[ga:gb], ref.indices[a:b]):
+                    mism += 1
+                    continue
+                s_ref = ref.dist2[a:b].astype(np.float64)
+                s_gpu = d2[ga:gb].astype(np.float64)
+                rel = np.abs(s_gpu - s_ref) / np.maximum(s_ref, 1e-300)
+                rel[(s_ref == 0) & (s_gpu == 0)] = 0.0
+                if rel.size:
+                    max_rel = max(max_rel, float(rel.max()))
+                checked_pairs += b - a
         if dt < budget_s / 8:
             size *= 2
-    return {"value": done / t_used, "unit": "queries/s", "cores": oracle.oracle_threads(),
-            "kind": "oracle",
-            "sample": f"{done} random queries of the {w.m} against all {w.n} points "
-                      f"(FP64 brute force, {t_used:.1f} s)"}
+    out = {"value": done / t_used, "unit": "queries/s", "cores": oracle.oracle_threads(),
+           "kind": "oracle",
+           "sample": f"{done} random queries of the {w.m} against all {w.n} points "
+                     f"(FP64 brute force, {t_used:.1f} s)"}
+    if gpu_csr is not None:
+        out["parity"] = {"rows": int(done), "pairs": int(checked_pairs),
+                         "rows_with_different_sets": int(mism), "max_rel_dist2_err": max_rel}
+    return out
 
 
 def run_reference(args):
@@ -172,8 +196,10 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    def step(stats=True):
+    def step(stats=True, e_mid=None):
         ix = snn.Index(X)
+        if e_mid is not None:
+            e_mid.record(stream)
         out = ix.query(None, w.R, precision=args.precision, stats=stats)
         return ix, out
 
@@ -182,7 +208,8 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
-    per_step, score_ms, stats_list = [], [], []
+    per_step, index_ms, score_ms, stats_list = [], [], [], []
+    last_out = None
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -191,15 +218,19 @@ def run_ours(args):
     for _ in range(args.steps):
         flush.fill_(1)
         e0 = torch.cuda.Event(enable_timing=True)
+        em = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        ix, out = step(stats=True)
+        ix, out = step(stats=True, e_mid=em)
         e1.record(stream)
         e1.synchronize()
         per_step.append(e0.elapsed_time(e1))
+        index_ms.append(e0.elapsed_time(em))
         score_ms.append(out.stats["ms_score"])
         stats_list.append(out.stats)
-        del ix, out
+        del ix
+        last_out = out
+        del out
     torch.cuda.synchronize()
     launches = snn.launch_count() - launches0
     clk = clocks.stop()
@@ -295,6 +326,7 @@ def run_ours(args):
         "nnz": st["nnz"], "candidates": st["candidates"], "band_pairs": st["band_pairs"],
         "survivors": st["survivors"], "exact_fp64": st["exact_fp64"],
         "recheck_fraction": (directed_surv - st["nnz"]) / max(1, st["candidates"]),
+        "index_build_ms": float(np.mean(index_ms)),
         "phase_ms": {k: st[k] for k in ("ms_prep", "ms_score", "ms_recheck", "ms_csr")},
         "roofline": roofline,
         "clocks": clk,
@@ -306,7 +338,9 @@ def run_ours(args):
     }
     if rank == 0:
         if args.cpu_baseline:
-            line["cpu_baseline"] = cpu_oracle_sample(w, budget_s=args.ref_budget)
+            csr_h = (last_out.offsets.cpu().numpy(), last_out.indices.cpu().numpy(),
+                     last_out.dist2.cpu().numpy())
+            line["cpu_baseline"] = cpu_oracle_sample(w, budget_s=args.ref_budget, gpu_csr=csr_h)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -175,7 +175,12 @@ typedef struct {
     const float *alpha;      /* n, sorted FP32 scores                       */
     const int32_t *order;    /* n, original id of each sorted position      */
     const float *points;     /* n x dp, raw points in sorted order          */
-    double alpha_err;        /* bound on |computed alpha_i - exact alpha_i| */
+    double alpha_err;        /* bound on |computed alpha_i - exact alpha_i|,
+                                alpha_i = (p_i - centre) . v1 exactly       */
+    const float *centre;     /* d, the centre c = fl32(mu) every point and
+                                query is shifted by before scoring (any fixed
+                                centre leaves distances unchanged,
+                                Section 3.1)                                 */
 } snn_index_view;
 
 snn_status snn_index_get_view(const snn_index *idx, snn_index_view *view);

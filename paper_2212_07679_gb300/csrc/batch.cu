@@ -30,7 +30,7 @@ __device__ __forceinline__ int find_set(const int64_t *__restrict__ off, int nse
 struct OosDesc {
     const float *Q;        // caller's queries
     int64_t ldq;
-    const double *mu64;
+    const float *cvec;     // the index's FP32 centre c = fl32(mu)
     const float *v32;
     int d, dp;
     int set;               // batch set number
@@ -52,7 +52,7 @@ __global__ void k_b_project(const OosDesc *__restrict__ od, const int64_t *__res
     for (int k = 0; k < o.d; ++k) {
         const float p = q[k];
         badl |= !isfinite(p);
-        const float x = (float)((double)p - o.mu64[k]);
+        const float x = p - o.cvec[k];
         a = fmaf(x, o.v32[k], a);
         b = fmaf(fabsf(x), fabsf(o.v32[k]), b);
     }
@@ -84,7 +84,7 @@ __global__ void k_b_gather(const OosDesc *__restrict__ od, const int64_t *__rest
         float pv = 0.f, x = 0.f;
         if (k < o.d) {
             pv = q[k];
-            x = (float)((double)pv - o.mu64[k]);
+            x = pv - o.cvec[k];
         }
         raw[k] = pv;
         xc[k] = x;
@@ -350,7 +350,7 @@ snn_status batch_query(int32_t nsets, const snn_index *const *idx, const float *
             OosDesc o;
             o.Q = Q[t];
             o.ldq = ldq_in[t];
-            o.mu64 = ix->mu64;
+            o.cvec = ix->mu32;
             o.v32 = ix->v32;
             o.d = ix->d;
             o.dp = ix->dp;

@@ -1,10 +1,12 @@
 // Index phase kernels (Algorithm 1, Section 3.1):
-//   column means mu (FP64 accumulation, NaN/Inf check),
-//   centred Gram matrix C = (X - mu)^T (X - mu) for the first principal
+//   column means mu (float-float per thread, FP64 across threads, NaN/Inf
+//   check) and the FP32 centre c = fl32(mu),
+//   centred Gram matrix C = (X - c)^T (X - c) for the first principal
 //   direction (Eq. (1): v1 is the dominant right singular vector of X, i.e.
-//   the dominant eigenvector of C),
-//   v1 by repeated squaring of C / trace(C) followed by FP64 power steps and
-//   FP64 normalisation,
+//   the dominant eigenvector of C) on CUDA cores for d <= 64 (larger d: the
+//   tensor-core kernels of gram_tc.cu),
+//   v1 for d <= 64 by repeated squaring of C / trace(C) in one CTA followed by
+//   FP64 power steps and FP64 normalisation,
 //   scores alpha_i = x_i^T v1 with a per-point rounding bound,
 //   gather of the sorted copies and halved squared norms xbar_i = x_i^T x_i/2.
 #include "index_kernels.cuh"
@@ -12,9 +14,13 @@
 namespace snn {
 
 // ------------------------------------------------------------ mean (K1)
-// Block b sums rows [b*rows, (b+1)*rows) of every column into part[b][c]
-// (FP64, fixed order: deterministic).  Thread (cx, ry) owns columns
-// cx, cx+TX, ... and rows ry, ry+TY, ...
+// Block (rb, cb) sums rows [rb*rows, (rb+1)*rows) of columns
+// [cb*TX, cb*TX + TX) into part[rb][c] (deterministic fixed order).  Each
+// thread keeps a float-float (hi, lo) sum of its rows: TwoSum of hi and the
+// element, the error added to lo, then a FastTwoSum renormalisation, so the
+// per-thread sum is accurate to a few units of 2^-48 of the sum of |x|; the
+// threads' sums are then combined in FP64.  Thread (cx, ry) owns column cx
+// and rows ry, ry+TY, ...
 __global__ void k_colsum_partial(const float *__restrict__ X, int64_t n, int d, int64_t ld,
                                  int64_t rows, double *__restrict__ part, int *__restrict__ bad) {
     extern __shared__ double sh[];   // [TY][TX]
@@ -22,31 +28,36 @@ __global__ void k_colsum_partial(const float *__restrict__ X, int64_t n, int d, 
     const int TY = blockDim.x / TX;
     const int t = threadIdx.x;
     const int cx = t % TX, ry = t / TX;
+    const int c = blockIdx.y * TX + cx;
     const int64_t r0 = int64_t(blockIdx.x) * rows;
     const int64_t r1 = min(n, r0 + rows);
     int badl = 0;
-    for (int c0 = 0; c0 < d; c0 += TX) {
+    float hi = 0.f, lo = 0.f;
+    if (ry < TY && c < d) {
+        for (int64_t r = r0 + ry; r < r1; r += TY) {
+            const float x = X[r * ld + c];
+            badl |= !isfinite(x);
+            const float s = hi + x;                       // TwoSum(hi, x)
+            const float bb = s - hi;
+            const float e = (hi - (s - bb)) + (x - bb);
+            const float l = lo + e;
+            hi = s + l;                                   // FastTwoSum(s, l)
+            lo = l - (hi - s);
+        }
+    }
+    if (ry < TY) sh[ry * TX + cx] = (double)hi + (double)lo;
+    __syncthreads();
+    if (t < TX && blockIdx.y * TX + t < d) {
         double acc = 0.0;
-        const int c = c0 + cx;
-        if (ry < TY && c < d) {
-            for (int64_t r = r0 + ry; r < r1; r += TY) {
-                float x = X[r * ld + c];
-                badl |= !isfinite(x);
-                acc += (double)x;
-            }
-        }
-        if (ry < TY) sh[ry * TX + cx] = acc;
-        __syncthreads();
-        if (t < TX && c0 + t < d) {
-            double s = 0.0;
-            for (int y = 0; y < TY; ++y) s += sh[y * TX + t];
-            part[int64_t(blockIdx.x) * d + c0 + t] = s;
-        }
-        __syncthreads();
+        for (int y = 0; y < TY; ++y) acc += sh[y * TX + t];
+        part[int64_t(blockIdx.x) * d + blockIdx.y * TX + t] = acc;
     }
     if (badl) atomicOr(bad, 1);
 }
 
+// mu = column means (FP64); the index centres every point with the FP32
+// vector c = fl32(mu) (any fixed centre leaves distances unchanged,
+// Section 3.1), so centring is one exact-input FP32 subtraction per value.
 __global__ void k_mean_final(const double *__restrict__ part, int nb, int d, int64_t n,
                              double *__restrict__ mu64, float *__restrict__ mu32) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -59,45 +70,42 @@ __global__ void k_mean_final(const double *__restrict__ part, int nb, int d, int
 }
 
 // ------------------------------------------------------------ Gram (K2)
-// Tiles of 64 x 64 entries of C over a chunk of rows; only tiles with
-// tj >= ti are computed (C is symmetric).  part[chunk][i][j], FP32 sums of
-// FP32 products of centred values x = fl32(p - mu).
-constexpr int kGT = 64;
-constexpr int kGK = 16;
+// Small d (d <= TG <= 64): the whole d x d matrix is one TG x TG tile.
+// (TG/4)^2 threads each own a 4 x 4 block of C; the block's 256 threads form
+// 256 / (TG/4)^2 row groups that take interleaved rows of a staged chunk of
+// centred rows x = fl32(p - c).  Row groups are summed in shared memory and
+// the block writes its partial C (FP32 sums over its rows) to part[b].
+constexpr int kGramStageRows = 64;
 
-__global__ void __launch_bounds__(256)
-k_gram_partial(const float *__restrict__ X, int64_t n, int d, int64_t ld,
-               const float *__restrict__ mu32, int64_t rows, int ntile,
-               float *__restrict__ part) {
-    const int ti = blockIdx.x / ntile, tj = blockIdx.x % ntile;
-    if (tj < ti) return;
-    __shared__ float A[kGK][kGT + 4];
-    __shared__ float B[kGK][kGT + 4];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int64_t r0 = int64_t(blockIdx.y) * rows;
+template <int TG>
+__device__ __forceinline__ void gram_small(const float *__restrict__ X, int64_t n, int d,
+                                           int64_t ld, const float *__restrict__ cvec,
+                                           int64_t rows, float *__restrict__ part) {
+    constexpr int TT = TG / 4;                  // threads per tile edge
+    constexpr int RG = 256 / (TT * TT);         // row groups
+    constexpr int LD = TG + 4;
+    __shared__ float S[kGramStageRows][LD];
+    __shared__ float red[RG > 1 ? RG : 1][RG > 1 ? TG : 1][RG > 1 ? TG + 1 : 1];
+    const int tt = threadIdx.x % (TT * TT), g = threadIdx.x / (TT * TT);
+    const int ty = tt / TT, tx = tt % TT;
+    const int64_t r0 = int64_t(blockIdx.x) * rows;
     const int64_t r1 = min(n, r0 + rows);
     float acc[4][4] = {};
-    for (int64_t rb = r0; rb < r1; rb += kGK) {
-        for (int e = threadIdx.x; e < kGK * kGT; e += 256) {
-            const int kk = e / kGT, c = e % kGT;
-            const int64_t r = rb + kk;
-            const int ci = ti * kGT + c, cj = tj * kGT + c;
-            float a = 0.f, b = 0.f;
-            if (r < r1) {
-                if (ci < d) a = X[r * ld + ci] - mu32[ci];
-                if (cj < d) b = X[r * ld + cj] - mu32[cj];
-            }
-            A[kk][c] = a;
-            B[kk][c] = b;
+    for (int64_t rb = r0; rb < r1; rb += kGramStageRows) {
+        const int nr = int(min(int64_t(kGramStageRows), r1 - rb));
+        for (int e = threadIdx.x; e < kGramStageRows * TG; e += 256) {
+            const int rr = e / TG, cc = e % TG;
+            float x = 0.f;
+            if (rr < nr && cc < d) x = X[(rb + rr) * ld + cc] - cvec[cc];
+            S[rr][cc] = x;
         }
         __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < kGK; ++kk) {
+        for (int rr = g; rr < nr; rr += RG) {
             float a[4], b[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                a[u] = A[kk][ty * 4 + u];
-                b[u] = B[kk][tx * 4 + u];
+                a[u] = S[rr][ty * 4 + u];
+                b[u] = S[rr][tx * 4 + u];
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
@@ -106,14 +114,44 @@ k_gram_partial(const float *__restrict__ X, int64_t n, int d, int64_t ld,
         }
         __syncthreads();
     }
-    float *out = part + int64_t(blockIdx.y) * d * d;
+    float *out = part + int64_t(blockIdx.x) * d * d;
+    if constexpr (RG > 1) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            const int i = ti * kGT + ty * 4 + u, j = tj * kGT + tx * 4 + w;
-            if (i < d && j < d) out[int64_t(i) * d + j] = acc[u][w];
+            for (int w = 0; w < 4; ++w) red[g][ty * 4 + u][tx * 4 + w] = acc[u][w];
+        __syncthreads();
+        for (int e = threadIdx.x; e < d * d; e += 256) {
+            const int i = e / d, j = e % d;
+            float v = 0.f;
+            for (int q = 0; q < RG; ++q) v += red[q][i][j];
+            out[e] = v;
         }
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const int i = ty * 4 + u, j = tx * 4 + w;
+                if (i < d && j < d) out[int64_t(i) * d + j] = acc[u][w];
+            }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_gram_small16(const float *X, int64_t n, int d, int64_t ld, const float *cvec, int64_t rows,
+               float *part) {
+    gram_small<16>(X, n, d, ld, cvec, rows, part);
+}
+__global__ void __launch_bounds__(256)
+k_gram_small32(const float *X, int64_t n, int d, int64_t ld, const float *cvec, int64_t rows,
+               float *part) {
+    gram_small<32>(X, n, d, ld, cvec, rows, part);
+}
+__global__ void __launch_bounds__(256)
+k_gram_small64(const float *X, int64_t n, int d, int64_t ld, const float *cvec, int64_t rows,
+               float *part) {
+    gram_small<64>(X, n, d, ld, cvec, rows, part);
 }
 
 // C64[i][j] = sum over chunks (FP64), upper triangle mirrored.
@@ -238,102 +276,6 @@ k_pc_small(const double *__restrict__ C, int d, double *__restrict__ v64, float 
     }
 }
 
-// Large d: the same steps with grid-wide kernels.
-__global__ void k_pc_init(const double *__restrict__ C, int d, float *__restrict__ M,
-                          double *__restrict__ trace_out) {
-    // one block computes trace(C), then the grid-stride scaling happens in a
-    // second launch (k_scale_by_trace)
-    __shared__ double red[32];
-    double part = 0.0;
-    for (int i = threadIdx.x; i < d; i += blockDim.x) part += C[int64_t(i) * d + i];
-    const double tr = block_sum_d(part, red);
-    if (threadIdx.x == 0) *trace_out = tr;
-}
-
-__global__ void k_scale_from_double(const double *__restrict__ C, int64_t count,
-                                    const double *__restrict__ tr, float *__restrict__ M) {
-    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (e >= count) return;
-    const double t = *tr;
-    M[e] = (t > 0.0 && isfinite(t)) ? (float)(C[e] / t) : 0.f;
-}
-
-// T = M * M (d x d, FP32), 64 x 64 tiles, 4 x 4 per thread.
-__global__ void __launch_bounds__(256)
-k_square(const float *__restrict__ M, int d, float *__restrict__ T) {
-    __shared__ float As[kGK][kGT + 4];
-    __shared__ float Bs[kGK][kGT + 4];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int i0 = blockIdx.y * kGT, j0 = blockIdx.x * kGT;
-    float acc[4][4] = {};
-    for (int k0 = 0; k0 < d; k0 += kGK) {
-        for (int e = threadIdx.x; e < kGK * kGT; e += 256) {
-            const int kk = e / kGT, c = e % kGT;
-            const int k = k0 + kk;
-            As[kk][c] = (k < d && i0 + c < d) ? M[int64_t(i0 + c) * d + k] : 0.f;
-            Bs[kk][c] = (k < d && j0 + c < d) ? M[int64_t(k) * d + j0 + c] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < kGK; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                a[u] = As[kk][ty * 4 + u];
-                b[u] = Bs[kk][tx * 4 + u];
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int w = 0; w < 4; ++w) acc[u][w] = fmaf(a[u], b[w], acc[u][w]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            const int i = i0 + ty * 4 + u, j = j0 + tx * 4 + w;
-            if (i < d && j < d) T[int64_t(i) * d + j] = acc[u][w];
-        }
-}
-
-// M = T / trace(T) (one block computes the trace into *scale first).
-__global__ void k_trace_f(const float *__restrict__ T, int d, float *__restrict__ scale) {
-    __shared__ float red[32];
-    float part = 0.f;
-    for (int i = threadIdx.x; i < d; i += blockDim.x) part += T[int64_t(i) * d + i];
-    const float tr = block_sum_f(part, red);
-    if (threadIdx.x == 0) *scale = (tr > 0.f && isfinite(tr)) ? 1.f / tr : 0.f;
-}
-
-__global__ void k_scale_f(const float *__restrict__ T, int64_t count, const float *__restrict__ scale,
-                          float *__restrict__ M) {
-    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (e >= count) return;
-    const float s = *scale;
-    // a zero scale (vanished trace) keeps the previous M
-    if (s > 0.f) M[e] = T[e] * s;
-}
-
-__global__ void k_pick_column(const float *__restrict__ M, int d, const double *__restrict__ tr,
-                              double *__restrict__ v) {
-    __shared__ int jbest;
-    if (threadIdx.x == 0) {
-        int jb = 0;
-        float best = -1.f;
-        for (int j = 0; j < d; ++j) {
-            float x = M[int64_t(j) * d + j];
-            if (x > best) { best = x; jb = j; }
-        }
-        jbest = jb;
-    }
-    __syncthreads();
-    const bool degenerate = !(*tr > 0.0) || !isfinite(*tr);
-    for (int i = threadIdx.x; i < d; i += blockDim.x)
-        v[i] = degenerate ? (i == 0 ? 1.0 : 0.0) : (double)M[int64_t(i) * d + jbest];
-}
-
 // w = C v (FP64), one warp per row.
 __global__ void k_matvec64(const double *__restrict__ C, int d, const double *__restrict__ v,
                            double *__restrict__ w) {
@@ -362,13 +304,14 @@ __global__ void k_normalise64(const double *__restrict__ w, int d, double *__res
 }
 
 // ------------------------------------------------------ projection (K4)
-// alpha_i = fl32(sum_k x_k v_k) with x_k = fl32(p_ik - mu_k) and FP32 FMA
-// accumulation.  |alpha_hat - alpha| <= (d+4) u32 sum_k |x_k||v_k| (1.01):
-// centring (u32 + 2 u64)|x_k|, v rounding u32 |v_k|, accumulation gamma_d.
+// alpha_i = fl32(sum_k x_k v_k) with x_k = fl32(p_ik - c_k) (c = fl32(mu)) and
+// FP32 FMA accumulation.  |alpha_hat - alpha| <= (d+4) u32 sum_k |x_k||v_k|
+// (1.01): centring u32 |x_k|, v rounding u32 |v_k|, accumulation gamma_d,
+// where alpha is the exact (p_i - c) . v1.
 // Writes the sort key of alpha and the point id; *eps_max gets the largest
 // bound.  One thread per point (d <= 32) or one warp per point.
 __global__ void k_project(const float *__restrict__ X, int64_t n, int d, int64_t ld,
-                          const double *__restrict__ mu64, const float *__restrict__ v32,
+                          const float *__restrict__ cvec, const float *__restrict__ v32,
                           uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
                           float *__restrict__ eps_max, int *__restrict__ bad) {
     const bool warp_mode = d > 32;
@@ -382,7 +325,7 @@ __global__ void k_project(const float *__restrict__ X, int64_t n, int d, int64_t
     for (int k = lane; k < d; k += step) {
         const float p = X[i * ld + k];
         badl |= !isfinite(p);
-        const float x = (float)((double)p - mu64[k]);
+        const float x = p - cvec[k];
         a = fmaf(x, v32[k], a);
         b = fmaf(fabsf(x), fabsf(v32[k]), b);
     }
@@ -404,11 +347,11 @@ __global__ void k_project(const float *__restrict__ X, int64_t n, int d, int64_t
 
 // ---------------------------------------------------------- gather (K6)
 // Sorted position r takes point order[r]: raw row (zero-padded to dp),
-// centred FP32 row, score, halved squared norm xbar = fl32(sum x_k^2)/2 and an
+// centred FP32 row x = fl32(p - c), score, halved squared norm xbar = fl32(sum x_k^2)/2 and an
 // upper bound on ||x||.  Padding entries are zero in both copies.
 __global__ void k_gather(const uint32_t *__restrict__ skeys, const uint32_t *__restrict__ order,
                          const float *__restrict__ X, int64_t n, int d, int64_t ld, int dp,
-                         const double *__restrict__ mu64, float *__restrict__ alpha,
+                         const float *__restrict__ cvec, float *__restrict__ alpha,
                          int32_t *__restrict__ order_out, float *__restrict__ praw,
                          float *__restrict__ xc, float *__restrict__ hx,
                          float *__restrict__ nrm) {
@@ -424,7 +367,7 @@ __global__ void k_gather(const uint32_t *__restrict__ skeys, const uint32_t *__r
         float p = 0.f, x = 0.f;
         if (k < d) {
             p = X[i * ld + k];
-            x = (float)((double)p - mu64[k]);
+            x = p - cvec[k];
         }
         praw[r * dp + k] = p;
         xc[r * dp + k] = x;

@@ -8,26 +8,35 @@ __global__ void k_colsum_partial(const float *X, int64_t n, int d, int64_t ld, i
                                  double *part, int *bad);
 __global__ void k_mean_final(const double *part, int nb, int d, int64_t n, double *mu64,
                              float *mu32);
-__global__ void k_gram_partial(const float *X, int64_t n, int d, int64_t ld, const float *mu32,
-                               int64_t rows, int ntile, float *part);
+// Small-d Gram partials for d <= 16 / 32 / 64 (one TG x TG tile per block).
+__global__ void k_gram_small16(const float *X, int64_t n, int d, int64_t ld, const float *cvec,
+                               int64_t rows, float *part);
+__global__ void k_gram_small32(const float *X, int64_t n, int d, int64_t ld, const float *cvec,
+                               int64_t rows, float *part);
+__global__ void k_gram_small64(const float *X, int64_t n, int d, int64_t ld, const float *cvec,
+                               int64_t rows, float *part);
 __global__ void k_gram_reduce(const float *part, int nchunk, int d, double *C);
 __global__ void k_pc_small(const double *C, int d, double *v64, float *v32);
-__global__ void k_pc_init(const double *C, int d, float *M, double *trace_out);
-__global__ void k_scale_from_double(const double *C, int64_t count, const double *tr, float *M);
-__global__ void k_square(const float *M, int d, float *T);
-__global__ void k_trace_f(const float *T, int d, float *scale);
-__global__ void k_scale_f(const float *T, int64_t count, const float *scale, float *M);
-__global__ void k_pick_column(const float *M, int d, const double *tr, double *v);
 __global__ void k_matvec64(const double *C, int d, const double *v, double *w);
 __global__ void k_normalise64(const double *w, int d, double *v, float *v32, int final_);
-__global__ void k_project(const float *X, int64_t n, int d, int64_t ld, const double *mu64,
+__global__ void k_project(const float *X, int64_t n, int d, int64_t ld, const float *cvec,
                           const float *v32, uint32_t *keys, uint32_t *vals, float *eps_max,
                           int *bad);
 __global__ void k_gather(const uint32_t *skeys, const uint32_t *order, const float *X, int64_t n,
-                         int d, int64_t ld, int dp, const double *mu64, float *alpha,
+                         int d, int64_t ld, int dp, const float *cvec, float *alpha,
                          int32_t *order_out, float *praw, float *xc, float *hx, float *nrm);
 
 constexpr int kPcSmallMaxD = 64;
-constexpr int kGramTile = 64;
+
+// Tensor-core Gram matrix and first direction for d > kPcSmallMaxD
+// (gram_tc.cu).  gram_tc: C (d x d, FP64, full) = sum_r x_r x_r^T over the
+// centred rows x = fl32(p - c).  first_direction_tc: v1 from C (FP64 and FP32
+// copies).  Stream-ordered; a bounded wait that expires sets *err (device)
+// to nonzero, which the caller reads with its other device flags.  Scratch
+// memory comes from `scr`.
+snn_status gram_tc(const float *X, int64_t n, int d, int64_t ld, const float *cvec, double *C,
+                   int *err, cudaStream_t s, Scratch &scr);
+snn_status first_direction_tc(const double *C, int d, double *v64, float *v32, int *err,
+                              cudaStream_t s, Scratch &scr);
 
 }  // namespace snn

@@ -135,7 +135,7 @@ static void index_release(snn_index *ix) {
 
 // ---------------------------------------------------------- index build
 static snn_status project_sort_gather(const float *X, int64_t n, int d, int64_t ld, int dp,
-                                      const double *mu64, const float *v32, cudaStream_t s,
+                                      const float *cvec, const float *v32, cudaStream_t s,
                                       Scratch &scr, float *eps_out, int *bad, float *alpha,
                                       int32_t *order, float *praw, float *xc, float *hx,
                                       float *nrm) {
@@ -145,11 +145,11 @@ static snn_status project_sort_gather(const float *X, int64_t n, int d, int64_t 
     SNN_TRY(scr.alloc(&ka, n));
     SNN_TRY(scr.alloc(&va, n));
     const int64_t pthreads = d > 32 ? n * 32 : n;
-    SNN_LAUNCH(k_project, grid_for(pthreads, 256), 256, 0, s)(X, n, d, ld, mu64, v32, keys, vals,
+    SNN_LAUNCH(k_project, grid_for(pthreads, 256), 256, 0, s)(X, n, d, ld, cvec, v32, keys, vals,
                                                       eps_out, bad);
     SNN_LAUNCH_CHECK();
     SNN_TRY(radix_sort_pairs<uint32_t>(keys, vals, ka, va, n, 32, s));
-    SNN_LAUNCH(k_gather, grid_for(pthreads, 256), 256, 0, s)(keys, vals, X, n, d, ld, dp, mu64, alpha,
+    SNN_LAUNCH(k_gather, grid_for(pthreads, 256), 256, 0, s)(keys, vals, X, n, d, ld, dp, cvec, alpha,
                                                      order, praw, xc, hx, nrm);
     SNN_LAUNCH_CHECK();
     return SNN_OK;
@@ -164,8 +164,8 @@ __global__ void k_max_nonneg(const float *__restrict__ x, int64_t n, float *__re
     if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
 }
 
-static snn_status first_direction(const double *C, int d, double *v64, float *v32, cudaStream_t s,
-                                  Scratch &scr) {
+static snn_status first_direction(const double *C, int d, double *v64, float *v32, int *err,
+                                  cudaStream_t s, Scratch &scr) {
     if (d <= kPcSmallMaxD) {
         const size_t smem = (2 * d + 32) * sizeof(double) + 32 * sizeof(float) +
                             2 * size_t(d) * d * sizeof(float);
@@ -173,40 +173,7 @@ static snn_status first_direction(const double *C, int d, double *v64, float *v3
         SNN_LAUNCH_CHECK();
         return SNN_OK;
     }
-    const int64_t dd = int64_t(d) * d;
-    float *M, *T, *scale;
-    double *tr, *w;
-    SNN_TRY(scr.alloc(&M, dd));
-    SNN_TRY(scr.alloc(&T, dd));
-    SNN_TRY(scr.alloc(&scale, 1));
-    SNN_TRY(scr.alloc(&tr, 1));
-    SNN_TRY(scr.alloc(&w, d));
-    SNN_LAUNCH(k_pc_init, 1, 1024, 0, s)(C, d, M, tr);
-    SNN_LAUNCH_CHECK();
-    SNN_LAUNCH(k_scale_from_double, grid_for(dd, 256), 256, 0, s)(C, dd, tr, M);
-    SNN_LAUNCH_CHECK();
-    const int nt = (int)cdiv(d, kGramTile);
-    for (int it = 0; it < 12; ++it) {
-        SNN_LAUNCH(k_square, dim3(nt, nt), 256, 0, s)(M, d, T);
-        SNN_LAUNCH_CHECK();
-        SNN_LAUNCH(k_trace_f, 1, 1024, 0, s)(T, d, scale);
-        SNN_LAUNCH_CHECK();
-        SNN_LAUNCH(k_scale_f, grid_for(dd, 256), 256, 0, s)(T, dd, scale, M);
-        SNN_LAUNCH_CHECK();
-    }
-    SNN_LAUNCH(k_pick_column, 1, 256, 0, s)(M, d, tr, v64);
-    SNN_LAUNCH_CHECK();
-    for (int it = 0; it < 4; ++it) {
-        SNN_LAUNCH(k_matvec64, grid_for(int64_t(d) * 32, 256), 256, 0, s)(C, d, v64, w);
-        SNN_LAUNCH_CHECK();
-        SNN_LAUNCH(k_normalise64, 1, 1024, 0, s)(w, d, v64, v32, 0);
-        SNN_LAUNCH_CHECK();
-    }
-    // final FP64 normalisation (also writes the FP32 copy)
-    SNN_CUDA(cudaMemcpyAsync(w, v64, d * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    SNN_LAUNCH(k_normalise64, 1, 1024, 0, s)(w, d, v64, v32, 1);
-    SNN_LAUNCH_CHECK();
-    return SNN_OK;
+    return first_direction_tc(C, d, v64, v32, err, s, scr);
 }
 
 static snn_status index_build(const float *X, int64_t n, int d, int64_t ld, cudaStream_t s,
@@ -245,55 +212,66 @@ static snn_status index_build(const float *X, int64_t n, int d, int64_t ld, cuda
     TRY_IX(dev_alloc(&ix->dconst, 4));
     {
         Scratch scr(s);
-        int *bad;
-        TRY_IX(scr.alloc(&bad, 1));
-        if (cudaMemsetAsync(bad, 0, sizeof(int), s) != cudaSuccess ||
+        int *bad;   // [0] NaN/Inf seen, [1] a bounded tensor-core wait expired
+        TRY_IX(scr.alloc(&bad, 2));
+        if (cudaMemsetAsync(bad, 0, 2 * sizeof(int), s) != cudaSuccess ||
             cudaMemsetAsync(ix->dconst, 0, 4 * sizeof(float), s) != cudaSuccess) {
             set_error("cudaMemsetAsync failed");
             TRY_IX(SNN_ECUDA);
         }
-        // K1: column means
-        const int64_t nb = std::min<int64_t>(cdiv(n, 2048), 1024);
+        // K1: column means (2-D grid: column chunks x row ranges, about four
+        // blocks per SM)
+        const int TX = d < 32 ? d : 32, TY = 256 / TX;
+        const int64_t ncb = cdiv(d, TX);
+        const int64_t nb = std::max<int64_t>(
+            1, std::min<int64_t>(cdiv(4 * device_sm_count(), ncb), cdiv(n, 64)));
         const int64_t rows = cdiv(n, nb);
         double *part;
         TRY_IX(scr.alloc(&part, size_t(nb) * d));
-        const int TX = d < 32 ? d : 32, TY = 256 / TX;
-        SNN_LAUNCH(k_colsum_partial, (unsigned)nb, TX * TY, TX * TY * sizeof(double), s)(X, n, d, ld, rows,
-                                                                               part, bad);
+        SNN_LAUNCH(k_colsum_partial, dim3(unsigned(nb), unsigned(ncb)), TX * TY,
+                   TX * TY * sizeof(double), s)(X, n, d, ld, rows, part, bad);
         if (cudaGetLastError() != cudaSuccess) { set_error("colsum launch"); TRY_IX(SNN_ECUDA); }
         SNN_LAUNCH(k_mean_final, grid_for(d, 128), 128, 0, s)(part, (int)nb, d, n, ix->mu64, ix->mu32);
         // K2: centred Gram matrix
-        const int ntile = (int)cdiv(d, kGramTile);
-        const int64_t grows = std::max<int64_t>(2048, cdiv(n, 512));
-        const int64_t nchunk = cdiv(n, grows);
-        float *gpart;
         double *C;
-        TRY_IX(scr.alloc(&gpart, size_t(nchunk) * d * d));
         TRY_IX(scr.alloc(&C, size_t(d) * d));
-        SNN_LAUNCH(k_gram_partial, dim3(ntile * ntile, (unsigned)nchunk), 256, 0, s)(X, n, d, ld, ix->mu32,
-                                                                             grows, ntile, gpart);
-        SNN_LAUNCH(k_gram_reduce, grid_for(int64_t(d) * d, 256), 256, 0, s)(gpart, (int)nchunk, d, C);
-        if (cudaGetLastError() != cudaSuccess) { set_error("gram launch"); TRY_IX(SNN_ECUDA); }
+        if (d <= kPcSmallMaxD) {
+            const int64_t gnb = std::max<int64_t>(
+                1, std::min<int64_t>(4 * device_sm_count(), cdiv(n, 256)));
+            const int64_t grows = cdiv(n, gnb);
+            float *gpart;
+            TRY_IX(scr.alloc(&gpart, size_t(gnb) * d * d));
+            auto gk = d <= 16 ? k_gram_small16 : (d <= 32 ? k_gram_small32 : k_gram_small64);
+            SNN_LAUNCH(gk, unsigned(gnb), 256, 0, s)(X, n, d, ld, ix->mu32, grows, gpart);
+            SNN_LAUNCH(k_gram_reduce, grid_for(int64_t(d) * d, 256), 256, 0, s)(gpart, (int)gnb, d, C);
+            if (cudaGetLastError() != cudaSuccess) { set_error("gram launch"); TRY_IX(SNN_ECUDA); }
+        } else {
+            TRY_IX(gram_tc(X, n, d, ld, ix->mu32, C, bad + 1, s, scr));
+        }
         // K3: first principal direction
-        TRY_IX(first_direction(C, d, ix->v64, ix->v32, s, scr));
+        TRY_IX(first_direction(C, d, ix->v64, ix->v32, bad + 1, s, scr));
         // K4-K6: scores, sort, gather
-        TRY_IX(project_sort_gather(X, n, d, ld, dp, ix->mu64, ix->v32, s, scr, ix->dconst + 0, bad,
+        TRY_IX(project_sort_gather(X, n, d, ld, dp, ix->mu32, ix->v32, s, scr, ix->dconst + 0, bad,
                                    ix->alpha, ix->order, ix->praw, ix->xc, ix->hx, ix->nrm));
         SNN_LAUNCH(k_max_nonneg, std::min<unsigned>(grid_for(n, 256), 1024), 256, 0, s)(ix->nrm, n,
                                                                                 ix->dconst + 1);
         if (cudaGetLastError() != cudaSuccess) { set_error("max launch"); TRY_IX(SNN_ECUDA); }
         float hc[2];
-        int hbad = 0;
+        int hbad[2] = {0, 0};
         if (cudaMemcpyAsync(hc, ix->dconst, 2 * sizeof(float), cudaMemcpyDeviceToHost, s) !=
                 cudaSuccess ||
-            cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(hbad, bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
             set_error("index build failed: %s", cudaGetErrorString(cudaGetLastError()));
             TRY_IX(SNN_ECUDA);
         }
-        if (hbad) {
+        if (hbad[0]) {
             set_error("X contains NaN or Inf");
             TRY_IX(SNN_EINVAL);
+        }
+        if (hbad[1]) {
+            set_error("index build: a bounded tensor-core wait expired");
+            TRY_IX(SNN_ETIMEOUT);
         }
         ix->alpha_err = hc[0];
         ix->nrm_max = hc[1];
@@ -395,7 +373,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         TRY_Q(scr.alloc(&qnrm, m));
         TRY_Q(scr.alloc(&eps_q, 1));
         CUDA_Q(cudaMemsetAsync(eps_q, 0, sizeof(float), s));
-        TRY_Q(project_sort_gather(Q, m, d, ldq, dp, ix->mu64, ix->v32, s, scr, eps_q, bad, qa,
+        TRY_Q(project_sort_gather(Q, m, d, ldq, dp, ix->mu32, ix->v32, s, scr, eps_q, bad, qa,
                                   qorder, qraw, qxc, qhy, qnrm));
         // NaN/Inf and norm range of the queries, checked before any scoring
         float *qnmax;
@@ -794,6 +772,7 @@ snn_status snn_index_get_view(const snn_index *idx, snn_index_view *view) {
     view->d = idx->d;
     view->dp = idx->dp;
     view->mu = idx->mu64;
+    view->centre = idx->mu32;
     view->v1 = idx->v64;
     view->alpha = idx->alpha;
     view->order = idx->order;

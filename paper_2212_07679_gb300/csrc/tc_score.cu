@@ -15,16 +15,61 @@
 // rejected exactly when the sign bit of acc_ij is set; all other pairs go to
 // the exact decision like the FP32 path's survivors.
 //
-// Warp roles (192 threads): warp 0 issues TMA loads, warp 1 owns TMEM and
-// issues the MMAs, warps 2-5 drain the accumulators.  Stages are guarded by
-// mbarriers; every wait is bounded and a timeout sets an error flag.
+// Warp roles: warp 0 issues TMA loads, warp 1 owns TMEM and issues the MMAs,
+// the remaining 8 (or 16, with two query tiles per item) warps drain the
+// accumulators.  Stages are guarded by mbarriers; every wait is bounded and a
+// timeout sets an error flag.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "index_struct.cuh"
+#include "tc_common.cuh"
 #include "tc_score.cuh"
 
 namespace snn {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn get_encode() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+snn_status make_map(CUtensorMap *map, const uint16_t *ptr, int64_t rows, int64_t K2, int bk,
+                    int box_rows) {
+    EncodeTiledFn enc = get_encode();
+    if (!enc) {
+        set_error("cuTensorMapEncodeTiled is unavailable");
+        return SNN_ENOTSUP;
+    }
+    cuuint64_t dims[2] = {cuuint64_t(K2), cuuint64_t(rows)};
+    cuuint64_t strides[1] = {cuuint64_t(K2) * 2};
+    cuuint32_t box[2] = {cuuint32_t(bk), cuuint32_t(box_rows)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(ptr), dims,
+                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
+                              : (bk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B),
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d)", int(r));
+        return SNN_ECUDA;
+    }
+    return SNN_OK;
+}
 
 namespace {
 
@@ -34,7 +79,6 @@ constexpr int kTM = 128;            // queries per tile (MMA M)
 __host__ __device__ constexpr int tc_epi_warps(int mt) { return 8 * mt; }
 __host__ __device__ constexpr int tc_threads(int mt) { return 64 + 32 * tc_epi_warps(mt); }
 constexpr int kExtra = 9;           // folded columns
-constexpr long long kTimeoutCycles = 4000000000LL;   // ~2 s
 // dynamic shared memory per CTA (minus base alignment and barriers) for 1
 // or 2 resident CTAs per SM
 __host__ __device__ constexpr int smem_budget(int cps, int align) {
@@ -80,129 +124,6 @@ struct TcShape {
 };
 
 __host__ __device__ constexpr int tc_npairs(int nsplit) { return nsplit == 2 ? 3 : 6; }
-
-// ------------------------------------------------------- PTX wrappers
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait; on timeout (or when another role already gave up) sets the
-// abort flags and returns false.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
-                                          int *err) {
-    const long long t0 = clock64();
-    while (!mbar_try(bar, parity)) {
-        if (*abort_flag) return false;
-        if (clock64() - t0 > kTimeoutCycles) {
-            *abort_flag = 1;
-            atomicOr(err, 1);
-            return false;
-        }
-    }
-    return true;
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
-                                            uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
-
-// Shared-memory matrix descriptor of a K-major tile whose rows are ROWB
-// bytes (128, 64 or 32, with the swizzle of that width); 8-row groups are
-// 8*ROWB apart.
-template <int ROWB>
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= uint64_t((saddr & 0x3FFFFu) >> 4);
-    d |= uint64_t(1) << 16;                         // leading byte offset (unused)
-    d |= uint64_t((8 * ROWB) >> 4) << 32;           // stride byte offset
-    d |= uint64_t(1) << 46;                         // descriptor version
-    d |= uint64_t(ROWB == 128 ? 2 : (ROWB == 64 ? 4 : 6)) << 61;   // 128B / 64B / 32B swizzle
-    return d;
-}
-
-// Instruction descriptor of kind::f16: BF16 A and B, FP32 D, both K-major,
-// M = 128, N = BN.
-template <int BN>
-__host__ __device__ constexpr uint32_t idesc_bf16() {
-    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) |
-           (uint32_t(kTM >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Loads 64 consecutive FP32 accumulator columns of this warp's 32 TMEM lanes
-// (32x32b shape, 64 repetitions) together with their maximum (the load's max
-// reduction over the 64 columns of each lane), and waits for them in the same
-// statement, so no use of the registers can be scheduled before the wait.
-__device__ __forceinline__ void tmem_ld64_max(uint32_t taddr, uint32_t (&r)[64], float &mx) {
-    asm volatile(
-        "tcgen05.ld.red.sync.aligned.32x32b.x64.max.f32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, %64, [%65];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
-          "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
-          "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
-          "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
-          "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63]),
-          "=f"(mx)
-        : "r"(taddr)
-        : "memory");
-}
-
 
 struct TcArgs {
     int64_t m;
@@ -250,7 +171,7 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
     constexpr int S = Sh::kStages;
     constexpr int NP = Sh::kNP;
     constexpr int CSTEP = BN / kBR;              // kBR-row chunks per MMA chunk
-    constexpr uint32_t kIdesc = idesc_bf16<BN>();
+    constexpr uint32_t kIdesc = idesc_bf16<kTM, BN>();
     // (A part, B part) products kept by the split: all with pa + pb <= NSPLIT-1
     constexpr int kPa[6] = {0, 0, 1, 0, 1, 2};
     constexpr int kPb[6] = {0, 1, 0, 2, 1, 0};
@@ -642,49 +563,6 @@ __global__ void k_tc_query_consts(const float *__restrict__ hy, const float *__r
     A = A >= 0.0 ? A / (1.0 - delta) : A / (1.0 + delta);
     A += 0x1p-22 * fabs(A) + 0x1p-100;
     Aq[i] = A;
-}
-
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn get_encode() {
-    static EncodeTiledFn fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                             &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-    }
-    return fn;
-}
-
-snn_status make_map(CUtensorMap *map, const uint16_t *ptr, int64_t rows, int K2, int bk,
-                    int box_rows) {
-    EncodeTiledFn enc = get_encode();
-    if (!enc) {
-        set_error("cuTensorMapEncodeTiled is unavailable");
-        return SNN_ENOTSUP;
-    }
-    cuuint64_t dims[2] = {cuuint64_t(K2), cuuint64_t(rows)};
-    cuuint64_t strides[1] = {cuuint64_t(K2) * 2};
-    cuuint32_t box[2] = {cuuint32_t(bk), cuuint32_t(box_rows)};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(ptr), dims,
-                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
-                              : (bk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B),
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) {
-        set_error("cuTensorMapEncodeTiled failed (%d)", int(r));
-        return SNN_ECUDA;
-    }
-    return SNN_OK;
 }
 
 // Rounding constant c of the folded test for a split and a dimension.

@@ -44,7 +44,7 @@ class ViewStruct(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32), ("dp", ctypes.c_int32),
                 ("mu", ctypes.c_void_p), ("v1", ctypes.c_void_p), ("alpha", ctypes.c_void_p),
                 ("order", ctypes.c_void_p), ("points", ctypes.c_void_p),
-                ("alpha_err", ctypes.c_double)]
+                ("alpha_err", ctypes.c_double), ("centre", ctypes.c_void_p)]
 
 
 def _load():
@@ -212,6 +212,7 @@ class Index:
             "order": cp(v.order, n, "<i4", torch.int32),
             "points": cp(v.points, n * dp, "<f4", torch.float32).view(n, dp)[:, :d],
             "alpha_err": v.alpha_err,
+            "centre": cp(v.centre, d, "<f4", torch.float32),
         }
 
     def close(self):

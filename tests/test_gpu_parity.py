@@ -145,9 +145,57 @@ def test_index_arrays(snn):
     ref = oracle.snn_index(w.P)
     assert abs(abs(float(v1 @ ref.v1)) - 1.0) < 1e-3
     assert np.allclose(v["mu"].cpu().numpy(), ref.mu, rtol=0, atol=1e-9)
-    # scores are within the recorded bound of the FP64 projection
-    a64 = (w.P[order].astype(np.float64) - v["mu"].cpu().numpy()) @ v1
+    # the centre is the FP32 rounding of the mean; scores are within the
+    # recorded bound of the FP64 projection of the points shifted by it
+    c = v["centre"].cpu().numpy()
+    assert np.array_equal(c, v["mu"].cpu().numpy().astype(np.float32))
+    a64 = (w.P[order].astype(np.float64) - c.astype(np.float64)) @ v1
     assert np.max(np.abs(alpha - a64)) <= v["alpha_err"]
+
+
+@pytest.mark.parametrize("d,n", [(100, 3000), (784, 5000), (130, 257)])
+def test_index_arrays_tensor_core_gram(snn, d, n):
+    """d > 64: the Gram matrix and the squarings run on the tensor cores.  The
+    first direction must agree with the oracle's (SVD of the centred data) and
+    the scores must stay within their recorded bound."""
+    if d == 784:
+        w = wl.lowrank_img(n=n, sub=1500)
+        P = w.P
+    else:
+        rng = np.random.default_rng(d)
+        # a dominant direction with a clear gap to the second
+        u = rng.standard_normal(d)
+        u /= np.linalg.norm(u)
+        P = (rng.standard_normal((n, d)) + 6.0 * rng.standard_normal((n, 1)) * u + 3.0).astype(np.float32)
+    ix = snn.Index(_dev(P))
+    v = ix.view()
+    order = v["order"].cpu().numpy()
+    alpha = v["alpha"].cpu().numpy()
+    assert np.all(np.diff(alpha) >= 0)
+    assert np.array_equal(np.sort(order), np.arange(n))
+    v1 = v["v1"].cpu().numpy()
+    assert abs(np.linalg.norm(v1) - 1.0) < 1e-12
+    ref = oracle.snn_index(P)
+    assert abs(abs(float(v1 @ ref.v1)) - 1.0) < 1e-3
+    c = v["centre"].cpu().numpy().astype(np.float64)
+    a64 = (P[order].astype(np.float64) - c) @ v1
+    assert np.max(np.abs(alpha - a64)) <= v["alpha_err"]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_high_d_degenerate_and_offset(snn, prec):
+    """d > 64 special cases of the tensor-core Gram: all points equal (C = 0,
+    v1 = e1), a large common offset, and a row count that is not a multiple
+    of the 64-row k-block."""
+    rng = np.random.default_rng(31)
+    same = np.repeat(rng.standard_normal((1, 96)).astype(np.float32), 333, axis=0)
+    got = _run(snn, same, None, 0.0, prec)
+    assert_csr_equal(got, oracle.brute_radius(same, None, 0.0), "identical d=96")
+    v1 = snn.Index(_dev(same)).view()["v1"].cpu().numpy()
+    assert v1[0] == 1.0 and np.all(v1[1:] == 0.0)
+    off = (rng.standard_normal((1111, 80)) * 0.5 + 3e3).astype(np.float32)
+    got = _run(snn, off, None, 3.0, prec)
+    assert_csr_equal(got, oracle.brute_radius(off, None, 3.0), "offset d=80")
 
 
 def test_invalid_inputs(snn):
