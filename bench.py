@@ -133,7 +133,7 @@ def cpu_oracle_sample(w, budget_s=15.0, seed=7, gpu_csr=None):
             for k, r in enumerate(rows):
                 a, b = ref.offsets[k], ref.offsets[k + 1]
                 ga, gb = off[r], off[r + 1]
-                if gb - ga != b - a or not np.array_equal(ids[ga:gb], ref.indices[a:b]):
+                if gb - ga != b - a or not np.array_equal(ids[ga:gb], ref.ids[a:b]):
                     mism += 1
                     continue
                 s_ref = ref.dist2[a:b].astype(np.float64)
