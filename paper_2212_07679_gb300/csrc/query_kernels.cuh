@@ -112,6 +112,17 @@ __global__ void k_decide_one(const uint2 *surv, int64_t nsurv, const float *qraw
                              const int32_t *qorder, const float *praw, const int32_t *porder,
                              int d, int dp, double R2, float *rec_d2, int32_t *rec_pos,
                              int32_t *counts, unsigned long long *n_fp64);
+// The same with 8 or 32 lanes per survivor (long rows: coalesced loads).
+#define SNN_DECIDE_DECL(name)                                                              \
+    __global__ void name(const uint2 *surv, int64_t nsurv, const float *qraw,              \
+                         const int32_t *qorder, const float *praw, const int32_t *porder,  \
+                         int d, int dp, double R2, float *rec_d2, int32_t *rec_pos,        \
+                         int32_t *counts, unsigned long long *n_fp64)
+SNN_DECIDE_DECL(k_decide_sym_g8);
+SNN_DECIDE_DECL(k_decide_one_g8);
+SNN_DECIDE_DECL(k_decide_sym_g32);
+SNN_DECIDE_DECL(k_decide_one_g32);
+#undef SNN_DECIDE_DECL
 __global__ void k_counts_to_i64(const int32_t *counts, int64_t m, int64_t *out);
 __global__ void k_scatter(const uint2 *surv, int64_t nsurv, const int32_t *qorder,
                           const int32_t *porder, const float *rec_d2, const int32_t *rec_pos, int sym,

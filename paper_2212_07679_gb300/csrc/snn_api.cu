@@ -543,14 +543,14 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     CUDA_Q(cudaMemsetAsync(counts, 0, m * sizeof(int32_t), s));
     const double R2 = R * R;
     if (nsurv > 0) {
-        if (sym)
-            SNN_LAUNCH(k_decide_sym, grid_for(nsurv, 256), 256, 0, s)(
-                surv, nsurv, qs.raw, qs.order, ds.raw, ds.order, d, dp, R2, rec_d2, rec_pos, counts,
-                ctr + 4);
-        else
-            SNN_LAUNCH(k_decide_one, grid_for(nsurv, 256), 256, 0, s)(
-                surv, nsurv, qs.raw, qs.order, ds.raw, ds.order, d, dp, R2, rec_d2, rec_pos, counts,
-                ctr + 4);
+        // lanes per survivor: 1 for short rows, 8 up to 128 dims, 32 beyond
+        const int G = d <= 32 ? 1 : (d <= 128 ? 8 : 32);
+        auto dk = G == 1 ? (sym ? k_decide_sym : k_decide_one)
+                         : (G == 8 ? (sym ? k_decide_sym_g8 : k_decide_one_g8)
+                                   : (sym ? k_decide_sym_g32 : k_decide_one_g32));
+        SNN_LAUNCH(dk, grid_for(nsurv * G, 256), 256, 0, s)(
+            surv, nsurv, qs.raw, qs.order, ds.raw, ds.order, d, dp, R2, rec_d2, rec_pos, counts,
+            ctr + 4);
         CUDA_Q(cudaGetLastError());
     }
     if (stats) cudaEventRecord(ev[3], s);

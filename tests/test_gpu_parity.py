@@ -198,6 +198,19 @@ def test_high_d_degenerate_and_offset(snn, prec):
     assert_csr_equal(got, oracle.brute_radius(off, None, 3.0), "offset d=80")
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_long_rows_exact_ties(snn, prec):
+    """Binary vectors: squared distances are integers, so many pairs sit
+    exactly on R^2 and take the FP64 fallback of the lane-group decision
+    (8 lanes per survivor at d = 72, 32 lanes at d = 200)."""
+    rng = np.random.default_rng(41)
+    for d, n, R in [(72, 600, 6.0), (200, 500, 10.0)]:
+        P = rng.integers(0, 2, (n, d)).astype(np.float32)
+        got = _run(snn, P, None, R, prec)
+        assert_csr_equal(got, oracle.brute_radius(P, None, R), f"binary d={d}")
+        assert got.stats["exact_fp64"] > 0
+
+
 def test_invalid_inputs(snn):
     P = np.random.default_rng(23).standard_normal((100, 4)).astype(np.float32)
     P[17, 2] = np.nan
