@@ -33,21 +33,23 @@ constexpr int kSquarings = 12;
 constexpr int kPowerSteps = 4;
 
 // out_p[i * n64 + r] (i < dpad features, r < n64 rows) = part p of the BF16
-// split of x = fl32(X[r][i] - c[i]) (c NULL: x = X[r][i]), or, with
-// trace_norm, of x = fl32(X[r][i] / trace(X)) for a square X.  Zero where
-// r >= n or i >= d.  Grid (n64 / 64, dpad / 64).
+// split of x = fl32(X[r][i] - c[i]) (c NULL: x = X[r][i]), or, with a
+// diagonal array `diag` of the square matrix X, of x = fl32(X[r][i] /
+// trace(X)).  Zero where r >= n or i >= d.  Grid (n64 / 64, dpad / 64).
 template <typename T, int NSPLIT>
 __global__ void __launch_bounds__(256)
 k_gram_pack(const T *__restrict__ X, int64_t n, int d, int64_t ld, const float *__restrict__ cvec,
-            int trace_norm, uint16_t *__restrict__ o0, uint16_t *__restrict__ o1, int64_t n64) {
+            const double *__restrict__ diag, uint16_t *__restrict__ o0, uint16_t *__restrict__ o1,
+            int64_t n64) {
     __shared__ __align__(16) uint16_t sh[NSPLIT][kPT][kPT + 8];   // [feature][row]
     __shared__ double s_inv;
     const int64_t r0 = int64_t(blockIdx.x) * kPT;
     const int i0 = blockIdx.y * kPT;
+    const bool trace_norm = diag != nullptr;
     if (trace_norm) {
         if (threadIdx.x < 32) {
             double tr = 0.0;
-            for (int i = threadIdx.x; i < d; i += 32) tr += (double)X[int64_t(i) * ld + i];
+            for (int i = threadIdx.x; i < d; i += 32) tr += diag[i];
             for (int o = 16; o; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
             if (threadIdx.x == 0) s_inv = (tr > 0.0 && isfinite(tr)) ? 1.0 / tr : 1.0;
         }
@@ -94,6 +96,8 @@ struct GramArgs {
     int kb_per;      // k-blocks per split
     int d;
     float *part;     // [split][d][d] FP32 partial tiles (upper triangle used)
+    double *C;       // DIRECT: the full symmetric result (FP64) ...
+    double *diag;    // ... and its diagonal
     int *err;
 };
 
@@ -118,7 +122,9 @@ __device__ __forceinline__ void mbar_wait_final(uint32_t bar, uint32_t parity, i
     }
 }
 
-template <int NSPLIT>
+// DIRECT (one split): the epilogue writes C[i][j], its mirror C[j][i] and the
+// diagonal itself; otherwise FP32 partial tiles for k_gram_reduce2.
+template <int NSPLIT, bool DIRECT>
 __global__ void __launch_bounds__(128, 1)
 k_gram_tc(const __grid_constant__ CUtensorMap m0, const __grid_constant__ CUtensorMap m1,
           GramArgs a) {
@@ -232,11 +238,25 @@ k_gram_tc(const __grid_constant__ CUtensorMap m0, const __grid_constant__ CUtens
             uint32_t r[64];
             tmem_ld64(tmem + (uint32_t(warp * 32) << 16) + uint32_t(h * 64), r);
             if (i < a.d) {
-                float *row = a.part + (int64_t(split) * a.d + i) * a.d;
                 const int j0 = bj * kGM + h * 64;
+                if (DIRECT) {
+                    double *row = a.C + int64_t(i) * a.d;
 #pragma unroll
-                for (int c = 0; c < 64; ++c)
-                    if (j0 + c < a.d) row[j0 + c] = __uint_as_float(r[c]);
+                    for (int c = 0; c < 64; ++c) {
+                        const int j = j0 + c;
+                        if (j < a.d) {
+                            const double v = (double)__uint_as_float(r[c]);
+                            row[j] = v;
+                            if (bi != bj) a.C[int64_t(j) * a.d + i] = v;
+                            if (j == i) a.diag[i] = v;
+                        }
+                    }
+                } else {
+                    float *row = a.part + (int64_t(split) * a.d + i) * a.d;
+#pragma unroll
+                    for (int c = 0; c < 64; ++c)
+                        if (j0 + c < a.d) row[j0 + c] = __uint_as_float(r[c]);
+                }
             }
         }
     }
@@ -253,34 +273,94 @@ k_gram_tc(const __grid_constant__ CUtensorMap m0, const __grid_constant__ CUtens
                      : "memory");
 }
 
-// v = the column of T with the largest diagonal entry; e1 when T has no
-// positive diagonal entry (C = 0: all points equal).
-__global__ void k_pick_column64(const double *__restrict__ T, int d, double *__restrict__ v) {
-    __shared__ int jbest;
-    __shared__ int degenerate;
-    if (threadIdx.x == 0) {
-        int jb = 0;
-        double best = 0.0;
-        for (int j = 0; j < d; ++j) {
-            const double x = T[int64_t(j) * d + j];
-            if (x > best) {
-                best = x;
-                jb = j;
-            }
-        }
-        jbest = jb;
-        degenerate = !(best > 0.0) || !isfinite(best);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < d; i += blockDim.x)
-        v[i] = degenerate ? (i == 0 ? 1.0 : 0.0) : T[int64_t(i) * d + jbest];
+// C[i][j] = sum over splits of the partial tiles (FP64), the upper triangle
+// mirrored; diag[i] = C[i][i].
+__global__ void k_gram_reduce2(const float *__restrict__ part, int nsplit, int d,
+                               double *__restrict__ C, double *__restrict__ diag) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= int64_t(d) * d) return;
+    const int i = int(e / d), j = int(e % d);
+    const int a = min(i, j), b = max(i, j);
+    double s = 0.0;
+    for (int c = 0; c < nsplit; ++c) s += (double)part[(int64_t(c) * d + a) * d + b];
+    C[e] = s;
+    if (i == j) diag[i] = s;
 }
 
-// C (d x d, FP64, full) = the Gram matrix of the columns held transposed in
-// the BF16 parts p0 (p1) of dpad x n64 elements; part: FP32 scratch.
-template <int NSPLIT>
+// v = row (= column) jbest of the symmetric T, jbest = the largest diagonal
+// entry (smallest index among equals); e1 when no diagonal entry is positive
+// (C = 0: all points equal).  One block.
+__global__ void __launch_bounds__(1024)
+k_pick_column64(const double *__restrict__ T, const double *__restrict__ diag, int d,
+                double *__restrict__ v) {
+    __shared__ double sb[32];
+    __shared__ int sj[32];
+    double best = 0.0;
+    int jb = 0x7fffffff;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        const double x = diag[j];
+        if (x > best) {
+            best = x;
+            jb = j;
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        const double b2 = __shfl_xor_sync(0xffffffffu, best, o);
+        const int j2 = __shfl_xor_sync(0xffffffffu, jb, o);
+        if (b2 > best || (b2 == best && j2 < jb)) {
+            best = b2;
+            jb = j2;
+        }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        sb[warp] = best;
+        sj[warp] = jb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nw; ++w)
+            if (sb[w] > sb[0] || (sb[w] == sb[0] && sj[w] < sj[0])) {
+                sb[0] = sb[w];
+                sj[0] = sj[w];
+            }
+    }
+    __syncthreads();
+    const bool degenerate = !(sb[0] > 0.0) || !isfinite(sb[0]);
+    const int jbest = sj[0];
+    for (int i = threadIdx.x; i < d; i += blockDim.x)
+        v[i] = degenerate ? (i == 0 ? 1.0 : 0.0) : T[int64_t(jbest) * d + i];
+}
+
+// w = C v / ||v|| (FP64; v = 0 gives w = 0), one warp per row.  Every block
+// computes ||v|| itself in the same fixed order.
+__global__ void __launch_bounds__(256)
+k_power64(const double *__restrict__ C, int d, const double *__restrict__ v,
+          double *__restrict__ w) {
+    __shared__ double red[8];
+    double p = 0.0;
+    for (int k = threadIdx.x; k < d; k += blockDim.x) p += v[k] * v[k];
+    for (int o = 16; o; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = p;
+    __syncthreads();
+    double nrm2 = 0.0;
+    for (int q = 0; q < 8; ++q) nrm2 += red[q];
+    const double inv = (nrm2 > 0.0 && isfinite(nrm2)) ? 1.0 / sqrt(nrm2) : 1.0;
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (row >= d) return;
+    double s = 0.0;
+    for (int k = lane; k < d; k += 32) s += C[int64_t(row) * d + k] * v[k];
+    for (int o = 16; o; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) w[row] = s * inv;
+}
+
+// C (d x d, FP64, full) and diag = the Gram matrix of the columns held
+// transposed in the BF16 parts p0 (p1) of dpad x n64 elements.  DIRECT: one
+// split, written by the tensor-core kernel itself; otherwise split K with
+// FP32 partials summed in FP64.
+template <int NSPLIT, bool DIRECT>
 snn_status gram_gemm(const uint16_t *p0, const uint16_t *p1, int d, int dpad, int64_t n64,
-                     double *C, int *err, cudaStream_t s, Scratch &scr) {
+                     double *C, double *diag, int *err, cudaStream_t s, Scratch &scr) {
     using Sh = GramShape<NSPLIT>;
     CUtensorMap maps[2];
     SNN_TRY(make_map(&maps[0], p0, dpad, n64, kGKB, kGM));
@@ -289,69 +369,84 @@ snn_status gram_gemm(const uint16_t *p0, const uint16_t *p1, int d, int dpad, in
     a.nb = dpad / kGM;
     a.ntiles = a.nb * (a.nb + 1) / 2;
     a.nkb = int(n64 / kGKB);
-    const int sms = device_sm_count();
-    int nsplitk = std::max(1, std::min(sms / a.ntiles, a.nkb / 2));
+    int nsplitk = 1;
+    if (!DIRECT) {
+        const int sms = device_sm_count();
+        nsplitk = std::max(1, std::min(sms / a.ntiles, a.nkb / 2));
+    }
     a.kb_per = int(cdiv(a.nkb, nsplitk));
     nsplitk = int(cdiv(a.nkb, a.kb_per));   // every split holds at least one k-block
     a.d = d;
     a.err = err;
-    SNN_TRY(scr.alloc(&a.part, size_t(nsplitk) * d * d));
-    auto kern = k_gram_tc<NSPLIT>;
+    a.C = C;
+    a.diag = diag;
+    a.part = nullptr;
+    if (!DIRECT) SNN_TRY(scr.alloc(&a.part, size_t(nsplitk) * d * d));
+    auto kern = k_gram_tc<NSPLIT, DIRECT>;
     SNN_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::kSmem)));
     SNN_LAUNCH(kern, unsigned(a.ntiles * nsplitk), 128, Sh::kSmem, s)(maps[0], maps[1], a);
     SNN_LAUNCH_CHECK();
-    SNN_LAUNCH(k_gram_reduce, unsigned(cdiv(int64_t(d) * d, 256)), 256, 0, s)(a.part, nsplitk, d, C);
-    SNN_LAUNCH_CHECK();
+    if (!DIRECT) {
+        SNN_LAUNCH(k_gram_reduce2, unsigned(cdiv(int64_t(d) * d, 256)), 256, 0, s)(a.part, nsplitk,
+                                                                                  d, C, diag);
+        SNN_LAUNCH_CHECK();
+    }
     return SNN_OK;
 }
 
 }  // namespace
 
 snn_status gram_tc(const float *X, int64_t n, int d, int64_t ld, const float *cvec, double *C,
-                   int *err, cudaStream_t s, Scratch &scr) {
+                   double *diag, int *err, cudaStream_t s, Scratch &scr) {
     const int dpad = int(cdiv(d, kGM) * kGM);
     const int64_t n64 = cdiv(n, kGKB) * kGKB;
     uint16_t *p0, *p1;
     SNN_TRY(scr.alloc(&p0, size_t(dpad) * n64));
     SNN_TRY(scr.alloc(&p1, size_t(dpad) * n64));
     auto pack = k_gram_pack<float, 2>;
-    SNN_LAUNCH(pack, dim3(unsigned(n64 / kPT), unsigned(dpad / kPT)), 256, 0, s)(X, n, d, ld, cvec,
-                                                                            0, p0, p1, n64);
+    SNN_LAUNCH(pack, dim3(unsigned(n64 / kPT), unsigned(dpad / kPT)), 256, 0, s)(
+        X, n, d, ld, cvec, nullptr, p0, p1, n64);
     SNN_LAUNCH_CHECK();
-    return gram_gemm<2>(p0, p1, d, dpad, n64, C, err, s, scr);
+    return gram_gemm<2, false>(p0, p1, d, dpad, n64, C, diag, err, s, scr);
 }
 
-snn_status first_direction_tc(const double *C, int d, double *v64, float *v32, int *err,
-                              cudaStream_t s, Scratch &scr) {
+snn_status first_direction_tc(const double *C, const double *diagC, int d, double *v64,
+                              float *v32, int *err, cudaStream_t s, Scratch &scr) {
     const int dpad = int(cdiv(d, kGM) * kGM);
     const int64_t n64 = cdiv(d, kGKB) * kGKB;
     uint16_t *p0;
-    double *T, *w;
+    double *T, *diag, *w0, *w1;
     SNN_TRY(scr.alloc(&p0, size_t(dpad) * n64));
     SNN_TRY(scr.alloc(&T, size_t(d) * d));
-    SNN_TRY(scr.alloc(&w, d));
+    SNN_TRY(scr.alloc(&diag, d));
+    SNN_TRY(scr.alloc(&w0, d));
+    SNN_TRY(scr.alloc(&w1, d));
     const dim3 pgrid(unsigned(n64 / kPT), unsigned(dpad / kPT));
     // M0 = C / trace(C); M_{k+1} = M_k^2 / trace(M_k^2), one BF16 part (only
     // the pruning power depends on the accuracy of v1)
-    const double *src = C;
     auto pack = k_gram_pack<double, 1>;
-    for (int it = 0; it < kSquarings; ++it) {
-        SNN_LAUNCH(pack, pgrid, 256, 0, s)(src, d, d, d, nullptr, 1, p0, nullptr, n64);
-        SNN_LAUNCH_CHECK();
-        SNN_TRY(gram_gemm<1>(p0, nullptr, d, dpad, n64, T, err, s, scr));
-        src = T;
-    }
-    SNN_LAUNCH(k_pick_column64, 1, 256, 0, s)(T, d, v64);
+    SNN_LAUNCH(pack, pgrid, 256, 0, s)(C, d, d, d, nullptr, diagC, p0, nullptr, n64);
     SNN_LAUNCH_CHECK();
-    for (int it = 0; it < kPowerSteps; ++it) {
-        SNN_LAUNCH(k_matvec64, unsigned(cdiv(int64_t(d) * 32, 256)), 256, 0, s)(C, d, v64, w);
-        SNN_LAUNCH_CHECK();
-        SNN_LAUNCH(k_normalise64, 1, 1024, 0, s)(w, d, v64, v32, 0);
-        SNN_LAUNCH_CHECK();
+    for (int it = 0; it < kSquarings; ++it) {
+        SNN_TRY((gram_gemm<1, true>(p0, nullptr, d, dpad, n64, T, diag, err, s, scr)));
+        if (it + 1 < kSquarings) {
+            SNN_LAUNCH(pack, pgrid, 256, 0, s)(T, d, d, d, nullptr, diag, p0, nullptr, n64);
+            SNN_LAUNCH_CHECK();
+        }
     }
-    // final FP64 normalisation (also writes the FP32 copy)
-    SNN_CUDA(cudaMemcpyAsync(w, v64, d * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    SNN_LAUNCH(k_normalise64, 1, 1024, 0, s)(w, d, v64, v32, 1);
+    SNN_LAUNCH(k_pick_column64, 1, 1024, 0, s)(T, diag, d, v64);
+    SNN_LAUNCH_CHECK();
+    // FP64 power steps on C (normalised on the fly), then FP64 normalisation
+    // into v64 (kept as is when C v vanished: C = 0)
+    const double *src = v64;
+    double *dst = w0;
+    for (int it = 0; it < kPowerSteps; ++it) {
+        SNN_LAUNCH(k_power64, unsigned(cdiv(int64_t(d) * 32, 256)), 256, 0, s)(C, d, src, dst);
+        SNN_LAUNCH_CHECK();
+        src = dst;
+        dst = dst == w0 ? w1 : w0;
+    }
+    SNN_LAUNCH(k_normalise64, 1, 1024, 0, s)(src, d, v64, v32, 1);
     SNN_LAUNCH_CHECK();
     return SNN_OK;
 }

@@ -30,13 +30,13 @@ constexpr int kPcSmallMaxD = 64;
 
 // Tensor-core Gram matrix and first direction for d > kPcSmallMaxD
 // (gram_tc.cu).  gram_tc: C (d x d, FP64, full) = sum_r x_r x_r^T over the
-// centred rows x = fl32(p - c).  first_direction_tc: v1 from C (FP64 and FP32
-// copies).  Stream-ordered; a bounded wait that expires sets *err (device)
-// to nonzero, which the caller reads with its other device flags.  Scratch
-// memory comes from `scr`.
+// centred rows x = fl32(p - c), and diag[i] = C[i][i].  first_direction_tc:
+// v1 from C and its diagonal (FP64 and FP32 copies).  Stream-ordered; a
+// bounded wait that expires sets *err (device) to nonzero, which the caller
+// reads with its other device flags.  Scratch memory comes from `scr`.
 snn_status gram_tc(const float *X, int64_t n, int d, int64_t ld, const float *cvec, double *C,
-                   int *err, cudaStream_t s, Scratch &scr);
-snn_status first_direction_tc(const double *C, int d, double *v64, float *v32, int *err,
-                              cudaStream_t s, Scratch &scr);
+                   double *diag, int *err, cudaStream_t s, Scratch &scr);
+snn_status first_direction_tc(const double *C, const double *diagC, int d, double *v64,
+                              float *v32, int *err, cudaStream_t s, Scratch &scr);
 
 }  // namespace snn

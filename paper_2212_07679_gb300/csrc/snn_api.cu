@@ -164,8 +164,8 @@ __global__ void k_max_nonneg(const float *__restrict__ x, int64_t n, float *__re
     if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
 }
 
-static snn_status first_direction(const double *C, int d, double *v64, float *v32, int *err,
-                                  cudaStream_t s, Scratch &scr) {
+static snn_status first_direction(const double *C, const double *diagC, int d, double *v64,
+                                  float *v32, int *err, cudaStream_t s, Scratch &scr) {
     if (d <= kPcSmallMaxD) {
         const size_t smem = (2 * d + 32) * sizeof(double) + 32 * sizeof(float) +
                             2 * size_t(d) * d * sizeof(float);
@@ -173,7 +173,7 @@ static snn_status first_direction(const double *C, int d, double *v64, float *v3
         SNN_LAUNCH_CHECK();
         return SNN_OK;
     }
-    return first_direction_tc(C, d, v64, v32, err, s, scr);
+    return first_direction_tc(C, diagC, d, v64, v32, err, s, scr);
 }
 
 static snn_status index_build(const float *X, int64_t n, int d, int64_t ld, cudaStream_t s,
@@ -233,8 +233,9 @@ static snn_status index_build(const float *X, int64_t n, int d, int64_t ld, cuda
         if (cudaGetLastError() != cudaSuccess) { set_error("colsum launch"); TRY_IX(SNN_ECUDA); }
         SNN_LAUNCH(k_mean_final, grid_for(d, 128), 128, 0, s)(part, (int)nb, d, n, ix->mu64, ix->mu32);
         // K2: centred Gram matrix
-        double *C;
+        double *C, *diagC;
         TRY_IX(scr.alloc(&C, size_t(d) * d));
+        TRY_IX(scr.alloc(&diagC, d));
         if (d <= kPcSmallMaxD) {
             const int64_t gnb = std::max<int64_t>(
                 1, std::min<int64_t>(4 * device_sm_count(), cdiv(n, 256)));
@@ -246,10 +247,10 @@ static snn_status index_build(const float *X, int64_t n, int d, int64_t ld, cuda
             SNN_LAUNCH(k_gram_reduce, grid_for(int64_t(d) * d, 256), 256, 0, s)(gpart, (int)gnb, d, C);
             if (cudaGetLastError() != cudaSuccess) { set_error("gram launch"); TRY_IX(SNN_ECUDA); }
         } else {
-            TRY_IX(gram_tc(X, n, d, ld, ix->mu32, C, bad + 1, s, scr));
+            TRY_IX(gram_tc(X, n, d, ld, ix->mu32, C, diagC, bad + 1, s, scr));
         }
         // K3: first principal direction
-        TRY_IX(first_direction(C, d, ix->v64, ix->v32, bad + 1, s, scr));
+        TRY_IX(first_direction(C, diagC, d, ix->v64, ix->v32, bad + 1, s, scr));
         // K4-K6: scores, sort, gather
         TRY_IX(project_sort_gather(X, n, d, ld, dp, ix->mu32, ix->v32, s, scr, ix->dconst + 0, bad,
                                    ix->alpha, ix->order, ix->praw, ix->xc, ix->hx, ix->nrm));
