@@ -185,10 +185,16 @@ typedef struct {
 
 snn_status snn_index_get_view(const snn_index *idx, snn_index_view *view);
 
-/* Releases a device buffer returned in an snn_csr (NULL is a no-op). */
+/* Releases a device buffer returned in an snn_csr (NULL, and pointers the
+ * library did not return, are no-ops).  Library buffers come from the
+ * device's stream-ordered memory pool and are released in order on the
+ * stream of the call that returned them: that stream must still exist, and
+ * work on other streams that reads the buffer must be ordered before the
+ * release (for example through an event). */
 void snn_free(void *p);
 
-/* Releases an index and all its device memory (NULL is a no-op). */
+/* Releases an index and all its device memory (NULL is a no-op), in order on
+ * the stream the index was built on (same rules as snn_free). */
 void snn_index_free(snn_index *idx);
 
 /* Message for the calling thread's last non-OK status ("" if none). */

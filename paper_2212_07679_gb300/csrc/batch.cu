@@ -14,7 +14,7 @@
 
 namespace snn {
 
-snn_status register_block(void *block, void *const *ptrs, int count);
+snn_status register_block(void *block, void *const *ptrs, int count, cudaStream_t s);
 
 namespace {
 
@@ -573,7 +573,7 @@ snn_status batch_query(int32_t nsets, const snn_index *const *idx, const float *
     const size_t bytes = size_t(off_words) * 8 + 2 * std::max<size_t>(idx_bytes, 256);
     char *block = nullptr;
     {
-        cudaError_t e = cudaMalloc(&block, bytes);
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&block), bytes, s);
         if (e != cudaSuccess) {
             cudaGetLastError();
             set_error("output allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
@@ -586,8 +586,7 @@ snn_status batch_query(int32_t nsets, const snn_index *const *idx, const float *
     int64_t *d_offpos;
     snn_status st = scr.alloc(&d_offpos, nsets);
     auto fail = [&](snn_status code) {
-        cudaStreamSynchronize(s);
-        cudaFree(block);
+        cudaFreeAsync(block, s);
         return code;
     };
     if (st != SNN_OK) return fail(st);
@@ -676,7 +675,7 @@ snn_status batch_query(int32_t nsets, const snn_index *const *idx, const float *
             ptrs.push_back(out[t].dist2);
         }
     }
-    st = register_block(block, ptrs.data(), int(ptrs.size()));
+    st = register_block(block, ptrs.data(), int(ptrs.size()), s);
     if (st != SNN_OK) {
         for (int32_t t = 0; t < nsets; ++t) std::memset(&out[t], 0, sizeof(out[t]));
         return fail(st);

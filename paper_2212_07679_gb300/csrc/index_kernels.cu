@@ -58,15 +58,20 @@ __global__ void k_colsum_partial(const float *__restrict__ X, int64_t n, int d, 
 // mu = column means (FP64); the index centres every point with the FP32
 // vector c = fl32(mu) (any fixed centre leaves distances unchanged,
 // Section 3.1), so centring is one exact-input FP32 subtraction per value.
+// One warp per column: lane-strided partial sums and a shuffle tree (short
+// FP64 dependency chains; fixed order, deterministic).
 __global__ void k_mean_final(const double *__restrict__ part, int nb, int d, int64_t n,
                              double *__restrict__ mu64, float *__restrict__ mu32) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (c >= d) return;
     double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += part[int64_t(b) * d + c];
-    double m = s / (double)n;
-    mu64[c] = m;
-    mu32[c] = (float)m;
+    for (int b = lane; b < nb; b += 32) s += part[int64_t(b) * d + c];
+    for (int o = 16; o; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        const double m = s / (double)n;
+        mu64[c] = m;
+        mu32[c] = (float)m;
+    }
 }
 
 // ------------------------------------------------------------ Gram (K2)
@@ -154,16 +159,19 @@ k_gram_small64(const float *X, int64_t n, int d, int64_t ld, const float *cvec, 
     gram_small<64>(X, n, d, ld, cvec, rows, part);
 }
 
-// C64[i][j] = sum over chunks (FP64), upper triangle mirrored.
+// C64[i][j] = sum over chunks (FP64), upper triangle mirrored.  One warp per
+// entry (lane-strided partial sums, shuffle tree: short FP64 chains).
 __global__ void k_gram_reduce(const float *__restrict__ part, int nchunk, int d,
                               double *__restrict__ C) {
-    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t e = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (e >= int64_t(d) * d) return;
     const int i = int(e / d), j = int(e % d);
     const int a = min(i, j), b = max(i, j);
     double s = 0.0;
-    for (int c = 0; c < nchunk; ++c) s += (double)part[int64_t(c) * d * d + int64_t(a) * d + b];
-    C[e] = s;
+    for (int c = lane; c < nchunk; c += 32) s += (double)part[int64_t(c) * d * d + int64_t(a) * d + b];
+    for (int o = 16; o; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) C[e] = s;
 }
 
 // ------------------------------------------------- first direction (K3)
@@ -313,21 +321,44 @@ __global__ void k_normalise64(const double *__restrict__ w, int d, double *__res
 __global__ void k_project(const float *__restrict__ X, int64_t n, int d, int64_t ld,
                           const float *__restrict__ cvec, const float *__restrict__ v32,
                           uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                          float *__restrict__ eps_max, int *__restrict__ bad) {
+                          float *__restrict__ eps_max, int *__restrict__ bad, int vec) {
     const bool warp_mode = d > 32;
     const int64_t gt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t i = warp_mode ? gt >> 5 : gt;
     const int lane = warp_mode ? int(threadIdx.x & 31) : 0;
     const int step = warp_mode ? 32 : 1;
-    if (i >= n) return;   // whole warps exit together in warp mode
+    const bool live = i < n;   // whole warps leave together in warp mode
+    if (warp_mode && !live) return;
     float a = 0.f, b = 0.f;
     int badl = 0;
-    for (int k = lane; k < d; k += step) {
-        const float p = X[i * ld + k];
-        badl |= !isfinite(p);
-        const float x = p - cvec[k];
-        a = fmaf(x, v32[k], a);
-        b = fmaf(fabsf(x), fabsf(v32[k]), b);
+    if (live) {
+        if (vec) {
+            // rows of d = 4k floats at 16-byte aligned addresses
+            const float4 *row = reinterpret_cast<const float4 *>(X + i * ld);
+            const float4 *c4 = reinterpret_cast<const float4 *>(cvec);
+            const float4 *w4 = reinterpret_cast<const float4 *>(v32);
+            for (int k = lane; k < d / 4; k += step) {
+                const float4 p = row[k], c = c4[k], w = w4[k];
+                badl |= !isfinite(p.x) | !isfinite(p.y) | !isfinite(p.z) | !isfinite(p.w);
+                const float x0 = p.x - c.x, x1 = p.y - c.y, x2 = p.z - c.z, x3 = p.w - c.w;
+                a = fmaf(x0, w.x, a);
+                a = fmaf(x1, w.y, a);
+                a = fmaf(x2, w.z, a);
+                a = fmaf(x3, w.w, a);
+                b = fmaf(fabsf(x0), fabsf(w.x), b);
+                b = fmaf(fabsf(x1), fabsf(w.y), b);
+                b = fmaf(fabsf(x2), fabsf(w.z), b);
+                b = fmaf(fabsf(x3), fabsf(w.w), b);
+            }
+        } else {
+            for (int k = lane; k < d; k += step) {
+                const float p = X[i * ld + k];
+                badl |= !isfinite(p);
+                const float x = p - cvec[k];
+                a = fmaf(x, v32[k], a);
+                b = fmaf(fabsf(x), fabsf(v32[k]), b);
+            }
+        }
     }
     if (warp_mode) {
         for (int o = 16; o; o >>= 1) {
@@ -336,10 +367,23 @@ __global__ void k_project(const float *__restrict__ X, int64_t n, int d, int64_t
             badl |= __shfl_down_sync(0xffffffffu, badl, o);
         }
     }
-    if (lane == 0) {
-        const float eps = (float)(d + 4) * kU32 * 1.01f * b + 1e-37f;
+    float eps = 0.f;
+    if (live && lane == 0) {
+        eps = (float)(d + 4) * kU32 * 1.01f * b + 1e-37f;
         keys[i] = float_to_key(a);
         vals[i] = (uint32_t)i;
+    }
+    if (!warp_mode) {
+        // one atomic per warp for the largest bound and the NaN flag
+        for (int o = 16; o; o >>= 1) {
+            eps = fmaxf(eps, __shfl_xor_sync(0xffffffffu, eps, o));
+            badl |= __shfl_xor_sync(0xffffffffu, badl, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomic_max_nonneg(eps_max, eps);
+            if (badl) atomicOr(bad, 1);
+        }
+    } else if (lane == 0) {
         atomic_max_nonneg(eps_max, eps);
         if (badl) atomicOr(bad, 1);
     }
@@ -354,7 +398,7 @@ __global__ void k_gather(const uint32_t *__restrict__ skeys, const uint32_t *__r
                          const float *__restrict__ cvec, float *__restrict__ alpha,
                          int32_t *__restrict__ order_out, float *__restrict__ praw,
                          float *__restrict__ xc, float *__restrict__ hx,
-                         float *__restrict__ nrm) {
+                         float *__restrict__ nrm, int vec) {
     const bool warp_mode = d > 32;
     const int64_t gt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t r = warp_mode ? gt >> 5 : gt;
@@ -363,15 +407,33 @@ __global__ void k_gather(const uint32_t *__restrict__ skeys, const uint32_t *__r
     if (r >= n) return;
     const int64_t i = order[r];
     float s = 0.f;
-    for (int k = lane; k < dp; k += step) {
-        float p = 0.f, x = 0.f;
-        if (k < d) {
-            p = X[i * ld + k];
-            x = p - cvec[k];
+    if (vec) {
+        // d = dp = 4k, 16-byte aligned rows
+        const float4 *src = reinterpret_cast<const float4 *>(X + i * ld);
+        const float4 *c4 = reinterpret_cast<const float4 *>(cvec);
+        float4 *pr = reinterpret_cast<float4 *>(praw + r * dp);
+        float4 *pc = reinterpret_cast<float4 *>(xc + r * dp);
+        for (int k = lane; k < dp / 4; k += step) {
+            const float4 p = src[k], c = c4[k];
+            const float4 x = make_float4(p.x - c.x, p.y - c.y, p.z - c.z, p.w - c.w);
+            pr[k] = p;
+            pc[k] = x;
+            s = fmaf(x.x, x.x, s);
+            s = fmaf(x.y, x.y, s);
+            s = fmaf(x.z, x.z, s);
+            s = fmaf(x.w, x.w, s);
         }
-        praw[r * dp + k] = p;
-        xc[r * dp + k] = x;
-        s = fmaf(x, x, s);
+    } else {
+        for (int k = lane; k < dp; k += step) {
+            float p = 0.f, x = 0.f;
+            if (k < d) {
+                p = X[i * ld + k];
+                x = p - cvec[k];
+            }
+            praw[r * dp + k] = p;
+            xc[r * dp + k] = x;
+            s = fmaf(x, x, s);
+        }
     }
     if (warp_mode)
         for (int o = 16; o; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);

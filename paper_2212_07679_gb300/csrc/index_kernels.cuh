@@ -21,10 +21,11 @@ __global__ void k_matvec64(const double *C, int d, const double *v, double *w);
 __global__ void k_normalise64(const double *w, int d, double *v, float *v32, int final_);
 __global__ void k_project(const float *X, int64_t n, int d, int64_t ld, const float *cvec,
                           const float *v32, uint32_t *keys, uint32_t *vals, float *eps_max,
-                          int *bad);
+                          int *bad, int vec);
 __global__ void k_gather(const uint32_t *skeys, const uint32_t *order, const float *X, int64_t n,
                          int d, int64_t ld, int dp, const float *cvec, float *alpha,
-                         int32_t *order_out, float *praw, float *xc, float *hx, float *nrm);
+                         int32_t *order_out, float *praw, float *xc, float *hx, float *nrm,
+                         int vec);
 
 constexpr int kPcSmallMaxD = 64;
 

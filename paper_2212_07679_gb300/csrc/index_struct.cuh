@@ -8,6 +8,8 @@ struct snn_index {
     int64_t n = 0;
     int d = 0, dp = 0;
     int device = 0;
+    cudaStream_t stream = nullptr;   // build stream: the index's arrays are
+                                     // released in order on it
     double *mu64 = nullptr;
     float *mu32 = nullptr;
     double *v64 = nullptr;

@@ -381,15 +381,15 @@ __device__ __forceinline__ double dist2_fp64(const float4 *pp, const float4 *pq,
     return S;
 }
 
+// Survivor s of min(*count, cap) (grid-stride: the count is read on the
+// device); rec_pos[cap + s] holds the slot in the mirrored row.
 template <bool kSym>
-__device__ __forceinline__ void decide_body(
-         const uint2 *__restrict__ surv, int64_t nsurv, const float *__restrict__ qraw,
+__device__ __forceinline__ void decide_one_survivor(
+         int64_t s, const uint2 *__restrict__ surv, int64_t cap, const float *__restrict__ qraw,
          const int32_t *__restrict__ qorder, const float *__restrict__ praw,
          const int32_t *__restrict__ porder, int d, int dp, double R2,
          float *__restrict__ rec_d2, int32_t *__restrict__ rec_pos, int32_t *__restrict__ counts,
          unsigned long long *__restrict__ n_fp64) {
-    const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (s >= nsurv) return;
     const uint2 e = surv[s];
     const float4 *pq = reinterpret_cast<const float4 *>(qraw + int64_t(e.x) * dp);
     const float4 *pp = reinterpret_cast<const float4 *>(praw + int64_t(e.y) * dp);
@@ -400,18 +400,18 @@ __device__ __forceinline__ void decide_body(
         const float bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            if (k4 * 4 + c < d) {
-                float sd, ed;
-                two_sum(av[c], -bv[c], sd, ed);
-                const float ph = __fmul_rn(sd, sd);
-                const float pl = __fmaf_rn(sd, sd, -ph);
-                const float cc = __fmaf_rn(__fadd_rn(sd, sd), ed, pl);
-                float s1, t1;
-                two_sum(H, ph, s1, t1);
-                const float t3 = __fadd_rn(__fadd_rn(t1, L), cc);
-                H = __fadd_rn(s1, t3);
-                L = __fsub_rn(t3, __fsub_rn(H, s1));
-            }
+            // padding columns (k >= d) are zero in both rows: such a step
+            // leaves (H, L) exactly unchanged
+            float sd, ed;
+            two_sum(av[c], -bv[c], sd, ed);
+            const float ph = __fmul_rn(sd, sd);
+            const float pl = __fmaf_rn(sd, sd, -ph);
+            const float cc = __fmaf_rn(__fadd_rn(sd, sd), ed, pl);
+            float s1, t1;
+            two_sum(H, ph, s1, t1);
+            const float t3 = __fadd_rn(__fadd_rn(t1, L), cc);
+            H = __fadd_rn(s1, t3);
+            L = __fsub_rn(t3, __fsub_rn(H, s1));
         }
     }
     const double S_df = (double)H + (double)L;   // exact: |L| <= ulp(H)/2
@@ -451,7 +451,21 @@ __device__ __forceinline__ void decide_body(
     }
     rec_d2[s] = d2;
     rec_pos[s] = p0;
-    if (kSym) rec_pos[nsurv + s] = p1;
+    if (kSym) rec_pos[cap + s] = p1;
+}
+
+template <bool kSym>
+__device__ __forceinline__ void decide_body(
+         const uint2 *__restrict__ surv, const unsigned long long *__restrict__ count, int64_t cap,
+         const float *__restrict__ qraw, const int32_t *__restrict__ qorder,
+         const float *__restrict__ praw, const int32_t *__restrict__ porder, int d, int dp,
+         double R2, float *__restrict__ rec_d2, int32_t *__restrict__ rec_pos,
+         int32_t *__restrict__ counts, unsigned long long *__restrict__ n_fp64) {
+    const int64_t nsurv = min((int64_t)*count, cap);
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < nsurv; s += stride)
+        decide_one_survivor<kSym>(s, surv, cap, qraw, qorder, praw, porder, d, dp, R2, rec_d2,
+                                  rec_pos, counts, n_fp64);
 }
 
 // The same decision with G lanes per survivor for long rows: lane l
@@ -464,25 +478,33 @@ __device__ __forceinline__ void decide_body(
 // the oracle's ascending loop on lane 0.
 template <bool kSym, int G>
 __device__ __forceinline__ void decide_group_body(
-         const uint2 *__restrict__ surv, int64_t nsurv, const float *__restrict__ qraw,
-         const int32_t *__restrict__ qorder, const float *__restrict__ praw,
-         const int32_t *__restrict__ porder, int d, int dp, double R2,
-         float *__restrict__ rec_d2, int32_t *__restrict__ rec_pos, int32_t *__restrict__ counts,
-         unsigned long long *__restrict__ n_fp64) {
-    const int64_t s = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / G;
+         const uint2 *__restrict__ surv, const unsigned long long *__restrict__ count, int64_t cap,
+         const float *__restrict__ qraw, const int32_t *__restrict__ qorder,
+         const float *__restrict__ praw, const int32_t *__restrict__ porder, int d, int dp,
+         double R2, float *__restrict__ rec_d2, int32_t *__restrict__ rec_pos,
+         int32_t *__restrict__ counts, unsigned long long *__restrict__ n_fp64) {
+    constexpr int GPW = 32 / G;   // groups per warp
+    const int64_t nsurv = min((int64_t)*count, cap);
     const int lane = int(threadIdx.x % G);
-    const bool valid = s < nsurv;   // groups past the end still join the shuffles
-    const uint2 e = valid ? surv[s] : make_uint2(0u, 0u);
-    const float4 *pq = reinterpret_cast<const float4 *>(qraw + int64_t(e.x) * dp);
-    const float4 *pp = reinterpret_cast<const float4 *>(praw + int64_t(e.y) * dp);
-    float H = 0.f, L = 0.f;
-    for (int k4 = lane; valid && k4 < dp / 4; k4 += G) {
-        const float4 a = pp[k4], b = pq[k4];
-        const float av[4] = {a.x, a.y, a.z, a.w};
-        const float bv[4] = {b.x, b.y, b.z, b.w};
+    const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t wstride = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    // the loop condition is the same for the whole warp; groups past the end
+    // still join the shuffles
+    for (int64_t base = gw * GPW; base < nsurv; base += wstride * GPW) {
+        const int64_t s = base + int((threadIdx.x & 31) / G);
+        const bool valid = s < nsurv;
+        const uint2 e = valid ? surv[s] : make_uint2(0u, 0u);
+        const float4 *pq = reinterpret_cast<const float4 *>(qraw + int64_t(e.x) * dp);
+        const float4 *pp = reinterpret_cast<const float4 *>(praw + int64_t(e.y) * dp);
+        float H = 0.f, L = 0.f;
+        for (int k4 = lane; valid && k4 < dp / 4; k4 += G) {
+            const float4 a = pp[k4], b = pq[k4];
+            const float av[4] = {a.x, a.y, a.z, a.w};
+            const float bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            if (k4 * 4 + c < d) {
+            for (int c = 0; c < 4; ++c) {
+                // padding columns (k >= d) are zero in both rows: such a step
+                // leaves (H, L) exactly unchanged
                 float sd, ed;
                 two_sum(av[c], -bv[c], sd, ed);
                 const float ph = __fmul_rn(sd, sd);
@@ -495,84 +517,81 @@ __device__ __forceinline__ void decide_group_body(
                 L = __fsub_rn(t3, __fsub_rn(H, s1));
             }
         }
-    }
 #pragma unroll
-    for (int o = G / 2; o; o >>= 1) {
-        const float H2 = __shfl_down_sync(0xffffffffu, H, o, G);
-        const float L2 = __shfl_down_sync(0xffffffffu, L, o, G);
-        float s1, t1;
-        two_sum(H, H2, s1, t1);
-        const float t3 = __fadd_rn(__fadd_rn(t1, L), L2);
-        H = __fadd_rn(s1, t3);
-        L = __fsub_rn(t3, __fsub_rn(H, s1));
-    }
-    if (lane != 0 || !valid) return;
-    const double S_df = (double)H + (double)L;   // exact: |L| <= ulp(H)/2
-    const double rel = ((7.0 * d + 6.0) * 0x1p-48 + (d + 3.0) * 0x1p-53) * 1.01;
-    const double tol = rel * S_df + (double)d * 0x1p-140;
-    bool fallback = !(H < 0x1p100f) || !(H >= 0.f);   // overflow / NaN
-    bool accept = false;
-    float d2 = H;
-    if (!fallback) {
-        if (S_df + tol < R2) accept = true;
-        else if (S_df - tol > R2) accept = false;
-        else fallback = true;
-        if (accept && !fallback && H > 0.f) {
-            const float up = __uint_as_float(__float_as_uint(H) + 1u);
-            const float dn = __uint_as_float(__float_as_uint(H) - 1u);
-            const double half_up = 0.5 * ((double)up - (double)H);
-            const double half_dn = 0.5 * ((double)H - (double)dn);
-            const double room = L >= 0.f ? half_up - (double)L : half_dn + (double)L;
-            if (room <= tol) fallback = true;
+        for (int o = G / 2; o; o >>= 1) {
+            const float H2 = __shfl_down_sync(0xffffffffu, H, o, G);
+            const float L2 = __shfl_down_sync(0xffffffffu, L, o, G);
+            float s1, t1;
+            two_sum(H, H2, s1, t1);
+            const float t3 = __fadd_rn(__fadd_rn(t1, L), L2);
+            H = __fadd_rn(s1, t3);
+            L = __fsub_rn(t3, __fsub_rn(H, s1));
         }
+        if (lane != 0 || !valid) continue;
+        const double S_df = (double)H + (double)L;   // exact: |L| <= ulp(H)/2
+        const double rel = ((7.0 * d + 6.0) * 0x1p-48 + (d + 3.0) * 0x1p-53) * 1.01;
+        const double tol = rel * S_df + (double)d * 0x1p-140;
+        bool fallback = !(H < 0x1p100f) || !(H >= 0.f);   // overflow / NaN
+        bool accept = false;
+        float d2 = H;
+        if (!fallback) {
+            if (S_df + tol < R2) accept = true;
+            else if (S_df - tol > R2) accept = false;
+            else fallback = true;
+            if (accept && !fallback && H > 0.f) {
+                const float up = __uint_as_float(__float_as_uint(H) + 1u);
+                const float dn = __uint_as_float(__float_as_uint(H) - 1u);
+                const double half_up = 0.5 * ((double)up - (double)H);
+                const double half_dn = 0.5 * ((double)H - (double)dn);
+                const double room = L >= 0.f ? half_up - (double)L : half_dn + (double)L;
+                if (room <= tol) fallback = true;
+            }
+        }
+        if (fallback) {
+            const double S = dist2_fp64(pp, pq, d, dp);
+            accept = S <= R2;
+            d2 = (float)S;
+            atomicAdd(n_fp64, 1ull);
+        }
+        int32_t p0 = -1, p1 = -1;
+        if (accept) {
+            const int32_t row = qorder[e.x], col = porder[e.y];
+            p0 = atomicAdd(&counts[row], 1);
+            if (kSym && e.x != e.y) p1 = atomicAdd(&counts[col], 1);
+        }
+        rec_d2[s] = d2;
+        rec_pos[s] = p0;
+        if (kSym) rec_pos[cap + s] = p1;
     }
-    if (fallback) {
-        const double S = dist2_fp64(pp, pq, d, dp);
-        accept = S <= R2;
-        d2 = (float)S;
-        atomicAdd(n_fp64, 1ull);
-    }
-    int32_t p0 = -1, p1 = -1;
-    if (accept) {
-        const int32_t row = qorder[e.x], col = porder[e.y];
-        p0 = atomicAdd(&counts[row], 1);
-        if (kSym && e.x != e.y) p1 = atomicAdd(&counts[col], 1);
-    }
-    rec_d2[s] = d2;
-    rec_pos[s] = p0;
-    if (kSym) rec_pos[nsurv + s] = p1;
 }
 
 #define SNN_DECIDE_ARGS                                                                      \
-    const uint2 *__restrict__ surv, int64_t nsurv, const float *__restrict__ qraw,             \
-        const int32_t *__restrict__ qorder, const float *__restrict__ praw,                    \
-        const int32_t *__restrict__ porder, int d, int dp, double R2,                          \
-        float *__restrict__ rec_d2, int32_t *__restrict__ rec_pos, int32_t *__restrict__ counts, \
-        unsigned long long *__restrict__ n_fp64
+    const uint2 *__restrict__ surv, const unsigned long long *__restrict__ count, int64_t cap, \
+        const float *__restrict__ qraw, const int32_t *__restrict__ qorder,                    \
+        const float *__restrict__ praw, const int32_t *__restrict__ porder, int d, int dp,     \
+        double R2, float *__restrict__ rec_d2, int32_t *__restrict__ rec_pos,                  \
+        int32_t *__restrict__ counts, unsigned long long *__restrict__ n_fp64
+#define SNN_DECIDE_PASS surv, count, cap, qraw, qorder, praw, porder, d, dp, R2, rec_d2, rec_pos, \
+                        counts, n_fp64
 __global__ void __launch_bounds__(256) k_decide_sym(SNN_DECIDE_ARGS) {
-    decide_body<true>(surv, nsurv, qraw, qorder, praw, porder, d, dp, R2, rec_d2, rec_pos, counts,
-                      n_fp64);
+    decide_body<true>(SNN_DECIDE_PASS);
 }
 __global__ void __launch_bounds__(256) k_decide_one(SNN_DECIDE_ARGS) {
-    decide_body<false>(surv, nsurv, qraw, qorder, praw, porder, d, dp, R2, rec_d2, rec_pos, counts,
-                       n_fp64);
+    decide_body<false>(SNN_DECIDE_PASS);
 }
 __global__ void __launch_bounds__(256) k_decide_sym_g8(SNN_DECIDE_ARGS) {
-    decide_group_body<true, 8>(surv, nsurv, qraw, qorder, praw, porder, d, dp, R2, rec_d2,
-                               rec_pos, counts, n_fp64);
+    decide_group_body<true, 8>(SNN_DECIDE_PASS);
 }
 __global__ void __launch_bounds__(256) k_decide_one_g8(SNN_DECIDE_ARGS) {
-    decide_group_body<false, 8>(surv, nsurv, qraw, qorder, praw, porder, d, dp, R2, rec_d2,
-                                rec_pos, counts, n_fp64);
+    decide_group_body<false, 8>(SNN_DECIDE_PASS);
 }
 __global__ void __launch_bounds__(256) k_decide_sym_g32(SNN_DECIDE_ARGS) {
-    decide_group_body<true, 32>(surv, nsurv, qraw, qorder, praw, porder, d, dp, R2, rec_d2,
-                                rec_pos, counts, n_fp64);
+    decide_group_body<true, 32>(SNN_DECIDE_PASS);
 }
 __global__ void __launch_bounds__(256) k_decide_one_g32(SNN_DECIDE_ARGS) {
-    decide_group_body<false, 32>(surv, nsurv, qraw, qorder, praw, porder, d, dp, R2, rec_d2,
-                                 rec_pos, counts, n_fp64);
+    decide_group_body<false, 32>(SNN_DECIDE_PASS);
 }
+#undef SNN_DECIDE_PASS
 #undef SNN_DECIDE_ARGS
 
 __global__ void k_counts_to_i64(const int32_t *__restrict__ counts, int64_t m,
@@ -583,7 +602,7 @@ __global__ void k_counts_to_i64(const int32_t *__restrict__ counts, int64_t m,
 
 // Writes each accepted pair at its row slot (and the mirrored pair of a
 // symmetric self-join), straight into the output CSR arrays.
-__global__ void k_scatter(const uint2 *__restrict__ surv, int64_t nsurv,
+__global__ void k_scatter(const uint2 *__restrict__ surv, int64_t nsurv, int64_t rstride,
                           const int32_t *__restrict__ qorder, const int32_t *__restrict__ porder,
                           const float *__restrict__ rec_d2, const int32_t *__restrict__ rec_pos,
                           int sym, const int64_t *__restrict__ offsets, int32_t *__restrict__ idx,
@@ -598,7 +617,7 @@ __global__ void k_scatter(const uint2 *__restrict__ surv, int64_t nsurv,
     idx[offsets[row] + p0] = col;
     d2[offsets[row] + p0] = v;
     if (sym) {
-        const int32_t p1 = rec_pos[nsurv + s];
+        const int32_t p1 = rec_pos[rstride + s];
         if (p1 >= 0) {
             idx[offsets[col] + p1] = row;
             d2[offsets[col] + p1] = v;

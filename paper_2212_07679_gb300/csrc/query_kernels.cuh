@@ -103,28 +103,23 @@ __global__ void k_query_windows(const float *qalpha, int64_t m, const float *alp
 __global__ void k_score_fp32_single(ScoreArgs a);
 __global__ void k_score_fp32_multi(ScoreArgs a);
 // Exact decision of survivors; _sym emits both orientations of a self-join
-// pair, _one emits the (query, point) orientation only.
-__global__ void k_decide_sym(const uint2 *surv, int64_t nsurv, const float *qraw,
-                             const int32_t *qorder, const float *praw, const int32_t *porder,
-                             int d, int dp, double R2, float *rec_d2, int32_t *rec_pos,
-                             int32_t *counts, unsigned long long *n_fp64);
-__global__ void k_decide_one(const uint2 *surv, int64_t nsurv, const float *qraw,
-                             const int32_t *qorder, const float *praw, const int32_t *porder,
-                             int d, int dp, double R2, float *rec_d2, int32_t *rec_pos,
-                             int32_t *counts, unsigned long long *n_fp64);
-// The same with 8 or 32 lanes per survivor (long rows: coalesced loads).
-#define SNN_DECIDE_DECL(name)                                                              \
-    __global__ void name(const uint2 *surv, int64_t nsurv, const float *qraw,              \
-                         const int32_t *qorder, const float *praw, const int32_t *porder,  \
-                         int d, int dp, double R2, float *rec_d2, int32_t *rec_pos,        \
-                         int32_t *counts, unsigned long long *n_fp64)
+// pair, _one emits the (query, point) orientation only; _g8 / _g32 use 8 or
+// 32 lanes per survivor (long rows).  The survivor count is read on the
+// device (min(*count, cap)); rec_pos[cap + s] is the mirrored slot.
+#define SNN_DECIDE_DECL(name)                                                                \
+    __global__ void name(const uint2 *surv, const unsigned long long *count, int64_t cap,    \
+                         const float *qraw, const int32_t *qorder, const float *praw,        \
+                         const int32_t *porder, int d, int dp, double R2, float *rec_d2,     \
+                         int32_t *rec_pos, int32_t *counts, unsigned long long *n_fp64)
+SNN_DECIDE_DECL(k_decide_sym);
+SNN_DECIDE_DECL(k_decide_one);
 SNN_DECIDE_DECL(k_decide_sym_g8);
 SNN_DECIDE_DECL(k_decide_one_g8);
 SNN_DECIDE_DECL(k_decide_sym_g32);
 SNN_DECIDE_DECL(k_decide_one_g32);
 #undef SNN_DECIDE_DECL
 __global__ void k_counts_to_i64(const int32_t *counts, int64_t m, int64_t *out);
-__global__ void k_scatter(const uint2 *surv, int64_t nsurv, const int32_t *qorder,
+__global__ void k_scatter(const uint2 *surv, int64_t nsurv, int64_t rstride, const int32_t *qorder,
                           const int32_t *porder, const float *rec_d2, const int32_t *rec_pos, int sym,
                           const int64_t *offsets, int32_t *idx, float *d2);
 

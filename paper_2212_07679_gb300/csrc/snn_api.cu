@@ -21,18 +21,25 @@ namespace {
 thread_local char g_err[512] = "";
 std::atomic<unsigned long long> g_launches{0};
 std::atomic<double> g_surv_hint{0.0};   // survivors per query of the last call
-std::once_flag g_pool_once;
 
-void pool_setup() {
+std::mutex g_pool_mu;
+uint64_t g_pool_done = 0;   // bit per device: release threshold raised
+}  // namespace
+
+// The default pool of the current device keeps freed memory cached (no
+// release threshold), so repeated calls reuse it without new allocations.
+void ensure_pool() {
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (g_pool_done & (uint64_t(1) << dev)) return;
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
         uint64_t thr = UINT64_MAX;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
+    g_pool_done |= uint64_t(1) << dev;
 }
-}  // namespace
 
 void set_error(const char *fmt, ...) {
     va_list ap;
@@ -49,14 +56,17 @@ namespace {
 struct SharedBlock {
     void *base;
     int refs;
+    cudaStream_t stream;   // stream of the call that allocated the block
 };
 std::mutex g_blocks_mu;
 std::unordered_map<void *, SharedBlock *> g_blocks;
 }  // namespace
 
-snn_status register_block(void *block, void *const *ptrs, int count) {
+// Registers library-returned pointers into one pool block allocated on
+// stream s; the block is released (stream-ordered, on s) with the last of them.
+snn_status register_block(void *block, void *const *ptrs, int count, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(g_blocks_mu);
-    SharedBlock *b = new (std::nothrow) SharedBlock{block, 0};
+    SharedBlock *b = new (std::nothrow) SharedBlock{block, 0, s};
     if (!b) {
         set_error("host allocation failed");
         return SNN_ENOMEM;
@@ -67,29 +77,25 @@ snn_status register_block(void *block, void *const *ptrs, int count) {
         ++b->refs;
     }
     if (b->refs == 0) {
-        cudaFree(block);
+        cudaFreeAsync(block, s);
         delete b;
     }
     return SNN_OK;
 }
 
+// Pointers the library does not know are left alone.
 static void free_device_ptr(void *p) {
     SharedBlock *b = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_blocks_mu);
         auto it = g_blocks.find(p);
-        if (it != g_blocks.end()) {
-            b = it->second;
-            g_blocks.erase(it);
-            if (--b->refs > 0) return;
-        }
+        if (it == g_blocks.end()) return;
+        b = it->second;
+        g_blocks.erase(it);
+        if (--b->refs > 0) return;
     }
-    if (b) {
-        cudaFree(b->base);
-        delete b;
-    } else {
-        cudaFree(p);
-    }
+    cudaFreeAsync(b->base, b->stream);
+    delete b;
 }
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
@@ -109,18 +115,30 @@ static unsigned grid_for(int64_t work, int threads) {
     return (unsigned)std::max<int64_t>(1, cdiv(work, threads));
 }
 
+// Library-owned device memory comes from the device's stream-ordered pool
+// (no device-wide synchronisation on allocation or release).
 template <typename T>
-static snn_status dev_alloc(T **p, size_t count) {
+static snn_status dev_alloc(T **p, size_t count, cudaStream_t s) {
     void *q = nullptr;
     size_t bytes = std::max<size_t>(count * sizeof(T), 16);
-    cudaError_t e = cudaMalloc(&q, bytes);
+    bytes = (bytes + 255) & ~size_t(255);
+    cudaError_t e = cudaMallocAsync(&q, bytes, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        set_error("cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
         return SNN_ENOMEM;
     }
     *p = static_cast<T *>(q);
     return SNN_OK;
+}
+
+// Returns an output array to the pool, or registers it so that snn_free
+// releases it (stream-ordered, on the stream of the call that made it).
+template <typename T>
+static snn_status own_output(T *p, cudaStream_t s) {
+    if (!p) return SNN_OK;
+    void *ptrs[1] = {p};
+    return register_block(p, ptrs, 1, s);
 }
 
 static void index_release(snn_index *ix) {
@@ -129,7 +147,7 @@ static void index_release(snn_index *ix) {
                     ix->praw, ix->xc,   ix->hx,    ix->nrm,        ix->dconst,     ix->tc_part[0],
                     ix->tc_part[1], ix->tc_part[2]};
     for (void *p : ptrs)
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, ix->stream);
     delete ix;
 }
 
@@ -145,12 +163,14 @@ static snn_status project_sort_gather(const float *X, int64_t n, int d, int64_t 
     SNN_TRY(scr.alloc(&ka, n));
     SNN_TRY(scr.alloc(&va, n));
     const int64_t pthreads = d > 32 ? n * 32 : n;
+    // float4 rows when every row starts on a 16-byte boundary and d = 4k
+    const int vec = (d % 4 == 0 && ld % 4 == 0 && reinterpret_cast<uintptr_t>(X) % 16 == 0) ? 1 : 0;
     SNN_LAUNCH(k_project, grid_for(pthreads, 256), 256, 0, s)(X, n, d, ld, cvec, v32, keys, vals,
-                                                      eps_out, bad);
+                                                      eps_out, bad, vec);
     SNN_LAUNCH_CHECK();
     SNN_TRY(radix_sort_pairs<uint32_t>(keys, vals, ka, va, n, 32, s));
     SNN_LAUNCH(k_gather, grid_for(pthreads, 256), 256, 0, s)(keys, vals, X, n, d, ld, dp, cvec, alpha,
-                                                     order, praw, xc, hx, nrm);
+                                                     order, praw, xc, hx, nrm, vec);
     SNN_LAUNCH_CHECK();
     return SNN_OK;
 }
@@ -178,7 +198,7 @@ static snn_status first_direction(const double *C, const double *diagC, int d, d
 
 static snn_status index_build(const float *X, int64_t n, int d, int64_t ld, cudaStream_t s,
                               snn_index **out) {
-    std::call_once(g_pool_once, pool_setup);
+    ensure_pool();
     snn_index *ix = new (std::nothrow) snn_index();
     if (!ix) {
         set_error("host allocation failed");
@@ -187,6 +207,7 @@ static snn_status index_build(const float *X, int64_t n, int d, int64_t ld, cuda
     ix->n = n;
     ix->d = d;
     ix->dp = (d + 3) & ~3;
+    ix->stream = s;
     cudaGetDevice(&ix->device);
     const int dp = ix->dp;
     snn_status st = SNN_OK;
@@ -199,17 +220,17 @@ static snn_status index_build(const float *X, int64_t n, int d, int64_t ld, cuda
             return st;                     \
         }                                  \
     } while (0)
-    TRY_IX(dev_alloc(&ix->mu64, d));
-    TRY_IX(dev_alloc(&ix->mu32, d));
-    TRY_IX(dev_alloc(&ix->v64, d));
-    TRY_IX(dev_alloc(&ix->v32, d));
-    TRY_IX(dev_alloc(&ix->alpha, n));
-    TRY_IX(dev_alloc(&ix->order, n));
-    TRY_IX(dev_alloc(&ix->praw, size_t(n) * dp));
-    TRY_IX(dev_alloc(&ix->xc, size_t(n) * dp));
-    TRY_IX(dev_alloc(&ix->hx, n));
-    TRY_IX(dev_alloc(&ix->nrm, n));
-    TRY_IX(dev_alloc(&ix->dconst, 4));
+    TRY_IX(dev_alloc(&ix->mu64, d, s));
+    TRY_IX(dev_alloc(&ix->mu32, d, s));
+    TRY_IX(dev_alloc(&ix->v64, d, s));
+    TRY_IX(dev_alloc(&ix->v32, d, s));
+    TRY_IX(dev_alloc(&ix->alpha, n, s));
+    TRY_IX(dev_alloc(&ix->order, n, s));
+    TRY_IX(dev_alloc(&ix->praw, size_t(n) * dp, s));
+    TRY_IX(dev_alloc(&ix->xc, size_t(n) * dp, s));
+    TRY_IX(dev_alloc(&ix->hx, n, s));
+    TRY_IX(dev_alloc(&ix->nrm, n, s));
+    TRY_IX(dev_alloc(&ix->dconst, 4, s));
     {
         Scratch scr(s);
         int *bad;   // [0] NaN/Inf seen, [1] a bounded tensor-core wait expired
@@ -231,7 +252,8 @@ static snn_status index_build(const float *X, int64_t n, int d, int64_t ld, cuda
         SNN_LAUNCH(k_colsum_partial, dim3(unsigned(nb), unsigned(ncb)), TX * TY,
                    TX * TY * sizeof(double), s)(X, n, d, ld, rows, part, bad);
         if (cudaGetLastError() != cudaSuccess) { set_error("colsum launch"); TRY_IX(SNN_ECUDA); }
-        SNN_LAUNCH(k_mean_final, grid_for(d, 128), 128, 0, s)(part, (int)nb, d, n, ix->mu64, ix->mu32);
+        SNN_LAUNCH(k_mean_final, grid_for(int64_t(d) * 32, 128), 128, 0, s)(part, (int)nb, d, n,
+                                                                           ix->mu64, ix->mu32);
         // K2: centred Gram matrix
         double *C, *diagC;
         TRY_IX(scr.alloc(&C, size_t(d) * d));
@@ -244,7 +266,8 @@ static snn_status index_build(const float *X, int64_t n, int d, int64_t ld, cuda
             TRY_IX(scr.alloc(&gpart, size_t(gnb) * d * d));
             auto gk = d <= 16 ? k_gram_small16 : (d <= 32 ? k_gram_small32 : k_gram_small64);
             SNN_LAUNCH(gk, unsigned(gnb), 256, 0, s)(X, n, d, ld, ix->mu32, grows, gpart);
-            SNN_LAUNCH(k_gram_reduce, grid_for(int64_t(d) * d, 256), 256, 0, s)(gpart, (int)gnb, d, C);
+            SNN_LAUNCH(k_gram_reduce, grid_for(int64_t(d) * d * 32, 256), 256, 0, s)(gpart, (int)gnb,
+                                                                                     d, C);
             if (cudaGetLastError() != cudaSuccess) { set_error("gram launch"); TRY_IX(SNN_ECUDA); }
         } else {
             TRY_IX(gram_tc(X, n, d, ld, ix->mu32, C, diagC, bad + 1, s, scr));
@@ -288,6 +311,45 @@ static snn_status index_build(const float *X, int64_t n, int d, int64_t ld, cuda
 }
 
 // ---------------------------------------------------------------- query
+// Everything the host needs after the scoring and decision, gathered on the
+// device and copied back with one transfer.
+struct Readback {
+    unsigned long long ctr[4];   // survivors, work, band pairs, candidates
+    int bad, err;                // NaN/Inf in the queries, expired wait
+    int64_t nnz;
+    unsigned cls[8];             // rows per length class
+    int64_t big_total;           // entries in rows longer than 4096
+};
+
+__global__ void k_readback(const unsigned long long *__restrict__ ctr, const int *__restrict__ bad,
+                           const int *__restrict__ err, const int64_t *__restrict__ nnz,
+                           const unsigned *__restrict__ cls, const int64_t *__restrict__ big_total,
+                           Readback *__restrict__ rb) {
+    const int t = threadIdx.x;
+    if (t < 4) rb->ctr[t] = ctr[t];
+    if (t < 8) rb->cls[t] = cls[t];
+    if (t == 0) {
+        rb->bad = *bad;
+        rb->err = *err;
+        rb->nnz = *nnz;
+        rb->big_total = *big_total;
+    }
+}
+
+// Pinned host buffer of the calling thread (allocated once, kept).
+static Readback *host_readback() {
+    thread_local Readback *p = nullptr;
+    if (!p) {
+        void *q = nullptr;
+        if (cudaMallocHost(&q, sizeof(Readback)) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        p = static_cast<Readback *>(q);
+    }
+    return p;
+}
+
 struct QueryScratch {
     float *alpha = nullptr, *raw = nullptr, *xc = nullptr, *hy = nullptr, *nrm = nullptr;
     int32_t *order = nullptr;
@@ -310,18 +372,22 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     out->offsets = nullptr;
     out->indices = nullptr;
     out->dist2 = nullptr;
-    SNN_TRY(dev_alloc(&out->offsets, m + 1));
+    ensure_pool();
+    SNN_TRY(dev_alloc(&out->offsets, m + 1, s));
     uint2 *surv = nullptr;
+    float *rec_d2 = nullptr;
+    int32_t *rec_pos = nullptr;
     auto fail = [&](snn_status st) {
-        if (surv) cudaFreeAsync(surv, s);
+        void *tmp[] = {surv, rec_d2, rec_pos, out->offsets, out->indices, out->dist2};
+        for (void *p : tmp)
+            if (p) cudaFreeAsync(p, s);
         surv = nullptr;
-        cudaStreamSynchronize(s);
-        if (out->offsets) cudaFree(out->offsets);
-        if (out->indices) cudaFree(out->indices);
-        if (out->dist2) cudaFree(out->dist2);
+        rec_d2 = nullptr;
+        rec_pos = nullptr;
         out->offsets = nullptr;
         out->indices = nullptr;
         out->dist2 = nullptr;
+        out->nnz = 0;
         return st;
     };
 #define TRY_Q(expr)                          \
@@ -340,8 +406,8 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
 
     if (m == 0) {
         CUDA_Q(cudaMemsetAsync(out->offsets, 0, sizeof(int64_t), s));
-        CUDA_Q(cudaStreamSynchronize(s));
         if (stats) std::memset(stats, 0, sizeof(*stats));
+        TRY_Q(own_output(out->offsets, s));
         return SNN_OK;
     }
     cudaEvent_t ev[5] = {};
@@ -444,7 +510,10 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     SNN_LAUNCH(k_item_tiles, grid_for(ntiles, 128), 128, 0, s)(item_off, ntiles, item_tile);
     CUDA_Q(cudaGetLastError());
 
-    // scoring with an adaptive survivor buffer
+    // scoring with an adaptive survivor buffer; the decision, the row counts,
+    // the offsets and the row classes follow without a host round trip, and
+    // one synchronisation then reads every count (a survivor overflow is
+    // detected there and the phase re-run with the exact size)
     double hint;
     {
         std::lock_guard<std::mutex> lk(ix->mu);
@@ -452,10 +521,9 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     }
     if (!(hint > 0)) hint = g_surv_hint.load(std::memory_order_relaxed);
     // generous first guess (the pool keeps the memory cached); an overflow
-    // costs one re-run of the scoring with the exact count
+    // costs one re-run with the exact count
     int64_t cap = std::max<int64_t>(int64_t(1) << 20,
                                     int64_t(std::ceil((hint > 0 ? hint * 1.25 : 96.0) * m)) + 4096);
-    CUDA_Q(cudaMallocAsync(&surv, size_t(cap) * sizeof(uint2), s));
     ScoreArgs sa;
     sa.q = qs;
     sa.x = ds;
@@ -473,11 +541,36 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     TRY_Q(scr.alloc(&dev_err, 1));
     CUDA_Q(cudaMemsetAsync(dev_err, 0, sizeof(int), s));
     sa.err = dev_err;
-    int herr = 0;
-    unsigned long long hctr[4] = {0, 0, 0, 0};
+    int32_t *counts, *lists, *big_list;
+    int64_t *counts64, *big_len, *toff;
+    unsigned *cls;
+    TRY_Q(scr.alloc(&counts, m));
+    TRY_Q(scr.alloc(&counts64, m));
+    TRY_Q(scr.alloc(&lists, 6 * m));
+    TRY_Q(scr.alloc(&big_list, m));
+    TRY_Q(scr.alloc(&big_len, m));
+    TRY_Q(scr.alloc(&toff, m + 1));
+    TRY_Q(scr.alloc(&cls, 8));
+    const double R2 = R * R;
+    // lanes per survivor in the decision: 1 for short rows, 8 up to 128
+    // dimensions, 32 beyond
+    const int G = d <= 32 ? 1 : (d <= 128 ? 8 : 32);
+    auto dk = G == 1 ? (sym ? k_decide_sym : k_decide_one)
+                     : (G == 8 ? (sym ? k_decide_sym_g8 : k_decide_one_g8)
+                               : (sym ? k_decide_sym_g32 : k_decide_one_g32));
+    // one host read-back per attempt (see Readback)
+    Readback *dev_rb = nullptr;
+    TRY_Q(scr.alloc(&dev_rb, 1));
+    Readback *hb = host_readback();
+    if (!hb) {
+        set_error("pinned host allocation failed");
+        return fail(SNN_ENOMEM);
+    }
     int64_t mma_fpp = 0;
-    int hbad = 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
+        CUDA_Q(cudaMallocAsync(&surv, size_t(cap) * sizeof(uint2), s));
+        CUDA_Q(cudaMallocAsync(&rec_d2, size_t(cap) * sizeof(float), s));
+        CUDA_Q(cudaMallocAsync(&rec_pos, size_t(sym ? 2 * cap : cap) * sizeof(int32_t), s));
         sa.surv = surv;
         sa.cap = cap;
         if (stats) cudaEventRecord(ev[1], s);
@@ -497,117 +590,110 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         }
         if (st != SNN_OK) return fail(st);
         if (stats) cudaEventRecord(ev[2], s);
-        cudaError_t e1 = cudaMemcpyAsync(hctr, ctr, 4 * sizeof(unsigned long long),
-                                         cudaMemcpyDeviceToHost, s);
-        cudaError_t e2 = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
-        cudaError_t e4 = cudaMemcpyAsync(&herr, dev_err, sizeof(int), cudaMemcpyDeviceToHost, s);
-        cudaError_t e3 = cudaStreamSynchronize(s);
-        if (e4 != cudaSuccess) e2 = e4;
-        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
-            set_error("scoring failed: %s", cudaGetErrorString(e3 != cudaSuccess ? e3 : e1));
-            return fail(SNN_ECUDA);
+        // exact decision for every survivor (compensated FP32, FP64 where
+        // needed), sized by the device-side survivor count
+        CUDA_Q(cudaMemsetAsync(counts, 0, m * sizeof(int32_t), s));
+        const unsigned dgrid =
+            std::min<unsigned>(grid_for(cap * G, 256), unsigned(16 * device_sm_count()));
+        SNN_LAUNCH(dk, dgrid, 256, 0, s)(surv, ctr, cap, qs.raw, qs.order, ds.raw, ds.order, d, dp,
+                                         R2, rec_d2, rec_pos, counts, ctr + 4);
+        CUDA_Q(cudaGetLastError());
+        if (stats) cudaEventRecord(ev[3], s);
+        SNN_LAUNCH(k_counts_to_i64, grid_for(m, 256), 256, 0, s)(counts, m, counts64);
+        CUDA_Q(cudaGetLastError());
+        TRY_Q(scan_exclusive<int64_t>(counts64, out->offsets, m, s));
+        // rows by length class (per-row sort below); long rows' sizes scanned
+        CUDA_Q(cudaMemsetAsync(cls, 0, 8 * sizeof(unsigned), s));
+        CUDA_Q(cudaMemsetAsync(big_len, 0, m * sizeof(int64_t), s));
+        SNN_LAUNCH(k_seg_classify, grid_for(m, 256), 256, 0, s)(out->offsets, m, lists, big_list,
+                                                                big_len, cls);
+        CUDA_Q(cudaGetLastError());
+        TRY_Q(scan_exclusive<int64_t>(big_len, toff, m, s));
+        SNN_LAUNCH(k_readback, 1, 32, 0, s)(ctr, bad, dev_err, out->offsets + m, cls, toff + m, dev_rb);
+        CUDA_Q(cudaGetLastError());
+        CUDA_Q(cudaMemcpyAsync(hb, dev_rb, sizeof(Readback), cudaMemcpyDeviceToHost, s));
+        {
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) {
+                set_error("query failed: %s", cudaGetErrorString(e));
+                return fail(SNN_ECUDA);
+            }
         }
-        if (hbad) {
+        if (hb->bad) {
             set_error("Q contains NaN or Inf");
             return fail(SNN_EINVAL);
         }
-        if (herr) {
+        if (hb->err) {
             set_error("tensor-core scoring: a bounded wait gave up (pipeline stalled)");
             return fail(SNN_ETIMEOUT);
         }
-        if ((int64_t)hctr[0] <= cap) break;
+        if ((int64_t)hb->ctr[0] <= cap) break;
         if (attempt == 1) {
             set_error("survivor buffer overflow after retry");
             return fail(SNN_EOVERFLOW);
         }
         cudaFreeAsync(surv, s);
+        cudaFreeAsync(rec_d2, s);
+        cudaFreeAsync(rec_pos, s);
         surv = nullptr;
-        cap = (int64_t)hctr[0] + 1024;
-        CUDA_Q(cudaMallocAsync(&surv, size_t(cap) * sizeof(uint2), s));
-        CUDA_Q(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long), s));
+        rec_d2 = nullptr;
+        rec_pos = nullptr;
+        cap = (int64_t)hb->ctr[0] + 1024;
+        CUDA_Q(cudaMemsetAsync(ctr, 0, 8 * sizeof(unsigned long long), s));
+        if (stats) {
+            // the band and candidate counters are recomputed by the re-run
+            SNN_LAUNCH(k_tile_band, grid_for(ntiles, 128), 128, 0, s)(
+                qs.alpha, m, ix->alpha, ix->n, Wbase, ix->dconst, eps_q, tile_lo, tile_hi, items,
+                ntiles, sym, ctr + 2);
+            SNN_LAUNCH(k_query_windows, grid_for(m, 256), 256, 0, s)(qs.alpha, m, ix->alpha, ix->n,
+                                                                     Wbase, ix->dconst, eps_q, ctr + 3);
+            CUDA_Q(cudaGetLastError());
+        }
     }
-    const int64_t nsurv = (int64_t)hctr[0];
+    const int64_t nsurv = (int64_t)hb->ctr[0];
     {
         std::lock_guard<std::mutex> lk(ix->mu);
         ix->surv_hint = double(nsurv) / double(m);
     }
     g_surv_hint.store(double(nsurv) / double(m), std::memory_order_relaxed);
-
-    // exact decision for every survivor (compensated FP32, FP64 where needed)
-    int32_t *rec_pos, *counts;
-    float *rec_d2;
-    int64_t *counts64;
-    TRY_Q(scr.alloc(&rec_d2, nsurv));
-    TRY_Q(scr.alloc(&rec_pos, sym ? 2 * nsurv : nsurv));
-    TRY_Q(scr.alloc(&counts, m));
-    TRY_Q(scr.alloc(&counts64, m));
-    CUDA_Q(cudaMemsetAsync(counts, 0, m * sizeof(int32_t), s));
-    const double R2 = R * R;
-    if (nsurv > 0) {
-        // lanes per survivor: 1 for short rows, 8 up to 128 dims, 32 beyond
-        const int G = d <= 32 ? 1 : (d <= 128 ? 8 : 32);
-        auto dk = G == 1 ? (sym ? k_decide_sym : k_decide_one)
-                         : (G == 8 ? (sym ? k_decide_sym_g8 : k_decide_one_g8)
-                                   : (sym ? k_decide_sym_g32 : k_decide_one_g32));
-        SNN_LAUNCH(dk, grid_for(nsurv * G, 256), 256, 0, s)(
-            surv, nsurv, qs.raw, qs.order, ds.raw, ds.order, d, dp, R2, rec_d2, rec_pos, counts,
-            ctr + 4);
-        CUDA_Q(cudaGetLastError());
-    }
-    if (stats) cudaEventRecord(ev[3], s);
-    SNN_LAUNCH(k_counts_to_i64, grid_for(m, 256), 256, 0, s)(counts, m, counts64);
-    CUDA_Q(cudaGetLastError());
-    TRY_Q(scan_exclusive<int64_t>(counts64, out->offsets, m, s));
-    int64_t nnz = 0;
-    CUDA_Q(cudaMemcpyAsync(&nnz, out->offsets + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    CUDA_Q(cudaStreamSynchronize(s));
+    const int64_t nnz = hb->nnz;
     if (nnz >= (int64_t(1) << 31)) {
         set_error("%lld neighbour pairs exceed this build's limit of 2^31-1", (long long)nnz);
         return fail(SNN_ENOTSUP);
     }
     out->nnz = nnz;
     if (nnz > 0) {
-        TRY_Q(dev_alloc(&out->indices, nnz));
-        TRY_Q(dev_alloc(&out->dist2, nnz));
-        SNN_LAUNCH(k_scatter, grid_for(nsurv, 256), 256, 0, s)(surv, nsurv, qs.order, ds.order,
+        TRY_Q(dev_alloc(&out->indices, nnz, s));
+        TRY_Q(dev_alloc(&out->dist2, nnz, s));
+        SNN_LAUNCH(k_scatter, grid_for(nsurv, 256), 256, 0, s)(surv, nsurv, cap, qs.order, ds.order,
                                                                rec_d2, rec_pos, sym, out->offsets,
                                                                out->indices, out->dist2);
         CUDA_Q(cudaGetLastError());
-        // per-row ascending column ids, in place
-        int32_t *lists, *big_list;
-        int64_t *big_len, *toff;
-        unsigned *cls;
-        TRY_Q(scr.alloc(&lists, 6 * m));
-        TRY_Q(scr.alloc(&big_list, m));
-        TRY_Q(scr.alloc(&big_len, m));
-        TRY_Q(scr.alloc(&toff, m + 1));
-        TRY_Q(scr.alloc(&cls, 8));
-        CUDA_Q(cudaMemsetAsync(cls, 0, 8 * sizeof(unsigned), s));
-        SNN_LAUNCH(k_seg_classify, grid_for(m, 256), 256, 0, s)(out->offsets, m, lists, big_list,
-                                                                big_len, cls);
-        const unsigned wgrid = std::min<unsigned>(grid_for(m * 32, 256), 16384);
-        SNN_LAUNCH(k_seg_sort_w1, wgrid, 256, 0, s)(lists, cls, out->offsets, out->indices,
-                                                     out->dist2);
-        SNN_LAUNCH(k_seg_sort_w2, wgrid, 256, 0, s)(lists + 5 * m, cls + 6, out->offsets,
-                                                     out->indices, out->dist2);
-        SNN_LAUNCH(k_seg_sort_w4, wgrid, 256, 0, s)(lists + m, cls + 1, out->offsets, out->indices,
-                                                     out->dist2);
-        SNN_LAUNCH(k_seg_sort_w8, wgrid, 256, 0, s)(lists + 4 * m, cls + 5, out->offsets,
-                                                     out->indices, out->dist2);
-        SNN_LAUNCH(k_seg_sort_w16, wgrid, 256, 0, s)(lists + 2 * m, cls + 2, out->offsets,
-                                                      out->indices, out->dist2);
-        SNN_LAUNCH(k_seg_sort_mid, std::min<unsigned>((unsigned)m, 4096), 256, 0, s)(
+        // per-row ascending column ids, in place; classes with no rows are
+        // skipped and the grids sized by the class counts
+        const unsigned *hc = hb->cls;
+        auto wgrid = [&](unsigned rows) {
+            return std::min<unsigned>(grid_for(int64_t(rows) * 32, 256), 16384);
+        };
+        if (hc[0]) SNN_LAUNCH(k_seg_sort_w1, wgrid(hc[0]), 256, 0, s)(lists, cls, out->offsets,
+                                                                     out->indices, out->dist2);
+        if (hc[6]) SNN_LAUNCH(k_seg_sort_w2, wgrid(hc[6]), 256, 0, s)(lists + 5 * m, cls + 6,
+                                                                     out->offsets, out->indices,
+                                                                     out->dist2);
+        if (hc[1]) SNN_LAUNCH(k_seg_sort_w4, wgrid(hc[1]), 256, 0, s)(lists + m, cls + 1, out->offsets,
+                                                                     out->indices, out->dist2);
+        if (hc[5]) SNN_LAUNCH(k_seg_sort_w8, wgrid(hc[5]), 256, 0, s)(lists + 4 * m, cls + 5,
+                                                                     out->offsets, out->indices,
+                                                                     out->dist2);
+        if (hc[2]) SNN_LAUNCH(k_seg_sort_w16, wgrid(hc[2]), 256, 0, s)(lists + 2 * m, cls + 2,
+                                                                      out->offsets, out->indices,
+                                                                      out->dist2);
+        if (hc[3]) SNN_LAUNCH(k_seg_sort_mid, std::min<unsigned>(hc[3], 4096), 256, 0, s)(
             lists + 3 * m, cls + 3, out->offsets, out->indices, out->dist2);
         CUDA_Q(cudaGetLastError());
-        unsigned hcls[8];
-        CUDA_Q(cudaMemcpyAsync(hcls, cls, sizeof(hcls), cudaMemcpyDeviceToHost, s));
-        CUDA_Q(cudaStreamSynchronize(s));
-        const int nbig = (int)hcls[4];
+        const int nbig = (int)hc[4];
         if (nbig > 0) {
-            TRY_Q(scan_exclusive<int64_t>(big_len, toff, nbig, s));
-            int64_t tot = 0;
-            CUDA_Q(cudaMemcpyAsync(&tot, toff + nbig, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-            CUDA_Q(cudaStreamSynchronize(s));
+            const int64_t tot = hb->big_total;
             uint64_t *bk, *bka;
             uint32_t *bv, *bva;
             float *gd2;
@@ -628,7 +714,11 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         }
     }
     cudaFreeAsync(surv, s);
+    cudaFreeAsync(rec_d2, s);
+    cudaFreeAsync(rec_pos, s);
     surv = nullptr;
+    rec_d2 = nullptr;
+    rec_pos = nullptr;
     if (stats) {
         cudaEventRecord(ev[4], s);
         unsigned long long nf = 0;
@@ -636,8 +726,8 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         CUDA_Q(cudaStreamSynchronize(s));
         stats->exact_fp64 = (int64_t)nf;
         stats->mma_flops_per_pair = mma_fpp;
-        stats->candidates = (int64_t)hctr[3];
-        stats->band_pairs = (int64_t)hctr[2];
+        stats->candidates = (int64_t)hb->ctr[3];
+        stats->band_pairs = (int64_t)hb->ctr[2];
         stats->survivors = nsurv;
         stats->nnz = nnz;
         cudaEventElapsedTime(&stats->ms_prep, ev[0], ev[1]);
@@ -646,6 +736,10 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         cudaEventElapsedTime(&stats->ms_csr, ev[3], ev[4]);
         for (auto &e : ev) cudaEventDestroy(e);
     }
+    // the caller owns the output arrays (released by snn_free)
+    TRY_Q(own_output(out->offsets, s));
+    TRY_Q(own_output(out->indices, s));
+    TRY_Q(own_output(out->dist2, s));
 #undef TRY_Q
 #undef CUDA_Q
     return SNN_OK;
@@ -716,7 +810,7 @@ snn_status snn_query_radius_batch(int32_t nsets, const snn_index *const *idx, co
         set_error("precision %d is not available in this build", (int)prec);
         return SNN_ENOTSUP;
     }
-    std::call_once(g_pool_once, pool_setup);
+    ensure_pool();
     return batch_query(nsets, idx, Q, m, ldq, R, static_cast<cudaStream_t>(stream), out);
 }
 
@@ -758,10 +852,9 @@ snn_status snn_dbscan(const float *X, int64_t n, int32_t d, int64_t ld, double e
             }
         }
     }
-    cudaStreamSynchronize(s);
-    cudaFree(csr.offsets);
-    if (csr.indices) cudaFree(csr.indices);
-    if (csr.dist2) cudaFree(csr.dist2);
+    free_device_ptr(csr.offsets);
+    free_device_ptr(csr.indices);
+    free_device_ptr(csr.dist2);
     index_release(ix);
     return st;
 }

@@ -642,13 +642,14 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
         std::lock_guard<std::mutex> lk(ix->mu);
         if (ix->tc_nsplit != nsplit || ix->tc_k2 != K2 || ix->tc_k2n != K2n) {
             for (int p = 0; p < 3; ++p) {
-                if (ix->tc_part[p]) cudaFree(ix->tc_part[p]);
+                if (ix->tc_part[p]) cudaFreeAsync(ix->tc_part[p], s);
                 ix->tc_part[p] = nullptr;
             }
             ix->tc_nsplit = 0;
             for (int p = 0; p < nsplit; ++p) {
                 const int w = p == 0 ? K2 : K2n;
-                cudaError_t e = cudaMalloc(&ix->tc_part[p], size_t(ix->n) * w * sizeof(uint16_t));
+                cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&ix->tc_part[p]),
+                                                size_t(ix->n) * w * sizeof(uint16_t), s);
                 if (e != cudaSuccess) {
                     set_error("BF16 operand allocation failed: %s", cudaGetErrorString(e));
                     return SNN_ENOMEM;
@@ -713,8 +714,10 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
     if (kp <= 64)
         return nsplit == 2 ? launch_tc<2, 64, 128, true, 1, 64, 1>(ix, sa, qp, K2, K2n, ts1, s)
                            : launch_tc<3, 64, 128, true, 1, 64, 1>(ix, sa, qp, K2, K2n, ts1, s);
-    return nsplit == 2 ? launch_tc<2, 64, 128, false, 1, 64, 1>(ix, sa, qp, K2, K2n, ts1, s)
-                       : launch_tc<3, 64, 128, false, 1, 64, 1>(ix, sa, qp, K2, K2n, ts1, s);
+    // high d: 128 x 256 accumulators (each query k-block feeds two 128-row
+    // halves of the band chunk), 32-column k-blocks, four stages
+    return nsplit == 2 ? launch_tc<2, 32, 256, false, 1, 32, 1>(ix, sa, qp, K2, K2n, ts1, s)
+                       : launch_tc<3, 32, 256, false, 1, 32, 1>(ix, sa, qp, K2, K2n, ts1, s);
 }
 
 }  // namespace snn
