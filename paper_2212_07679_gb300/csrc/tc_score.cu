@@ -106,7 +106,11 @@ struct TcShape {
     static constexpr int kBStage = kTB0 + (NSPLIT - 1) * kTB1;
     static constexpr int kAResBytes = ARES ? 2 * kASlot : 0;
     static constexpr int kStageBytes = ARES ? kBStage : kASlot + kBStage;
-    static constexpr int kStagesRaw = (kSmemBudget - kAResBytes) / kStageBytes;
+    // per-epilogue-warp staging of survivors (flushed in batches: one
+    // global atomic per batch instead of one per 32-column group)
+    static constexpr int kStgEntries = 128;
+    static constexpr int kStgBytes = tc_epi_warps(MT) * kStgEntries * 8;
+    static constexpr int kStagesRaw = (kSmemBudget - kAResBytes - kStgBytes) / kStageBytes;
     static constexpr int kStages = kStagesRaw > 8 ? 8 : kStagesRaw;
     static constexpr int kNP = NSPLIT == 2 ? 3 : 6;     // MMAs per k-step
     static constexpr int kKSteps = BK / 16;             // k-steps per k-block
@@ -115,7 +119,8 @@ struct TcShape {
     static constexpr uint32_t kTmemCols = 2 * MT * BN;
     static constexpr int kEpiWarps = tc_epi_warps(MT);
     static constexpr int kThreads = tc_threads(MT);
-    static constexpr size_t kSmem = size_t(kAResBytes) + size_t(kStages) * kStageBytes + kAlign + 256;
+    static constexpr size_t kSmem =
+        size_t(kAResBytes) + size_t(kStages) * kStageBytes + kAlign + 256 + kStgBytes;
     static_assert(kStagesRaw >= 2, "shape does not fit shared memory");
     static_assert(ARES || NW == BK, "narrow parts need a resident query tile");
     static_assert(MT == 1 || ARES, "several query tiles per item need a resident query tile");
@@ -205,6 +210,8 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
     volatile int *s_abort = reinterpret_cast<volatile int *>(gmisc + 4);
     volatile int *s_consumed = reinterpret_cast<volatile int *>(gmisc + 8);
     volatile int *s_aconsumed = reinterpret_cast<volatile int *>(gmisc + 12);
+    // survivor staging: kStgEntries per epilogue warp, after the barriers
+    uint2 *s_stg = reinterpret_cast<uint2 *>(gbase + (bar0 - base) + 256);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const CUtensorMap *qa[3] = {&qa0, &qa1, &qa2};
@@ -350,6 +357,22 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
         const int ht = sub >> 1;                   // which query sub-tile
         const int qi = ht * kTM + quad * 32 + lane;   // query row within the item's tiles
         constexpr int kGroups = BN / 32 / 2;       // 32-column groups per warp
+        constexpr int kStg = Sh::kStgEntries;
+        uint2 *stg = s_stg + ew * kStg;
+        int scount = 0;                            // staged entries (warp-uniform)
+        // moves the staged survivors to the global list: one atomic, then
+        // coalesced 8-byte stores
+        auto flush = [&]() {
+            if (scount == 0) return;
+            __syncwarp();
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(a.count, (unsigned long long)scount);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            for (int k = lane; k < scount; k += 32)
+                if (base + k < (unsigned long long)a.cap) a.surv[base + k] = stg[k];
+            __syncwarp();
+            scount = 0;
+        };
         int chunk = 0;
         bool ok = true;
         for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
@@ -412,15 +435,28 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                                 if (lane >= o) incl += y;
                             }
                             const int wtot = __shfl_sync(0xffffffffu, incl, 31);
-                            unsigned long long pos = 0;
-                            if (lane == 31) pos = atomicAdd(a.count, (unsigned long long)wtot);
-                            pos = __shfl_sync(0xffffffffu, pos, 31) + (unsigned long long)(incl - cnt);
-                            while (mask) {
-                                const int i = __ffs(mask) - 1;
-                                mask &= mask - 1;
-                                if (pos < (unsigned long long)a.cap)
-                                    a.surv[pos] = make_uint2(unsigned(q), unsigned(j0 + cb * 32 + i));
-                                ++pos;
+                            if (scount + wtot > kStg) flush();
+                            if (wtot <= kStg) {
+                                int p = scount + incl - cnt;
+                                while (mask) {
+                                    const int i = __ffs(mask) - 1;
+                                    mask &= mask - 1;
+                                    stg[p++] = make_uint2(unsigned(q), unsigned(j0 + cb * 32 + i));
+                                }
+                                scount += wtot;
+                            } else {
+                                // more than a staging buffer at once: straight out
+                                unsigned long long pos = 0;
+                                if (lane == 31) pos = atomicAdd(a.count, (unsigned long long)wtot);
+                                pos = __shfl_sync(0xffffffffu, pos, 31) +
+                                      (unsigned long long)(incl - cnt);
+                                while (mask) {
+                                    const int i = __ffs(mask) - 1;
+                                    mask &= mask - 1;
+                                    if (pos < (unsigned long long)a.cap)
+                                        a.surv[pos] = make_uint2(unsigned(q), unsigned(j0 + cb * 32 + i));
+                                    ++pos;
+                                }
                             }
                         }
                     }
@@ -429,6 +465,7 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                 mbar_arrive(tempty_bar(b));
             }
         }
+        flush();
     }
     __syncthreads();
     // drain TMA copies still in flight (only after an abort)
