@@ -183,56 +183,43 @@ k_b_decide(const uint2 *__restrict__ surv, int64_t nsurv, const SetDesc *__restr
     const float4 *pq = reinterpret_cast<const float4 *>(sd.q_raw + ql * dp);
     const float4 *pp = reinterpret_cast<const float4 *>(sd.x_raw + int64_t(e.y) * dp);
     float H = 0.f, L = 0.f;
+    bool nz = false;
     for (int k4 = 0; k4 < dp / 4; ++k4) {
         const float4 a = pp[k4], b = pq[k4];
         const float av[4] = {a.x, a.y, a.z, a.w};
         const float bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            if (k4 * 4 + c < d) {
-                float sd_, ed;
-                two_sum_b(av[c], -bv[c], sd_, ed);
-                const float ph = __fmul_rn(sd_, sd_);
-                const float pl = __fmaf_rn(sd_, sd_, -ph);
-                const float cc = __fmaf_rn(__fadd_rn(sd_, sd_), ed, pl);
-                float s1, t1;
-                two_sum_b(H, ph, s1, t1);
-                const float t3 = __fadd_rn(__fadd_rn(t1, L), cc);
-                H = __fadd_rn(s1, t3);
-                L = __fsub_rn(t3, __fsub_rn(H, s1));
-            }
+            // padding columns (k >= d) are zero in both rows: such a step
+            // leaves (H, L) exactly unchanged
+            float sd_, ed;
+            two_sum_b(av[c], -bv[c], sd_, ed);
+            nz |= sd_ != 0.f;
+            const float ph = __fmul_rn(sd_, sd_);
+            const float pl = __fmaf_rn(sd_, sd_, -ph);
+            const float cc = __fmaf_rn(__fadd_rn(sd_, sd_), ed, pl);
+            float s1, t1;
+            two_sum_b(H, ph, s1, t1);
+            const float t3 = __fadd_rn(__fadd_rn(t1, L), cc);
+            H = __fadd_rn(s1, t3);
+            L = __fsub_rn(t3, __fsub_rn(H, s1));
         }
     }
-    const double S_df = (double)H + (double)L;
-    const double rel = ((7.0 * d + 6.0) * 0x1p-48 + (d + 3.0) * 0x1p-53) * 1.01;
-    const double tol = rel * S_df + (double)d * 0x1p-140;
     const double R2 = sd.R2;
-    bool fallback = !(H < 0x1p100f) || !(H >= 0.f);
-    bool accept = false;
-    float d2 = H;
-    if (!fallback) {
-        if (S_df + tol < R2) accept = true;
-        else if (S_df - tol > R2) accept = false;
-        else fallback = true;
-        if (accept && !fallback && H > 0.f) {
-            const float up = __uint_as_float(__float_as_uint(H) + 1u);
-            const float dn = __uint_as_float(__float_as_uint(H) - 1u);
-            const double half_up = 0.5 * ((double)up - (double)H);
-            const double half_dn = 0.5 * ((double)H - (double)dn);
-            const double room = L >= 0.f ? half_up - (double)L : half_dn + (double)L;
-            if (room <= tol) fallback = true;
-        }
-    }
-    if (fallback) {
+    const DecideConsts dc = decide_consts(d, R2);
+    float d2 = 0.f;
+    int v = decide_df(H, L, nz, dc, &d2);
+    if (v == 2) {
         double S = 0.0;
         for (int k = 0; k < d; ++k) {
             const double t = __dsub_rn((double)sd.x_raw[int64_t(e.y) * dp + k],
                                        (double)sd.q_raw[ql * dp + k]);
             S = __dadd_rn(S, __dmul_rn(t, t));
         }
-        accept = S <= R2;
+        v = S <= R2 ? 1 : 0;
         d2 = (float)S;
     }
+    const bool accept = v == 1;
     int32_t p0 = -1, p1 = -1;
     if (accept) {
         const int64_t row = sd.q_glob + sd.q_order[ql];

@@ -387,13 +387,14 @@ template <bool kSym>
 __device__ __forceinline__ void decide_one_survivor(
          int64_t s, const uint2 *__restrict__ surv, int64_t cap, const float *__restrict__ qraw,
          const int32_t *__restrict__ qorder, const float *__restrict__ praw,
-         const int32_t *__restrict__ porder, int d, int dp, double R2,
+         const int32_t *__restrict__ porder, int d, int dp, double R2, const DecideConsts &dc,
          float *__restrict__ rec_d2, int32_t *__restrict__ rec_pos, int32_t *__restrict__ counts,
          unsigned long long *__restrict__ n_fp64) {
     const uint2 e = surv[s];
     const float4 *pq = reinterpret_cast<const float4 *>(qraw + int64_t(e.x) * dp);
     const float4 *pp = reinterpret_cast<const float4 *>(praw + int64_t(e.y) * dp);
     float H = 0.f, L = 0.f;
+    bool nz = false;
     for (int k4 = 0; k4 < dp / 4; ++k4) {
         const float4 a = pp[k4], b = pq[k4];
         const float av[4] = {a.x, a.y, a.z, a.w};
@@ -404,6 +405,7 @@ __device__ __forceinline__ void decide_one_survivor(
             // leaves (H, L) exactly unchanged
             float sd, ed;
             two_sum(av[c], -bv[c], sd, ed);
+            nz |= sd != 0.f;
             const float ph = __fmul_rn(sd, sd);
             const float pl = __fmaf_rn(sd, sd, -ph);
             const float cc = __fmaf_rn(__fadd_rn(sd, sd), ed, pl);
@@ -414,32 +416,15 @@ __device__ __forceinline__ void decide_one_survivor(
             L = __fsub_rn(t3, __fsub_rn(H, s1));
         }
     }
-    const double S_df = (double)H + (double)L;   // exact: |L| <= ulp(H)/2
-    const double rel = ((7.0 * d + 6.0) * 0x1p-48 + (d + 3.0) * 0x1p-53) * 1.01;
-    const double tol = rel * S_df + (double)d * 0x1p-140;
-    bool fallback = !(H < 0x1p100f) || !(H >= 0.f);   // overflow / NaN
-    bool accept = false;
-    float d2 = H;
-    if (!fallback) {
-        if (S_df + tol < R2) accept = true;
-        else if (S_df - tol > R2) accept = false;
-        else fallback = true;
-        if (accept && !fallback && H > 0.f) {
-            // distance of S to the rounding boundaries of H = fl32(S)
-            const float up = __uint_as_float(__float_as_uint(H) + 1u);
-            const float dn = __uint_as_float(__float_as_uint(H) - 1u);
-            const double half_up = 0.5 * ((double)up - (double)H);
-            const double half_dn = 0.5 * ((double)H - (double)dn);
-            const double room = L >= 0.f ? half_up - (double)L : half_dn + (double)L;
-            if (room <= tol) fallback = true;
-        }
-    }
-    if (fallback) {
+    float d2 = 0.f;
+    int v = decide_df(H, L, nz, dc, &d2);
+    if (v == 2) {
         const double S = dist2_fp64(pp, pq, d, dp);
-        accept = S <= R2;
+        v = S <= R2 ? 1 : 0;
         d2 = (float)S;
         atomicAdd(n_fp64, 1ull);
     }
+    const bool accept = v == 1;
     // record: dist2 and the slot of the pair within its row (from the
     // counting atomic, so the scatter needs no atomics); -1 = not a neighbour.
     // A symmetric self-join pair also takes a slot in the mirrored row.
@@ -463,8 +448,9 @@ __device__ __forceinline__ void decide_body(
          int32_t *__restrict__ counts, unsigned long long *__restrict__ n_fp64) {
     const int64_t nsurv = min((int64_t)*count, cap);
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    const DecideConsts dc = decide_consts(d, R2);
     for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < nsurv; s += stride)
-        decide_one_survivor<kSym>(s, surv, cap, qraw, qorder, praw, porder, d, dp, R2, rec_d2,
+        decide_one_survivor<kSym>(s, surv, cap, qraw, qorder, praw, porder, d, dp, R2, dc, rec_d2,
                                   rec_pos, counts, n_fp64);
 }
 
@@ -485,6 +471,7 @@ __device__ __forceinline__ void decide_group_body(
          int32_t *__restrict__ counts, unsigned long long *__restrict__ n_fp64) {
     constexpr int GPW = 32 / G;   // groups per warp
     const int64_t nsurv = min((int64_t)*count, cap);
+    const DecideConsts dc = decide_consts(d, R2);
     const int lane = int(threadIdx.x % G);
     const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t wstride = (int64_t(gridDim.x) * blockDim.x) >> 5;
@@ -497,6 +484,7 @@ __device__ __forceinline__ void decide_group_body(
         const float4 *pq = reinterpret_cast<const float4 *>(qraw + int64_t(e.x) * dp);
         const float4 *pp = reinterpret_cast<const float4 *>(praw + int64_t(e.y) * dp);
         float H = 0.f, L = 0.f;
+        bool nz = false;
         for (int k4 = lane; valid && k4 < dp / 4; k4 += G) {
             const float4 a = pp[k4], b = pq[k4];
             const float av[4] = {a.x, a.y, a.z, a.w};
@@ -507,6 +495,7 @@ __device__ __forceinline__ void decide_group_body(
                 // leaves (H, L) exactly unchanged
                 float sd, ed;
                 two_sum(av[c], -bv[c], sd, ed);
+                nz |= sd != 0.f;
                 const float ph = __fmul_rn(sd, sd);
                 const float pl = __fmaf_rn(sd, sd, -ph);
                 const float cc = __fmaf_rn(__fadd_rn(sd, sd), ed, pl);
@@ -527,32 +516,17 @@ __device__ __forceinline__ void decide_group_body(
             H = __fadd_rn(s1, t3);
             L = __fsub_rn(t3, __fsub_rn(H, s1));
         }
+        if (G > 1) nz = __any_sync(0xffffffffu, nz);   // (any lane of the warp: conservative)
         if (lane != 0 || !valid) continue;
-        const double S_df = (double)H + (double)L;   // exact: |L| <= ulp(H)/2
-        const double rel = ((7.0 * d + 6.0) * 0x1p-48 + (d + 3.0) * 0x1p-53) * 1.01;
-        const double tol = rel * S_df + (double)d * 0x1p-140;
-        bool fallback = !(H < 0x1p100f) || !(H >= 0.f);   // overflow / NaN
-        bool accept = false;
-        float d2 = H;
-        if (!fallback) {
-            if (S_df + tol < R2) accept = true;
-            else if (S_df - tol > R2) accept = false;
-            else fallback = true;
-            if (accept && !fallback && H > 0.f) {
-                const float up = __uint_as_float(__float_as_uint(H) + 1u);
-                const float dn = __uint_as_float(__float_as_uint(H) - 1u);
-                const double half_up = 0.5 * ((double)up - (double)H);
-                const double half_dn = 0.5 * ((double)H - (double)dn);
-                const double room = L >= 0.f ? half_up - (double)L : half_dn + (double)L;
-                if (room <= tol) fallback = true;
-            }
-        }
-        if (fallback) {
+        float d2 = 0.f;
+        int v = decide_df(H, L, nz, dc, &d2);
+        if (v == 2) {
             const double S = dist2_fp64(pp, pq, d, dp);
-            accept = S <= R2;
+            v = S <= R2 ? 1 : 0;
             d2 = (float)S;
             atomicAdd(n_fp64, 1ull);
         }
+        const bool accept = v == 1;
         int32_t p0 = -1, p1 = -1;
         if (accept) {
             const int32_t row = qorder[e.x], col = porder[e.y];

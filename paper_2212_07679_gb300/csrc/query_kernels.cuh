@@ -102,6 +102,52 @@ __global__ void k_query_windows(const float *qalpha, int64_t m, const float *alp
                                 unsigned long long *cand);
 __global__ void k_score_fp32_single(ScoreArgs a);
 __global__ void k_score_fp32_multi(ScoreArgs a);
+// Tier-1 membership and dist2 from the compensated FP32 value H + L of S
+// (|H + L - S_true| <= (7d + 5) u^2 S, and the FP64 oracle within
+// gamma_{d+2} S of S_true) with FP32 arithmetic only (FP64 is slow on this
+// part).  R^2 = fl64(R*R) is held as the float pair (r2h, r2l) with
+// |R^2 - r2h - r2l| <= 2^-48 R^2.  D = fl(fl(H - r2h) + fl(L - r2l)) is within
+// 2^-46 max(H, r2h) of H + L - R^2 (H - r2h is exact when the two are within a
+// factor of two; otherwise |D| is far beyond the tolerance and only its sign
+// matters).  Returns 1 (accept, *d2 = (float)S), 0 (reject) or 2 (take the
+// FP64 loop: near-ties, values near a float rounding boundary, overflow,
+// underflow).  nz: some coordinate differs (H = 0 with nz may be an
+// underflow).
+struct DecideConsts {
+    float r2h, r2l, rel, rel2, tiny;
+};
+
+__device__ __forceinline__ DecideConsts decide_consts(int d, double R2) {
+    DecideConsts c;
+    c.r2h = (float)R2;
+    c.r2l = (float)(R2 - (double)c.r2h);
+    c.rel = (float)(((7.0 * d + 6.0) * 0x1p-48 + (d + 3.0) * 0x1p-53) * 1.02);
+    c.rel2 = 0x1p-45f;
+    c.tiny = (float)(d * 0x1p-140);
+    return c;
+}
+
+__device__ __forceinline__ int decide_df(float H, float L, bool nz, const DecideConsts &c,
+                                         float *d2) {
+    if (!(H < 0x1p100f) || !(H >= 0.f)) return 2;      // overflow / NaN
+    if (H < 0x1p-100f && nz) return 2;                 // possible underflow
+    const float T = __fmul_ru(__fmaf_ru(c.rel, H, __fmaf_ru(c.rel2, fmaxf(H, c.r2h), c.tiny)),
+                              1.f + 0x1p-20f);
+    const float D = __fadd_rn(__fsub_rn(H, c.r2h), __fsub_rn(L, c.r2l));
+    if (D > T) return 0;
+    if (!(D < -T)) return 2;
+    if (H > 0.f) {
+        // (float)S = H unless S lies within T of a rounding boundary of H
+        const float up = __uint_as_float(__float_as_uint(H) + 1u);
+        const float dn = __uint_as_float(__float_as_uint(H) - 1u);
+        const float half_up = 0.5f * __fsub_rn(up, H), half_dn = 0.5f * __fsub_rn(H, dn);
+        const float room = L >= 0.f ? __fsub_rn(half_up, L) : __fadd_rn(half_dn, L);
+        if (!(room > __fmaf_ru(0x1p-22f, half_up, T))) return 2;
+    }
+    *d2 = H;
+    return 1;
+}
+
 // Exact decision of survivors; _sym emits both orientations of a self-join
 // pair, _one emits the (query, point) orientation only; _g8 / _g32 use 8 or
 // 32 lanes per survivor (long rows).  The survivor count is read on the

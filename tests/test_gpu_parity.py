@@ -121,6 +121,11 @@ def test_edge_cases(snn, prec):
     cases.append(("d=17 ragged", rng.integers(-2, 3, (777, 17)).astype(np.float32), None, 2.0))
     off = (rng.standard_normal((900, 5)) + 1e4).astype(np.float32)
     cases.append(("large offset", off, None, 1.2))
+    # squared distances in the FP32 subnormal range (the compensated tier
+    # underflows there and must hand the pair to the FP64 loop)
+    tiny = np.array([[0, 0], [2.0 ** -74, 0], [0, 2.0 ** -60], [1e-30, 1e-30], [2.0 ** -80, 2.0 ** -80]],
+                    np.float32)
+    cases.append(("subnormal distances", tiny, None, 1e-20))
     grid = np.stack(np.meshgrid(np.arange(12), np.arange(12), np.arange(12)), -1).reshape(-1, 3)
     cases.append(("integer grid exact ties", grid.astype(np.float32), None, 1.0))
     cases.append(("all within R (long rows)", rng.random((4500, 3)).astype(np.float32), None, 2.0))
