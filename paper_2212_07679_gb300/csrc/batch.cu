@@ -234,8 +234,7 @@ k_b_decide(const uint2 *__restrict__ surv, int64_t nsurv, const SetDesc *__restr
 __global__ void k_b_scatter(const uint2 *__restrict__ surv, int64_t nsurv,
                             const SetDesc *__restrict__ sets, const int32_t *__restrict__ qset,
                             const float *__restrict__ rec_d2, const int32_t *__restrict__ rec_pos,
-                            const int64_t *__restrict__ offsets, int32_t *__restrict__ idx,
-                            float *__restrict__ d2) {
+                            const int64_t *__restrict__ offsets, uint64_t *__restrict__ tmp) {
     const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (s >= nsurv) return;
     const int32_t p0 = rec_pos[s];
@@ -244,16 +243,10 @@ __global__ void k_b_scatter(const uint2 *__restrict__ surv, int64_t nsurv,
     const SetDesc &sd = sets[qset[e.x]];
     const int64_t ql = int64_t(e.x) - sd.q_glob;
     const int32_t qrow = sd.q_order[ql], col = sd.x_order[e.y];
-    const float v = rec_d2[s];
-    const int64_t o = offsets[sd.q_glob + qrow] + p0;
-    idx[o] = col;
-    d2[o] = v;
+    const uint64_t vb = __float_as_uint(rec_d2[s]);
+    tmp[offsets[sd.q_glob + qrow] + p0] = (uint64_t(uint32_t(col)) << 32) | vb;
     const int32_t p1 = rec_pos[nsurv + s];
-    if (p1 >= 0) {
-        const int64_t o1 = offsets[sd.q_glob + col] + p1;
-        idx[o1] = qrow;
-        d2[o1] = v;
-    }
+    if (p1 >= 0) tmp[offsets[sd.q_glob + col] + p1] = (uint64_t(uint32_t(qrow)) << 32) | vb;
 }
 
 // Per-set offsets, rebased to start at 0, into the output block: entry
@@ -588,8 +581,10 @@ snn_status batch_query(int32_t nsets, const snn_index *const *idx, const float *
     SNN_LAUNCH(k_b_offsets_end, unsigned(cdiv(nsets, 128)), 128, 0, s)(goff, d_qglob, nsets, out_off,
                                                                        d_offpos);
     if (nsurv > 0 && nnz > 0) {
+        uint64_t *tmp;
+        if ((st = scr.alloc(&tmp, nnz)) != SNN_OK) return fail(st);
         SNN_LAUNCH(k_b_scatter, unsigned(cdiv(nsurv, 256)), 256, 0, s)(
-            surv, nsurv, d_sets, qset, rec_d2, rec_pos, goff, gidx, gd2);
+            surv, nsurv, d_sets, qset, rec_d2, rec_pos, goff, tmp);
         // per-row ascending ids over the global CSR (rows of every set)
         int32_t *lists, *big_list;
         int64_t *big_len, *toff;
@@ -604,13 +599,13 @@ snn_status batch_query(int32_t nsets, const snn_index *const *idx, const float *
         SNN_LAUNCH(k_seg_classify, unsigned(cdiv(M, 256)), 256, 0, s)(goff, M, lists, big_list,
                                                                       big_len, cls);
         const unsigned wgrid = std::min<unsigned>(unsigned(cdiv(M * 32, 256)), 16384);
-        SNN_LAUNCH(k_seg_sort_w1, wgrid, 256, 0, s)(lists, cls, goff, gidx, gd2);
-        SNN_LAUNCH(k_seg_sort_w2, wgrid, 256, 0, s)(lists + 5 * M, cls + 6, goff, gidx, gd2);
-        SNN_LAUNCH(k_seg_sort_w4, wgrid, 256, 0, s)(lists + M, cls + 1, goff, gidx, gd2);
-        SNN_LAUNCH(k_seg_sort_w8, wgrid, 256, 0, s)(lists + 4 * M, cls + 5, goff, gidx, gd2);
-        SNN_LAUNCH(k_seg_sort_w16, wgrid, 256, 0, s)(lists + 2 * M, cls + 2, goff, gidx, gd2);
+        SNN_LAUNCH(k_seg_sort_w1, wgrid, 256, 0, s)(lists, cls, goff, tmp, gidx, gd2);
+        SNN_LAUNCH(k_seg_sort_w2, wgrid, 256, 0, s)(lists + 5 * M, cls + 6, goff, tmp, gidx, gd2);
+        SNN_LAUNCH(k_seg_sort_w4, wgrid, 256, 0, s)(lists + M, cls + 1, goff, tmp, gidx, gd2);
+        SNN_LAUNCH(k_seg_sort_w8, wgrid, 256, 0, s)(lists + 4 * M, cls + 5, goff, tmp, gidx, gd2);
+        SNN_LAUNCH(k_seg_sort_w16, wgrid, 256, 0, s)(lists + 2 * M, cls + 2, goff, tmp, gidx, gd2);
         SNN_LAUNCH(k_seg_sort_mid, std::min<unsigned>(unsigned(M), 4096), 256, 0, s)(
-            lists + 3 * M, cls + 3, goff, gidx, gd2);
+            lists + 3 * M, cls + 3, goff, tmp, gidx, gd2);
         unsigned hcls[8];
         if (cudaMemcpyAsync(hcls, cls, sizeof(hcls), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
@@ -633,8 +628,8 @@ snn_status batch_query(int32_t nsets, const snn_index *const *idx, const float *
             if (st == SNN_OK) st = scr.alloc(&bva, tot);
             if (st == SNN_OK) st = scr.alloc(&bd2, tot);
             if (st != SNN_OK) return fail(st);
-            SNN_LAUNCH(k_seg_big_gather, nbig, 256, 0, s)(big_list, nbig, goff, toff, gidx, gd2, bk,
-                                                          bv, bd2);
+            SNN_LAUNCH(k_seg_big_gather, nbig, 256, 0, s)(big_list, nbig, goff, toff, tmp, bk, bv,
+                                                          bd2);
             int bits = 32;
             while ((int64_t(1) << (bits - 32)) < nbig) ++bits;
             if ((st = radix_sort_pairs<uint64_t>(bk, bv, bka, bva, tot, bits, s)) != SNN_OK)

@@ -388,8 +388,8 @@ __device__ __forceinline__ void decide_one_survivor(
          int64_t s, const uint2 *__restrict__ surv, int64_t cap, const float *__restrict__ qraw,
          const int32_t *__restrict__ qorder, const float *__restrict__ praw,
          const int32_t *__restrict__ porder, int d, int dp, double R2, const DecideConsts &dc,
-         float *__restrict__ rec_d2, int32_t *__restrict__ rec_pos, int32_t *__restrict__ counts,
-         unsigned long long *__restrict__ n_fp64) {
+         float *__restrict__ rec_d2, int32_t *__restrict__ rec_pos, uint2 *__restrict__ rec_rc,
+         int32_t *__restrict__ counts, unsigned long long *__restrict__ n_fp64) {
     const uint2 e = surv[s];
     const float4 *pq = reinterpret_cast<const float4 *>(qraw + int64_t(e.x) * dp);
     const float4 *pp = reinterpret_cast<const float4 *>(praw + int64_t(e.y) * dp);
@@ -433,6 +433,7 @@ __device__ __forceinline__ void decide_one_survivor(
         const int32_t row = qorder[e.x], col = porder[e.y];
         p0 = atomicAdd(&counts[row], 1);
         if (kSym && e.x != e.y) p1 = atomicAdd(&counts[col], 1);
+        rec_rc[s] = make_uint2(uint32_t(row), uint32_t(col));
     }
     rec_d2[s] = d2;
     rec_pos[s] = p0;
@@ -445,13 +446,14 @@ __device__ __forceinline__ void decide_body(
          const float *__restrict__ qraw, const int32_t *__restrict__ qorder,
          const float *__restrict__ praw, const int32_t *__restrict__ porder, int d, int dp,
          double R2, float *__restrict__ rec_d2, int32_t *__restrict__ rec_pos,
-         int32_t *__restrict__ counts, unsigned long long *__restrict__ n_fp64) {
+         uint2 *__restrict__ rec_rc, int32_t *__restrict__ counts,
+         unsigned long long *__restrict__ n_fp64) {
     const int64_t nsurv = min((int64_t)*count, cap);
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     const DecideConsts dc = decide_consts(d, R2);
     for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < nsurv; s += stride)
         decide_one_survivor<kSym>(s, surv, cap, qraw, qorder, praw, porder, d, dp, R2, dc, rec_d2,
-                                  rec_pos, counts, n_fp64);
+                                  rec_pos, rec_rc, counts, n_fp64);
 }
 
 // The same decision with G lanes per survivor for long rows: lane l
@@ -468,7 +470,8 @@ __device__ __forceinline__ void decide_group_body(
          const float *__restrict__ qraw, const int32_t *__restrict__ qorder,
          const float *__restrict__ praw, const int32_t *__restrict__ porder, int d, int dp,
          double R2, float *__restrict__ rec_d2, int32_t *__restrict__ rec_pos,
-         int32_t *__restrict__ counts, unsigned long long *__restrict__ n_fp64) {
+         uint2 *__restrict__ rec_rc, int32_t *__restrict__ counts,
+         unsigned long long *__restrict__ n_fp64) {
     constexpr int GPW = 32 / G;   // groups per warp
     const int64_t nsurv = min((int64_t)*count, cap);
     const DecideConsts dc = decide_consts(d, R2);
@@ -532,6 +535,7 @@ __device__ __forceinline__ void decide_group_body(
             const int32_t row = qorder[e.x], col = porder[e.y];
             p0 = atomicAdd(&counts[row], 1);
             if (kSym && e.x != e.y) p1 = atomicAdd(&counts[col], 1);
+            rec_rc[s] = make_uint2(uint32_t(row), uint32_t(col));
         }
         rec_d2[s] = d2;
         rec_pos[s] = p0;
@@ -544,9 +548,10 @@ __device__ __forceinline__ void decide_group_body(
         const float *__restrict__ qraw, const int32_t *__restrict__ qorder,                    \
         const float *__restrict__ praw, const int32_t *__restrict__ porder, int d, int dp,     \
         double R2, float *__restrict__ rec_d2, int32_t *__restrict__ rec_pos,                  \
-        int32_t *__restrict__ counts, unsigned long long *__restrict__ n_fp64
+        uint2 *__restrict__ rec_rc, int32_t *__restrict__ counts,                              \
+        unsigned long long *__restrict__ n_fp64
 #define SNN_DECIDE_PASS surv, count, cap, qraw, qorder, praw, porder, d, dp, R2, rec_d2, rec_pos, \
-                        counts, n_fp64
+                        rec_rc, counts, n_fp64
 __global__ void __launch_bounds__(256) k_decide_sym(SNN_DECIDE_ARGS) {
     decide_body<true>(SNN_DECIDE_PASS);
 }
@@ -575,27 +580,21 @@ __global__ void k_counts_to_i64(const int32_t *__restrict__ counts, int64_t m,
 }
 
 // Writes each accepted pair at its row slot (and the mirrored pair of a
-// symmetric self-join), straight into the output CSR arrays.
-__global__ void k_scatter(const uint2 *__restrict__ surv, int64_t nsurv, int64_t rstride,
-                          const int32_t *__restrict__ qorder, const int32_t *__restrict__ porder,
-                          const float *__restrict__ rec_d2, const int32_t *__restrict__ rec_pos,
-                          int sym, const int64_t *__restrict__ offsets, int32_t *__restrict__ idx,
-                          float *__restrict__ d2) {
+// symmetric self-join) as one packed entry (id << 32 | dist2 bits) of the
+// row-grouped staging array; the per-row sort writes the output arrays.
+__global__ void k_scatter(const uint2 *__restrict__ rec_rc, const int32_t *__restrict__ rec_pos,
+                          const float *__restrict__ rec_d2, int64_t nsurv, int64_t rstride, int sym,
+                          const int64_t *__restrict__ offsets, uint64_t *__restrict__ tmp) {
     const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (s >= nsurv) return;
     const int32_t p0 = rec_pos[s];
     if (p0 < 0) return;
-    const uint2 e = surv[s];
-    const int32_t row = qorder[e.x], col = porder[e.y];
-    const float v = rec_d2[s];
-    idx[offsets[row] + p0] = col;
-    d2[offsets[row] + p0] = v;
+    const uint2 rc = rec_rc[s];
+    const uint64_t vb = __float_as_uint(rec_d2[s]);
+    tmp[offsets[rc.x] + p0] = (uint64_t(rc.y) << 32) | vb;
     if (sym) {
         const int32_t p1 = rec_pos[rstride + s];
-        if (p1 >= 0) {
-            idx[offsets[col] + p1] = row;
-            d2[offsets[col] + p1] = v;
-        }
+        if (p1 >= 0) tmp[offsets[rc.y] + p1] = (uint64_t(rc.x) << 32) | vb;
     }
 }
 
@@ -609,7 +608,7 @@ __global__ void k_seg_classify(const int64_t *__restrict__ offsets, int64_t m,
     const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (r >= m) return;
     const int64_t len = offsets[r + 1] - offsets[r];
-    if (len <= 1) return;   // nothing to order (the scatter wrote it in place)
+    if (len == 0) return;
     if (len <= kSegSmall) {
         lists[atomicAdd(&counters[0], 1u)] = (int32_t)r;
     } else if (len <= 2 * kSegSmall) {
@@ -629,94 +628,92 @@ __global__ void k_seg_classify(const int64_t *__restrict__ offsets, int64_t m,
     }
 }
 
-// One warp per row of <= 32*E entries: bitonic network over E registers x 32
-// lanes (element r*32 + lane lives in register r of that lane).
+// One warp per row of <= 32*E packed entries (id << 32 | dist2 bits; ids are
+// unique in a row, so ordering the packed values orders the ids).  Bitonic
+// network over the blocked layout: lane l holds entries l*E .. l*E+E-1, so the
+// steps with distance < E are compare-exchanges inside a lane and only the
+// 15 steps with distance >= E cross lanes; every step is branch-free.
+__device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int m) {
+    const uint32_t lo = __shfl_xor_sync(0xffffffffu, uint32_t(v), m);
+    const uint32_t hi = __shfl_xor_sync(0xffffffffu, uint32_t(v >> 32), m);
+    return (uint64_t(hi) << 32) | lo;
+}
+
 template <int E>
 __device__ __forceinline__ void seg_sort_warp(const int32_t *__restrict__ list, unsigned total,
                                               const int64_t *__restrict__ offsets,
-                                              int32_t *idx, float *d2) {
+                                              const uint64_t *__restrict__ tmp,
+                                              int32_t *__restrict__ idx, float *__restrict__ d2) {
+    constexpr int N = 32 * E;
     const int lane = threadIdx.x & 31;
     const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
     for (int64_t w = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); w < total; w += nw) {
         const int32_t r = list[w];
         const int64_t o = offsets[r];
         const int len = int(offsets[r + 1] - o);
-        int32_t key[E];
-        float val[E];
+        uint64_t v[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            const int i = e * 32 + lane;
-            key[e] = i < len ? idx[o + i] : INT32_MAX;
-            val[e] = i < len ? d2[o + i] : 0.f;
+            const int i = lane * E + e;
+            v[e] = i < len ? tmp[o + i] : ~uint64_t(0);
         }
 #pragma unroll
-        for (int k = 2; k <= 32 * E; k <<= 1) {
+        for (int k = 2; k <= N; k <<= 1) {
 #pragma unroll
             for (int j = k >> 1; j > 0; j >>= 1) {
-                if (j >= 32) {
-                    const int jr = j >> 5;
+                if (j >= E) {
+                    const int lj = j / E;
+                    const bool lower = (lane & lj) == 0;
 #pragma unroll
                     for (int e = 0; e < E; ++e) {
-                        const int pe = e ^ jr;
-                        if (pe > e) {
-                            const bool asc = ((e * 32 + lane) & k) == 0;
-                            if ((key[e] > key[pe]) == asc) {
-                                const int32_t tk = key[e]; key[e] = key[pe]; key[pe] = tk;
-                                const float tv = val[e]; val[e] = val[pe]; val[pe] = tv;
-                            }
-                        }
+                        const uint64_t p = shfl_xor_u64(v[e], lj);
+                        const bool asc = ((lane * E + e) & k) == 0;
+                        const bool keep_min = lower == asc;
+                        const bool pl = p < v[e];
+                        v[e] = (keep_min == pl) ? p : v[e];
                     }
                 } else {
 #pragma unroll
                     for (int e = 0; e < E; ++e) {
-                        const int32_t pk = __shfl_xor_sync(0xffffffffu, key[e], j);
-                        const float pv = __shfl_xor_sync(0xffffffffu, val[e], j);
-                        const bool asc = ((e * 32 + lane) & k) == 0;
-                        const bool lower = (lane & j) == 0;
-                        const bool take = (lower == asc) ? (pk < key[e]) : (pk > key[e]);
-                        if (take) { key[e] = pk; val[e] = pv; }
+                        const int pe = e ^ j;
+                        if (pe > e) {
+                            const bool asc = ((lane * E + e) & k) == 0;
+                            const uint64_t a = v[e], b = v[pe];
+                            const bool sw = (a > b) == asc;
+                            v[e] = sw ? b : a;
+                            v[pe] = sw ? a : b;
+                        }
                     }
                 }
             }
         }
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            const int i = e * 32 + lane;
+            const int i = lane * E + e;
             if (i < len) {
-                idx[o + i] = key[e];
-                d2[o + i] = val[e];
+                idx[o + i] = int32_t(uint32_t(v[e] >> 32));
+                d2[o + i] = __uint_as_float(uint32_t(v[e]));
             }
         }
     }
 }
 
-__global__ void k_seg_sort_w1(const int32_t *__restrict__ list, const unsigned *__restrict__ count,
-                              const int64_t *__restrict__ offsets, int32_t *idx, float *d2) {
-    seg_sort_warp<1>(list, *count, offsets, idx, d2);
-}
-__global__ void k_seg_sort_w16(const int32_t *__restrict__ list, const unsigned *__restrict__ count,
-                              const int64_t *__restrict__ offsets, int32_t *idx, float *d2) {
-    seg_sort_warp<16>(list, *count, offsets, idx, d2);
-}
-__global__ void k_seg_sort_w8(const int32_t *__restrict__ list, const unsigned *__restrict__ count,
-                              const int64_t *__restrict__ offsets, int32_t *idx, float *d2) {
-    seg_sort_warp<8>(list, *count, offsets, idx, d2);
-}
-__global__ void k_seg_sort_w2(const int32_t *__restrict__ list, const unsigned *__restrict__ count,
-                              const int64_t *__restrict__ offsets, int32_t *idx, float *d2) {
-    seg_sort_warp<2>(list, *count, offsets, idx, d2);
-}
-__global__ void k_seg_sort_w4(const int32_t *__restrict__ list, const unsigned *__restrict__ count,
-                              const int64_t *__restrict__ offsets, int32_t *idx, float *d2) {
-    seg_sort_warp<4>(list, *count, offsets, idx, d2);
+#define SNN_SEG_ARGS                                                                            \
+    const int32_t *__restrict__ list, const unsigned *__restrict__ count,                       \
+        const int64_t *__restrict__ offsets, const uint64_t *__restrict__ tmp, int32_t *idx,   \
+        float *d2
+__global__ void k_seg_sort_w1(SNN_SEG_ARGS) { seg_sort_warp<1>(list, *count, offsets, tmp, idx, d2); }
+__global__ void k_seg_sort_w2(SNN_SEG_ARGS) { seg_sort_warp<2>(list, *count, offsets, tmp, idx, d2); }
+__global__ void k_seg_sort_w4(SNN_SEG_ARGS) { seg_sort_warp<4>(list, *count, offsets, tmp, idx, d2); }
+__global__ void k_seg_sort_w8(SNN_SEG_ARGS) { seg_sort_warp<8>(list, *count, offsets, tmp, idx, d2); }
+__global__ void k_seg_sort_w16(SNN_SEG_ARGS) {
+    seg_sort_warp<16>(list, *count, offsets, tmp, idx, d2);
 }
 
-// One block per row of <= 4096 entries: bitonic sort in shared memory.
-__global__ void __launch_bounds__(256)
-k_seg_sort_mid(const int32_t *__restrict__ list, const unsigned *__restrict__ count,
-               const int64_t *__restrict__ offsets, int32_t *idx, float *d2) {
-    __shared__ int32_t sk[kSegMid];
-    __shared__ float sv[kSegMid];
+// One block per row of <= 4096 entries: bitonic sort of the packed entries
+// in shared memory.
+__global__ void __launch_bounds__(256) k_seg_sort_mid(SNN_SEG_ARGS) {
+    __shared__ uint64_t sk[kSegMid];
     const unsigned total = *count;
     for (unsigned w = blockIdx.x; w < total; w += gridDim.x) {
         const int32_t r = list[w];
@@ -725,10 +722,7 @@ k_seg_sort_mid(const int32_t *__restrict__ list, const unsigned *__restrict__ co
         int N = 64;
         while (N < len) N <<= 1;
         __syncthreads();
-        for (int i = threadIdx.x; i < N; i += blockDim.x) {
-            sk[i] = i < len ? idx[o + i] : INT32_MAX;
-            sv[i] = i < len ? d2[o + i] : 0.f;
-        }
+        for (int i = threadIdx.x; i < N; i += blockDim.x) sk[i] = i < len ? tmp[o + i] : ~uint64_t(0);
         __syncthreads();
         for (int k = 2; k <= N; k <<= 1) {
             for (int j = k >> 1; j > 0; j >>= 1) {
@@ -736,37 +730,37 @@ k_seg_sort_mid(const int32_t *__restrict__ list, const unsigned *__restrict__ co
                     const int ixj = i ^ j;
                     if (ixj > i) {
                         const bool asc = (i & k) == 0;
-                        const int32_t a = sk[i], b = sk[ixj];
-                        if ((a > b) == asc) {
-                            sk[i] = b; sk[ixj] = a;
-                            const float t = sv[i]; sv[i] = sv[ixj]; sv[ixj] = t;
-                        }
+                        const uint64_t a = sk[i], b = sk[ixj];
+                        const bool sw = (a > b) == asc;
+                        sk[i] = sw ? b : a;
+                        sk[ixj] = sw ? a : b;
                     }
                 }
                 __syncthreads();
             }
         }
         for (int i = threadIdx.x; i < len; i += blockDim.x) {
-            idx[o + i] = sk[i];
-            d2[o + i] = sv[i];
+            idx[o + i] = int32_t(uint32_t(sk[i] >> 32));
+            d2[o + i] = __uint_as_float(uint32_t(sk[i]));
         }
     }
 }
+#undef SNN_SEG_ARGS
 
 // Long rows: keys (big-row rank << 32 | column), values = source position.
 __global__ void k_seg_big_gather(const int32_t *__restrict__ big_list, int nbig,
                                  const int64_t *__restrict__ offsets, const int64_t *__restrict__ toff,
-                                 const int32_t *__restrict__ idx, const float *__restrict__ d2,
-                                 uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                                 float *__restrict__ gd2) {
+                                 const uint64_t *__restrict__ tmp, uint64_t *__restrict__ keys,
+                                 uint32_t *__restrict__ vals, float *__restrict__ gd2) {
     const int b = blockIdx.x;
     if (b >= nbig) return;
     const int32_t r = big_list[b];
     const int64_t o = offsets[r], len = offsets[r + 1] - o, t0 = toff[b];
     for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
-        keys[t0 + i] = (uint64_t(b) << 32) | uint64_t(uint32_t(idx[o + i]));
+        const uint64_t v = tmp[o + i];
+        keys[t0 + i] = (uint64_t(b) << 32) | (v >> 32);
         vals[t0 + i] = uint32_t(t0 + i);
-        gd2[t0 + i] = d2[o + i];
+        gd2[t0 + i] = __uint_as_float(uint32_t(v));
     }
 }
 

@@ -156,7 +156,8 @@ __device__ __forceinline__ int decide_df(float H, float L, bool nz, const Decide
     __global__ void name(const uint2 *surv, const unsigned long long *count, int64_t cap,    \
                          const float *qraw, const int32_t *qorder, const float *praw,        \
                          const int32_t *porder, int d, int dp, double R2, float *rec_d2,     \
-                         int32_t *rec_pos, int32_t *counts, unsigned long long *n_fp64)
+                         int32_t *rec_pos, uint2 *rec_rc, int32_t *counts,                   \
+                         unsigned long long *n_fp64)
 SNN_DECIDE_DECL(k_decide_sym);
 SNN_DECIDE_DECL(k_decide_one);
 SNN_DECIDE_DECL(k_decide_sym_g8);
@@ -165,9 +166,9 @@ SNN_DECIDE_DECL(k_decide_sym_g32);
 SNN_DECIDE_DECL(k_decide_one_g32);
 #undef SNN_DECIDE_DECL
 __global__ void k_counts_to_i64(const int32_t *counts, int64_t m, int64_t *out);
-__global__ void k_scatter(const uint2 *surv, int64_t nsurv, int64_t rstride, const int32_t *qorder,
-                          const int32_t *porder, const float *rec_d2, const int32_t *rec_pos, int sym,
-                          const int64_t *offsets, int32_t *idx, float *d2);
+__global__ void k_scatter(const uint2 *rec_rc, const int32_t *rec_pos, const float *rec_d2,
+                          int64_t nsurv, int64_t rstride, int sym, const int64_t *offsets,
+                          uint64_t *tmp);
 
 // Segmented sort of CSR rows by column id.
 constexpr int kSegSmall = 32;
@@ -175,20 +176,20 @@ constexpr int kSegMid = 4096;
 __global__ void k_seg_classify(const int64_t *offsets, int64_t m, int32_t *lists,
                                int32_t *big_list, int64_t *big_len, unsigned *counters);
 __global__ void k_seg_sort_w1(const int32_t *list, const unsigned *count, const int64_t *offsets,
-                              int32_t *idx, float *d2);
+                          const uint64_t *tmp, int32_t *idx, float *d2);
 __global__ void k_seg_sort_w16(const int32_t *list, const unsigned *count, const int64_t *offsets,
-                              int32_t *idx, float *d2);
+                          const uint64_t *tmp, int32_t *idx, float *d2);
 __global__ void k_seg_sort_w8(const int32_t *list, const unsigned *count, const int64_t *offsets,
-                              int32_t *idx, float *d2);
+                          const uint64_t *tmp, int32_t *idx, float *d2);
 __global__ void k_seg_sort_w2(const int32_t *list, const unsigned *count, const int64_t *offsets,
-                              int32_t *idx, float *d2);
+                          const uint64_t *tmp, int32_t *idx, float *d2);
 __global__ void k_seg_sort_w4(const int32_t *list, const unsigned *count, const int64_t *offsets,
-                              int32_t *idx, float *d2);
+                          const uint64_t *tmp, int32_t *idx, float *d2);
 __global__ void k_seg_sort_mid(const int32_t *list, const unsigned *count, const int64_t *offsets,
-                               int32_t *idx, float *d2);
+                          const uint64_t *tmp, int32_t *idx, float *d2);
 __global__ void k_seg_big_gather(const int32_t *big_list, int nbig, const int64_t *offsets,
-                                 const int64_t *toff, const int32_t *idx, const float *d2,
-                                 uint64_t *keys, uint32_t *vals, float *gd2);
+                                 const int64_t *toff, const uint64_t *tmp, uint64_t *keys,
+                                 uint32_t *vals, float *gd2);
 __global__ void k_seg_big_scatter(const uint64_t *keys, const uint32_t *vals, int64_t total,
                                   const int32_t *big_list, const int64_t *offsets,
                                   const int64_t *toff, const float *gd2, int32_t *idx, float *d2);

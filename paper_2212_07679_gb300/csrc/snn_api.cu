@@ -374,14 +374,15 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     out->dist2 = nullptr;
     ensure_pool();
     SNN_TRY(dev_alloc(&out->offsets, m + 1, s));
-    uint2 *surv = nullptr;
+    uint2 *surv = nullptr, *rec_rc = nullptr;
     float *rec_d2 = nullptr;
     int32_t *rec_pos = nullptr;
     auto fail = [&](snn_status st) {
-        void *tmp[] = {surv, rec_d2, rec_pos, out->offsets, out->indices, out->dist2};
+        void *tmp[] = {surv, rec_rc, rec_d2, rec_pos, out->offsets, out->indices, out->dist2};
         for (void *p : tmp)
             if (p) cudaFreeAsync(p, s);
         surv = nullptr;
+        rec_rc = nullptr;
         rec_d2 = nullptr;
         rec_pos = nullptr;
         out->offsets = nullptr;
@@ -571,6 +572,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         CUDA_Q(cudaMallocAsync(&surv, size_t(cap) * sizeof(uint2), s));
         CUDA_Q(cudaMallocAsync(&rec_d2, size_t(cap) * sizeof(float), s));
         CUDA_Q(cudaMallocAsync(&rec_pos, size_t(sym ? 2 * cap : cap) * sizeof(int32_t), s));
+        CUDA_Q(cudaMallocAsync(&rec_rc, size_t(cap) * sizeof(uint2), s));
         sa.surv = surv;
         sa.cap = cap;
         if (stats) cudaEventRecord(ev[1], s);
@@ -596,7 +598,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         const unsigned dgrid =
             std::min<unsigned>(grid_for(cap * G, 256), unsigned(16 * device_sm_count()));
         SNN_LAUNCH(dk, dgrid, 256, 0, s)(surv, ctr, cap, qs.raw, qs.order, ds.raw, ds.order, d, dp,
-                                         R2, rec_d2, rec_pos, counts, ctr + 4);
+                                         R2, rec_d2, rec_pos, rec_rc, counts, ctr + 4);
         CUDA_Q(cudaGetLastError());
         if (stats) cudaEventRecord(ev[3], s);
         SNN_LAUNCH(k_counts_to_i64, grid_for(m, 256), 256, 0, s)(counts, m, counts64);
@@ -635,9 +637,11 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         cudaFreeAsync(surv, s);
         cudaFreeAsync(rec_d2, s);
         cudaFreeAsync(rec_pos, s);
+        cudaFreeAsync(rec_rc, s);
         surv = nullptr;
         rec_d2 = nullptr;
         rec_pos = nullptr;
+        rec_rc = nullptr;
         cap = (int64_t)hb->ctr[0] + 1024;
         CUDA_Q(cudaMemsetAsync(ctr, 0, 8 * sizeof(unsigned long long), s));
         if (stats) {
@@ -665,9 +669,10 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     if (nnz > 0) {
         TRY_Q(dev_alloc(&out->indices, nnz, s));
         TRY_Q(dev_alloc(&out->dist2, nnz, s));
-        SNN_LAUNCH(k_scatter, grid_for(nsurv, 256), 256, 0, s)(surv, nsurv, cap, qs.order, ds.order,
-                                                               rec_d2, rec_pos, sym, out->offsets,
-                                                               out->indices, out->dist2);
+        uint64_t *tmp;
+        TRY_Q(scr.alloc(&tmp, nnz));
+        SNN_LAUNCH(k_scatter, grid_for(nsurv, 256), 256, 0, s)(rec_rc, rec_pos, rec_d2, nsurv, cap,
+                                                               sym, out->offsets, tmp);
         CUDA_Q(cudaGetLastError());
         // per-row ascending column ids, in place; classes with no rows are
         // skipped and the grids sized by the class counts
@@ -675,21 +680,20 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         auto wgrid = [&](unsigned rows) {
             return std::min<unsigned>(grid_for(int64_t(rows) * 32, 256), 16384);
         };
-        if (hc[0]) SNN_LAUNCH(k_seg_sort_w1, wgrid(hc[0]), 256, 0, s)(lists, cls, out->offsets,
-                                                                     out->indices, out->dist2);
-        if (hc[6]) SNN_LAUNCH(k_seg_sort_w2, wgrid(hc[6]), 256, 0, s)(lists + 5 * m, cls + 6,
-                                                                     out->offsets, out->indices,
-                                                                     out->dist2);
-        if (hc[1]) SNN_LAUNCH(k_seg_sort_w4, wgrid(hc[1]), 256, 0, s)(lists + m, cls + 1, out->offsets,
-                                                                     out->indices, out->dist2);
-        if (hc[5]) SNN_LAUNCH(k_seg_sort_w8, wgrid(hc[5]), 256, 0, s)(lists + 4 * m, cls + 5,
-                                                                     out->offsets, out->indices,
-                                                                     out->dist2);
-        if (hc[2]) SNN_LAUNCH(k_seg_sort_w16, wgrid(hc[2]), 256, 0, s)(lists + 2 * m, cls + 2,
-                                                                      out->offsets, out->indices,
-                                                                      out->dist2);
+        int32_t *oi = out->indices;
+        float *od = out->dist2;
+        const int64_t *oo = out->offsets;
+        if (hc[0]) SNN_LAUNCH(k_seg_sort_w1, wgrid(hc[0]), 256, 0, s)(lists, cls, oo, tmp, oi, od);
+        if (hc[6]) SNN_LAUNCH(k_seg_sort_w2, wgrid(hc[6]), 256, 0, s)(lists + 5 * m, cls + 6, oo, tmp,
+                                                                     oi, od);
+        if (hc[1]) SNN_LAUNCH(k_seg_sort_w4, wgrid(hc[1]), 256, 0, s)(lists + m, cls + 1, oo, tmp, oi,
+                                                                     od);
+        if (hc[5]) SNN_LAUNCH(k_seg_sort_w8, wgrid(hc[5]), 256, 0, s)(lists + 4 * m, cls + 5, oo, tmp,
+                                                                     oi, od);
+        if (hc[2]) SNN_LAUNCH(k_seg_sort_w16, wgrid(hc[2]), 256, 0, s)(lists + 2 * m, cls + 2, oo,
+                                                                      tmp, oi, od);
         if (hc[3]) SNN_LAUNCH(k_seg_sort_mid, std::min<unsigned>(hc[3], 4096), 256, 0, s)(
-            lists + 3 * m, cls + 3, out->offsets, out->indices, out->dist2);
+            lists + 3 * m, cls + 3, oo, tmp, oi, od);
         CUDA_Q(cudaGetLastError());
         const int nbig = (int)hc[4];
         if (nbig > 0) {
@@ -702,8 +706,8 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
             TRY_Q(scr.alloc(&bv, tot));
             TRY_Q(scr.alloc(&bva, tot));
             TRY_Q(scr.alloc(&gd2, tot));
-            SNN_LAUNCH(k_seg_big_gather, nbig, 256, 0, s)(big_list, nbig, out->offsets, toff,
-                                                          out->indices, out->dist2, bk, bv, gd2);
+            SNN_LAUNCH(k_seg_big_gather, nbig, 256, 0, s)(big_list, nbig, out->offsets, toff, tmp,
+                                                          bk, bv, gd2);
             CUDA_Q(cudaGetLastError());
             int bits = 32;
             while ((int64_t(1) << (bits - 32)) < nbig) ++bits;
@@ -716,9 +720,11 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     cudaFreeAsync(surv, s);
     cudaFreeAsync(rec_d2, s);
     cudaFreeAsync(rec_pos, s);
+    cudaFreeAsync(rec_rc, s);
     surv = nullptr;
     rec_d2 = nullptr;
     rec_pos = nullptr;
+    rec_rc = nullptr;
     if (stats) {
         cudaEventRecord(ev[4], s);
         unsigned long long nf = 0;
