@@ -30,19 +30,24 @@ __global__ void k_query_consts(const float *__restrict__ hy, const float *__rest
     thrA[i] = __double2float_ru(a + 4.0 * kU64 * (fabs(a) + 0.5 * r * r + (double)hy[i]));
 }
 
+// Binary searches over the sorted FP32 scores with FP64 thresholds, in FP32:
+// for a float a, a < x <=> a < ru(x) and a <= x <=> a <= rd(x), with ru / rd
+// the float roundings of x upward / downward (one conversion per search).
 __device__ __forceinline__ int64_t lower_bound_ge(const float *__restrict__ a, int64_t n, double x) {
+    const float xf = __double2float_ru(x);
     int64_t lo = 0, hi = n;
     while (lo < hi) {
         int64_t mid = (lo + hi) >> 1;
-        if ((double)a[mid] < x) lo = mid + 1; else hi = mid;
+        if (a[mid] < xf) lo = mid + 1; else hi = mid;
     }
     return lo;
 }
 __device__ __forceinline__ int64_t upper_bound_gt(const float *__restrict__ a, int64_t n, double x) {
+    const float xf = __double2float_rd(x);
     int64_t lo = 0, hi = n;
     while (lo < hi) {
         int64_t mid = (lo + hi) >> 1;
-        if ((double)a[mid] <= x) lo = mid + 1; else hi = mid;
+        if (a[mid] <= xf) lo = mid + 1; else hi = mid;
     }
     return lo;
 }

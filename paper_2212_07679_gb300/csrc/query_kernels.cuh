@@ -131,8 +131,9 @@ __device__ __forceinline__ int decide_df(float H, float L, bool nz, const Decide
                                          float *d2) {
     if (!(H < 0x1p100f) || !(H >= 0.f)) return 2;      // overflow / NaN
     if (H < 0x1p-100f && nz) return 2;                 // possible underflow
-    const float T = __fmul_ru(__fmaf_ru(c.rel, H, __fmaf_ru(c.rel2, fmaxf(H, c.r2h), c.tiny)),
-                              1.f + 0x1p-20f);
+    // three round-to-nearest operations (relative error below 2^-22 in all),
+    // then a 2^-20 margin: T is never below its exact value
+    const float T = fmaf(c.rel, H, fmaf(c.rel2, fmaxf(H, c.r2h), c.tiny)) * (1.f + 0x1p-20f);
     const float D = __fadd_rn(__fsub_rn(H, c.r2h), __fsub_rn(L, c.r2l));
     if (D > T) return 0;
     if (!(D < -T)) return 2;
@@ -142,7 +143,7 @@ __device__ __forceinline__ int decide_df(float H, float L, bool nz, const Decide
         const float dn = __uint_as_float(__float_as_uint(H) - 1u);
         const float half_up = 0.5f * __fsub_rn(up, H), half_dn = 0.5f * __fsub_rn(H, dn);
         const float room = L >= 0.f ? __fsub_rn(half_up, L) : __fadd_rn(half_dn, L);
-        if (!(room > __fmaf_ru(0x1p-22f, half_up, T))) return 2;
+        if (!(room > fmaf(0x1p-22f, half_up, T))) return 2;
     }
     *d2 = H;
     return 1;

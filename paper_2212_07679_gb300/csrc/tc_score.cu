@@ -526,60 +526,68 @@ __device__ __forceinline__ void split3(double w, uint16_t (&o)[3]) {
     }
 }
 
-// Row r of an operand: split parts of the centred row, then the folded
+// Rows of an operand: split parts of the centred row, then the folded
 // columns (data side: -(1-c) xbar_j split, ||x_j|| rounded up three times,
-// ones; query side: ones, c ||y_i|| split, A'_i split).  One warp per row,
-// lanes over columns (coalesced 2-byte stores).
+// ones; query side: ones, c ||y_i|| split, A'_i split).  One warp per 32
+// rows: the data columns row by row with the lanes over the columns
+// (coalesced 2-byte stores), the folded columns with one lane per row (their
+// few FP64 operations then run on full warps).
 template <int NSPLIT>
 __global__ void k_tc_pack(const float *__restrict__ xc, int dp, const float *__restrict__ hx,
                           const float *__restrict__ nrm, const double *__restrict__ Aq,
                           int64_t rows, int d, int K2, int K2n, double c, int query_side,
                           uint16_t *__restrict__ p0, uint16_t *__restrict__ p1,
                           uint16_t *__restrict__ p2) {
-    const int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t r0 = ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * 32;
     const int lane = threadIdx.x & 31;
-    if (r >= rows) return;
-    const float *xr = xc + r * dp;
-    const int64_t ro = r * K2;
-    for (int k = lane; k < K2; k += 32) {
-        uint16_t v0 = 0, v1 = 0, v2 = 0;
-        if (k < d) {
-            const float x = xr[k];
-            const __nv_bfloat16 h = __float2bfloat16_rn(x);
-            const float xr1 = x - __bfloat162float(h);               // exact
-            const __nv_bfloat16 l = __float2bfloat16_rn(xr1);
-            v0 = bf16_bits(h);
-            v1 = bf16_bits(l);
-            if (NSPLIT == 3) v2 = bf16_bits(__float2bfloat16_rn(xr1 - __bfloat162float(l)));
-        } else if (k < d + kExtra) {
-            const int t = k - d;
-            uint16_t sp[3];
-            if (!query_side) {
-                if (t < 3) {
-                    split3(-(1.0 - c) * (double)hx[r], sp);
-                    v0 = sp[t];
-                } else if (t < 6) {
-                    v0 = bf16_bits(__float2bfloat16_ru(nrm[r]));
-                } else {
-                    v0 = bf16_bits(__float2bfloat16_rn(1.0f));
-                }
-            } else {
-                if (t < 3) {
-                    v0 = bf16_bits(__float2bfloat16_rn(1.0f));
-                } else if (t < 6) {
-                    split3(c * (double)nrm[r], sp);
-                    v0 = sp[t - 3];
-                } else {
-                    split3(Aq[r], sp);
-                    v0 = sp[t - 6];
-                }
+    if (r0 >= rows) return;   // whole warps leave together
+    const int nr = int(min(int64_t(32), rows - r0));
+    for (int rr = 0; rr < nr; ++rr) {
+        const int64_t r = r0 + rr;
+        const float *xr = xc + r * dp;
+        const int64_t ro = r * K2;
+        for (int k = lane; k < K2; k += 32) {
+            uint16_t v0 = 0, v1 = 0, v2 = 0;
+            if (k < d) {
+                const float x = xr[k];
+                const __nv_bfloat16 h = __float2bfloat16_rn(x);
+                const float xr1 = x - __bfloat162float(h);               // exact
+                const __nv_bfloat16 l = __float2bfloat16_rn(xr1);
+                v0 = bf16_bits(h);
+                v1 = bf16_bits(l);
+                if (NSPLIT == 3) v2 = bf16_bits(__float2bfloat16_rn(xr1 - __bfloat162float(l)));
+            }
+            if (k < d || k >= d + kExtra) p0[ro + k] = v0;   // folded columns: below
+            // parts 2 and 3 hold data columns only (zero elsewhere), rows of
+            // K2n columns
+            if (k < K2n) {
+                if (NSPLIT >= 2) p1[r * K2n + k] = v1;
+                if (NSPLIT >= 3) p2[r * K2n + k] = v2;
             }
         }
-        p0[ro + k] = v0;
-        // parts 2 and 3 hold data columns only, rows of K2n columns
-        if (k < K2n) {
-            if (NSPLIT >= 2) p1[r * K2n + k] = v1;
-            if (NSPLIT >= 3) p2[r * K2n + k] = v2;
+    }
+    if (lane < nr) {
+        const int64_t r = r0 + lane;
+        uint16_t *f = p0 + r * K2 + d;
+        uint16_t sp[3];
+        const uint16_t one = bf16_bits(__float2bfloat16_rn(1.0f));
+        if (!query_side) {
+            split3(-(1.0 - c) * (double)hx[r], sp);
+            const uint16_t nb = bf16_bits(__float2bfloat16_ru(nrm[r]));
+            for (int t = 0; t < 3; ++t) {
+                f[t] = sp[t];
+                f[3 + t] = nb;
+                f[6 + t] = one;
+            }
+        } else {
+            uint16_t sa[3];
+            split3(c * (double)nrm[r], sp);
+            split3(Aq[r], sa);
+            for (int t = 0; t < 3; ++t) {
+                f[t] = one;
+                f[3 + t] = sp[t];
+                f[6 + t] = sa[t];
+            }
         }
     }
 }
@@ -693,7 +701,7 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
                 }
             }
             auto packer = nsplit == 2 ? k_tc_pack<2> : k_tc_pack<3>;
-            SNN_LAUNCH(packer, unsigned(cdiv(ix->n * 32, 256)), 256, 0, s)(
+            SNN_LAUNCH(packer, unsigned(cdiv(cdiv(ix->n, 32) * 32, 256)), 256, 0, s)(
                 ix->xc, ix->dp, ix->hx, ix->nrm, nullptr, ix->n, d, K2, K2n, c, 0, ix->tc_part[0],
                 ix->tc_part[1], ix->tc_part[2]);
             SNN_LAUNCH_CHECK();
@@ -716,7 +724,8 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
         sa.q.hx, sa.q.nrm, m, d, Rx, e_data, 0x1p-23 + u_k, Aq);
     SNN_LAUNCH_CHECK();
     auto packer = nsplit == 2 ? k_tc_pack<2> : k_tc_pack<3>;
-    SNN_LAUNCH(packer, unsigned(cdiv(m * 32, 256)), 256, 0, s)(sa.q.xc, ix->dp, sa.q.hx, sa.q.nrm, Aq,
+    SNN_LAUNCH(packer, unsigned(cdiv(cdiv(m, 32) * 32, 256)), 256, 0, s)(sa.q.xc, ix->dp, sa.q.hx,
+                                                                       sa.q.nrm, Aq,
                                                             m, d, K2, K2n, c, 1, qp[0], qp[1], qp[2]);
     SNN_LAUNCH_CHECK();
     TileSet ts1{sa.tile_lo, sa.tile_hi, sa.item_off, sa.item_tile, sa.ntiles};
