@@ -206,7 +206,7 @@ k_b_decide(const uint2 *__restrict__ surv, int64_t nsurv, const SetDesc *__restr
         }
     }
     const double R2 = sd.R2;
-    const DecideConsts dc = decide_consts(d, R2);
+    const DecideConsts &dc = sd.dc;
     float d2 = 0.f;
     int v = decide_df(H, L, nz, dc, &d2);
     if (v == 2) {
@@ -308,6 +308,7 @@ snn_status batch_query(int32_t nsets, const snn_index *const *idx, const float *
         d.q_glob = qglob[t];
         d.tile0 = tile0[t];
         d.R2 = R_in[t] * R_in[t];
+        d.dc = decide_consts(d.d, d.R2);
         d.Rx = R_in[t] * (1.0 + (ix->d + 8) * 0x1p-52);
         d.Wbase = d.Rx * (1.0 + (ix->d + 4) * 0x1p-52) * (1.0 + 0x1p-30);
         d.e_data = 1.0001 * (double)kU32 * (double)ix->nrm_max;

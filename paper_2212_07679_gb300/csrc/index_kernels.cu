@@ -177,7 +177,7 @@ __global__ void k_gram_reduce(const float *__restrict__ part, int nchunk, int d,
 // ------------------------------------------------- first direction (K3)
 // Small d: one CTA.  M = C / trace(C) in FP32 shared memory, squared
 // kSquarings times (M <- M*M / trace), so M tends to v1 v1^T; the column with
-// the largest diagonal entry seeds FP64 power steps v <- C v / ||C v||.
+// the largest diagonal entry seeds power steps v <- C v / ||C v||.
 constexpr int kSquarings = 12;
 constexpr int kPowerSteps = 4;
 
@@ -207,28 +207,40 @@ __device__ float block_sum_f(float v, float *red) {
 
 __global__ void __launch_bounds__(1024)
 k_pc_small(const double *__restrict__ C, int d, double *__restrict__ v64, float *__restrict__ v32) {
+    // FP64 is slow on this part: everything but the final normalisation runs
+    // in FP32 (v1's accuracy only affects pruning; the FP64 normalisation
+    // makes ||v64|| = 1 to FP64 precision, which the score bounds assume)
     extern __shared__ unsigned char smem[];
-    double *v = reinterpret_cast<double *>(smem);          // d
-    double *w = v + d;                                     // d
-    double *red = w + d;                                   // 32
+    double *vd = reinterpret_cast<double *>(smem);         // d
+    double *red = vd + d;                                  // 32
     float *redf = reinterpret_cast<float *>(red + 32);     // 32
-    float *M = redf + 32;                                  // d*d
-    float *T = M + d * d;                                  // d*d
+    float *v = redf + 32;                                  // d
+    float *w = v + d;                                      // d
+    float *M = w + d;                                      // d*d
+    float *T = M + d * d;                                  // d*d (later: C in FP32)
     const int t = threadIdx.x, nt = blockDim.x;
+    const int warp = t >> 5, lane = t & 31, nw = nt >> 5;
     const int dd = d * d;
 
-    double tr = 0.0;
-    for (int i = 0; i < d; ++i) tr += C[int64_t(i) * d + i];
+    if (warp == 0) {
+        double tr = 0.0;
+        for (int i = lane; i < d; i += 32) tr += C[int64_t(i) * d + i];
+        for (int o = 16; o; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+        if (lane == 0) red[0] = tr;
+    }
+    __syncthreads();
+    const double tr = red[0];
     const bool degenerate = !(tr > 0.0) || !isfinite(tr);
     if (!degenerate) {
-        for (int e = t; e < dd; e += nt) M[e] = (float)(C[e] / tr);
+        const float inv_tr = (float)(1.0 / tr);
+        for (int e = t; e < dd; e += nt) M[e] = (float)C[e] * inv_tr;
         __syncthreads();
         for (int it = 0; it < kSquarings; ++it) {
             for (int e = t; e < dd; e += nt) {
                 const int i = e / d, j = e % d;
-                float s = 0.f;
-                for (int k = 0; k < d; ++k) s = fmaf(M[i * d + k], M[k * d + j], s);
-                T[e] = s;
+                float acc = 0.f;
+                for (int k = 0; k < d; ++k) acc = fmaf(M[i * d + k], M[k * d + j], acc);
+                T[e] = acc;
             }
             __syncthreads();
             float part = 0.f;
@@ -243,44 +255,50 @@ k_pc_small(const double *__restrict__ C, int d, double *__restrict__ v64, float 
         int jbest = 0;
         float best = -1.f;
         for (int j = 0; j < d; ++j) {
-            float x = M[j * d + j];
+            const float x = M[j * d + j];
             if (x > best) { best = x; jbest = j; }
         }
-        for (int i = t; i < d; i += nt) v[i] = (double)M[i * d + jbest];
+        for (int i = t; i < d; i += nt) v[i] = M[i * d + jbest];
+        // FP32 copy of C for the power steps
+        for (int e = t; e < dd; e += nt) T[e] = (float)C[e];
         __syncthreads();
-    } else {
-        for (int i = t; i < d; i += nt) v[i] = (i == 0) ? 1.0 : 0.0;
-        __syncthreads();
-    }
-    // FP64 power steps on C (skipped for C = 0) and FP64 normalisation
-    for (int it = 0; it < (degenerate ? 0 : kPowerSteps); ++it) {
-        for (int i = t; i < d; i += nt) {
-            double s = 0.0;
-            for (int k = 0; k < d; ++k) s += C[int64_t(i) * d + k] * v[k];
-            w[i] = s;
+        // power steps v <- C v / ||C v|| (FP32, one warp per row)
+        for (int it = 0; it < kPowerSteps; ++it) {
+            for (int i = warp; i < d; i += nw) {
+                float s = 0.f;
+                for (int k = lane; k < d; k += 32) s = fmaf(T[i * d + k], v[k], s);
+                for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0) w[i] = s;
+            }
+            __syncthreads();
+            float part = 0.f;
+            for (int i = t; i < d; i += nt) part += w[i] * w[i];
+            const float n2 = block_sum_f(part, redf);
+            if (!(n2 > 0.f) || !isfinite(n2)) break;
+            const float inv = 1.f / sqrtf(n2);
+            for (int i = t; i < d; i += nt) v[i] = w[i] * inv;
+            __syncthreads();
         }
-        __syncthreads();
-        double part = 0.0;
-        for (int i = t; i < d; i += nt) part += w[i] * w[i];
-        const double nrm2 = block_sum_d(part, red);
-        if (!(nrm2 > 0.0) || !isfinite(nrm2)) break;
-        const double inv = 1.0 / sqrt(nrm2);
-        for (int i = t; i < d; i += nt) v[i] = w[i] * inv;
+    } else {
+        for (int i = t; i < d; i += nt) v[i] = (i == 0) ? 1.f : 0.f;
         __syncthreads();
     }
-    double part = 0.0;
-    for (int i = t; i < d; i += nt) part += v[i] * v[i];
-    double nrm2 = block_sum_d(part, red);
-    if (!(nrm2 > 0.0) || !isfinite(nrm2)) {
-        for (int i = t; i < d; i += nt) v[i] = (i == 0) ? 1.0 : 0.0;
-        __syncthreads();
-        nrm2 = 1.0;
-    }
-    const double inv = 1.0 / sqrt(nrm2);
-    for (int i = t; i < d; i += nt) {
-        const double x = v[i] * inv;
-        v64[i] = x;
-        v32[i] = (float)x;
+    // FP64 normalisation (one warp)
+    if (warp == 0) {
+        double n2 = 0.0;
+        for (int i = lane; i < d; i += 32) n2 += (double)v[i] * (double)v[i];
+        for (int o = 16; o; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+        const bool ok = n2 > 0.0 && isfinite(n2);
+        const double inv = ok ? 1.0 / sqrt(n2) : 1.0;
+        for (int i = lane; i < d; i += 32) {
+            const double x = ok ? (double)v[i] * inv : (i == 0 ? 1.0 : 0.0);
+            vd[i] = x;
+        }
+        __syncwarp();
+        for (int i = lane; i < d; i += 32) {
+            v64[i] = vd[i];
+            v32[i] = (float)vd[i];
+        }
     }
 }
 

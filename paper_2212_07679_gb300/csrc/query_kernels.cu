@@ -450,12 +450,11 @@ __device__ __forceinline__ void decide_body(
          const uint2 *__restrict__ surv, const unsigned long long *__restrict__ count, int64_t cap,
          const float *__restrict__ qraw, const int32_t *__restrict__ qorder,
          const float *__restrict__ praw, const int32_t *__restrict__ porder, int d, int dp,
-         double R2, float *__restrict__ rec_d2, int32_t *__restrict__ rec_pos,
-         uint2 *__restrict__ rec_rc, int32_t *__restrict__ counts,
+         double R2, const DecideConsts &dc, float *__restrict__ rec_d2,
+         int32_t *__restrict__ rec_pos, uint2 *__restrict__ rec_rc, int32_t *__restrict__ counts,
          unsigned long long *__restrict__ n_fp64) {
     const int64_t nsurv = min((int64_t)*count, cap);
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    const DecideConsts dc = decide_consts(d, R2);
     for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < nsurv; s += stride)
         decide_one_survivor<kSym>(s, surv, cap, qraw, qorder, praw, porder, d, dp, R2, dc, rec_d2,
                                   rec_pos, rec_rc, counts, n_fp64);
@@ -474,12 +473,11 @@ __device__ __forceinline__ void decide_group_body(
          const uint2 *__restrict__ surv, const unsigned long long *__restrict__ count, int64_t cap,
          const float *__restrict__ qraw, const int32_t *__restrict__ qorder,
          const float *__restrict__ praw, const int32_t *__restrict__ porder, int d, int dp,
-         double R2, float *__restrict__ rec_d2, int32_t *__restrict__ rec_pos,
-         uint2 *__restrict__ rec_rc, int32_t *__restrict__ counts,
+         double R2, const DecideConsts &dc, float *__restrict__ rec_d2,
+         int32_t *__restrict__ rec_pos, uint2 *__restrict__ rec_rc, int32_t *__restrict__ counts,
          unsigned long long *__restrict__ n_fp64) {
     constexpr int GPW = 32 / G;   // groups per warp
     const int64_t nsurv = min((int64_t)*count, cap);
-    const DecideConsts dc = decide_consts(d, R2);
     const int lane = int(threadIdx.x % G);
     const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t wstride = (int64_t(gridDim.x) * blockDim.x) >> 5;
@@ -552,11 +550,11 @@ __device__ __forceinline__ void decide_group_body(
     const uint2 *__restrict__ surv, const unsigned long long *__restrict__ count, int64_t cap, \
         const float *__restrict__ qraw, const int32_t *__restrict__ qorder,                    \
         const float *__restrict__ praw, const int32_t *__restrict__ porder, int d, int dp,     \
-        double R2, float *__restrict__ rec_d2, int32_t *__restrict__ rec_pos,                  \
+        double R2, DecideConsts dc, float *__restrict__ rec_d2, int32_t *__restrict__ rec_pos,  \
         uint2 *__restrict__ rec_rc, int32_t *__restrict__ counts,                              \
         unsigned long long *__restrict__ n_fp64
-#define SNN_DECIDE_PASS surv, count, cap, qraw, qorder, praw, porder, d, dp, R2, rec_d2, rec_pos, \
-                        rec_rc, counts, n_fp64
+#define SNN_DECIDE_PASS surv, count, cap, qraw, qorder, praw, porder, d, dp, R2, dc, rec_d2,      \
+                        rec_pos, rec_rc, counts, n_fp64
 __global__ void __launch_bounds__(256) k_decide_sym(SNN_DECIDE_ARGS) {
     decide_body<true>(SNN_DECIDE_PASS);
 }

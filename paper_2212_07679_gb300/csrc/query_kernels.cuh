@@ -62,6 +62,11 @@ struct ScoreJob {
 };
 
 // Per-set descriptor of a batched query (device memory).
+// Constants of the FP32 tier-1 decision (see decide_df).
+struct DecideConsts {
+    float r2h, r2l, rel, rel2, tiny;
+};
+
 struct SetDesc {
     int64_t m, n;               // queries, data points
     int d, dp, sym;             // dims, row stride, symmetric self-join
@@ -69,6 +74,7 @@ struct SetDesc {
     int64_t q_glob;             // first global query number of the set
     int64_t tile0;              // first global tile of the set
     double R2, Wbase;           // fl64(R*R), band half-width base
+    DecideConsts dc;            // decision constants for R2
     const float *q_alpha, *q_raw, *q_xc, *q_hx, *q_nrm;
     const int32_t *q_order;
     const float *x_alpha, *x_raw, *x_xc, *x_hx, *x_nrm;
@@ -113,11 +119,10 @@ __global__ void k_score_fp32_multi(ScoreArgs a);
 // FP64 loop: near-ties, values near a float rounding boundary, overflow,
 // underflow).  nz: some coordinate differs (H = 0 with nz may be an
 // underflow).
-struct DecideConsts {
-    float r2h, r2l, rel, rel2, tiny;
-};
 
-__device__ __forceinline__ DecideConsts decide_consts(int d, double R2) {
+
+// (computed on the host and passed to the kernels: FP64 is slow on this part)
+__host__ __device__ inline DecideConsts decide_consts(int d, double R2) {
     DecideConsts c;
     c.r2h = (float)R2;
     c.r2l = (float)(R2 - (double)c.r2h);
@@ -156,8 +161,8 @@ __device__ __forceinline__ int decide_df(float H, float L, bool nz, const Decide
 #define SNN_DECIDE_DECL(name)                                                                \
     __global__ void name(const uint2 *surv, const unsigned long long *count, int64_t cap,    \
                          const float *qraw, const int32_t *qorder, const float *praw,        \
-                         const int32_t *porder, int d, int dp, double R2, float *rec_d2,     \
-                         int32_t *rec_pos, uint2 *rec_rc, int32_t *counts,                   \
+                         const int32_t *porder, int d, int dp, double R2, DecideConsts dc,   \
+                         float *rec_d2, int32_t *rec_pos, uint2 *rec_rc, int32_t *counts,    \
                          unsigned long long *n_fp64)
 SNN_DECIDE_DECL(k_decide_sym);
 SNN_DECIDE_DECL(k_decide_one);

@@ -187,7 +187,7 @@ __global__ void k_max_nonneg(const float *__restrict__ x, int64_t n, float *__re
 static snn_status first_direction(const double *C, const double *diagC, int d, double *v64,
                                   float *v32, int *err, cudaStream_t s, Scratch &scr) {
     if (d <= kPcSmallMaxD) {
-        const size_t smem = (2 * d + 32) * sizeof(double) + 32 * sizeof(float) +
+        const size_t smem = (d + 32) * sizeof(double) + (32 + 2 * d) * sizeof(float) +
                             2 * size_t(d) * d * sizeof(float);
         SNN_LAUNCH(k_pc_small, 1, 1024, smem, s)(C, d, v64, v32);
         SNN_LAUNCH_CHECK();
@@ -598,7 +598,8 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         const unsigned dgrid =
             std::min<unsigned>(grid_for(cap * G, 256), unsigned(16 * device_sm_count()));
         SNN_LAUNCH(dk, dgrid, 256, 0, s)(surv, ctr, cap, qs.raw, qs.order, ds.raw, ds.order, d, dp,
-                                         R2, rec_d2, rec_pos, rec_rc, counts, ctr + 4);
+                                         R2, decide_consts(d, R2), rec_d2, rec_pos, rec_rc, counts,
+                                         ctr + 4);
         CUDA_Q(cudaGetLastError());
         if (stats) cudaEventRecord(ev[3], s);
         SNN_LAUNCH(k_counts_to_i64, grid_for(m, 256), 256, 0, s)(counts, m, counts64);
