@@ -74,15 +74,23 @@ snn_status make_map(CUtensorMap *map, const uint16_t *ptr, int64_t rows, int64_t
 namespace {
 
 constexpr int kTM = 128;            // queries per tile (MMA M)
-// epilogue: two warps per TMEM lane quadrant and query sub-tile (half the
-// columns each); producer and MMA warps in front
-__host__ __device__ constexpr int tc_epi_warps(int mt) { return 8 * mt; }
-__host__ __device__ constexpr int tc_threads(int mt) { return 64 + 32 * tc_epi_warps(mt); }
+// epilogue: per TMEM lane quadrant and query sub-tile, two warps (half the
+// columns each) for chunks of 128 or more rows, one warp below; producer and
+// MMA warps in front
+__host__ __device__ constexpr int tc_halves(int bn) { return bn >= 128 ? 2 : 1; }
+__host__ __device__ constexpr int tc_epi_warps(int mt, int bn) { return 4 * mt * tc_halves(bn); }
+__host__ __device__ constexpr int tc_threads(int mt, int bn) { return 64 + 32 * tc_epi_warps(mt, bn); }
+// accumulator buffers in a CTA's share of the 512 TMEM columns (cps CTAs per
+// SM): four when they fit (the MMAs of three chunks then cover the hand-back
+// latency of the fourth), else two
+__host__ __device__ constexpr int tc_nbuf(int mt, int bn, int cps) {
+    return 4 * mt * bn <= 512 / cps ? 4 : 2;
+}
 constexpr int kExtra = 9;           // folded columns
 // dynamic shared memory per CTA (minus base alignment and barriers) for 1
 // or 2 resident CTAs per SM
 __host__ __device__ constexpr int smem_budget(int cps, int align) {
-    return (cps == 1 ? 232448 : 115712) - align - 256;
+    return (cps == 1 ? 232448 : 115712) - align - 512;
 }
 
 // Shape of one kernel instance: NSPLIT BF16 parts, BK columns per k-block
@@ -109,22 +117,23 @@ struct TcShape {
     // per-epilogue-warp staging of survivors (flushed in batches: one
     // global atomic per batch instead of one per 32-column group)
     static constexpr int kStgEntries = 128;
-    static constexpr int kStgBytes = tc_epi_warps(MT) * kStgEntries * 8;
+    static constexpr int kStgBytes = tc_epi_warps(MT, BN) * kStgEntries * 8;
     static constexpr int kStagesRaw = (kSmemBudget - kAResBytes - kStgBytes) / kStageBytes;
-    static constexpr int kStages = kStagesRaw > 8 ? 8 : kStagesRaw;
+    static constexpr int kStages = kStagesRaw > 12 ? 12 : kStagesRaw;
     static constexpr int kNP = NSPLIT == 2 ? 3 : 6;     // MMAs per k-step
     static constexpr int kKSteps = BK / 16;             // k-steps per k-block
     static constexpr int kRowBytes = BK * 2;
     static constexpr int kRowBytesN = NW * 2;
-    static constexpr uint32_t kTmemCols = 2 * MT * BN;
-    static constexpr int kEpiWarps = tc_epi_warps(MT);
-    static constexpr int kThreads = tc_threads(MT);
+    static constexpr uint32_t kTmemCols = tc_nbuf(MT, BN, CPS) * MT * BN;
+    static constexpr int kEpiWarps = tc_epi_warps(MT, BN);
+    static constexpr int kThreads = tc_threads(MT, BN);
+    static constexpr int kNBuf = tc_nbuf(MT, BN, CPS);
     static constexpr size_t kSmem =
-        size_t(kAResBytes) + size_t(kStages) * kStageBytes + kAlign + 256 + kStgBytes;
+        size_t(kAResBytes) + size_t(kStages) * kStageBytes + kAlign + 512 + kStgBytes;
     static_assert(kStagesRaw >= 2, "shape does not fit shared memory");
     static_assert(ARES || NW == BK, "narrow parts need a resident query tile");
     static_assert(MT == 1 || ARES, "several query tiles per item need a resident query tile");
-    static_assert(kTmemCols <= 512, "accumulators exceed TMEM");
+    static_assert(kTmemCols * CPS <= 512, "accumulators exceed TMEM");
     static_assert(NW == 16 || NW == 32 || NW == 64, "unsupported part width");
 };
 
@@ -167,7 +176,7 @@ __device__ __forceinline__ ItemInfo item_info(const TcArgs &a, int64_t item) {
 }
 
 template <int NSPLIT, int BK, int BN, bool ARES, int CPS, int NW, int MT>
-__global__ void __launch_bounds__(tc_threads(MT), CPS)
+__global__ void __launch_bounds__(tc_threads(MT, BN), CPS)
 k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUtensorMap qa1,
            const __grid_constant__ CUtensorMap qa2, const __grid_constant__ CUtensorMap xb0,
            const __grid_constant__ CUtensorMap xb1, const __grid_constant__ CUtensorMap xb2,
@@ -175,7 +184,7 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
     using Sh = TcShape<NSPLIT, BK, BN, ARES, CPS, NW, MT>;
     constexpr int S = Sh::kStages;
     constexpr int NP = Sh::kNP;
-    constexpr int CSTEP = BN / kBR;              // kBR-row chunks per MMA chunk
+    constexpr int NB = Sh::kNBuf;                // accumulator buffers
     constexpr uint32_t kIdesc = idesc_bf16<kTM, BN>();
     // (A part, B part) products kept by the split: all with pa + pb <= NSPLIT-1
     constexpr int kPa[6] = {0, 0, 1, 0, 1, 2};
@@ -201,17 +210,18 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
     auto empty_bar = [&](int s) { return bar0 + 8u * (S + s); };
     auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * S + b); };
-    auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * S + 2 + b); };
-    const uint32_t done_bar = bar0 + 8u * (2 * S + 4);
-    auto afull_bar = [&](int k) { return bar0 + 8u * (2 * S + 5 + k); };
-    auto aempty_bar = [&](int k) { return bar0 + 8u * (2 * S + 7 + k); };
-    unsigned char *gmisc = gbase + (bar0 - base) + 8 * (2 * S + 9);
+    auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * S + NB + b); };
+    const uint32_t done_bar = bar0 + 8u * (2 * S + 2 * NB);
+    auto afull_bar = [&](int k) { return bar0 + 8u * (2 * S + 2 * NB + 1 + k); };
+    auto aempty_bar = [&](int k) { return bar0 + 8u * (2 * S + 2 * NB + 3 + k); };
+    unsigned char *gmisc = gbase + (bar0 - base) + 8 * (2 * S + 2 * NB + 5);
+    static_assert(8 * (2 * S + 2 * NB + 5) + 16 <= 512, "barrier area");
     volatile uint32_t *s_tmem = reinterpret_cast<volatile uint32_t *>(gmisc);
     volatile int *s_abort = reinterpret_cast<volatile int *>(gmisc + 4);
     volatile int *s_consumed = reinterpret_cast<volatile int *>(gmisc + 8);
     volatile int *s_aconsumed = reinterpret_cast<volatile int *>(gmisc + 12);
     // survivor staging: kStgEntries per epilogue warp, after the barriers
-    uint2 *s_stg = reinterpret_cast<uint2 *>(gbase + (bar0 - base) + 256);
+    uint2 *s_stg = reinterpret_cast<uint2 *>(gbase + (bar0 - base) + 512);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const CUtensorMap *qa[3] = {&qa0, &qa1, &qa2};
@@ -222,11 +232,13 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
             mbar_init(full_bar(s), 1);
             mbar_init(empty_bar(s), 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NB; ++b) {
             mbar_init(tfull_bar(b), 1);
-            mbar_init(tempty_bar(b), 32 * Sh::kEpiWarps);
-            mbar_init(afull_bar(b), 1);
-            mbar_init(aempty_bar(b), 1);
+            mbar_init(tempty_bar(b), Sh::kEpiWarps);   // one arrival per epilogue warp
+        }
+        for (int k = 0; k < 2; ++k) {
+            mbar_init(afull_bar(k), 1);
+            mbar_init(aempty_bar(k), 1);
         }
         mbar_init(done_bar, 1);
         *s_abort = 0;
@@ -236,8 +248,7 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) {
-        // two accumulators of BN FP32 columns
-        // two accumulator sets of MT x BN FP32 columns
+        // NB accumulator sets of MT x BN FP32 columns
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32((const void *)s_tmem)),
                      "n"(Sh::kTmemCols)
@@ -269,8 +280,8 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                         tma_load_2d(a_tile(k, p), qa[p], 0, int(f.q0), afull_bar(k));
                     a_issued = itm + 1;
                 }
-                for (int64_t c = f.c_first; c < f.c_end && !*s_abort; c += CSTEP) {
-                    const int64_t j0 = f.band_lo + c * kBR;
+                for (int64_t jr = f.c_first * kBR; jr < f.c_end * kBR && !*s_abort; jr += BN) {
+                    const int64_t j0 = f.band_lo + jr;
                     for (int kb = 0; kb < a.nkb; ++kb, ++it) {
                         const int s = it % S;
                         const uint32_t round = uint32_t(it / S);
@@ -300,9 +311,9 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                     *s_aconsumed = itm + 1;
                     tmem_fence_after();
                 }
-                for (int64_t c = f.c_first; c < f.c_end && ok; c += CSTEP, ++chunk) {
-                    const int b = chunk & 1;
-                    const uint32_t use = uint32_t(chunk >> 1);
+                for (int64_t jr = f.c_first * kBR; jr < f.c_end * kBR && ok; jr += BN, ++chunk) {
+                    const int b = chunk % NB;
+                    const uint32_t use = uint32_t(chunk / NB);
                     if (!(ok = mbar_wait(tempty_bar(b), (use & 1u) ^ 1u, s_abort, a.err))) break;
                     tmem_fence_after();
                     const uint32_t dt0 = tmem + uint32_t(b * MT * BN);
@@ -353,10 +364,11 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
         const int ew = warp - 2;                   // 0 .. kEpiWarps-1
         const int quad = warp & 3;                 // TMEM lanes 32*quad .. +31
         const int sub = ew >> 2;
-        const int half = sub & 1;                  // which half of the columns
-        const int ht = sub >> 1;                   // which query sub-tile
+        constexpr int kHalves = tc_halves(BN);
+        const int half = sub % kHalves;            // which half of the columns
+        const int ht = sub / kHalves;              // which query sub-tile
         const int qi = ht * kTM + quad * 32 + lane;   // query row within the item's tiles
-        constexpr int kGroups = BN / 32 / 2;       // 32-column groups per warp
+        constexpr int kGroups = BN / 32 / kHalves; // 32-column groups per warp
         constexpr int kStg = Sh::kStgEntries;
         uint2 *stg = s_stg + ew * kStg;
         int scount = 0;                            // staged entries (warp-uniform)
@@ -378,10 +390,10 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
         for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
             const ItemInfo f = item_info<MT>(a, item);
             const int64_t q = f.q0 + qi;
-            for (int64_t c = f.c_first; c < f.c_end && ok; c += CSTEP, ++chunk) {
-                const int64_t j0 = f.band_lo + c * kBR;
-                const int b = chunk & 1;
-                const uint32_t use = uint32_t(chunk >> 1);
+            for (int64_t jr = f.c_first * kBR; jr < f.c_end * kBR && ok; jr += BN, ++chunk) {
+                const int64_t j0 = f.band_lo + jr;
+                const int b = chunk % NB;
+                const uint32_t use = uint32_t(chunk / NB);
                 ok = mbar_wait(tfull_bar(b), use & 1u, s_abort, a.err);
                 if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
                 tmem_fence_after();
@@ -397,6 +409,13 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                     float mx;
                     const int cb0 = half * kGroups + g2;
                     tmem_ld64_max(tbase + uint32_t(cb0 * 32), rr, mx);
+                    if (kGroups == 2) {
+                        // this warp's only load of the chunk is complete: hand
+                        // the accumulator back before the survivor processing
+                        tmem_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(tempty_bar(b));
+                    }
                     // every accumulator of the 64 columns negative: all rejected
                     // (an acceptable pair's accumulator is strictly positive)
                     const bool any = !(mx < 0.f);
@@ -461,8 +480,13 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                         }
                     }
                 }
-                tmem_fence_before();
-                mbar_arrive(tempty_bar(b));
+                if (kGroups != 2) {
+                    // the warp's TMEM loads are complete (waited per thread):
+                    // one arrival for the whole warp
+                    tmem_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(tempty_bar(b));
+                }
             }
         }
         flush();
