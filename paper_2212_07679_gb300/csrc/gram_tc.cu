@@ -39,19 +39,19 @@ constexpr int kPowerSteps = 4;
 template <typename T, int NSPLIT>
 __global__ void __launch_bounds__(256)
 k_gram_pack(const T *__restrict__ X, int64_t n, int d, int64_t ld, const float *__restrict__ cvec,
-            const double *__restrict__ diag, uint16_t *__restrict__ o0, uint16_t *__restrict__ o1,
+            const T *__restrict__ diag, uint16_t *__restrict__ o0, uint16_t *__restrict__ o1,
             int64_t n64) {
     __shared__ __align__(16) uint16_t sh[NSPLIT][kPT][kPT + 8];   // [feature][row]
-    __shared__ double s_inv;
+    __shared__ T s_inv;
     const int64_t r0 = int64_t(blockIdx.x) * kPT;
     const int i0 = blockIdx.y * kPT;
     const bool trace_norm = diag != nullptr;
     if (trace_norm) {
         if (threadIdx.x < 32) {
-            double tr = 0.0;
+            T tr = T(0);
             for (int i = threadIdx.x; i < d; i += 32) tr += diag[i];
             for (int o = 16; o; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
-            if (threadIdx.x == 0) s_inv = (tr > 0.0 && isfinite(tr)) ? 1.0 / tr : 1.0;
+            if (threadIdx.x == 0) s_inv = (tr > T(0) && isfinite(tr)) ? T(1) / tr : T(1);
         }
         __syncthreads();
     }
@@ -65,7 +65,7 @@ k_gram_pack(const T *__restrict__ X, int64_t n, int d, int64_t ld, const float *
         if (r < n && i < d) {
             const T v = X[r * ld + i];
             if (trace_norm)
-                x = (float)((double)v * s_inv);
+                x = (float)(v * s_inv);
             else
                 x = cvec ? (float)v - cvec[i] : (float)v;
         }
@@ -96,8 +96,8 @@ struct GramArgs {
     int kb_per;      // k-blocks per split
     int d;
     float *part;     // [split][d][d] FP32 partial tiles (upper triangle used)
-    double *C;       // DIRECT: the full symmetric result (FP64) ...
-    double *diag;    // ... and its diagonal
+    float *Cf;       // DIRECT: the full symmetric result (FP32) ...
+    float *diagf;    // ... and its diagonal
     int *err;
 };
 
@@ -240,15 +240,15 @@ k_gram_tc(const __grid_constant__ CUtensorMap m0, const __grid_constant__ CUtens
             if (i < a.d) {
                 const int j0 = bj * kGM + h * 64;
                 if (DIRECT) {
-                    double *row = a.C + int64_t(i) * a.d;
+                    float *row = a.Cf + int64_t(i) * a.d;
 #pragma unroll
                     for (int c = 0; c < 64; ++c) {
                         const int j = j0 + c;
                         if (j < a.d) {
-                            const double v = (double)__uint_as_float(r[c]);
+                            const float v = __uint_as_float(r[c]);
                             row[j] = v;
-                            if (bi != bj) a.C[int64_t(j) * a.d + i] = v;
-                            if (j == i) a.diag[i] = v;
+                            if (bi != bj) a.Cf[int64_t(j) * a.d + i] = v;
+                            if (j == i) a.diagf[i] = v;
                         }
                     }
                 } else {
@@ -291,14 +291,14 @@ __global__ void k_gram_reduce2(const float *__restrict__ part, int nsplit, int d
 // entry (smallest index among equals); e1 when no diagonal entry is positive
 // (C = 0: all points equal).  One block.
 __global__ void __launch_bounds__(1024)
-k_pick_column64(const double *__restrict__ T, const double *__restrict__ diag, int d,
+k_pick_column64(const float *__restrict__ T, const float *__restrict__ diag, int d,
                 double *__restrict__ v) {
     __shared__ double sb[32];
     __shared__ int sj[32];
     double best = 0.0;
     int jb = 0x7fffffff;
     for (int j = threadIdx.x; j < d; j += blockDim.x) {
-        const double x = diag[j];
+        const double x = (double)diag[j];
         if (x > best) {
             best = x;
             jb = j;
@@ -329,7 +329,7 @@ k_pick_column64(const double *__restrict__ T, const double *__restrict__ diag, i
     const bool degenerate = !(sb[0] > 0.0) || !isfinite(sb[0]);
     const int jbest = sj[0];
     for (int i = threadIdx.x; i < d; i += blockDim.x)
-        v[i] = degenerate ? (i == 0 ? 1.0 : 0.0) : T[int64_t(jbest) * d + i];
+        v[i] = degenerate ? (i == 0 ? 1.0 : 0.0) : (double)T[int64_t(jbest) * d + i];
 }
 
 // w = C v / ||v|| (FP64; v = 0 gives w = 0), one warp per row.  Every block
@@ -360,7 +360,8 @@ k_power64(const double *__restrict__ C, int d, const double *__restrict__ v,
 // FP32 partials summed in FP64.
 template <int NSPLIT, bool DIRECT>
 snn_status gram_gemm(const uint16_t *p0, const uint16_t *p1, int d, int dpad, int64_t n64,
-                     double *C, double *diag, int *err, cudaStream_t s, Scratch &scr) {
+                     double *C, double *diag, float *Cf, float *diagf, int *err, cudaStream_t s,
+                     Scratch &scr) {
     using Sh = GramShape<NSPLIT>;
     CUtensorMap maps[2];
     SNN_TRY(make_map(&maps[0], p0, dpad, n64, kGKB, kGM));
@@ -378,8 +379,8 @@ snn_status gram_gemm(const uint16_t *p0, const uint16_t *p1, int d, int dpad, in
     nsplitk = int(cdiv(a.nkb, a.kb_per));   // every split holds at least one k-block
     a.d = d;
     a.err = err;
-    a.C = C;
-    a.diag = diag;
+    a.Cf = Cf;
+    a.diagf = diagf;
     a.part = nullptr;
     if (!DIRECT) SNN_TRY(scr.alloc(&a.part, size_t(nsplitk) * d * d));
     auto kern = k_gram_tc<NSPLIT, DIRECT>;
@@ -407,7 +408,7 @@ snn_status gram_tc(const float *X, int64_t n, int d, int64_t ld, const float *cv
     SNN_LAUNCH(pack, dim3(unsigned(n64 / kPT), unsigned(dpad / kPT)), 256, 0, s)(
         X, n, d, ld, cvec, nullptr, p0, p1, n64);
     SNN_LAUNCH_CHECK();
-    return gram_gemm<2, false>(p0, p1, d, dpad, n64, C, diag, err, s, scr);
+    return gram_gemm<2, false>(p0, p1, d, dpad, n64, C, diag, nullptr, nullptr, err, s, scr);
 }
 
 snn_status first_direction_tc(const double *C, const double *diagC, int d, double *v64,
@@ -415,22 +416,25 @@ snn_status first_direction_tc(const double *C, const double *diagC, int d, doubl
     const int dpad = int(cdiv(d, kGM) * kGM);
     const int64_t n64 = cdiv(d, kGKB) * kGKB;
     uint16_t *p0;
-    double *T, *diag, *w0, *w1;
+    float *T, *diag;
+    double *w0, *w1;
     SNN_TRY(scr.alloc(&p0, size_t(dpad) * n64));
     SNN_TRY(scr.alloc(&T, size_t(d) * d));
     SNN_TRY(scr.alloc(&diag, d));
     SNN_TRY(scr.alloc(&w0, d));
     SNN_TRY(scr.alloc(&w1, d));
     const dim3 pgrid(unsigned(n64 / kPT), unsigned(dpad / kPT));
-    // M0 = C / trace(C); M_{k+1} = M_k^2 / trace(M_k^2), one BF16 part (only
-    // the pruning power depends on the accuracy of v1)
-    auto pack = k_gram_pack<double, 1>;
-    SNN_LAUNCH(pack, pgrid, 256, 0, s)(C, d, d, d, nullptr, diagC, p0, nullptr, n64);
+    // M0 = C / trace(C); M_{k+1} = M_k^2 / trace(M_k^2), one BF16 part and
+    // FP32 powers (only the pruning power depends on the accuracy of v1)
+    auto pack64 = k_gram_pack<double, 1>;
+    auto pack32 = k_gram_pack<float, 1>;
+    SNN_LAUNCH(pack64, pgrid, 256, 0, s)(C, d, d, d, nullptr, diagC, p0, nullptr, n64);
     SNN_LAUNCH_CHECK();
     for (int it = 0; it < kSquarings; ++it) {
-        SNN_TRY((gram_gemm<1, true>(p0, nullptr, d, dpad, n64, T, diag, err, s, scr)));
+        SNN_TRY((gram_gemm<1, true>(p0, nullptr, d, dpad, n64, nullptr, nullptr, T, diag, err, s,
+                                    scr)));
         if (it + 1 < kSquarings) {
-            SNN_LAUNCH(pack, pgrid, 256, 0, s)(T, d, d, d, nullptr, diag, p0, nullptr, n64);
+            SNN_LAUNCH(pack32, pgrid, 256, 0, s)(T, d, d, d, nullptr, diag, p0, nullptr, n64);
             SNN_LAUNCH_CHECK();
         }
     }
