@@ -566,30 +566,47 @@ __global__ void k_tc_pack(const float *__restrict__ xc, int dp, const float *__r
     const int lane = threadIdx.x & 31;
     if (r0 >= rows) return;   // whole warps leave together
     const int nr = int(min(int64_t(32), rows - r0));
-    for (int rr = 0; rr < nr; ++rr) {
+    // data columns, four per lane (float4 loads, 8-byte stores); the lanes of
+    // a warp cover lpr = min(32, K2 / 4) quads of one row and 32 / lpr rows at
+    // a time.  Quads over the folded columns are written as zeros here and
+    // overwritten below (after __syncwarp).
+    const int lpr = K2 / 4 < 32 ? K2 / 4 : 32;
+    const int rpi = 32 / lpr;
+    const int sub = lane / lpr, ql = lane % lpr;
+    for (int rr = sub; rr < nr; rr += rpi) {
         const int64_t r = r0 + rr;
-        const float *xr = xc + r * dp;
-        const int64_t ro = r * K2;
-        for (int k = lane; k < K2; k += 32) {
-            uint16_t v0 = 0, v1 = 0, v2 = 0;
-            if (k < d) {
-                const float x = xr[k];
-                const __nv_bfloat16 h = __float2bfloat16_rn(x);
-                const float xr1 = x - __bfloat162float(h);               // exact
-                const __nv_bfloat16 l = __float2bfloat16_rn(xr1);
-                v0 = bf16_bits(h);
-                v1 = bf16_bits(l);
-                if (NSPLIT == 3) v2 = bf16_bits(__float2bfloat16_rn(xr1 - __bfloat162float(l)));
+        const float4 *xr4 = reinterpret_cast<const float4 *>(xc + r * dp);
+        for (int k0 = ql * 4; k0 < K2; k0 += lpr * 4) {
+            const float4 x4 = k0 < dp ? xr4[k0 / 4] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
+            uint16_t v0[4], v1[4], v2[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                v0[e] = v1[e] = v2[e] = 0;
+                if (k0 + e < d) {
+                    const float x = xv[e];
+                    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+                    const float xr1 = x - __bfloat162float(h);               // exact
+                    const __nv_bfloat16 l = __float2bfloat16_rn(xr1);
+                    v0[e] = bf16_bits(h);
+                    v1[e] = bf16_bits(l);
+                    if (NSPLIT == 3) v2[e] = bf16_bits(__float2bfloat16_rn(xr1 - __bfloat162float(l)));
+                }
             }
-            if (k < d || k >= d + kExtra) p0[ro + k] = v0;   // folded columns: below
+            auto pack4 = [](const uint16_t *v) {
+                return make_uint2(uint32_t(v[0]) | (uint32_t(v[1]) << 16),
+                                  uint32_t(v[2]) | (uint32_t(v[3]) << 16));
+            };
+            *reinterpret_cast<uint2 *>(p0 + r * K2 + k0) = pack4(v0);
             // parts 2 and 3 hold data columns only (zero elsewhere), rows of
             // K2n columns
-            if (k < K2n) {
-                if (NSPLIT >= 2) p1[r * K2n + k] = v1;
-                if (NSPLIT >= 3) p2[r * K2n + k] = v2;
+            if (k0 < K2n) {
+                if (NSPLIT >= 2) *reinterpret_cast<uint2 *>(p1 + r * K2n + k0) = pack4(v1);
+                if (NSPLIT >= 3) *reinterpret_cast<uint2 *>(p2 + r * K2n + k0) = pack4(v2);
             }
         }
     }
+    __syncwarp();
     if (lane < nr) {
         const int64_t r = r0 + lane;
         uint16_t *f = p0 + r * K2 + d;
