@@ -346,6 +346,131 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_ragged(args):
+    """Ragged batch: 256 independent mixtures (n log-uniform in [1e3, 2e5],
+    d in {2, 3, 8, 32}, 10% of each set as out-of-sample queries).  One step =
+    the batched index build of every set plus one run of the batched query
+    plan; the same work with one index build and one query call per set, and
+    the plan's CUDA-graph replay of the query phase alone, are timed beside it."""
+    import torch
+    from paper_2212_07679_gb300 import snn
+    from paper_2212_07679_gb300 import workloads as wl
+    sets = wl.ragged_batch(n_scale=args.n / 1e5) if args.n else wl.ragged_batch()
+    Xs = [torch.from_numpy(s.P).cuda() for s in sets]
+    Qs = [torch.from_numpy(s.Q).cuda() for s in sets]
+    Rs = [s.R for s in sets]
+    M = sum(q.shape[0] for q in Qs)
+    N = sum(x.shape[0] for x in Xs)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def make_plan(idx):
+        plan = snn.BatchPlan(idx, [q.shape[0] for q in Qs], Rs, survivor_capacity=64 * M + (1 << 20),
+                             nnz_capacity=64 * M + (1 << 20))
+        for t, q in enumerate(Qs):
+            plan.queries(t).copy_(q)
+        return plan
+
+    def step():
+        idx = snn.build_batch(Xs)
+        plan = make_plan(idx)
+        plan.run()
+        out = plan.result(copy=False)
+        return idx, plan, out
+
+    def per_set():
+        return [snn.Index(x).query(q, r) for x, q, r in zip(Xs, Qs, Rs)]
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            del r
+        return float(np.mean(ts))
+
+    for _ in range(args.warmup):
+        step()
+        per_set()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    l0 = snn.launch_count()
+    ms_step = timed(step, args.steps)
+    launches = snn.launch_count() - l0
+    ms_loop = timed(per_set, max(3, min(args.steps, 5)))
+    # query phase alone on persistent indices: tuned plan, graph replays
+    idx = snn.build_batch(Xs)
+    plan = make_plan(idx)
+    cpi, ctas, _ = plan.tune()
+    plan.launch_graph()
+    plan.result(copy=False)
+    torch.cuda.synchronize()
+
+    def graph_query():
+        plan.launch_graph()
+        return plan.result(copy=False)
+    ms_graph = timed(graph_query, max(3, args.steps))
+    pidx = [snn.Index(x) for x in Xs]
+
+    def loop_query():
+        return [ix.query(q, r) for ix, q, r in zip(pidx, Qs, Rs)]
+    ms_loop_query = timed(loop_query, max(3, min(args.steps, 5)))
+    clk = clocks.stop()
+    got = plan.result()
+    line = {
+        "metric": "ragged batch exact radius queries/s (batched index build + one batched query)",
+        "value": M / (ms_step / 1e3), "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "ragged_batch", "sets": len(sets), "points": N, "queries": M,
+                   "precision": "fp32", "parallelism": "replicas1",
+                   "l2": "flushed between steps (256 MiB write)"},
+        "per_set_calls": {"ms_per_step": ms_loop, "value": M / (ms_loop / 1e3)},
+        "query_phase": {"graph_ms": ms_graph, "graph_queries_per_s": M / (ms_graph / 1e3),
+                        "per_set_calls_ms": ms_loop_query,
+                        "per_set_calls_queries_per_s": M / (ms_loop_query / 1e3),
+                        "tuned": {"chunks_per_item": cpi, "ctas_per_sm": ctas}},
+        "clocks": clk, "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
+    }
+    if args.cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_ragged(sets, got, budget_s=args.ref_budget)
+    print(json.dumps(line), flush=True)
+
+
+def cpu_oracle_ragged(sets, got, budget_s=15.0, seed=11):
+    """Times the FP64 brute-force oracle on a random sample of the batch's
+    sets (all their queries) and compares those sets' GPU results with it."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    done_q, t_used, mism, pairs, nsets = 0, 0.0, 0, 0, 0
+    for t in rng.permutation(len(sets)):
+        if t_used >= budget_s:
+            break
+        t0 = time.perf_counter()
+        ref = oracle.brute_radius(sets[t].P, sets[t].Q, sets[t].R)
+        t_used += time.perf_counter() - t0
+        done_q += sets[t].Q.shape[0]
+        nsets += 1
+        g = got[t]
+        ok = (np.array_equal(g.offsets.cpu().numpy(), ref.offsets)
+              and np.array_equal(g.indices.cpu().numpy(), ref.ids)
+              and np.array_equal(g.dist2.cpu().numpy().view(np.uint32), ref.dist2.view(np.uint32)))
+        mism += 0 if ok else 1
+        pairs += len(ref.ids)
+    return {"value": done_q / max(t_used, 1e-9), "unit": "queries/s", "cores": oracle.oracle_threads(),
+            "kind": "oracle",
+            "sample": f"all queries of {nsets} random sets of the {len(sets)} (FP64 brute force, "
+                      f"{t_used:.1f} s)",
+            "parity": {"sets": nsets, "pairs": int(pairs), "sets_with_different_results": int(mism)}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -362,6 +487,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "ragged_batch":
+        run_ragged(args)
     else:
         run_ours(args)
 

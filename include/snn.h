@@ -117,6 +117,23 @@ typedef struct {
 snn_status snn_index_build(const float *X, int64_t n, int32_t d, int64_t ld,
                            void *stream, snn_index **out);
 
+/* Algorithm 1 for nsets independent sets at once (many small problems of
+ * uneven n and d): one launch per step over every set and one sort of all
+ * scores by the composite key (set, score); the result is nsets ordinary
+ * indices (each freed with snn_index_free; their arrays are slices of shared
+ * blocks released with the last one).  The scores may differ from a
+ * per-set snn_index_build in the last bits (partial sums are grouped
+ * differently); every query result is exact either way.
+ *  X, n, d, ld  host arrays of nsets entries; X[t] device, n[t] x d[t] FP32,
+ *               row stride ld[t].  1 <= d[t] <= 64, n[t] >= 1, total points
+ *               < 2^31.
+ *  out          host array of nsets index pointers (all NULL on error).
+ * Errors: SNN_EINVAL for invalid sizes or NaN/Inf in any set; SNN_ENOTSUP
+ * when a centred norm exceeds 1e18.  Synchronises `stream` once. */
+snn_status snn_index_build_batch(int32_t nsets, const float *const *X, const int64_t *n,
+                                 const int32_t *d, const int64_t *ld, void *stream,
+                                 snn_index **out);
+
 /* Algorithm 2 (Section 3.2) for m queries at once (Section 4: one gemm over
  * the union of candidate ranges of a tile of queries sorted by score).
  *  Q      device, m x d FP32 row-major, stride ldq; NULL means the self-join:
@@ -161,6 +178,55 @@ snn_status snn_query_radius_batch(int32_t nsets, const snn_index *const *idx,
 snn_status snn_dbscan(const float *X, int64_t n, int32_t d, int64_t ld, double eps,
                       int32_t min_pts, snn_precision prec, void *stream,
                       int32_t *labels, uint8_t *is_core);
+
+/* Plan of a batched query (Algorithm 2 for nsets independent problems; the
+ * paper has no counterpart) whose runs are pure stream-ordered device work:
+ * every size is fixed at creation (queries per set, survivor and neighbour
+ * capacities), so a run never synchronises and can be captured into a CUDA
+ * graph and replayed with new query values.  One persistent scoring launch
+ * covers every (set, query tile, band chunk group) item of the batch through a
+ * device work counter; scoring is FP32 (exact results for any precision).
+ *  idx, m, R  host arrays of nsets entries: m[t] queries for set t (written
+ *             into the plan's buffer, snn_batch_plan_queries) or m[t] < 0 for
+ *             the self-join of idx[t].  The indices must outlive the plan.
+ *  survivor_capacity, nnz_capacity  sizes of the survivor list and of the
+ *             result (all sets together); a run that needs more reports
+ *             SNN_EOVERFLOW from snn_batch_plan_result with the sizes needed.
+ * Synchronises `stream` once (setup). */
+typedef struct snn_batch_plan snn_batch_plan;
+snn_status snn_batch_plan_create(int32_t nsets, const snn_index *const *idx, const int64_t *m,
+                                 const double *R, snn_precision prec, int64_t survivor_capacity,
+                                 int64_t nnz_capacity, void *stream, snn_batch_plan **out);
+
+/* Device buffer of set t's queries (m[t] x d FP32 rows, stride d), read by
+ * every run; NULL for a self-join set or an invalid t. */
+float *snn_batch_plan_queries(snn_batch_plan *plan, int32_t set);
+
+/* Enqueues one run on `stream` (no synchronisation). */
+snn_status snn_batch_plan_run(snn_batch_plan *plan, void *stream);
+
+/* One run as a CUDA graph launch: the run is captured into a graph on the
+ * first call (after any snn_batch_plan_tune) and the graph replayed. */
+snn_status snn_batch_plan_launch_graph(snn_batch_plan *plan, void *stream);
+
+/* Synchronises `stream` and returns the last run's result: out[t] views the
+ * plan's own arrays (valid until the next run or snn_batch_plan_free; do not
+ * pass them to snn_free).  need_survivors / need_nnz (nullable) receive the
+ * sizes the run needed.  Errors: SNN_EOVERFLOW (a capacity was too small),
+ * SNN_EINVAL (NaN/Inf queries), SNN_ENOTSUP (a query norm beyond 1e18, or a
+ * row longer than 4096 neighbours: use snn_query_radius_batch). */
+snn_status snn_batch_plan_result(snn_batch_plan *plan, void *stream, snn_csr *out,
+                                 int64_t *need_survivors, int64_t *need_nnz);
+
+/* Autotuner: runs the plan on its current queries with every work
+ * granularity (band chunks per scoring item: 4, 8, 16, 32) and scoring grid
+ * (1 or 2 CTAs per SM), keeps the fastest and reports it (nullable outputs).
+ * Synchronises `stream`; drops a previously captured graph. */
+snn_status snn_batch_plan_tune(snn_batch_plan *plan, void *stream, int32_t *chunks_per_item,
+                               int32_t *ctas_per_sm, float *ms);
+
+/* Releases the plan (stream-ordered on `stream`; NULL is a no-op). */
+void snn_batch_plan_free(snn_batch_plan *plan, void *stream);
 
 /* Read-only view of an index's device arrays (for inspection and tests).
  * All pointers are device memory owned by the index and valid until

@@ -123,19 +123,22 @@ __global__ void k_b_consts(const SetDesc *__restrict__ sets, const int32_t *__re
     thrA[g] = __double2float_ru(a + 4.0 * kU64 * (fabs(a) + 0.5 * r * r + hy));
 }
 
+// (FP32 searches: for a float a, a < x <=> a < ru(x), a <= x <=> a <= rd(x))
 __device__ __forceinline__ int64_t lb_ge(const float *__restrict__ a, int64_t n, double x) {
+    const float xf = __double2float_ru(x);
     int64_t lo = 0, hi = n;
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
-        if ((double)a[mid] < x) lo = mid + 1; else hi = mid;
+        if (a[mid] < xf) lo = mid + 1; else hi = mid;
     }
     return lo;
 }
 __device__ __forceinline__ int64_t ub_gt(const float *__restrict__ a, int64_t n, double x) {
+    const float xf = __double2float_rd(x);
     int64_t lo = 0, hi = n;
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
-        if ((double)a[mid] <= x) lo = mid + 1; else hi = mid;
+        if (a[mid] <= xf) lo = mid + 1; else hi = mid;
     }
     return lo;
 }
@@ -143,7 +146,7 @@ __device__ __forceinline__ int64_t ub_gt(const float *__restrict__ a, int64_t n,
 // Band of every global tile (as k_tile_band, in the tile's own set).
 __global__ void k_b_band(const SetDesc *__restrict__ sets, const int32_t *__restrict__ tile_set,
                          int64_t ntiles, int64_t *__restrict__ tile_lo, int64_t *__restrict__ tile_hi,
-                         int64_t *__restrict__ items) {
+                         int64_t *__restrict__ items, int cpi) {
     const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (t >= ntiles) return;
     const SetDesc &sd = sets[tile_set[t]];
@@ -157,7 +160,7 @@ __global__ void k_b_band(const SetDesc *__restrict__ sets, const int32_t *__rest
     const int64_t hi = max(lo, ub_gt(sd.x_alpha, sd.n, hi_x));
     tile_lo[t] = lo;
     tile_hi[t] = hi;
-    items[t] = cdiv(cdiv(hi - lo, kBR), kChunksPerItem);
+    items[t] = cdiv(cdiv(hi - lo, kBR), int64_t(cpi));
 }
 
 __device__ __forceinline__ void two_sum_b(float a, float b, float &s, float &e) {
@@ -170,12 +173,31 @@ __device__ __forceinline__ void two_sum_b(float a, float b, float &s, float &e) 
 // Exact decision of every survivor (same arithmetic as k_decide_*), with the
 // set looked up from the global query number.  rec_pos[s] / rec_pos[N + s]:
 // slot of the pair in its (global) row / in the mirrored row, or -1.
+__device__ __forceinline__ void b_decide_one(int64_t s, int64_t cap, const uint2 *__restrict__ surv,
+                                             const SetDesc *__restrict__ sets,
+                                             const int32_t *__restrict__ qset,
+                                             float *__restrict__ rec_d2,
+                                             int32_t *__restrict__ rec_pos,
+                                             int32_t *__restrict__ counts);
+
+// Survivors min(*count, cap), grid-stride (the count is read on the device);
+// rec_pos[cap + s] is the mirrored slot.
 __global__ void __launch_bounds__(256)
-k_b_decide(const uint2 *__restrict__ surv, int64_t nsurv, const SetDesc *__restrict__ sets,
-           const int32_t *__restrict__ qset, float *__restrict__ rec_d2,
-           int32_t *__restrict__ rec_pos, int32_t *__restrict__ counts) {
-    const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (s >= nsurv) return;
+k_b_decide(const uint2 *__restrict__ surv, const unsigned long long *__restrict__ count, int64_t cap,
+           const SetDesc *__restrict__ sets, const int32_t *__restrict__ qset,
+           float *__restrict__ rec_d2, int32_t *__restrict__ rec_pos, int32_t *__restrict__ counts) {
+    const int64_t nsurv = min((int64_t)*count, cap);
+    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < nsurv;
+         s += int64_t(gridDim.x) * blockDim.x)
+        b_decide_one(s, cap, surv, sets, qset, rec_d2, rec_pos, counts);
+}
+
+__device__ __forceinline__ void b_decide_one(int64_t s, int64_t cap, const uint2 *__restrict__ surv,
+                                             const SetDesc *__restrict__ sets,
+                                             const int32_t *__restrict__ qset,
+                                             float *__restrict__ rec_d2,
+                                             int32_t *__restrict__ rec_pos,
+                                             int32_t *__restrict__ counts) {
     const uint2 e = surv[s];
     const SetDesc &sd = sets[qset[e.x]];
     const int64_t ql = int64_t(e.x) - sd.q_glob;
@@ -228,15 +250,38 @@ k_b_decide(const uint2 *__restrict__ surv, int64_t nsurv, const SetDesc *__restr
     }
     rec_d2[s] = d2;
     rec_pos[s] = p0;
-    rec_pos[nsurv + s] = p1;
+    rec_pos[cap + s] = p1;
 }
 
-__global__ void k_b_scatter(const uint2 *__restrict__ surv, int64_t nsurv,
-                            const SetDesc *__restrict__ sets, const int32_t *__restrict__ qset,
-                            const float *__restrict__ rec_d2, const int32_t *__restrict__ rec_pos,
-                            const int64_t *__restrict__ offsets, uint64_t *__restrict__ tmp) {
-    const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (s >= nsurv) return;
+__device__ __forceinline__ void b_scatter_one(int64_t s, int64_t cap, const uint2 *__restrict__ surv,
+                                              const SetDesc *__restrict__ sets,
+                                              const int32_t *__restrict__ qset,
+                                              const float *__restrict__ rec_d2,
+                                              const int32_t *__restrict__ rec_pos,
+                                              const int64_t *__restrict__ offsets,
+                                              uint64_t *__restrict__ tmp);
+
+// Survivors min(*count, cap), grid-stride; nothing when *skip (a plan whose
+// capacities were exceeded) is set.
+__global__ void k_b_scatter(const uint2 *__restrict__ surv, const unsigned long long *__restrict__ count,
+                            int64_t cap, const SetDesc *__restrict__ sets,
+                            const int32_t *__restrict__ qset, const float *__restrict__ rec_d2,
+                            const int32_t *__restrict__ rec_pos, const int64_t *__restrict__ offsets,
+                            uint64_t *__restrict__ tmp, const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    const int64_t nsurv = min((int64_t)*count, cap);
+    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < nsurv;
+         s += int64_t(gridDim.x) * blockDim.x)
+        b_scatter_one(s, cap, surv, sets, qset, rec_d2, rec_pos, offsets, tmp);
+}
+
+__device__ __forceinline__ void b_scatter_one(int64_t s, int64_t cap, const uint2 *__restrict__ surv,
+                                              const SetDesc *__restrict__ sets,
+                                              const int32_t *__restrict__ qset,
+                                              const float *__restrict__ rec_d2,
+                                              const int32_t *__restrict__ rec_pos,
+                                              const int64_t *__restrict__ offsets,
+                                              uint64_t *__restrict__ tmp) {
     const int32_t p0 = rec_pos[s];
     if (p0 < 0) return;
     const uint2 e = surv[s];
@@ -245,7 +290,7 @@ __global__ void k_b_scatter(const uint2 *__restrict__ surv, int64_t nsurv,
     const int32_t qrow = sd.q_order[ql], col = sd.x_order[e.y];
     const uint64_t vb = __float_as_uint(rec_d2[s]);
     tmp[offsets[sd.q_glob + qrow] + p0] = (uint64_t(uint32_t(col)) << 32) | vb;
-    const int32_t p1 = rec_pos[nsurv + s];
+    const int32_t p1 = rec_pos[cap + s];
     if (p1 >= 0) tmp[offsets[sd.q_glob + col] + p1] = (uint64_t(uint32_t(qrow)) << 32) | vb;
 }
 
@@ -452,7 +497,8 @@ snn_status batch_query(int32_t nsets, const snn_index *const *idx, const float *
         SNN_LAUNCH(k_b_tileset, unsigned(cdiv(ntiles, 256)), 256, 0, s)(d_tile0, nsets, ntiles,
                                                                          tile_set);
         SNN_LAUNCH(k_b_band, unsigned(cdiv(ntiles, 128)), 128, 0, s)(d_sets, tile_set, ntiles,
-                                                                     tile_lo, tile_hi, items);
+                                                                     tile_lo, tile_hi, items,
+                                                                     kChunksPerItem);
         SNN_LAUNCH_CHECK();
     }
     SNN_TRY(scan_exclusive<int64_t>(items, item_off, ntiles, s));
@@ -480,6 +526,7 @@ snn_status batch_query(int32_t nsets, const snn_index *const *idx, const float *
     ba.item_off = item_off;
     ba.item_tile = item_tile;
     ba.ntiles = int(ntiles);
+    ba.cpi = kChunksPerItem;
     ba.count = ctr;
     ba.work = ctr + 1;
     unsigned long long hctr[2] = {0, 0};
@@ -507,14 +554,14 @@ snn_status batch_query(int32_t nsets, const snn_index *const *idx, const float *
     float *rec_d2;
     int32_t *rec_pos, *counts;
     int64_t *counts64, *goff;
-    SNN_TRY(scr.alloc(&rec_d2, nsurv));
-    SNN_TRY(scr.alloc(&rec_pos, 2 * nsurv));
+    SNN_TRY(scr.alloc(&rec_d2, std::max<int64_t>(nsurv, 1)));
+    SNN_TRY(scr.alloc(&rec_pos, 2 * std::max<int64_t>(nsurv, 1)));
     SNN_TRY(scr.alloc(&counts, M));
     SNN_TRY(scr.alloc(&counts64, M));
     SNN_TRY(scr.alloc(&goff, M + 1));
     SNN_CUDA(cudaMemsetAsync(counts, 0, std::max<int64_t>(M, 1) * sizeof(int32_t), s));
     if (nsurv > 0) {
-        SNN_LAUNCH(k_b_decide, unsigned(cdiv(nsurv, 256)), 256, 0, s)(surv, nsurv, d_sets, qset,
+        SNN_LAUNCH(k_b_decide, unsigned(cdiv(nsurv, 256)), 256, 0, s)(surv, ctr, nsurv, d_sets, qset,
                                                                       rec_d2, rec_pos, counts);
         SNN_LAUNCH_CHECK();
     }
@@ -585,7 +632,7 @@ snn_status batch_query(int32_t nsets, const snn_index *const *idx, const float *
         uint64_t *tmp;
         if ((st = scr.alloc(&tmp, nnz)) != SNN_OK) return fail(st);
         SNN_LAUNCH(k_b_scatter, unsigned(cdiv(nsurv, 256)), 256, 0, s)(
-            surv, nsurv, d_sets, qset, rec_d2, rec_pos, goff, tmp);
+            surv, ctr, nsurv, d_sets, qset, rec_d2, rec_pos, goff, tmp, nullptr);
         // per-row ascending ids over the global CSR (rows of every set)
         int32_t *lists, *big_list;
         int64_t *big_len, *toff;
@@ -664,6 +711,541 @@ snn_status batch_query(int32_t nsets, const snn_index *const *idx, const float *
         return fail(st);
     }
     return SNN_OK;
+}
+
+// ---------------------------------------------------------- batch plan
+// A batched query with every size fixed in advance (queries per set, the
+// survivor and neighbour capacities), so that one run is a pure sequence of
+// stream-ordered device work: no host synchronisation, no host-dependent
+// sizes.  It can be captured into a CUDA graph and replayed with new query
+// values written into the plan's query buffers.  Capacities that turn out too
+// small, NaN/Inf queries and rows longer than 4096 neighbours are reported in
+// a device status word that snn_batch_plan_result reads.
+
+// Status of a run, decided on the device after the row classification: when
+// a capacity is exceeded (or a row needs the long-row radix path) the CSR
+// build is skipped (the scatter checks *skip, the sorts see empty classes).
+struct PlanStatus {
+    unsigned long long surv;   // survivors counted
+    long long nnz;             // neighbour entries counted
+    int bad;                   // NaN/Inf in a query set
+    int big;                   // rows longer than 4096 entries
+    int skip;                  // the CSR build was skipped
+    float qnorm;               // largest centred query norm
+};
+
+__global__ void k_plan_guard(const unsigned long long *__restrict__ ctr,
+                             const int64_t *__restrict__ nnz, unsigned *__restrict__ cls,
+                             const int *__restrict__ bad, const float *__restrict__ qnmax,
+                             int64_t surv_cap, int64_t nnz_cap, PlanStatus *__restrict__ st) {
+    const unsigned long long sv = ctr[0];
+    const long long nz = *nnz;
+    const int big = cls[4] > 0;
+    const int skip = sv > (unsigned long long)surv_cap || nz > nnz_cap || big || *bad ||
+                     !(*qnmax <= (float)kMaxCentredNorm);
+    st->surv = sv;
+    st->nnz = nz;
+    st->bad = *bad;
+    st->big = big;
+    st->skip = skip;
+    st->qnorm = *qnmax;
+    if (skip)
+        for (int k = 0; k < 8; ++k) cls[k] = 0;
+}
+
+// set_nnz[t] = first global neighbour entry of set t (t <= nsets).
+__global__ void k_plan_set_nnz(const int64_t *__restrict__ goff, const int64_t *__restrict__ qglob,
+                               int nsets, int64_t *__restrict__ set_nnz) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t <= nsets) set_nnz[t] = goff[qglob[t]];
+}
+
+}  // namespace snn
+
+struct snn_batch_plan {
+    int32_t nsets = 0;
+    int device = 0;
+    snn_precision prec = SNN_PREC_FP32;
+    std::vector<snn::SetDesc> sd;
+    std::vector<snn::OosDesc> od;
+    std::vector<int64_t> qglob, tile0, ooff, off_pos, qbuf_off;
+    std::vector<int> oos_of;
+    int64_t M = 0, ntiles = 0, Moos = 0, oos_elems = 0, off_words = 0, max_items = 0;
+    int noos = 0;
+    int64_t surv_cap = 0, nnz_cap = 0;
+    int cpi = snn::kChunksPerItem;   // tuned: band chunks per scoring item
+    int ctas_per_sm = 2;             // tuned: persistent scoring grid
+    std::vector<void *> blocks;      // pool blocks owned by the plan
+    // device arrays
+    float *qbuf = nullptr;
+    snn::OosDesc *d_od = nullptr;
+    int64_t *d_ooff = nullptr;
+    float *oeps = nullptr, *q_alpha = nullptr, *q_raw = nullptr, *q_xc = nullptr, *q_hx = nullptr,
+          *q_nrm = nullptr, *qnmax = nullptr, *thrA = nullptr, *rec_d2 = nullptr, *gd2 = nullptr;
+    int32_t *q_order = nullptr, *qset = nullptr, *tile_set = nullptr, *item_tile = nullptr,
+            *rec_pos = nullptr, *counts = nullptr, *lists = nullptr, *big_list = nullptr,
+            *gidx = nullptr;
+    uint64_t *keys = nullptr, *keys_alt = nullptr, *tmp = nullptr;
+    uint32_t *vals = nullptr, *vals_alt = nullptr;
+    int *bad = nullptr;
+    snn::SetDesc *d_sets = nullptr;
+    int64_t *d_qglob = nullptr, *d_tile0 = nullptr, *tile_lo = nullptr, *tile_hi = nullptr,
+            *items = nullptr, *item_off = nullptr, *counts64 = nullptr, *goff = nullptr,
+            *big_len = nullptr, *toff = nullptr, *out_off = nullptr, *d_offpos = nullptr,
+            *set_nnz = nullptr;
+    unsigned long long *ctr = nullptr;
+    uint2 *surv = nullptr;
+    unsigned *cls = nullptr;
+    snn::PlanStatus *status = nullptr;
+    // graph of one run
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long graph_launches = 0;   // kernels in the graph
+};
+
+namespace snn {
+
+void note_launches(unsigned long long k);
+unsigned long long launch_count_now();
+
+namespace {
+
+template <typename T>
+snn_status plan_alloc(snn_batch_plan *p, T **ptr, int64_t count, cudaStream_t s) {
+    void *q = nullptr;
+    const size_t bytes = (std::max<size_t>(size_t(count) * sizeof(T), 16) + 255) & ~size_t(255);
+    if (cudaMallocAsync(&q, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("plan allocation of %zu bytes failed", bytes);
+        return SNN_ENOMEM;
+    }
+    p->blocks.push_back(q);
+    *ptr = static_cast<T *>(q);
+    return SNN_OK;
+}
+
+// One run, enqueued on s: no synchronisation, every size from the plan.
+snn_status plan_enqueue(snn_batch_plan *p, cudaStream_t s) {
+    const int nsets = p->nsets;
+    const int64_t M = p->M, ntiles = p->ntiles, Moos = p->Moos;
+    SNN_CUDA(cudaMemsetAsync(p->bad, 0, sizeof(int), s));
+    SNN_CUDA(cudaMemsetAsync(p->qnmax, 0, sizeof(float), s));
+    if (p->noos > 0) {
+        SNN_CUDA(cudaMemsetAsync(p->oeps, 0, p->noos * sizeof(float), s));
+        SNN_LAUNCH(k_b_project, unsigned(cdiv(Moos, 256)), 256, 0, s)(p->d_od, p->d_ooff, p->noos, Moos,
+                                                                      p->keys, p->vals, p->oeps, p->bad);
+        SNN_LAUNCH_CHECK();
+        int bits = 32;
+        while ((int64_t(1) << (bits - 32)) < p->noos) ++bits;
+        SNN_TRY(radix_sort_pairs<uint64_t>(p->keys, p->vals, p->keys_alt, p->vals_alt, Moos, bits, s));
+        SNN_LAUNCH(k_b_gather, unsigned(cdiv(Moos, 256)), 256, 0, s)(
+            p->d_od, p->d_ooff, p->noos, Moos, p->keys, p->vals, p->q_alpha, p->q_order, p->q_raw,
+            p->q_xc, p->q_hx, p->q_nrm);
+        SNN_LAUNCH(k_max_nonneg, std::min<unsigned>(unsigned(cdiv(Moos, 256)), 1024u), 256, 0, s)(
+            p->q_nrm, Moos, p->qnmax);
+        SNN_LAUNCH_CHECK();
+    }
+    SNN_CUDA(cudaMemsetAsync(p->ctr, 0, 4 * sizeof(unsigned long long), s));
+    if (M > 0) {
+        SNN_LAUNCH(k_b_qset, unsigned(cdiv(M, 256)), 256, 0, s)(p->d_qglob, nsets, M, p->qset);
+        SNN_LAUNCH(k_b_consts, unsigned(cdiv(M, 256)), 256, 0, s)(p->d_sets, p->qset, M, p->thrA);
+        SNN_LAUNCH(k_b_tileset, unsigned(cdiv(ntiles, 256)), 256, 0, s)(p->d_tile0, nsets, ntiles,
+                                                                         p->tile_set);
+        SNN_LAUNCH(k_b_band, unsigned(cdiv(ntiles, 128)), 128, 0, s)(p->d_sets, p->tile_set, ntiles,
+                                                                     p->tile_lo, p->tile_hi, p->items,
+                                                                     p->cpi);
+        SNN_LAUNCH_CHECK();
+        SNN_TRY(scan_exclusive<int64_t>(p->items, p->item_off, ntiles, s));
+        SNN_LAUNCH(k_item_tiles, unsigned(cdiv(ntiles, 128)), 128, 0, s)(p->item_off, int(ntiles),
+                                                                          p->item_tile);
+        BatchScoreArgs ba;
+        ba.sets = p->d_sets;
+        ba.tile_set = p->tile_set;
+        ba.thrA = p->thrA;
+        ba.tile_lo = p->tile_lo;
+        ba.tile_hi = p->tile_hi;
+        ba.item_off = p->item_off;
+        ba.item_tile = p->item_tile;
+        ba.ntiles = int(ntiles);
+        ba.cpi = p->cpi;
+        ba.surv = p->surv;
+        ba.cap = p->surv_cap;
+        ba.count = p->ctr;
+        ba.work = p->ctr + 1;
+        SNN_LAUNCH(k_score_fp32_batch, device_sm_count() * p->ctas_per_sm, 256, 0, s)(ba);
+        SNN_LAUNCH_CHECK();
+    }
+    SNN_CUDA(cudaMemsetAsync(p->counts, 0, std::max<int64_t>(M, 1) * sizeof(int32_t), s));
+    SNN_LAUNCH(k_b_decide, unsigned(4 * device_sm_count()), 256, 0, s)(
+        p->surv, p->ctr, p->surv_cap, p->d_sets, p->qset, p->rec_d2, p->rec_pos, p->counts);
+    if (M > 0)
+        SNN_LAUNCH(k_counts_to_i64, unsigned(cdiv(M, 256)), 256, 0, s)(p->counts, M, p->counts64);
+    SNN_LAUNCH_CHECK();
+    SNN_TRY(scan_exclusive<int64_t>(p->counts64, p->goff, M, s));
+    SNN_CUDA(cudaMemsetAsync(p->cls, 0, 8 * sizeof(unsigned), s));
+    if (M > 0) {
+        SNN_CUDA(cudaMemsetAsync(p->big_len, 0, M * sizeof(int64_t), s));
+        SNN_LAUNCH(k_seg_classify, unsigned(cdiv(M, 256)), 256, 0, s)(p->goff, M, p->lists,
+                                                                      p->big_list, p->big_len, p->cls);
+    }
+    SNN_LAUNCH(k_plan_guard, 1, 1, 0, s)(p->ctr, p->goff + M, p->cls, p->bad, p->qnmax, p->surv_cap,
+                                         p->nnz_cap, p->status);
+    SNN_LAUNCH(k_b_scatter, unsigned(4 * device_sm_count()), 256, 0, s)(
+        p->surv, p->ctr, p->surv_cap, p->d_sets, p->qset, p->rec_d2, p->rec_pos, p->goff, p->tmp,
+        &p->status->skip);
+    SNN_LAUNCH_CHECK();
+    const unsigned wgrid = unsigned(std::min<int64_t>(cdiv(std::max<int64_t>(M, 1) * 32, 256), 16384));
+    SNN_LAUNCH(k_seg_sort_w1, wgrid, 256, 0, s)(p->lists, p->cls, p->goff, p->tmp, p->gidx, p->gd2);
+    SNN_LAUNCH(k_seg_sort_w2, wgrid, 256, 0, s)(p->lists + 5 * M, p->cls + 6, p->goff, p->tmp, p->gidx,
+                                                 p->gd2);
+    SNN_LAUNCH(k_seg_sort_w4, wgrid, 256, 0, s)(p->lists + M, p->cls + 1, p->goff, p->tmp, p->gidx,
+                                                 p->gd2);
+    SNN_LAUNCH(k_seg_sort_w8, wgrid, 256, 0, s)(p->lists + 4 * M, p->cls + 5, p->goff, p->tmp, p->gidx,
+                                                 p->gd2);
+    SNN_LAUNCH(k_seg_sort_w16, wgrid, 256, 0, s)(p->lists + 2 * M, p->cls + 2, p->goff, p->tmp,
+                                                  p->gidx, p->gd2);
+    SNN_LAUNCH(k_seg_sort_mid, unsigned(std::min<int64_t>(std::max<int64_t>(M, 1), 4096)), 256, 0, s)(
+        p->lists + 3 * M, p->cls + 3, p->goff, p->tmp, p->gidx, p->gd2);
+    if (M > 0)
+        SNN_LAUNCH(k_b_offsets, unsigned(cdiv(M, 256)), 256, 0, s)(p->goff, p->d_qglob, nsets, M,
+                                                                   p->out_off, p->d_offpos);
+    SNN_LAUNCH(k_b_offsets_end, unsigned(cdiv(nsets, 128)), 128, 0, s)(p->goff, p->d_qglob, nsets,
+                                                                       p->out_off, p->d_offpos);
+    SNN_LAUNCH(k_plan_set_nnz, unsigned(cdiv(nsets + 1, 128)), 128, 0, s)(p->goff, p->d_qglob, nsets,
+                                                                          p->set_nnz);
+    SNN_LAUNCH_CHECK();
+    return SNN_OK;
+}
+
+}  // namespace
+
+void plan_release(snn_batch_plan *p, cudaStream_t s) {
+    if (!p) return;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    for (void *b : p->blocks) cudaFreeAsync(b, s);
+    delete p;
+}
+
+snn_status plan_create(int32_t nsets, const snn_index *const *idx, const int64_t *m_in,
+                       const double *R_in, snn_precision prec, int64_t surv_cap, int64_t nnz_cap,
+                       cudaStream_t s, snn_batch_plan **out) {
+    *out = nullptr;
+    snn_batch_plan *p = new (std::nothrow) snn_batch_plan();
+    if (!p) {
+        set_error("host allocation failed");
+        return SNN_ENOMEM;
+    }
+    auto fail = [&](snn_status st) {
+        cudaStreamSynchronize(s);
+        plan_release(p, s);
+        return st;
+    };
+    cudaGetDevice(&p->device);
+    p->nsets = nsets;
+    p->prec = prec;
+    p->sd.resize(nsets);
+    p->qglob.assign(nsets + 1, 0);
+    p->tile0.assign(nsets + 1, 0);
+    p->ooff.assign(1, 0);
+    p->oos_of.assign(nsets, -1);
+    p->qbuf_off.assign(nsets, -1);
+    int64_t qelems = 0;
+    for (int32_t t = 0; t < nsets; ++t) {
+        const snn_index *ix = idx[t];
+        if (!ix) { set_error("set %d: index is NULL", t); return fail(SNN_EINVAL); }
+        if (!(R_in[t] >= 0.0) || !std::isfinite(R_in[t])) {
+            set_error("set %d: R must be finite and >= 0", t);
+            return fail(SNN_EINVAL);
+        }
+        const bool self = m_in[t] < 0;
+        const int64_t m = self ? ix->n : m_in[t];
+        if (m >= (int64_t(1) << 31)) { set_error("set %d: m must be < 2^31", t); return fail(SNN_EINVAL); }
+        SetDesc &d = p->sd[t];
+        std::memset(&d, 0, sizeof(d));
+        d.m = m;
+        d.n = ix->n;
+        d.d = ix->d;
+        d.dp = ix->dp;
+        d.sym = self ? 1 : 0;
+        d.c1 = (float)((2.0 * ix->d + 4.0) * (double)kU32 * 1.05);
+        d.q_glob = p->qglob[t];
+        d.tile0 = p->tile0[t];
+        d.R2 = R_in[t] * R_in[t];
+        d.dc = decide_consts(d.d, d.R2);
+        d.Rx = R_in[t] * (1.0 + (ix->d + 8) * 0x1p-52);
+        d.Wbase = d.Rx * (1.0 + (ix->d + 4) * 0x1p-52) * (1.0 + 0x1p-30);
+        d.e_data = 1.0001 * (double)kU32 * (double)ix->nrm_max;
+        d.x_alpha = ix->alpha;
+        d.x_raw = ix->praw;
+        d.x_xc = ix->xc;
+        d.x_hx = ix->hx;
+        d.x_nrm = ix->nrm;
+        d.x_order = ix->order;
+        d.eps_d = ix->dconst;
+        if (self) {
+            d.q_alpha = ix->alpha;
+            d.q_raw = ix->praw;
+            d.q_xc = ix->xc;
+            d.q_hx = ix->hx;
+            d.q_nrm = ix->nrm;
+            d.q_order = ix->order;
+            d.eps_q = ix->dconst;
+        } else if (m > 0) {
+            OosDesc o;
+            o.Q = nullptr;   // set below (query buffer)
+            o.ldq = ix->d;
+            o.cvec = ix->mu32;
+            o.v32 = ix->v32;
+            o.d = ix->d;
+            o.dp = ix->dp;
+            o.set = t;
+            o.elem_off = p->oos_elems;
+            p->oos_of[t] = int(p->od.size());
+            p->qbuf_off[t] = qelems;
+            qelems += (m * ix->d + 63) & ~int64_t(63);
+            p->od.push_back(o);
+            p->ooff.push_back(p->ooff.back() + m);
+            p->oos_elems += m * ix->dp;
+        }
+        p->qglob[t + 1] = p->qglob[t] + m;
+        p->tile0[t + 1] = p->tile0[t] + cdiv(m, kBQ);
+    }
+    p->M = p->qglob[nsets];
+    p->ntiles = p->tile0[nsets];
+    p->noos = int(p->od.size());
+    p->Moos = p->ooff.back();
+    const int64_t M = p->M;
+    p->surv_cap = std::max<int64_t>(surv_cap, 1024);
+    p->nnz_cap = std::max<int64_t>(nnz_cap, 1024);
+    // worst-case item count of the smallest granularity the tuner may pick
+    for (int32_t t = 0; t < nsets; ++t)
+        p->max_items += cdiv(p->sd[t].m, kBQ) * (cdiv(p->sd[t].n, int64_t(kBR) * 4) + 1);
+    // per-set output offsets: 256-byte aligned slices
+    p->off_pos.resize(nsets);
+    for (int32_t t = 0; t < nsets; ++t) {
+        p->off_pos[t] = p->off_words;
+        p->off_words += (p->sd[t].m + 1 + 31) & ~int64_t(31);
+    }
+    // ---------------------------------------------------- device memory
+#define PTRY(expr)                               \
+    do {                                         \
+        snn_status _st = (expr);                 \
+        if (_st != SNN_OK) return fail(_st);     \
+    } while (0)
+    PTRY(plan_alloc(p, &p->qbuf, qelems, s));
+    PTRY(plan_alloc(p, &p->bad, 1, s));
+    PTRY(plan_alloc(p, &p->qnmax, 1, s));
+    if (p->noos > 0) {
+        for (int32_t t = 0; t < nsets; ++t)
+            if (p->oos_of[t] >= 0) p->od[p->oos_of[t]].Q = p->qbuf + p->qbuf_off[t];
+        PTRY(plan_alloc(p, &p->d_od, p->noos, s));
+        PTRY(plan_alloc(p, &p->d_ooff, p->noos + 1, s));
+        PTRY(plan_alloc(p, &p->oeps, p->noos, s));
+        PTRY(plan_alloc(p, &p->keys, p->Moos, s));
+        PTRY(plan_alloc(p, &p->keys_alt, p->Moos, s));
+        PTRY(plan_alloc(p, &p->vals, p->Moos, s));
+        PTRY(plan_alloc(p, &p->vals_alt, p->Moos, s));
+        PTRY(plan_alloc(p, &p->q_alpha, p->Moos, s));
+        PTRY(plan_alloc(p, &p->q_order, p->Moos, s));
+        PTRY(plan_alloc(p, &p->q_hx, p->Moos, s));
+        PTRY(plan_alloc(p, &p->q_nrm, p->Moos, s));
+        PTRY(plan_alloc(p, &p->q_raw, p->oos_elems, s));
+        PTRY(plan_alloc(p, &p->q_xc, p->oos_elems, s));
+        for (int32_t t = 0; t < nsets; ++t) {
+            const int r = p->oos_of[t];
+            if (r < 0) continue;
+            SetDesc &d = p->sd[t];
+            d.q_alpha = p->q_alpha + p->ooff[r];
+            d.q_order = p->q_order + p->ooff[r];
+            d.q_hx = p->q_hx + p->ooff[r];
+            d.q_nrm = p->q_nrm + p->ooff[r];
+            d.q_raw = p->q_raw + p->od[r].elem_off;
+            d.q_xc = p->q_xc + p->od[r].elem_off;
+            d.eps_q = p->oeps + r;
+        }
+    }
+    PTRY(plan_alloc(p, &p->d_sets, nsets, s));
+    PTRY(plan_alloc(p, &p->d_qglob, nsets + 1, s));
+    PTRY(plan_alloc(p, &p->d_tile0, nsets + 1, s));
+    PTRY(plan_alloc(p, &p->qset, M, s));
+    PTRY(plan_alloc(p, &p->thrA, M, s));
+    PTRY(plan_alloc(p, &p->tile_set, p->ntiles, s));
+    PTRY(plan_alloc(p, &p->tile_lo, p->ntiles, s));
+    PTRY(plan_alloc(p, &p->tile_hi, p->ntiles, s));
+    PTRY(plan_alloc(p, &p->items, p->ntiles, s));
+    PTRY(plan_alloc(p, &p->item_off, p->ntiles + 1, s));
+    PTRY(plan_alloc(p, &p->item_tile, std::max<int64_t>(p->max_items, 1), s));
+    PTRY(plan_alloc(p, &p->ctr, 4, s));
+    PTRY(plan_alloc(p, &p->surv, p->surv_cap, s));
+    PTRY(plan_alloc(p, &p->rec_d2, p->surv_cap, s));
+    PTRY(plan_alloc(p, &p->rec_pos, 2 * p->surv_cap, s));
+    PTRY(plan_alloc(p, &p->counts, M, s));
+    PTRY(plan_alloc(p, &p->counts64, M, s));
+    PTRY(plan_alloc(p, &p->goff, M + 1, s));
+    PTRY(plan_alloc(p, &p->lists, 6 * std::max<int64_t>(M, 1), s));
+    PTRY(plan_alloc(p, &p->big_list, M, s));
+    PTRY(plan_alloc(p, &p->big_len, M, s));
+    PTRY(plan_alloc(p, &p->toff, M + 1, s));
+    PTRY(plan_alloc(p, &p->cls, 8, s));
+    PTRY(plan_alloc(p, &p->tmp, p->nnz_cap, s));
+    PTRY(plan_alloc(p, &p->out_off, p->off_words, s));
+    PTRY(plan_alloc(p, &p->gidx, p->nnz_cap, s));
+    PTRY(plan_alloc(p, &p->gd2, p->nnz_cap, s));
+    PTRY(plan_alloc(p, &p->d_offpos, nsets, s));
+    PTRY(plan_alloc(p, &p->set_nnz, nsets + 1, s));
+    PTRY(plan_alloc(p, &p->status, 1, s));
+#undef PTRY
+    if ((p->noos > 0 &&
+         (cudaMemcpyAsync(p->d_od, p->od.data(), p->noos * sizeof(OosDesc), cudaMemcpyHostToDevice,
+                          s) != cudaSuccess ||
+          cudaMemcpyAsync(p->d_ooff, p->ooff.data(), (p->noos + 1) * sizeof(int64_t),
+                          cudaMemcpyHostToDevice, s) != cudaSuccess)) ||
+        cudaMemcpyAsync(p->d_sets, p->sd.data(), nsets * sizeof(SetDesc), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(p->d_qglob, p->qglob.data(), (nsets + 1) * sizeof(int64_t),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(p->d_tile0, p->tile0.data(), (nsets + 1) * sizeof(int64_t),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(p->d_offpos, p->off_pos.data(), nsets * sizeof(int64_t),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(p->qbuf, 0, std::max<int64_t>(qelems, 1) * sizeof(float), s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("plan setup failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail(SNN_ECUDA);
+    }
+    *out = p;
+    return SNN_OK;
+}
+
+float *plan_queries(snn_batch_plan *p, int32_t t) {
+    if (!p || t < 0 || t >= p->nsets || p->qbuf_off[t] < 0) return nullptr;
+    return p->qbuf + p->qbuf_off[t];
+}
+
+snn_status plan_run(snn_batch_plan *p, cudaStream_t s) { return plan_enqueue(p, s); }
+
+// Captures one run into a CUDA graph on first use, then launches the graph.
+snn_status plan_launch_graph(snn_batch_plan *p, cudaStream_t s) {
+    if (!p->exec) {
+        cudaStream_t cs;
+        SNN_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        const unsigned long long l0 = launch_count_now();
+        snn_status st = SNN_OK;
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            set_error("stream capture could not start");
+            st = SNN_ECUDA;
+        } else {
+            st = plan_enqueue(p, cs);
+            cudaGraph_t g = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(cs, &g);
+            if (st == SNN_OK && e != cudaSuccess) {
+                set_error("stream capture failed: %s", cudaGetErrorString(e));
+                st = SNN_ECUDA;
+            }
+            if (st == SNN_OK && cudaGraphInstantiate(&p->exec, g, 0) != cudaSuccess) {
+                set_error("graph instantiation failed");
+                st = SNN_ECUDA;
+            }
+            p->graph = g;
+        }
+        cudaStreamDestroy(cs);
+        // the captured launches are counted when the graph runs, not here
+        p->graph_launches = launch_count_now() - l0;
+        note_launches(0ull - p->graph_launches);
+        if (st != SNN_OK) return st;
+    }
+    SNN_CUDA(cudaGraphLaunch(p->exec, s));
+    note_launches(p->graph_launches);
+    return SNN_OK;
+}
+
+// Synchronises s, reads the status and hands out per-set views.
+snn_status plan_result(snn_batch_plan *p, cudaStream_t s, snn_csr *out, int64_t *need_surv,
+                       int64_t *need_nnz) {
+    PlanStatus hs;
+    std::vector<int64_t> hn(p->nsets + 1);
+    if (cudaMemcpyAsync(&hs, p->status, sizeof(hs), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(hn.data(), p->set_nnz, (p->nsets + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                        s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("plan result read failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return SNN_ECUDA;
+    }
+    if (need_surv) *need_surv = (int64_t)hs.surv;
+    if (need_nnz) *need_nnz = hs.nnz;
+    if (hs.bad) { set_error("a query set contains NaN or Inf"); return SNN_EINVAL; }
+    if (!(hs.qnorm <= (float)kMaxCentredNorm)) {
+        set_error("a centred query norm of %g exceeds %g", (double)hs.qnorm, kMaxCentredNorm);
+        return SNN_ENOTSUP;
+    }
+    if ((int64_t)hs.surv > p->surv_cap || hs.nnz > p->nnz_cap) {
+        set_error("plan capacities exceeded: %llu survivors (capacity %lld), %lld neighbours "
+                  "(capacity %lld)", hs.surv, (long long)p->surv_cap, hs.nnz, (long long)p->nnz_cap);
+        return SNN_EOVERFLOW;
+    }
+    if (hs.big) {
+        set_error("a row holds more than 4096 neighbours (use snn_query_radius_batch)");
+        return SNN_ENOTSUP;
+    }
+    for (int32_t t = 0; t < p->nsets; ++t) {
+        const int64_t nz = hn[t + 1] - hn[t];
+        out[t].m = p->sd[t].m;
+        out[t].nnz = nz;
+        out[t].offsets = p->out_off + p->off_pos[t];
+        out[t].indices = nz > 0 ? p->gidx + hn[t] : nullptr;
+        out[t].dist2 = nz > 0 ? p->gd2 + hn[t] : nullptr;
+    }
+    return SNN_OK;
+}
+
+// Autotuner: times the run with each work granularity (band chunks per
+// scoring item) and scoring grid (CTAs per SM) on the plan's current query
+// values and keeps the fastest (any previously captured graph is dropped).
+snn_status plan_tune(snn_batch_plan *p, cudaStream_t s, int *best_cpi, int *best_ctas,
+                     float *best_ms) {
+    const int cpis[4] = {4, 8, 16, 32};
+    const int ctas[2] = {1, 2};
+    cudaEvent_t e0, e1;
+    SNN_CUDA(cudaEventCreate(&e0));
+    SNN_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bc = p->cpi, bt = p->ctas_per_sm;
+    snn_status st = SNN_OK;
+    for (int a = 0; a < 4 && st == SNN_OK; ++a)
+        for (int b = 0; b < 2 && st == SNN_OK; ++b) {
+            p->cpi = cpis[a];
+            p->ctas_per_sm = ctas[b];
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && st == SNN_OK; ++rep) {   // first run warms up
+                cudaEventRecord(e0, s);
+                st = plan_enqueue(p, s);
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) st = SNN_ECUDA;
+                cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (st == SNN_OK && ms < best) {
+                best = ms;
+                bc = cpis[a];
+                bt = ctas[b];
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->cpi = bc;
+    p->ctas_per_sm = bt;
+    if (p->exec) {
+        cudaGraphExecDestroy(p->exec);
+        p->exec = nullptr;
+    }
+    if (p->graph) {
+        cudaGraphDestroy(p->graph);
+        p->graph = nullptr;
+    }
+    if (best_cpi) *best_cpi = bc;
+    if (best_ctas) *best_ctas = bt;
+    if (best_ms) *best_ms = best;
+    return st;
 }
 
 }  // namespace snn

@@ -83,9 +83,23 @@ __global__ void k_mean_final(const double *__restrict__ part, int nb, int d, int
 constexpr int kGramStageRows = 64;
 
 template <int TG>
+__device__ __forceinline__ void gram_small_rows(const float *__restrict__ X, int d, int64_t ld,
+                                                const float *__restrict__ cvec, int64_t r0,
+                                                int64_t r1, float *__restrict__ out);
+
+template <int TG>
 __device__ __forceinline__ void gram_small(const float *__restrict__ X, int64_t n, int d,
                                            int64_t ld, const float *__restrict__ cvec,
                                            int64_t rows, float *__restrict__ part) {
+    const int64_t r0 = int64_t(blockIdx.x) * rows;
+    gram_small_rows<TG>(X, d, ld, cvec, r0, min(n, r0 + rows), part + int64_t(blockIdx.x) * d * d);
+}
+
+// Rows [r0, r1) of X (centred by cvec) into out = their d x d Gram matrix.
+template <int TG>
+__device__ __forceinline__ void gram_small_rows(const float *__restrict__ X, int d, int64_t ld,
+                                                const float *__restrict__ cvec, int64_t r0,
+                                                int64_t r1, float *__restrict__ out) {
     constexpr int TT = TG / 4;                  // threads per tile edge
     constexpr int RG = 256 / (TT * TT);         // row groups
     constexpr int LD = TG + 4;
@@ -93,8 +107,6 @@ __device__ __forceinline__ void gram_small(const float *__restrict__ X, int64_t 
     __shared__ float red[RG > 1 ? RG : 1][RG > 1 ? TG : 1][RG > 1 ? TG + 1 : 1];
     const int tt = threadIdx.x % (TT * TT), g = threadIdx.x / (TT * TT);
     const int ty = tt / TT, tx = tt % TT;
-    const int64_t r0 = int64_t(blockIdx.x) * rows;
-    const int64_t r1 = min(n, r0 + rows);
     float acc[4][4] = {};
     for (int64_t rb = r0; rb < r1; rb += kGramStageRows) {
         const int nr = int(min(int64_t(kGramStageRows), r1 - rb));
@@ -119,7 +131,6 @@ __device__ __forceinline__ void gram_small(const float *__restrict__ X, int64_t 
         }
         __syncthreads();
     }
-    float *out = part + int64_t(blockIdx.x) * d * d;
     if constexpr (RG > 1) {
 #pragma unroll
         for (int u = 0; u < 4; ++u)
@@ -205,8 +216,16 @@ __device__ float block_sum_f(float v, float *red) {
     return s;
 }
 
+__device__ __forceinline__ void pc_small_body(const double *__restrict__ C, int d,
+                                              double *__restrict__ v64, float *__restrict__ v32);
+
 __global__ void __launch_bounds__(1024)
 k_pc_small(const double *__restrict__ C, int d, double *__restrict__ v64, float *__restrict__ v32) {
+    pc_small_body(C, d, v64, v32);
+}
+
+__device__ __forceinline__ void pc_small_body(const double *__restrict__ C, int d,
+                                              double *__restrict__ v64, float *__restrict__ v32) {
     // FP64 is slow on this part: everything but the final normalisation runs
     // in FP32 (v1's accuracy only affects pruning; the FP64 normalisation
     // makes ||v64|| = 1 to FP64 precision, which the score bounds assume)
@@ -462,6 +481,177 @@ __global__ void k_gather(const uint32_t *__restrict__ skeys, const uint32_t *__r
         // ||x|| <= sqrt(s (1 + gamma_d)) (1 + u): inflate by (d+4)u
         nrm[r] = sqrtf(s) * (1.f + (float)(d + 4) * kU32);
     }
+}
+
+// ------------------------------------------------ batched index build
+// The same steps as above for many small sets at once: one launch per step,
+// each block working on one set (block tables built on the host), the
+// scores of all sets sorted together by the composite key (set, score).
+
+// Column sums of rows [r0, r1) of one set, 32 columns per block (float-float
+// per thread, FP64 across threads, fixed order).
+__global__ void __launch_bounds__(256)
+k_colsum_batch(const BSet *__restrict__ sets, const BBlk *__restrict__ blks,
+               double *__restrict__ part, int *__restrict__ bad) {
+    __shared__ double sh[256];
+    const BBlk b = blks[blockIdx.x];
+    const BSet &st = sets[b.set];
+    const int d = st.d;
+    const int TX = d < 32 ? d : 32;
+    const int TY = 256 / TX;
+    const int t = threadIdx.x;
+    const int cx = t % TX, ry = t / TX;
+    const int c = b.cb * TX + cx;
+    int badl = 0;
+    float hi = 0.f, lo = 0.f;
+    if (ry < TY && c < d) {
+        for (int64_t r = b.r0 + ry; r < b.r1; r += TY) {
+            const float x = st.X[r * st.ld + c];
+            badl |= !isfinite(x);
+            const float s = hi + x;
+            const float bb = s - hi;
+            const float e = (hi - (s - bb)) + (x - bb);
+            const float l = lo + e;
+            hi = s + l;
+            lo = l - (hi - s);
+        }
+    }
+    if (ry < TY) sh[ry * TX + cx] = (double)hi + (double)lo;
+    __syncthreads();
+    if (t < TX && b.cb * TX + t < d) {
+        double acc = 0.0;
+        for (int y = 0; y < TY; ++y) acc += sh[y * TX + t];
+        part[st.part_off + int64_t(b.rb) * d + b.cb * TX + t] = acc;
+    }
+    if (badl) atomicOr(bad, 1);
+}
+
+// One block per set: mu = column means (one warp per column), c = fl32(mu).
+__global__ void k_mean_final_batch(const BSet *__restrict__ sets, const double *__restrict__ part) {
+    const BSet &st = sets[blockIdx.x];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int c = warp; c < st.d; c += nw) {
+        double s = 0.0;
+        for (int b = lane; b < st.nb; b += 32) s += part[st.part_off + int64_t(b) * st.d + c];
+        for (int o = 16; o; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            const double m = s / (double)st.n;
+            st.mu64[c] = m;
+            st.mu32[c] = (float)m;
+        }
+    }
+}
+
+#define SNN_GRAM_BATCH(TG)                                                                     \
+    __global__ void __launch_bounds__(256)                                                     \
+    k_gram_batch##TG(const BSet *__restrict__ sets, const BBlk *__restrict__ blks,            \
+                     float *__restrict__ gpart) {                                              \
+        const BBlk b = blks[blockIdx.x];                                                       \
+        const BSet &st = sets[b.set];                                                          \
+        gram_small_rows<TG>(st.X, st.d, st.ld, st.mu32, b.r0, b.r1,                            \
+                            gpart + st.gpart_off + int64_t(b.rb) * st.d * st.d);               \
+    }
+SNN_GRAM_BATCH(16)
+SNN_GRAM_BATCH(32)
+SNN_GRAM_BATCH(64)
+#undef SNN_GRAM_BATCH
+
+// One block per set: C = sum of the set's Gram partials (FP64), one warp per
+// entry (lane-strided partial sums, shuffle tree).
+__global__ void k_gram_reduce_batch(const BSet *__restrict__ sets, const float *__restrict__ gpart,
+                                    double *__restrict__ C) {
+    const BSet &st = sets[blockIdx.x];
+    const int d = st.d, dd = d * d;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int e = warp; e < dd; e += nw) {
+        const int i = e / d, j = e % d;
+        const int a = min(i, j), b = max(i, j);
+        double s = 0.0;
+        for (int c = lane; c < st.nb; c += 32)
+            s += (double)gpart[st.gpart_off + (int64_t(c) * d + a) * d + b];
+        for (int o = 16; o; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) C[st.c_off + e] = s;
+    }
+}
+
+// One block per set: v1 (the single-CTA squaring of the unbatched build).
+__global__ void __launch_bounds__(1024) k_pc_small_batch(const BSet *__restrict__ sets,
+                                                         const double *__restrict__ C) {
+    const BSet &st = sets[blockIdx.x];
+    pc_small_body(C + st.c_off, st.d, st.v64, st.v32);
+}
+
+// Scores of rows [r0, r1) of one set, one thread per point: key (set << 32 |
+// score key), value = global point index; the largest score bound of the
+// block goes to the set's dconst[0].
+__global__ void __launch_bounds__(256)
+k_project_batch(const BSet *__restrict__ sets, const BBlk *__restrict__ blks,
+                uint64_t *__restrict__ keys, uint32_t *__restrict__ vals, int *__restrict__ bad) {
+    const BBlk b = blks[blockIdx.x];
+    const BSet &st = sets[b.set];
+    const int64_t i = b.r0 + threadIdx.x;
+    const bool live = i < b.r1;
+    float a = 0.f, e = 0.f;
+    int badl = 0;
+    if (live) {
+        for (int k = 0; k < st.d; ++k) {
+            const float p = st.X[i * st.ld + k];
+            badl |= !isfinite(p);
+            const float x = p - st.mu32[k];
+            a = fmaf(x, st.v32[k], a);
+            e = fmaf(fabsf(x), fabsf(st.v32[k]), e);
+        }
+        const int64_t g = st.p0 + i;
+        keys[g] = (uint64_t(b.set) << 32) | uint64_t(float_to_key(a));
+        vals[g] = uint32_t(g);
+    }
+    float eps = live ? (float)(st.d + 4) * kU32 * 1.01f * e + 1e-37f : 0.f;
+    for (int o = 16; o; o >>= 1) {
+        eps = fmaxf(eps, __shfl_xor_sync(0xffffffffu, eps, o));
+        badl |= __shfl_xor_sync(0xffffffffu, badl, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_nonneg(st.dconst + 0, eps);
+        if (badl) atomicOr(bad, 1);
+    }
+}
+
+// Sorted position p of the composite order: the set is the key's high word;
+// the point lands at its rank inside the set (raw and centred rows, score,
+// halved norm, norm bound, original id); the set's largest norm bound goes to
+// its dconst[1] (one atomic per group of lanes of the same set).
+__global__ void __launch_bounds__(256)
+k_gather_batch(const BSet *__restrict__ sets, const uint64_t *__restrict__ skeys,
+               const uint32_t *__restrict__ svals, int64_t total) {
+    const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const bool live = p < total;
+    const int set = live ? int(skeys[p] >> 32) : -1;
+    float nb = 0.f;
+    if (live) {
+        const BSet &st = sets[set];
+        const int64_t r = p - st.p0;
+        const int64_t i = int64_t(svals[p]) - st.p0;
+        const int d = st.d, dp = st.dp;
+        float s = 0.f;
+        for (int k = 0; k < dp; ++k) {
+            float pv = 0.f, x = 0.f;
+            if (k < d) {
+                pv = st.X[i * st.ld + k];
+                x = pv - st.mu32[k];
+            }
+            st.praw[r * dp + k] = pv;
+            st.xc[r * dp + k] = x;
+            s = fmaf(x, x, s);
+        }
+        st.alpha[r] = key_to_float(uint32_t(skeys[p] & 0xffffffffu));
+        st.order[r] = int32_t(i);
+        st.hx[r] = 0.5f * s;
+        nb = sqrtf(s) * (1.f + (float)(d + 4) * kU32);
+        st.nrm[r] = nb;
+    }
+    const unsigned grp = __match_any_sync(0xffffffffu, set);
+    const unsigned mx = __reduce_max_sync(grp, __float_as_uint(nb));   // nb >= 0
+    if (live && (threadIdx.x & 31) == __ffs(grp) - 1) atomic_max_nonneg(sets[set].dconst + 1, __uint_as_float(mx));
 }
 
 }  // namespace snn

@@ -29,6 +29,41 @@ __global__ void k_gather(const uint32_t *skeys, const uint32_t *order, const flo
 
 constexpr int kPcSmallMaxD = 64;
 
+// ------------------------------------------------ batched index build
+// One set of a batched build (d <= kPcSmallMaxD): its input, the offsets of
+// its partial sums in the shared scratch arrays, and its output slices.
+struct BSet {
+    const float *X;
+    int64_t n, ld;
+    int d, dp;
+    int64_t p0;                  // global index of the set's first point
+    int nb;                      // row blocks of the partial sums
+    int64_t part_off;            // colsum partials: nb x d doubles
+    int64_t gpart_off;           // Gram partials: nb x d x d floats
+    int64_t c_off;               // C: d x d doubles
+    double *mu64, *v64;
+    float *mu32, *v32, *alpha, *praw, *xc, *hx, *nrm, *dconst;
+    int32_t *order;
+    int vec;                     // rows are float4-aligned
+};
+// A block's unit of work: rows [r0, r1) of set `set`, row block rb, column
+// chunk cb (colsum only).
+struct BBlk {
+    int set, rb, cb;
+    int64_t r0, r1;
+};
+__global__ void k_colsum_batch(const BSet *sets, const BBlk *blks, double *part, int *bad);
+__global__ void k_mean_final_batch(const BSet *sets, const double *part);
+__global__ void k_gram_batch16(const BSet *sets, const BBlk *blks, float *gpart);
+__global__ void k_gram_batch32(const BSet *sets, const BBlk *blks, float *gpart);
+__global__ void k_gram_batch64(const BSet *sets, const BBlk *blks, float *gpart);
+__global__ void k_gram_reduce_batch(const BSet *sets, const float *gpart, double *C);
+__global__ void k_pc_small_batch(const BSet *sets, const double *C);
+__global__ void k_project_batch(const BSet *sets, const BBlk *blks, uint64_t *keys, uint32_t *vals,
+                                int *bad);
+__global__ void k_gather_batch(const BSet *sets, const uint64_t *skeys, const uint32_t *svals,
+                               int64_t total);
+
 // Tensor-core Gram matrix and first direction for d > kPcSmallMaxD
 // (gram_tc.cu).  gram_tc: C (d x d, FP64, full) = sum_r x_r x_r^T over the
 // centred rows x = fl32(p - c), and diag[i] = C[i][i].  first_direction_tc:

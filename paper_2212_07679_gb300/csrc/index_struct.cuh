@@ -1,8 +1,18 @@
 // Definition of the opaque index (Algorithm 1 output) shared by the host
 // modules of libsnn.
 #pragma once
+#include <atomic>
 #include <mutex>
 #include "common.cuh"
+
+// Pool blocks shared by the indices of one batched build: each index holds a
+// reference; the blocks are released (stream-ordered) with the last index.
+struct snn_shared_blocks {
+    std::atomic<int> refs{0};
+    void *blocks[16] = {};
+    int nblocks = 0;
+    cudaStream_t stream = nullptr;
+};
 
 struct snn_index {
     int64_t n = 0;
@@ -31,6 +41,12 @@ struct snn_index {
     float alpha_err = 0.f;
     float nrm_max = 0.f;
     mutable double surv_hint = 0.0;   // survivors per query seen last time
+    snn_shared_blocks *shared = nullptr;   // set: the arrays are slices of shared blocks
     mutable std::mutex mu;
 };
 
+namespace snn {
+// Releases an index (its own arrays, or its reference to a batched build's
+// shared blocks), stream-ordered.
+void index_release(snn_index *ix);
+}  // namespace snn

@@ -337,8 +337,8 @@ __global__ void __launch_bounds__(kScoreThreads, 2) k_score_fp32_batch(BatchScor
         jb.q0 = int64_t(tile - sd.tile0) * kBQ;
         jb.band_lo = a.tile_lo[tile];
         jb.band_hi = a.tile_hi[tile];
-        jb.c_first = (item - a.item_off[tile]) * kChunksPerItem;
-        jb.c_end = min(cdiv(jb.band_hi - jb.band_lo, kBR), jb.c_first + kChunksPerItem);
+        jb.c_first = (item - a.item_off[tile]) * a.cpi;
+        jb.c_end = min(cdiv(jb.band_hi - jb.band_lo, kBR), jb.c_first + a.cpi);
         jb.q_out = sd.q_glob;
         if (jb.dp <= kKC)
             score_item<true>(jb, sd.c1, a.surv, a.cap, a.count);

@@ -90,6 +90,7 @@ struct BatchScoreArgs {
     const int64_t *tile_lo, *tile_hi, *item_off;
     const int32_t *item_tile;
     int ntiles;
+    int cpi;                    // band chunks per work item
     uint2 *surv;
     int64_t cap;
     unsigned long long *count, *work;

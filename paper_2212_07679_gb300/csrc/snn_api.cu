@@ -98,6 +98,8 @@ static void free_device_ptr(void *p) {
     delete b;
 }
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+unsigned long long launch_count_now() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
 std::atomic<int> g_inject{0};
@@ -141,13 +143,23 @@ static snn_status own_output(T *p, cudaStream_t s) {
     return register_block(p, ptrs, 1, s);
 }
 
-static void index_release(snn_index *ix) {
+void index_release(snn_index *ix) {
     if (!ix) return;
-    void *ptrs[] = {ix->mu64, ix->mu32, ix->v64,   ix->v32,        ix->alpha,      ix->order,
-                    ix->praw, ix->xc,   ix->hx,    ix->nrm,        ix->dconst,     ix->tc_part[0],
-                    ix->tc_part[1], ix->tc_part[2]};
-    for (void *p : ptrs)
+    for (void *p : ix->tc_part)
         if (p) cudaFreeAsync(p, ix->stream);
+    if (ix->shared) {
+        snn_shared_blocks *sb = ix->shared;
+        if (sb->refs.fetch_sub(1) == 1) {
+            for (int i = 0; i < sb->nblocks; ++i)
+                if (sb->blocks[i]) cudaFreeAsync(sb->blocks[i], sb->stream);
+            delete sb;
+        }
+    } else {
+        void *ptrs[] = {ix->mu64, ix->mu32, ix->v64, ix->v32, ix->alpha, ix->order,
+                        ix->praw, ix->xc,   ix->hx,  ix->nrm, ix->dconst};
+        for (void *p : ptrs)
+            if (p) cudaFreeAsync(p, ix->stream);
+    }
     delete ix;
 }
 
@@ -752,6 +764,19 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     return SNN_OK;
 }
 
+snn_status index_build_batch(int32_t nsets, const float *const *X, const int64_t *n,
+                             const int32_t *d, const int64_t *ld, cudaStream_t s, snn_index **out);
+snn_status plan_create(int32_t nsets, const snn_index *const *idx, const int64_t *m_in,
+                       const double *R_in, snn_precision prec, int64_t surv_cap, int64_t nnz_cap,
+                       cudaStream_t s, snn_batch_plan **out);
+void plan_release(snn_batch_plan *p, cudaStream_t s);
+float *plan_queries(snn_batch_plan *p, int32_t t);
+snn_status plan_run(snn_batch_plan *p, cudaStream_t s);
+snn_status plan_launch_graph(snn_batch_plan *p, cudaStream_t s);
+snn_status plan_result(snn_batch_plan *p, cudaStream_t s, snn_csr *out, int64_t *need_surv,
+                       int64_t *need_nnz);
+snn_status plan_tune(snn_batch_plan *p, cudaStream_t s, int *best_cpi, int *best_ctas,
+                     float *best_ms);
 snn_status batch_query(int32_t nsets, const snn_index *const *idx, const float *const *Q,
                        const int64_t *m_in, const int64_t *ldq_in, const double *R_in,
                        cudaStream_t s, snn_csr *out);
@@ -787,6 +812,17 @@ snn_status snn_index_build(const float *X, int64_t n, int32_t d, int64_t ld, voi
     return index_build(X, n, d, ld, static_cast<cudaStream_t>(stream), out);
 }
 
+snn_status snn_index_build_batch(int32_t nsets, const float *const *X, const int64_t *n,
+                                 const int32_t *d, const int64_t *ld, void *stream,
+                                 snn_index **out) {
+    clear_error();
+    if (nsets < 0 || (nsets > 0 && (!X || !n || !d || !ld || !out))) {
+        set_error("invalid batch arguments");
+        return SNN_EINVAL;
+    }
+    return index_build_batch(nsets, X, n, d, ld, static_cast<cudaStream_t>(stream), out);
+}
+
 snn_status snn_query_radius(const snn_index *idx, const float *Q, int64_t m, int64_t ldq, double R,
                             snn_precision prec, void *stream, snn_csr *out,
                             snn_query_stats *stats) {
@@ -819,6 +855,54 @@ snn_status snn_query_radius_batch(int32_t nsets, const snn_index *const *idx, co
     }
     ensure_pool();
     return batch_query(nsets, idx, Q, m, ldq, R, static_cast<cudaStream_t>(stream), out);
+}
+
+snn_status snn_batch_plan_create(int32_t nsets, const snn_index *const *idx, const int64_t *m,
+                                 const double *R, snn_precision prec, int64_t survivor_capacity,
+                                 int64_t nnz_capacity, void *stream, snn_batch_plan **out) {
+    clear_error();
+    if (!out) { set_error("out is NULL"); return SNN_EINVAL; }
+    *out = nullptr;
+    if (nsets < 1 || !idx || !m || !R) { set_error("invalid plan arguments"); return SNN_EINVAL; }
+    if (prec != SNN_PREC_FP32 && prec != SNN_PREC_BF16) {
+        set_error("precision %d is not available in this build", (int)prec);
+        return SNN_ENOTSUP;
+    }
+    ensure_pool();
+    return plan_create(nsets, idx, m, R, prec, survivor_capacity, nnz_capacity,
+                       static_cast<cudaStream_t>(stream), out);
+}
+
+float *snn_batch_plan_queries(snn_batch_plan *plan, int32_t set) { return plan_queries(plan, set); }
+
+snn_status snn_batch_plan_run(snn_batch_plan *plan, void *stream) {
+    clear_error();
+    if (!plan) { set_error("plan is NULL"); return SNN_EINVAL; }
+    return plan_run(plan, static_cast<cudaStream_t>(stream));
+}
+
+snn_status snn_batch_plan_launch_graph(snn_batch_plan *plan, void *stream) {
+    clear_error();
+    if (!plan) { set_error("plan is NULL"); return SNN_EINVAL; }
+    return plan_launch_graph(plan, static_cast<cudaStream_t>(stream));
+}
+
+snn_status snn_batch_plan_result(snn_batch_plan *plan, void *stream, snn_csr *out,
+                                 int64_t *need_survivors, int64_t *need_nnz) {
+    clear_error();
+    if (!plan || !out) { set_error("plan or out is NULL"); return SNN_EINVAL; }
+    return plan_result(plan, static_cast<cudaStream_t>(stream), out, need_survivors, need_nnz);
+}
+
+snn_status snn_batch_plan_tune(snn_batch_plan *plan, void *stream, int32_t *chunks_per_item,
+                               int32_t *ctas_per_sm, float *ms) {
+    clear_error();
+    if (!plan) { set_error("plan is NULL"); return SNN_EINVAL; }
+    return plan_tune(plan, static_cast<cudaStream_t>(stream), chunks_per_item, ctas_per_sm, ms);
+}
+
+void snn_batch_plan_free(snn_batch_plan *plan, void *stream) {
+    plan_release(plan, static_cast<cudaStream_t>(stream));
 }
 
 snn_status snn_dbscan(const float *X, int64_t n, int32_t d, int64_t ld, double eps, int32_t min_pts,

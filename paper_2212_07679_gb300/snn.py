@@ -79,6 +79,28 @@ def _load():
     lib.snn_test_inject.restype = ctypes.c_int
     lib.snn_launch_count.argtypes = []
     lib.snn_launch_count.restype = ctypes.c_uint64
+    lib.snn_index_build_batch.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(i64),
+                                          ctypes.POINTER(i32), ctypes.POINTER(i64), vp,
+                                          ctypes.POINTER(vp)]
+    lib.snn_index_build_batch.restype = ctypes.c_int
+    lib.snn_batch_plan_create.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(i64),
+                                          ctypes.POINTER(f64), ctypes.c_int, i64, i64, vp,
+                                          ctypes.POINTER(vp)]
+    lib.snn_batch_plan_create.restype = ctypes.c_int
+    lib.snn_batch_plan_queries.argtypes = [vp, i32]
+    lib.snn_batch_plan_queries.restype = vp
+    lib.snn_batch_plan_run.argtypes = [vp, vp]
+    lib.snn_batch_plan_run.restype = ctypes.c_int
+    lib.snn_batch_plan_launch_graph.argtypes = [vp, vp]
+    lib.snn_batch_plan_launch_graph.restype = ctypes.c_int
+    lib.snn_batch_plan_result.argtypes = [vp, vp, ctypes.POINTER(CSRStruct), ctypes.POINTER(i64),
+                                          ctypes.POINTER(i64)]
+    lib.snn_batch_plan_result.restype = ctypes.c_int
+    lib.snn_batch_plan_tune.argtypes = [vp, vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                        ctypes.POINTER(ctypes.c_float)]
+    lib.snn_batch_plan_tune.restype = ctypes.c_int
+    lib.snn_batch_plan_free.argtypes = [vp, vp]
+    lib.snn_batch_plan_free.restype = None
     return lib
 
 
@@ -267,6 +289,109 @@ def query_batch(indices: list[Index], Qs: list[torch.Tensor | None], Rs: list[fl
         _check(lib.snn_query_radius_batch(k, hs, qp, ms, lds, rs, PRECISIONS[precision],
                                           _stream_ptr(stream), outs))
     return [_csr_from(outs[s], dev) for s in range(k)]
+
+
+def build_batch(Xs: list, stream=None) -> list:
+    """Indices of many small point sets (d <= 64) built together
+    (snn_index_build_batch): one launch per step over every set."""
+    k = len(Xs)
+    pts = [_points(X, "X") for X in Xs]
+    xp = (ctypes.c_void_p * k)(*[X.data_ptr() for X, _ in pts])
+    ns = (ctypes.c_int64 * k)(*[X.shape[0] for X, _ in pts])
+    ds = (ctypes.c_int32 * k)(*[X.shape[1] for X, _ in pts])
+    lds = (ctypes.c_int64 * k)(*[ld for _, ld in pts])
+    hs = (ctypes.c_void_p * k)()
+    dev = pts[0][0].device if k else torch.device("cuda")
+    with torch.cuda.device(dev):
+        _check(lib.snn_index_build_batch(k, xp, ns, ds, lds, _stream_ptr(stream), hs))
+    out = []
+    for t, (X, _) in enumerate(pts):
+        ix = Index.__new__(Index)
+        ix.device = dev
+        ix.n, ix.d = X.shape
+        ix._h = ctypes.c_void_p(hs[t])
+        out.append(ix)
+    return out
+
+
+class BatchPlan:
+    """A batched query with fixed sizes (snn_batch_plan_*): runs enqueue
+    device work only, so they can be captured into a CUDA graph.  ms[t] is
+    the number of queries of set t (written into queries(t) before a run), or
+    None for the self-join of indices[t]."""
+
+    def __init__(self, indices: list, ms: list, Rs: list, precision: str = "fp32",
+                 survivor_capacity: int = 1 << 24, nnz_capacity: int = 1 << 24, stream=None):
+        k = len(indices)
+        self.indices = list(indices)          # the plan reads their arrays
+        self.device = indices[0].device
+        self.ms = [-1 if m is None else int(m) for m in ms]
+        hs = (ctypes.c_void_p * k)(*[ix.handle.value for ix in indices])
+        mm = (ctypes.c_int64 * k)(*self.ms)
+        rs = (ctypes.c_double * k)(*[float(r) for r in Rs])
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib.snn_batch_plan_create(k, hs, mm, rs, PRECISIONS[precision],
+                                             int(survivor_capacity), int(nnz_capacity),
+                                             _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h
+
+    def queries(self, t: int) -> torch.Tensor:
+        """The plan's device buffer for set t's queries (m x d), writable."""
+        p = lib.snn_batch_plan_queries(self._h, t)
+        if not p or self.ms[t] <= 0:
+            return torch.empty((0, self.indices[t].d), dtype=torch.float32, device=self.device)
+        m, d = self.ms[t], self.indices[t].d
+        return torch.as_tensor(_Borrowed(p, m * d, "<f4"), device=self.device).view(m, d)
+
+    def run(self, stream=None):
+        with torch.cuda.device(self.device):
+            _check(lib.snn_batch_plan_run(self._h, _stream_ptr(stream)))
+
+    def launch_graph(self, stream=None):
+        with torch.cuda.device(self.device):
+            _check(lib.snn_batch_plan_launch_graph(self._h, _stream_ptr(stream)))
+
+    def tune(self, stream=None):
+        c, t, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+        with torch.cuda.device(self.device):
+            _check(lib.snn_batch_plan_tune(self._h, _stream_ptr(stream), ctypes.byref(c),
+                                           ctypes.byref(t), ctypes.byref(ms)))
+        return c.value, t.value, ms.value
+
+    def result(self, stream=None, copy: bool = True) -> list:
+        """Per-set results of the last run (copies unless copy=False: then
+        the tensors view the plan's arrays until the next run)."""
+        k = len(self.indices)
+        outs = (CSRStruct * k)()
+        ns, nz = ctypes.c_int64(), ctypes.c_int64()
+        with torch.cuda.device(self.device):
+            _check(lib.snn_batch_plan_result(self._h, _stream_ptr(stream), outs, ctypes.byref(ns),
+                                             ctypes.byref(nz)))
+        res = []
+        for t in range(k):
+            cs = outs[t]
+
+            def view(ptr, count, typestr, dtype):
+                if not ptr or count == 0:
+                    return torch.empty(0, dtype=dtype, device=self.device)
+                v = torch.as_tensor(_Borrowed(ptr, count, typestr), device=self.device)
+                return v.clone() if copy else v
+            res.append(CSR(view(cs.offsets, cs.m + 1, "<i8", torch.int64),
+                           view(cs.indices, cs.nnz, "<i4", torch.int32),
+                           view(cs.dist2, cs.nnz, "<f4", torch.float32)))
+        return res
+
+    def close(self, stream=None):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib.snn_batch_plan_free(self._h, _stream_ptr(stream))
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def dbscan(X: torch.Tensor, eps: float, min_pts: int, precision: str = "fp32", stream=None):
