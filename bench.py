@@ -243,30 +243,52 @@ def run_ours(args):
     ms_step = float(t_max.item()) / args.steps
     value = world * w.m / (ms_step / 1e3)
 
-    # the other scoring precision on the same workload, same timing rules
-    compare = None
-    if args.compare:
-        other = "fp32" if args.precision == "bf16" else "bf16"
-        for _ in range(2):
-            ix = snn.Index(X)
-            ix.query(None, w.R, precision=other)
-            del ix
-        times = []
-        for _ in range(max(3, min(args.steps, 5))):
-            flush.fill_(1)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ix = snn.Index(X)
-            out = ix.query(None, w.R, precision=other, stats=True)
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-            ost = out.stats
-            del ix, out
+    def time_precision(prec, products=None):
+        # another scoring precision on the same workload, same timing rules;
+        # its CSR is compared with the headline run's on the device
+        if products is not None:
+            os.environ["SNN_FP8_PRODUCTS"] = str(products)
+        try:
+            for _ in range(2):
+                ix = snn.Index(X)
+                ix.query(None, w.R, precision=prec)
+                del ix
+            times = []
+            for _ in range(max(3, min(args.steps, 5))):
+                flush.fill_(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ix = snn.Index(X)
+                out = ix.query(None, w.R, precision=prec, stats=True)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+                ost = out.stats
+                same = (torch.equal(out.offsets, last_out.offsets) and torch.equal(out.indices, last_out.indices)
+                        and torch.equal(out.dist2.view(torch.int32), last_out.dist2.view(torch.int32)))
+                del ix, out
+        finally:
+            if products is not None:
+                os.environ.pop("SNN_FP8_PRODUCTS", None)
         oms = float(np.mean(times))
-        compare = {"precision": other, "value": w.m / (oms / 1e3), "unit": "queries/s",
-                   "ms_per_step": oms, "score_ms": ost["ms_score"], "survivors": ost["survivors"]}
+        dsurv = 2 * ost["survivors"] - w.m if w.Q is None else ost["survivors"]
+        res = {"precision": prec, "value": w.m / (oms / 1e3), "unit": "queries/s",
+               "ms_per_step": oms, "score_ms": ost["ms_score"], "recheck_ms": ost["ms_recheck"],
+               "survivors": ost["survivors"],
+               "recheck_fraction": (dsurv - ost["nnz"]) / max(1, ost["candidates"]),
+               "csr_identical_to_headline": bool(same)}
+        if prec == "fp8":
+            res["products_per_kstep"] = products
+            res["precision_used"] = ["fp32", "bf16", "fp8"][ost["precision_used"]]
+            res["mma_flops_per_pair"] = ost["mma_flops_per_pair"]
+        return res
+
+    compare, fp8_variants = None, None
+    if args.compare:
+        compare = time_precision("fp32" if args.precision != "fp32" else "bf16")
+        if args.precision == "bf16" and w.d > 55:
+            fp8_variants = [time_precision("fp8", k) for k in (3, 4, 6)]
 
     # end to end through host buffers: pinned X in, CSR out, every step
     e2e_ms, h2d, d2h = [], 0, 0
@@ -295,13 +317,16 @@ def run_ours(args):
     achieved = flops / (sm / 1e3) / 1e12
     effective = 2.0 * w.d * st["candidates"] / (sm / 1e3) / 1e12
     directed_surv = 2 * st["survivors"] - w.m if w.Q is None else st["survivors"]
-    if args.precision == "bf16":
-        # tensor-bound scoring, timed inside a multi-kernel step: sustained peak
-        peak = float(peaks["bf16_tflops_sustained"])
+    if args.precision in ("bf16", "fp8"):
+        # tensor-bound scoring, timed inside a multi-kernel step: sustained
+        # peak (e4m3: the BF16 figure x 2, the nominal dense ratio)
+        f8 = args.precision == "fp8" and st["precision_used"] == 2
+        peak = float(peaks["bf16_tflops_sustained"]) * (2.0 if f8 else 1.0)
         pipe = st["mma_flops_per_pair"] * st["band_pairs"] / (sm / 1e3) / 1e12
         roofline = {"kernel": "k_score_tc", "bound": "tensor", "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                    "peak_source": f"MEASURED_PEAKS.json bf16_tflops_sustained ({src})",
+                    "peak_source": (f"MEASURED_PEAKS.json bf16_tflops_sustained x 2 (e4m3 nominal ratio; {src})"
+                                    if f8 else f"MEASURED_PEAKS.json bf16_tflops_sustained ({src})"),
                     "algorithmic": "2d flop per scored pair (Eq. (4)); the symmetric self-join "
                                    "scores each unordered pair once",
                     "effective_tflops": effective, "score_ms": sm,
@@ -316,10 +341,12 @@ def run_ours(args):
                                    "scores each unordered pair once",
                     "effective_tflops": effective, "score_ms": sm}
     line = {
-        "metric": "exact radius queries/s (self-join; BF16 tensor-core or FP32 rejection, exact decision)",
+        "metric": "exact radius queries/s (self-join; BF16/FP8 tensor-core or FP32 rejection, exact decision)",
         "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32+f64" if args.precision == "bf16" else "f32+f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"bf16": "bf16+f32+f64", "fp8": "e4m3+bf16+f32+f64"}.get(args.precision, "f32+f64"),
+        "data": "synthetic",
         "config": workload_config(args, w),
         "pairs_scored_per_s": st["band_pairs"] / (ms_step / 1e3),
         "candidate_pairs_per_s": st["candidates"] / (ms_step / 1e3),
@@ -331,6 +358,7 @@ def run_ours(args):
         "roofline": roofline,
         "clocks": clk,
         "other_precision": compare,
+        "fp8_variants": fp8_variants,
         "gpu_launches": launches,
         "gpu_launches_per_step": launches / args.steps,
         "e2e": {"value": w.m / (np.median(e2e_ms) / 1e3), "unit": "queries/s",
@@ -529,7 +557,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="gmm_aniso")
     ap.add_argument("--n", type=int, default=0)
-    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8"])
     ap.add_argument("--no-compare", dest="compare", action="store_false",
                     help="skip timing the other precision beside the headline one")
     ap.add_argument("--ref-budget", type=float, default=15.0)

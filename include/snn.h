@@ -55,7 +55,14 @@ typedef enum {
 typedef enum {
     SNN_PREC_FP32 = 0,      /* FP32 CUDA-core dot products                  */
     SNN_PREC_BF16 = 1,      /* BF16 tcgen05 tensor-core dot products        */
-    SNN_PREC_FP8E4M3 = 2    /* FP8 e4m3 with per-row scale (not yet built)  */
+    SNN_PREC_FP8E4M3 = 2    /* FP8 e4m3 tcgen05 dot products, each row
+                               scaled by its own power of two; used for
+                               d > 55 with norms and R below 2^20, BF16
+                               elsewhere (see precision_used).  Three e4m3
+                               parts, six products per k-step; the
+                               environment variable SNN_FP8_PRODUCTS = 3 or
+                               4 selects two parts (faster scoring, wider
+                               bound)                                      */
 } snn_precision;
 
 /* Opaque index (Algorithm 1 output): mean mu, first principal direction v1,
@@ -91,7 +98,10 @@ typedef struct {
  *  exact_fp64  survivors whose decision or distance needed the FP64 loop
  *              itself (the compensated FP32 evaluation settles the rest);
  *  mma_flops_per_pair  tensor-core flops executed per scored pair (BF16
- *              split products and folded threshold columns; 0 for FP32);
+ *              or e4m3 split products and folded threshold columns; 0 for
+ *              FP32);
+ *  precision_used  the rejection arithmetic that ran (an FP8 request runs
+ *              BF16 where FP8 is not available);
  *  ms_*        device time of the phases (CUDA events on `stream`). */
 typedef struct {
     int64_t candidates;
@@ -104,6 +114,7 @@ typedef struct {
     float ms_score;
     float ms_recheck;
     float ms_csr;
+    int32_t precision_used;
 } snn_query_stats;
 
 /* Algorithm 1 (Section 3.1): centre, first principal direction, scores,

@@ -38,6 +38,15 @@ struct snn_index {
     int tc_nsplit = 0;
     int tc_k2 = 0;                // row width of part 1 (columns)
     int tc_k2n = 0;               // row width of parts 2 and 3
+    // FP8 e4m3 operands (built on first use): f8_part[p] is n x f8_k8 bytes,
+    // part p of each row scaled by its power of two; f8_fold is n x 16 bf16,
+    // the folded threshold and error-bound columns.  Keyed by the split, the
+    // products per k-step and the row width.
+    uint8_t *f8_part[3] = {nullptr, nullptr, nullptr};
+    uint16_t *f8_fold = nullptr;
+    int f8_nsplit = 0;
+    int f8_np = 0;
+    int f8_k8 = 0;
     float alpha_err = 0.f;
     float nrm_max = 0.f;
     mutable double surv_hint = 0.0;   // survivors per query seen last time

@@ -147,6 +147,9 @@ void index_release(snn_index *ix) {
     if (!ix) return;
     for (void *p : ix->tc_part)
         if (p) cudaFreeAsync(p, ix->stream);
+    for (void *p : ix->f8_part)
+        if (p) cudaFreeAsync(p, ix->stream);
+    if (ix->f8_fold) cudaFreeAsync(ix->f8_fold, ix->stream);
     if (ix->shared) {
         snn_shared_blocks *sb = ix->shared;
         if (sb->refs.fetch_sub(1) == 1) {
@@ -580,6 +583,9 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         return fail(SNN_ENOMEM);
     }
     int64_t mma_fpp = 0;
+    // FP8 where its shape and ranges allow it, BF16 otherwise
+    const snn_precision used =
+        prec == SNN_PREC_FP8E4M3 && !f8_eligible(ix, Rx) ? SNN_PREC_BF16 : prec;
     for (int attempt = 0; attempt < 2; ++attempt) {
         CUDA_Q(cudaMallocAsync(&surv, size_t(cap) * sizeof(uint2), s));
         CUDA_Q(cudaMallocAsync(&rec_d2, size_t(cap) * sizeof(float), s));
@@ -589,7 +595,9 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         sa.cap = cap;
         if (stats) cudaEventRecord(ev[1], s);
         snn_status st = SNN_OK;
-        if (prec == SNN_PREC_BF16) {
+        if (used == SNN_PREC_FP8E4M3) {
+            st = f8_score_launch(ix, sa, s, Rx, e_data, scr, &mma_fpp);
+        } else if (used == SNN_PREC_BF16) {
             st = tc_score_launch(ix, sa, s, Rx, e_data, scr, &mma_fpp);
         } else {
             const int grid = device_sm_count() * 2;
@@ -745,6 +753,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         CUDA_Q(cudaStreamSynchronize(s));
         stats->exact_fp64 = (int64_t)nf;
         stats->mma_flops_per_pair = mma_fpp;
+        stats->precision_used = (int32_t)used;
         stats->candidates = (int64_t)hb->ctr[3];
         stats->band_pairs = (int64_t)hb->ctr[2];
         stats->survivors = nsurv;
@@ -834,7 +843,7 @@ snn_status snn_query_radius(const snn_index *idx, const float *Q, int64_t m, int
         if (m < 0 || m >= (int64_t(1) << 31)) { set_error("m must be in [0, 2^31)"); return SNN_EINVAL; }
         if (ldq < idx->d) { set_error("ldq must be >= d"); return SNN_EINVAL; }
     }
-    if (prec != SNN_PREC_FP32 && prec != SNN_PREC_BF16) {
+    if (prec != SNN_PREC_FP32 && prec != SNN_PREC_BF16 && prec != SNN_PREC_FP8E4M3) {
         set_error("precision %d is not available in this build", (int)prec);
         return SNN_ENOTSUP;
     }
@@ -849,7 +858,7 @@ snn_status snn_query_radius_batch(int32_t nsets, const snn_index *const *idx, co
         set_error("invalid batch arguments");
         return SNN_EINVAL;
     }
-    if (prec != SNN_PREC_FP32 && prec != SNN_PREC_BF16) {
+    if (prec != SNN_PREC_FP32 && prec != SNN_PREC_BF16 && prec != SNN_PREC_FP8E4M3) {
         set_error("precision %d is not available in this build", (int)prec);
         return SNN_ENOTSUP;
     }
@@ -864,7 +873,7 @@ snn_status snn_batch_plan_create(int32_t nsets, const snn_index *const *idx, con
     if (!out) { set_error("out is NULL"); return SNN_EINVAL; }
     *out = nullptr;
     if (nsets < 1 || !idx || !m || !R) { set_error("invalid plan arguments"); return SNN_EINVAL; }
-    if (prec != SNN_PREC_FP32 && prec != SNN_PREC_BF16) {
+    if (prec != SNN_PREC_FP32 && prec != SNN_PREC_BF16 && prec != SNN_PREC_FP8E4M3) {
         set_error("precision %d is not available in this build", (int)prec);
         return SNN_ENOTSUP;
     }

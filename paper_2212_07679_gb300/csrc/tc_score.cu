@@ -15,12 +15,22 @@
 // rejected exactly when the sign bit of acc_ij is set; all other pairs go to
 // the exact decision like the FP32 path's survivors.
 //
+// The FP8 variant splits each row, scaled by a power of two of its own, into
+// e4m3 parts (tcgen05.mma kind::f8f6f4, K = 32 per instruction) and folds the
+// threshold together with a per-pair bound on every dropped term (built from
+// the measured norms of the parts and of the exact residual) into one final
+// BF16 k-step of the same accumulator.
+//
 // Warp roles: warp 0 issues TMA loads, warp 1 owns TMEM and issues the MMAs,
 // the remaining 8 (or 16, with two query tiles per item) warps drain the
 // accumulators.  Stages are guarded by mbarriers; every wait is bounded and a
 // timeout sets an error flag.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include <algorithm>
+#include <cstdlib>
 
 #include "index_struct.cuh"
 #include "tc_common.cuh"
@@ -102,7 +112,10 @@ __host__ __device__ constexpr int smem_budget(int cps, int align) {
 // the next item's tile loads while the current one is in use; CPS resident
 // CTAs per SM; MT query tiles of 128 per work item (each band chunk is loaded
 // once and multiplied with all MT tiles, M = 128 per MMA).
-template <int NSPLIT, int BK, int BN, bool ARES, int CPS = 1, int NW = BK, int MT = 1>
+// F8NP > 0: FP8 e4m3 data k-blocks of 2 BK bytes per row (BK = NW = 16 or
+// 32: one or two K = 32 steps of F8NP products each), then one 32-byte BF16
+// k-block of folded columns in part 1's slots.
+template <int NSPLIT, int BK, int BN, bool ARES, int CPS = 1, int NW = BK, int MT = 1, int F8NP = 0>
 struct TcShape {
     static constexpr int kAlign = BK == 64 ? 1024 : 512;
     static constexpr int kSmemBudget = smem_budget(CPS, kAlign);
@@ -120,7 +133,7 @@ struct TcShape {
     static constexpr int kStgBytes = tc_epi_warps(MT, BN) * kStgEntries * 8;
     static constexpr int kStagesRaw = (kSmemBudget - kAResBytes - kStgBytes) / kStageBytes;
     static constexpr int kStages = kStagesRaw > 12 ? 12 : kStagesRaw;
-    static constexpr int kNP = NSPLIT == 2 ? 3 : 6;     // MMAs per k-step
+    static constexpr int kNP = F8NP ? F8NP : (NSPLIT == 2 ? 3 : 6);   // MMAs per k-step
     static constexpr int kKSteps = BK / 16;             // k-steps per k-block
     static constexpr int kRowBytes = BK * 2;
     static constexpr int kRowBytesN = NW * 2;
@@ -135,6 +148,9 @@ struct TcShape {
     static_assert(MT == 1 || ARES, "several query tiles per item need a resident query tile");
     static_assert(kTmemCols * CPS <= 512, "accumulators exceed TMEM");
     static_assert(NW == 16 || NW == 32 || NW == 64, "unsupported part width");
+    static_assert(!F8NP || ((BK == 16 || BK == 32) && NW == BK && !ARES && MT == 1), "FP8 shape");
+    static_assert(!F8NP || (NSPLIT == 2 && (F8NP == 3 || F8NP == 4)) || (NSPLIT == 3 && F8NP == 6),
+                  "FP8 products");
 };
 
 __host__ __device__ constexpr int tc_npairs(int nsplit) { return nsplit == 2 ? 3 : 6; }
@@ -175,13 +191,14 @@ __device__ __forceinline__ ItemInfo item_info(const TcArgs &a, int64_t item) {
     return f;
 }
 
-template <int NSPLIT, int BK, int BN, bool ARES, int CPS, int NW, int MT>
+template <int NSPLIT, int BK, int BN, bool ARES, int CPS, int NW, int MT, int F8NP>
 __global__ void __launch_bounds__(tc_threads(MT, BN), CPS)
 k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUtensorMap qa1,
            const __grid_constant__ CUtensorMap qa2, const __grid_constant__ CUtensorMap xb0,
            const __grid_constant__ CUtensorMap xb1, const __grid_constant__ CUtensorMap xb2,
+           const __grid_constant__ CUtensorMap qf, const __grid_constant__ CUtensorMap xf,
            TcArgs a) {
-    using Sh = TcShape<NSPLIT, BK, BN, ARES, CPS, NW, MT>;
+    using Sh = TcShape<NSPLIT, BK, BN, ARES, CPS, NW, MT, F8NP>;
     constexpr int S = Sh::kStages;
     constexpr int NP = Sh::kNP;
     constexpr int NB = Sh::kNBuf;                // accumulator buffers
@@ -189,6 +206,10 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
     // (A part, B part) products kept by the split: all with pa + pb <= NSPLIT-1
     constexpr int kPa[6] = {0, 0, 1, 0, 1, 2};
     constexpr int kPb[6] = {0, 1, 0, 2, 1, 0};
+    // FP8: the same list, except that four products keep (1,1) as the fourth
+    constexpr int kPa8[6] = {0, 0, 1, F8NP == 4 ? 1 : 0, 1, 2};
+    constexpr int kPb8[6] = {0, 1, 0, F8NP == 4 ? 1 : 2, 1, 0};
+    constexpr uint32_t kIdesc8 = idesc_e4m3<kTM, BN>();
 
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -286,11 +307,18 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                         const int s = it % S;
                         const uint32_t round = uint32_t(it / S);
                         if (!mbar_wait(empty_bar(s), (round & 1u) ^ 1u, s_abort, a.err)) break;
-                        mbar_expect_tx(full_bar(s), uint32_t(Sh::kStageBytes));
-                        for (int p = 0; p < NSPLIT; ++p) {
-                            const int kx = kb * (p == 0 ? BK : NW);
-                            if (!ARES) tma_load_2d(a_tile(s, p), qa[p], kx, int(f.q0), full_bar(s));
-                            tma_load_2d(b_tile(s, p), xb[p], kx, int(j0), full_bar(s));
+                        if (F8NP && kb == a.nkb - 1) {
+                            // folded BF16 columns, 32 bytes per row, in part 1's slots
+                            mbar_expect_tx(full_bar(s), uint32_t((kTM + BN) * 32));
+                            tma_load_2d(a_tile(s, 0), &qf, 0, int(f.q0), full_bar(s));
+                            tma_load_2d(b_tile(s, 0), &xf, 0, int(j0), full_bar(s));
+                        } else {
+                            mbar_expect_tx(full_bar(s), uint32_t(Sh::kStageBytes));
+                            for (int p = 0; p < NSPLIT; ++p) {
+                                const int kx = kb * (p == 0 ? BK : NW);
+                                if (!ARES) tma_load_2d(a_tile(s, p), qa[p], kx, int(f.q0), full_bar(s));
+                                tma_load_2d(b_tile(s, p), xb[p], kx, int(j0), full_bar(s));
+                            }
                         }
                         issued = it + 1;
                     }
@@ -322,6 +350,28 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                         const uint32_t round = uint32_t(it / S);
                         if (!(ok = mbar_wait(full_bar(s), round & 1u, s_abort, a.err))) break;
                         tmem_fence_after();
+                        if constexpr (F8NP != 0) {
+                            if (kb == a.nkb - 1) {
+                                // the folded columns: one BF16 K = 16 step
+                                mma_bf16(dt0, smem_desc<32>(a_tile(s, 0)), smem_desc<32>(b_tile(s, 0)),
+                                         kIdesc, 1u);
+                            } else {
+#pragma unroll
+                                for (int ks = 0; ks < Sh::kKSteps; ++ks) {
+                                    // 32-byte k steps; the last block may hold one
+                                    const int kg = kb * Sh::kKSteps + ks;
+                                    if (kg >= a.ksteps_data) break;
+#pragma unroll
+                                    for (int pr = 0; pr < F8NP; ++pr)
+                                        mma_e4m3(dt0, smem_desc<Sh::kRowBytes>(a_tile(s, kPa8[pr]) + 32u * ks),
+                                                 smem_desc<Sh::kRowBytes>(b_tile(s, kPb8[pr]) + 32u * ks),
+                                                 kIdesc8, (kg | pr) != 0 ? 1u : 0u);
+                                }
+                            }
+                            mma_commit(empty_bar(s));
+                            *s_consumed = it + 1;
+                            continue;
+                        }
 #pragma unroll
                         for (int ks = 0; ks < Sh::kKSteps; ++ks) {
                             const int kg = kb * Sh::kKSteps + ks;
@@ -633,12 +683,153 @@ __global__ void k_tc_pack(const float *__restrict__ xc, int dp, const float *__r
     }
 }
 
+// ------------------------------------------------ FP8 operand packing
+// Value of an e4m3 byte (1 sign, 4 exponent bits with bias 7, 3 mantissa
+// bits; exponent field 0 holds the subnormals m 2^-9).
+__device__ __forceinline__ float e4m3_value(uint32_t b) {
+    const uint32_t e = (b >> 3) & 15u, m = b & 7u;
+    const float mag = e == 0 ? float(m) * 0x1p-9f : __uint_as_float(((e + 120u) << 23) | (m << 20));
+    return (b & 0x80u) ? -mag : mag;
+}
+
+__device__ __forceinline__ float warp_sum_ru(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = __fadd_ru(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ uint16_t bf16_up(double v) {
+    return bf16_bits(__float2bfloat16_ru(__double2float_ru(v)));
+}
+
+// FP8 rows, one warp per row.  The centred FP32 row x is scaled by 2^s, s
+// chosen from its largest |x_k| so that the scaled row x' peaks in
+// [128, 256) (clamped to [-23, 24]), and split x' = x_1 + ... + x_P + e with
+// e4m3 parts (each the rounding of the remainder, which stays exact in
+// FP32).  The norms of x', of the parts and of the residual e are summed with
+// upward rounding, so the bounds built from them hold whatever the
+// conversion's rounding.  16 folded BF16 columns follow (scaled units):
+//   data:  -(1-ch) hx 2^s (split in 3) | 2^s x3 | Nx | ||x'|| | ||e_x|| |
+//          ||x_2|| (3 products) or ||x_2||, ||x_3|| (3 parts) | zeros
+//   query: 2^s x3 | A'_i 2^s (split in 3) | kacc Ny | ||e_y|| |
+//          ||y'|| + ||e_y|| | ||y_2|| or ||y_3||, ||y_2|| + ||y_3|| | zeros
+// (Nx = sum of the parts' norms; the query side's bound entries are inflated
+// by 1 + 2 kacc.)  Their products are the rank-one terms of the bound on
+// x'.y' minus the kept products, plus kacc Nx Ny for the accumulation.
+template <int NSPLIT, int NP>
+__global__ void k_f8_pack(const float *__restrict__ xc, int dp, const float *__restrict__ hx,
+                          const double *__restrict__ Aq, int64_t rows, int d, int K8, double ch,
+                          double kacc, int query_side, uint8_t *__restrict__ p0,
+                          uint8_t *__restrict__ p1, uint8_t *__restrict__ p2,
+                          uint16_t *__restrict__ fold) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; r < rows; r += nwarps) {
+        const float4 *xr = reinterpret_cast<const float4 *>(xc + r * dp);
+        float mx = 0.f;
+        for (int k0 = lane * 4; k0 < d; k0 += 128) {
+            const float4 v = xr[k0 / 4];
+            const float xv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (k0 + e < d) mx = fmaxf(mx, fabsf(xv[e]));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        int sg = 0;
+        if (mx > 0.f) {
+            int ex;
+            frexpf(mx, &ex);                   // mx in [2^(ex-1), 2^ex)
+            sg = min(24, max(-23, 8 - ex));
+        }
+        const float sc = __uint_as_float(uint32_t(127 + sg) << 23);   // 2^sg
+        float sx = 0.f, se = 0.f, sp[3] = {0.f, 0.f, 0.f};
+        for (int k0 = lane * 4; k0 < K8; k0 += 128) {
+            const float4 v = k0 < d ? xr[k0 / 4] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float xv[4] = {v.x, v.y, v.z, v.w};
+            uint32_t w[3] = {0u, 0u, 0u};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float x = k0 + e < d ? xv[e] * sc : 0.f;
+                sx = __fmaf_ru(x, x, sx);
+                float rem = x;
+#pragma unroll
+                for (int p = 0; p < NSPLIT; ++p) {
+                    const uint32_t b = __nv_cvt_float_to_fp8(rem, __NV_SATFINITE, __NV_E4M3);
+                    const float pv = e4m3_value(b);
+                    rem -= pv;                         // exact (pv within a factor 2 of rem, or 0)
+                    sp[p] = __fmaf_ru(pv, pv, sp[p]);
+                    w[p] |= b << (8 * e);
+                }
+                se = __fmaf_ru(rem, rem, se);
+            }
+            *reinterpret_cast<uint32_t *>(p0 + r * K8 + k0) = w[0];
+            *reinterpret_cast<uint32_t *>(p1 + r * K8 + k0) = w[1];
+            if (NSPLIT == 3) *reinterpret_cast<uint32_t *>(p2 + r * K8 + k0) = w[2];
+        }
+        sx = warp_sum_ru(sx);
+        se = warp_sum_ru(se);
+#pragma unroll
+        for (int p = 0; p < NSPLIT; ++p) sp[p] = warp_sum_ru(sp[p]);
+        if (lane == 0) {
+            const float nx = __fsqrt_ru(sx);
+            // + 2^-100 covers scaling underflow of tiny elements (s < 0)
+            const float ne = __fadd_ru(__fsqrt_ru(se), 0x1p-100f);
+            float np[3], nsum = 0.f;
+#pragma unroll
+            for (int p = 0; p < NSPLIT; ++p) {
+                np[p] = __fsqrt_ru(sp[p]);
+                nsum = __fadd_ru(nsum, np[p]);
+            }
+            uint16_t f[16];
+#pragma unroll
+            for (int t = 0; t < 16; ++t) f[t] = 0;
+            const uint16_t one = bf16_bits(__float2bfloat16_rn(sc));   // exact power of two
+            uint16_t sp3[3];
+            if (!query_side) {
+                split3(-(1.0 - ch) * (double)hx[r] * (double)sc, sp3);
+                for (int t = 0; t < 3; ++t) {
+                    f[t] = sp3[t];
+                    f[3 + t] = one;
+                }
+                f[6] = bf16_up(nsum);
+                f[7] = bf16_up(nx);
+                f[8] = bf16_up(ne);
+                if (NP == 3) f[9] = bf16_up(np[1]);
+                if (NP == 6) {
+                    f[9] = bf16_up(np[1]);
+                    f[10] = bf16_up(np[2]);
+                }
+            } else {
+                const double infl = 1.0 + 2.0 * kacc;
+                split3(Aq[r] * (double)sc, sp3);
+                for (int t = 0; t < 3; ++t) {
+                    f[t] = one;
+                    f[3 + t] = sp3[t];
+                }
+                f[6] = bf16_up(kacc * (double)nsum * infl);
+                f[7] = bf16_up((double)ne * infl);
+                f[8] = bf16_up(((double)nx + (double)ne) * infl);
+                if (NP == 3) f[9] = bf16_up((double)np[1] * infl);
+                if (NP == 6) {
+                    f[9] = bf16_up((double)np[2] * infl);
+                    f[10] = bf16_up(((double)np[1] + (double)np[2]) * infl);
+                }
+            }
+            uint4 *fo = reinterpret_cast<uint4 *>(fold + r * 16);
+            const uint32_t *fw = reinterpret_cast<const uint32_t *>(f);
+            fo[0] = make_uint4(fw[0], fw[1], fw[2], fw[3]);
+            fo[1] = make_uint4(fw[4], fw[5], fw[6], fw[7]);
+        }
+    }
+}
+
 // A'_i >= (Rx + e_data + e_i)^2/2 - ||y_i||^2/2, inflated so that its split
 // representation and the accumulation rounding (delta) keep the sign test
 // conservative, plus a margin that makes an acceptable pair's acc positive.
 __global__ void k_tc_query_consts(const float *__restrict__ hy, const float *__restrict__ qn,
                                   int64_t m, int d, double Rx, double e_data, double delta,
-                                  double *__restrict__ Aq) {
+                                  double margin, double *__restrict__ Aq) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= m) return;
     const double ei = 1.0001 * (double)kU32 * (double)qn[i];
@@ -647,7 +838,7 @@ __global__ void k_tc_query_consts(const float *__restrict__ hy, const float *__r
     double A = 0.5 * r * r - hy_low;
     A += 4.0 * kU64 * (fabs(A) + 0.5 * r * r + (double)hy[i]);
     A = A >= 0.0 ? A / (1.0 - delta) : A / (1.0 + delta);
-    A += 0x1p-22 * fabs(A) + 0x1p-100;
+    A += 0x1p-22 * fabs(A) + margin;
     Aq[i] = A;
 }
 
@@ -666,25 +857,14 @@ double tc_constant(int nsplit, int d, double *u_k_out) {
     return 1.02 * (c_mn > c_hx ? c_mn : c_hx);
 }
 
-template <int NSPLIT, int BK, int BN, bool ARES, int CPS, int NW, int MT>
-snn_status launch_tc(const snn_index *ix, const ScoreArgs &sa, const uint16_t *const *qp,
-                     int K2, int K2n, const TileSet &ts, cudaStream_t s) {
-    using Sh = TcShape<NSPLIT, BK, BN, ARES, CPS, NW, MT>;
-    CUtensorMap maps[6];
-    for (int p = 0; p < 3; ++p) {
-        const int pp = p < NSPLIT ? p : 0;
-        const int k2 = pp == 0 ? K2 : K2n, box = pp == 0 ? BK : NW;
-        SNN_TRY(make_map(&maps[p], qp[pp], sa.q.m, k2, box, kTM * MT));
-        SNN_TRY(make_map(&maps[3 + p], ix->tc_part[pp], ix->n, k2, box, BN));
-    }
-    auto kern = k_score_tc<NSPLIT, BK, BN, ARES, CPS, NW, MT>;
-    SNN_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::kSmem)));
+// Work list, survivor output and error flag of a scoring launch.
+TcArgs tc_args(const snn_index *ix, const ScoreArgs &sa, const TileSet &ts) {
     TcArgs a;
     a.m = sa.q.m;
     a.n = ix->n;
-    a.ksteps = int(cdiv(ix->d + kExtra, 16));
-    a.ksteps_data = int(cdiv(ix->d, 16));
-    a.nkb = K2 / BK;
+    a.ksteps = 0;
+    a.ksteps_data = 0;
+    a.nkb = 0;
     a.tile_lo = ts.lo;
     a.tile_hi = ts.hi;
     a.item_off = ts.item_off;
@@ -696,13 +876,147 @@ snn_status launch_tc(const snn_index *ix, const ScoreArgs &sa, const uint16_t *c
     a.count = sa.count;
     a.err = sa.err;
     a.stall = take_injected_fault() == SNN_FAULT_STALL_TC_PRODUCER ? 1 : 0;
-    SNN_LAUNCH(kern, device_sm_count() * CPS, Sh::kThreads, Sh::kSmem, s)(maps[0], maps[1], maps[2],
-                                                                 maps[3], maps[4], maps[5], a);
+    return a;
+}
+
+// maps: query parts 1-3, data parts 1-3, query folded, data folded
+template <int NSPLIT, int BK, int BN, bool ARES, int CPS, int NW, int MT, int F8NP>
+snn_status run_tc(const CUtensorMap (&maps)[8], const TcArgs &a, cudaStream_t s) {
+    using Sh = TcShape<NSPLIT, BK, BN, ARES, CPS, NW, MT, F8NP>;
+    auto kern = k_score_tc<NSPLIT, BK, BN, ARES, CPS, NW, MT, F8NP>;
+    SNN_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::kSmem)));
+    SNN_LAUNCH(kern, device_sm_count() * CPS, Sh::kThreads, Sh::kSmem, s)(
+        maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], maps[6], maps[7], a);
     SNN_LAUNCH_CHECK();
     return SNN_OK;
 }
 
+template <int NSPLIT, int BK, int BN, bool ARES, int CPS, int NW, int MT>
+snn_status launch_tc(const snn_index *ix, const ScoreArgs &sa, const uint16_t *const *qp,
+                     int K2, int K2n, const TileSet &ts, cudaStream_t s) {
+    CUtensorMap maps[8];
+    for (int p = 0; p < 3; ++p) {
+        const int pp = p < NSPLIT ? p : 0;
+        const int k2 = pp == 0 ? K2 : K2n, box = pp == 0 ? BK : NW;
+        SNN_TRY(make_map(&maps[p], qp[pp], sa.q.m, k2, box, kTM * MT));
+        SNN_TRY(make_map(&maps[3 + p], ix->tc_part[pp], ix->n, k2, box, BN));
+    }
+    maps[6] = maps[0];   // no folded block of its own
+    maps[7] = maps[3];
+    TcArgs a = tc_args(ix, sa, ts);
+    a.ksteps = int(cdiv(ix->d + kExtra, 16));
+    a.ksteps_data = int(cdiv(ix->d, 16));
+    a.nkb = K2 / BK;
+    return run_tc<NSPLIT, BK, BN, ARES, CPS, NW, MT, 0>(maps, a, s);
+}
+
+// FP8 shape: 128 queries x 256 band rows, k-blocks of 2 BK bytes per row (BK
+// 16-bit pairs; one or two e4m3 K = 32 steps of F8NP products each; a block
+// that reaches past the row is zero-filled by the copy), then the folded BF16
+// block.  64-byte blocks halve the copy's row requests per MMA, which is what
+// bounds the two-part variants with 32-byte blocks.
+template <int NSPLIT, int F8NP, int BK>
+snn_status launch_f8(const snn_index *ix, const ScoreArgs &sa, uint8_t *const *qp,
+                     const uint16_t *qfold, int K8, const TileSet &ts, cudaStream_t s) {
+    CUtensorMap maps[8];
+    for (int p = 0; p < 3; ++p) {
+        const int pp = p < NSPLIT ? p : 0;
+        // e4m3 rows as 16-bit pairs: K8 / 2 elements, boxes of BK pairs
+        SNN_TRY(make_map(&maps[p], reinterpret_cast<const uint16_t *>(qp[pp]), sa.q.m, K8 / 2, BK, kTM));
+        SNN_TRY(make_map(&maps[3 + p], reinterpret_cast<const uint16_t *>(ix->f8_part[pp]), ix->n,
+                         K8 / 2, BK, 256));
+    }
+    SNN_TRY(make_map(&maps[6], qfold, sa.q.m, 16, 16, kTM));
+    SNN_TRY(make_map(&maps[7], ix->f8_fold, ix->n, 16, 16, 256));
+    TcArgs a = tc_args(ix, sa, ts);
+    a.ksteps_data = K8 / 32;
+    a.nkb = int(cdiv(K8, 2 * BK)) + 1;
+    return run_tc<NSPLIT, BK, 256, false, 1, BK, 1, F8NP>(maps, a, s);
+}
+
 }  // namespace
+
+bool f8_eligible(const snn_index *ix, double Rx) {
+    return ix->d + kExtra > 64 && double(ix->nrm_max) <= 0x1p20 && Rx <= 0x1p20;
+}
+
+snn_status f8_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream_t s, double Rx,
+                           double e_data, Scratch &scr, int64_t *mma_flops_per_pair) {
+    snn_index *ix = const_cast<snn_index *>(ixc);
+    const int d = ix->d;
+    // products per k-step: 6 by default (three parts: a bound close to the
+    // two-part BF16 split's at the same tensor time); 4 (two parts with
+    // x_2.y_2 kept) or 3 (two parts) on request, which score faster but send
+    // more pairs to the exact decision
+    int np = 6;
+    if (const char *e = getenv("SNN_FP8_PRODUCTS")) {
+        const int v = atoi(e);
+        if (v == 3 || v == 4 || v == 6) np = v;
+    }
+    const int nsplit = np == 6 ? 3 : 2;
+    const int K8 = int(cdiv(d, 32) * 32);
+    const int ksteps = K8 / 32;
+    // accumulation: every instruction (e4m3 or the folded BF16 step) is
+    // charged 2^-20 of its input accumulator plus its products
+    const int ninstr = ksteps * np + 1;
+    const double kacc = 0x1p-20 * (ninstr + 1);
+    // halved norm: its FP32 evaluation, its 3-part split, the accumulation
+    const double ch = 1.02 * (0x1p-23 + 1.05 * (d + 2) * 0x1p-24 + kacc);
+    const int pack_threads = 256;
+    auto pack_grid = [&](int64_t rows) {
+        return unsigned(std::min<int64_t>(cdiv(rows, pack_threads / 32), int64_t(16) * device_sm_count()));
+    };
+    auto packer = np == 3 ? k_f8_pack<2, 3> : (np == 4 ? k_f8_pack<2, 4> : k_f8_pack<3, 6>);
+    {
+        std::lock_guard<std::mutex> lk(ix->mu);
+        if (ix->f8_nsplit != nsplit || ix->f8_np != np || ix->f8_k8 != K8) {
+            for (int p = 0; p < 3; ++p) {
+                if (ix->f8_part[p]) cudaFreeAsync(ix->f8_part[p], s);
+                ix->f8_part[p] = nullptr;
+            }
+            if (ix->f8_fold) cudaFreeAsync(ix->f8_fold, s);
+            ix->f8_fold = nullptr;
+            ix->f8_nsplit = 0;
+            cudaError_t e = cudaSuccess;
+            for (int p = 0; p < nsplit && e == cudaSuccess; ++p)
+                e = cudaMallocAsync(reinterpret_cast<void **>(&ix->f8_part[p]), size_t(ix->n) * K8, s);
+            if (e == cudaSuccess)
+                e = cudaMallocAsync(reinterpret_cast<void **>(&ix->f8_fold),
+                                    size_t(ix->n) * 16 * sizeof(uint16_t), s);
+            if (e != cudaSuccess) {
+                set_error("FP8 operand allocation failed: %s", cudaGetErrorString(e));
+                return SNN_ENOMEM;
+            }
+            SNN_LAUNCH(packer, pack_grid(ix->n), pack_threads, 0, s)(
+                ix->xc, ix->dp, ix->hx, nullptr, ix->n, d, K8, ch, kacc, 0, ix->f8_part[0],
+                ix->f8_part[1], ix->f8_part[2], ix->f8_fold);
+            SNN_LAUNCH_CHECK();
+            ix->f8_nsplit = nsplit;
+            ix->f8_np = np;
+            ix->f8_k8 = K8;
+        }
+    }
+    if (mma_flops_per_pair) *mma_flops_per_pair = int64_t(2) * 32 * np * ksteps + 2 * 16;
+    const int64_t m = sa.q.m;
+    double *Aq;
+    uint8_t *qp[3] = {nullptr, nullptr, nullptr};
+    uint16_t *qfold;
+    SNN_TRY(scr.alloc(&Aq, m));
+    for (int p = 0; p < nsplit; ++p) SNN_TRY(scr.alloc(&qp[p], size_t(m) * K8));
+    SNN_TRY(scr.alloc(&qfold, size_t(m) * 16));
+    // a margin of 2^-60 keeps A'_i 2^(s_x + s_y) a normal FP32 number
+    SNN_LAUNCH(k_tc_query_consts, unsigned(cdiv(m, 256)), 256, 0, s)(
+        sa.q.hx, sa.q.nrm, m, d, Rx, e_data, 0x1p-23 + kacc, 0x1p-60, Aq);
+    SNN_LAUNCH_CHECK();
+    SNN_LAUNCH(packer, pack_grid(m), pack_threads, 0, s)(sa.q.xc, ix->dp, nullptr, Aq, m, d, K8, ch,
+                                                        kacc, 1, qp[0], qp[1], qp[2], qfold);
+    SNN_LAUNCH_CHECK();
+    TileSet ts1{sa.tile_lo, sa.tile_hi, sa.item_off, sa.item_tile, sa.ntiles};
+    // 64-byte k-blocks: four stages of 48 KB (two parts) or three of 72 KB
+    if (np == 3) return launch_f8<2, 3, 32>(ix, sa, qp, qfold, K8, ts1, s);
+    if (np == 4) return launch_f8<2, 4, 32>(ix, sa, qp, qfold, K8, ts1, s);
+    return launch_f8<3, 6, 32>(ix, sa, qp, qfold, K8, ts1, s);
+}
 
 snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream_t s,
                            double Rx, double e_data, Scratch &scr, int64_t *mma_flops_per_pair) {
@@ -762,7 +1076,7 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
     SNN_TRY(scr.alloc(&Aq, m));
     for (int p = 0; p < nsplit; ++p) SNN_TRY(scr.alloc(&qp[p], size_t(m) * (p == 0 ? K2 : K2n)));
     SNN_LAUNCH(k_tc_query_consts, unsigned(cdiv(m, 256)), 256, 0, s)(
-        sa.q.hx, sa.q.nrm, m, d, Rx, e_data, 0x1p-23 + u_k, Aq);
+        sa.q.hx, sa.q.nrm, m, d, Rx, e_data, 0x1p-23 + u_k, 0x1p-100, Aq);
     SNN_LAUNCH_CHECK();
     auto packer = nsplit == 2 ? k_tc_pack<2> : k_tc_pack<3>;
     SNN_LAUNCH(packer, unsigned(cdiv(cdiv(m, 32) * 32, 256)), 256, 0, s)(sa.q.xc, ix->dp, sa.q.hx,

@@ -17,4 +17,11 @@ namespace snn {
 snn_status tc_score_launch(const snn_index *ix, const ScoreArgs &a, cudaStream_t s, double Rx,
                            double e_data, Scratch &scr, int64_t *mma_flops_per_pair);
 
+// FP8 e4m3 variant of tc_score_launch (per-row power-of-two scales, folded
+// per-pair error bound).  Available where f8_eligible holds: the streamed
+// high-dimensional shape (d + 9 > 64) with norms and radius below 2^20.
+bool f8_eligible(const snn_index *ix, double Rx);
+snn_status f8_score_launch(const snn_index *ix, const ScoreArgs &a, cudaStream_t s, double Rx,
+                           double e_data, Scratch &scr, int64_t *mma_flops_per_pair);
+
 }  // namespace snn

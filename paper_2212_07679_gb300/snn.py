@@ -37,7 +37,8 @@ class StatsStruct(ctypes.Structure):
                 ("survivors", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("exact_fp64", ctypes.c_int64), ("mma_flops_per_pair", ctypes.c_int64),
                 ("ms_prep", ctypes.c_float), ("ms_score", ctypes.c_float),
-                ("ms_recheck", ctypes.c_float), ("ms_csr", ctypes.c_float)]
+                ("ms_recheck", ctypes.c_float), ("ms_csr", ctypes.c_float),
+                ("precision_used", ctypes.c_int32)]
 
 
 class ViewStruct(ctypes.Structure):
