@@ -290,22 +290,23 @@ def run_ours(args):
         if args.precision == "bf16" and w.d > 55:
             fp8_variants = [time_precision("fp8", k) for k in (3, 4, 6)]
 
-    # end to end through host buffers: pinned X in, CSR out, every step
+    # end to end through host buffers: pinned X in, CSR out into reused
+    # pinned buffers (CSR.to_host), every step; one untimed pass sizes them
     e2e_ms, h2d, d2h = [], 0, 0
-    for _ in range(max(1, min(args.steps, 3))):
+    hbufs = snn.HostBuffers()
+    for it in range(1 + max(1, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         Xd = X_host.to("cuda", non_blocking=True)
         ix = snn.Index(Xd)
         out = ix.query(None, w.R, precision=args.precision)
-        off_h = out.offsets.cpu()
-        idx_h = out.indices.cpu()
-        d2_h = out.dist2.cpu()
+        host = out.to_host(hbufs)
         torch.cuda.synchronize()
-        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        if it > 0:
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
         h2d = X_host.numel() * 4
-        d2h = off_h.numel() * 8 + idx_h.numel() * 4 + d2_h.numel() * 4
-        del ix, out, Xd
+        d2h = host.offsets.numel() * 8 + host.indices.numel() * 4 + host.dist2.numel() * 4
+        del ix, out, Xd, host
 
     st = stats_list[-1]
     peaks, src = load_peaks()
@@ -452,6 +453,29 @@ def run_ragged(args):
     ms_loop_query = timed(loop_query, max(3, min(args.steps, 5)))
     clk = clocks.stop()
     got = plan.result()
+    # end to end: every set's points and queries from pinned host memory,
+    # batched build, one plan run, every result copied into pinned buffers
+    Xh = [torch.from_numpy(s.P).pin_memory() for s in sets]
+    Qh = [torch.from_numpy(s.Q).pin_memory() for s in sets]
+    hb = [snn.HostBuffers() for _ in sets]
+    e2e_ms, d2h = [], 0
+    for it in range(1 + max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xd = [x.to("cuda", non_blocking=True) for x in Xh]
+        ex = snn.build_batch(xd)
+        ep = snn.BatchPlan(ex, [q.shape[0] for q in Qh], Rs, survivor_capacity=64 * M + (1 << 20),
+                           nnz_capacity=64 * M + (1 << 20))
+        for t, q in enumerate(Qh):
+            ep.queries(t).copy_(q, non_blocking=True)
+        ep.run()
+        outs = [o.to_host(b) for o, b in zip(ep.result(copy=False), hb)]
+        torch.cuda.synchronize()
+        if it > 0:
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        d2h = sum(o.offsets.numel() * 8 + o.nnz * 8 for o in outs)
+        ep.close()
+        del xd, ex, ep, outs
     line = {
         "metric": "ragged batch exact radius queries/s (batched index build + one batched query)",
         "value": M / (ms_step / 1e3), "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
@@ -466,6 +490,9 @@ def run_ragged(args):
                         "per_set_calls_queries_per_s": M / (ms_loop_query / 1e3),
                         "tuned": {"chunks_per_item": cpi, "ctas_per_sm": ctas}},
         "clocks": clk, "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
+        "e2e": {"value": M / (np.median(e2e_ms) / 1e3), "unit": "queries/s",
+                "h2d_bytes_per_step": int(sum(x.numel() + q.numel() for x, q in zip(Xh, Qh)) * 4),
+                "d2h_bytes_per_step": int(d2h)},
     }
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_ragged(sets, got, budget_s=args.ref_budget)
@@ -530,6 +557,22 @@ def run_dbscan(args):
     launches = snn.launch_count() - l0
     clk = clocks.stop()
     ms = float(np.mean(ts))
+    # end to end: pinned points in, labels and core flags out into pinned
+    # buffers, every step
+    X_host = torch.from_numpy(w.P).pin_memory()
+    lab_h = torch.empty(w.n, dtype=torch.int32, pin_memory=True)
+    core_h = torch.empty(w.n, dtype=torch.uint8, pin_memory=True)
+    e2e_ms = []
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Xd = X_host.to("cuda", non_blocking=True)
+        lb, cr = snn.dbscan(Xd, eps, min_pts, precision=args.precision)
+        lab_h.copy_(lb, non_blocking=True)
+        core_h.copy_(cr, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        del Xd, lb, cr
     lab = labels.cpu().numpy()
     line = {
         "metric": "DBSCAN points/s (exact eps-neighbourhoods by SNN self-join, union-find labels)",
@@ -543,6 +586,9 @@ def run_dbscan(args):
         "clusters": int(len(np.unique(lab[lab >= 0]))), "core_points": int(core.sum().item()),
         "noise_points": int((lab < 0).sum()),
         "clocks": clk, "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
+        "e2e": {"value": w.n / (np.median(e2e_ms) / 1e3), "unit": "points/s",
+                "h2d_bytes_per_step": int(X_host.numel() * 4),
+                "d2h_bytes_per_step": int(w.n * 4 + w.n)},
     }
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample(w, budget_s=args.ref_budget)

@@ -603,9 +603,10 @@ __device__ __forceinline__ void split3(double w, uint16_t (&o)[3]) {
 // Rows of an operand: split parts of the centred row, then the folded
 // columns (data side: -(1-c) xbar_j split, ||x_j|| rounded up three times,
 // ones; query side: ones, c ||y_i|| split, A'_i split).  One warp per 32
-// rows: the data columns row by row with the lanes over the columns
-// (coalesced 2-byte stores), the folded columns with one lane per row (their
-// few FP64 operations then run on full warps).
+// rows: the data columns as a flat run of (row, 4-column quad) items over
+// the lanes, eight loads in flight per lane before the conversions (float4
+// loads, 8-byte stores, coalesced in both arrays), then the folded columns
+// with one lane per row (their few FP64 operations then run on full warps).
 template <int NSPLIT>
 __global__ void k_tc_pack(const float *__restrict__ xc, int dp, const float *__restrict__ hx,
                           const float *__restrict__ nrm, const double *__restrict__ Aq,
@@ -616,25 +617,34 @@ __global__ void k_tc_pack(const float *__restrict__ xc, int dp, const float *__r
     const int lane = threadIdx.x & 31;
     if (r0 >= rows) return;   // whole warps leave together
     const int nr = int(min(int64_t(32), rows - r0));
-    // data columns, four per lane (float4 loads, 8-byte stores); the lanes of
-    // a warp cover lpr = min(32, K2 / 4) quads of one row and 32 / lpr rows at
-    // a time.  Quads over the folded columns are written as zeros here and
-    // overwritten below (after __syncwarp).
-    const int lpr = K2 / 4 < 32 ? K2 / 4 : 32;
-    const int rpi = 32 / lpr;
-    const int sub = lane / lpr, ql = lane % lpr;
-    for (int rr = sub; rr < nr; rr += rpi) {
-        const int64_t r = r0 + rr;
-        const float4 *xr4 = reinterpret_cast<const float4 *>(xc + r * dp);
-        for (int k0 = ql * 4; k0 < K2; k0 += lpr * 4) {
-            const float4 x4 = k0 < dp ? xr4[k0 / 4] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
+    // quads over the folded columns are written as zeros here and
+    // overwritten below (after __syncwarp)
+    const int nq = K2 / 4;                 // quads per packed row
+    const int total = nr * nq;
+    constexpr int U = 8;
+    for (int base = 0; base < total; base += 32 * U) {
+        float4 xv[U];
+#pragma unroll
+        for (int t = 0; t < U; ++t) {
+            const int it = base + t * 32 + lane;
+            const int rr = it / nq, k0 = (it - rr * nq) * 4;
+            xv[t] = (it < total && k0 < dp)
+                        ? reinterpret_cast<const float4 *>(xc + (r0 + rr) * dp)[k0 / 4]
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int t = 0; t < U; ++t) {
+            const int it = base + t * 32 + lane;
+            if (it >= total) break;
+            const int rr = it / nq, k0 = (it - rr * nq) * 4;
+            const int64_t r = r0 + rr;
+            const float xs[4] = {xv[t].x, xv[t].y, xv[t].z, xv[t].w};
             uint16_t v0[4], v1[4], v2[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 v0[e] = v1[e] = v2[e] = 0;
                 if (k0 + e < d) {
-                    const float x = xv[e];
+                    const float x = xs[e];
                     const __nv_bfloat16 h = __float2bfloat16_rn(x);
                     const float xr1 = x - __bfloat162float(h);               // exact
                     const __nv_bfloat16 l = __float2bfloat16_rn(xr1);
@@ -724,15 +734,29 @@ __global__ void k_f8_pack(const float *__restrict__ xc, int dp, const float *__r
                           uint16_t *__restrict__ fold) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    constexpr int U = 8;                   // quads per lane in flight (1,024 columns a warp)
+    const bool one_chunk = K8 <= 128 * U;  // the row stays in registers between the passes
     for (int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; r < rows; r += nwarps) {
         const float4 *xr = reinterpret_cast<const float4 *>(xc + r * dp);
-        float mx = 0.f;
-        for (int k0 = lane * 4; k0 < d; k0 += 128) {
-            const float4 v = xr[k0 / 4];
-            const float xv[4] = {v.x, v.y, v.z, v.w};
+        float4 xv[U];
+        auto load = [&](int kc) {
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (k0 + e < d) mx = fmaxf(mx, fabsf(xv[e]));
+            for (int t = 0; t < U; ++t) {
+                const int k0 = kc + (lane + 32 * t) * 4;
+                xv[t] = k0 < d ? xr[k0 / 4] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        };
+        float mx = 0.f;
+        for (int kc = 0; kc < d; kc += 128 * U) {
+            load(kc);
+#pragma unroll
+            for (int t = 0; t < U; ++t) {
+                const int k0 = kc + (lane + 32 * t) * 4;
+                const float xs[4] = {xv[t].x, xv[t].y, xv[t].z, xv[t].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (k0 + e < d) mx = fmaxf(mx, fabsf(xs[e]));
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -744,28 +768,33 @@ __global__ void k_f8_pack(const float *__restrict__ xc, int dp, const float *__r
         }
         const float sc = __uint_as_float(uint32_t(127 + sg) << 23);   // 2^sg
         float sx = 0.f, se = 0.f, sp[3] = {0.f, 0.f, 0.f};
-        for (int k0 = lane * 4; k0 < K8; k0 += 128) {
-            const float4 v = k0 < d ? xr[k0 / 4] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float xv[4] = {v.x, v.y, v.z, v.w};
-            uint32_t w[3] = {0u, 0u, 0u};
+        for (int kc = 0; kc < K8; kc += 128 * U) {
+            if (!one_chunk) load(kc);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float x = k0 + e < d ? xv[e] * sc : 0.f;
-                sx = __fmaf_ru(x, x, sx);
-                float rem = x;
+            for (int t = 0; t < U; ++t) {
+                const int k0 = kc + (lane + 32 * t) * 4;
+                if (k0 >= K8) break;
+                const float xs[4] = {xv[t].x, xv[t].y, xv[t].z, xv[t].w};
+                uint32_t w[3] = {0u, 0u, 0u};
 #pragma unroll
-                for (int p = 0; p < NSPLIT; ++p) {
-                    const uint32_t b = __nv_cvt_float_to_fp8(rem, __NV_SATFINITE, __NV_E4M3);
-                    const float pv = e4m3_value(b);
-                    rem -= pv;                         // exact (pv within a factor 2 of rem, or 0)
-                    sp[p] = __fmaf_ru(pv, pv, sp[p]);
-                    w[p] |= b << (8 * e);
+                for (int e = 0; e < 4; ++e) {
+                    const float x = k0 + e < d ? xs[e] * sc : 0.f;
+                    sx = __fmaf_ru(x, x, sx);
+                    float rem = x;
+#pragma unroll
+                    for (int p = 0; p < NSPLIT; ++p) {
+                        const uint32_t b = __nv_cvt_float_to_fp8(rem, __NV_SATFINITE, __NV_E4M3);
+                        const float pv = e4m3_value(b);
+                        rem -= pv;                     // exact (pv within a factor 2 of rem, or 0)
+                        sp[p] = __fmaf_ru(pv, pv, sp[p]);
+                        w[p] |= b << (8 * e);
+                    }
+                    se = __fmaf_ru(rem, rem, se);
                 }
-                se = __fmaf_ru(rem, rem, se);
+                *reinterpret_cast<uint32_t *>(p0 + r * K8 + k0) = w[0];
+                *reinterpret_cast<uint32_t *>(p1 + r * K8 + k0) = w[1];
+                if (NSPLIT == 3) *reinterpret_cast<uint32_t *>(p2 + r * K8 + k0) = w[2];
             }
-            *reinterpret_cast<uint32_t *>(p0 + r * K8 + k0) = w[0];
-            *reinterpret_cast<uint32_t *>(p1 + r * K8 + k0) = w[1];
-            if (NSPLIT == 3) *reinterpret_cast<uint32_t *>(p2 + r * K8 + k0) = w[2];
         }
         sx = warp_sum_ru(sx);
         se = warp_sum_ru(se);

@@ -165,6 +165,36 @@ class CSR:
     def nnz(self) -> int:
         return self.indices.numel()
 
+    def to_host(self, buffers: "HostBuffers | None" = None, stream=None) -> "CSR":
+        """Copies the lists into pinned host memory (reused from `buffers` when
+        given) with asynchronous copies on `stream` (default: the current
+        stream), then waits for them.  Returns a CSR of host tensors."""
+        b = buffers if buffers is not None else HostBuffers()
+        off = b.take("offsets", self.offsets.numel(), torch.int64)
+        idx = b.take("indices", self.indices.numel(), torch.int32)
+        d2 = b.take("dist2", self.dist2.numel(), torch.float32)
+        s = stream if stream is not None else torch.cuda.current_stream(self.offsets.device)
+        with torch.cuda.stream(s):
+            off.copy_(self.offsets, non_blocking=True)
+            idx.copy_(self.indices, non_blocking=True)
+            d2.copy_(self.dist2, non_blocking=True)
+        s.synchronize()
+        return CSR(off, idx, d2, self.stats)
+
+
+class HostBuffers:
+    """Pinned host storage for CSR.to_host, grown on demand and reused."""
+
+    def __init__(self):
+        self._bufs = {}
+
+    def take(self, name: str, n: int, dtype) -> torch.Tensor:
+        t = self._bufs.get(name)
+        if t is None or t.numel() < n or t.dtype != dtype:
+            t = torch.empty(max(1, n + n // 4), dtype=dtype, pin_memory=True)
+            self._bufs[name] = t
+        return t[:n]
+
 
 def _csr_from(cs: CSRStruct, device, stats=None) -> CSR:
     off = _wrap(cs.offsets, cs.m + 1, "<i8", torch.int64, device)

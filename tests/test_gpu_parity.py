@@ -433,3 +433,21 @@ def test_full_size_ragged_batch_sampled(snn):
         rows = rng.choice(s.m, size=min(2, s.m), replace=False)
         _check_sampled_rows(got, s.P, s.Q, s.R, rows)
         assert got.m == s.m
+
+
+def test_to_host_pinned_copies(snn):
+    """CSR.to_host copies into pinned, reused host buffers; the copies equal
+    the device arrays, and a larger result regrows the buffers."""
+    rng = np.random.default_rng(71)
+    P = rng.standard_normal((3000, 5)).astype(np.float32)
+    ix = snn.Index(_dev(P))
+    bufs = snn.HostBuffers()
+    for R in (0.5, 1.2, 0.8):
+        out = ix.query(None, R, precision="bf16")
+        host = out.to_host(bufs)
+        assert host.offsets.is_pinned() and host.indices.is_pinned() and host.dist2.is_pinned()
+        assert host.nnz == out.nnz and host.m == out.m
+        assert np.array_equal(host.offsets.numpy(), out.offsets.cpu().numpy())
+        assert np.array_equal(host.indices.numpy(), out.indices.cpu().numpy())
+        assert np.array_equal(host.dist2.numpy().view(np.uint32), out.dist2.cpu().numpy().view(np.uint32))
+        assert_csr_equal(out, oracle.brute_radius(P, None, R), f"R={R}")
