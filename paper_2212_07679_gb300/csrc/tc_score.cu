@@ -351,6 +351,7 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                         if (!(ok = mbar_wait(full_bar(s), round & 1u, s_abort, a.err))) break;
                         tmem_fence_after();
                         if constexpr (F8NP != 0) {
+                            static_assert(Sh::kRowBytesN == Sh::kRowBytes, "FP8 parts share one width");
                             if (kb == a.nkb - 1) {
                                 // the folded columns: one BF16 K = 16 step
                                 mma_bf16(dt0, smem_desc<32>(a_tile(s, 0)), smem_desc<32>(b_tile(s, 0)),
@@ -368,33 +369,31 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                                                  kIdesc8, (kg | pr) != 0 ? 1u : 0u);
                                 }
                             }
-                            mma_commit(empty_bar(s));
-                            *s_consumed = it + 1;
-                            continue;
-                        }
+                        } else {
 #pragma unroll
-                        for (int ks = 0; ks < Sh::kKSteps; ++ks) {
-                            const int kg = kb * Sh::kKSteps + ks;
-                            if (kg >= a.ksteps) break;
-                            // the folded columns live in part 0 only: a k step
-                            // without data columns needs the (0,0) product alone
-                            const int np = kg < a.ksteps_data ? NP : 1;
+                            for (int ks = 0; ks < Sh::kKSteps; ++ks) {
+                                const int kg = kb * Sh::kKSteps + ks;
+                                if (kg >= a.ksteps) break;
+                                // the folded columns live in part 0 only: a k step
+                                // without data columns needs the (0,0) product alone
+                                const int np = kg < a.ksteps_data ? NP : 1;
 #pragma unroll
-                            for (int pr = 0; pr < NP; ++pr) {
-                                if (pr >= np) break;
-                                const uint32_t bb = b_tile(s, kPb[pr]) + 32u * ks;
-                                const uint64_t bd = kPb[pr] == 0 ? smem_desc<Sh::kRowBytes>(bb)
-                                                                 : smem_desc<Sh::kRowBytesN>(bb);
+                                for (int pr = 0; pr < NP; ++pr) {
+                                    if (pr >= np) break;
+                                    const uint32_t bb = b_tile(s, kPb[pr]) + 32u * ks;
+                                    const uint64_t bd = kPb[pr] == 0 ? smem_desc<Sh::kRowBytes>(bb)
+                                                                     : smem_desc<Sh::kRowBytesN>(bb);
 #pragma unroll
-                                for (int h = 0; h < MT; ++h) {
-                                    // query sub-tile h: 128 rows further into the A tile
-                                    const uint32_t arow = kPa[pr] == 0 ? Sh::kRowBytes : Sh::kRowBytesN;
-                                    const uint32_t aa = a_tile(ARES ? aslot : s, kPa[pr]) +
-                                                        uint32_t(h * kTM) * arow + 32u * ks;
-                                    const uint64_t ad = kPa[pr] == 0 ? smem_desc<Sh::kRowBytes>(aa)
-                                                                     : smem_desc<Sh::kRowBytesN>(aa);
-                                    mma_bf16(dt0 + uint32_t(h * BN), ad, bd, kIdesc,
-                                             (kb | ks | pr) != 0 ? 1u : 0u);
+                                    for (int h = 0; h < MT; ++h) {
+                                        // query sub-tile h: 128 rows further into the A tile
+                                        const uint32_t arow = kPa[pr] == 0 ? Sh::kRowBytes : Sh::kRowBytesN;
+                                        const uint32_t aa = a_tile(ARES ? aslot : s, kPa[pr]) +
+                                                            uint32_t(h * kTM) * arow + 32u * ks;
+                                        const uint64_t ad = kPa[pr] == 0 ? smem_desc<Sh::kRowBytes>(aa)
+                                                                         : smem_desc<Sh::kRowBytesN>(aa);
+                                        mma_bf16(dt0 + uint32_t(h * BN), ad, bd, kIdesc,
+                                                 (kb | ks | pr) != 0 ? 1u : 0u);
+                                    }
                                 }
                             }
                         }
