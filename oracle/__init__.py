@@ -12,7 +12,10 @@ Contents:
                              independent implementation for small inputs);
 * ``pair_dist2``          -- the same definition for sampled (query, point) pairs;
 * ``cpu_snn``             -- Algorithms 1 and 2 in FP64 (plain CPU SNN);
-* ``dbscan``              -- DBSCAN on top of the brute-force neighbour lists.
+* ``dbscan``              -- DBSCAN on top of the brute-force neighbour lists;
+* ``cosine_radius``       -- cosine / angular search by the Euclidean reduction
+                             of Section 3 (``normalize_rows`` and the radius
+                             mappings).
 
 Pins (tests/test_oracle_*.py): hand cases under tests/golden/, exact
 invariants, the paper's printed return ratios (Tables 1 and 2) and the
@@ -23,7 +26,10 @@ from .brute import (brute_radius, brute_radius_numpy, pair_dist2, build_oracle,
                     oracle_threads, CSR)
 from .cpu_snn import SNNIndex, snn_index, snn_query, snn_radius
 from .dbscan import dbscan, dbscan_bfs
+from .cosine import (normalize_rows, radius_for_cosine_distance, radius_for_cosine_similarity,
+                     cosine_radius)
 
 __all__ = ["brute_radius", "brute_radius_numpy", "pair_dist2", "build_oracle",
            "oracle_threads", "CSR", "SNNIndex", "snn_index", "snn_query", "snn_radius",
-           "dbscan", "dbscan_bfs"]
+           "dbscan", "dbscan_bfs", "normalize_rows", "radius_for_cosine_distance",
+           "radius_for_cosine_similarity", "cosine_radius"]
