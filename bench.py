@@ -13,6 +13,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -97,13 +98,23 @@ def make_workload(args):
         return wl.lowrank_img(n=args.n) if args.n else wl.lowrank_img()
     if args.workload == "blobs3d":
         return wl.blobs3d(n=args.n) if args.n else wl.blobs3d()
+    if args.workload == "glove_like":
+        return wl.glove_like(n=args.n) if args.n else wl.glove_like()
     raise SystemExit(f"unknown workload {args.workload}")
+
+
+def is_cosine(w):
+    return w.extra.get("measure") == "cosine distance"
 
 
 def workload_config(args, w, extra=None):
     cfg = {"workload": f"{w.name} self-join", "n": w.n, "d": w.d, "queries": w.m,
            "R": w.R, "precision": args.precision, "parallelism": f"replicas{args.gpus}",
            "l2": "flushed between steps (256 MiB write)"}
+    if is_cosine(w):
+        cfg["workload"] = f"{w.name} cosine self-join (rows normalised inside the step)"
+        cfg["cosine_distance_bound"] = w.R
+        cfg["R"] = math.sqrt(2.0 * w.R)
     if extra:
         cfg.update(extra)
     return cfg
@@ -118,13 +129,17 @@ def cpu_oracle_sample(w, budget_s=15.0, seed=7, gpu_csr=None):
     import oracle
     rng = np.random.default_rng(seed)
     order = rng.permutation(w.m)
-    Qall = w.P if w.Q is None else w.Q
+    P, R = w.P, w.R
+    if is_cosine(w):
+        # the Euclidean search on the oracle's normalised rows
+        P, R = oracle.normalize_rows(w.P), oracle.radius_for_cosine_distance(w.R)
+    Qall = P if w.Q is None else w.Q
     done, t_used, size = 0, 0.0, 16
     mism, max_rel, checked_pairs = 0, 0.0, 0
     while t_used < budget_s and done < w.m:
         rows = order[done:done + size]
         t0 = time.perf_counter()
-        ref = oracle.brute_radius(w.P, Qall[rows], w.R)
+        ref = oracle.brute_radius(P, Qall[rows], R)
         dt = time.perf_counter() - t0
         t_used += dt
         done += len(rows)
@@ -196,11 +211,18 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
+    # cosine workloads: rows normalised on the device inside every step, and
+    # the Euclidean radius of the cosine-distance bound
+    Rq = snn.radius_for_cosine_distance(w.R) if is_cosine(w) else w.R
+
+    def index_of(Xd):
+        return snn.Index(snn.normalize_rows(Xd) if is_cosine(w) else Xd)
+
     def step(stats=True, e_mid=None):
-        ix = snn.Index(X)
+        ix = index_of(X)
         if e_mid is not None:
             e_mid.record(stream)
-        out = ix.query(None, w.R, precision=args.precision, stats=stats)
+        out = ix.query(None, Rq, precision=args.precision, stats=stats)
         return ix, out
 
     for _ in range(args.warmup):
@@ -250,8 +272,8 @@ def run_ours(args):
             os.environ["SNN_FP8_PRODUCTS"] = str(products)
         try:
             for _ in range(2):
-                ix = snn.Index(X)
-                ix.query(None, w.R, precision=prec)
+                ix = index_of(X)
+                ix.query(None, Rq, precision=prec)
                 del ix
             times = []
             for _ in range(max(3, min(args.steps, 5))):
@@ -259,8 +281,8 @@ def run_ours(args):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                ix = snn.Index(X)
-                out = ix.query(None, w.R, precision=prec, stats=True)
+                ix = index_of(X)
+                out = ix.query(None, Rq, precision=prec, stats=True)
                 e1.record(stream)
                 e1.synchronize()
                 times.append(e0.elapsed_time(e1))
@@ -298,8 +320,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         Xd = X_host.to("cuda", non_blocking=True)
-        ix = snn.Index(Xd)
-        out = ix.query(None, w.R, precision=args.precision)
+        ix = index_of(Xd)
+        out = ix.query(None, Rq, precision=args.precision)
         host = out.to_host(hbufs)
         torch.cuda.synchronize()
         if it > 0:

@@ -58,11 +58,11 @@ typedef enum {
     SNN_PREC_FP8E4M3 = 2    /* FP8 e4m3 tcgen05 dot products, each row
                                scaled by its own power of two; used for
                                d > 55 with norms and R below 2^20, BF16
-                               elsewhere (see precision_used).  Three e4m3
-                               parts, six products per k-step; the
-                               environment variable SNN_FP8_PRODUCTS = 3 or
-                               4 selects two parts (faster scoring, wider
-                               bound)                                      */
+                               elsewhere (see precision_used).  Two e4m3
+                               parts (3 or 4 products per k-step) where the
+                               largest norm is within about 2R, else three
+                               (6 products); the environment variable
+                               SNN_FP8_PRODUCTS = 3, 4 or 6 overrides       */
 } snn_precision;
 
 /* Opaque index (Algorithm 1 output): mean mu, first principal direction v1,
@@ -172,6 +172,33 @@ snn_status snn_query_radius_batch(int32_t nsets, const snn_index *const *idx,
                                   const float *const *Q, const int64_t *m,
                                   const int64_t *ldq, const double *R,
                                   snn_precision prec, void *stream, snn_csr *out);
+
+/* Cosine and angular distances (Section 3): for unit vectors u, v the
+ * cosine distance 1 - u.v equals ||u - v||^2 / 2, and the angle between them
+ * is at most alpha exactly when ||u - v||^2 <= 2 - 2 cos(alpha).  A cosine or
+ * angular search is the Euclidean search (snn_index_build, snn_query_radius)
+ * on rows normalised by snn_normalize_rows, with the radius from
+ * snn_radius_for_cosine_distance or snn_radius_for_cosine_similarity; the
+ * returned dist2 is then twice the cosine distance of the normalised rows.
+ *
+ * snn_normalize_rows: row i of X becomes u_k = fl32(x_k * r), r =
+ * 1 / sqrt(sum over ascending k of x_k^2), all in FP64 with every operation
+ * rounded to nearest and no fused multiply-add; a row of zeros stays zero, a
+ * NaN or infinity makes its row NaN (which the index build then rejects).
+ *  X, out  device, n x d FP32 with row strides ld, ldo (elements, >= d); out
+ *          may be X (in place, ldo == ld).
+ *  stream  cudaStream_t; the call is stream-ordered and does not synchronise.
+ * Errors: SNN_EINVAL for n < 0, d < 1, ld or ldo < d, NULL arrays (n > 0);
+ * SNN_ECUDA if the launch fails. */
+snn_status snn_normalize_rows(const float *X, int64_t n, int32_t d, int64_t ld, float *out,
+                              int64_t ldo, void *stream);
+
+/* Radius of the Euclidean search on normalised rows: sqrt(2 c) for a cosine
+ * distance bound c in [0, 2]; sqrt(2 - 2 t) for a cosine similarity bound t
+ * in [-1, 1] (t = cos(alpha) for an angle bound alpha).  FP64, correctly
+ * rounded square root; NaN outside the ranges. */
+double snn_radius_for_cosine_distance(double c);
+double snn_radius_for_cosine_similarity(double t);
 
 /* DBSCAN with SNN as its neighbour search (Section 6.4).
  *  X        device, n x d FP32, stride ld.

@@ -972,11 +972,15 @@ snn_status f8_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
                            double e_data, Scratch &scr, int64_t *mma_flops_per_pair) {
     snn_index *ix = const_cast<snn_index *>(ixc);
     const int d = ix->d;
-    // products per k-step: 6 by default (three parts: a bound close to the
-    // two-part BF16 split's at the same tensor time); 4 (two parts with
-    // x_2.y_2 kept) or 3 (two parts) on request, which score faster but send
-    // more pairs to the exact decision
-    int np = 6;
+    // products per k-step: the cheapest split whose bound stays a small
+    // fraction of R^2.  Two parts leave about 2.5e-3 (three products) or
+    // 1.8e-3 (four, x_2.y_2 kept) of ||x|| ||y|| unresolved, three parts
+    // about 1e-4; twice that for the largest norms should stay within 1.5 %
+    // of R^2, which keeps the extra exact decisions small (normalised rows:
+    // three products; the 784-dim images, norms 3.5x R: six).
+    // SNN_FP8_PRODUCTS = 3, 4 or 6 overrides.
+    const double N2 = double(ix->nrm_max) * double(ix->nrm_max), R2r = Rx * Rx;
+    int np = N2 <= 3.0 * R2r ? 3 : (N2 <= 4.2 * R2r ? 4 : 6);
     if (const char *e = getenv("SNN_FP8_PRODUCTS")) {
         const int v = atoi(e);
         if (v == 3 || v == 4 || v == 6) np = v;

@@ -76,6 +76,12 @@ def _load():
     lib.snn_last_error.restype = ctypes.c_char_p
     lib.snn_version.argtypes = []
     lib.snn_version.restype = ctypes.c_char_p
+    lib.snn_normalize_rows.argtypes = [vp, i64, i32, i64, vp, i64, vp]
+    lib.snn_normalize_rows.restype = ctypes.c_int
+    lib.snn_radius_for_cosine_distance.argtypes = [f64]
+    lib.snn_radius_for_cosine_distance.restype = f64
+    lib.snn_radius_for_cosine_similarity.argtypes = [f64]
+    lib.snn_radius_for_cosine_similarity.restype = f64
     lib.snn_test_inject.argtypes = [ctypes.c_int32]
     lib.snn_test_inject.restype = ctypes.c_int
     lib.snn_launch_count.argtypes = []
@@ -290,6 +296,54 @@ def radius_search(X: torch.Tensor, Q: torch.Tensor | None, R: float, precision: 
                   stats: bool = False) -> CSR:
     """Index X and query every row of Q (None: self-join)."""
     return Index(X).query(Q, R, precision, stats)
+
+
+def normalize_rows(X: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Unit rows for cosine / angular search (Section 3): u = fl32(x r),
+    r = 1 / sqrt(sum of x_k^2) in FP64 (see snn_normalize_rows)."""
+    X, ld = _points(X, "X")
+    if out is None:
+        out = torch.empty_like(X)
+    o, ldo = _points(out, "out")
+    if o.shape != X.shape:
+        raise ValueError("out must have the shape of X")
+    with torch.cuda.device(X.device):
+        _check(lib.snn_normalize_rows(ctypes.c_void_p(X.data_ptr()), X.shape[0], X.shape[1], ld,
+                                      ctypes.c_void_p(o.data_ptr()), ldo, _stream_ptr(stream)))
+    return o
+
+
+def radius_for_cosine_distance(c: float) -> float:
+    """Euclidean radius on unit rows for cosine distance <= c: sqrt(2 c)."""
+    r = lib.snn_radius_for_cosine_distance(float(c))
+    if r != r:
+        raise ValueError("cosine distance bound must lie in [0, 2]")
+    return r
+
+
+def radius_for_cosine_similarity(t: float) -> float:
+    """Euclidean radius on unit rows for cosine similarity >= t (an angle
+    bound alpha: t = cos(alpha)): sqrt(2 - 2 t)."""
+    r = lib.snn_radius_for_cosine_similarity(float(t))
+    if r != r:
+        raise ValueError("cosine similarity bound must lie in [-1, 1]")
+    return r
+
+
+def cosine_radius_search(X: torch.Tensor, Q: torch.Tensor | None = None, *,
+                         cos_sim: float | None = None, cos_dist: float | None = None,
+                         precision: str = "bf16", stats: bool = False, stream=None) -> CSR:
+    """All rows of X within a cosine similarity (>= cos_sim) or cosine
+    distance (<= cos_dist) bound of each row of Q (None: self-join), by the
+    Euclidean search on normalised rows; dist2 is twice the cosine distance
+    of the normalised rows."""
+    if (cos_sim is None) == (cos_dist is None):
+        raise ValueError("give exactly one of cos_sim and cos_dist")
+    R = (radius_for_cosine_similarity(cos_sim) if cos_sim is not None
+         else radius_for_cosine_distance(cos_dist))
+    U = normalize_rows(X, stream=stream)
+    V = None if Q is None else normalize_rows(Q, stream=stream)
+    return Index(U, stream=stream).query(V, R, precision, stats, stream=stream)
 
 
 def query_batch(indices: list[Index], Qs: list[torch.Tensor | None], Rs: list[float],

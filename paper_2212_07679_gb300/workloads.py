@@ -15,7 +15,10 @@ used):
 * ``lowrank_img``   -- 784-dim images near a rank-20 subspace (n=70,000);
 * ``ragged_batch``  -- 256 independent mixtures of uneven n and d;
 * ``blobs3d``       -- 3-d particle blobs plus uniform noise (n=5e5, DBSCAN);
-* ``uniform_cube``  -- uniform points in [0,1]^d (the Section 6.1/6.2 data).
+* ``uniform_cube``  -- uniform points in [0,1]^d (the Section 6.1/6.2 data);
+* ``glove_like``    -- word-vector-like directions for cosine / angular search
+                       (a synthetic stand-in for the GloVe100 vectors of
+                       Section 6.3; R holds a cosine-distance bound).
 
 The radius for a workload is a quantile of the pairwise Euclidean distances
 of a seeded subsample (all i<j pairs, ``numpy.quantile`` default linear
@@ -186,8 +189,30 @@ def gaussian_blob(n: int, d: int, s: float, seed: int) -> np.ndarray:
     return (rng_for(seed).standard_normal((n, d)) * std[None, :]).astype(np.float32)
 
 
+def glove_like(n: int = 200_000, d: int = 100, clusters: int = 200, spread: float = 0.75,
+               nbrs: float = 20.0, sub: int = 4000, seed: int = SEED_BASE + 6) -> Workload:
+    """Direction data for cosine / angular search: cluster directions
+    N(0, I_d), members = direction + spread * N(0, I_d), each row scaled by a
+    log-normal magnitude (exp N(0, 0.5^2); the cosine ignores it); self-join.
+    R is a cosine-distance bound: the nbrs/(n-1) quantile of the i<j cosine
+    distances of a seeded subsample (scipy pdist, metric "cosine")."""
+    rng = rng_for(seed)
+    dirs = rng.standard_normal((clusters, d))
+    lab = rng.integers(0, clusters, size=n)
+    X = np.empty((n, d), dtype=np.float32)
+    step = 65536
+    for s0 in range(0, n, step):
+        e = min(n, s0 + step)
+        blk = dirs[lab[s0:e]] + spread * rng.standard_normal((e - s0, d))
+        X[s0:e] = blk * np.exp(0.5 * rng.standard_normal((e - s0, 1)))
+    k = min(sub, n)
+    idx = np.sort(rng.choice(n, size=k, replace=False))
+    c = float(np.quantile(pdist(X[idx].astype(np.float64), metric="cosine"), nbrs / (n - 1)))
+    return Workload("glove_like", X, None, c, extra={"labels": lab, "measure": "cosine distance"})
+
+
 def by_name(name: str, **kw):
     """Workload factory by name (sizes overridable for smaller parity cases)."""
     table = {"gmm_iso": gmm_iso, "gmm_aniso": gmm_aniso, "lowrank_img": lowrank_img,
-             "blobs3d": blobs3d, "ragged_batch": ragged_batch}
+             "blobs3d": blobs3d, "ragged_batch": ragged_batch, "glove_like": glove_like}
     return table[name](**kw)

@@ -80,3 +80,33 @@ def test_fault_injection_arguments_need_no_gpu(libpath):
     lib.snn_test_inject.argtypes = [ctypes.c_int32]
     assert lib.snn_test_inject(99) == 1
     assert lib.snn_test_inject(0) == 0
+
+
+def test_cosine_radius_mappings_match_the_oracle(libpath):
+    # host-only entry points: the FP64 radius of the Euclidean reduction
+    import oracle
+    lib = ctypes.CDLL(libpath)
+    for fn in ("snn_radius_for_cosine_distance", "snn_radius_for_cosine_similarity"):
+        getattr(lib, fn).argtypes = [ctypes.c_double]
+        getattr(lib, fn).restype = ctypes.c_double
+    for c in (0.0, 1e-9, 0.013, 0.5, 1.0, 1.75, 2.0):
+        assert lib.snn_radius_for_cosine_distance(c) == oracle.radius_for_cosine_distance(c)
+    for t in (-1.0, -0.3, 0.0, 0.5, 0.8660254037844387, 0.99, 1.0):
+        assert lib.snn_radius_for_cosine_similarity(t) == oracle.radius_for_cosine_similarity(t)
+    for bad in (-0.1, 2.5, float("nan")):
+        r = lib.snn_radius_for_cosine_distance(bad)
+        assert r != r
+    r = lib.snn_radius_for_cosine_similarity(1.5)
+    assert r != r
+
+
+def test_normalize_rows_argument_validation_needs_no_gpu(libpath):
+    lib = ctypes.CDLL(libpath)
+    lib.snn_normalize_rows.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
+                                       ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+    p = ctypes.c_void_p(16)
+    assert lib.snn_normalize_rows(None, 10, 3, 3, p, 3, None) == 1     # X NULL
+    assert lib.snn_normalize_rows(p, 10, 3, 2, p, 3, None) == 1        # ld < d
+    assert lib.snn_normalize_rows(p, 10, 3, 3, p, 2, None) == 1        # ldo < d
+    assert lib.snn_normalize_rows(p, -1, 3, 3, p, 3, None) == 1        # n < 0
+    assert lib.snn_normalize_rows(p, 0, 3, 3, p, 3, None) == 0         # nothing to do
