@@ -173,6 +173,35 @@ snn_status snn_query_radius_batch(int32_t nsets, const snn_index *const *idx,
                                   const int64_t *ldq, const double *R,
                                   snn_precision prec, void *stream, snn_csr *out);
 
+/* Streaming updates of a built index (Section 1: the index suits an online
+ * setting).  Algorithm 2 is exact for any unit direction v and any centre, so
+ * new points are scored with the index's own centre and direction (no PCA
+ * refresh; a stale direction only weakens the pruning) and merged into the
+ * sorted order, and deleted points are compacted out.  The result of every
+ * later query equals that of an index built on the updated point set.
+ * The caller orders an update after every query that uses the index (the
+ * index's arrays are replaced in order on `stream`); cached tensor-core
+ * operands are rebuilt by the next query.  Both calls synchronise `stream`
+ * once (to validate before the index is changed); on an error the index is
+ * unchanged.
+ *
+ * snn_index_insert: the k rows of X (device, k x d FP32, row stride ld >= d)
+ * become points n, n+1, ..., n+k-1.
+ * Errors: SNN_EINVAL for k < 0, NULL arguments, ld < d, n + k >= 2^31 or a
+ * NaN/Inf in X; SNN_ENOTSUP for a centred norm above 1e18; SNN_ENOMEM /
+ * SNN_ECUDA on device failures.  k = 0 does nothing.
+ *
+ * snn_index_delete: removes the points whose ids are listed in ids (device,
+ * count int32; repeats allowed).  The remaining points are renumbered
+ * 0, 1, ... in their previous id order, as if their rows had been erased from
+ * X.  Errors: SNN_EINVAL for count < 0, NULL arguments, an id outside [0, n)
+ * or a deletion of every point. */
+snn_status snn_index_insert(snn_index *idx, const float *X, int64_t k, int64_t ld, void *stream);
+snn_status snn_index_delete(snn_index *idx, const int32_t *ids, int64_t count, void *stream);
+
+/* Number of points of an index (host value; -1 for NULL). */
+int64_t snn_index_size(const snn_index *idx);
+
 /* Cosine and angular distances (Section 3): for unit vectors u, v the
  * cosine distance 1 - u.v equals ||u - v||^2 / 2, and the angle between them
  * is at most alpha exactly when ||u - v||^2 <= 2 - 2 cos(alpha).  A cosine or

@@ -14,6 +14,7 @@
 #include "query_kernels.cuh"
 #include "tc_score.cuh"
 #include "index_struct.cuh"
+#include "update_kernels.cuh"
 
 namespace snn {
 
@@ -322,6 +323,245 @@ static snn_status index_build(const float *X, int64_t n, int d, int64_t ld, cuda
     }
 #undef TRY_IX
     *out = ix;
+    return SNN_OK;
+}
+
+// ------------------------------------------------------ streaming updates
+// Per-position arrays of an index: scores, ids, raw and centred rows, halved
+// norms, norm bounds.
+struct PosArrays {
+    float *alpha = nullptr, *praw = nullptr, *xc = nullptr, *hx = nullptr, *nrm = nullptr;
+    int32_t *order = nullptr;
+    snn_status alloc(int64_t n, int dp, cudaStream_t s) {
+        SNN_TRY(dev_alloc(&alpha, n, s));
+        SNN_TRY(dev_alloc(&order, n, s));
+        SNN_TRY(dev_alloc(&praw, size_t(n) * dp, s));
+        SNN_TRY(dev_alloc(&xc, size_t(n) * dp, s));
+        SNN_TRY(dev_alloc(&hx, n, s));
+        SNN_TRY(dev_alloc(&nrm, n, s));
+        return SNN_OK;
+    }
+    void release(cudaStream_t s) {
+        void *ptrs[] = {alpha, order, praw, xc, hx, nrm};
+        for (void *p : ptrs)
+            if (p) cudaFreeAsync(p, s);
+        *this = PosArrays();
+    }
+};
+
+// Gives an index of a batched build its own centre, direction and constants
+// and drops its reference to the shared blocks (freed in order on s with the
+// last reference, after the copies and any kernel already queued on s).
+// Returns whether the index was sharing.
+static snn_status detach_shared(snn_index *ix, cudaStream_t s, bool *was_shared) {
+    *was_shared = ix->shared != nullptr;
+    if (!ix->shared) return SNN_OK;
+    double *mu64 = nullptr, *v64 = nullptr;
+    float *mu32 = nullptr, *v32 = nullptr, *dconst = nullptr;
+    snn_status st = SNN_OK;
+    if ((st = dev_alloc(&mu64, ix->d, s)) != SNN_OK || (st = dev_alloc(&v64, ix->d, s)) != SNN_OK ||
+        (st = dev_alloc(&mu32, ix->d, s)) != SNN_OK || (st = dev_alloc(&v32, ix->d, s)) != SNN_OK ||
+        (st = dev_alloc(&dconst, 4, s)) != SNN_OK) {
+        void *ptrs[] = {mu64, v64, mu32, v32, dconst};
+        for (void *p : ptrs)
+            if (p) cudaFreeAsync(p, s);
+        return st;
+    }
+    cudaMemcpyAsync(mu64, ix->mu64, ix->d * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(v64, ix->v64, ix->d * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(mu32, ix->mu32, ix->d * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(v32, ix->v32, ix->d * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(dconst, ix->dconst, 4 * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    snn_shared_blocks *sb = ix->shared;
+    if (sb->refs.fetch_sub(1) == 1) {
+        for (int i = 0; i < sb->nblocks; ++i)
+            if (sb->blocks[i]) cudaFreeAsync(sb->blocks[i], s);
+        delete sb;
+    }
+    ix->shared = nullptr;
+    ix->mu64 = mu64;
+    ix->v64 = v64;
+    ix->mu32 = mu32;
+    ix->v32 = v32;
+    ix->dconst = dconst;
+    ix->alpha = nullptr;   // slices of the released blocks
+    ix->order = nullptr;
+    ix->praw = nullptr;
+    ix->xc = nullptr;
+    ix->hx = nullptr;
+    ix->nrm = nullptr;
+    return SNN_OK;
+}
+
+// Replaces the per-position arrays (the old ones, when the index owns them,
+// are freed in order on s) and drops the cached tensor-core operands.
+static void install(snn_index *ix, PosArrays &a, int64_t n, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(ix->mu);
+    void *old[] = {ix->alpha, ix->order, ix->praw, ix->xc, ix->hx, ix->nrm};
+    for (void *p : old)
+        if (p) cudaFreeAsync(p, s);
+    for (auto &p : ix->tc_part) {
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+    }
+    for (auto &p : ix->f8_part) {
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+    }
+    if (ix->f8_fold) cudaFreeAsync(ix->f8_fold, s);
+    ix->f8_fold = nullptr;
+    ix->tc_nsplit = ix->tc_k2 = ix->tc_k2n = 0;
+    ix->f8_nsplit = ix->f8_np = ix->f8_k8 = 0;
+    ix->alpha = a.alpha;
+    ix->order = a.order;
+    ix->praw = a.praw;
+    ix->xc = a.xc;
+    ix->hx = a.hx;
+    ix->nrm = a.nrm;
+    a = PosArrays();
+    ix->n = n;
+    ix->stream = s;
+}
+
+// New points take ids n, n+1, ...: scored with the index's centre and
+// direction, sorted, and merged into the sorted order.
+static snn_status index_insert(snn_index *ix, const float *X, int64_t k, int64_t ld, cudaStream_t s) {
+    ensure_pool();
+    const int d = ix->d, dp = ix->dp;
+    const int64_t n = ix->n;
+    Scratch scr(s);
+    PosArrays nw, out;
+    int *bad;
+    float *add;   // [0] score error bound of the new points, [1] their largest norm bound
+    SNN_TRY(scr.alloc(&bad, 1));
+    SNN_TRY(scr.alloc(&add, 2));
+    SNN_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    SNN_CUDA(cudaMemsetAsync(add, 0, 2 * sizeof(float), s));
+    SNN_TRY(scr.alloc(&nw.alpha, k));
+    SNN_TRY(scr.alloc(&nw.order, k));
+    SNN_TRY(scr.alloc(&nw.praw, size_t(k) * dp));
+    SNN_TRY(scr.alloc(&nw.xc, size_t(k) * dp));
+    SNN_TRY(scr.alloc(&nw.hx, k));
+    SNN_TRY(scr.alloc(&nw.nrm, k));
+    SNN_TRY(project_sort_gather(X, k, d, ld, dp, ix->mu32, ix->v32, s, scr, add, bad, nw.alpha,
+                                nw.order, nw.praw, nw.xc, nw.hx, nw.nrm));
+    SNN_LAUNCH(k_max_nonneg, std::min<unsigned>(grid_for(k, 256), 1024), 256, 0, s)(nw.nrm, k, add + 1);
+    SNN_LAUNCH_CHECK();
+    int64_t *pos_old, *pos_new;
+    SNN_TRY(scr.alloc(&pos_old, n));
+    SNN_TRY(scr.alloc(&pos_new, k));
+    snn_status st = out.alloc(n + k, dp, s);
+    if (st != SNN_OK) {
+        out.release(s);
+        return st;
+    }
+    SNN_LAUNCH(k_merge_ranks, grid_for(n + k, 256), 256, 0, s)(ix->alpha, n, nw.alpha, k, pos_old, pos_new);
+    SNN_LAUNCH(k_place, grid_for(n * (dp / 4), 256), 256, 0, s)(
+        ix->alpha, ix->order, 0, ix->hx, ix->nrm, ix->praw, ix->xc, n, dp, pos_old, out.alpha, out.order,
+        out.hx, out.nrm, out.praw, out.xc);
+    SNN_LAUNCH(k_place, grid_for(k * (dp / 4), 256), 256, 0, s)(
+        nw.alpha, nw.order, int32_t(n), nw.hx, nw.nrm, nw.praw, nw.xc, k, dp, pos_new, out.alpha,
+        out.order, out.hx, out.nrm, out.praw, out.xc);
+    if (cudaGetLastError() != cudaSuccess) {
+        set_error("insert launch failed");
+        out.release(s);
+        return SNN_ECUDA;
+    }
+    float hadd[2];
+    int hbad = 0;
+    if (cudaMemcpyAsync(hadd, add, sizeof(hadd), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("insert failed: %s", cudaGetErrorString(cudaGetLastError()));
+        out.release(s);
+        return SNN_ECUDA;
+    }
+    if (hbad) {
+        set_error("X contains NaN or Inf");
+        out.release(s);
+        return SNN_EINVAL;
+    }
+    if (!(hadd[1] <= kMaxCentredNorm)) {
+        set_error("a centred point norm of %g exceeds %g", (double)hadd[1], kMaxCentredNorm);
+        out.release(s);
+        return SNN_ENOTSUP;
+    }
+    bool shared = false;
+    if ((st = detach_shared(ix, s, &shared)) != SNN_OK) {
+        out.release(s);
+        return st;
+    }
+    SNN_LAUNCH(k_update_consts, 1, 32, 0, s)(ix->dconst, add);
+    SNN_LAUNCH_CHECK();
+    ix->alpha_err = std::max(ix->alpha_err, hadd[0]);
+    ix->nrm_max = std::max(ix->nrm_max, hadd[1]);
+    install(ix, out, n + k, s);
+    return SNN_OK;
+}
+
+// Removes the listed ids; the kept points are renumbered 0, 1, ... in their
+// previous id order (as if their rows were erased from X).
+static snn_status index_delete(snn_index *ix, const int32_t *ids, int64_t cnt, cudaStream_t s) {
+    ensure_pool();
+    const int dp = ix->dp;
+    const int64_t n = ix->n;
+    Scratch scr(s);
+    uint8_t *del;
+    int *bad;
+    int64_t *keep_id, *keep_pos, *newid, *newpos, *total;
+    SNN_TRY(scr.alloc(&del, n));
+    SNN_TRY(scr.alloc(&bad, 1));
+    SNN_TRY(scr.alloc(&keep_id, n));
+    SNN_TRY(scr.alloc(&keep_pos, n));
+    SNN_TRY(scr.alloc(&newid, n));
+    SNN_TRY(scr.alloc(&newpos, n));
+    SNN_TRY(scr.alloc(&total, 1));
+    SNN_CUDA(cudaMemsetAsync(del, 0, n, s));
+    SNN_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    SNN_LAUNCH(k_mark_deleted, grid_for(cnt, 256), 256, 0, s)(ids, cnt, n, del, bad);
+    SNN_LAUNCH(k_keep_flags, grid_for(n, 256), 256, 0, s)(del, ix->order, n, keep_id, keep_pos);
+    SNN_LAUNCH_CHECK();
+    SNN_TRY(scan_exclusive<int64_t>(keep_id, newid, n, s));
+    SNN_TRY(scan_exclusive<int64_t>(keep_pos, newpos, n, s));
+    SNN_LAUNCH(k_kept_total, 1, 32, 0, s)(keep_pos, newpos, n, total);
+    SNN_LAUNCH_CHECK();
+    int64_t kept = 0;
+    int hbad = 0;
+    if (cudaMemcpyAsync(&kept, total, sizeof(kept), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("delete failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return SNN_ECUDA;
+    }
+    if (hbad) {
+        set_error("an id to delete is outside [0, n)");
+        return SNN_EINVAL;
+    }
+    if (kept < 1) {
+        set_error("deleting every point would leave an empty index");
+        return SNN_EINVAL;
+    }
+    if (kept == n) return SNN_OK;
+    PosArrays out;
+    snn_status st = out.alloc(kept, dp, s);
+    if (st != SNN_OK) {
+        out.release(s);
+        return st;
+    }
+    SNN_LAUNCH(k_compact, grid_for(n * (dp / 4), 256), 256, 0, s)(
+        del, ix->alpha, ix->order, ix->hx, ix->nrm, ix->praw, ix->xc, n, dp, newpos, newid, out.alpha,
+        out.order, out.hx, out.nrm, out.praw, out.xc);
+    if (cudaGetLastError() != cudaSuccess) {
+        set_error("delete launch failed");
+        out.release(s);
+        return SNN_ECUDA;
+    }
+    bool shared = false;
+    if ((st = detach_shared(ix, s, &shared)) != SNN_OK) {
+        out.release(s);
+        return st;
+    }
+    install(ix, out, kept, s);
     return SNN_OK;
 }
 
@@ -980,6 +1220,28 @@ void snn_free(void *p) {
 }
 
 void snn_index_free(snn_index *idx) { index_release(idx); }
+
+snn_status snn_index_insert(snn_index *idx, const float *X, int64_t k, int64_t ld, void *stream) {
+    clear_error();
+    if (!idx) { set_error("index is NULL"); return SNN_EINVAL; }
+    if (k < 0) { set_error("k must be >= 0"); return SNN_EINVAL; }
+    if (k == 0) return SNN_OK;
+    if (!X) { set_error("X is NULL"); return SNN_EINVAL; }
+    if (ld < idx->d) { set_error("ld must be >= d"); return SNN_EINVAL; }
+    if (idx->n + k >= (int64_t(1) << 31)) { set_error("n + k must be below 2^31"); return SNN_EINVAL; }
+    return index_insert(idx, X, k, ld, static_cast<cudaStream_t>(stream));
+}
+
+int64_t snn_index_size(const snn_index *idx) { return idx ? idx->n : -1; }
+
+snn_status snn_index_delete(snn_index *idx, const int32_t *ids, int64_t count, void *stream) {
+    clear_error();
+    if (!idx) { set_error("index is NULL"); return SNN_EINVAL; }
+    if (count < 0) { set_error("count must be >= 0"); return SNN_EINVAL; }
+    if (count == 0) return SNN_OK;
+    if (!ids) { set_error("ids is NULL"); return SNN_EINVAL; }
+    return index_delete(idx, ids, count, static_cast<cudaStream_t>(stream));
+}
 
 const char *snn_last_error(void) { return g_err; }
 

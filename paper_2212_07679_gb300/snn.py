@@ -76,6 +76,12 @@ def _load():
     lib.snn_last_error.restype = ctypes.c_char_p
     lib.snn_version.argtypes = []
     lib.snn_version.restype = ctypes.c_char_p
+    lib.snn_index_insert.argtypes = [vp, vp, i64, i64, vp]
+    lib.snn_index_insert.restype = ctypes.c_int
+    lib.snn_index_delete.argtypes = [vp, vp, i64, vp]
+    lib.snn_index_delete.restype = ctypes.c_int
+    lib.snn_index_size.argtypes = [vp]
+    lib.snn_index_size.restype = i64
     lib.snn_normalize_rows.argtypes = [vp, i64, i32, i64, vp, i64, vp]
     lib.snn_normalize_rows.restype = ctypes.c_int
     lib.snn_radius_for_cosine_distance.argtypes = [f64]
@@ -225,6 +231,29 @@ class Index:
     @property
     def handle(self):
         return self._h
+
+    def insert(self, X: torch.Tensor, stream=None) -> None:
+        """Adds the rows of X as points n, n+1, ... (snn_index_insert)."""
+        if self._h is None:
+            raise ValueError("index is closed")
+        X, ld = _points(X, "X")
+        if X.shape[1] != self.d:
+            raise ValueError(f"X must have {self.d} columns")
+        with torch.cuda.device(self.device):
+            _check(lib.snn_index_insert(self._h, ctypes.c_void_p(X.data_ptr()), X.shape[0], ld,
+                                        _stream_ptr(stream)))
+        self.n = int(lib.snn_index_size(self._h))
+
+    def delete(self, ids, stream=None) -> None:
+        """Removes the listed point ids; the rest are renumbered 0, 1, ... in
+        their previous order (snn_index_delete)."""
+        if self._h is None:
+            raise ValueError("index is closed")
+        t = torch.as_tensor(ids, dtype=torch.int32, device=self.device).contiguous()
+        with torch.cuda.device(self.device):
+            _check(lib.snn_index_delete(self._h, ctypes.c_void_p(t.data_ptr()), t.numel(),
+                                        _stream_ptr(stream)))
+        self.n = int(lib.snn_index_size(self._h))
 
     def query(self, Q: torch.Tensor | None = None, R: float = 0.0, precision: str = "fp32",
               stats: bool = False, stream=None) -> CSR:
