@@ -27,7 +27,7 @@
 // timeout sets an error flag.
 #include <cuda.h>
 #include <cuda_bf16.h>
-#include <cuda_fp8.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <cstdlib>
@@ -693,12 +693,19 @@ __global__ void k_tc_pack(const float *__restrict__ xc, int dp, const float *__r
 }
 
 // ------------------------------------------------ FP8 operand packing
-// Value of an e4m3 byte (1 sign, 4 exponent bits with bias 7, 3 mantissa
-// bits; exponent field 0 holds the subnormals m 2^-9).
-__device__ __forceinline__ float e4m3_value(uint32_t b) {
-    const uint32_t e = (b >> 3) & 15u, m = b & 7u;
-    const float mag = e == 0 ? float(m) * 0x1p-9f : __uint_as_float(((e + 120u) << 23) | (m << 20));
-    return (b & 0x80u) ? -mag : mag;
+// Two FP32 values rounded to e4m3 (RN, saturating to +-448): hi in bits 8-15,
+// lo in bits 0-7; and two e4m3 bytes back to FP32 (exact, through f16).
+__device__ __forceinline__ uint32_t e4m3x2(float hi, float lo) {
+    unsigned short r;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+__device__ __forceinline__ void e4m3x2_values(uint32_t b2, float &hi, float &lo) {
+    uint32_t h2;
+    asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h2) : "h"((unsigned short)b2));
+    const __half2 hh = *reinterpret_cast<const __half2 *>(&h2);
+    lo = __low2float(hh);
+    hi = __high2float(hh);
 }
 
 __device__ __forceinline__ float warp_sum_ru(float v) {
@@ -776,19 +783,26 @@ __global__ void k_f8_pack(const float *__restrict__ xc, int dp, const float *__r
                 const float xs[4] = {xv[t].x, xv[t].y, xv[t].z, xv[t].w};
                 uint32_t w[3] = {0u, 0u, 0u};
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float x = k0 + e < d ? xs[e] * sc : 0.f;
-                    sx = __fmaf_ru(x, x, sx);
-                    float rem = x;
+                for (int e = 0; e < 4; e += 2) {
+                    // elements e (low byte) and e + 1 (high byte) together
+                    const float x0 = k0 + e < d ? xs[e] * sc : 0.f;
+                    const float x1 = k0 + e + 1 < d ? xs[e + 1] * sc : 0.f;
+                    sx = __fmaf_ru(x0, x0, sx);
+                    sx = __fmaf_ru(x1, x1, sx);
+                    float r0 = x0, r1 = x1;
 #pragma unroll
                     for (int p = 0; p < NSPLIT; ++p) {
-                        const uint32_t b = __nv_cvt_float_to_fp8(rem, __NV_SATFINITE, __NV_E4M3);
-                        const float pv = e4m3_value(b);
-                        rem -= pv;                     // exact (pv within a factor 2 of rem, or 0)
-                        sp[p] = __fmaf_ru(pv, pv, sp[p]);
-                        w[p] |= b << (8 * e);
+                        const uint32_t b2 = e4m3x2(r1, r0);
+                        float v1, v0;
+                        e4m3x2_values(b2, v1, v0);
+                        r0 -= v0;                      // exact (v within a factor 2 of r, or 0)
+                        r1 -= v1;
+                        sp[p] = __fmaf_ru(v0, v0, sp[p]);
+                        sp[p] = __fmaf_ru(v1, v1, sp[p]);
+                        w[p] |= b2 << (8 * e);
                     }
-                    se = __fmaf_ru(rem, rem, se);
+                    se = __fmaf_ru(r0, r0, se);
+                    se = __fmaf_ru(r1, r1, se);
                 }
                 *reinterpret_cast<uint32_t *>(p0 + r * K8 + k0) = w[0];
                 *reinterpret_cast<uint32_t *>(p1 + r * K8 + k0) = w[1];
