@@ -103,6 +103,25 @@ def make_workload(args):
     raise SystemExit(f"unknown workload {args.workload}")
 
 
+def job_max_ms(local_ms: float, world: int) -> float:
+    """The job's time: the largest of the ranks' timed totals (an all-reduce
+    MAX over the process group; on the device for NCCL, on the host for gloo)."""
+    if world <= 1:
+        return float(local_ms)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, ms_step: float) -> float:
+    """Units all ranks processed per second (replicas: each rank runs the whole
+    workload, so the job processes world x units per step)."""
+    return world * units_per_rank / (ms_step / 1e3)
+
+
 def is_cosine(w):
     return w.extra.get("measure") == "cosine distance"
 
@@ -259,11 +278,8 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     total_ms = float(np.sum(per_step))
-    t_max = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms_step = float(t_max.item()) / args.steps
-    value = world * w.m / (ms_step / 1e3)
+    ms_step = job_max_ms(total_ms, world) / args.steps
+    value = whole_job_rate(w.m, world, ms_step)
 
     def time_precision(prec, products=None):
         # another scoring precision on the same workload, same timing rules;
