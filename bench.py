@@ -100,6 +100,9 @@ def make_workload(args):
         return wl.blobs3d(n=args.n) if args.n else wl.blobs3d()
     if args.workload == "glove_like":
         return wl.glove_like(n=args.n) if args.n else wl.glove_like()
+    if args.workload == "gmm_aniso_oos":
+        n = args.n or 1_000_000
+        return wl.gmm_aniso(n=n, queries=n)
     raise SystemExit(f"unknown workload {args.workload}")
 
 
@@ -127,7 +130,8 @@ def is_cosine(w):
 
 
 def workload_config(args, w, extra=None):
-    cfg = {"workload": f"{w.name} self-join", "n": w.n, "d": w.d, "queries": w.m,
+    kind = "self-join" if w.Q is None else "out-of-sample queries"
+    cfg = {"workload": f"{w.name} {kind}", "n": w.n, "d": w.d, "queries": w.m,
            "R": w.R, "precision": args.precision, "parallelism": f"replicas{args.gpus}",
            "l2": "flushed between steps (256 MiB write)"}
     if is_cosine(w):
@@ -227,6 +231,8 @@ def run_ours(args):
     w = make_workload(args)
     X_host = torch.from_numpy(w.P).pin_memory()
     X = X_host.cuda()
+    Q_host = None if w.Q is None else torch.from_numpy(w.Q).pin_memory()
+    Qd = None if Q_host is None else Q_host.cuda()
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -241,7 +247,7 @@ def run_ours(args):
         ix = index_of(X)
         if e_mid is not None:
             e_mid.record(stream)
-        out = ix.query(None, Rq, precision=args.precision, stats=stats)
+        out = ix.query(Qd, Rq, precision=args.precision, stats=stats)
         return ix, out
 
     for _ in range(args.warmup):
@@ -289,7 +295,7 @@ def run_ours(args):
         try:
             for _ in range(2):
                 ix = index_of(X)
-                ix.query(None, Rq, precision=prec)
+                ix.query(Qd, Rq, precision=prec)
                 del ix
             times = []
             for _ in range(max(3, min(args.steps, 5))):
@@ -298,7 +304,7 @@ def run_ours(args):
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
                 ix = index_of(X)
-                out = ix.query(None, Rq, precision=prec, stats=True)
+                out = ix.query(Qd, Rq, precision=prec, stats=True)
                 e1.record(stream)
                 e1.synchronize()
                 times.append(e0.elapsed_time(e1))
@@ -336,15 +342,16 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         Xd = X_host.to("cuda", non_blocking=True)
+        Qe = None if Q_host is None else Q_host.to("cuda", non_blocking=True)
         ix = index_of(Xd)
-        out = ix.query(None, Rq, precision=args.precision)
+        out = ix.query(Qe, Rq, precision=args.precision)
         host = out.to_host(hbufs)
         torch.cuda.synchronize()
         if it > 0:
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
-        h2d = X_host.numel() * 4
+        h2d = (X_host.numel() + (0 if Q_host is None else Q_host.numel())) * 4
         d2h = host.offsets.numel() * 8 + host.indices.numel() * 4 + host.dist2.numel() * 4
-        del ix, out, Xd, host
+        del ix, out, Xd, Qe, host
 
     st = stats_list[-1]
     peaks, src = load_peaks()

@@ -102,15 +102,20 @@ def random_rotation(rng, d):
 
 
 def gmm_aniso(n: int = 1_000_000, d: int = 16, clusters: int = 50, nbrs: float = 50.0,
-              sub: int = 4000, seed: int = SEED_BASE + 2) -> Workload:
+              sub: int = 4000, seed: int = SEED_BASE + 2, queries: int = 0) -> Workload:
     """Anisotropic rotated mixture: per-axis std 0.9^i, one random rotation,
-    centres U[-20,20]^d; self-join; R gives ~``nbrs`` neighbours per point."""
+    centres U[-20,20]^d; self-join; R gives ~``nbrs`` neighbours per point.
+    With ``queries`` > 0, that many further draws of the same mixture form a
+    separate query set (the points and R are those of the self-join)."""
     rng = rng_for(seed)
     centres = rng.uniform(-20.0, 20.0, size=(clusters, d))
     rot = random_rotation(rng, d)
     std = 0.9 ** np.arange(d)
     P, lab = _mixture(rng, n, centres, std, rot)
     R = subsample_radius(P, nbrs / (n - 1), sub, rng)
+    if queries > 0:
+        Q, _ = _mixture(rng, queries, centres, std, rot)
+        return Workload("gmm_aniso_oos", P, Q, R, extra={"labels": lab})
     return Workload("gmm_aniso", P, None, R, extra={"labels": lab})
 
 
