@@ -15,7 +15,8 @@ Contents:
 * ``dbscan``              -- DBSCAN on top of the brute-force neighbour lists;
 * ``cosine_radius``       -- cosine / angular search by the Euclidean reduction
                              of Section 3 (``normalize_rows`` and the radius
-                             mappings).
+                             mappings);
+* ``brute_inner_product`` -- inner-product threshold search (FP64 dot products).
 
 Pins (tests/test_oracle_*.py): hand cases under tests/golden/, exact
 invariants, the paper's printed return ratios (Tables 1 and 2) and the
@@ -28,8 +29,9 @@ from .cpu_snn import SNNIndex, snn_index, snn_query, snn_radius
 from .dbscan import dbscan, dbscan_bfs
 from .cosine import (normalize_rows, radius_for_cosine_distance, radius_for_cosine_similarity,
                      cosine_radius)
+from .inner_product import dot_fp64, brute_inner_product
 
 __all__ = ["brute_radius", "brute_radius_numpy", "pair_dist2", "build_oracle",
            "oracle_threads", "CSR", "SNNIndex", "snn_index", "snn_query", "snn_radius",
            "dbscan", "dbscan_bfs", "normalize_rows", "radius_for_cosine_distance",
-           "radius_for_cosine_similarity", "cosine_radius"]
+           "radius_for_cosine_similarity", "cosine_radius", "dot_fp64", "brute_inner_product"]
