@@ -173,6 +173,50 @@ snn_status snn_query_radius_batch(int32_t nsets, const snn_index *const *idx,
                                   const int64_t *ldq, const double *R,
                                   snn_precision prec, void *stream, snn_csr *out);
 
+/* Radius search with one radius per query (out-of-sample queries): query i
+ * takes the points with S <= fl64(R[i]*R[i]) (S as in snn_query_radius).
+ *  R       device, m FP64 radii in query order (finite, >= 0).
+ * Other arguments, output and errors as snn_query_radius (Q must be given);
+ * SNN_EINVAL also for a negative, NaN or infinite radius.  Synchronises
+ * `stream` once more (the radii are validated first). */
+snn_status snn_query_radius_each(const snn_index *idx, const float *Q, int64_t m, int64_t ldq,
+                                 const double *R, snn_precision prec, void *stream, snn_csr *out,
+                                 snn_query_stats *stats);
+
+/* Inner-product threshold search (the maximum-inner-product variant of
+ * Section 3).  Returns, for every query q (row of Q), the points p (rows of
+ * P) with D(p, q) >= tau, where D is the FP64 dot product summed over
+ * ascending k with every product and sum rounded to nearest and no fused
+ * multiply-add; ids ascending, and the CSR's dist2 array holds fl32(D).
+ * Section 3 turns p.q into a Euclidean distance of augmented rows,
+ * ||p~ - q~||^2 = xi^2 + ||q||^2 - 2 p.q with p~ = [sqrt(xi^2 - ||p||^2), p],
+ * q~ = [0, q], xi = max ||p||; the search prunes with SNN on those rows
+ * (one radius, for the largest query norm, widened by the rounding of the
+ * augmented coordinate) and decides every remaining pair on the exact dot
+ * product.
+ *  P, Q    device FP32, n x d and m x d, row strides ldp, ldq (>= d).
+ *  tau     finite threshold.
+ *  prec    rejection arithmetic of the Euclidean stage (see snn_precision).
+ *  out     host struct receiving the CSR (device arrays; free each with
+ *          snn_free).
+ *  stats   optional: xi, the Euclidean radius, the Euclidean candidates and
+ *          their survivors, the pairs returned and those the FP64 loop decided.
+ * Errors: SNN_EINVAL for NULL arguments, n or m outside [1, 2^31), d outside
+ * [1, 4095], ld < d, a non-finite tau, NaN/Inf in P or Q; as
+ * snn_query_radius otherwise.  Synchronises `stream`. */
+typedef struct {
+    double xi;
+    double radius;
+    int64_t band_pairs;
+    int64_t survivors;
+    int64_t candidates;
+    int64_t nnz;
+    int64_t exact_fp64;
+} snn_ip_stats;
+snn_status snn_inner_product_search(const float *P, int64_t n, int32_t d, int64_t ldp, const float *Q,
+                                    int64_t m, int64_t ldq, double tau, snn_precision prec, void *stream,
+                                    snn_csr *out, snn_ip_stats *stats);
+
 /* Streaming updates of a built index (Section 1: the index suits an online
  * setting).  Algorithm 2 is exact for any unit direction v and any centre, so
  * new points are scored with the index's own centre and direction (no PCA

@@ -119,7 +119,8 @@ constexpr double kMaxCentredNorm = 1e18;
 constexpr double kU64 = 1.1102230246251565e-16;  // 2^-53
 
 // ------------------------------------------------- library-wide primitives
-// Exclusive prefix sum: out[0..n] with out[n] = total.  T = int64_t/uint32_t.
+// Exclusive prefix sum: out[0..n] with out[n] = total, so out must hold
+// n + 1 entries.  T = int64_t/uint32_t.
 template <typename T>
 snn_status scan_exclusive(const T *in, T *out, int64_t n, cudaStream_t s);
 

@@ -20,11 +20,11 @@ namespace snn {
 // hy_i = fl32(||y_i||^2)/2 underestimates ||y_i||^2/2 by at most gamma_d.
 __global__ void k_query_consts(const float *__restrict__ hy, const float *__restrict__ qn,
                                int64_t m, int d, double Rx, double e_data,
-                               float *__restrict__ thrA) {
+                               float *__restrict__ thrA, const double *__restrict__ Rq) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= m) return;
     const double ei = 1.0001 * (double)kU32 * (double)qn[i];
-    const double r = Rx + e_data + ei;
+    const double r = (Rq ? radius_slack(Rq[i], d) : Rx) + e_data + ei;
     const double hy_low = (double)hy[i] * (1.0 - 1.05 * (d + 2) * (double)kU32);
     const double a = 0.5 * r * r - hy_low;
     thrA[i] = __double2float_ru(a + 4.0 * kU64 * (fabs(a) + 0.5 * r * r + (double)hy[i]));
@@ -62,15 +62,27 @@ __global__ void k_tile_band(const float *__restrict__ qalpha, int64_t m,
                             const float *__restrict__ eps_d, const float *__restrict__ eps_q,
                             int64_t *__restrict__ tile_lo, int64_t *__restrict__ tile_hi,
                             int64_t *__restrict__ items, int ntiles, int sym,
-                            unsigned long long *__restrict__ band_pairs) {
+                            unsigned long long *__restrict__ band_pairs, const double *__restrict__ Rq,
+                            int d) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ntiles) return;
-    const double W = Wbase + (double)*eps_d + (double)*eps_q;
+    const double eps = (double)*eps_d + (double)*eps_q;
+    const double W = Wbase + eps;
     const int64_t q0 = int64_t(t) * kBQ;
     const int64_t q1 = min(m, q0 + kBQ) - 1;
     const double a0 = (double)qalpha[q0], a1 = (double)qalpha[q1];
-    const double lo_x = (a0 - W) - 4.0 * kU64 * (fabs(a0) + W);
-    const double hi_x = (a1 + W) + 4.0 * kU64 * (fabs(a1) + W);
+    double lo_x = (a0 - W) - 4.0 * kU64 * (fabs(a0) + W);
+    double hi_x = (a1 + W) + 4.0 * kU64 * (fabs(a1) + W);
+    if (Rq) {
+        // the union of the tile's windows, each with its own radius
+        lo_x = 1e308;
+        hi_x = -1e308;
+        for (int64_t q = q0; q <= q1; ++q) {
+            const double a = (double)qalpha[q], Wq = window_base(Rq[q], d) + eps;
+            lo_x = fmin(lo_x, (a - Wq) - 4.0 * kU64 * (fabs(a) + Wq));
+            hi_x = fmax(hi_x, (a + Wq) + 4.0 * kU64 * (fabs(a) + Wq));
+        }
+    }
     // symmetric self-join: a tile scores only rows at or after its own first
     // query, each unordered pair once (the mirror is emitted on acceptance)
     const int64_t lo = sym ? q0 : lower_bound_ge(alpha, n, lo_x);
@@ -94,11 +106,11 @@ __global__ void k_item_tiles(const int64_t *__restrict__ item_off, int ntiles,
 __global__ void k_query_windows(const float *__restrict__ qalpha, int64_t m,
                                 const float *__restrict__ alpha, int64_t n, double Wbase,
                                 const float *__restrict__ eps_d, const float *__restrict__ eps_q,
-                                unsigned long long *__restrict__ cand) {
+                                unsigned long long *__restrict__ cand, const double *__restrict__ Rq, int d) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const double W = Wbase + (double)*eps_d + (double)*eps_q;
     unsigned long long c = 0;
     if (i < m) {
+        const double W = (Rq ? window_base(Rq[i], d) : Wbase) + (double)*eps_d + (double)*eps_q;
         const double a = (double)qalpha[i];
         const double slack = 4.0 * kU64 * (fabs(a) + W);
         const int64_t lo = lower_bound_ge(alpha, n, a - W - slack);
@@ -107,6 +119,17 @@ __global__ void k_query_windows(const float *__restrict__ qalpha, int64_t m,
     }
     for (int o = 16; o; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(cand, c);
+}
+
+__global__ void k_query_radii(const double *__restrict__ R, const int32_t *__restrict__ qorder, int64_t m,
+                              int d, double *__restrict__ Rs, double *__restrict__ R2s,
+                              DecideConsts *__restrict__ dcs) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const double r = R[qorder[i]];
+    Rs[i] = r;
+    R2s[i] = __dmul_rn(r, r);
+    dcs[i] = decide_consts(d, __dmul_rn(r, r));
 }
 
 // ------------------------------------------------------------ FP32 score
@@ -392,10 +415,13 @@ template <bool kSym>
 __device__ __forceinline__ void decide_one_survivor(
          int64_t s, const uint2 *__restrict__ surv, int64_t cap, const float *__restrict__ qraw,
          const int32_t *__restrict__ qorder, const float *__restrict__ praw,
-         const int32_t *__restrict__ porder, int d, int dp, double R2, const DecideConsts &dc,
+         const int32_t *__restrict__ porder, int d, int dp, double R2, const DecideConsts &dc0,
+         const double *__restrict__ R2q, const DecideConsts *__restrict__ dcq,
          float *__restrict__ rec_d2, int32_t *__restrict__ rec_pos, uint2 *__restrict__ rec_rc,
          int32_t *__restrict__ counts, unsigned long long *__restrict__ n_fp64) {
     const uint2 e = surv[s];
+    const DecideConsts dc = dcq ? dcq[e.x] : dc0;
+    const double R2e = R2q ? R2q[e.x] : R2;
     const float4 *pq = reinterpret_cast<const float4 *>(qraw + int64_t(e.x) * dp);
     const float4 *pp = reinterpret_cast<const float4 *>(praw + int64_t(e.y) * dp);
     float H = 0.f, L = 0.f;
@@ -425,7 +451,7 @@ __device__ __forceinline__ void decide_one_survivor(
     int v = decide_df(H, L, nz, dc, &d2);
     if (v == 2) {
         const double S = dist2_fp64(pp, pq, d, dp);
-        v = S <= R2 ? 1 : 0;
+        v = S <= R2e ? 1 : 0;
         d2 = (float)S;
         atomicAdd(n_fp64, 1ull);
     }
@@ -450,14 +476,15 @@ __device__ __forceinline__ void decide_body(
          const uint2 *__restrict__ surv, const unsigned long long *__restrict__ count, int64_t cap,
          const float *__restrict__ qraw, const int32_t *__restrict__ qorder,
          const float *__restrict__ praw, const int32_t *__restrict__ porder, int d, int dp,
-         double R2, const DecideConsts &dc, float *__restrict__ rec_d2,
+         double R2, const DecideConsts &dc, const double *__restrict__ R2q,
+         const DecideConsts *__restrict__ dcq, float *__restrict__ rec_d2,
          int32_t *__restrict__ rec_pos, uint2 *__restrict__ rec_rc, int32_t *__restrict__ counts,
          unsigned long long *__restrict__ n_fp64) {
     const int64_t nsurv = min((int64_t)*count, cap);
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < nsurv; s += stride)
-        decide_one_survivor<kSym>(s, surv, cap, qraw, qorder, praw, porder, d, dp, R2, dc, rec_d2,
-                                  rec_pos, rec_rc, counts, n_fp64);
+        decide_one_survivor<kSym>(s, surv, cap, qraw, qorder, praw, porder, d, dp, R2, dc, R2q, dcq,
+                                  rec_d2, rec_pos, rec_rc, counts, n_fp64);
 }
 
 // The same decision with G lanes per survivor for long rows: lane l
@@ -473,7 +500,8 @@ __device__ __forceinline__ void decide_group_body(
          const uint2 *__restrict__ surv, const unsigned long long *__restrict__ count, int64_t cap,
          const float *__restrict__ qraw, const int32_t *__restrict__ qorder,
          const float *__restrict__ praw, const int32_t *__restrict__ porder, int d, int dp,
-         double R2, const DecideConsts &dc, float *__restrict__ rec_d2,
+         double R2, const DecideConsts &dc0, const double *__restrict__ R2q,
+         const DecideConsts *__restrict__ dcq, float *__restrict__ rec_d2,
          int32_t *__restrict__ rec_pos, uint2 *__restrict__ rec_rc, int32_t *__restrict__ counts,
          unsigned long long *__restrict__ n_fp64) {
     constexpr int GPW = 32 / G;   // groups per warp
@@ -524,11 +552,13 @@ __device__ __forceinline__ void decide_group_body(
         }
         if (G > 1) nz = __any_sync(0xffffffffu, nz);   // (any lane of the warp: conservative)
         if (lane != 0 || !valid) continue;
+        const DecideConsts dc = dcq ? dcq[e.x] : dc0;
+        const double R2e = R2q ? R2q[e.x] : R2;
         float d2 = 0.f;
         int v = decide_df(H, L, nz, dc, &d2);
         if (v == 2) {
             const double S = dist2_fp64(pp, pq, d, dp);
-            v = S <= R2 ? 1 : 0;
+            v = S <= R2e ? 1 : 0;
             d2 = (float)S;
             atomicAdd(n_fp64, 1ull);
         }
@@ -550,11 +580,12 @@ __device__ __forceinline__ void decide_group_body(
     const uint2 *__restrict__ surv, const unsigned long long *__restrict__ count, int64_t cap, \
         const float *__restrict__ qraw, const int32_t *__restrict__ qorder,                    \
         const float *__restrict__ praw, const int32_t *__restrict__ porder, int d, int dp,     \
-        double R2, DecideConsts dc, float *__restrict__ rec_d2, int32_t *__restrict__ rec_pos,  \
-        uint2 *__restrict__ rec_rc, int32_t *__restrict__ counts,                              \
+        double R2, DecideConsts dc, const double *__restrict__ R2q,                            \
+        const DecideConsts *__restrict__ dcq, float *__restrict__ rec_d2,                      \
+        int32_t *__restrict__ rec_pos, uint2 *__restrict__ rec_rc, int32_t *__restrict__ counts, \
         unsigned long long *__restrict__ n_fp64
-#define SNN_DECIDE_PASS surv, count, cap, qraw, qorder, praw, porder, d, dp, R2, dc, rec_d2,      \
-                        rec_pos, rec_rc, counts, n_fp64
+#define SNN_DECIDE_PASS surv, count, cap, qraw, qorder, praw, porder, d, dp, R2, dc, R2q, dcq,  \
+                        rec_d2, rec_pos, rec_rc, counts, n_fp64
 __global__ void __launch_bounds__(256) k_decide_sym(SNN_DECIDE_ARGS) {
     decide_body<true>(SNN_DECIDE_PASS);
 }

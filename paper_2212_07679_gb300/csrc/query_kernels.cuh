@@ -48,6 +48,7 @@ struct ScoreArgs {
     unsigned long long *count;  // survivors found (may exceed cap)
     unsigned long long *work;   // work-item counter
     int *err;                   // device error flag (bounded waits that gave up)
+    const double *Rq = nullptr; // per-query radii (sorted query order), or null
 };
 
 // One work item of the FP32 scorer: a 128-query tile against band chunks
@@ -98,15 +99,29 @@ struct BatchScoreArgs {
 
 __global__ void k_score_fp32_batch(BatchScoreArgs a);
 __global__ void k_item_tiles(const int64_t *item_off, int ntiles, int32_t *item_tile);
+// Largest true distance the FP64 test with radius R can accept (the FP64
+// rounding of S, R*R and the comparison).
+__host__ __device__ inline double radius_slack(double R, int d) { return R * (1.0 + (d + 8) * 0x1p-52); }
+// Window half-width base for a radius: |alpha_j - alpha_q| <= ||v|| D + eps_j + eps_q.
+__host__ __device__ inline double window_base(double R, int d) {
+    return radius_slack(R, d) * (1.0 + (d + 4) * 0x1p-52) * (1.0 + 0x1p-30);
+}
+
+// Per-query radii (sorted query order): Rq non-null replaces the scalar
+// radius arguments of the kernels below with Rq[i] for query i.
 __global__ void k_query_consts(const float *hy, const float *qn, int64_t m, int d, double Rx,
-                               double e_data, float *thrA);
+                               double e_data, float *thrA, const double *Rq);
 __global__ void k_tile_band(const float *qalpha, int64_t m, const float *alpha, int64_t n,
                             double Wbase, const float *eps_d, const float *eps_q,
                             int64_t *tile_lo, int64_t *tile_hi, int64_t *items, int ntiles,
-                            int sym, unsigned long long *band_pairs);
+                            int sym, unsigned long long *band_pairs, const double *Rq, int d);
 __global__ void k_query_windows(const float *qalpha, int64_t m, const float *alpha, int64_t n,
                                 double Wbase, const float *eps_d, const float *eps_q,
-                                unsigned long long *cand);
+                                unsigned long long *cand, const double *Rq, int d);
+// Per-query radii in sorted query order (Rs[i] = R[qorder[i]]), fl64(R*R)
+// and the decision constants of each.
+__global__ void k_query_radii(const double *R, const int32_t *qorder, int64_t m, int d, double *Rs,
+                              double *R2s, DecideConsts *dcs);
 __global__ void k_score_fp32_single(ScoreArgs a);
 __global__ void k_score_fp32_multi(ScoreArgs a);
 // Tier-1 membership and dist2 from the compensated FP32 value H + L of S
@@ -157,12 +172,14 @@ __device__ __forceinline__ int decide_df(float H, float L, bool nz, const Decide
 
 // Exact decision of survivors; _sym emits both orientations of a self-join
 // pair, _one emits the (query, point) orientation only; _g8 / _g32 use 8 or
-// 32 lanes per survivor (long rows).  The survivor count is read on the
+// 32 lanes per survivor (long rows).  R2q / dcq non-null: per-query fl64(R*R)
+// and decision constants (sorted query order) instead of R2 / dc.  The survivor count is read on the
 // device (min(*count, cap)); rec_pos[cap + s] is the mirrored slot.
 #define SNN_DECIDE_DECL(name)                                                                \
     __global__ void name(const uint2 *surv, const unsigned long long *count, int64_t cap,    \
                          const float *qraw, const int32_t *qorder, const float *praw,        \
                          const int32_t *porder, int d, int dp, double R2, DecideConsts dc,   \
+                         const double *R2q, const DecideConsts *dcq,                         \
                          float *rec_d2, int32_t *rec_pos, uint2 *rec_rc, int32_t *counts,    \
                          unsigned long long *n_fp64)
 SNN_DECIDE_DECL(k_decide_sym);

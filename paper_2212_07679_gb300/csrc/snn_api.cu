@@ -15,6 +15,7 @@
 #include "tc_score.cuh"
 #include "index_struct.cuh"
 #include "update_kernels.cuh"
+#include "inner_product.cuh"
 
 namespace snn {
 
@@ -508,14 +509,13 @@ static snn_status index_delete(snn_index *ix, const int32_t *ids, int64_t cnt, c
     Scratch scr(s);
     uint8_t *del;
     int *bad;
-    int64_t *keep_id, *keep_pos, *newid, *newpos, *total;
+    int64_t *keep_id, *keep_pos, *newid, *newpos;
     SNN_TRY(scr.alloc(&del, n));
     SNN_TRY(scr.alloc(&bad, 1));
     SNN_TRY(scr.alloc(&keep_id, n));
     SNN_TRY(scr.alloc(&keep_pos, n));
-    SNN_TRY(scr.alloc(&newid, n));
-    SNN_TRY(scr.alloc(&newpos, n));
-    SNN_TRY(scr.alloc(&total, 1));
+    SNN_TRY(scr.alloc(&newid, n + 1));    // exclusive scans: n + 1 entries
+    SNN_TRY(scr.alloc(&newpos, n + 1));
     SNN_CUDA(cudaMemsetAsync(del, 0, n, s));
     SNN_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
     SNN_LAUNCH(k_mark_deleted, grid_for(cnt, 256), 256, 0, s)(ids, cnt, n, del, bad);
@@ -523,11 +523,9 @@ static snn_status index_delete(snn_index *ix, const int32_t *ids, int64_t cnt, c
     SNN_LAUNCH_CHECK();
     SNN_TRY(scan_exclusive<int64_t>(keep_id, newid, n, s));
     SNN_TRY(scan_exclusive<int64_t>(keep_pos, newpos, n, s));
-    SNN_LAUNCH(k_kept_total, 1, 32, 0, s)(keep_pos, newpos, n, total);
-    SNN_LAUNCH_CHECK();
     int64_t kept = 0;
     int hbad = 0;
-    if (cudaMemcpyAsync(&kept, total, sizeof(kept), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+    if (cudaMemcpyAsync(&kept, newpos + n, sizeof(kept), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         set_error("delete failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -614,11 +612,12 @@ struct QueryScratch {
 
 // Largest true distance the FP64 test S <= fl64(R*R) can still accept:
 // S >= D^2 (1 - gamma_{d+2}) and fl64(R*R) <= R^2 (1 + u).
-static double radius_slack(double R, int d) { return R * (1.0 + (d + 8) * 0x1p-52); }
-
+// R: the radius, or with per-query radii Rdev (device, m, query order; out-of-
+// sample queries only) the smallest of them, Rmax the largest (host choices:
+// the BF16 split, the FP8 availability).
 static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int64_t ldq,
                              double R, snn_precision prec, cudaStream_t s, snn_csr *out,
-                             snn_query_stats *stats) {
+                             snn_query_stats *stats, const double *Rdev = nullptr, double Rmax = 0.0) {
     const bool self = (Q == nullptr);
     if (self) m = ix->n;
     const int d = ix->d, dp = ix->dp;
@@ -730,11 +729,21 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     const double Rx = radius_slack(R, d);
     const double e_data = 1.0001 * (double)kU32 * (double)ix->nrm_max;
     // window half-width: |alpha_j - alpha_q| <= ||v|| D + eps_j + eps_q
-    const double Wbase = Rx * (1.0 + (d + 4) * 0x1p-52) * (1.0 + 0x1p-30);
+    const double Wbase = window_base(R, d);
+    // per-query radii, constants and decision constants in sorted order
+    double *Rs = nullptr, *R2s = nullptr;
+    DecideConsts *dcs = nullptr;
+    if (Rdev) {
+        TRY_Q(scr.alloc(&Rs, m));
+        TRY_Q(scr.alloc(&R2s, m));
+        TRY_Q(scr.alloc(&dcs, m));
+        SNN_LAUNCH(k_query_radii, grid_for(m, 256), 256, 0, s)(Rdev, qs.order, m, d, Rs, R2s, dcs);
+        CUDA_Q(cudaGetLastError());
+    }
 
     float *thrA;
     TRY_Q(scr.alloc(&thrA, m));
-    SNN_LAUNCH(k_query_consts, grid_for(m, 256), 256, 0, s)(qs.hx, qs.nrm, m, d, Rx, e_data, thrA);
+    SNN_LAUNCH(k_query_consts, grid_for(m, 256), 256, 0, s)(qs.hx, qs.nrm, m, d, Rx, e_data, thrA, Rs);
     CUDA_Q(cudaGetLastError());
 
     const int ntiles = (int)cdiv(m, kBQ);
@@ -750,11 +759,11 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     CUDA_Q(cudaMemsetAsync(ctr, 0, 8 * sizeof(unsigned long long), s));
     SNN_LAUNCH(k_tile_band, grid_for(ntiles, 128), 128, 0, s)(qs.alpha, m, ix->alpha, ix->n, Wbase,
                                                       ix->dconst, eps_q, tile_lo, tile_hi, items,
-                                                      ntiles, sym, stats ? ctr + 2 : nullptr);
+                                                      ntiles, sym, stats ? ctr + 2 : nullptr, Rs, d);
     CUDA_Q(cudaGetLastError());
     if (stats) {
         SNN_LAUNCH(k_query_windows, grid_for(m, 256), 256, 0, s)(qs.alpha, m, ix->alpha, ix->n, Wbase,
-                                                         ix->dconst, eps_q, ctr + 3);
+                                                         ix->dconst, eps_q, ctr + 3, Rs, d);
         CUDA_Q(cudaGetLastError());
     }
     TRY_Q(scan_exclusive<int64_t>(items, item_off, ntiles, s));
@@ -797,6 +806,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     TRY_Q(scr.alloc(&dev_err, 1));
     CUDA_Q(cudaMemsetAsync(dev_err, 0, sizeof(int), s));
     sa.err = dev_err;
+    sa.Rq = Rs;
     int32_t *counts, *lists, *big_list;
     int64_t *counts64, *big_len, *toff;
     unsigned *cls;
@@ -825,7 +835,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     int64_t mma_fpp = 0;
     // FP8 where its shape and ranges allow it, BF16 otherwise
     const snn_precision used =
-        prec == SNN_PREC_FP8E4M3 && !f8_eligible(ix, Rx) ? SNN_PREC_BF16 : prec;
+        prec == SNN_PREC_FP8E4M3 && !f8_eligible(ix, Rdev ? radius_slack(Rmax, d) : Rx) ? SNN_PREC_BF16 : prec;
     for (int attempt = 0; attempt < 2; ++attempt) {
         CUDA_Q(cudaMallocAsync(&surv, size_t(cap) * sizeof(uint2), s));
         CUDA_Q(cudaMallocAsync(&rec_d2, size_t(cap) * sizeof(float), s));
@@ -858,7 +868,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         const unsigned dgrid =
             std::min<unsigned>(grid_for(cap * G, 256), unsigned(16 * device_sm_count()));
         SNN_LAUNCH(dk, dgrid, 256, 0, s)(surv, ctr, cap, qs.raw, qs.order, ds.raw, ds.order, d, dp,
-                                         R2, decide_consts(d, R2), rec_d2, rec_pos, rec_rc, counts,
+                                         R2, decide_consts(d, R2), R2s, dcs, rec_d2, rec_pos, rec_rc, counts,
                                          ctr + 4);
         CUDA_Q(cudaGetLastError());
         if (stats) cudaEventRecord(ev[3], s);
@@ -909,9 +919,9 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
             // the band and candidate counters are recomputed by the re-run
             SNN_LAUNCH(k_tile_band, grid_for(ntiles, 128), 128, 0, s)(
                 qs.alpha, m, ix->alpha, ix->n, Wbase, ix->dconst, eps_q, tile_lo, tile_hi, items,
-                ntiles, sym, ctr + 2);
+                ntiles, sym, ctr + 2, Rs, d);
             SNN_LAUNCH(k_query_windows, grid_for(m, 256), 256, 0, s)(qs.alpha, m, ix->alpha, ix->n,
-                                                                     Wbase, ix->dconst, eps_q, ctr + 3);
+                                                                     Wbase, ix->dconst, eps_q, ctr + 3, Rs, d);
             CUDA_Q(cudaGetLastError());
         }
     }
@@ -1034,6 +1044,141 @@ static snn_status check_finite_r(double R, const char *what) {
     if (!(R >= 0.0) || !std::isfinite(R)) {
         set_error("%s must be finite and >= 0", what);
         return SNN_EINVAL;
+    }
+    return SNN_OK;
+}
+
+// Inner-product threshold search: the Euclidean search on augmented rows
+// (p~ = [sqrt(xi^2 - ||p||^2), p], q~ = [0, q]) with a radius for the largest
+// query norm gives a superset of the pairs with p.q >= tau; the exact FP64
+// dot-product decision then keeps the pairs of the definition, in id order.
+static snn_status ip_search(const float *P, int64_t n, int d, int64_t ldp, const float *Q, int64_t m,
+                            int64_t ldq, double tau, snn_precision prec, cudaStream_t s, snn_csr *out,
+                            snn_ip_stats *st) {
+    ensure_pool();
+    Scratch scr(s);
+    double *sqP, *sqQ, *mx;
+    int *bad;
+    unsigned long long *nf;
+    SNN_TRY(scr.alloc(&sqP, n));
+    SNN_TRY(scr.alloc(&sqQ, m));
+    SNN_TRY(scr.alloc(&mx, 2));
+    SNN_TRY(scr.alloc(&bad, 1));
+    SNN_TRY(scr.alloc(&nf, 1));
+    SNN_CUDA(cudaMemsetAsync(mx, 0, 2 * sizeof(double), s));
+    SNN_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    SNN_CUDA(cudaMemsetAsync(nf, 0, sizeof(unsigned long long), s));
+    SNN_LAUNCH(k_row_sq64, grid_for(n, 256), 256, 0, s)(P, n, d, ldp, sqP, mx, bad);
+    SNN_LAUNCH(k_row_sq64, grid_for(m, 256), 256, 0, s)(Q, m, d, ldq, sqQ, mx + 1, bad);
+    SNN_LAUNCH_CHECK();
+    double hm[2];
+    int hbad = 0;
+    if (cudaMemcpyAsync(hm, mx, sizeof(hm), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("inner-product search failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return SNN_ECUDA;
+    }
+    if (hbad) {
+        set_error("P or Q contains NaN or Inf, or a squared norm overflows");
+        return SNN_EINVAL;
+    }
+    // one radius per query (Rq^2 = xi^2 + ||q||^2 - 2 tau plus the slack);
+    // the largest for the host choices
+    const double R2 = (hm[0] + hm[1] - 2.0 * tau) + 0x1p-20 * (hm[0] + hm[1]);
+    const double Rmax = R2 > 0.0 ? std::sqrt(R2) * (1.0 + 0x1p-40) : 0.0;
+    if (st) {
+        st->xi = std::sqrt(hm[0]);
+        st->radius = Rmax;
+    }
+    double *Rq;
+    SNN_TRY(scr.alloc(&Rq, m));
+    SNN_LAUNCH(k_ip_radii, grid_for(m, 256), 256, 0, s)(sqQ, m, mx, tau, Rq);
+    SNN_LAUNCH_CHECK();
+    float *Pa, *Qa;
+    SNN_TRY(scr.alloc(&Pa, size_t(n) * (d + 1)));
+    SNN_TRY(scr.alloc(&Qa, size_t(m) * (d + 1)));
+    SNN_LAUNCH(k_augment, grid_for(n, 256), 256, 0, s)(P, n, d, ldp, sqP, mx, 0, Pa);
+    SNN_LAUNCH(k_augment, grid_for(m, 256), 256, 0, s)(Q, m, d, ldq, sqQ, mx, 1, Qa);
+    SNN_LAUNCH_CHECK();
+    snn_index *ix = nullptr;
+    SNN_TRY(index_build(Pa, n, d + 1, d + 1, s, &ix));
+    snn_csr cand;
+    std::memset(&cand, 0, sizeof(cand));
+    snn_query_stats qst;
+    snn_status rc = query_impl(ix, Qa, m, d + 1, Rmax, prec, s, &cand, st ? &qst : nullptr, Rq, Rmax);
+    index_release(ix);
+    if (rc != SNN_OK) return rc;
+    auto drop = [&](snn_csr &c) {
+        free_device_ptr(c.offsets);
+        if (c.indices) free_device_ptr(c.indices);
+        if (c.dist2) free_device_ptr(c.dist2);
+        std::memset(&c, 0, sizeof(c));
+    };
+    const int64_t nnz = cand.nnz;
+    if (st) {
+        st->candidates = nnz;
+        st->survivors = qst.survivors;
+        st->band_pairs = qst.band_pairs;
+    }
+    out->m = m;
+    if (nnz == 0) {
+        *out = cand;   // every row empty
+        if (st) st->nnz = 0, st->exact_fp64 = 0;
+        return SNN_OK;
+    }
+    int64_t *rows, *keep, *pos;
+    float *vals;
+    SNN_TRY(scr.alloc(&rows, nnz));
+    SNN_TRY(scr.alloc(&keep, nnz));
+    SNN_TRY(scr.alloc(&pos, nnz + 1));    // exclusive scan: nnz + 1 entries
+    SNN_TRY(scr.alloc(&vals, nnz));
+    SNN_LAUNCH(k_csr_rows, grid_for(nnz, 256), 256, 0, s)(cand.offsets, m, nnz, rows);
+    const int G = d <= 32 ? 1 : (d <= 128 ? 8 : 32);
+    auto dk = G == 1 ? k_ip_decide_g1 : (G == 8 ? k_ip_decide_g8 : k_ip_decide_g32);
+    const unsigned dgrid = std::min<unsigned>(grid_for(nnz * G, 256), unsigned(16 * device_sm_count()));
+    SNN_LAUNCH(dk, dgrid, 256, 0, s)(rows, cand.indices, nnz, P, ldp, Q, ldq, d, tau, keep, vals, nf);
+    SNN_LAUNCH_CHECK();
+    snn_status st2 = scan_exclusive<int64_t>(keep, pos, nnz, s);
+    if (st2 != SNN_OK) { drop(cand); return st2; }
+    int64_t *offs = nullptr;
+    if ((st2 = dev_alloc(&offs, m + 1, s)) != SNN_OK) { drop(cand); return st2; }
+    SNN_LAUNCH(k_ip_offsets, grid_for(m + 1, 256), 256, 0, s)(cand.offsets, m, pos, offs);
+    int64_t kept = 0;
+    unsigned long long hnf = 0;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&kept, offs + m, sizeof(kept), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&hnf, nf, sizeof(hnf), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("inner-product filter failed: %s", cudaGetErrorString(cudaGetLastError()));
+        cudaFreeAsync(offs, s);
+        drop(cand);
+        return SNN_ECUDA;
+    }
+    int32_t *oid = nullptr;
+    float *oval = nullptr;
+    if (kept > 0) {
+        if ((st2 = dev_alloc(&oid, kept, s)) != SNN_OK || (st2 = dev_alloc(&oval, kept, s)) != SNN_OK) {
+            if (oid) cudaFreeAsync(oid, s);
+            cudaFreeAsync(offs, s);
+            drop(cand);
+            return st2;
+        }
+        SNN_LAUNCH(k_ip_compact, grid_for(nnz, 256), 256, 0, s)(cand.indices, vals, keep, pos, nnz, oid, oval);
+        SNN_LAUNCH_CHECK();
+    }
+    drop(cand);
+    out->m = m;
+    out->nnz = kept;
+    out->offsets = offs;
+    out->indices = oid;
+    out->dist2 = oval;
+    SNN_TRY(own_output(offs, s));
+    SNN_TRY(own_output(oid, s));
+    SNN_TRY(own_output(oval, s));
+    if (st) {
+        st->nnz = kept;
+        st->exact_fp64 = (int64_t)hnf;
     }
     return SNN_OK;
 }
@@ -1233,6 +1378,68 @@ snn_status snn_index_insert(snn_index *idx, const float *X, int64_t k, int64_t l
 }
 
 int64_t snn_index_size(const snn_index *idx) { return idx ? idx->n : -1; }
+
+snn_status snn_query_radius_each(const snn_index *idx, const float *Q, int64_t m, int64_t ldq,
+                                 const double *R, snn_precision prec, void *stream, snn_csr *out,
+                                 snn_query_stats *stats) {
+    clear_error();
+    if (!out) { set_error("out is NULL"); return SNN_EINVAL; }
+    std::memset(out, 0, sizeof(*out));
+    if (!idx) { set_error("index is NULL"); return SNN_EINVAL; }
+    if (!Q || m < 1 || m >= (int64_t(1) << 31) || ldq < idx->d || !R) {
+        set_error("Q (m in [1, 2^31), ldq >= d) and R must be given");
+        return SNN_EINVAL;
+    }
+    if (prec != SNN_PREC_FP32 && prec != SNN_PREC_BF16 && prec != SNN_PREC_FP8E4M3) {
+        set_error("precision %d is not available in this build", (int)prec);
+        return SNN_ENOTSUP;
+    }
+    ensure_pool();
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double hm[2] = {0.0, 0.0};
+    int hbad = 0;
+    {
+        Scratch scr(s);
+        double *mm;
+        int *bad;
+        SNN_TRY(scr.alloc(&mm, 2));
+        SNN_TRY(scr.alloc(&bad, 1));
+        const unsigned long long init[2] = {~0ull, 0ull};
+        SNN_CUDA(cudaMemcpyAsync(mm, init, sizeof(init), cudaMemcpyHostToDevice, s));
+        SNN_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+        SNN_LAUNCH(k_radii_minmax, grid_for(m, 256), 256, 0, s)(R, m, mm, bad);
+        SNN_LAUNCH_CHECK();
+        SNN_CUDA(cudaMemcpyAsync(hm, mm, sizeof(hm), cudaMemcpyDeviceToHost, s));
+        SNN_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SNN_CUDA(cudaStreamSynchronize(s));
+    }
+    if (hbad) {
+        set_error("every radius must be finite and >= 0");
+        return SNN_EINVAL;
+    }
+    return query_impl(idx, Q, m, ldq, hm[0], prec, s, out, stats, R, hm[1]);
+}
+
+snn_status snn_inner_product_search(const float *P, int64_t n, int32_t d, int64_t ldp, const float *Q,
+                                    int64_t m, int64_t ldq, double tau, snn_precision prec, void *stream,
+                                    snn_csr *out, snn_ip_stats *stats) {
+    clear_error();
+    if (!out) { set_error("out is NULL"); return SNN_EINVAL; }
+    std::memset(out, 0, sizeof(*out));
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (d > 4095) { set_error("d must be at most 4095 (one augmented column)"); return SNN_EINVAL; }
+    SNN_TRY(validate_points(P, n, d, ldp));
+    if (m < 1 || m >= (int64_t(1) << 31) || !Q || ldq < d) {
+        set_error("Q must hold m in [1, 2^31) rows with ldq >= d");
+        return SNN_EINVAL;
+    }
+    if (!std::isfinite(tau)) { set_error("tau must be finite"); return SNN_EINVAL; }
+    if (prec != SNN_PREC_FP32 && prec != SNN_PREC_BF16 && prec != SNN_PREC_FP8E4M3) {
+        set_error("precision %d is not available in this build", (int)prec);
+        return SNN_ENOTSUP;
+    }
+    return ip_search(P, n, d, ldp, Q, m, ldq, tau, prec, static_cast<cudaStream_t>(stream), out, stats);
+}
 
 snn_status snn_index_delete(snn_index *idx, const int32_t *ids, int64_t count, void *stream) {
     clear_error();

@@ -871,11 +871,11 @@ __global__ void k_f8_pack(const float *__restrict__ xc, int dp, const float *__r
 // conservative, plus a margin that makes an acceptable pair's acc positive.
 __global__ void k_tc_query_consts(const float *__restrict__ hy, const float *__restrict__ qn,
                                   int64_t m, int d, double Rx, double e_data, double delta,
-                                  double margin, double *__restrict__ Aq) {
+                                  double margin, double *__restrict__ Aq, const double *__restrict__ Rq) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= m) return;
     const double ei = 1.0001 * (double)kU32 * (double)qn[i];
-    const double r = Rx + e_data + ei;
+    const double r = (Rq ? radius_slack(Rq[i], d) : Rx) + e_data + ei;
     const double hy_low = (double)hy[i] * (1.0 - 1.05 * (d + 2) * (double)kU32);
     double A = 0.5 * r * r - hy_low;
     A += 4.0 * kU64 * (fabs(A) + 0.5 * r * r + (double)hy[i]);
@@ -1052,7 +1052,7 @@ snn_status f8_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
     SNN_TRY(scr.alloc(&qfold, size_t(m) * 16));
     // a margin of 2^-60 keeps A'_i 2^(s_x + s_y) a normal FP32 number
     SNN_LAUNCH(k_tc_query_consts, unsigned(cdiv(m, 256)), 256, 0, s)(
-        sa.q.hx, sa.q.nrm, m, d, Rx, e_data, 0x1p-23 + kacc, 0x1p-60, Aq);
+        sa.q.hx, sa.q.nrm, m, d, Rx, e_data, 0x1p-23 + kacc, 0x1p-60, Aq, sa.Rq);
     SNN_LAUNCH_CHECK();
     SNN_LAUNCH(packer, pack_grid(m), pack_threads, 0, s)(sa.q.xc, ix->dp, nullptr, Aq, m, d, K8, ch,
                                                         kacc, 1, qp[0], qp[1], qp[2], qfold);
@@ -1122,7 +1122,7 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
     SNN_TRY(scr.alloc(&Aq, m));
     for (int p = 0; p < nsplit; ++p) SNN_TRY(scr.alloc(&qp[p], size_t(m) * (p == 0 ? K2 : K2n)));
     SNN_LAUNCH(k_tc_query_consts, unsigned(cdiv(m, 256)), 256, 0, s)(
-        sa.q.hx, sa.q.nrm, m, d, Rx, e_data, 0x1p-23 + u_k, 0x1p-100, Aq);
+        sa.q.hx, sa.q.nrm, m, d, Rx, e_data, 0x1p-23 + u_k, 0x1p-100, Aq, sa.Rq);
     SNN_LAUNCH_CHECK();
     auto packer = nsplit == 2 ? k_tc_pack<2> : k_tc_pack<3>;
     SNN_LAUNCH(packer, unsigned(cdiv(cdiv(m, 32) * 32, 256)), 256, 0, s)(sa.q.xc, ix->dp, sa.q.hx,

@@ -83,11 +83,6 @@ __global__ void k_keep_flags(const uint8_t *__restrict__ del, const int32_t *__r
     keep_pos[t] = del[order[t]] ? 0 : 1;
 }
 
-__global__ void k_kept_total(const int64_t *__restrict__ keep, const int64_t *__restrict__ scan, int64_t n,
-                             int64_t *__restrict__ total) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) *total = scan[n - 1] + keep[n - 1];
-}
-
 __global__ void k_compact(const uint8_t *__restrict__ del, const float *__restrict__ alpha,
                           const int32_t *__restrict__ order, const float *__restrict__ hx,
                           const float *__restrict__ nrm, const float *__restrict__ praw,

@@ -29,9 +29,6 @@ __global__ void k_mark_deleted(const int32_t *ids, int64_t cnt, int64_t n, uint8
 __global__ void k_keep_flags(const uint8_t *del, const int32_t *order, int64_t n, int64_t *keep_id,
                              int64_t *keep_pos);
 
-// *total = scan[n-1] + keep[n-1] (kept entries after an exclusive scan).
-__global__ void k_kept_total(const int64_t *keep, const int64_t *scan, int64_t n, int64_t *total);
-
 // Kept entry at sorted position i to position newpos[i], its id renumbered to
 // newid[id] (the kept ids in ascending order become 0, 1, ...).
 __global__ void k_compact(const uint8_t *del, const float *alpha, const int32_t *order, const float *hx,

@@ -41,6 +41,12 @@ class StatsStruct(ctypes.Structure):
                 ("precision_used", ctypes.c_int32)]
 
 
+class IPStatsStruct(ctypes.Structure):
+    _fields_ = [("xi", ctypes.c_double), ("radius", ctypes.c_double), ("band_pairs", ctypes.c_int64),
+                ("survivors", ctypes.c_int64), ("candidates", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("exact_fp64", ctypes.c_int64)]
+
+
 class ViewStruct(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32), ("dp", ctypes.c_int32),
                 ("mu", ctypes.c_void_p), ("v1", ctypes.c_void_p), ("alpha", ctypes.c_void_p),
@@ -82,6 +88,12 @@ def _load():
     lib.snn_index_delete.restype = ctypes.c_int
     lib.snn_index_size.argtypes = [vp]
     lib.snn_index_size.restype = i64
+    lib.snn_query_radius_each.argtypes = [vp, vp, i64, i64, vp, ctypes.c_int, vp,
+                                          ctypes.POINTER(CSRStruct), ctypes.POINTER(StatsStruct)]
+    lib.snn_query_radius_each.restype = ctypes.c_int
+    lib.snn_inner_product_search.argtypes = [vp, i64, i32, i64, vp, i64, i64, f64, ctypes.c_int, vp,
+                                             ctypes.POINTER(CSRStruct), ctypes.POINTER(IPStatsStruct)]
+    lib.snn_inner_product_search.restype = ctypes.c_int
     lib.snn_normalize_rows.argtypes = [vp, i64, i32, i64, vp, i64, vp]
     lib.snn_normalize_rows.restype = ctypes.c_int
     lib.snn_radius_for_cosine_distance.argtypes = [f64]
@@ -284,6 +296,26 @@ class Index:
             sd = {k: getattr(st, k) for k, _ in StatsStruct._fields_}
         return _csr_from(cs, self.device, sd)
 
+    def query_each(self, Q: torch.Tensor, R, precision: str = "fp32", stats: bool = False,
+                   stream=None) -> CSR:
+        """Out-of-sample queries with one radius each (snn_query_radius_each);
+        R: a float64 sequence or tensor of len(Q) radii."""
+        if self._h is None:
+            raise ValueError("index is closed")
+        Q, ldq = _points(Q, "Q")
+        Rt = torch.as_tensor(R, dtype=torch.float64, device=self.device).contiguous()
+        if Rt.numel() != Q.shape[0]:
+            raise ValueError("one radius per query row")
+        cs = CSRStruct()
+        st = StatsStruct() if stats else None
+        with torch.cuda.device(self.device):
+            _check(lib.snn_query_radius_each(self._h, ctypes.c_void_p(Q.data_ptr()), Q.shape[0], ldq,
+                                             ctypes.c_void_p(Rt.data_ptr()), PRECISIONS[precision],
+                                             _stream_ptr(stream), ctypes.byref(cs),
+                                             ctypes.byref(st) if st is not None else None))
+        sd = {k: getattr(st, k) for k, _ in StatsStruct._fields_} if st is not None else None
+        return _csr_from(cs, self.device, sd)
+
     def view(self) -> dict:
         """Device arrays of the index (copies), for inspection and tests."""
         v = ViewStruct()
@@ -373,6 +405,25 @@ def cosine_radius_search(X: torch.Tensor, Q: torch.Tensor | None = None, *,
     U = normalize_rows(X, stream=stream)
     V = None if Q is None else normalize_rows(Q, stream=stream)
     return Index(U, stream=stream).query(V, R, precision, stats, stream=stream)
+
+
+def inner_product_search(P: torch.Tensor, Q: torch.Tensor, tau: float, precision: str = "bf16",
+                         stats: bool = False, stream=None) -> CSR:
+    """Every row of P whose FP64 dot product with a row of Q reaches tau
+    (snn_inner_product_search); the CSR's dist2 holds the dot products."""
+    P, ldp = _points(P, "P")
+    Q, ldq = _points(Q, "Q")
+    if P.shape[1] != Q.shape[1]:
+        raise ValueError("P and Q must have the same number of columns")
+    cs = CSRStruct()
+    st = IPStatsStruct() if stats else None
+    with torch.cuda.device(P.device):
+        _check(lib.snn_inner_product_search(ctypes.c_void_p(P.data_ptr()), P.shape[0], P.shape[1], ldp,
+                                            ctypes.c_void_p(Q.data_ptr()), Q.shape[0], ldq, float(tau),
+                                            PRECISIONS[precision], _stream_ptr(stream), ctypes.byref(cs),
+                                            ctypes.byref(st) if st is not None else None))
+    sd = {k: getattr(st, k) for k, _ in IPStatsStruct._fields_} if st is not None else None
+    return _csr_from(cs, P.device, sd)
 
 
 def query_batch(indices: list[Index], Qs: list[torch.Tensor | None], Rs: list[float],

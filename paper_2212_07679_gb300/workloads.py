@@ -18,7 +18,9 @@ used):
 * ``uniform_cube``  -- uniform points in [0,1]^d (the Section 6.1/6.2 data);
 * ``glove_like``    -- word-vector-like directions for cosine / angular search
                        (a synthetic stand-in for the GloVe100 vectors of
-                       Section 6.3; R holds a cosine-distance bound).
+                       Section 6.3; R holds a cosine-distance bound);
+* ``mips_like``     -- the same vectors with separate queries for the
+                       inner-product threshold search (R holds the threshold).
 
 The radius for a workload is a quantile of the pairwise Euclidean distances
 of a seeded subsample (all i<j pairs, ``numpy.quantile`` default linear
@@ -216,8 +218,31 @@ def glove_like(n: int = 200_000, d: int = 100, clusters: int = 200, spread: floa
     return Workload("glove_like", X, None, c, extra={"labels": lab, "measure": "cosine distance"})
 
 
+def mips_like(n: int = 200_000, d: int = 100, m: int = 10_000, clusters: int = 200,
+              spread: float = 0.75, nbrs: float = 20.0, sub: int = 4000,
+              seed: int = SEED_BASE + 7) -> Workload:
+    """Inner-product threshold search on word-vector-like rows (the vectors of
+    ``glove_like``, magnitudes kept) with m queries drawn the same way; R is
+    the threshold tau: the 1 - nbrs/n quantile of the dot products of a
+    seeded subsample of points with a subsample of queries (float64)."""
+    rng = rng_for(seed)
+    dirs = rng.standard_normal((clusters, d))
+
+    def draw(k):
+        lab = rng.integers(0, clusters, size=k)
+        X = dirs[lab] + spread * rng.standard_normal((k, d))
+        return (X * np.exp(0.5 * rng.standard_normal((k, 1)))).astype(np.float32)
+    P = draw(n)
+    Q = draw(m)
+    ps = P[rng.choice(n, size=min(sub, n), replace=False)].astype(np.float64)
+    qs = Q[rng.choice(m, size=min(sub // 4, m), replace=False)].astype(np.float64)
+    tau = float(np.quantile(ps @ qs.T, 1.0 - nbrs / n))
+    return Workload("mips_like", P, Q, tau, extra={"measure": "inner product"})
+
+
 def by_name(name: str, **kw):
     """Workload factory by name (sizes overridable for smaller parity cases)."""
     table = {"gmm_iso": gmm_iso, "gmm_aniso": gmm_aniso, "lowrank_img": lowrank_img,
-             "blobs3d": blobs3d, "ragged_batch": ragged_batch, "glove_like": glove_like}
+             "blobs3d": blobs3d, "ragged_batch": ragged_batch, "glove_like": glove_like,
+             "mips_like": mips_like}
     return table[name](**kw)
