@@ -71,15 +71,17 @@ def test_edge_cases(snn):
                f"magnitudes tau={tau}")
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
-def test_query_radius_each(snn, prec):
+@pytest.mark.parametrize("prec,d", [("fp32", 10), ("bf16", 10), ("bf16", 100), ("fp8", 100)])
+def test_query_radius_each(snn, prec, d):
     """One radius per query: each row equals the oracle run with that radius."""
     rng = np.random.default_rng(103)
-    P = (rng.standard_normal((4000, 10)) * 2).astype(np.float32)
-    Q = (rng.standard_normal((600, 10)) * 2).astype(np.float32)
-    R = rng.uniform(0.0, 3.0, 600)
+    scale = 2.0 if d == 10 else 0.4
+    P = (rng.standard_normal((4000, d)) * scale).astype(np.float32)
+    Q = (rng.standard_normal((600, d)) * scale).astype(np.float32)
+    R = rng.uniform(0.0, 3.0 if d == 10 else 6.0, 600)
     R[::50] = 0.0
-    got = snn.Index(_dev(P)).query_each(_dev(Q), R, precision=prec)
+    got = snn.Index(_dev(P)).query_each(_dev(Q), R, precision=prec, stats=True)
+    assert got.stats["precision_used"] == {"fp32": 0, "bf16": 1, "fp8": 2}[prec]
     off = got.offsets.cpu().numpy()
     idx = got.indices.cpu().numpy()
     d2 = got.dist2.cpu().numpy()
