@@ -189,10 +189,12 @@ class CSR:
     def nnz(self) -> int:
         return self.indices.numel()
 
-    def to_host(self, buffers: "HostBuffers | None" = None, stream=None) -> "CSR":
+    def to_host(self, buffers: "HostBuffers | None" = None, stream=None, blocking: bool = True) -> "CSR":
         """Copies the lists into pinned host memory (reused from `buffers` when
         given) with asynchronous copies on `stream` (default: the current
-        stream), then waits for them.  Returns a CSR of host tensors."""
+        stream), then waits for them (blocking=False: returns at once; the
+        host tensors are complete once `stream` has reached this point).
+        Returns a CSR of host tensors."""
         b = buffers if buffers is not None else HostBuffers()
         off = b.take("offsets", self.offsets.numel(), torch.int64)
         idx = b.take("indices", self.indices.numel(), torch.int32)
@@ -202,7 +204,8 @@ class CSR:
             off.copy_(self.offsets, non_blocking=True)
             idx.copy_(self.indices, non_blocking=True)
             d2.copy_(self.dist2, non_blocking=True)
-        s.synchronize()
+        if blocking:
+            s.synchronize()
         return CSR(off, idx, d2, self.stats)
 
 
