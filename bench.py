@@ -854,6 +854,36 @@ def run_stream(args):
     print(json.dumps(line), flush=True)
 
 
+def run_peaks(args):
+    """Throughput probes of the arithmetic units the kernels use (tcgen05 BF16
+    and e4m3 MMAs, FP32 and FP64 FMAs), each timed with CUDA events over
+    `steps` launches after `warmup` launches, with clocks sampled meanwhile.
+    These check the ratios the rooflines rely on (e4m3 = 2 x BF16, the FP32
+    lane count x clock); the rooflines themselves keep the driver-measured
+    denominators."""
+    import torch
+    from paper_2212_07679_gb300 import snn
+    torch.cuda.set_device(0)
+    iters = {"bf16_mma": 1 << 17, "e4m3_mma": 1 << 17, "fp32_fma": 1 << 18, "fp64_fma": 1 << 12}
+    for k, it in iters.items():
+        for _ in range(max(1, args.warmup)):
+            snn.measure_peak(k, it)
+    clk = ClockSampler(0)
+    clk.start()
+    res = {}
+    for k, it in iters.items():
+        res[k] = max(snn.measure_peak(k, it) for _ in range(max(1, args.steps))) / 1e12
+    clocks = clk.stop()
+    peaks, src = load_peaks()
+    line = {"metric": "probe_peak_tflops", "value": res["e4m3_mma"], "unit": "TFLOP/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "e4m3",
+            "data": "synthetic", "config": {"workload": "peak_probes", "iters": iters},
+            "probes_tflops": res, "e4m3_over_bf16": res["e4m3_mma"] / res["bf16_mma"],
+            "bf16_probe_over_measured_burst": res["bf16_mma"] / float(peaks["bf16_tflops"]),
+            "fp32_lane_clock_model_tflops": FP32_PEAK_TFLOPS, "peaks_source": src, "clocks": clocks}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -878,6 +908,8 @@ def main():
         run_stream(args)
     elif args.workload == "mips_like":
         run_mips(args)
+    elif args.workload == "peaks":
+        run_peaks(args)
     else:
         run_ours(args)
 

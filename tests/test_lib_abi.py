@@ -110,3 +110,14 @@ def test_normalize_rows_argument_validation_needs_no_gpu(libpath):
     assert lib.snn_normalize_rows(p, 10, 3, 3, p, 2, None) == 1        # ldo < d
     assert lib.snn_normalize_rows(p, -1, 3, 3, p, 3, None) == 1        # n < 0
     assert lib.snn_normalize_rows(p, 0, 3, 3, p, 3, None) == 0         # nothing to do
+
+
+def test_peak_probe_validation_needs_no_gpu(libpath):
+    lib = ctypes.CDLL(libpath)
+    lib.snn_measure_peak.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
+                                     ctypes.POINTER(ctypes.c_double)]
+    out = ctypes.c_double()
+    assert lib.snn_measure_peak(4, 1024, None, ctypes.byref(out)) == 1       # unknown kind
+    assert lib.snn_measure_peak(-1, 1024, None, ctypes.byref(out)) == 1
+    assert lib.snn_measure_peak(0, 63, None, ctypes.byref(out)) == 1         # iters < 64
+    assert lib.snn_measure_peak(0, 1024, None, None) == 1                    # NULL output
