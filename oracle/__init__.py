@@ -16,7 +16,9 @@ Contents:
 * ``cosine_radius``       -- cosine / angular search by the Euclidean reduction
                              of Section 3 (``normalize_rows`` and the radius
                              mappings);
-* ``brute_inner_product`` -- inner-product threshold search (FP64 dot products).
+* ``brute_inner_product`` -- inner-product threshold search (FP64 dot products);
+* ``tie_audit``           -- pairs where the FP64 definition's decision differs
+                             from exact rational arithmetic (boundary band only).
 
 Pins (tests/test_oracle_*.py): hand cases under tests/golden/, exact
 invariants, the paper's printed return ratios (Tables 1 and 2) and the
@@ -30,8 +32,10 @@ from .dbscan import dbscan, dbscan_bfs
 from .cosine import (normalize_rows, radius_for_cosine_distance, radius_for_cosine_similarity,
                      cosine_radius)
 from .inner_product import dot_fp64, brute_inner_product
+from .tie_audit import tie_audit, exact_is_neighbour
 
 __all__ = ["brute_radius", "brute_radius_numpy", "pair_dist2", "build_oracle",
            "oracle_threads", "CSR", "SNNIndex", "snn_index", "snn_query", "snn_radius",
            "dbscan", "dbscan_bfs", "normalize_rows", "radius_for_cosine_distance",
-           "radius_for_cosine_similarity", "cosine_radius", "dot_fp64", "brute_inner_product"]
+           "radius_for_cosine_similarity", "cosine_radius", "dot_fp64", "brute_inner_product",
+           "tie_audit", "exact_is_neighbour"]
