@@ -54,7 +54,11 @@ typedef enum {
  * The output is identical for every precision; only the speed differs. */
 typedef enum {
     SNN_PREC_FP32 = 0,      /* FP32 CUDA-core dot products                  */
-    SNN_PREC_BF16 = 1,      /* BF16 tcgen05 tensor-core dot products        */
+    SNN_PREC_BF16 = 1,      /* BF16 tcgen05 tensor-core dot products, each
+                               value split into two or three BF16 parts
+                               (chosen from the largest norm and R; the
+                               environment variable SNN_BF16_PARTS = 2 or 3
+                               overrides)                                   */
     SNN_PREC_FP8E4M3 = 2    /* FP8 e4m3 tcgen05 dot products, each row
                                scaled by its own power of two; used for
                                d > 55 with norms and R below 2^20, BF16

@@ -132,6 +132,23 @@ snn_status radix_sort_pairs(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals
 
 int device_sm_count();
 
+// Small device-to-host reads that use no copy engine.  A one-block kernel on
+// `s` copies each source into a mapped pinned buffer of the calling host
+// thread, the stream is synchronised, and the bytes are copied to the host
+// destinations.  A cudaMemcpyAsync read of a few bytes would queue on the
+// device-to-host copy engine behind any bulk transfer another stream has
+// issued (a CSR read-back of hundreds of MB delays it by milliseconds);
+// the kernel's stores reach host memory directly.  At most kMaxHostReads
+// entries and kHostReadBytes bytes in total per call.
+struct HostRead {
+    const void *src;   // device
+    void *dst;         // host
+    int bytes;
+};
+constexpr int kMaxHostReads = 8;
+constexpr int kHostReadBytes = 2048;
+snn_status read_to_host(const HostRead *reads, int n, cudaStream_t s);
+
 // out = max(out, max_i x[i]) for non-negative x (snn_api.cu).
 __global__ void k_max_nonneg(const float *x, int64_t n, float *out);
 

@@ -115,6 +115,73 @@ int device_sm_count() {
     return sms > 0 ? sms : 1;
 }
 
+namespace {
+struct ReadList {
+    const unsigned char *src[kMaxHostReads];
+    int bytes[kMaxHostReads];
+    int off[kMaxHostReads];
+    int n;
+};
+
+__global__ void k_read_to_mailbox(ReadList L, unsigned char *mbox) {
+    for (int i = 0; i < L.n; ++i)
+        for (int b = threadIdx.x; b < L.bytes[i]; b += blockDim.x) mbox[L.off[i] + b] = L.src[i][b];
+    __threadfence_system();
+}
+
+// Mapped pinned buffer of the calling thread (allocated once, kept).
+unsigned char *host_mailbox(unsigned char **dev) {
+    thread_local unsigned char *host = nullptr, *devp = nullptr;
+    if (!host) {
+        void *h = nullptr, *d = nullptr;
+        if (cudaHostAlloc(&h, kHostReadBytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        if (cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFreeHost(h);
+            return nullptr;
+        }
+        host = static_cast<unsigned char *>(h);
+        devp = static_cast<unsigned char *>(d);
+    }
+    *dev = devp;
+    return host;
+}
+}  // namespace
+
+snn_status read_to_host(const HostRead *reads, int n, cudaStream_t s) {
+    if (n < 0 || n > kMaxHostReads) {
+        set_error("read_to_host: %d entries (at most %d)", n, kMaxHostReads);
+        return SNN_EINVAL;
+    }
+    unsigned char *dev = nullptr;
+    unsigned char *host = host_mailbox(&dev);
+    if (!host) {
+        set_error("mapped pinned host allocation failed");
+        return SNN_ENOMEM;
+    }
+    ReadList L{};
+    int off = 0;
+    for (int i = 0; i < n; ++i) {
+        L.src[i] = static_cast<const unsigned char *>(reads[i].src);
+        L.bytes[i] = reads[i].bytes;
+        L.off[i] = off;
+        off += (reads[i].bytes + 7) & ~7;
+        if (reads[i].bytes < 0 || off > kHostReadBytes) {
+            set_error("read_to_host: more than %d bytes", kHostReadBytes);
+            return SNN_EINVAL;
+        }
+    }
+    L.n = n;
+    SNN_LAUNCH(k_read_to_mailbox, 1, 128, 0, s)(L, dev);
+    SNN_LAUNCH_CHECK();
+    SNN_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < n; ++i) memcpy(reads[i].dst, host + L.off[i], size_t(reads[i].bytes));
+    return SNN_OK;
+}
+
 static unsigned grid_for(int64_t work, int threads) {
     return (unsigned)std::max<int64_t>(1, cdiv(work, threads));
 }
@@ -299,12 +366,9 @@ static snn_status index_build(const float *X, int64_t n, int d, int64_t ld, cuda
         if (cudaGetLastError() != cudaSuccess) { set_error("max launch"); TRY_IX(SNN_ECUDA); }
         float hc[2];
         int hbad[2] = {0, 0};
-        if (cudaMemcpyAsync(hc, ix->dconst, 2 * sizeof(float), cudaMemcpyDeviceToHost, s) !=
-                cudaSuccess ||
-            cudaMemcpyAsync(hbad, bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess) {
-            set_error("index build failed: %s", cudaGetErrorString(cudaGetLastError()));
-            TRY_IX(SNN_ECUDA);
+        {
+            const HostRead rd[] = {{ix->dconst, hc, int(sizeof(hc))}, {bad, hbad, int(sizeof(hbad))}};
+            TRY_IX(read_to_host(rd, 2, s));
         }
         if (hbad[0]) {
             set_error("X contains NaN or Inf");
@@ -470,12 +534,13 @@ static snn_status index_insert(snn_index *ix, const float *X, int64_t k, int64_t
     }
     float hadd[2];
     int hbad = 0;
-    if (cudaMemcpyAsync(hadd, add, sizeof(hadd), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {
-        set_error("insert failed: %s", cudaGetErrorString(cudaGetLastError()));
-        out.release(s);
-        return SNN_ECUDA;
+    {
+        const HostRead rd[] = {{add, hadd, int(sizeof(hadd))}, {bad, &hbad, int(sizeof(int))}};
+        const snn_status st = read_to_host(rd, 2, s);
+        if (st != SNN_OK) {
+            out.release(s);
+            return st;
+        }
     }
     if (hbad) {
         set_error("X contains NaN or Inf");
@@ -525,11 +590,9 @@ static snn_status index_delete(snn_index *ix, const int32_t *ids, int64_t cnt, c
     SNN_TRY(scan_exclusive<int64_t>(keep_pos, newpos, n, s));
     int64_t kept = 0;
     int hbad = 0;
-    if (cudaMemcpyAsync(&kept, newpos + n, sizeof(kept), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {
-        set_error("delete failed: %s", cudaGetErrorString(cudaGetLastError()));
-        return SNN_ECUDA;
+    {
+        const HostRead rd[] = {{newpos + n, &kept, int(sizeof(kept))}, {bad, &hbad, int(sizeof(int))}};
+        SNN_TRY(read_to_host(rd, 2, s));
     }
     if (hbad) {
         set_error("an id to delete is outside [0, n)");
@@ -565,7 +628,7 @@ static snn_status index_delete(snn_index *ix, const int32_t *ids, int64_t cnt, c
 
 // ---------------------------------------------------------------- query
 // Everything the host needs after the scoring and decision, gathered on the
-// device and copied back with one transfer.
+// device and read back at once (read_to_host).
 struct Readback {
     unsigned long long ctr[4];   // survivors, work, band pairs, candidates
     int bad, err;                // NaN/Inf in the queries, expired wait
@@ -589,19 +652,6 @@ __global__ void k_readback(const unsigned long long *__restrict__ ctr, const int
     }
 }
 
-// Pinned host buffer of the calling thread (allocated once, kept).
-static Readback *host_readback() {
-    thread_local Readback *p = nullptr;
-    if (!p) {
-        void *q = nullptr;
-        if (cudaMallocHost(&q, sizeof(Readback)) != cudaSuccess) {
-            cudaGetLastError();
-            return nullptr;
-        }
-        p = static_cast<Readback *>(q);
-    }
-    return p;
-}
 
 struct QueryScratch {
     float *alpha = nullptr, *raw = nullptr, *xc = nullptr, *hy = nullptr, *nrm = nullptr;
@@ -705,9 +755,10 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         CUDA_Q(cudaGetLastError());
         float hq = 0.f;
         int hb = 0;
-        CUDA_Q(cudaMemcpyAsync(&hq, qnmax, sizeof(float), cudaMemcpyDeviceToHost, s));
-        CUDA_Q(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CUDA_Q(cudaStreamSynchronize(s));
+        {
+            const HostRead rd[] = {{qnmax, &hq, int(sizeof(float))}, {bad, &hb, int(sizeof(int))}};
+            TRY_Q(read_to_host(rd, 2, s));
+        }
         if (hb) {
             set_error("Q contains NaN or Inf");
             return fail(SNN_EINVAL);
@@ -827,11 +878,8 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     // one host read-back per attempt (see Readback)
     Readback *dev_rb = nullptr;
     TRY_Q(scr.alloc(&dev_rb, 1));
-    Readback *hb = host_readback();
-    if (!hb) {
-        set_error("pinned host allocation failed");
-        return fail(SNN_ENOMEM);
-    }
+    Readback hb_store{};
+    Readback *hb = &hb_store;
     int64_t mma_fpp = 0;
     // FP8 where its shape and ranges allow it, BF16 otherwise
     const snn_precision used =
@@ -884,13 +932,9 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         TRY_Q(scan_exclusive<int64_t>(big_len, toff, m, s));
         SNN_LAUNCH(k_readback, 1, 32, 0, s)(ctr, bad, dev_err, out->offsets + m, cls, toff + m, dev_rb);
         CUDA_Q(cudaGetLastError());
-        CUDA_Q(cudaMemcpyAsync(hb, dev_rb, sizeof(Readback), cudaMemcpyDeviceToHost, s));
         {
-            cudaError_t e = cudaStreamSynchronize(s);
-            if (e != cudaSuccess) {
-                set_error("query failed: %s", cudaGetErrorString(e));
-                return fail(SNN_ECUDA);
-            }
+            const HostRead rd[] = {{dev_rb, hb, int(sizeof(Readback))}};
+            TRY_Q(read_to_host(rd, 1, s));
         }
         if (hb->bad) {
             set_error("Q contains NaN or Inf");
@@ -999,8 +1043,10 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     if (stats) {
         cudaEventRecord(ev[4], s);
         unsigned long long nf = 0;
-        CUDA_Q(cudaMemcpyAsync(&nf, ctr + 4, sizeof(nf), cudaMemcpyDeviceToHost, s));
-        CUDA_Q(cudaStreamSynchronize(s));
+        {
+            const HostRead rd[] = {{ctr + 4, &nf, int(sizeof(nf))}};
+            TRY_Q(read_to_host(rd, 1, s));
+        }
         stats->exact_fp64 = (int64_t)nf;
         stats->mma_flops_per_pair = mma_fpp;
         stats->precision_used = (int32_t)used;
@@ -1073,11 +1119,9 @@ static snn_status ip_search(const float *P, int64_t n, int d, int64_t ldp, const
     SNN_LAUNCH_CHECK();
     double hm[2];
     int hbad = 0;
-    if (cudaMemcpyAsync(hm, mx, sizeof(hm), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {
-        set_error("inner-product search failed: %s", cudaGetErrorString(cudaGetLastError()));
-        return SNN_ECUDA;
+    {
+        const HostRead rd[] = {{mx, hm, int(sizeof(hm))}, {bad, &hbad, int(sizeof(int))}};
+        SNN_TRY(read_to_host(rd, 2, s));
     }
     if (hbad) {
         set_error("P or Q contains NaN or Inf, or a squared norm overflows");
@@ -1146,14 +1190,20 @@ static snn_status ip_search(const float *P, int64_t n, int d, int64_t ldp, const
     SNN_LAUNCH(k_ip_offsets, grid_for(m + 1, 256), 256, 0, s)(cand.offsets, m, pos, offs);
     int64_t kept = 0;
     unsigned long long hnf = 0;
-    if (cudaGetLastError() != cudaSuccess ||
-        cudaMemcpyAsync(&kept, offs + m, sizeof(kept), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaMemcpyAsync(&hnf, nf, sizeof(hnf), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {
-        set_error("inner-product filter failed: %s", cudaGetErrorString(cudaGetLastError()));
-        cudaFreeAsync(offs, s);
-        drop(cand);
-        return SNN_ECUDA;
+    {
+        snn_status st = SNN_OK;
+        if (cudaGetLastError() != cudaSuccess) {
+            set_error("inner-product filter launch failed");
+            st = SNN_ECUDA;
+        } else {
+            const HostRead rd[] = {{offs + m, &kept, int(sizeof(kept))}, {nf, &hnf, int(sizeof(hnf))}};
+            st = read_to_host(rd, 2, s);
+        }
+        if (st != SNN_OK) {
+            cudaFreeAsync(offs, s);
+            drop(cand);
+            return st;
+        }
     }
     int32_t *oid = nullptr;
     float *oval = nullptr;
@@ -1409,9 +1459,8 @@ snn_status snn_query_radius_each(const snn_index *idx, const float *Q, int64_t m
         SNN_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
         SNN_LAUNCH(k_radii_minmax, grid_for(m, 256), 256, 0, s)(R, m, mm, bad);
         SNN_LAUNCH_CHECK();
-        SNN_CUDA(cudaMemcpyAsync(hm, mm, sizeof(hm), cudaMemcpyDeviceToHost, s));
-        SNN_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
-        SNN_CUDA(cudaStreamSynchronize(s));
+        const HostRead rd[] = {{mm, hm, int(sizeof(hm))}, {bad, &hbad, int(sizeof(int))}};
+        SNN_TRY(read_to_host(rd, 2, s));
     }
     if (hbad) {
         set_error("every radius must be finite and >= 0");

@@ -1073,7 +1073,11 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
     // R^2/2 for the largest norms; otherwise use three parts
     const double N = (double)ix->nrm_max;
     const double c2 = tc_constant(2, d, nullptr);
-    const int nsplit = (c2 * 1.5 * N * N <= 0.02 * R2h) ? 2 : 3;
+    int nsplit = (c2 * 1.5 * N * N <= 0.02 * R2h) ? 2 : 3;
+    if (const char *e = getenv("SNN_BF16_PARTS")) {
+        const int v = atoi(e);
+        if (v == 2 || v == 3) nsplit = v;
+    }
     double u_k = 0.0;
     const double c = tc_constant(nsplit, d, &u_k);
     // shape: one 32- or 64-column k-block holds everything for low d (query
