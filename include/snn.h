@@ -29,6 +29,11 @@
  *    and no output is owned by the caller.
  *  - Limits: 1 <= d <= 4096, 1 <= n < 2^31, m < 2^31, total neighbour pairs
  *    of one call < 2^31 (SNN_ENOTSUP beyond that).
+ *  - Environment variables (read at each call; none changes any result):
+ *    SNN_BF16_PARTS = 2 or 3 and SNN_FP8_PRODUCTS = 3, 4 or 6 fix the
+ *    tensor-core split (see snn_precision); SNN_SORT_KEYS64 = 1 makes the
+ *    per-row sort of the CSR build use 64-bit keys even where 32-bit keys
+ *    (id and position in the row) fit.
  */
 #ifndef SNN_H
 #define SNN_H

@@ -316,6 +316,14 @@ __global__ void k_b_offsets_end(const int64_t *__restrict__ goff, const int64_t 
 }  // namespace
 
 // Host side of snn_query_radius_batch.
+// Exclusive bound on the point ids in any set's rows (selects the per-row
+// sort's key width).
+static uint32_t ids_bound(const std::vector<SetDesc> &sd) {
+    int64_t n = 0;
+    for (const SetDesc &d : sd) n = std::max<int64_t>(n, d.n);
+    return uint32_t(n);
+}
+
 snn_status batch_query(int32_t nsets, const snn_index *const *idx, const float *const *Q,
                        const int64_t *m_in, const int64_t *ldq_in, const double *R_in,
                        cudaStream_t s, snn_csr *out) {
@@ -647,13 +655,14 @@ snn_status batch_query(int32_t nsets, const snn_index *const *idx, const float *
         SNN_LAUNCH(k_seg_classify, unsigned(cdiv(M, 256)), 256, 0, s)(goff, M, lists, big_list,
                                                                       big_len, cls);
         const unsigned wgrid = std::min<unsigned>(unsigned(cdiv(M * 32, 256)), 16384);
-        SNN_LAUNCH(k_seg_sort_w1, wgrid, 256, 0, s)(lists, cls, goff, tmp, gidx, gd2);
-        SNN_LAUNCH(k_seg_sort_w2, wgrid, 256, 0, s)(lists + 5 * M, cls + 6, goff, tmp, gidx, gd2);
-        SNN_LAUNCH(k_seg_sort_w4, wgrid, 256, 0, s)(lists + M, cls + 1, goff, tmp, gidx, gd2);
-        SNN_LAUNCH(k_seg_sort_w8, wgrid, 256, 0, s)(lists + 4 * M, cls + 5, goff, tmp, gidx, gd2);
-        SNN_LAUNCH(k_seg_sort_w16, wgrid, 256, 0, s)(lists + 2 * M, cls + 2, goff, tmp, gidx, gd2);
+        const uint32_t ib = ids_bound(sd);
+        SNN_LAUNCH(k_seg_sort_w1, wgrid, 256, 0, s)(lists, cls, goff, tmp, gidx, gd2, ib);
+        SNN_LAUNCH(k_seg_sort_w2, wgrid, 256, 0, s)(lists + 5 * M, cls + 6, goff, tmp, gidx, gd2, ib);
+        SNN_LAUNCH(k_seg_sort_w4, wgrid, 256, 0, s)(lists + M, cls + 1, goff, tmp, gidx, gd2, ib);
+        SNN_LAUNCH(k_seg_sort_w8, wgrid, 256, 0, s)(lists + 4 * M, cls + 5, goff, tmp, gidx, gd2, ib);
+        SNN_LAUNCH(k_seg_sort_w16, wgrid, 256, 0, s)(lists + 2 * M, cls + 2, goff, tmp, gidx, gd2, ib);
         SNN_LAUNCH(k_seg_sort_mid, std::min<unsigned>(unsigned(M), 4096), 256, 0, s)(
-            lists + 3 * M, cls + 3, goff, tmp, gidx, gd2);
+            lists + 3 * M, cls + 3, goff, tmp, gidx, gd2, ib);
         unsigned hcls[8];
         if (cudaMemcpyAsync(hcls, cls, sizeof(hcls), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
@@ -895,17 +904,18 @@ snn_status plan_enqueue(snn_batch_plan *p, cudaStream_t s) {
         &p->status->skip);
     SNN_LAUNCH_CHECK();
     const unsigned wgrid = unsigned(std::min<int64_t>(cdiv(std::max<int64_t>(M, 1) * 32, 256), 16384));
-    SNN_LAUNCH(k_seg_sort_w1, wgrid, 256, 0, s)(p->lists, p->cls, p->goff, p->tmp, p->gidx, p->gd2);
+    const uint32_t ib = ids_bound(p->sd);
+    SNN_LAUNCH(k_seg_sort_w1, wgrid, 256, 0, s)(p->lists, p->cls, p->goff, p->tmp, p->gidx, p->gd2, ib);
     SNN_LAUNCH(k_seg_sort_w2, wgrid, 256, 0, s)(p->lists + 5 * M, p->cls + 6, p->goff, p->tmp, p->gidx,
-                                                 p->gd2);
+                                                 p->gd2, ib);
     SNN_LAUNCH(k_seg_sort_w4, wgrid, 256, 0, s)(p->lists + M, p->cls + 1, p->goff, p->tmp, p->gidx,
-                                                 p->gd2);
+                                                 p->gd2, ib);
     SNN_LAUNCH(k_seg_sort_w8, wgrid, 256, 0, s)(p->lists + 4 * M, p->cls + 5, p->goff, p->tmp, p->gidx,
-                                                 p->gd2);
+                                                 p->gd2, ib);
     SNN_LAUNCH(k_seg_sort_w16, wgrid, 256, 0, s)(p->lists + 2 * M, p->cls + 2, p->goff, p->tmp,
-                                                  p->gidx, p->gd2);
+                                                  p->gidx, p->gd2, ib);
     SNN_LAUNCH(k_seg_sort_mid, unsigned(std::min<int64_t>(std::max<int64_t>(M, 1), 4096)), 256, 0, s)(
-        p->lists + 3 * M, p->cls + 3, p->goff, p->tmp, p->gidx, p->gd2);
+        p->lists + 3 * M, p->cls + 3, p->goff, p->tmp, p->gidx, p->gd2, ib);
     if (M > 0)
         SNN_LAUNCH(k_b_offsets, unsigned(cdiv(M, 256)), 256, 0, s)(p->goff, p->d_qglob, nsets, M,
                                                                    p->out_off, p->d_offpos);

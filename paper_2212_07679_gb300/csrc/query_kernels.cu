@@ -667,66 +667,114 @@ __global__ void k_seg_classify(const int64_t *__restrict__ offsets, int64_t m,
 // network over the blocked layout: lane l holds entries l*E .. l*E+E-1, so the
 // steps with distance < E are compare-exchanges inside a lane and only the
 // 15 steps with distance >= E cross lanes; every step is branch-free.
+// When every id of the call is below 2^(32 - log2(32E)) the network runs on
+// 32-bit keys (id << log2(32E) | position in the row), which halves the
+// shuffles and replaces each 64-bit compare-and-select by a min and a max;
+// the distances are then fetched by position after the sort.
 __device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int m) {
     const uint32_t lo = __shfl_xor_sync(0xffffffffu, uint32_t(v), m);
     const uint32_t hi = __shfl_xor_sync(0xffffffffu, uint32_t(v >> 32), m);
     return (uint64_t(hi) << 32) | lo;
 }
 
+template <int E, typename T>
+__device__ __forceinline__ void bitonic_warp(T (&v)[E], int lane) {
+    constexpr int N = 32 * E;
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= E) {
+                const int lj = j / E;
+                const bool lower = (lane & lj) == 0;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    T p;
+                    if constexpr (sizeof(T) == 8) p = shfl_xor_u64(v[e], lj);
+                    else p = __shfl_xor_sync(0xffffffffu, v[e], lj);
+                    const bool asc = ((lane * E + e) & k) == 0;
+                    const bool keep_min = lower == asc;
+                    if constexpr (sizeof(T) == 8) {
+                        const bool pl = p < v[e];
+                        v[e] = (keep_min == pl) ? p : v[e];
+                    } else {
+                        const T lo = min(p, v[e]), hi = max(p, v[e]);
+                        v[e] = keep_min ? lo : hi;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int pe = e ^ j;
+                    if (pe > e) {
+                        const bool asc = ((lane * E + e) & k) == 0;
+                        const T a = v[e], b = v[pe];
+                        if constexpr (sizeof(T) == 8) {
+                            const bool sw = (a > b) == asc;
+                            v[e] = sw ? b : a;
+                            v[pe] = sw ? a : b;
+                        } else {
+                            const T lo = min(a, b), hi = max(a, b);
+                            v[e] = asc ? lo : hi;
+                            v[pe] = asc ? hi : lo;
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
 template <int E>
 __device__ __forceinline__ void seg_sort_warp(const int32_t *__restrict__ list, unsigned total,
                                               const int64_t *__restrict__ offsets,
                                               const uint64_t *__restrict__ tmp,
-                                              int32_t *__restrict__ idx, float *__restrict__ d2) {
+                                              int32_t *__restrict__ idx, float *__restrict__ d2,
+                                              uint32_t id_bound) {
     constexpr int N = 32 * E;
+    constexpr int LB = E == 1 ? 5 : (E == 2 ? 6 : (E == 4 ? 7 : (E == 8 ? 8 : 9)));
+    static_assert((1 << LB) == N, "position bits");
+    const bool k32 = id_bound <= (1u << (32 - LB));
+    // 32-bit words of the packed entries: [2i] = dist2 bits, [2i+1] = id
+    const uint32_t *__restrict__ w32 = reinterpret_cast<const uint32_t *>(tmp);
     const int lane = threadIdx.x & 31;
     const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
     for (int64_t w = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); w < total; w += nw) {
         const int32_t r = list[w];
         const int64_t o = offsets[r];
         const int len = int(offsets[r + 1] - o);
-        uint64_t v[E];
+        if (k32) {
+            uint32_t v[E];
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int i = lane * E + e;
-            v[e] = i < len ? tmp[o + i] : ~uint64_t(0);
-        }
+            for (int e = 0; e < E; ++e) {
+                const int i = lane * E + e;
+                v[e] = i < len ? (w32[2 * (o + i) + 1] << LB) | uint32_t(i) : 0xffffffffu;
+            }
+            bitonic_warp<E>(v, lane);
 #pragma unroll
-        for (int k = 2; k <= N; k <<= 1) {
-#pragma unroll
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                if (j >= E) {
-                    const int lj = j / E;
-                    const bool lower = (lane & lj) == 0;
-#pragma unroll
-                    for (int e = 0; e < E; ++e) {
-                        const uint64_t p = shfl_xor_u64(v[e], lj);
-                        const bool asc = ((lane * E + e) & k) == 0;
-                        const bool keep_min = lower == asc;
-                        const bool pl = p < v[e];
-                        v[e] = (keep_min == pl) ? p : v[e];
-                    }
-                } else {
-#pragma unroll
-                    for (int e = 0; e < E; ++e) {
-                        const int pe = e ^ j;
-                        if (pe > e) {
-                            const bool asc = ((lane * E + e) & k) == 0;
-                            const uint64_t a = v[e], b = v[pe];
-                            const bool sw = (a > b) == asc;
-                            v[e] = sw ? b : a;
-                            v[pe] = sw ? a : b;
-                        }
-                    }
+            for (int e = 0; e < E; ++e) {
+                const int i = lane * E + e;
+                if (i < len) {
+                    const uint32_t src = v[e] & uint32_t(N - 1);
+                    idx[o + i] = int32_t(v[e] >> LB);
+                    d2[o + i] = __uint_as_float(w32[2 * (o + src)]);
                 }
             }
-        }
+        } else {
+            uint64_t v[E];
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int i = lane * E + e;
-            if (i < len) {
-                idx[o + i] = int32_t(uint32_t(v[e] >> 32));
-                d2[o + i] = __uint_as_float(uint32_t(v[e]));
+            for (int e = 0; e < E; ++e) {
+                const int i = lane * E + e;
+                v[e] = i < len ? tmp[o + i] : ~uint64_t(0);
+            }
+            bitonic_warp<E>(v, lane);
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int i = lane * E + e;
+                if (i < len) {
+                    idx[o + i] = int32_t(uint32_t(v[e] >> 32));
+                    d2[o + i] = __uint_as_float(uint32_t(v[e]));
+                }
             }
         }
     }
@@ -735,19 +783,42 @@ __device__ __forceinline__ void seg_sort_warp(const int32_t *__restrict__ list, 
 #define SNN_SEG_ARGS                                                                            \
     const int32_t *__restrict__ list, const unsigned *__restrict__ count,                       \
         const int64_t *__restrict__ offsets, const uint64_t *__restrict__ tmp, int32_t *idx,   \
-        float *d2
-__global__ void k_seg_sort_w1(SNN_SEG_ARGS) { seg_sort_warp<1>(list, *count, offsets, tmp, idx, d2); }
-__global__ void k_seg_sort_w2(SNN_SEG_ARGS) { seg_sort_warp<2>(list, *count, offsets, tmp, idx, d2); }
-__global__ void k_seg_sort_w4(SNN_SEG_ARGS) { seg_sort_warp<4>(list, *count, offsets, tmp, idx, d2); }
-__global__ void k_seg_sort_w8(SNN_SEG_ARGS) { seg_sort_warp<8>(list, *count, offsets, tmp, idx, d2); }
+        float *d2, uint32_t id_bound
+__global__ void k_seg_sort_w1(SNN_SEG_ARGS) { seg_sort_warp<1>(list, *count, offsets, tmp, idx, d2, id_bound); }
+__global__ void k_seg_sort_w2(SNN_SEG_ARGS) { seg_sort_warp<2>(list, *count, offsets, tmp, idx, d2, id_bound); }
+__global__ void k_seg_sort_w4(SNN_SEG_ARGS) { seg_sort_warp<4>(list, *count, offsets, tmp, idx, d2, id_bound); }
+__global__ void k_seg_sort_w8(SNN_SEG_ARGS) { seg_sort_warp<8>(list, *count, offsets, tmp, idx, d2, id_bound); }
 __global__ void k_seg_sort_w16(SNN_SEG_ARGS) {
-    seg_sort_warp<16>(list, *count, offsets, tmp, idx, d2);
+    seg_sort_warp<16>(list, *count, offsets, tmp, idx, d2, id_bound);
 }
 
-// One block per row of <= 4096 entries: bitonic sort of the packed entries
-// in shared memory.
+// One block per row of <= 4096 entries: bitonic sort in shared memory, of
+// 32-bit keys (id << 12 | position) when every id is below 2^20, else of the
+// packed 64-bit entries.
+template <typename T>
+__device__ __forceinline__ void block_bitonic(T *sk, int N) {
+    for (int k = 2; k <= N; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < N; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const bool asc = (i & k) == 0;
+                    const T a = sk[i], b = sk[ixj];
+                    const bool sw = (a > b) == asc;
+                    sk[i] = sw ? b : a;
+                    sk[ixj] = sw ? a : b;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_seg_sort_mid(SNN_SEG_ARGS) {
     __shared__ uint64_t sk[kSegMid];
+    uint32_t *sk32 = reinterpret_cast<uint32_t *>(sk);
+    const uint32_t *__restrict__ w32 = reinterpret_cast<const uint32_t *>(tmp);
+    const bool k32 = id_bound <= (1u << 20);
     const unsigned total = *count;
     for (unsigned w = blockIdx.x; w < total; w += gridDim.x) {
         const int32_t r = list[w];
@@ -756,26 +827,24 @@ __global__ void __launch_bounds__(256) k_seg_sort_mid(SNN_SEG_ARGS) {
         int N = 64;
         while (N < len) N <<= 1;
         __syncthreads();
-        for (int i = threadIdx.x; i < N; i += blockDim.x) sk[i] = i < len ? tmp[o + i] : ~uint64_t(0);
-        __syncthreads();
-        for (int k = 2; k <= N; k <<= 1) {
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int i = threadIdx.x; i < N; i += blockDim.x) {
-                    const int ixj = i ^ j;
-                    if (ixj > i) {
-                        const bool asc = (i & k) == 0;
-                        const uint64_t a = sk[i], b = sk[ixj];
-                        const bool sw = (a > b) == asc;
-                        sk[i] = sw ? b : a;
-                        sk[ixj] = sw ? a : b;
-                    }
-                }
-                __syncthreads();
+        if (k32) {
+            for (int i = threadIdx.x; i < N; i += blockDim.x)
+                sk32[i] = i < len ? (w32[2 * (o + i) + 1] << 12) | uint32_t(i) : 0xffffffffu;
+            __syncthreads();
+            block_bitonic(sk32, N);
+            for (int i = threadIdx.x; i < len; i += blockDim.x) {
+                const uint32_t v = sk32[i];
+                idx[o + i] = int32_t(v >> 12);
+                d2[o + i] = __uint_as_float(w32[2 * (o + (v & 4095u))]);
             }
-        }
-        for (int i = threadIdx.x; i < len; i += blockDim.x) {
-            idx[o + i] = int32_t(uint32_t(sk[i] >> 32));
-            d2[o + i] = __uint_as_float(uint32_t(sk[i]));
+        } else {
+            for (int i = threadIdx.x; i < N; i += blockDim.x) sk[i] = i < len ? tmp[o + i] : ~uint64_t(0);
+            __syncthreads();
+            block_bitonic(sk, N);
+            for (int i = threadIdx.x; i < len; i += blockDim.x) {
+                idx[o + i] = int32_t(uint32_t(sk[i] >> 32));
+                d2[o + i] = __uint_as_float(uint32_t(sk[i]));
+            }
         }
     }
 }

@@ -194,23 +194,24 @@ __global__ void k_scatter(const uint2 *rec_rc, const int32_t *rec_pos, const flo
                           int64_t nsurv, int64_t rstride, int sym, const int64_t *offsets,
                           uint64_t *tmp);
 
-// Segmented sort of CSR rows by column id.
+// Segmented sort of CSR rows by column id; id_bound is an exclusive upper
+// bound on the ids (it selects 32-bit sort keys where they fit).
 constexpr int kSegSmall = 32;
 constexpr int kSegMid = 4096;
 __global__ void k_seg_classify(const int64_t *offsets, int64_t m, int32_t *lists,
                                int32_t *big_list, int64_t *big_len, unsigned *counters);
 __global__ void k_seg_sort_w1(const int32_t *list, const unsigned *count, const int64_t *offsets,
-                          const uint64_t *tmp, int32_t *idx, float *d2);
+                          const uint64_t *tmp, int32_t *idx, float *d2, uint32_t id_bound);
 __global__ void k_seg_sort_w16(const int32_t *list, const unsigned *count, const int64_t *offsets,
-                          const uint64_t *tmp, int32_t *idx, float *d2);
+                          const uint64_t *tmp, int32_t *idx, float *d2, uint32_t id_bound);
 __global__ void k_seg_sort_w8(const int32_t *list, const unsigned *count, const int64_t *offsets,
-                          const uint64_t *tmp, int32_t *idx, float *d2);
+                          const uint64_t *tmp, int32_t *idx, float *d2, uint32_t id_bound);
 __global__ void k_seg_sort_w2(const int32_t *list, const unsigned *count, const int64_t *offsets,
-                          const uint64_t *tmp, int32_t *idx, float *d2);
+                          const uint64_t *tmp, int32_t *idx, float *d2, uint32_t id_bound);
 __global__ void k_seg_sort_w4(const int32_t *list, const unsigned *count, const int64_t *offsets,
-                          const uint64_t *tmp, int32_t *idx, float *d2);
+                          const uint64_t *tmp, int32_t *idx, float *d2, uint32_t id_bound);
 __global__ void k_seg_sort_mid(const int32_t *list, const unsigned *count, const int64_t *offsets,
-                          const uint64_t *tmp, int32_t *idx, float *d2);
+                          const uint64_t *tmp, int32_t *idx, float *d2, uint32_t id_bound);
 __global__ void k_seg_big_gather(const int32_t *big_list, int nbig, const int64_t *offsets,
                                  const int64_t *toff, const uint64_t *tmp, uint64_t *keys,
                                  uint32_t *vals, float *gd2);

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <unordered_map>
@@ -998,17 +999,21 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         int32_t *oi = out->indices;
         float *od = out->dist2;
         const int64_t *oo = out->offsets;
-        if (hc[0]) SNN_LAUNCH(k_seg_sort_w1, wgrid(hc[0]), 256, 0, s)(lists, cls, oo, tmp, oi, od);
+        // ids are point ids of the index; SNN_SORT_KEYS64=1 forces the
+        // 64-bit sort keys (both widths give the same rows)
+        const char *k64 = getenv("SNN_SORT_KEYS64");
+        const uint32_t ib = (k64 && k64[0] == '1') ? 0xffffffffu : uint32_t(ix->n);
+        if (hc[0]) SNN_LAUNCH(k_seg_sort_w1, wgrid(hc[0]), 256, 0, s)(lists, cls, oo, tmp, oi, od, ib);
         if (hc[6]) SNN_LAUNCH(k_seg_sort_w2, wgrid(hc[6]), 256, 0, s)(lists + 5 * m, cls + 6, oo, tmp,
-                                                                     oi, od);
+                                                                     oi, od, ib);
         if (hc[1]) SNN_LAUNCH(k_seg_sort_w4, wgrid(hc[1]), 256, 0, s)(lists + m, cls + 1, oo, tmp, oi,
-                                                                     od);
+                                                                     od, ib);
         if (hc[5]) SNN_LAUNCH(k_seg_sort_w8, wgrid(hc[5]), 256, 0, s)(lists + 4 * m, cls + 5, oo, tmp,
-                                                                     oi, od);
+                                                                     oi, od, ib);
         if (hc[2]) SNN_LAUNCH(k_seg_sort_w16, wgrid(hc[2]), 256, 0, s)(lists + 2 * m, cls + 2, oo,
-                                                                      tmp, oi, od);
+                                                                      tmp, oi, od, ib);
         if (hc[3]) SNN_LAUNCH(k_seg_sort_mid, std::min<unsigned>(hc[3], 4096), 256, 0, s)(
-            lists + 3 * m, cls + 3, oo, tmp, oi, od);
+            lists + 3 * m, cls + 3, oo, tmp, oi, od, ib);
         CUDA_Q(cudaGetLastError());
         const int nbig = (int)hc[4];
         if (nbig > 0) {

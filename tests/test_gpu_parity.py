@@ -451,3 +451,23 @@ def test_to_host_pinned_copies(snn):
         assert np.array_equal(host.indices.numpy(), out.indices.cpu().numpy())
         assert np.array_equal(host.dist2.numpy().view(np.uint32), out.dist2.cpu().numpy().view(np.uint32))
         assert_csr_equal(out, oracle.brute_radius(P, None, R), f"R={R}")
+
+
+@pytest.mark.parametrize("keys64", ["0", "1"])
+def test_row_sort_key_widths(snn, monkeypatch, keys64):
+    """Rows of every length class (warp sorts up to 512, block sort up to
+    4,096, radix beyond) with the 32-bit sort keys (id, position) and with
+    the 64-bit packed keys forced by SNN_SORT_KEYS64: both equal the oracle."""
+    monkeypatch.setenv("SNN_SORT_KEYS64", keys64)
+    rng = np.random.default_rng(43)
+    parts = [rng.normal(0.0, 0.01, (5000, 3)),                 # rows of ~5,000 (radix)
+             rng.normal(5.0, 0.01, (1500, 3)),                 # ~1,500 (block sort)
+             rng.normal(-5.0, 0.3, (3000, 3)),                 # tens to hundreds (warp sorts)
+             rng.uniform(-20.0, 20.0, (2000, 3))]              # short rows
+    P = np.concatenate(parts).astype(np.float32)
+    P = P[rng.permutation(len(P))]
+    got = _run(snn, P, None, 0.2, "bf16")
+    ref = oracle.brute_radius(P, None, 0.2)
+    lens = np.diff(ref.offsets)
+    assert lens.max() > 4096 and ((lens > 512) & (lens <= 4096)).any() and (lens <= 32).any()
+    assert_csr_equal(got, ref, f"keys64={keys64}")
