@@ -29,6 +29,30 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x m
 HBM_PEAK_FALLBACK = 6800.0
 
 
+# DRAM bytes of one scorer launch at full size, from one-pass ncu counters
+# (profiles/k_score_tc_dram_traffic_full_size.md), valid only for the scorer
+# sources they were taken with (hash below); any other build reports null.
+SCORER_SOURCES = ["tc_score.cu", "tc_score.cuh", "tc_common.cuh", "common.cuh", "index_struct.cuh",
+                  "query_kernels.cuh"]
+SCORER_TRAFFIC = {
+    "sha": "0105b4a6d63a377a",
+    "profile": "profiles/k_score_tc_dram_traffic_full_size.md",
+    ("gmm_aniso", 1000000, "bf16"): 257319680 + 180205568,
+    ("lowrank_img", 70000, "bf16"): 7361981184 + 9142784,
+}
+
+
+def scorer_traffic(workload: str, n: int, precision: str):
+    import hashlib
+    h = hashlib.sha256()
+    for f in SCORER_SOURCES:
+        with open(os.path.join(ROOT, "paper_2212_07679_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != SCORER_TRAFFIC["sha"]:
+        return None
+    return SCORER_TRAFFIC.get((workload, n, precision))
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -428,8 +452,13 @@ def run_ours(args):
         f8 = args.precision == "fp8" and st["precision_used"] == 2
         peak = float(peaks["bf16_tflops_sustained"]) * (2.0 if f8 else 1.0)
         pipe = st["mma_flops_per_pair"] * st["band_pairs"] / (sm / 1e3) / 1e12
+        used = ["fp32", "bf16", "fp8"][st["precision_used"]]
+        traffic = scorer_traffic(w.name, w.n, used) if w.Q is None else None
         roofline = {"kernel": "k_score_tc", "bound": "tensor", "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                    "traffic_source": (f"{SCORER_TRAFFIC['profile']} (dram__bytes_read.sum + "
+                                       "dram__bytes_write.sum of one full-size launch)") if traffic else
+                                      "no full-size capture of this kernel build and workload",
                     "peak_source": (f"MEASURED_PEAKS.json bf16_tflops_sustained x 2 (e4m3 nominal ratio; {src})"
                                     if f8 else f"MEASURED_PEAKS.json bf16_tflops_sustained ({src})"),
                     "algorithmic": "2d flop per scored pair (Eq. (4)); the symmetric self-join "
