@@ -420,12 +420,21 @@ snn_status snn_sort_scores_noalloc(const float *alpha, int64_t n, float *alpha_s
 
 /* Test-only fault injection (the paper has no counterpart): arms a one-shot
  * fault for the next call that reaches it, to exercise failure detection
- * without faulting the GPU.  SNN_FAULT_STALL_TC_PRODUCER makes the next
- * tensor-core scoring launch issue no TMA loads; its consumers' bounded waits
- * (about 2 s of SM clock) expire, the kernel frees its TMEM and exits, and the
- * query returns SNN_ETIMEOUT with the CUDA context still usable.  0 disarms.
- * Returns SNN_EINVAL for an unknown fault. */
+ * without faulting the GPU (one fault is armed at a time).
+ *  SNN_FAULT_STALL_TC_PRODUCER  the next tensor-core scoring launch issues no
+ *      TMA loads; its consumers' bounded waits (about 2 s of SM clock) expire,
+ *      the kernel frees its TMEM and exits, and the query returns
+ *      SNN_ETIMEOUT with the CUDA context still usable.
+ *  SNN_FAULT_SMALL_SURVIVOR_BUFFER  the next query sizes its survivor buffer
+ *      at one entry: the scoring overflows it (counting, never writing past
+ *      the end) and the query re-runs with the exact size; the result is
+ *      unchanged.
+ *  SNN_FAULT_DEVICE_ALLOC  the next library device allocation fails: the
+ *      call returns SNN_ENOMEM and releases what it had allocated.
+ * 0 disarms.  Returns SNN_EINVAL for an unknown fault. */
 #define SNN_FAULT_STALL_TC_PRODUCER 1
+#define SNN_FAULT_SMALL_SURVIVOR_BUFFER 2
+#define SNN_FAULT_DEVICE_ALLOC 3
 snn_status snn_test_inject(int32_t fault);
 
 /* Throughput probe for roofline denominators (the paper has no counterpart).

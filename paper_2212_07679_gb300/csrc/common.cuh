@@ -47,6 +47,10 @@ struct Status {
     } while (0)
 
 // ------------------------------------------------- stream-ordered scratch
+// One-shot fault armed by snn_test_inject: true (and disarmed) when fault
+// `which` is armed; another armed fault stays armed.
+bool take_fault(int which);
+
 // Device scratch taken from the stream-ordered pool and returned on
 // destruction (cudaFreeAsync on the same stream).
 class Scratch {
@@ -62,6 +66,10 @@ class Scratch {
         size_t bytes = count * sizeof(T);
         if (bytes == 0) bytes = 16;
         bytes = (bytes + 255) & ~size_t(255);
+        if (take_fault(SNN_FAULT_DEVICE_ALLOC)) {
+            set_error("device scratch of %zu bytes: injected test fault", bytes);
+            return SNN_ENOMEM;
+        }
         cudaError_t e = cudaMallocAsync(&q, bytes, s_);
         if (e != cudaSuccess) {
             set_error("device scratch of %zu bytes: %s", bytes, cudaGetErrorString(e));
@@ -152,8 +160,6 @@ snn_status read_to_host(const HostRead *reads, int n, cudaStream_t s);
 // out = max(out, max_i x[i]) for non-negative x (snn_api.cu).
 __global__ void k_max_nonneg(const float *x, int64_t n, float *out);
 
-// One-shot fault armed by snn_test_inject (0 = none); reading clears it.
-int take_injected_fault();
 
 // Allocation-free stable sort of FP32 scores (noalloc_sort.cu).
 snn_status sort_scores_noalloc(const float *alpha, int64_t n, float *alpha_sorted, int32_t *order,

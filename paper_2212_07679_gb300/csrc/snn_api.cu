@@ -107,7 +107,10 @@ unsigned long long launch_count_now() { return g_launches.load(std::memory_order
 namespace {
 std::atomic<int> g_inject{0};
 }
-int take_injected_fault() { return g_inject.exchange(0); }
+bool take_fault(int which) {
+    int expect = which;
+    return which != 0 && g_inject.compare_exchange_strong(expect, 0);
+}
 
 int device_sm_count() {
     int dev = 0, sms = 0;
@@ -194,6 +197,10 @@ static snn_status dev_alloc(T **p, size_t count, cudaStream_t s) {
     void *q = nullptr;
     size_t bytes = std::max<size_t>(count * sizeof(T), 16);
     bytes = (bytes + 255) & ~size_t(255);
+    if (take_fault(SNN_FAULT_DEVICE_ALLOC)) {
+        set_error("device allocation of %zu bytes failed: injected test fault", bytes);
+        return SNN_ENOMEM;
+    }
     cudaError_t e = cudaMallocAsync(&q, bytes, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -841,6 +848,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     // costs one re-run with the exact count
     int64_t cap = std::max<int64_t>(int64_t(1) << 20,
                                     int64_t(std::ceil((hint > 0 ? hint * 1.25 : 96.0) * m)) + 4096);
+    if (take_fault(SNN_FAULT_SMALL_SURVIVOR_BUFFER)) cap = 1;   // forces the overflow re-run
     ScoreArgs sa;
     sa.q = qs;
     sa.x = ds;
@@ -1512,7 +1520,8 @@ uint64_t snn_launch_count(void) { return g_launches.load(std::memory_order_relax
 
 snn_status snn_test_inject(int32_t fault) {
     clear_error();
-    if (fault != 0 && fault != SNN_FAULT_STALL_TC_PRODUCER) {
+    if (fault != 0 && fault != SNN_FAULT_STALL_TC_PRODUCER && fault != SNN_FAULT_SMALL_SURVIVOR_BUFFER &&
+        fault != SNN_FAULT_DEVICE_ALLOC) {
         set_error("unknown fault %d", (int)fault);
         return SNN_EINVAL;
     }

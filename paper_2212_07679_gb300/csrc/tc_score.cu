@@ -917,7 +917,7 @@ TcArgs tc_args(const snn_index *ix, const ScoreArgs &sa, const TileSet &ts) {
     a.cap = sa.cap;
     a.count = sa.count;
     a.err = sa.err;
-    a.stall = take_injected_fault() == SNN_FAULT_STALL_TC_PRODUCER ? 1 : 0;
+    a.stall = take_fault(SNN_FAULT_STALL_TC_PRODUCER) ? 1 : 0;
     return a;
 }
 

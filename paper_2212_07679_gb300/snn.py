@@ -582,6 +582,8 @@ def version() -> str:
 
 
 SNN_FAULT_STALL_TC_PRODUCER = 1
+SNN_FAULT_SMALL_SURVIVOR_BUFFER = 2
+SNN_FAULT_DEVICE_ALLOC = 3
 
 
 def test_inject(fault: int) -> None:

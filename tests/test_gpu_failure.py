@@ -58,3 +58,58 @@ def test_norm_range_guard(snn):
     with pytest.raises(snn.SNNError) as e:
         ix.query(_dev(far), 1.0)
     assert e.value.status == snn.SNN_ENOTSUP
+
+
+@pytest.mark.parametrize("prec,oos", [("fp32", False), ("bf16", False), ("bf16", True)])
+def test_survivor_overflow_rerun_gives_the_same_result(snn, prec, oos):
+    """A one-entry survivor buffer overflows at once; the scorer counts
+    without writing past the end and the query re-runs with the exact size."""
+    rng = np.random.default_rng(35)
+    P = rng.standard_normal((5000, 16)).astype(np.float32)
+    Q = rng.standard_normal((700, 16)).astype(np.float32) if oos else None
+    R = 3.0
+    ix = snn.Index(_dev(P))
+    snn.test_inject(snn.SNN_FAULT_SMALL_SURVIVOR_BUFFER)
+    got = ix.query(None if Q is None else _dev(Q), R, precision=prec, stats=True)
+    ref = oracle.brute_radius(P, Q, R)
+    assert got.stats["survivors"] > 1
+    assert np.array_equal(got.offsets.cpu().numpy(), ref.offsets)
+    assert np.array_equal(got.indices.cpu().numpy(), ref.ids)
+    assert np.array_equal(got.dist2.cpu().numpy().view(np.uint32), ref.dist2.view(np.uint32))
+
+
+def test_device_allocation_failure_is_reported_and_recovered(snn):
+    """An injected allocation failure makes the call return SNN_ENOMEM; the
+    call releases what it held, an index survives a failed insert unchanged,
+    and the next calls succeed."""
+    rng = np.random.default_rng(36)
+    P = rng.standard_normal((3000, 8)).astype(np.float32)
+    R = 1.5
+    try:
+        snn.test_inject(snn.SNN_FAULT_DEVICE_ALLOC)
+        with pytest.raises(snn.SNNError) as e:
+            snn.Index(_dev(P))
+        assert e.value.status == snn.SNN_ENOMEM
+        ix = snn.Index(_dev(P))
+        ref = oracle.brute_radius(P, None, R)
+        snn.test_inject(snn.SNN_FAULT_DEVICE_ALLOC)
+        with pytest.raises(snn.SNNError) as e:
+            ix.query(None, R, precision="bf16")
+        assert e.value.status == snn.SNN_ENOMEM
+        got = ix.query(None, R, precision="bf16")
+        assert np.array_equal(got.indices.cpu().numpy(), ref.ids)
+        # a failed insert leaves the index as it was
+        snn.test_inject(snn.SNN_FAULT_DEVICE_ALLOC)
+        extra = rng.standard_normal((500, 8)).astype(np.float32)
+        with pytest.raises(snn.SNNError) as e:
+            ix.insert(_dev(extra))
+        assert e.value.status == snn.SNN_ENOMEM
+        got = ix.query(None, R, precision="fp32")
+        assert np.array_equal(got.offsets.cpu().numpy(), ref.offsets)
+        assert np.array_equal(got.indices.cpu().numpy(), ref.ids)
+        ix.insert(_dev(extra))
+        both = np.concatenate([P, extra])
+        got = ix.query(None, R, precision="fp32")
+        assert np.array_equal(got.indices.cpu().numpy(), oracle.brute_radius(both, None, R).ids)
+    finally:
+        snn.test_inject(0)

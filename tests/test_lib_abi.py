@@ -79,6 +79,9 @@ def test_fault_injection_arguments_need_no_gpu(libpath):
     lib = ctypes.CDLL(libpath)
     lib.snn_test_inject.argtypes = [ctypes.c_int32]
     assert lib.snn_test_inject(99) == 1
+    assert lib.snn_test_inject(4) == 1
+    for fault in (1, 2, 3):           # armed, then disarmed: no GPU call reaches them
+        assert lib.snn_test_inject(fault) == 0
     assert lib.snn_test_inject(0) == 0
 
 
