@@ -12,6 +12,8 @@ Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
 from __future__ import annotations
 
 import argparse
+import contextlib
+import gc
 import json
 import math
 import os
@@ -51,6 +53,20 @@ def scorer_traffic(workload: str, n: int, precision: str):
     if h.hexdigest()[:16] != SCORER_TRAFFIC["sha"]:
         return None
     return SCORER_TRAFFIC.get((workload, n, precision))
+
+
+@contextlib.contextmanager
+def no_gc():
+    """Python's cyclic garbage collector off inside a timed region (as timeit
+    does): a full collection of the interpreter's objects can stall the host
+    for tens of milliseconds, which would be charged to whichever step it
+    lands in."""
+    gc.collect()
+    gc.disable()
+    try:
+        yield
+    finally:
+        gc.enable()
 
 
 def load_peaks():
@@ -323,22 +339,23 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks.start()
     launches0 = snn.launch_count()
-    for _ in range(args.steps):
-        flush.fill_(1)
-        e0 = torch.cuda.Event(enable_timing=True)
-        em = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ix, out = step(stats=True, e_mid=em)
-        e1.record(stream)
-        e1.synchronize()
-        per_step.append(e0.elapsed_time(e1))
-        index_ms.append(e0.elapsed_time(em))
-        score_ms.append(out.stats["ms_score"])
-        stats_list.append(out.stats)
-        del ix
-        last_out = out
-        del out
+    with no_gc():
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            em = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ix, out = step(stats=True, e_mid=em)
+            e1.record(stream)
+            e1.synchronize()
+            per_step.append(e0.elapsed_time(e1))
+            index_ms.append(e0.elapsed_time(em))
+            score_ms.append(out.stats["ms_score"])
+            stats_list.append(out.stats)
+            del ix
+            last_out = out
+            del out
     torch.cuda.synchronize()
     launches = snn.launch_count() - launches0
     clk = clocks.stop()
@@ -418,22 +435,24 @@ def run_ours(args):
     d2h = host.offsets.numel() * 8 + host.indices.numel() * 4 + host.dist2.numel() * 4
     del host
     e2e_ms = []
-    for it in range(max(1, min(args.steps, 3))):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        e2e_step(streams[0], hbufs[0], True)
-        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    with no_gc():
+        for it in range(max(1, min(args.steps, 3))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_step(streams[0], hbufs[0], True)
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
     # three pipelined passes of n_pipe steps each; the median pass is
     # reported (one pass can catch a host-side stall), all three are listed
     n_pipe = max(4, min(args.steps, 8))
     pipe_passes = []
     for _ in range(3):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for it in range(n_pipe):
-            e2e_step(streams[it % 2], hbufs[it % 2], False)
-        torch.cuda.synchronize()
-        pipe_passes.append(1e3 * (time.perf_counter() - t0) / n_pipe)
+        with no_gc():
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for it in range(n_pipe):
+                e2e_step(streams[it % 2], hbufs[it % 2], False)
+            torch.cuda.synchronize()
+            pipe_passes.append(1e3 * (time.perf_counter() - t0) / n_pipe)
     e2e_pipe_ms = float(np.median(pipe_passes))
 
     st = stats_list[-1]

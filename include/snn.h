@@ -383,6 +383,27 @@ void snn_free(void *p);
  * the stream the index was built on (same rules as snn_free). */
 void snn_index_free(snn_index *idx);
 
+/* Index checkpoint (the paper has no counterpart): the index record of
+ * Algorithm 1 -- n, d, the centre mu, the direction v1, the sorted scores,
+ * the permutation, the halved norms, the norm bounds and the sorted raw and
+ * centred rows -- as one little-endian byte image in caller-owned host
+ * memory.  The tensor-core operands derived from it are not stored; a loaded
+ * index rebuilds them on first use, and every query on it returns exactly
+ * what the saved index returned.
+ * snn_index_saved_size: *bytes = the image size of idx.
+ * snn_index_save: writes the image into buf (host, >= that size), with
+ *   device-to-host copies on `stream`, which it synchronises.
+ * snn_index_load: a new index (free with snn_index_free) on the current
+ *   device from an image in buf (host, `bytes` long), with host-to-device
+ *   copies on `stream`, which it synchronises.
+ * Errors: SNN_EINVAL for NULL arguments, a buffer shorter than the image, or
+ * an image whose magic, version or sizes do not match this format (checked on
+ * the host before any device work); SNN_ENOMEM / SNN_ECUDA on device
+ * failures. */
+snn_status snn_index_saved_size(const snn_index *idx, int64_t *bytes);
+snn_status snn_index_save(const snn_index *idx, void *buf, int64_t bytes, void *stream);
+snn_status snn_index_load(const void *buf, int64_t bytes, void *stream, snn_index **out);
+
 /* Message for the calling thread's last non-OK status ("" if none). */
 const char *snn_last_error(void);
 

@@ -73,7 +73,7 @@ def build(verbose: bool = False, extra: list[str] | None = None, jobs: int | Non
     stamp = LIB + ".stamp"
     if todo or not os.path.exists(LIB) or not os.path.exists(stamp) or open(stamp).read() != link_tag:
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -327,6 +327,7 @@ static uint32_t ids_bound(const std::vector<SetDesc> &sd) {
 snn_status batch_query(int32_t nsets, const snn_index *const *idx, const float *const *Q,
                        const int64_t *m_in, const int64_t *ldq_in, const double *R_in,
                        cudaStream_t s, snn_csr *out) {
+    NvtxPhase nvtx_("snn batched query");
     for (int32_t t = 0; t < nsets; ++t) std::memset(&out[t], 0, sizeof(out[t]));
     if (nsets == 0) return SNN_OK;
     // ------------------------------------------------------- host plan
@@ -835,6 +836,7 @@ snn_status plan_alloc(snn_batch_plan *p, T **ptr, int64_t count, cudaStream_t s)
 
 // One run, enqueued on s: no synchronisation, every size from the plan.
 snn_status plan_enqueue(snn_batch_plan *p, cudaStream_t s) {
+    NvtxPhase nvtx_("snn batch plan run");
     const int nsets = p->nsets;
     const int64_t M = p->M, ntiles = p->ntiles, Moos = p->Moos;
     SNN_CUDA(cudaMemsetAsync(p->bad, 0, sizeof(int), s));

@@ -22,6 +22,7 @@ int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 snn_status index_build_batch(int32_t nsets, const float *const *X, const int64_t *n,
                              const int32_t *d, const int64_t *ld, cudaStream_t s,
                              snn_index **out) {
+    NvtxPhase nvtx_("snn batched index build");
     ensure_pool();
     for (int32_t t = 0; t < nsets; ++t) out[t] = nullptr;
     if (nsets == 0) return SNN_OK;

@@ -7,9 +7,26 @@
 #include <cstdarg>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "snn.h"
 
 namespace snn {
+
+// NVTX ranges over the library's calls and their phases (visible in Nsight
+// Systems; without a tool attached each push/pop is a cheap no-op).  The
+// range is popped when the object goes out of scope, on every return path.
+class NvtxPhase {
+  public:
+    explicit NvtxPhase(const char *name) { nvtxRangePushA(name); }
+    void next(const char *name) {
+        nvtxRangePop();
+        nvtxRangePushA(name);
+    }
+    ~NvtxPhase() { nvtxRangePop(); }
+    NvtxPhase(const NvtxPhase &) = delete;
+    NvtxPhase &operator=(const NvtxPhase &) = delete;
+};
 
 // ---------------------------------------------------------------- errors
 void set_error(const char *fmt, ...);

@@ -45,6 +45,7 @@ extern "C" {
 
 snn_status snn_normalize_rows(const float *X, int64_t n, int32_t d, int64_t ld, float *out,
                               int64_t ldo, void *stream) {
+    NvtxPhase nvtx_("snn normalize rows");
     clear_error();
     if (n < 0 || d < 1 || ld < d || ldo < d || (n > 0 && (!X || !out))) {
         set_error("invalid arguments (n >= 0, d >= 1, ld and ldo >= d, non-NULL arrays)");

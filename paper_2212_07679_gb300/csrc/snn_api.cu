@@ -243,6 +243,143 @@ void index_release(snn_index *ix) {
     delete ix;
 }
 
+// ------------------------------------------------- index save / load
+// Serialised index: a fixed header, then the arrays of the index record in
+// this order, each starting on a 16-byte boundary: mu64[d], mu32[d], v64[d],
+// v32[d], dconst[4], alpha[n], order[n], hx[n], nrm[n], praw[n*dp], xc[n*dp].
+// Derived operands (the BF16 / e4m3 splits) are not stored: they are rebuilt
+// on first use.  Little-endian, as on both host architectures this targets.
+namespace {
+struct SavedHeader {
+    char magic[8];          // "SNNIDX\0\1"
+    int32_t version, d;
+    int64_t n;
+    int32_t dp, reserved;
+    float alpha_err, nrm_max;
+};
+constexpr char kSaveMagic[8] = {'S', 'N', 'N', 'I', 'D', 'X', 0, 1};
+constexpr int32_t kSaveVersion = 1;
+
+struct SavedArray {
+    size_t off, bytes;
+};
+
+// Byte offsets of the arrays after the header (16-byte aligned) and the total.
+int64_t saved_layout(int64_t n, int d, int dp, SavedArray (&a)[11]) {
+    const size_t sz[11] = {sizeof(double) * d, sizeof(float) * d, sizeof(double) * d, sizeof(float) * d,
+                           sizeof(float) * 4,  sizeof(float) * n, sizeof(int32_t) * n, sizeof(float) * n,
+                           sizeof(float) * n,  sizeof(float) * n * dp, sizeof(float) * n * dp};
+    size_t off = (sizeof(SavedHeader) + 15) & ~size_t(15);
+    for (int i = 0; i < 11; ++i) {
+        a[i] = {off, sz[i]};
+        off = (off + sz[i] + 15) & ~size_t(15);
+    }
+    return int64_t(off);
+}
+
+void *saved_ptr(const snn_index *ix, int i) {
+    void *p[11] = {ix->mu64, ix->mu32, ix->v64, ix->v32, ix->dconst, ix->alpha,
+                   ix->order, ix->hx, ix->nrm, ix->praw, ix->xc};
+    return p[i];
+}
+}  // namespace
+
+static snn_status index_save(const snn_index *ix, void *buf, int64_t bytes, cudaStream_t s) {
+    NvtxPhase nvtx_("snn index save");
+    SavedArray a[11];
+    const int64_t need = saved_layout(ix->n, ix->d, ix->dp, a);
+    if (bytes < need) {
+        set_error("the buffer holds %lld bytes, the index needs %lld", (long long)bytes, (long long)need);
+        return SNN_EINVAL;
+    }
+    unsigned char *b = static_cast<unsigned char *>(buf);
+    std::memset(b, 0, size_t(need));
+    SavedHeader h{};
+    std::memcpy(h.magic, kSaveMagic, 8);
+    h.version = kSaveVersion;
+    h.d = ix->d;
+    h.n = ix->n;
+    h.dp = ix->dp;
+    h.alpha_err = ix->alpha_err;
+    h.nrm_max = ix->nrm_max;
+    std::memcpy(b, &h, sizeof(h));
+    for (int i = 0; i < 11; ++i)
+        SNN_CUDA(cudaMemcpyAsync(b + a[i].off, saved_ptr(ix, i), a[i].bytes, cudaMemcpyDeviceToHost, s));
+    SNN_CUDA(cudaStreamSynchronize(s));
+    return SNN_OK;
+}
+
+static snn_status index_load(const void *buf, int64_t bytes, cudaStream_t s, snn_index **out) {
+    NvtxPhase nvtx_("snn index load");
+    SavedHeader h{};
+    if (bytes < int64_t(sizeof(h))) {
+        set_error("the buffer is shorter than an index header");
+        return SNN_EINVAL;
+    }
+    std::memcpy(&h, buf, sizeof(h));
+    if (std::memcmp(h.magic, kSaveMagic, 8) != 0 || h.version != kSaveVersion) {
+        set_error("not a saved index of this format (magic or version differs)");
+        return SNN_EINVAL;
+    }
+    if (h.d < 1 || h.d > 4096 || h.dp != ((h.d + 3) & ~3) || h.n < 1 || h.n >= (int64_t(1) << 31) ||
+        !(h.alpha_err >= 0.f) || !(h.nrm_max >= 0.f) || !(double(h.nrm_max) <= kMaxCentredNorm)) {
+        set_error("corrupt index header (n %lld, d %d, dp %d)", (long long)h.n, h.d, h.dp);
+        return SNN_EINVAL;
+    }
+    SavedArray a[11];
+    const int64_t need = saved_layout(h.n, h.d, h.dp, a);
+    if (bytes < need) {
+        set_error("the buffer holds %lld bytes, a saved index of n %lld, d %d needs %lld",
+                  (long long)bytes, (long long)h.n, h.d, (long long)need);
+        return SNN_EINVAL;
+    }
+    ensure_pool();
+    snn_index *ix = new (std::nothrow) snn_index();
+    if (!ix) {
+        set_error("host allocation failed");
+        return SNN_ENOMEM;
+    }
+    ix->n = h.n;
+    ix->d = h.d;
+    ix->dp = h.dp;
+    ix->stream = s;
+    ix->alpha_err = h.alpha_err;
+    ix->nrm_max = h.nrm_max;
+    cudaGetDevice(&ix->device);
+    snn_status st = SNN_OK;
+    const int64_t n = h.n, nd = h.n * h.dp;
+    const int d = h.d;
+    if (st == SNN_OK) st = dev_alloc(&ix->mu64, d, s);
+    if (st == SNN_OK) st = dev_alloc(&ix->mu32, d, s);
+    if (st == SNN_OK) st = dev_alloc(&ix->v64, d, s);
+    if (st == SNN_OK) st = dev_alloc(&ix->v32, d, s);
+    if (st == SNN_OK) st = dev_alloc(&ix->dconst, 4, s);
+    if (st == SNN_OK) st = dev_alloc(&ix->alpha, n, s);
+    if (st == SNN_OK) st = dev_alloc(&ix->order, n, s);
+    if (st == SNN_OK) st = dev_alloc(&ix->hx, n, s);
+    if (st == SNN_OK) st = dev_alloc(&ix->nrm, n, s);
+    if (st == SNN_OK) st = dev_alloc(&ix->praw, nd, s);
+    if (st == SNN_OK) st = dev_alloc(&ix->xc, nd, s);
+    const unsigned char *b = static_cast<const unsigned char *>(buf);
+    for (int i = 0; i < 11 && st == SNN_OK; ++i)
+        if (cudaMemcpyAsync(saved_ptr(ix, i), b + a[i].off, a[i].bytes, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess) {
+            set_error("index load copy failed: %s", cudaGetErrorString(cudaGetLastError()));
+            st = SNN_ECUDA;
+        }
+    if (st == SNN_OK && cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("index load failed: %s", cudaGetErrorString(cudaGetLastError()));
+        st = SNN_ECUDA;
+    }
+    if (st != SNN_OK) {
+        cudaStreamSynchronize(s);
+        index_release(ix);
+        return st;
+    }
+    *out = ix;
+    return SNN_OK;
+}
+
 // ---------------------------------------------------------- index build
 static snn_status project_sort_gather(const float *X, int64_t n, int d, int64_t ld, int dp,
                                       const float *cvec, const float *v32, cudaStream_t s,
@@ -290,6 +427,7 @@ static snn_status first_direction(const double *C, const double *diagC, int d, d
 
 static snn_status index_build(const float *X, int64_t n, int d, int64_t ld, cudaStream_t s,
                               snn_index **out) {
+    NvtxPhase nvtx_("snn index build");
     ensure_pool();
     snn_index *ix = new (std::nothrow) snn_index();
     if (!ix) {
@@ -499,6 +637,7 @@ static void install(snn_index *ix, PosArrays &a, int64_t n, cudaStream_t s) {
 // New points take ids n, n+1, ...: scored with the index's centre and
 // direction, sorted, and merged into the sorted order.
 static snn_status index_insert(snn_index *ix, const float *X, int64_t k, int64_t ld, cudaStream_t s) {
+    NvtxPhase nvtx_("snn index insert");
     ensure_pool();
     const int d = ix->d, dp = ix->dp;
     const int64_t n = ix->n;
@@ -576,6 +715,7 @@ static snn_status index_insert(snn_index *ix, const float *X, int64_t k, int64_t
 // Removes the listed ids; the kept points are renumbered 0, 1, ... in their
 // previous id order (as if their rows were erased from X).
 static snn_status index_delete(snn_index *ix, const int32_t *ids, int64_t cnt, cudaStream_t s) {
+    NvtxPhase nvtx_("snn index delete");
     ensure_pool();
     const int dp = ix->dp;
     const int64_t n = ix->n;
@@ -676,6 +816,7 @@ struct QueryScratch {
 static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int64_t ldq,
                              double R, snn_precision prec, cudaStream_t s, snn_csr *out,
                              snn_query_stats *stats, const double *Rdev = nullptr, double Rmax = 0.0) {
+    NvtxPhase nvtx_("snn query: prepare");
     const bool self = (Q == nullptr);
     if (self) m = ix->n;
     const int d = ix->d, dp = ix->dp;
@@ -893,6 +1034,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     // FP8 where its shape and ranges allow it, BF16 otherwise
     const snn_precision used =
         prec == SNN_PREC_FP8E4M3 && !f8_eligible(ix, Rdev ? radius_slack(Rmax, d) : Rx) ? SNN_PREC_BF16 : prec;
+    nvtx_.next("snn query: score and decide");
     for (int attempt = 0; attempt < 2; ++attempt) {
         CUDA_Q(cudaMallocAsync(&surv, size_t(cap) * sizeof(uint2), s));
         CUDA_Q(cudaMallocAsync(&rec_d2, size_t(cap) * sizeof(float), s));
@@ -990,6 +1132,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         return fail(SNN_ENOTSUP);
     }
     out->nnz = nnz;
+    nvtx_.next("snn query: CSR");
     if (nnz > 0) {
         TRY_Q(dev_alloc(&out->indices, nnz, s));
         TRY_Q(dev_alloc(&out->dist2, nnz, s));
@@ -1114,6 +1257,7 @@ static snn_status check_finite_r(double R, const char *what) {
 static snn_status ip_search(const float *P, int64_t n, int d, int64_t ldp, const float *Q, int64_t m,
                             int64_t ldq, double tau, snn_precision prec, cudaStream_t s, snn_csr *out,
                             snn_ip_stats *st) {
+    NvtxPhase nvtx_("snn inner-product search");
     ensure_pool();
     Scratch scr(s);
     double *sqP, *sqQ, *mx;
@@ -1364,6 +1508,7 @@ void snn_batch_plan_free(snn_batch_plan *plan, void *stream) {
 
 snn_status snn_dbscan(const float *X, int64_t n, int32_t d, int64_t ld, double eps, int32_t min_pts,
                       snn_precision prec, void *stream, int32_t *labels, uint8_t *is_core) {
+    NvtxPhase nvtx_("snn dbscan");
     clear_error();
     SNN_TRY(validate_points(X, n, d, ld));
     SNN_TRY(check_finite_r(eps, "eps"));
@@ -1428,6 +1573,27 @@ void snn_free(void *p) {
 }
 
 void snn_index_free(snn_index *idx) { index_release(idx); }
+
+snn_status snn_index_saved_size(const snn_index *idx, int64_t *bytes) {
+    clear_error();
+    if (!idx || !bytes) { set_error("index or bytes is NULL"); return SNN_EINVAL; }
+    SavedArray a[11];
+    *bytes = saved_layout(idx->n, idx->d, idx->dp, a);
+    return SNN_OK;
+}
+
+snn_status snn_index_save(const snn_index *idx, void *buf, int64_t bytes, void *stream) {
+    clear_error();
+    if (!idx || !buf) { set_error("index or buffer is NULL"); return SNN_EINVAL; }
+    return index_save(idx, buf, bytes, static_cast<cudaStream_t>(stream));
+}
+
+snn_status snn_index_load(const void *buf, int64_t bytes, void *stream, snn_index **out) {
+    clear_error();
+    if (!buf || !out) { set_error("buffer or out is NULL"); return SNN_EINVAL; }
+    *out = nullptr;
+    return index_load(buf, bytes, static_cast<cudaStream_t>(stream), out);
+}
 
 snn_status snn_index_insert(snn_index *idx, const float *X, int64_t k, int64_t ld, void *stream) {
     clear_error();

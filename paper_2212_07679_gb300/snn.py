@@ -104,6 +104,12 @@ def _load():
     lib.snn_test_inject.restype = ctypes.c_int
     lib.snn_launch_count.argtypes = []
     lib.snn_launch_count.restype = ctypes.c_uint64
+    lib.snn_index_saved_size.argtypes = [vp, ctypes.POINTER(i64)]
+    lib.snn_index_saved_size.restype = ctypes.c_int
+    lib.snn_index_save.argtypes = [vp, ctypes.c_char_p, i64, vp]
+    lib.snn_index_save.restype = ctypes.c_int
+    lib.snn_index_load.argtypes = [ctypes.c_char_p, i64, vp, ctypes.POINTER(vp)]
+    lib.snn_index_load.restype = ctypes.c_int
     lib.snn_measure_peak.argtypes = [i32, i64, vp, ctypes.POINTER(f64)]
     lib.snn_measure_peak.restype = ctypes.c_int
     lib.snn_index_build_batch.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(i64),
@@ -248,6 +254,33 @@ class Index:
     @property
     def handle(self):
         return self._h
+
+    def save(self, stream=None) -> bytes:
+        """The index record as a byte image (snn_index_save): store it with
+        open(path, "wb").write(...) and restore it with Index.load."""
+        if self._h is None:
+            raise ValueError("index is closed")
+        nb = ctypes.c_int64()
+        _check(lib.snn_index_saved_size(self._h, ctypes.byref(nb)))
+        buf = ctypes.create_string_buffer(nb.value)
+        with torch.cuda.device(self.device):
+            _check(lib.snn_index_save(self._h, buf, nb.value, _stream_ptr(stream)))
+        return buf.raw
+
+    @classmethod
+    def load(cls, image: bytes, device=None, stream=None) -> "Index":
+        """An index from a byte image of Index.save (snn_index_load), on
+        `device` (default: the current CUDA device)."""
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(dev):
+            _check(lib.snn_index_load(image, len(image), _stream_ptr(stream), ctypes.byref(h)))
+        ix = cls.__new__(cls)
+        ix.device = dev
+        ix._h = h
+        ix.n = int(lib.snn_index_size(h))
+        ix.d = int.from_bytes(image[12:16], "little", signed=True)
+        return ix
 
     def insert(self, X: torch.Tensor, stream=None) -> None:
         """Adds the rows of X as points n, n+1, ... (snn_index_insert)."""

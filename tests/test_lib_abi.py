@@ -124,3 +124,29 @@ def test_peak_probe_validation_needs_no_gpu(libpath):
     assert lib.snn_measure_peak(-1, 1024, None, ctypes.byref(out)) == 1
     assert lib.snn_measure_peak(0, 63, None, ctypes.byref(out)) == 1         # iters < 64
     assert lib.snn_measure_peak(0, 1024, None, None) == 1                    # NULL output
+
+
+def test_index_image_validation_needs_no_gpu(libpath):
+    # a saved-index image is checked on the host before any device work
+    import struct
+    lib = ctypes.CDLL(libpath)
+    lib.snn_index_load.argtypes = [ctypes.c_char_p, ctypes.c_int64, ctypes.c_void_p,
+                                   ctypes.POINTER(ctypes.c_void_p)]
+    lib.snn_index_saved_size.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]
+    out = ctypes.c_void_p()
+    nb = ctypes.c_int64()
+    assert lib.snn_index_saved_size(None, ctypes.byref(nb)) == 1
+
+    def header(magic=b"SNNIDX\x00\x01", version=1, d=8, n=100, dp=8):
+        return magic + struct.pack("<iiqiiff", version, d, n, dp, 0, 0.0, 1.0)
+
+    good = header()
+    assert lib.snn_index_load(good[:20], 20, None, ctypes.byref(out)) == 1          # short header
+    assert lib.snn_index_load(header(magic=b"NOTANIDX"), 40, None, ctypes.byref(out)) == 1
+    assert lib.snn_index_load(header(version=2), 40, None, ctypes.byref(out)) == 1
+    assert lib.snn_index_load(header(d=0, dp=0), 40, None, ctypes.byref(out)) == 1
+    assert lib.snn_index_load(header(dp=12), 40, None, ctypes.byref(out)) == 1    # dp != roundup(d, 4)
+    assert lib.snn_index_load(header(n=0), 40, None, ctypes.byref(out)) == 1
+    assert lib.snn_index_load(good, len(good), None, ctypes.byref(out)) == 1      # arrays missing
+    assert lib.snn_index_load(None, 0, None, ctypes.byref(out)) == 1
+    assert out.value is None
