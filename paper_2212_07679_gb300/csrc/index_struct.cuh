@@ -31,13 +31,15 @@ struct snn_index {
     float *hx = nullptr;
     float *nrm = nullptr;
     float *dconst = nullptr;      // device: [0] alpha error bound, [1] max norm
-    // BF16 split operands of the tensor-core path (built on first use):
-    // tc_part[p] is n x tc_k2 bf16, part p of the split of each centred row
-    // plus the folded threshold columns.
+    // 16-bit split operands of the tensor-core path (built on first use):
+    // tc_part[p] is n x tc_k2 16-bit values, part p of the split of each
+    // centred row (FP16 or BF16) plus the folded threshold columns (BF16).
     uint16_t *tc_part[3] = {nullptr, nullptr, nullptr};
     int tc_nsplit = 0;
     int tc_k2 = 0;                // row width of part 1 (columns)
     int tc_k2n = 0;               // row width of parts 2 and 3
+    int tc_f16 = 0;               // the parts are FP16 (of x 2^tc_sigma), else BF16
+    int tc_sigma = 0;
     // FP8 e4m3 operands (built on first use): f8_part[p] is n x f8_k8 bytes,
     // part p of each row scaled by its power of two; f8_fold is n x 16 bf16,
     // the folded threshold and error-bound columns.  Keyed by the split, the

@@ -49,6 +49,7 @@ struct ScoreArgs {
     unsigned long long *work;   // work-item counter
     int *err;                   // device error flag (bounded waits that gave up)
     const double *Rq = nullptr; // per-query radii (sorted query order), or null
+    double q_nrm_max = 0.0;     // largest centred query norm bound (tensor-core scaling)
 };
 
 // One work item of the FP32 scorer: a 128-query tile against band chunks

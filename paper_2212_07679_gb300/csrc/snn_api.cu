@@ -818,6 +818,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
                              snn_query_stats *stats, const double *Rdev = nullptr, double Rmax = 0.0) {
     NvtxPhase nvtx_("snn query: prepare");
     const bool self = (Q == nullptr);
+    double q_nrm_max = self ? (double)ix->nrm_max : 0.0;   // largest centred query norm bound
     if (self) m = ix->n;
     const int d = ix->d, dp = ix->dp;
     out->m = m;
@@ -917,6 +918,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
                       "overflow", (double)hq, kMaxCentredNorm);
             return fail(SNN_ENOTSUP);
         }
+        q_nrm_max = (double)hq;
         qs.alpha = qa;
         qs.order = qorder;
         qs.raw = qraw;
@@ -1008,6 +1010,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     CUDA_Q(cudaMemsetAsync(dev_err, 0, sizeof(int), s));
     sa.err = dev_err;
     sa.Rq = Rs;
+    sa.q_nrm_max = q_nrm_max;
     int32_t *counts, *lists, *big_list;
     int64_t *counts64, *big_len, *toff;
     unsigned *cls;
@@ -1047,7 +1050,9 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         if (used == SNN_PREC_FP8E4M3) {
             st = f8_score_launch(ix, sa, s, Rx, e_data, scr, &mma_fpp);
         } else if (used == SNN_PREC_BF16) {
-            st = tc_score_launch(ix, sa, s, Rx, e_data, scr, &mma_fpp);
+            // with per-query radii the constants come from Rq; the largest
+            // radius sets the operand scaling
+            st = tc_score_launch(ix, sa, s, Rdev ? radius_slack(Rmax, d) : Rx, e_data, scr, &mma_fpp);
         } else {
             const int grid = device_sm_count() * 2;
             if (dp <= 16)

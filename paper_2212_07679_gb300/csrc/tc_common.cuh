@@ -95,6 +95,12 @@ __host__ __device__ constexpr uint32_t idesc_bf16() {
            (uint32_t(M >> 4) << 24);
 }
 
+// The same with FP16 A and B (format code 0 for both).
+template <int M, int N>
+__host__ __device__ constexpr uint32_t idesc_f16() {
+    return (1u << 4) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
 __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
                                          uint32_t idesc, uint32_t accumulate) {
     asm volatile(

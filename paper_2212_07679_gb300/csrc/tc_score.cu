@@ -172,6 +172,7 @@ struct TcArgs {
     unsigned long long *count;
     int *err;
     int stall;                  // test fault: the producer issues no loads
+    int f16;                    // data k steps hold FP16 parts (folded ones BF16)
 };
 
 struct ItemInfo {
@@ -203,6 +204,9 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
     constexpr int NP = Sh::kNP;
     constexpr int NB = Sh::kNBuf;                // accumulator buffers
     constexpr uint32_t kIdesc = idesc_bf16<kTM, BN>();
+    // FP16 data parts: both operands of a data k step are FP16 and both of a
+    // folded k step BF16 (the folded columns start on a k step boundary)
+    constexpr uint32_t kIdescF16 = idesc_f16<kTM, BN>();
     // (A part, B part) products kept by the split: all with pa + pb <= NSPLIT-1
     constexpr int kPa[6] = {0, 0, 1, 0, 1, 2};
     constexpr int kPb[6] = {0, 1, 0, 2, 1, 0};
@@ -377,6 +381,7 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                                 // the folded columns live in part 0 only: a k step
                                 // without data columns needs the (0,0) product alone
                                 const int np = kg < a.ksteps_data ? NP : 1;
+                                const uint32_t idk = (a.f16 && kg < a.ksteps_data) ? kIdescF16 : kIdesc;
 #pragma unroll
                                 for (int pr = 0; pr < NP; ++pr) {
                                     if (pr >= np) break;
@@ -391,7 +396,7 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                                                             uint32_t(h * kTM) * arow + 32u * ks;
                                         const uint64_t ad = kPa[pr] == 0 ? smem_desc<Sh::kRowBytes>(aa)
                                                                          : smem_desc<Sh::kRowBytesN>(aa);
-                                        mma_bf16(dt0 + uint32_t(h * BN), ad, bd, kIdesc,
+                                        mma_bf16(dt0 + uint32_t(h * BN), ad, bd, idk,
                                                  (kb | ks | pr) != 0 ? 1u : 0u);
                                     }
                                 }
@@ -599,6 +604,21 @@ __device__ __forceinline__ void split3(double w, uint16_t (&o)[3]) {
     }
 }
 
+// How k_tc_pack writes a row: FP16 parts of x 2^sigma (f16 = 1, two parts)
+// or BF16 parts of x; the folded columns from fold_col, scaled by fs1 =
+// 2^sigma (norms) and fs2 = 2^(2 sigma) (squares).
+struct TcPackMode {
+    int f16;
+    int fold_col;
+    float xscale;
+    double fs1, fs2;
+};
+
+__device__ __forceinline__ uint16_t half_bits(float v) {
+    const __half h = __float2half_rn(v);   // v is already an FP16 value
+    return *reinterpret_cast<const uint16_t *>(&h);
+}
+
 // Rows of an operand: split parts of the centred row, then the folded
 // columns (data side: -(1-c) xbar_j split, ||x_j|| rounded up three times,
 // ones; query side: ones, c ||y_i|| split, A'_i split).  One warp per 32
@@ -611,7 +631,7 @@ __global__ void k_tc_pack(const float *__restrict__ xc, int dp, const float *__r
                           const float *__restrict__ nrm, const double *__restrict__ Aq,
                           int64_t rows, int d, int K2, int K2n, double c, int query_side,
                           uint16_t *__restrict__ p0, uint16_t *__restrict__ p1,
-                          uint16_t *__restrict__ p2) {
+                          uint16_t *__restrict__ p2, TcPackMode pm) {
     const int64_t r0 = ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * 32;
     const int lane = threadIdx.x & 31;
     if (r0 >= rows) return;   // whole warps leave together
@@ -643,13 +663,27 @@ __global__ void k_tc_pack(const float *__restrict__ xc, int dp, const float *__r
             for (int e = 0; e < 4; ++e) {
                 v0[e] = v1[e] = v2[e] = 0;
                 if (k0 + e < d) {
-                    const float x = xs[e];
-                    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-                    const float xr1 = x - __bfloat162float(h);               // exact
-                    const __nv_bfloat16 l = __float2bfloat16_rn(xr1);
-                    v0[e] = bf16_bits(h);
-                    v1[e] = bf16_bits(l);
-                    if (NSPLIT == 3) v2[e] = bf16_bits(__float2bfloat16_rn(xr1 - __bfloat162float(l)));
+                    if (NSPLIT == 2 && pm.f16) {
+                        // FP16 parts of x 2^sigma (exact scaling, |x 2^sigma| < 2^14);
+                        // parts below the FP16 normal range are set to zero, so no
+                        // subnormal ever reaches the tensor core
+                        const float x = xs[e] * pm.xscale;
+                        float hf = __half2float(__float2half_rn(x));
+                        if (fabsf(hf) < 0x1p-14f) hf = 0.f;
+                        const float xr1 = x - hf;                             // exact
+                        float lf = __half2float(__float2half_rn(xr1));
+                        if (fabsf(lf) < 0x1p-14f) lf = 0.f;
+                        v0[e] = half_bits(hf);
+                        v1[e] = half_bits(lf);
+                    } else {
+                        const float x = xs[e];
+                        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+                        const float xr1 = x - __bfloat162float(h);               // exact
+                        const __nv_bfloat16 l = __float2bfloat16_rn(xr1);
+                        v0[e] = bf16_bits(h);
+                        v1[e] = bf16_bits(l);
+                        if (NSPLIT == 3) v2[e] = bf16_bits(__float2bfloat16_rn(xr1 - __bfloat162float(l)));
+                    }
                 }
             }
             auto pack4 = [](const uint16_t *v) {
@@ -667,13 +701,15 @@ __global__ void k_tc_pack(const float *__restrict__ xc, int dp, const float *__r
     }
     __syncwarp();
     if (lane < nr) {
+        // folded columns (BF16) from column fold_col, in the scaled units
+        // (x 2^sigma, squares x 2^(2 sigma); both 1 without FP16 parts)
         const int64_t r = r0 + lane;
-        uint16_t *f = p0 + r * K2 + d;
+        uint16_t *f = p0 + r * K2 + pm.fold_col;
         uint16_t sp[3];
         const uint16_t one = bf16_bits(__float2bfloat16_rn(1.0f));
         if (!query_side) {
-            split3(-(1.0 - c) * (double)hx[r], sp);
-            const uint16_t nb = bf16_bits(__float2bfloat16_ru(nrm[r]));
+            split3(-(1.0 - c) * (double)hx[r] * pm.fs2, sp);
+            const uint16_t nb = bf16_bits(__float2bfloat16_ru(float((double)nrm[r] * pm.fs1)));
             for (int t = 0; t < 3; ++t) {
                 f[t] = sp[t];
                 f[3 + t] = nb;
@@ -681,8 +717,8 @@ __global__ void k_tc_pack(const float *__restrict__ xc, int dp, const float *__r
             }
         } else {
             uint16_t sa[3];
-            split3(c * (double)nrm[r], sp);
-            split3(Aq[r], sa);
+            split3(c * (double)nrm[r] * pm.fs1, sp);
+            split3(Aq[r] * pm.fs2, sa);
             for (int t = 0; t < 3; ++t) {
                 f[t] = one;
                 f[3 + t] = sp[t];
@@ -871,13 +907,16 @@ __global__ void k_f8_pack(const float *__restrict__ xc, int dp, const float *__r
 // conservative, plus a margin that makes an acceptable pair's acc positive.
 __global__ void k_tc_query_consts(const float *__restrict__ hy, const float *__restrict__ qn,
                                   int64_t m, int d, double Rx, double e_data, double delta,
-                                  double margin, double *__restrict__ Aq, const double *__restrict__ Rq) {
+                                  double margin, double *__restrict__ Aq, const double *__restrict__ Rq,
+                                  double abs_n, double abs_q) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= m) return;
     const double ei = 1.0001 * (double)kU32 * (double)qn[i];
     const double r = (Rq ? radius_slack(Rq[i], d) : Rx) + e_data + ei;
     const double hy_low = (double)hy[i] * (1.0 - 1.05 * (d + 2) * (double)kU32);
-    double A = 0.5 * r * r - hy_low;
+    // abs_n + abs_q ||y||: the absolute part of the FP16 split bound (0 for
+    // BF16 parts)
+    double A = 0.5 * r * r - hy_low + (abs_n + abs_q * (double)qn[i]);
     A += 4.0 * kU64 * (fabs(A) + 0.5 * r * r + (double)hy[i]);
     A = A >= 0.0 ? A / (1.0 - delta) : A / (1.0 + delta);
     A += 0x1p-22 * fabs(A) + margin;
@@ -885,14 +924,19 @@ __global__ void k_tc_query_consts(const float *__restrict__ hy, const float *__r
 }
 
 // Rounding constant c of the folded test for a split and a dimension.
-double tc_constant(int nsplit, int d, double *u_k_out) {
-    const int ksteps = int(cdiv(d + kExtra, 16));
+double tc_constant(int nsplit, int d, double *u_k_out, bool f16) {
     const int ksteps_data = int(cdiv(d, 16));
+    // FP16 parts: the folded columns take a k step of their own
+    const int ksteps = f16 ? ksteps_data + 1 : int(cdiv(d + kExtra, 16));
     const int ninstr = tc_npairs(nsplit) * ksteps_data + (ksteps - ksteps_data);
     // FP32 accumulation: each MMA instruction is charged 2^-22 of (|C_in| +
     // sum of its |products|), i.e. (ninstr + 1) 2^-22 of all |products|
     const double u_k = 0x1p-22 * (ninstr + 1);
-    const double quant = nsplit == 2 ? 3.1 * 0x1p-16 : 4.2 * 0x1p-24;
+    // dropped split terms, relative to sum |x_k y_k|: BF16 parts 3.1 2^-16
+    // (two) or 4.2 2^-24 (three); two FP16 parts 3.01 2^-22 (x2.y2 + a.e_y +
+    // e_x.y', each part within half an FP16 ulp), plus an absolute part for
+    // the parts set to zero below the FP16 normal range (in the constants A)
+    const double quant = f16 ? 3.01 * 0x1p-22 : (nsplit == 2 ? 3.1 * 0x1p-16 : 4.2 * 0x1p-24);
     const double c_mn = (quant + 1.01 * u_k) / (1.0 - 0x1p-23 - u_k);
     const double c_hx = 0x1p-23 + 1.05 * (d + 2) * 0x1p-24 + u_k;
     if (u_k_out) *u_k_out = u_k;
@@ -918,6 +962,7 @@ TcArgs tc_args(const snn_index *ix, const ScoreArgs &sa, const TileSet &ts) {
     a.count = sa.count;
     a.err = sa.err;
     a.stall = take_fault(SNN_FAULT_STALL_TC_PRODUCER) ? 1 : 0;
+    a.f16 = 0;
     return a;
 }
 
@@ -935,7 +980,7 @@ snn_status run_tc(const CUtensorMap (&maps)[8], const TcArgs &a, cudaStream_t s)
 
 template <int NSPLIT, int BK, int BN, bool ARES, int CPS, int NW, int MT>
 snn_status launch_tc(const snn_index *ix, const ScoreArgs &sa, const uint16_t *const *qp,
-                     int K2, int K2n, const TileSet &ts, cudaStream_t s) {
+                     int K2, int K2n, const TileSet &ts, cudaStream_t s, int f16) {
     CUtensorMap maps[8];
     for (int p = 0; p < 3; ++p) {
         const int pp = p < NSPLIT ? p : 0;
@@ -946,9 +991,10 @@ snn_status launch_tc(const snn_index *ix, const ScoreArgs &sa, const uint16_t *c
     maps[6] = maps[0];   // no folded block of its own
     maps[7] = maps[3];
     TcArgs a = tc_args(ix, sa, ts);
-    a.ksteps = int(cdiv(ix->d + kExtra, 16));
     a.ksteps_data = int(cdiv(ix->d, 16));
+    a.ksteps = f16 ? a.ksteps_data + 1 : int(cdiv(ix->d + kExtra, 16));
     a.nkb = K2 / BK;
+    a.f16 = f16;
     return run_tc<NSPLIT, BK, BN, ARES, CPS, NW, MT, 0>(maps, a, s);
 }
 
@@ -1052,7 +1098,7 @@ snn_status f8_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
     SNN_TRY(scr.alloc(&qfold, size_t(m) * 16));
     // a margin of 2^-60 keeps A'_i 2^(s_x + s_y) a normal FP32 number
     SNN_LAUNCH(k_tc_query_consts, unsigned(cdiv(m, 256)), 256, 0, s)(
-        sa.q.hx, sa.q.nrm, m, d, Rx, e_data, 0x1p-23 + kacc, 0x1p-60, Aq, sa.Rq);
+        sa.q.hx, sa.q.nrm, m, d, Rx, e_data, 0x1p-23 + kacc, 0x1p-60, Aq, sa.Rq, 0.0, 0.0);
     SNN_LAUNCH_CHECK();
     SNN_LAUNCH(packer, pack_grid(m), pack_threads, 0, s)(sa.q.xc, ix->dp, nullptr, Aq, m, d, K8, ch,
                                                         kacc, 1, qp[0], qp[1], qp[2], qfold);
@@ -1068,29 +1114,48 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
                            double Rx, double e_data, Scratch &scr, int64_t *mma_flops_per_pair) {
     snn_index *ix = const_cast<snn_index *>(ixc);
     const int d = ix->d;
-    const double R2h = 0.5 * Rx * Rx;
-    // the two-part split suffices when its slack stays a small fraction of
-    // R^2/2 for the largest norms; otherwise use three parts
-    const double N = (double)ix->nrm_max;
-    const double c2 = tc_constant(2, d, nullptr);
-    int nsplit = (c2 * 1.5 * N * N <= 0.02 * R2h) ? 2 : 3;
+    // operands: two FP16 parts of the rows scaled by 2^sigma (the default),
+    // or two or three BF16 parts (SNN_BF16_PARTS = 2 or 3).  Two FP16 parts
+    // need the MMAs of two BF16 parts and bound the dropped terms as tightly
+    // as three BF16 parts do.
+    bool f16 = true;
+    int nsplit = 2;
     if (const char *e = getenv("SNN_BF16_PARTS")) {
         const int v = atoi(e);
-        if (v == 2 || v == 3) nsplit = v;
+        if (v == 2 || v == 3) {
+            f16 = false;
+            nsplit = v;
+        }
     }
+    // sigma: the largest of the centred norms of the data and the queries
+    // and the radius, scaled, lies in [2^13, 2^14), so every scaled
+    // coordinate is an FP16 number and every scaled folded value (squares of
+    // these, halved) stays below 2^28
+    const double N = std::max(std::max<double>((double)ix->nrm_max, sa.q_nrm_max), Rx);
+    int sigma = 0;
+    if (f16 && N > 0.0) sigma = std::min(120, std::max(-120, 13 - std::ilogb(N)));
+    const double fs1 = std::ldexp(1.0, sigma), fs2 = std::ldexp(1.0, 2 * sigma);
     double u_k = 0.0;
-    const double c = tc_constant(nsplit, d, &u_k);
+    const double c = tc_constant(nsplit, d, &u_k, f16);
+    // absolute part of the FP16 bound, in unscaled units: 1.001 2^-14 sqrt(d)
+    // (||x'|| + ||y'||) + 2 d 2^-28 in scaled units (parts below 2^-14 are zero)
+    const double abs_q = f16 ? 1.001 * std::sqrt(double(d)) * std::ldexp(1.0, -14 - sigma) : 0.0;
+    const double abs_n = f16 ? abs_q * (double)ix->nrm_max + 2.0 * d * std::ldexp(1.0, -28 - 2 * sigma) : 0.0;
     // shape: one 32- or 64-column k-block holds everything for low d (query
-    // tile resident for a whole item); 64-column k-blocks streamed otherwise
-    const int kp = d + kExtra;
+    // tile resident for a whole item); 64-column k-blocks streamed otherwise.
+    // With FP16 parts the folded columns start on a k step boundary.
+    const int fold_col = f16 ? int(cdiv(d, 16) * 16) : d;
+    const int kp = fold_col + kExtra;
     const int bk = kp <= 32 ? 32 : 64;
     const int K2 = int(cdiv(kp, bk) * bk);
     // parts 2 and 3 carry no folded columns: with every data column inside
     // the first 16, their rows are 16 columns wide (low-d shape only)
     const int K2n = (kp <= 32 && d <= 16) ? 16 : K2;
+    const TcPackMode pm{f16 ? 1 : 0, fold_col, float(fs1), fs1, fs2};
     {
         std::lock_guard<std::mutex> lk(ix->mu);
-        if (ix->tc_nsplit != nsplit || ix->tc_k2 != K2 || ix->tc_k2n != K2n) {
+        if (ix->tc_nsplit != nsplit || ix->tc_k2 != K2 || ix->tc_k2n != K2n || ix->tc_f16 != int(f16) ||
+            ix->tc_sigma != sigma) {
             for (int p = 0; p < 3; ++p) {
                 if (ix->tc_part[p]) cudaFreeAsync(ix->tc_part[p], s);
                 ix->tc_part[p] = nullptr;
@@ -1101,22 +1166,24 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
                 cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&ix->tc_part[p]),
                                                 size_t(ix->n) * w * sizeof(uint16_t), s);
                 if (e != cudaSuccess) {
-                    set_error("BF16 operand allocation failed: %s", cudaGetErrorString(e));
+                    set_error("tensor-core operand allocation failed: %s", cudaGetErrorString(e));
                     return SNN_ENOMEM;
                 }
             }
             auto packer = nsplit == 2 ? k_tc_pack<2> : k_tc_pack<3>;
             SNN_LAUNCH(packer, unsigned(cdiv(cdiv(ix->n, 32) * 32, 256)), 256, 0, s)(
                 ix->xc, ix->dp, ix->hx, ix->nrm, nullptr, ix->n, d, K2, K2n, c, 0, ix->tc_part[0],
-                ix->tc_part[1], ix->tc_part[2]);
+                ix->tc_part[1], ix->tc_part[2], pm);
             SNN_LAUNCH_CHECK();
             ix->tc_nsplit = nsplit;
             ix->tc_k2 = K2;
             ix->tc_k2n = K2n;
+            ix->tc_f16 = int(f16);
+            ix->tc_sigma = sigma;
         }
     }
     if (mma_flops_per_pair) {
-        const int64_t ks_all = cdiv(d + kExtra, 16), ks_data = cdiv(d, 16);
+        const int64_t ks_data = cdiv(d, 16), ks_all = f16 ? ks_data + 1 : cdiv(d + kExtra, 16);
         *mma_flops_per_pair = int64_t(2) * 16 * (ks_data * tc_npairs(nsplit) + (ks_all - ks_data));
     }
     // query operands (per call): same split, query-side folded columns
@@ -1126,13 +1193,14 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
     SNN_TRY(scr.alloc(&Aq, m));
     for (int p = 0; p < nsplit; ++p) SNN_TRY(scr.alloc(&qp[p], size_t(m) * (p == 0 ? K2 : K2n)));
     SNN_LAUNCH(k_tc_query_consts, unsigned(cdiv(m, 256)), 256, 0, s)(
-        sa.q.hx, sa.q.nrm, m, d, Rx, e_data, 0x1p-23 + u_k, 0x1p-100, Aq, sa.Rq);
+        sa.q.hx, sa.q.nrm, m, d, Rx, e_data, 0x1p-23 + u_k, 0x1p-100, Aq, sa.Rq, abs_n, abs_q);
     SNN_LAUNCH_CHECK();
     auto packer = nsplit == 2 ? k_tc_pack<2> : k_tc_pack<3>;
     SNN_LAUNCH(packer, unsigned(cdiv(cdiv(m, 32) * 32, 256)), 256, 0, s)(sa.q.xc, ix->dp, sa.q.hx,
                                                                        sa.q.nrm, Aq,
-                                                            m, d, K2, K2n, c, 1, qp[0], qp[1], qp[2]);
+                                                            m, d, K2, K2n, c, 1, qp[0], qp[1], qp[2], pm);
     SNN_LAUNCH_CHECK();
+    const int F = f16 ? 1 : 0;
     TileSet ts1{sa.tile_lo, sa.tile_hi, sa.item_off, sa.item_tile, sa.ntiles};
     if (kp <= 32 && K2n == 16) {
         // low d: the band traffic per pair dominates, so every band chunk is
@@ -1154,21 +1222,21 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
         SNN_LAUNCH(k_item_tiles, unsigned(cdiv(ng, 128)), 128, 0, s)(off2, ng, it2);
         SNN_LAUNCH_CHECK();
         TileSet ts2{lo2, hi2, off2, it2, ng};
-        return nsplit == 2 ? launch_tc<2, 32, 128, true, 1, 16, MT>(ix, sa, qp, K2, K2n, ts2, s)
-                           : launch_tc<3, 32, 128, true, 1, 16, MT>(ix, sa, qp, K2, K2n, ts2, s);
+        return nsplit == 2 ? launch_tc<2, 32, 128, true, 1, 16, MT>(ix, sa, qp, K2, K2n, ts2, s, F)
+                           : launch_tc<3, 32, 128, true, 1, 16, MT>(ix, sa, qp, K2, K2n, ts2, s, 0);
     }
     // other low-d shapes: two CTAs per SM with a resident query tile, so that
     // one CTA's pipeline bubbles overlap the other's MMAs
     if (kp <= 32)
-        return nsplit == 2 ? launch_tc<2, 32, 128, true, 2, 32, 1>(ix, sa, qp, K2, K2n, ts1, s)
-                           : launch_tc<3, 32, 128, true, 2, 32, 1>(ix, sa, qp, K2, K2n, ts1, s);
+        return nsplit == 2 ? launch_tc<2, 32, 128, true, 2, 32, 1>(ix, sa, qp, K2, K2n, ts1, s, F)
+                           : launch_tc<3, 32, 128, true, 2, 32, 1>(ix, sa, qp, K2, K2n, ts1, s, 0);
     if (kp <= 64)
-        return nsplit == 2 ? launch_tc<2, 64, 128, true, 1, 64, 1>(ix, sa, qp, K2, K2n, ts1, s)
-                           : launch_tc<3, 64, 128, true, 1, 64, 1>(ix, sa, qp, K2, K2n, ts1, s);
+        return nsplit == 2 ? launch_tc<2, 64, 128, true, 1, 64, 1>(ix, sa, qp, K2, K2n, ts1, s, F)
+                           : launch_tc<3, 64, 128, true, 1, 64, 1>(ix, sa, qp, K2, K2n, ts1, s, 0);
     // high d: 128 x 256 accumulators (each query k-block feeds two 128-row
     // halves of the band chunk), 32-column k-blocks, four stages
-    return nsplit == 2 ? launch_tc<2, 32, 256, false, 1, 32, 1>(ix, sa, qp, K2, K2n, ts1, s)
-                       : launch_tc<3, 32, 256, false, 1, 32, 1>(ix, sa, qp, K2, K2n, ts1, s);
+    return nsplit == 2 ? launch_tc<2, 32, 256, false, 1, 32, 1>(ix, sa, qp, K2, K2n, ts1, s, F)
+                       : launch_tc<3, 32, 256, false, 1, 32, 1>(ix, sa, qp, K2, K2n, ts1, s, 0);
 }
 
 }  // namespace snn

@@ -471,3 +471,45 @@ def test_row_sort_key_widths(snn, monkeypatch, keys64):
     lens = np.diff(ref.offsets)
     assert lens.max() > 4096 and ((lens > 512) & (lens <= 4096)).any() and (lens <= 32).any()
     assert_csr_equal(got, ref, f"keys64={keys64}")
+
+
+@pytest.mark.parametrize("parts", ["2", "3"])
+@pytest.mark.parametrize("d,spread", [(12, 40.0), (16, 3.0), (40, 10.0), (100, 2.0)])
+def test_tensor_core_shapes_bf16_parts(snn, monkeypatch, parts, d, spread):
+    """The BF16 operand splits (two or three parts, SNN_BF16_PARTS) on every
+    kernel shape; the default FP16 parts are covered above."""
+    monkeypatch.setenv("SNN_BF16_PARTS", parts)
+    rng = np.random.default_rng(200 + d)
+    centres = rng.uniform(-spread, spread, size=(6, d))
+    lab = rng.integers(0, 6, size=4000)
+    P = (centres[lab] + rng.standard_normal((4000, d))).astype(np.float32)
+    Q = (centres[rng.integers(0, 6, size=500)] + rng.standard_normal((500, d))).astype(np.float32)
+    R = float(np.sqrt(2.0 * d) * 0.8)
+    for q in (None, Q):
+        got = _run(snn, P, q, R, "bf16")
+        assert_csr_equal(got, oracle.brute_radius(P, q, R), f"parts={parts} d={d}")
+
+
+@pytest.mark.parametrize("d", [16, 40, 200])
+def test_fp16_parts_scaling_and_small_values(snn, d):
+    """FP16 parts of rows scaled by 2^sigma: data far above and far below
+    the FP16 range (sigma < 0 and sigma > 0), rows mixing magnitudes over
+    thirty binades (parts below the FP16 normal range set to zero), and a
+    radius far above the norms; every case equals the oracle bit for bit."""
+    rng = np.random.default_rng(300 + d)
+    base = rng.standard_normal((3000, d))
+    base[:, ::3] *= 2.0 ** -30                     # tiny columns next to unit ones
+    base[::7] *= 2.0 ** -12                        # whole rows 4096x smaller
+    for scale in (2.0 ** 40, 1.0, 2.0 ** -60):
+        P = (base * scale).astype(np.float32)
+        Q = (rng.standard_normal((400, d)) * scale).astype(np.float32)
+        R = float(np.quantile(np.linalg.norm(P[:300, None, :] - P[None, :300, :], axis=2), 0.02))
+        for q in (None, Q):
+            got = _run(snn, P, q, R, "bf16")
+            assert_csr_equal(got, oracle.brute_radius(P, q, R), f"d={d} scale={scale}")
+    P = base.astype(np.float32)
+    R = float(50.0 * np.sqrt(d))                    # every pair inside
+    got = _run(snn, P, None, R, "bf16")
+    ref = oracle.brute_radius(P, None, R)
+    assert ref.nnz == 3000 * 3000
+    assert_csr_equal(got, ref, f"d={d} large R")
