@@ -30,8 +30,8 @@
  *  - Limits: 1 <= d <= 4096, 1 <= n < 2^31, m < 2^31, total neighbour pairs
  *    of one call < 2^31 (SNN_ENOTSUP beyond that).
  *  - Environment variables (read at each call; none changes any result):
- *    SNN_BF16_PARTS = 2 or 3 and SNN_FP8_PRODUCTS = 3, 4 or 6 fix the
- *    tensor-core split (see snn_precision); SNN_SORT_KEYS64 = 1 makes the
+ *    SNN_TC_SPLIT = bf16x2, bf16x3 or fp16x2 and SNN_FP8_PRODUCTS = 3, 4 or 6
+ *    fix the tensor-core split (see snn_precision); SNN_SORT_KEYS64 = 1 makes the
  *    per-row sort of the CSR build use 64-bit keys even where 32-bit keys
  *    (id and position in the row) fit.
  */
@@ -59,11 +59,13 @@ typedef enum {
  * The output is identical for every precision; only the speed differs. */
 typedef enum {
     SNN_PREC_FP32 = 0,      /* FP32 CUDA-core dot products                  */
-    SNN_PREC_BF16 = 1,      /* BF16 tcgen05 tensor-core dot products, each
-                               value split into two or three BF16 parts
-                               (chosen from the largest norm and R; the
-                               environment variable SNN_BF16_PARTS = 2 or 3
-                               overrides)                                   */
+    SNN_PREC_BF16 = 1,      /* 16-bit tcgen05 tensor-core dot products: two
+                               BF16 parts of each value where that bound is
+                               tight enough for the norms and R, else two
+                               FP16 parts of the rows scaled by a power of
+                               two (folded threshold columns in BF16); the
+                               environment variable SNN_TC_SPLIT = bf16x2,
+                               bf16x3 or fp16x2 overrides                   */
     SNN_PREC_FP8E4M3 = 2    /* FP8 e4m3 tcgen05 dot products, each row
                                scaled by its own power of two; used for
                                d > 55 with norms and R below 2^20, BF16

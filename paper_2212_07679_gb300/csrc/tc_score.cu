@@ -31,6 +31,7 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <cstring>
 
 #include "index_struct.cuh"
 #include "tc_common.cuh"
@@ -1114,18 +1115,19 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
                            double Rx, double e_data, Scratch &scr, int64_t *mma_flops_per_pair) {
     snn_index *ix = const_cast<snn_index *>(ixc);
     const int d = ix->d;
-    // operands: two FP16 parts of the rows scaled by 2^sigma (the default),
-    // or two or three BF16 parts (SNN_BF16_PARTS = 2 or 3).  Two FP16 parts
-    // need the MMAs of two BF16 parts and bound the dropped terms as tightly
-    // as three BF16 parts do.
-    bool f16 = true;
+    // operands: two BF16 parts where their bound stays a small fraction of
+    // R^2/2 for the largest norms (high d, moderate norms), else two FP16
+    // parts of the rows scaled by 2^sigma, which need the MMAs of two BF16
+    // parts and bound the dropped terms as tightly as three BF16 parts do.
+    // SNN_TC_SPLIT = bf16x2, bf16x3 or fp16x2 overrides.
+    const double c2 = tc_constant(2, d, nullptr, false);
+    const double Nd = (double)ix->nrm_max;
+    bool f16 = !(c2 * 1.5 * Nd * Nd <= 0.02 * 0.5 * Rx * Rx);
     int nsplit = 2;
-    if (const char *e = getenv("SNN_BF16_PARTS")) {
-        const int v = atoi(e);
-        if (v == 2 || v == 3) {
-            f16 = false;
-            nsplit = v;
-        }
+    if (const char *e = getenv("SNN_TC_SPLIT")) {
+        if (!strcmp(e, "bf16x2")) f16 = false;
+        else if (!strcmp(e, "bf16x3")) f16 = false, nsplit = 3;
+        else if (!strcmp(e, "fp16x2")) f16 = true;
     }
     // sigma: the largest of the centred norms of the data and the queries
     // and the radius, scaled, lies in [2^13, 2^14), so every scaled

@@ -473,12 +473,12 @@ def test_row_sort_key_widths(snn, monkeypatch, keys64):
     assert_csr_equal(got, ref, f"keys64={keys64}")
 
 
-@pytest.mark.parametrize("parts", ["2", "3"])
+@pytest.mark.parametrize("split", ["bf16x2", "bf16x3", "fp16x2"])
 @pytest.mark.parametrize("d,spread", [(12, 40.0), (16, 3.0), (40, 10.0), (100, 2.0)])
-def test_tensor_core_shapes_bf16_parts(snn, monkeypatch, parts, d, spread):
-    """The BF16 operand splits (two or three parts, SNN_BF16_PARTS) on every
-    kernel shape; the default FP16 parts are covered above."""
-    monkeypatch.setenv("SNN_BF16_PARTS", parts)
+def test_tensor_core_shapes_forced_split(snn, monkeypatch, split, d, spread):
+    """Every 16-bit operand split (SNN_TC_SPLIT) on every kernel shape,
+    whatever the automatic choice would be."""
+    monkeypatch.setenv("SNN_TC_SPLIT", split)
     rng = np.random.default_rng(200 + d)
     centres = rng.uniform(-spread, spread, size=(6, d))
     lab = rng.integers(0, 6, size=4000)
@@ -487,15 +487,16 @@ def test_tensor_core_shapes_bf16_parts(snn, monkeypatch, parts, d, spread):
     R = float(np.sqrt(2.0 * d) * 0.8)
     for q in (None, Q):
         got = _run(snn, P, q, R, "bf16")
-        assert_csr_equal(got, oracle.brute_radius(P, q, R), f"parts={parts} d={d}")
+        assert_csr_equal(got, oracle.brute_radius(P, q, R), f"split={split} d={d}")
 
 
 @pytest.mark.parametrize("d", [16, 40, 200])
-def test_fp16_parts_scaling_and_small_values(snn, d):
+def test_fp16_parts_scaling_and_small_values(snn, monkeypatch, d):
     """FP16 parts of rows scaled by 2^sigma: data far above and far below
     the FP16 range (sigma < 0 and sigma > 0), rows mixing magnitudes over
     thirty binades (parts below the FP16 normal range set to zero), and a
     radius far above the norms; every case equals the oracle bit for bit."""
+    monkeypatch.setenv("SNN_TC_SPLIT", "fp16x2")
     rng = np.random.default_rng(300 + d)
     base = rng.standard_normal((3000, d))
     base[:, ::3] *= 2.0 ** -30                     # tiny columns next to unit ones
