@@ -550,7 +550,12 @@ __device__ __forceinline__ void decide_group_body(
             H = __fadd_rn(s1, t3);
             L = __fsub_rn(t3, __fsub_rn(H, s1));
         }
-        if (G > 1) nz = __any_sync(0xffffffffu, nz);   // (any lane of the warp: conservative)
+        if (G > 1) {
+            // any nonzero difference in this survivor's group of G lanes
+            const unsigned b = __ballot_sync(0xffffffffu, nz);
+            const unsigned gm = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1));
+            nz = (b & gm) != 0u;
+        }
         if (lane != 0 || !valid) continue;
         const DecideConsts dc = dcq ? dcq[e.x] : dc0;
         const double R2e = R2q ? R2q[e.x] : R2;

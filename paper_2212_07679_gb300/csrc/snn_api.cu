@@ -1023,7 +1023,8 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     TRY_Q(scr.alloc(&cls, 8));
     const double R2 = R * R;
     // lanes per survivor in the decision: 1 for short rows, 8 up to 128
-    // dimensions, 32 beyond
+    // dimensions, 32 beyond (four lanes at d = 16 measured slower: 1.16
+    // against 0.85 ms on the 10^6-point self-join)
     const int G = d <= 32 ? 1 : (d <= 128 ? 8 : 32);
     auto dk = G == 1 ? (sym ? k_decide_sym : k_decide_one)
                      : (G == 8 ? (sym ? k_decide_sym_g8 : k_decide_one_g8)
