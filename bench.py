@@ -953,8 +953,8 @@ def run_peaks(args):
     and e4m3 MMAs, FP32 and FP64 FMAs), each timed with CUDA events over
     `steps` launches after `warmup` launches, with clocks sampled meanwhile.
     These check the ratios the rooflines rely on (e4m3 = 2 x BF16, the FP32
-    lane count x clock); the rooflines themselves keep the driver-measured
-    denominators."""
+    lane count x clock); the rooflines themselves keep the denominators of
+    MEASURED_PEAKS.json."""
     import torch
     from paper_2212_07679_gb300 import snn
     torch.cuda.set_device(0)

@@ -56,3 +56,35 @@ def test_single_rank_and_rate():
     assert bench.job_max_ms(7.0, 1) == 7.0
     # two replicas of 1,000 queries in 10 ms: 200,000 queries/s for the job
     assert bench.whole_job_rate(1000, 2, 10.0) == pytest.approx(2.0e5)
+
+
+def test_scorer_traffic_is_tied_to_the_scorer_sources(tmp_path, monkeypatch):
+    """roofline.traffic comes from a capture of one scorer build: it is
+    reported for the captured workloads while the scorer sources hash to the
+    recorded value, and null for any other workload or source."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    import hashlib
+    h = hashlib.sha256()
+    for f in bench.SCORER_SOURCES:
+        with open(os.path.join(ROOT, "paper_2212_07679_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    expect = (bench.SCORER_TRAFFIC[("gmm_aniso", 1000000, "bf16")]
+              if h.hexdigest()[:16] == bench.SCORER_TRAFFIC["sha"] else None)
+    assert bench.scorer_traffic("gmm_aniso", 1000000, "bf16") == expect
+    assert bench.scorer_traffic("gmm_aniso", 12345, "bf16") is None
+    assert bench.scorer_traffic("glove_like", 200000, "bf16") is None
+    monkeypatch.setitem(bench.SCORER_TRAFFIC, "sha", "0000000000000000")
+    assert bench.scorer_traffic("gmm_aniso", 1000000, "bf16") is None
+
+
+def test_timed_regions_run_without_the_cyclic_collector():
+    import gc
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    assert gc.isenabled()
+    with bench.no_gc():
+        assert not gc.isenabled()
+    assert gc.isenabled()
