@@ -69,6 +69,27 @@ def no_gc():
         gc.enable()
 
 
+SPLIT_NAMES = {0: "none", 1: "bf16x2", 2: "bf16x3", 3: "fp16x2", 13: "e4m3x2 (3 products)",
+               14: "e4m3x2 (4 products)", 16: "e4m3x3 (6 products)"}
+
+
+def split_name(code: int) -> str:
+    return SPLIT_NAMES.get(int(code), str(code))
+
+
+def split_dtype(code: int) -> str:
+    """Arithmetic the step computes in: the scorer's operand type (with its
+    BF16 folded columns), FP32 accumulation and decisions, FP64 fallback."""
+    code = int(code)
+    if code == 3:
+        return "f16+bf16+f32+f64"
+    if code in (1, 2):
+        return "bf16+f32+f64"
+    if code >= 10:
+        return "e4m3+bf16+f32+f64"
+    return "f32+f64"
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -498,7 +519,8 @@ def run_ours(args):
         "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"bf16": "bf16+f32+f64", "fp8": "e4m3+bf16+f32+f64"}.get(args.precision, "f32+f64"),
+        "dtype": split_dtype(st.get("split_used", 0)),
+        "tc_split": split_name(st.get("split_used", 0)),
         "data": "synthetic",
         "config": workload_config(args, w),
         "pairs_scored_per_s": st["band_pairs"] / (ms_step / 1e3),

@@ -113,6 +113,9 @@ typedef struct {
  *              FP32);
  *  precision_used  the rejection arithmetic that ran (an FP8 request runs
  *              BF16 where FP8 is not available);
+ *  split_used  operand split of the tensor-core scorer: SNN_SPLIT_NONE (FP32
+ *              scoring), SNN_SPLIT_BF16X2, SNN_SPLIT_BF16X3, SNN_SPLIT_FP16X2,
+ *              or for e4m3 SNN_SPLIT_E4M3 + products per k-step (3, 4, 6);
  *  ms_*        device time of the phases (CUDA events on `stream`). */
 typedef struct {
     int64_t candidates;
@@ -126,7 +129,14 @@ typedef struct {
     float ms_recheck;
     float ms_csr;
     int32_t precision_used;
+    int32_t split_used;
 } snn_query_stats;
+
+#define SNN_SPLIT_NONE 0
+#define SNN_SPLIT_BF16X2 1
+#define SNN_SPLIT_BF16X3 2
+#define SNN_SPLIT_FP16X2 3
+#define SNN_SPLIT_E4M3 10
 
 /* Algorithm 1 (Section 3.1): centre, first principal direction, scores,
  * sort, halved norms.

@@ -1035,6 +1035,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     Readback hb_store{};
     Readback *hb = &hb_store;
     int64_t mma_fpp = 0;
+    int split_used = SNN_SPLIT_NONE;
     // FP8 where its shape and ranges allow it, BF16 otherwise
     const snn_precision used =
         prec == SNN_PREC_FP8E4M3 && !f8_eligible(ix, Rdev ? radius_slack(Rmax, d) : Rx) ? SNN_PREC_BF16 : prec;
@@ -1049,11 +1050,12 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         if (stats) cudaEventRecord(ev[1], s);
         snn_status st = SNN_OK;
         if (used == SNN_PREC_FP8E4M3) {
-            st = f8_score_launch(ix, sa, s, Rx, e_data, scr, &mma_fpp);
+            st = f8_score_launch(ix, sa, s, Rx, e_data, scr, &mma_fpp, &split_used);
         } else if (used == SNN_PREC_BF16) {
             // with per-query radii the constants come from Rq; the largest
             // radius sets the operand scaling
-            st = tc_score_launch(ix, sa, s, Rdev ? radius_slack(Rmax, d) : Rx, e_data, scr, &mma_fpp);
+            st = tc_score_launch(ix, sa, s, Rdev ? radius_slack(Rmax, d) : Rx, e_data, scr, &mma_fpp,
+                                 &split_used);
         } else {
             const int grid = device_sm_count() * 2;
             if (dp <= 16)
@@ -1212,6 +1214,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         stats->exact_fp64 = (int64_t)nf;
         stats->mma_flops_per_pair = mma_fpp;
         stats->precision_used = (int32_t)used;
+        stats->split_used = (int32_t)split_used;
         stats->candidates = (int64_t)hb->ctr[3];
         stats->band_pairs = (int64_t)hb->ctr[2];
         stats->survivors = nsurv;

@@ -1030,7 +1030,7 @@ bool f8_eligible(const snn_index *ix, double Rx) {
 }
 
 snn_status f8_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream_t s, double Rx,
-                           double e_data, Scratch &scr, int64_t *mma_flops_per_pair) {
+                           double e_data, Scratch &scr, int64_t *mma_flops_per_pair, int *split_used) {
     snn_index *ix = const_cast<snn_index *>(ixc);
     const int d = ix->d;
     // products per k-step: the cheapest split whose bound stays a small
@@ -1047,6 +1047,7 @@ snn_status f8_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
         if (v == 3 || v == 4 || v == 6) np = v;
     }
     const int nsplit = np == 6 ? 3 : 2;
+    if (split_used) *split_used = SNN_SPLIT_E4M3 + np;
     const int K8 = int(cdiv(d, 32) * 32);
     const int ksteps = K8 / 32;
     // accumulation: every instruction (e4m3 or the folded BF16 step) is
@@ -1112,7 +1113,8 @@ snn_status f8_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
 }
 
 snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream_t s,
-                           double Rx, double e_data, Scratch &scr, int64_t *mma_flops_per_pair) {
+                           double Rx, double e_data, Scratch &scr, int64_t *mma_flops_per_pair,
+                           int *split_used) {
     snn_index *ix = const_cast<snn_index *>(ixc);
     const int d = ix->d;
     // operands: two BF16 parts where their bound stays a small fraction of
@@ -1146,6 +1148,7 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
     // shape: one 32- or 64-column k-block holds everything for low d (query
     // tile resident for a whole item); 64-column k-blocks streamed otherwise.
     // With FP16 parts the folded columns start on a k step boundary.
+    if (split_used) *split_used = f16 ? SNN_SPLIT_FP16X2 : (nsplit == 3 ? SNN_SPLIT_BF16X3 : SNN_SPLIT_BF16X2);
     const int fold_col = f16 ? int(cdiv(d, 16) * 16) : d;
     const int kp = fold_col + kExtra;
     const int bk = kp <= 32 ? 32 : 64;

@@ -485,8 +485,10 @@ def test_tensor_core_shapes_forced_split(snn, monkeypatch, split, d, spread):
     P = (centres[lab] + rng.standard_normal((4000, d))).astype(np.float32)
     Q = (centres[rng.integers(0, 6, size=500)] + rng.standard_normal((500, d))).astype(np.float32)
     R = float(np.sqrt(2.0 * d) * 0.8)
+    want = {"bf16x2": snn.SNN_SPLIT_BF16X2, "bf16x3": snn.SNN_SPLIT_BF16X3, "fp16x2": snn.SNN_SPLIT_FP16X2}[split]
     for q in (None, Q):
         got = _run(snn, P, q, R, "bf16")
+        assert got.stats["split_used"] == want
         assert_csr_equal(got, oracle.brute_radius(P, q, R), f"split={split} d={d}")
 
 
