@@ -37,10 +37,10 @@ HBM_PEAK_FALLBACK = 6800.0
 SCORER_SOURCES = ["tc_score.cu", "tc_score.cuh", "tc_common.cuh", "common.cuh", "index_struct.cuh",
                   "query_kernels.cuh"]
 SCORER_TRAFFIC = {
-    "sha": "0a1a3a6c595fcb32",
+    "sha": "42745175c21e5a17",
     "profile": "profiles/k_score_tc_dram_traffic_full_size.md",
-    ("gmm_aniso", 1000000, "bf16"): 192510208 + 172125440,
-    ("lowrank_img", 70000, "bf16"): 7257413632 + 9203968,
+    ("gmm_aniso", 1000000, "bf16"): 192556288 + 171962368,
+    ("lowrank_img", 70000, "bf16"): 6992338688 + 9428992,
 }
 
 
