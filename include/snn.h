@@ -115,8 +115,11 @@ typedef struct {
  *              BF16 where FP8 is not available);
  *  split_used  operand split of the tensor-core scorer: SNN_SPLIT_NONE (FP32
  *              scoring), SNN_SPLIT_BF16X2, SNN_SPLIT_BF16X3, SNN_SPLIT_FP16X2,
- *              or for e4m3 SNN_SPLIT_E4M3 + products per k-step (3, 4, 6);
- *  ms_*        device time of the phases (CUDA events on `stream`). */
+ *              SNN_SPLIT_FP16X1, or for e4m3 SNN_SPLIT_E4M3 + products per
+ *              k-step (3, 4, 6);
+ *  ms_*        device time of the phases (CUDA events on `stream`);
+ *              ms_score covers the operand packing and the scoring launch,
+ *              ms_score_kernel the scoring launch alone. */
 typedef struct {
     int64_t candidates;
     int64_t band_pairs;
@@ -130,12 +133,15 @@ typedef struct {
     float ms_csr;
     int32_t precision_used;
     int32_t split_used;
+    float ms_score_kernel;
+    int32_t reserved;
 } snn_query_stats;
 
 #define SNN_SPLIT_NONE 0
 #define SNN_SPLIT_BF16X2 1
 #define SNN_SPLIT_BF16X3 2
 #define SNN_SPLIT_FP16X2 3
+#define SNN_SPLIT_FP16X1 4
 #define SNN_SPLIT_E4M3 10
 
 /* Algorithm 1 (Section 3.1): centre, first principal direction, scores,

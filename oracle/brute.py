@@ -154,6 +154,52 @@ def pair_dist2(P: np.ndarray, Q: np.ndarray | None, qi: np.ndarray, pj: np.ndarr
     return out
 
 
+def radius_rows(P: np.ndarray, Q: np.ndarray | None, rows: np.ndarray, R: float,
+                margin: float = 1e-9) -> CSR:
+    """The neighbour lists of the query rows ``rows`` of Q (Q=None: of P), by
+    the definition of ``brute_radius``, for large P (sampled checks at full
+    size).  Row t of the result belongs to query ``rows[t]``.
+
+    A float64 matrix product gives G = ||p||^2 + ||q||^2 - 2 p.q.  In any
+    summation order it is within gamma_{d+2} (||p||^2 + ||q||^2 + 2 sum |p_k
+    q_k|) <= 2 gamma_{d+2} (||p||^2 + ||q||^2) of the exact ||p - q||^2
+    (gamma_k = k u / (1 - k u), u = 2^-53), and the definition's S is within
+    gamma_{d+2} ||p - q||^2 of it, so every pair with S <= fl64(R*R) has
+    G <= R2 + margin (R2 + ||p||^2 + ||q||^2) whenever margin >= 4
+    gamma_{d+2}.  Every pair inside that margin is then evaluated by the
+    definition itself (``snn_oracle_pairs``: ascending k, FP64, no FMA) and
+    decided by S <= R2; the product only discards pairs that are certainly
+    outside."""
+    P = _as_f32(P)
+    Qs = _as_f32((P if Q is None else _as_f32(Q))[np.asarray(rows, dtype=np.int64)])
+    n, d = P.shape
+    u = 2.0 ** -53
+    if not margin >= 4.0 * (d + 2) * u / (1.0 - (d + 2) * u):
+        raise ValueError("margin below the rounding bound of the matrix product")
+    R2 = float(np.float64(R) * np.float64(R))
+    P64 = P.astype(np.float64)
+    pn = np.einsum("ij,ij->i", P64, P64)
+    m = Qs.shape[0]
+    step = max(1, int(2e7 // max(n, 1)))
+    qi_all, pj_all = [], []
+    for a in range(0, m, step):
+        Qc = Qs[a:a + step].astype(np.float64)
+        qn = np.einsum("ij,ij->i", Qc, Qc)
+        G = qn[:, None] + pn[None, :] - 2.0 * (Qc @ P64.T)
+        mask = G <= R2 + margin * (R2 + qn[:, None] + pn[None, :])
+        qi, pj = np.nonzero(mask)          # row-major: ascending j within a row
+        qi_all.append(qi + a)
+        pj_all.append(pj)
+    qi = np.concatenate(qi_all) if qi_all else np.zeros(0, np.int64)
+    pj = np.concatenate(pj_all) if pj_all else np.zeros(0, np.int64)
+    S = pair_dist2(P, Qs, qi, pj)
+    keep = S <= R2
+    counts = np.bincount(qi[keep], minlength=m)
+    offsets = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(counts, out=offsets[1:])
+    return CSR(offsets, pj[keep].astype(np.int32), S[keep].astype(np.float32))
+
+
 def brute_row(P: np.ndarray, q: np.ndarray, R: float):
     """One query row against all of P: (ascending ids, dist2 float32)."""
     csr = brute_radius(P, np.asarray(q, dtype=np.float32).reshape(1, -1), R)

@@ -14,6 +14,20 @@ struct snn_shared_blocks {
     cudaStream_t stream = nullptr;
 };
 
+// One packed operand set of the tensor-core scorers: part[p] holds part p of
+// the split of every centred row (n x k2 16-bit values for part 1, n x k2n
+// for parts 2 and 3; FP16 or BF16, or e4m3 bytes), fold the separate block
+// of 16 folded BF16 columns per row where the kind has one.
+struct snn_tc_operands {
+    int kind = 0;                 // SNN_SPLIT_* code (e4m3: + products); 0: free slot
+    int k2 = 0, k2n = 0;          // row widths (elements)
+    int sigma = 0;                // two FP16 parts: the rows are scaled by 2^sigma
+    void *part[3] = {nullptr, nullptr, nullptr};
+    uint16_t *fold = nullptr;
+    cudaEvent_t ready = nullptr;  // recorded on the packing stream after packing
+};
+constexpr int kMaxTcOperands = 8;
+
 struct snn_index {
     int64_t n = 0;
     int d = 0, dp = 0;
@@ -31,24 +45,12 @@ struct snn_index {
     float *hx = nullptr;
     float *nrm = nullptr;
     float *dconst = nullptr;      // device: [0] alpha error bound, [1] max norm
-    // 16-bit split operands of the tensor-core path (built on first use):
-    // tc_part[p] is n x tc_k2 16-bit values, part p of the split of each
-    // centred row (FP16 or BF16) plus the folded threshold columns (BF16).
-    uint16_t *tc_part[3] = {nullptr, nullptr, nullptr};
-    int tc_nsplit = 0;
-    int tc_k2 = 0;                // row width of part 1 (columns)
-    int tc_k2n = 0;               // row width of parts 2 and 3
-    int tc_f16 = 0;               // the parts are FP16 (of x 2^tc_sigma), else BF16
-    int tc_sigma = 0;
-    // FP8 e4m3 operands (built on first use): f8_part[p] is n x f8_k8 bytes,
-    // part p of each row scaled by its power of two; f8_fold is n x 16 bf16,
-    // the folded threshold and error-bound columns.  Keyed by the split, the
-    // products per k-step and the row width.
-    uint8_t *f8_part[3] = {nullptr, nullptr, nullptr};
-    uint16_t *f8_fold = nullptr;
-    int f8_nsplit = 0;
-    int f8_np = 0;
-    int f8_k8 = 0;
+    // Packed operands of the tensor-core scorers, one entry per operand kind
+    // (split, row widths, scale), built on first use and kept until the
+    // index is released or updated; an entry is never replaced while the
+    // index lives, so a scorer on any stream may read it once its stream has
+    // waited for the entry's `ready` event.
+    snn_tc_operands tc_ops[kMaxTcOperands];
     float alpha_err = 0.f;
     float nrm_max = 0.f;
     mutable double surv_hint = 0.0;   // survivors per query seen last time

@@ -50,6 +50,7 @@ struct ScoreArgs {
     int *err;                   // device error flag (bounded waits that gave up)
     const double *Rq = nullptr; // per-query radii (sorted query order), or null
     double q_nrm_max = 0.0;     // largest centred query norm bound (tensor-core scaling)
+    cudaEvent_t ev_kernel[2] = {nullptr, nullptr};   // host: recorded around the scoring launch
 };
 
 // One work item of the FP32 scorer: a 128-query tile against band chunks

@@ -222,11 +222,7 @@ static snn_status own_output(T *p, cudaStream_t s) {
 
 void index_release(snn_index *ix) {
     if (!ix) return;
-    for (void *p : ix->tc_part)
-        if (p) cudaFreeAsync(p, ix->stream);
-    for (void *p : ix->f8_part)
-        if (p) cudaFreeAsync(p, ix->stream);
-    if (ix->f8_fold) cudaFreeAsync(ix->f8_fold, ix->stream);
+    release_tc_operands(ix, ix->stream);
     if (ix->shared) {
         snn_shared_blocks *sb = ix->shared;
         if (sb->refs.fetch_sub(1) == 1) {
@@ -611,18 +607,7 @@ static void install(snn_index *ix, PosArrays &a, int64_t n, cudaStream_t s) {
     void *old[] = {ix->alpha, ix->order, ix->praw, ix->xc, ix->hx, ix->nrm};
     for (void *p : old)
         if (p) cudaFreeAsync(p, s);
-    for (auto &p : ix->tc_part) {
-        if (p) cudaFreeAsync(p, s);
-        p = nullptr;
-    }
-    for (auto &p : ix->f8_part) {
-        if (p) cudaFreeAsync(p, s);
-        p = nullptr;
-    }
-    if (ix->f8_fold) cudaFreeAsync(ix->f8_fold, s);
-    ix->f8_fold = nullptr;
-    ix->tc_nsplit = ix->tc_k2 = ix->tc_k2n = 0;
-    ix->f8_nsplit = ix->f8_np = ix->f8_k8 = 0;
+    release_tc_operands(ix, s);
     ix->alpha = a.alpha;
     ix->order = a.order;
     ix->praw = a.praw;
@@ -865,7 +850,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         TRY_Q(own_output(out->offsets, s));
         return SNN_OK;
     }
-    cudaEvent_t ev[5] = {};
+    cudaEvent_t ev[7] = {};
     if (stats) {
         for (auto &e : ev) cudaEventCreate(&e);
         cudaEventRecord(ev[0], s);
@@ -1011,6 +996,10 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     sa.err = dev_err;
     sa.Rq = Rs;
     sa.q_nrm_max = q_nrm_max;
+    if (stats) {
+        sa.ev_kernel[0] = ev[5];
+        sa.ev_kernel[1] = ev[6];
+    }
     int32_t *counts, *lists, *big_list;
     int64_t *counts64, *big_len, *toff;
     unsigned *cls;
@@ -1058,10 +1047,12 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
                                  &split_used);
         } else {
             const int grid = device_sm_count() * 2;
+            if (stats) cudaEventRecord(ev[5], s);
             if (dp <= 16)
                 SNN_LAUNCH(k_score_fp32_single, grid, 256, 0, s)(sa);
             else
                 SNN_LAUNCH(k_score_fp32_multi, grid, 256, 0, s)(sa);
+            if (stats) cudaEventRecord(ev[6], s);
             if (cudaGetLastError() != cudaSuccess) {
                 set_error("score kernel launch failed");
                 st = SNN_ECUDA;
@@ -1223,6 +1214,8 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         cudaEventElapsedTime(&stats->ms_score, ev[1], ev[2]);
         cudaEventElapsedTime(&stats->ms_recheck, ev[2], ev[3]);
         cudaEventElapsedTime(&stats->ms_csr, ev[3], ev[4]);
+        cudaEventElapsedTime(&stats->ms_score_kernel, ev[5], ev[6]);
+        stats->reserved = 0;
         for (auto &e : ev) cudaEventDestroy(e);
     }
     // the caller owns the output arrays (released by snn_free)

@@ -116,6 +116,8 @@ __host__ __device__ constexpr int smem_budget(int cps, int align) {
 // F8NP > 0: FP8 e4m3 data k-blocks of 2 BK bytes per row (BK = NW = 16 or
 // 32: one or two K = 32 steps of F8NP products each), then one 32-byte BF16
 // k-block of folded columns in part 1's slots.
+// NSPLIT = 1: one FP16 part, one MMA per 16-column k step, then the same
+// separate block of folded BF16 columns (streamed shape only).
 template <int NSPLIT, int BK, int BN, bool ARES, int CPS = 1, int NW = BK, int MT = 1, int F8NP = 0>
 struct TcShape {
     static constexpr int kAlign = BK == 64 ? 1024 : 512;
@@ -134,7 +136,9 @@ struct TcShape {
     static constexpr int kStgBytes = tc_epi_warps(MT, BN) * kStgEntries * 8;
     static constexpr int kStagesRaw = (kSmemBudget - kAResBytes - kStgBytes) / kStageBytes;
     static constexpr int kStages = kStagesRaw > 12 ? 12 : kStagesRaw;
-    static constexpr int kNP = F8NP ? F8NP : (NSPLIT == 2 ? 3 : 6);   // MMAs per k-step
+    static constexpr int kNP = F8NP ? F8NP : (NSPLIT == 1 ? 1 : (NSPLIT == 2 ? 3 : 6));   // MMAs per k-step
+    // the folded columns come in a k-block of their own (32 bytes per row)
+    static constexpr bool kFoldBlock = F8NP != 0 || NSPLIT == 1;
     static constexpr int kKSteps = BK / 16;             // k-steps per k-block
     static constexpr int kRowBytes = BK * 2;
     static constexpr int kRowBytesN = NW * 2;
@@ -152,6 +156,8 @@ struct TcShape {
     static_assert(!F8NP || ((BK == 16 || BK == 32) && NW == BK && !ARES && MT == 1), "FP8 shape");
     static_assert(!F8NP || (NSPLIT == 2 && (F8NP == 3 || F8NP == 4)) || (NSPLIT == 3 && F8NP == 6),
                   "FP8 products");
+    static_assert(NSPLIT != 1 || (!F8NP && !ARES && MT == 1 && NW == BK && BK == 32),
+                  "one FP16 part: streamed shape with 32-column k-blocks");
 };
 
 __host__ __device__ constexpr int tc_npairs(int nsplit) { return nsplit == 2 ? 3 : 6; }
@@ -312,7 +318,7 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                         const int s = it % S;
                         const uint32_t round = uint32_t(it / S);
                         if (!mbar_wait(empty_bar(s), (round & 1u) ^ 1u, s_abort, a.err)) break;
-                        if (F8NP && kb == a.nkb - 1) {
+                        if (Sh::kFoldBlock && kb == a.nkb - 1) {
                             // folded BF16 columns, 32 bytes per row, in part 1's slots
                             mbar_expect_tx(full_bar(s), uint32_t((kTM + BN) * 32));
                             tma_load_2d(a_tile(s, 0), &qf, 0, int(f.q0), full_bar(s));
@@ -355,7 +361,23 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                         const uint32_t round = uint32_t(it / S);
                         if (!(ok = mbar_wait(full_bar(s), round & 1u, s_abort, a.err))) break;
                         tmem_fence_after();
-                        if constexpr (F8NP != 0) {
+                        if constexpr (NSPLIT == 1) {
+                            if (kb == a.nkb - 1) {
+                                // the folded columns: one BF16 K = 16 step
+                                mma_bf16(dt0, smem_desc<32>(a_tile(s, 0)), smem_desc<32>(b_tile(s, 0)),
+                                         kIdesc, 1u);
+                            } else {
+#pragma unroll
+                                for (int ks = 0; ks < Sh::kKSteps; ++ks) {
+                                    // FP16 data k steps; the last block may hold one
+                                    const int kg = kb * Sh::kKSteps + ks;
+                                    if (kg >= a.ksteps_data) break;
+                                    mma_bf16(dt0, smem_desc<Sh::kRowBytes>(a_tile(s, 0) + 32u * ks),
+                                             smem_desc<Sh::kRowBytes>(b_tile(s, 0) + 32u * ks), kIdescF16,
+                                             kg != 0 ? 1u : 0u);
+                                }
+                            }
+                        } else if constexpr (F8NP != 0) {
                             static_assert(Sh::kRowBytesN == Sh::kRowBytes, "FP8 parts share one width");
                             if (kb == a.nkb - 1) {
                                 // the folded columns: one BF16 K = 16 step
@@ -755,6 +777,54 @@ __device__ __forceinline__ uint16_t bf16_up(double v) {
     return bf16_bits(__float2bfloat16_ru(__double2float_ru(v)));
 }
 
+// The 16 folded BF16 columns of a row scaled by sc = 2^s (every bound entry
+// rounded up; the query side's inflated by 1 + 2 kacc):
+//   data:  -(1-ch) lead 2^s (split in 3, lead = halved norm) | 2^s x3 | nsum |
+//          ||x'|| | ||e_x|| | b9 | b10 | zeros
+//   query: 2^s x3 | lead 2^s (split in 3, lead = A'_i) | kacc nsum | ||e_y|| |
+//          ||y'|| + ||e_y|| | b9 | b10 | zeros
+// (nsum = sum of the parts' norms, e the exact residual of the split, b9 and
+// b10 the norms that bound dropped products, zero where none are dropped).
+// Their products are the rank-one terms of the bound on x'.y' minus the kept
+// products, plus kacc Nx Ny for the accumulation.
+__device__ __forceinline__ void write_fold16(uint16_t *__restrict__ out, int query_side, float sc,
+                                             double lead, double ch, double kacc, float nsum, float nx,
+                                             float ne, double b9, double b10) {
+    uint16_t f[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) f[t] = 0;
+    const uint16_t one = bf16_bits(__float2bfloat16_rn(sc));   // exact power of two
+    uint16_t sp3[3];
+    if (!query_side) {
+        split3(-(1.0 - ch) * lead * (double)sc, sp3);
+        for (int t = 0; t < 3; ++t) {
+            f[t] = sp3[t];
+            f[3 + t] = one;
+        }
+        f[6] = bf16_up(nsum);
+        f[7] = bf16_up(nx);
+        f[8] = bf16_up(ne);
+        f[9] = bf16_up(b9);
+        f[10] = bf16_up(b10);
+    } else {
+        const double infl = 1.0 + 2.0 * kacc;
+        split3(lead * (double)sc, sp3);
+        for (int t = 0; t < 3; ++t) {
+            f[t] = one;
+            f[3 + t] = sp3[t];
+        }
+        f[6] = bf16_up(kacc * (double)nsum * infl);
+        f[7] = bf16_up((double)ne * infl);
+        f[8] = bf16_up(((double)nx + (double)ne) * infl);
+        f[9] = bf16_up(b9 * infl);
+        f[10] = bf16_up(b10 * infl);
+    }
+    uint4 *fo = reinterpret_cast<uint4 *>(out);
+    const uint32_t *fw = reinterpret_cast<const uint32_t *>(f);
+    fo[0] = make_uint4(fw[0], fw[1], fw[2], fw[3]);
+    fo[1] = make_uint4(fw[4], fw[5], fw[6], fw[7]);
+}
+
 // FP8 rows, one warp per row.  The centred FP32 row x is scaled by 2^s, s
 // chosen from its largest |x_k| so that the scaled row x' peaks in
 // [128, 256) (clamped to [-23, 24]), and split x' = x_1 + ... + x_P + e with
@@ -854,51 +924,114 @@ __global__ void k_f8_pack(const float *__restrict__ xc, int dp, const float *__r
             const float nx = __fsqrt_ru(sx);
             // + 2^-100 covers scaling underflow of tiny elements (s < 0)
             const float ne = __fadd_ru(__fsqrt_ru(se), 0x1p-100f);
-            float np[3], nsum = 0.f;
+            float np[3] = {0.f, 0.f, 0.f}, nsum = 0.f;
 #pragma unroll
             for (int p = 0; p < NSPLIT; ++p) {
                 np[p] = __fsqrt_ru(sp[p]);
                 nsum = __fadd_ru(nsum, np[p]);
             }
-            uint16_t f[16];
-#pragma unroll
-            for (int t = 0; t < 16; ++t) f[t] = 0;
-            const uint16_t one = bf16_bits(__float2bfloat16_rn(sc));   // exact power of two
-            uint16_t sp3[3];
+            // the dropped products' norms: x_2.y_2 (three products), or
+            // x_2.y_3 + x_3.y_2 + x_3.y_3 (three parts)
+            double b9 = 0.0, b10 = 0.0;
             if (!query_side) {
-                split3(-(1.0 - ch) * (double)hx[r] * (double)sc, sp3);
-                for (int t = 0; t < 3; ++t) {
-                    f[t] = sp3[t];
-                    f[3 + t] = one;
-                }
-                f[6] = bf16_up(nsum);
-                f[7] = bf16_up(nx);
-                f[8] = bf16_up(ne);
-                if (NP == 3) f[9] = bf16_up(np[1]);
-                if (NP == 6) {
-                    f[9] = bf16_up(np[1]);
-                    f[10] = bf16_up(np[2]);
-                }
+                if (NP == 3 || NP == 6) b9 = np[1];
+                if (NP == 6) b10 = np[2];
             } else {
-                const double infl = 1.0 + 2.0 * kacc;
-                split3(Aq[r] * (double)sc, sp3);
-                for (int t = 0; t < 3; ++t) {
-                    f[t] = one;
-                    f[3 + t] = sp3[t];
-                }
-                f[6] = bf16_up(kacc * (double)nsum * infl);
-                f[7] = bf16_up((double)ne * infl);
-                f[8] = bf16_up(((double)nx + (double)ne) * infl);
-                if (NP == 3) f[9] = bf16_up((double)np[1] * infl);
+                if (NP == 3) b9 = np[1];
                 if (NP == 6) {
-                    f[9] = bf16_up((double)np[2] * infl);
-                    f[10] = bf16_up(((double)np[1] + (double)np[2]) * infl);
+                    b9 = np[2];
+                    b10 = (double)np[1] + (double)np[2];
                 }
             }
-            uint4 *fo = reinterpret_cast<uint4 *>(fold + r * 16);
-            const uint32_t *fw = reinterpret_cast<const uint32_t *>(f);
-            fo[0] = make_uint4(fw[0], fw[1], fw[2], fw[3]);
-            fo[1] = make_uint4(fw[4], fw[5], fw[6], fw[7]);
+            write_fold16(fold + r * 16, query_side, sc, query_side ? Aq[r] : (double)hx[r], ch, kacc, nsum,
+                         nx, ne, b9, b10);
+        }
+    }
+}
+
+// One FP16 part per row (the single-part 16-bit scorer), one warp per row.
+// The centred FP32 row x is scaled by 2^s, s from its largest |x_k| so that
+// the scaled row x' peaks in [2^14, 2^15) (clamped to [-23, 24]), and
+// rounded once to FP16: x' = x_1 + e, with x_1 set to zero where it would
+// fall below the FP16 normal range (or above its largest finite value) and
+// the residual e exact in FP32 (Sterbenz).  The norms of x', x_1 and e are
+// summed with upward rounding; the 16 folded BF16 columns (write_fold16: one
+// part, no dropped products) bound x'.y' - x_1.y_1 = x'.e_y + e_x.y' - e_x.e_y
+// and the accumulation per pair.  Rows of K2 FP16 values (zero beyond d).
+__global__ void k_h1_pack(const float *__restrict__ xc, int dp, const float *__restrict__ hx,
+                          const double *__restrict__ Aq, int64_t rows, int d, int K2, double ch,
+                          double kacc, int query_side, uint16_t *__restrict__ p0,
+                          uint16_t *__restrict__ fold) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    constexpr int U = 8;                   // quads per lane in flight (1,024 columns a warp)
+    const bool one_chunk = K2 <= 128 * U;  // the row stays in registers between the passes
+    for (int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; r < rows; r += nwarps) {
+        const float4 *xr = reinterpret_cast<const float4 *>(xc + r * dp);
+        float4 xv[U];
+        auto load = [&](int kc) {
+#pragma unroll
+            for (int t = 0; t < U; ++t) {
+                const int k0 = kc + (lane + 32 * t) * 4;
+                xv[t] = k0 < d ? xr[k0 / 4] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        };
+        float mx = 0.f;
+        for (int kc = 0; kc < d; kc += 128 * U) {
+            load(kc);
+#pragma unroll
+            for (int t = 0; t < U; ++t) {
+                const int k0 = kc + (lane + 32 * t) * 4;
+                const float xs[4] = {xv[t].x, xv[t].y, xv[t].z, xv[t].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (k0 + e < d) mx = fmaxf(mx, fabsf(xs[e]));
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        int sg = 0;
+        if (mx > 0.f) {
+            int ex;
+            frexpf(mx, &ex);                   // mx in [2^(ex-1), 2^ex)
+            sg = min(24, max(-23, 15 - ex));
+        }
+        const float sc = __uint_as_float(uint32_t(127 + sg) << 23);   // 2^sg
+        float sx = 0.f, se = 0.f, s1 = 0.f;
+        for (int kc = 0; kc < K2; kc += 128 * U) {
+            if (!one_chunk) load(kc);
+#pragma unroll
+            for (int t = 0; t < U; ++t) {
+                const int k0 = kc + (lane + 32 * t) * 4;
+                if (k0 >= K2) break;
+                const float xs[4] = {xv[t].x, xv[t].y, xv[t].z, xv[t].w};
+                uint16_t hb[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float x = k0 + e < d ? xs[e] * sc : 0.f;
+                    const __half h = __float2half_rn(x);
+                    float hf = __half2float(h);
+                    const bool keep = fabsf(hf) >= 0x1p-14f && fabsf(hf) <= 65504.f;
+                    hf = keep ? hf : 0.f;
+                    const float rr = x - hf;   // exact: hf is 0 or within a factor 2 of x
+                    sx = __fmaf_ru(x, x, sx);
+                    s1 = __fmaf_ru(hf, hf, s1);
+                    se = __fmaf_ru(rr, rr, se);
+                    hb[e] = keep ? *reinterpret_cast<const uint16_t *>(&h) : uint16_t(0);
+                }
+                *reinterpret_cast<uint2 *>(p0 + r * K2 + k0) =
+                    make_uint2(uint32_t(hb[0]) | (uint32_t(hb[1]) << 16), uint32_t(hb[2]) | (uint32_t(hb[3]) << 16));
+            }
+        }
+        sx = warp_sum_ru(sx);
+        se = warp_sum_ru(se);
+        s1 = warp_sum_ru(s1);
+        if (lane == 0) {
+            const float nx = __fsqrt_ru(sx);
+            const float ne = __fadd_ru(__fsqrt_ru(se), 0x1p-100f);
+            const float n1 = __fsqrt_ru(s1);
+            write_fold16(fold + r * 16, query_side, sc, query_side ? Aq[r] : (double)hx[r], ch, kacc, n1,
+                         nx, ne, 0.0, 0.0);
         }
     }
 }
@@ -969,25 +1102,28 @@ TcArgs tc_args(const snn_index *ix, const ScoreArgs &sa, const TileSet &ts) {
 
 // maps: query parts 1-3, data parts 1-3, query folded, data folded
 template <int NSPLIT, int BK, int BN, bool ARES, int CPS, int NW, int MT, int F8NP>
-snn_status run_tc(const CUtensorMap (&maps)[8], const TcArgs &a, cudaStream_t s) {
+snn_status run_tc(const CUtensorMap (&maps)[8], const TcArgs &a, const ScoreArgs &sa, cudaStream_t s) {
     using Sh = TcShape<NSPLIT, BK, BN, ARES, CPS, NW, MT, F8NP>;
     auto kern = k_score_tc<NSPLIT, BK, BN, ARES, CPS, NW, MT, F8NP>;
     SNN_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::kSmem)));
+    if (sa.ev_kernel[0]) cudaEventRecord(sa.ev_kernel[0], s);
     SNN_LAUNCH(kern, device_sm_count() * CPS, Sh::kThreads, Sh::kSmem, s)(
         maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], maps[6], maps[7], a);
     SNN_LAUNCH_CHECK();
+    if (sa.ev_kernel[1]) cudaEventRecord(sa.ev_kernel[1], s);
     return SNN_OK;
 }
 
 template <int NSPLIT, int BK, int BN, bool ARES, int CPS, int NW, int MT>
-snn_status launch_tc(const snn_index *ix, const ScoreArgs &sa, const uint16_t *const *qp,
-                     int K2, int K2n, const TileSet &ts, cudaStream_t s, int f16) {
+snn_status launch_tc(const snn_index *ix, const snn_tc_operands &op, const ScoreArgs &sa,
+                     const uint16_t *const *qp, int K2, int K2n, const TileSet &ts, cudaStream_t s,
+                     int f16) {
     CUtensorMap maps[8];
     for (int p = 0; p < 3; ++p) {
         const int pp = p < NSPLIT ? p : 0;
         const int k2 = pp == 0 ? K2 : K2n, box = pp == 0 ? BK : NW;
         SNN_TRY(make_map(&maps[p], qp[pp], sa.q.m, k2, box, kTM * MT));
-        SNN_TRY(make_map(&maps[3 + p], ix->tc_part[pp], ix->n, k2, box, BN));
+        SNN_TRY(make_map(&maps[3 + p], static_cast<const uint16_t *>(op.part[pp]), ix->n, k2, box, BN));
     }
     maps[6] = maps[0];   // no folded block of its own
     maps[7] = maps[3];
@@ -996,7 +1132,7 @@ snn_status launch_tc(const snn_index *ix, const ScoreArgs &sa, const uint16_t *c
     a.ksteps = f16 ? a.ksteps_data + 1 : int(cdiv(ix->d + kExtra, 16));
     a.nkb = K2 / BK;
     a.f16 = f16;
-    return run_tc<NSPLIT, BK, BN, ARES, CPS, NW, MT, 0>(maps, a, s);
+    return run_tc<NSPLIT, BK, BN, ARES, CPS, NW, MT, 0>(maps, a, sa, s);
 }
 
 // FP8 shape: 128 queries x 256 band rows, k-blocks of 2 BK bytes per row (BK
@@ -1005,25 +1141,94 @@ snn_status launch_tc(const snn_index *ix, const ScoreArgs &sa, const uint16_t *c
 // block.  64-byte blocks halve the copy's row requests per MMA, which is what
 // bounds the two-part variants with 32-byte blocks.
 template <int NSPLIT, int F8NP, int BK>
-snn_status launch_f8(const snn_index *ix, const ScoreArgs &sa, uint8_t *const *qp,
-                     const uint16_t *qfold, int K8, const TileSet &ts, cudaStream_t s) {
+snn_status launch_f8(const snn_index *ix, const snn_tc_operands &op, const ScoreArgs &sa,
+                     uint8_t *const *qp, const uint16_t *qfold, int K8, const TileSet &ts, cudaStream_t s) {
     CUtensorMap maps[8];
     for (int p = 0; p < 3; ++p) {
         const int pp = p < NSPLIT ? p : 0;
         // e4m3 rows as 16-bit pairs: K8 / 2 elements, boxes of BK pairs
         SNN_TRY(make_map(&maps[p], reinterpret_cast<const uint16_t *>(qp[pp]), sa.q.m, K8 / 2, BK, kTM));
-        SNN_TRY(make_map(&maps[3 + p], reinterpret_cast<const uint16_t *>(ix->f8_part[pp]), ix->n,
-                         K8 / 2, BK, 256));
+        SNN_TRY(make_map(&maps[3 + p], static_cast<const uint16_t *>(op.part[pp]), ix->n, K8 / 2, BK, 256));
     }
     SNN_TRY(make_map(&maps[6], qfold, sa.q.m, 16, 16, kTM));
-    SNN_TRY(make_map(&maps[7], ix->f8_fold, ix->n, 16, 16, 256));
+    SNN_TRY(make_map(&maps[7], op.fold, ix->n, 16, 16, 256));
     TcArgs a = tc_args(ix, sa, ts);
     a.ksteps_data = K8 / 32;
     a.nkb = int(cdiv(K8, 2 * BK)) + 1;
-    return run_tc<NSPLIT, BK, 256, false, 1, BK, 1, F8NP>(maps, a, s);
+    return run_tc<NSPLIT, BK, 256, false, 1, BK, 1, F8NP>(maps, a, sa, s);
+}
+
+// The operands of `kind` (row widths k2, k2n, scale sigma) from the index's
+// cache, packed on stream s by `pack` (which receives the new entry with its
+// arrays allocated) when the cache has none.  s then waits for the entry's
+// ready event, so an entry packed on another stream is complete before the
+// scorer reads it.  Entries are never replaced while the index lives.
+template <class Pack>
+snn_status cached_operands(snn_index *ix, int kind, int k2, int k2n, int sigma, const size_t (&bytes)[4],
+                           cudaStream_t s, Pack &&pack, const snn_tc_operands **out) {
+    std::lock_guard<std::mutex> lk(ix->mu);
+    snn_tc_operands *hit = nullptr, *slot = nullptr;
+    for (auto &e : ix->tc_ops) {
+        if (e.kind == kind && e.k2 == k2 && e.k2n == k2n && e.sigma == sigma) {
+            hit = &e;
+            break;
+        }
+        if (!e.kind && !slot) slot = &e;
+    }
+    if (!hit) {
+        if (!slot) {
+            set_error("tensor-core operand cache of the index is full");
+            return SNN_ENOTSUP;
+        }
+        snn_tc_operands e;
+        e.kind = kind;
+        e.k2 = k2;
+        e.k2n = k2n;
+        e.sigma = sigma;
+        cudaError_t err = cudaSuccess;
+        for (int p = 0; p < 3 && err == cudaSuccess; ++p)
+            if (bytes[p]) err = cudaMallocAsync(&e.part[p], bytes[p], s);
+        if (err == cudaSuccess && bytes[3])
+            err = cudaMallocAsync(reinterpret_cast<void **>(&e.fold), bytes[3], s);
+        if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming);
+        snn_status st = SNN_OK;
+        if (err != cudaSuccess) {
+            cudaGetLastError();
+            set_error("tensor-core operand allocation failed: %s", cudaGetErrorString(err));
+            st = SNN_ENOMEM;
+        } else {
+            st = pack(e);
+            if (st == SNN_OK && cudaEventRecord(e.ready, s) != cudaSuccess) {
+                set_error("cudaEventRecord failed");
+                st = SNN_ECUDA;
+            }
+        }
+        if (st != SNN_OK) {
+            for (void *p : e.part)
+                if (p) cudaFreeAsync(p, s);
+            if (e.fold) cudaFreeAsync(e.fold, s);
+            if (e.ready) cudaEventDestroy(e.ready);
+            return st;
+        }
+        *slot = e;
+        hit = slot;
+    }
+    SNN_CUDA(cudaStreamWaitEvent(s, hit->ready, 0));
+    *out = hit;
+    return SNN_OK;
 }
 
 }  // namespace
+
+void release_tc_operands(snn_index *ix, cudaStream_t s) {
+    for (auto &e : ix->tc_ops) {
+        for (void *p : e.part)
+            if (p) cudaFreeAsync(p, s);
+        if (e.fold) cudaFreeAsync(e.fold, s);
+        if (e.ready) cudaEventDestroy(e.ready);
+        e = snn_tc_operands();
+    }
+}
 
 bool f8_eligible(const snn_index *ix, double Rx) {
     return ix->d + kExtra > 64 && double(ix->nrm_max) <= 0x1p20 && Rx <= 0x1p20;
@@ -1061,35 +1266,19 @@ snn_status f8_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
         return unsigned(std::min<int64_t>(cdiv(rows, pack_threads / 32), int64_t(16) * device_sm_count()));
     };
     auto packer = np == 3 ? k_f8_pack<2, 3> : (np == 4 ? k_f8_pack<2, 4> : k_f8_pack<3, 6>);
-    {
-        std::lock_guard<std::mutex> lk(ix->mu);
-        if (ix->f8_nsplit != nsplit || ix->f8_np != np || ix->f8_k8 != K8) {
-            for (int p = 0; p < 3; ++p) {
-                if (ix->f8_part[p]) cudaFreeAsync(ix->f8_part[p], s);
-                ix->f8_part[p] = nullptr;
-            }
-            if (ix->f8_fold) cudaFreeAsync(ix->f8_fold, s);
-            ix->f8_fold = nullptr;
-            ix->f8_nsplit = 0;
-            cudaError_t e = cudaSuccess;
-            for (int p = 0; p < nsplit && e == cudaSuccess; ++p)
-                e = cudaMallocAsync(reinterpret_cast<void **>(&ix->f8_part[p]), size_t(ix->n) * K8, s);
-            if (e == cudaSuccess)
-                e = cudaMallocAsync(reinterpret_cast<void **>(&ix->f8_fold),
-                                    size_t(ix->n) * 16 * sizeof(uint16_t), s);
-            if (e != cudaSuccess) {
-                set_error("FP8 operand allocation failed: %s", cudaGetErrorString(e));
-                return SNN_ENOMEM;
-            }
-            SNN_LAUNCH(packer, pack_grid(ix->n), pack_threads, 0, s)(
-                ix->xc, ix->dp, ix->hx, nullptr, ix->n, d, K8, ch, kacc, 0, ix->f8_part[0],
-                ix->f8_part[1], ix->f8_part[2], ix->f8_fold);
-            SNN_LAUNCH_CHECK();
-            ix->f8_nsplit = nsplit;
-            ix->f8_np = np;
-            ix->f8_k8 = K8;
-        }
-    }
+    const size_t pb = size_t(ix->n) * K8;
+    const size_t bytes[4] = {pb, pb, nsplit == 3 ? pb : 0, size_t(ix->n) * 16 * sizeof(uint16_t)};
+    const snn_tc_operands *op = nullptr;
+    SNN_TRY(cached_operands(ix, SNN_SPLIT_E4M3 + np, K8, K8, 0, bytes, s,
+                            [&](snn_tc_operands &e) -> snn_status {
+                                SNN_LAUNCH(packer, pack_grid(ix->n), pack_threads, 0, s)(
+                                    ix->xc, ix->dp, ix->hx, nullptr, ix->n, d, K8, ch, kacc, 0,
+                                    static_cast<uint8_t *>(e.part[0]), static_cast<uint8_t *>(e.part[1]),
+                                    static_cast<uint8_t *>(e.part[2]), e.fold);
+                                SNN_LAUNCH_CHECK();
+                                return SNN_OK;
+                            },
+                            &op));
     if (mma_flops_per_pair) *mma_flops_per_pair = int64_t(2) * 32 * np * ksteps + 2 * 16;
     const int64_t m = sa.q.m;
     double *Aq;
@@ -1107,48 +1296,125 @@ snn_status f8_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
     SNN_LAUNCH_CHECK();
     TileSet ts1{sa.tile_lo, sa.tile_hi, sa.item_off, sa.item_tile, sa.ntiles};
     // 64-byte k-blocks: four stages of 48 KB (two parts) or three of 72 KB
-    if (np == 3) return launch_f8<2, 3, 32>(ix, sa, qp, qfold, K8, ts1, s);
-    if (np == 4) return launch_f8<2, 4, 32>(ix, sa, qp, qfold, K8, ts1, s);
-    return launch_f8<3, 6, 32>(ix, sa, qp, qfold, K8, ts1, s);
+    if (np == 3) return launch_f8<2, 3, 32>(ix, *op, sa, qp, qfold, K8, ts1, s);
+    if (np == 4) return launch_f8<2, 4, 32>(ix, *op, sa, qp, qfold, K8, ts1, s);
+    return launch_f8<3, 6, 32>(ix, *op, sa, qp, qfold, K8, ts1, s);
 }
+
+namespace {
+
+// One FP16 part per row (per-row power-of-two scales) with the per-pair
+// residual bound folded into a separate BF16 k-block: one MMA per 16-column
+// k step.  Streamed shape: 128 queries x 256 band rows, 32-column k-blocks.
+snn_status h1_score_launch(snn_index *ix, const ScoreArgs &sa, cudaStream_t s, double Rx, double e_data,
+                           Scratch &scr, int64_t *mma_flops_per_pair) {
+    const int d = ix->d;
+    const int K2 = int(cdiv(d, 16) * 16);
+    const int ksteps = K2 / 16;
+    // accumulation: every instruction (the FP16 steps and the folded BF16
+    // step) is charged 2^-22 of its input accumulator plus its products
+    const double kacc = 0x1p-22 * (ksteps + 2);
+    // halved norm: its FP32 evaluation, its 3-part split, the accumulation
+    const double ch = 1.02 * (0x1p-23 + 1.05 * (d + 2) * 0x1p-24 + kacc);
+    const int pack_threads = 256;
+    auto pack_grid = [&](int64_t rows) {
+        return unsigned(std::min<int64_t>(cdiv(rows, pack_threads / 32), int64_t(16) * device_sm_count()));
+    };
+    const size_t bytes[4] = {size_t(ix->n) * K2 * sizeof(uint16_t), 0, 0, size_t(ix->n) * 16 * sizeof(uint16_t)};
+    const snn_tc_operands *op = nullptr;
+    SNN_TRY(cached_operands(ix, SNN_SPLIT_FP16X1, K2, 0, 0, bytes, s,
+                            [&](snn_tc_operands &e) -> snn_status {
+                                SNN_LAUNCH(k_h1_pack, pack_grid(ix->n), pack_threads, 0, s)(
+                                    ix->xc, ix->dp, ix->hx, nullptr, ix->n, d, K2, ch, kacc, 0,
+                                    static_cast<uint16_t *>(e.part[0]), e.fold);
+                                SNN_LAUNCH_CHECK();
+                                return SNN_OK;
+                            },
+                            &op));
+    if (mma_flops_per_pair) *mma_flops_per_pair = int64_t(2) * 16 * (ksteps + 1);
+    const int64_t m = sa.q.m;
+    double *Aq;
+    uint16_t *qp, *qfold;
+    SNN_TRY(scr.alloc(&Aq, m));
+    SNN_TRY(scr.alloc(&qp, size_t(m) * K2));
+    SNN_TRY(scr.alloc(&qfold, size_t(m) * 16));
+    // a margin of 2^-60 keeps A'_i 2^(s_x + s_y) a normal FP32 number
+    SNN_LAUNCH(k_tc_query_consts, unsigned(cdiv(m, 256)), 256, 0, s)(
+        sa.q.hx, sa.q.nrm, m, d, Rx, e_data, 0x1p-23 + kacc, 0x1p-60, Aq, sa.Rq, 0.0, 0.0);
+    SNN_LAUNCH_CHECK();
+    SNN_LAUNCH(k_h1_pack, pack_grid(m), pack_threads, 0, s)(sa.q.xc, ix->dp, nullptr, Aq, m, d, K2, ch, kacc,
+                                                           1, qp, qfold);
+    SNN_LAUNCH_CHECK();
+    CUtensorMap maps[8];
+    SNN_TRY(make_map(&maps[0], qp, m, K2, 32, kTM));
+    SNN_TRY(make_map(&maps[3], static_cast<const uint16_t *>(op->part[0]), ix->n, K2, 32, 256));
+    maps[1] = maps[2] = maps[0];
+    maps[4] = maps[5] = maps[3];
+    SNN_TRY(make_map(&maps[6], qfold, m, 16, 16, kTM));
+    SNN_TRY(make_map(&maps[7], op->fold, ix->n, 16, 16, 256));
+    TileSet ts{sa.tile_lo, sa.tile_hi, sa.item_off, sa.item_tile, sa.ntiles};
+    TcArgs a = tc_args(ix, sa, ts);
+    a.ksteps_data = ksteps;
+    a.nkb = int(cdiv(K2, 32)) + 1;
+    return run_tc<1, 32, 256, false, 1, 32, 1, 0>(maps, a, sa, s);
+}
+
+}  // namespace
 
 snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream_t s,
                            double Rx, double e_data, Scratch &scr, int64_t *mma_flops_per_pair,
                            int *split_used) {
     snn_index *ix = const_cast<snn_index *>(ixc);
     const int d = ix->d;
-    // operands: two BF16 parts where their bound stays a small fraction of
-    // R^2/2 for the largest norms (high d, moderate norms), else two FP16
-    // parts of the rows scaled by 2^sigma, which need the MMAs of two BF16
-    // parts and bound the dropped terms as tightly as three BF16 parts do.
-    // SNN_TC_SPLIT = bf16x2, bf16x3 or fp16x2 overrides.
+    const double Nd = (double)ix->nrm_max, Nq = sa.q_nrm_max;
+    // operands, chosen by how tight their bound is against R^2 for the
+    // largest norms:
+    // * one FP16 part per row (per-row scales, the per-pair bound built from
+    //   the exact residual norms): one MMA per k step.  Streamed shape only
+    //   (d + 9 > 64) and norms below 2^20.  Its residual is typically about
+    //   2^-12 of the row norm, so the bound is about 4 2^-12 ||x|| ||y||;
+    // * two BF16 parts where their bound stays a small fraction of R^2/2
+    //   (high d, moderate norms);
+    // * else two FP16 parts of the rows scaled by 2^sigma, which need the
+    //   MMAs of two BF16 parts and bound the dropped terms as tightly as three
+    //   BF16 parts do.
+    // SNN_TC_SPLIT = fp16x1, bf16x2, bf16x3 or fp16x2 overrides (fp16x1 only
+    // where its shape and ranges allow it).
+    const bool h1_ok = d + kExtra > 64 && Nd <= 0x1p20 && Nq <= 0x1p20 && Rx <= 0x1p20;
+    bool h1 = h1_ok && 4.0 * 0x1p-12 * Nd * Nq <= 0.02 * Rx * Rx;
     const double c2 = tc_constant(2, d, nullptr, false);
-    const double Nd = (double)ix->nrm_max;
     bool f16 = !(c2 * 1.5 * Nd * Nd <= 0.02 * 0.5 * Rx * Rx);
     int nsplit = 2;
     if (const char *e = getenv("SNN_TC_SPLIT")) {
-        if (!strcmp(e, "bf16x2")) f16 = false;
-        else if (!strcmp(e, "bf16x3")) f16 = false, nsplit = 3;
-        else if (!strcmp(e, "fp16x2")) f16 = true;
+        if (!strcmp(e, "bf16x2")) f16 = false, h1 = false;
+        else if (!strcmp(e, "bf16x3")) f16 = false, nsplit = 3, h1 = false;
+        else if (!strcmp(e, "fp16x2")) f16 = true, h1 = false;
+        else if (!strcmp(e, "fp16x1")) h1 = h1_ok;
     }
-    // sigma: the largest of the centred norms of the data and the queries
-    // and the radius, scaled, lies in [2^13, 2^14), so every scaled
-    // coordinate is an FP16 number and every scaled folded value (squares of
-    // these, halved) stays below 2^28
-    const double N = std::max(std::max<double>((double)ix->nrm_max, sa.q_nrm_max), Rx);
+    if (h1) {
+        if (split_used) *split_used = SNN_SPLIT_FP16X1;
+        return h1_score_launch(ix, sa, s, Rx, e_data, scr, mma_flops_per_pair);
+    }
+    // sigma, from the index alone: the largest centred data norm, scaled,
+    // lies in [2^13, 2^14), so every scaled data coordinate is an FP16
+    // number.  Query coordinates are at most the query norms; where those,
+    // scaled, could leave the FP16 range this call takes BF16 parts.
     int sigma = 0;
-    if (f16 && N > 0.0) sigma = std::min(120, std::max(-120, 13 - std::ilogb(N)));
+    if (Nd > 0.0) sigma = std::min(120, std::max(-120, 13 - std::ilogb(Nd)));
+    if (f16 && !(std::ldexp(Nq, sigma) <= 60000.0)) f16 = false;
+    if (!f16) sigma = 0;
     const double fs1 = std::ldexp(1.0, sigma), fs2 = std::ldexp(1.0, 2 * sigma);
     double u_k = 0.0;
     const double c = tc_constant(nsplit, d, &u_k, f16);
     // absolute part of the FP16 bound, in unscaled units: 1.001 2^-14 sqrt(d)
     // (||x'|| + ||y'||) + 2 d 2^-28 in scaled units (parts below 2^-14 are zero)
     const double abs_q = f16 ? 1.001 * std::sqrt(double(d)) * std::ldexp(1.0, -14 - sigma) : 0.0;
-    const double abs_n = f16 ? abs_q * (double)ix->nrm_max + 2.0 * d * std::ldexp(1.0, -28 - 2 * sigma) : 0.0;
+    const double abs_n = f16 ? abs_q * Nd + 2.0 * d * std::ldexp(1.0, -28 - 2 * sigma) : 0.0;
     // shape: one 32- or 64-column k-block holds everything for low d (query
     // tile resident for a whole item); 64-column k-blocks streamed otherwise.
     // With FP16 parts the folded columns start on a k step boundary.
-    if (split_used) *split_used = f16 ? SNN_SPLIT_FP16X2 : (nsplit == 3 ? SNN_SPLIT_BF16X3 : SNN_SPLIT_BF16X2);
+    const int kind = f16 ? SNN_SPLIT_FP16X2 : (nsplit == 3 ? SNN_SPLIT_BF16X3 : SNN_SPLIT_BF16X2);
+    if (split_used) *split_used = kind;
     const int fold_col = f16 ? int(cdiv(d, 16) * 16) : d;
     const int kp = fold_col + kExtra;
     const int bk = kp <= 32 ? 32 : 64;
@@ -1157,36 +1423,20 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
     // the first 16, their rows are 16 columns wide (low-d shape only)
     const int K2n = (kp <= 32 && d <= 16) ? 16 : K2;
     const TcPackMode pm{f16 ? 1 : 0, fold_col, float(fs1), fs1, fs2};
-    {
-        std::lock_guard<std::mutex> lk(ix->mu);
-        if (ix->tc_nsplit != nsplit || ix->tc_k2 != K2 || ix->tc_k2n != K2n || ix->tc_f16 != int(f16) ||
-            ix->tc_sigma != sigma) {
-            for (int p = 0; p < 3; ++p) {
-                if (ix->tc_part[p]) cudaFreeAsync(ix->tc_part[p], s);
-                ix->tc_part[p] = nullptr;
-            }
-            ix->tc_nsplit = 0;
-            for (int p = 0; p < nsplit; ++p) {
-                const int w = p == 0 ? K2 : K2n;
-                cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&ix->tc_part[p]),
-                                                size_t(ix->n) * w * sizeof(uint16_t), s);
-                if (e != cudaSuccess) {
-                    set_error("tensor-core operand allocation failed: %s", cudaGetErrorString(e));
-                    return SNN_ENOMEM;
-                }
-            }
-            auto packer = nsplit == 2 ? k_tc_pack<2> : k_tc_pack<3>;
-            SNN_LAUNCH(packer, unsigned(cdiv(cdiv(ix->n, 32) * 32, 256)), 256, 0, s)(
-                ix->xc, ix->dp, ix->hx, ix->nrm, nullptr, ix->n, d, K2, K2n, c, 0, ix->tc_part[0],
-                ix->tc_part[1], ix->tc_part[2], pm);
-            SNN_LAUNCH_CHECK();
-            ix->tc_nsplit = nsplit;
-            ix->tc_k2 = K2;
-            ix->tc_k2n = K2n;
-            ix->tc_f16 = int(f16);
-            ix->tc_sigma = sigma;
-        }
-    }
+    const size_t bytes[4] = {size_t(ix->n) * K2 * sizeof(uint16_t), size_t(ix->n) * K2n * sizeof(uint16_t),
+                             nsplit == 3 ? size_t(ix->n) * K2n * sizeof(uint16_t) : 0, 0};
+    const snn_tc_operands *op = nullptr;
+    SNN_TRY(cached_operands(ix, kind, K2, K2n, sigma, bytes, s,
+                            [&](snn_tc_operands &e) -> snn_status {
+                                auto packer = nsplit == 2 ? k_tc_pack<2> : k_tc_pack<3>;
+                                SNN_LAUNCH(packer, unsigned(cdiv(cdiv(ix->n, 32) * 32, 256)), 256, 0, s)(
+                                    ix->xc, ix->dp, ix->hx, ix->nrm, nullptr, ix->n, d, K2, K2n, c, 0,
+                                    static_cast<uint16_t *>(e.part[0]), static_cast<uint16_t *>(e.part[1]),
+                                    static_cast<uint16_t *>(e.part[2]), pm);
+                                SNN_LAUNCH_CHECK();
+                                return SNN_OK;
+                            },
+                            &op));
     if (mma_flops_per_pair) {
         const int64_t ks_data = cdiv(d, 16), ks_all = f16 ? ks_data + 1 : cdiv(d + kExtra, 16);
         *mma_flops_per_pair = int64_t(2) * 16 * (ks_data * tc_npairs(nsplit) + (ks_all - ks_data));
@@ -1227,21 +1477,21 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
         SNN_LAUNCH(k_item_tiles, unsigned(cdiv(ng, 128)), 128, 0, s)(off2, ng, it2);
         SNN_LAUNCH_CHECK();
         TileSet ts2{lo2, hi2, off2, it2, ng};
-        return nsplit == 2 ? launch_tc<2, 32, 128, true, 1, 16, MT>(ix, sa, qp, K2, K2n, ts2, s, F)
-                           : launch_tc<3, 32, 128, true, 1, 16, MT>(ix, sa, qp, K2, K2n, ts2, s, 0);
+        return nsplit == 2 ? launch_tc<2, 32, 128, true, 1, 16, MT>(ix, *op, sa, qp, K2, K2n, ts2, s, F)
+                           : launch_tc<3, 32, 128, true, 1, 16, MT>(ix, *op, sa, qp, K2, K2n, ts2, s, 0);
     }
     // other low-d shapes: two CTAs per SM with a resident query tile, so that
     // one CTA's pipeline bubbles overlap the other's MMAs
     if (kp <= 32)
-        return nsplit == 2 ? launch_tc<2, 32, 128, true, 2, 32, 1>(ix, sa, qp, K2, K2n, ts1, s, F)
-                           : launch_tc<3, 32, 128, true, 2, 32, 1>(ix, sa, qp, K2, K2n, ts1, s, 0);
+        return nsplit == 2 ? launch_tc<2, 32, 128, true, 2, 32, 1>(ix, *op, sa, qp, K2, K2n, ts1, s, F)
+                           : launch_tc<3, 32, 128, true, 2, 32, 1>(ix, *op, sa, qp, K2, K2n, ts1, s, 0);
     if (kp <= 64)
-        return nsplit == 2 ? launch_tc<2, 64, 128, true, 1, 64, 1>(ix, sa, qp, K2, K2n, ts1, s, F)
-                           : launch_tc<3, 64, 128, true, 1, 64, 1>(ix, sa, qp, K2, K2n, ts1, s, 0);
+        return nsplit == 2 ? launch_tc<2, 64, 128, true, 1, 64, 1>(ix, *op, sa, qp, K2, K2n, ts1, s, F)
+                           : launch_tc<3, 64, 128, true, 1, 64, 1>(ix, *op, sa, qp, K2, K2n, ts1, s, 0);
     // high d: 128 x 256 accumulators (each query k-block feeds two 128-row
     // halves of the band chunk), 32-column k-blocks, four stages
-    return nsplit == 2 ? launch_tc<2, 32, 256, false, 1, 32, 1>(ix, sa, qp, K2, K2n, ts1, s, F)
-                       : launch_tc<3, 32, 256, false, 1, 32, 1>(ix, sa, qp, K2, K2n, ts1, s, 0);
+    return nsplit == 2 ? launch_tc<2, 32, 256, false, 1, 32, 1>(ix, *op, sa, qp, K2, K2n, ts1, s, F)
+                       : launch_tc<3, 32, 256, false, 1, 32, 1>(ix, *op, sa, qp, K2, K2n, ts1, s, 0);
 }
 
 }  // namespace snn

@@ -27,4 +27,9 @@ snn_status f8_score_launch(const snn_index *ix, const ScoreArgs &a, cudaStream_t
                            double e_data, Scratch &scr, int64_t *mma_flops_per_pair,
                            int *split_used = nullptr);
 
+// Releases the index's packed tensor-core operands (stream-ordered on s) and
+// empties its operand cache.  The caller holds the index's lock or owns the
+// index exclusively (release, update).
+void release_tc_operands(snn_index *ix, cudaStream_t s);
+
 }  // namespace snn

@@ -38,7 +38,8 @@ class StatsStruct(ctypes.Structure):
                 ("exact_fp64", ctypes.c_int64), ("mma_flops_per_pair", ctypes.c_int64),
                 ("ms_prep", ctypes.c_float), ("ms_score", ctypes.c_float),
                 ("ms_recheck", ctypes.c_float), ("ms_csr", ctypes.c_float),
-                ("precision_used", ctypes.c_int32), ("split_used", ctypes.c_int32)]
+                ("precision_used", ctypes.c_int32), ("split_used", ctypes.c_int32),
+                ("ms_score_kernel", ctypes.c_float), ("reserved", ctypes.c_int32)]
 
 
 class IPStatsStruct(ctypes.Structure):
@@ -614,7 +615,8 @@ def version() -> str:
     return lib.snn_version().decode()
 
 
-SNN_SPLIT_NONE, SNN_SPLIT_BF16X2, SNN_SPLIT_BF16X3, SNN_SPLIT_FP16X2, SNN_SPLIT_E4M3 = 0, 1, 2, 3, 10
+SNN_SPLIT_NONE, SNN_SPLIT_BF16X2, SNN_SPLIT_BF16X3, SNN_SPLIT_FP16X2, SNN_SPLIT_FP16X1, SNN_SPLIT_E4M3 = (
+    0, 1, 2, 3, 4, 10)
 SNN_FAULT_STALL_TC_PRODUCER = 1
 SNN_FAULT_SMALL_SURVIVOR_BUFFER = 2
 SNN_FAULT_DEVICE_ALLOC = 3

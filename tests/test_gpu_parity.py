@@ -473,11 +473,14 @@ def test_row_sort_key_widths(snn, monkeypatch, keys64):
     assert_csr_equal(got, ref, f"keys64={keys64}")
 
 
-@pytest.mark.parametrize("split", ["bf16x2", "bf16x3", "fp16x2"])
-@pytest.mark.parametrize("d,spread", [(12, 40.0), (16, 3.0), (40, 10.0), (100, 2.0)])
+@pytest.mark.parametrize("split", ["bf16x2", "bf16x3", "fp16x2", "fp16x1"])
+@pytest.mark.parametrize("d,spread", [(12, 40.0), (16, 3.0), (40, 10.0), (100, 2.0), (300, 6.0)])
 def test_tensor_core_shapes_forced_split(snn, monkeypatch, split, d, spread):
     """Every 16-bit operand split (SNN_TC_SPLIT) on every kernel shape,
-    whatever the automatic choice would be."""
+    whatever the automatic choice would be (one FP16 part exists for the
+    streamed shape only, d + 9 > 64)."""
+    if split == "fp16x1" and d + 9 <= 64:
+        pytest.skip("one FP16 part: streamed shape only")
     monkeypatch.setenv("SNN_TC_SPLIT", split)
     rng = np.random.default_rng(200 + d)
     centres = rng.uniform(-spread, spread, size=(6, d))
@@ -485,7 +488,8 @@ def test_tensor_core_shapes_forced_split(snn, monkeypatch, split, d, spread):
     P = (centres[lab] + rng.standard_normal((4000, d))).astype(np.float32)
     Q = (centres[rng.integers(0, 6, size=500)] + rng.standard_normal((500, d))).astype(np.float32)
     R = float(np.sqrt(2.0 * d) * 0.8)
-    want = {"bf16x2": snn.SNN_SPLIT_BF16X2, "bf16x3": snn.SNN_SPLIT_BF16X3, "fp16x2": snn.SNN_SPLIT_FP16X2}[split]
+    want = {"bf16x2": snn.SNN_SPLIT_BF16X2, "bf16x3": snn.SNN_SPLIT_BF16X3, "fp16x2": snn.SNN_SPLIT_FP16X2,
+            "fp16x1": snn.SNN_SPLIT_FP16X1}[split]
     for q in (None, Q):
         got = _run(snn, P, q, R, "bf16")
         assert got.stats["split_used"] == want
@@ -516,3 +520,76 @@ def test_fp16_parts_scaling_and_small_values(snn, monkeypatch, d):
     ref = oracle.brute_radius(P, None, R)
     assert ref.nnz == 3000 * 3000
     assert_csr_equal(got, ref, f"d={d} large R")
+
+
+@pytest.mark.parametrize("d", [64, 100, 784])
+def test_fp16_single_part_scaling_and_small_values(snn, monkeypatch, d):
+    """One FP16 part per row with its own power-of-two scale and the per-pair
+    bound from the exact residual norms: data far above and far below the
+    FP16 range, columns thirty binades below the others (rounded to zero and
+    carried by the residual), rows 4096x smaller than the rest, a radius far
+    above the norms (every pair inside), and out-of-sample queries of another
+    scale; every case equals the oracle bit for bit."""
+    monkeypatch.setenv("SNN_TC_SPLIT", "fp16x1")
+    rng = np.random.default_rng(400 + d)
+    base = rng.standard_normal((2500, d))
+    base[:, ::3] *= 2.0 ** -30
+    base[::7] *= 2.0 ** -12
+    for scale in (2.0 ** 12, 1.0, 2.0 ** -40):
+        P = (base * scale).astype(np.float32)
+        Q = (rng.standard_normal((300, d)) * scale * 1.5).astype(np.float32)
+        R = float(np.quantile(np.linalg.norm(P[:300, None, :] - P[None, :300, :], axis=2), 0.02))
+        for q in (None, Q):
+            got = _run(snn, P, q, R, "bf16")
+            assert got.stats["split_used"] == snn.SNN_SPLIT_FP16X1, (d, scale)
+            assert_csr_equal(got, oracle.brute_radius(P, q, R), f"d={d} scale={scale}")
+    P = base.astype(np.float32)
+    R = float(50.0 * np.sqrt(d))
+    got = _run(snn, P, None, R, "bf16")
+    ref = oracle.brute_radius(P, None, R)
+    assert ref.nnz == 2500 * 2500
+    assert_csr_equal(got, ref, f"d={d} large R")
+
+
+def test_lowrank_img_single_part_default(snn):
+    """On the image-like data the automatic choice is one FP16 part per row
+    (one MMA per k step); the set equals the oracle's and the survivors stay
+    within a small multiple of the neighbour pairs."""
+    w = wl.lowrank_img(n=6007, sub=2000)
+    got = _run(snn, w.P, None, w.R, "bf16")
+    assert got.stats["split_used"] == snn.SNN_SPLIT_FP16X1
+    assert got.stats["mma_flops_per_pair"] == 2 * 16 * (784 // 16 + 1)
+    assert_csr_equal(got, oracle.brute_radius(w.P, None, w.R), "lowrank_img fp16x1")
+    directed = 2 * got.stats["survivors"] - w.n
+    assert directed <= 4 * got.nnz
+
+
+@pytest.mark.parametrize("split", ["fp16x2", "fp16x1"])
+def test_operand_cache_two_streams(snn, monkeypatch, split):
+    """Queries of very different norm scales on one index from two streams,
+    interleaved: the packed operands of the index are built once per kind
+    and never replaced while queries may read them (the second stream waits
+    for the packing of the first), and queries whose scaled coordinates would
+    leave the FP16 range take BF16 parts for their call.  Every result
+    equals the oracle."""
+    monkeypatch.setenv("SNN_TC_SPLIT", split)
+    d = 16 if split == "fp16x2" else 100
+    rng = np.random.default_rng(501)
+    P = rng.standard_normal((6000, d)).astype(np.float32)
+    ix = snn.Index(_dev(P))
+    Qs = [(rng.standard_normal((700, d)) * sc).astype(np.float32) for sc in (1.0, 40.0, 0.25)]
+    Rs = [2.5, 60.0, 0.8]
+    Qd = [_dev(Q) for Q in Qs]
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = []
+    for rep in range(2):
+        for k, R in enumerate(Rs):
+            st = streams[(k + rep) % 2]
+            outs.append((k, ix.query(Qd[k], R, precision="bf16", stream=st, stats=True)))
+    torch.cuda.synchronize()
+    for k, got in outs:
+        assert_csr_equal(got, oracle.brute_radius(P, Qs[k], Rs[k]), f"{split} set {k}")
+    if split == "fp16x2":
+        used = {k: got.stats["split_used"] for k, got in outs}
+        assert used[0] == snn.SNN_SPLIT_FP16X2 and used[1] == snn.SNN_SPLIT_BF16X2

@@ -223,3 +223,32 @@ def test_table2_d3_ratios(golden_dir):
                 continue
             got = _ratio_excl_self(P, float(Rs))
             assert abs(got - ref) <= 0.12 * ref, (d, Rs, got, ref)
+
+
+def test_radius_rows_equals_brute_force():
+    """The row-sampled oracle (a float64 product discards pairs certainly
+    outside, the FP64 definition decides the rest) returns exactly the rows
+    of the full brute force: random clusters, exact ties on an integer grid
+    (S == R^2 on the boundary), duplicates, negative and large coordinates,
+    and out-of-sample queries."""
+    rng = np.random.default_rng(91)
+    cases = []
+    P = (rng.standard_normal((3000, 20)) + 50.0 * rng.standard_normal((5, 20))[rng.integers(0, 5, 3000)])
+    cases.append((P.astype(np.float32), None, 4.5))
+    g = np.stack(np.meshgrid(np.arange(12), np.arange(12), np.arange(12)), -1).reshape(-1, 3) - 6
+    cases.append((g.astype(np.float32), None, 2.0))
+    dup = np.repeat(rng.standard_normal((40, 7)), 9, axis=0).astype(np.float32)
+    cases.append((dup, None, 0.0))
+    P2 = (rng.standard_normal((2000, 64)) * 1e3).astype(np.float32)
+    Q2 = (rng.standard_normal((300, 64)) * 1e3).astype(np.float32)
+    cases.append((P2, Q2, float(np.sqrt(2 * 64) * 1e3 * 0.9)))
+    for P, Q, R in cases:
+        m = P.shape[0] if Q is None else Q.shape[0]
+        rows = rng.choice(m, size=min(m, 257), replace=False)
+        got = oracle.radius_rows(P, Q, rows, R)
+        ref = oracle.brute_radius(P, (P if Q is None else Q)[rows], R)
+        assert np.array_equal(got.offsets, ref.offsets)
+        assert np.array_equal(got.ids, ref.ids)
+        assert np.array_equal(got.dist2.view(np.uint32), ref.dist2.view(np.uint32))
+    with pytest.raises(ValueError):
+        oracle.radius_rows(P2, None, [0], 1.0, margin=1e-16)
