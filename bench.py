@@ -291,6 +291,330 @@ def cpu_snn_sample(w, budget_s=8.0, seed=11, gpu_csr=None):
     return out
 
 
+# ---------------------------------------------------------------- per config
+EPI_OPS_PER_PAIR = 5   # the per-pair epilogue of the low-d scorer (TMEM load, FMA, two compares, ballot)
+ALU_ISSUE_TOPS = 152 * 128 * 2.070e9 / 1e12   # FP32 lanes x max clock: operations per second
+
+
+def scorer_roofline(st, d, kernel_ms, precision_used, peaks, src):
+    """Roofline of the scoring kernel of one query call (kernel time from the
+    CUDA events around its launch).  High d: the tensor pipe (2d flop per
+    scored pair).  d <= 32: the per-pair epilogue on the FP32 pipe, as the
+    scoring model for low d says (the MMA is one or two k steps), with the
+    tensor fraction beside it.  The FP32 scorer: 2d flop per pair on the FP32
+    pipe."""
+    pairs = st["band_pairs"]
+    t = kernel_ms / 1e3
+    flops = 2.0 * d * pairs
+    peak_bf16 = float(peaks["bf16_tflops_sustained"])
+    if precision_used == 0:
+        ach = flops / t / 1e12
+        return {"kernel": "k_score_fp32_single" if d <= 16 else "k_score_fp32_multi", "bound": "alu",
+                "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
+                "traffic": None, "score_ms": kernel_ms,
+                "algorithmic": "2d flop per scored pair (Eq. (4))",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)"}
+    f8 = precision_used == 2
+    peak_t = peak_bf16 * (2.0 if f8 else 1.0)
+    ach_t = flops / t / 1e12
+    tensor = {"kernel": "k_score_tc", "bound": "tensor", "achieved": ach_t, "peak": peak_t, "unit": "TFLOP/s",
+              "frac": ach_t / peak_t, "traffic": None, "score_ms": kernel_ms,
+              "algorithmic": "2d flop per scored pair (Eq. (4)); a symmetric self-join scores each "
+                             "unordered pair once",
+              "executed_frac": st["mma_flops_per_pair"] * pairs / t / 1e12 / peak_t,
+              "mma_flops_per_pair": st["mma_flops_per_pair"],
+              "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained x 2 (e4m3 nominal ratio; %s)" % src
+                              if f8 else "MEASURED_PEAKS.json bf16_tflops_sustained (%s)" % src)}
+    if d > 32:
+        return tensor
+    ach = EPI_OPS_PER_PAIR * pairs / t / 1e12
+    return {"kernel": "k_score_tc", "bound": "alu", "achieved": ach, "peak": ALU_ISSUE_TOPS,
+            "unit": "Tops/s", "frac": ach / ALU_ISSUE_TOPS, "traffic": None, "score_ms": kernel_ms,
+            "algorithmic": f"{EPI_OPS_PER_PAIR} FP32-pipe operations per scored pair (the low-d "
+                           "epilogue: TMEM load, FMA, two compares, ballot)",
+            "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (derived)",
+            "tensor": {k: tensor[k] for k in ("achieved", "peak", "frac", "executed_frac", "unit")}}
+
+
+def _timed_steps(fn, steps, warmup, flush, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ts, last = [], None
+    with no_gc():
+        for _ in range(steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            last = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+    return ts, last
+
+
+def _compare_rows(got_host, ref, rows):
+    """Rows of a GPU CSR (host arrays) against the oracle's rows: sets must be
+    identical; returns (rows with different sets, pairs, max rel dist2 error)."""
+    off, ids, d2 = got_host
+    mism, pairs, max_rel = 0, 0, 0.0
+    for t, r in enumerate(rows):
+        a, b = ref.offsets[t], ref.offsets[t + 1]
+        ga, gb = off[r], off[r + 1]
+        if gb - ga != b - a or not np.array_equal(ids[ga:gb], ref.ids[a:b]):
+            mism += 1
+            continue
+        s_ref = ref.dist2[a:b].astype(np.float64)
+        s_gpu = d2[ga:gb].astype(np.float64)
+        rel = np.abs(s_gpu - s_ref) / np.maximum(s_ref, 1e-300)
+        rel[(s_ref == 0) & (s_gpu == 0)] = 0.0
+        if rel.size:
+            max_rel = max(max_rel, float(rel.max()))
+        pairs += b - a
+    return mism, pairs, max_rel
+
+
+def _oracle_rows_check(w, got_host, nrows, seed):
+    """The oracle's neighbour lists of nrows random query rows (all rows when
+    there are fewer), by oracle.radius_rows, compared with the GPU CSR."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    rows = np.arange(w.m) if w.m <= nrows else np.sort(rng.choice(w.m, nrows, replace=False))
+    t0 = time.perf_counter()
+    ref = oracle.radius_rows(w.P, w.Q, rows, w.R)
+    dt = time.perf_counter() - t0
+    mism, pairs, max_rel = _compare_rows(got_host, ref, rows)
+    return {"rows": int(len(rows)), "pairs": int(pairs), "rows_with_different_sets": int(mism),
+            "max_rel_dist2_err": max_rel, "oracle": "oracle.radius_rows (FP64 definition on every pair "
+            "within a rigorous margin of R^2 of a float64 product)", "oracle_s": dt}
+
+
+def _oracle_rate(w, budget_s, seed):
+    """The FP64 brute-force oracle timed on a bounded query sample."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(w.m)
+    Qall = w.P if w.Q is None else w.Q
+    done, used, size = 0, 0.0, 4
+    while used < budget_s and done < w.m:
+        rows = order[done:done + size]
+        t0 = time.perf_counter()
+        oracle.brute_radius(w.P, Qall[rows], w.R)
+        used += time.perf_counter() - t0
+        done += len(rows)
+        size *= 2
+    return {"value": done / used, "unit": "queries/s", "cores": oracle.oracle_threads(), "kind": "oracle",
+            "sample": f"{done} random queries of the {w.m} against all {w.n} points (FP64 brute force, "
+                      f"{used:.1f} s)"}
+
+
+def per_config_query(args, w, label, snn, torch, flush, stream, variants=("fp32",), steps=5, warmup=3):
+    """One query workload: index build + exact query per step, the 16-bit
+    tensor-core path; the other precisions beside it at identical output."""
+    peaks, src = load_peaks()
+    X = torch.from_numpy(w.P).cuda()
+    Qd = None if w.Q is None else torch.from_numpy(w.Q).cuda()
+
+    def step(prec):
+        def f():
+            ix = snn.Index(X)
+            return ix.query(Qd, w.R, precision=prec, stats=True)
+        return f
+    ts, out = _timed_steps(step("bf16"), steps, warmup, flush, stream)
+    st = out.stats
+    ms = float(np.median(ts))
+    # index build alone, same timing rules
+    tsi, _ = _timed_steps(lambda: snn.Index(X), steps, 2, flush, stream)
+    directed = 2 * st["survivors"] - w.m if w.Q is None else st["survivors"]
+    res = {"workload": label, "n": w.n, "d": w.d, "queries": w.m, "R": w.R,
+           "value": w.m / (ms / 1e3), "unit": "queries/s", "ms_per_step": ms, "steps": steps,
+           "index_build_ms": float(np.median(tsi)),
+           "candidate_pairs_per_s": st["candidates"] / (ms / 1e3),
+           "pairs_scored_per_s": st["band_pairs"] / (ms / 1e3),
+           "tc_split": split_name(st["split_used"]), "dtype": split_dtype(st["split_used"]),
+           "nnz": st["nnz"], "candidates": st["candidates"], "band_pairs": st["band_pairs"],
+           "survivors": st["survivors"], "exact_fp64": st["exact_fp64"],
+           "recheck_fraction": (directed - st["nnz"]) / max(1, st["candidates"]),
+           "phase_ms": {k: st[k] for k in ("ms_prep", "ms_score", "ms_score_kernel", "ms_recheck", "ms_csr")},
+           "roofline": scorer_roofline(st, w.d, st["ms_score_kernel"], st["precision_used"], peaks, src)}
+    others = {}
+    for prec in variants:
+        tso, o = _timed_steps(step(prec), 3, 1, flush, stream)
+        so = o.stats
+        same = (torch.equal(o.offsets, out.offsets) and torch.equal(o.indices, out.indices)
+                and torch.equal(o.dist2.view(torch.int32), out.dist2.view(torch.int32)))
+        od = 2 * so["survivors"] - w.m if w.Q is None else so["survivors"]
+        others[prec] = {"value": w.m / (np.median(tso) / 1e3), "ms_per_step": float(np.median(tso)),
+                        "score_kernel_ms": so["ms_score_kernel"], "recheck_ms": so["ms_recheck"],
+                        "precision_used": ["fp32", "bf16", "fp8"][so["precision_used"]],
+                        "tc_split": split_name(so["split_used"]), "survivors": so["survivors"],
+                        "recheck_fraction": (od - so["nnz"]) / max(1, so["candidates"]),
+                        "roofline": scorer_roofline(so, w.d, so["ms_score_kernel"], so["precision_used"],
+                                                    peaks, src),
+                        "csr_identical": bool(same)}
+        del o
+    res["other_precisions"] = others
+    if "fp32" in others:
+        res["speedup_vs_fp32_path"] = res["value"] / others["fp32"]["value"]
+    if args.cpu_baseline:
+        host = (out.offsets.cpu().numpy(), out.indices.cpu().numpy(), out.dist2.cpu().numpy())
+        res["parity"] = _oracle_rows_check(w, host, args.parity_rows, seed=31)
+        res["max_rel_dist2_err"] = res["parity"]["max_rel_dist2_err"]
+        res["cpu_baseline"] = _oracle_rate(w, args.cfg_budget, seed=32)
+    del out, X, Qd
+    torch.cuda.synchronize()
+    return res
+
+
+def per_config_ragged(args, snn, torch, flush, stream, steps=5, warmup=2):
+    """Ragged batch: the batched index build of every set plus one run of the
+    batched query plan per step; one index build and one query call per set
+    beside it; the tuned plan's graph-replayed query phase."""
+    from paper_2212_07679_gb300 import workloads as wl
+    t0 = time.perf_counter()
+    sets = wl.ragged_batch()
+    gen_s = time.perf_counter() - t0
+    Xs = [torch.from_numpy(s.P).cuda() for s in sets]
+    Qs = [torch.from_numpy(s.Q).cuda() for s in sets]
+    Rs = [s.R for s in sets]
+    M = sum(q.shape[0] for q in Qs)
+    N = sum(x.shape[0] for x in Xs)
+
+    def make_plan(idx):
+        plan = snn.BatchPlan(idx, [q.shape[0] for q in Qs], Rs, survivor_capacity=64 * M + (1 << 20),
+                             nnz_capacity=64 * M + (1 << 20))
+        for t, q in enumerate(Qs):
+            plan.queries(t).copy_(q)
+        return plan
+
+    def step():
+        idx = snn.build_batch(Xs)
+        plan = make_plan(idx)
+        plan.run()
+        return plan.result(copy=False)
+
+    ts, _ = _timed_steps(step, steps, warmup, flush, stream)
+    tsl, _ = _timed_steps(lambda: [snn.Index(x).query(q, r) for x, q, r in zip(Xs, Qs, Rs)], 3, 1, flush,
+                          stream)
+    idx = snn.build_batch(Xs)
+    plan = make_plan(idx)
+    cpi, ctas, _ = plan.tune()
+
+    def graph_query():
+        plan.launch_graph()
+        return plan.result(copy=False)
+    tsg, _ = _timed_steps(graph_query, steps, 2, flush, stream)
+    plan.launch_graph()
+    got = plan.result()
+    ms = float(np.median(ts))
+    res = {"workload": "ragged_batch (256 mixtures, batched build + one batched query)", "sets": len(sets),
+           "points": N, "queries": M, "value": M / (ms / 1e3), "unit": "queries/s", "ms_per_step": ms,
+           "steps": steps, "per_set_calls": {"ms_per_step": float(np.median(tsl)),
+                                            "value": M / (np.median(tsl) / 1e3)},
+           "query_phase_graph_ms": float(np.median(tsg)),
+           "tuned": {"chunks_per_item": cpi, "ctas_per_sm": ctas}, "generation_s": gen_s}
+    if args.cpu_baseline:
+        import oracle
+        rng = np.random.default_rng(33)
+        mism, pairs, max_rel, rows_done = 0, 0, 0.0, 0
+        per_set = max(1, args.parity_rows // len(sets))
+        t0 = time.perf_counter()
+        for t, s in enumerate(sets):
+            rows = np.sort(rng.choice(s.m, min(per_set, s.m), replace=False))
+            ref = oracle.radius_rows(s.P, s.Q, rows, s.R)
+            g = got[t]
+            host = (g.offsets.cpu().numpy(), g.indices.cpu().numpy(), g.dist2.cpu().numpy())
+            a, b, c = _compare_rows(host, ref, rows)
+            mism += a
+            pairs += b
+            max_rel = max(max_rel, c)
+            rows_done += len(rows)
+        res["parity"] = {"rows": rows_done, "pairs": int(pairs), "rows_with_different_sets": int(mism),
+                         "max_rel_dist2_err": max_rel, "oracle_s": time.perf_counter() - t0,
+                         "oracle": "oracle.radius_rows on random rows of every set"}
+        res["max_rel_dist2_err"] = max_rel
+    plan.close()
+    del idx, Xs, Qs, got
+    torch.cuda.synchronize()
+    return res
+
+
+def per_config_dbscan(args, snn, torch, flush, stream, steps=5, warmup=3):
+    """DBSCAN on the 5e5-point 3-d particle set (eps 0.4, minPts 10): index
+    build, exact self-join, core flags and union-find labels per step."""
+    import oracle  # noqa: F401  (parity below only)
+    from paper_2212_07679_gb300 import workloads as wl
+    peaks, src = load_peaks()
+    w = wl.blobs3d()
+    X = torch.from_numpy(w.P).cuda()
+    eps, min_pts = w.R, w.extra["min_pts"]
+    ts, (labels, core) = _timed_steps(lambda: snn.dbscan(X, eps, min_pts, precision="bf16"), steps, warmup,
+                                      flush, stream)
+    ms = float(np.median(ts))
+    # the self-join inside the step, once more with statistics
+    out = snn.Index(X).query(None, eps, precision="bf16", stats=True)
+    st = out.stats
+    lab = labels.cpu().numpy()
+    cr = core.cpu().numpy().astype(bool)
+    res = {"workload": "blobs3d DBSCAN (self-join + core flags + union-find)", "n": w.n, "d": w.d,
+           "eps": eps, "min_pts": min_pts, "value": w.n / (ms / 1e3), "unit": "points/s", "ms_per_step": ms,
+           "steps": steps, "clusters": int(len(np.unique(lab[lab >= 0]))), "core_points": int(cr.sum()),
+           "self_join": {"nnz": st["nnz"], "candidates": st["candidates"], "band_pairs": st["band_pairs"],
+                         "survivors": st["survivors"],
+                         "recheck_fraction": (2 * st["survivors"] - w.n - st["nnz"]) / max(1, st["candidates"]),
+                         "tc_split": split_name(st["split_used"]),
+                         "phase_ms": {k: st[k] for k in ("ms_prep", "ms_score", "ms_score_kernel", "ms_recheck",
+                                                         "ms_csr")}},
+           "roofline": scorer_roofline(st, w.d, st["ms_score_kernel"], st["precision_used"], peaks, src)}
+    if args.cpu_baseline:
+        import oracle
+        rng = np.random.default_rng(34)
+        rows = np.sort(rng.choice(w.n, args.parity_rows, replace=False))
+        t0 = time.perf_counter()
+        ref = oracle.radius_rows(w.P, None, rows, eps)
+        host = (out.offsets.cpu().numpy(), out.indices.cpu().numpy(), out.dist2.cpu().numpy())
+        mism, pairs, max_rel = _compare_rows(host, ref, rows)
+        bad_core = bad_label = 0
+        for t, r in enumerate(rows):
+            nb = ref.row(t)[0]
+            if cr[r] != (len(nb) >= min_pts):
+                bad_core += 1
+                continue
+            core_nb = nb[cr[nb]]
+            if cr[r]:
+                bad_label += int(not np.all(lab[core_nb] == lab[r]))
+            elif len(core_nb):
+                bad_label += int(lab[r] != lab[core_nb.min()])
+            else:
+                bad_label += int(lab[r] != -1)
+        res["parity"] = {"rows": int(len(rows)), "pairs": int(pairs), "rows_with_different_sets": int(mism),
+                         "max_rel_dist2_err": max_rel, "rows_with_wrong_core_flag": int(bad_core),
+                         "rows_with_wrong_label": int(bad_label), "oracle_s": time.perf_counter() - t0,
+                         "oracle": "oracle.radius_rows rows; core flag = |N| >= minPts; labels checked "
+                                   "against the rows' core neighbours"}
+        res["max_rel_dist2_err"] = max_rel
+        res["cpu_baseline"] = _oracle_rate(w, args.cfg_budget, seed=35)
+    del X, out
+    torch.cuda.synchronize()
+    return res
+
+
+def per_config_block(args, snn, torch, flush, stream):
+    from paper_2212_07679_gb300 import workloads as wl
+    out = {}
+    t0 = time.perf_counter()
+    out["cfg1_gmm_iso"] = per_config_query(args, wl.gmm_iso(), "gmm_iso: 500 queries drawn from 2,000 points",
+                                           snn, torch, flush, stream)
+    out["cfg3_lowrank_img"] = per_config_query(args, wl.lowrank_img(), "lowrank_img self-join", snn, torch,
+                                               flush, stream, variants=("fp32", "fp8"))
+    out["cfg5_blobs3d_dbscan"] = per_config_dbscan(args, snn, torch, flush, stream)
+    out["cfg4_ragged_batch"] = per_config_ragged(args, snn, torch, flush, stream)
+    out["wall_s"] = time.perf_counter() - t0
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -305,7 +629,10 @@ def run_reference(args):
     line = {"impl": "reference", "metric": "exact radius queries/s & pairs scored/s: BF16+FP64 recheck vs FP32, % roofline",
             "metric_detail": "exact radius queries/s of the FP64 brute-force oracle on the host cores", "value": qps,
             "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * w.m / qps, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * w.m / qps, "extrapolated_from_sample": True,
+            "ms_per_step_note": ("each step times the oracle on a bounded query sample; ms_per_step is the "
+                                 "time all queries would take at the sampled rate"),
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args, w),
             "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": steps[-1]["cores"],
@@ -463,11 +790,11 @@ def run_ours(args):
             t0 = time.perf_counter()
             e2e_step(streams[0], hbufs[0], True)
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    # three pipelined passes of n_pipe steps each; the median pass is
-    # reported (one pass can catch a host-side stall), all three are listed
+    # five pipelined passes of n_pipe steps each; the median pass is
+    # reported (one pass can catch a host-side stall), all five are listed
     n_pipe = max(4, min(args.steps, 8))
     pipe_passes = []
-    for _ in range(3):
+    for _ in range(5):
         with no_gc():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -483,39 +810,21 @@ def run_ours(args):
     # executed: pairs the kernel actually scored (the symmetric self-join
     # scores each unordered pair once); effective: the candidate pairs of
     # the per-query candidate ranges of Algorithm 2 that this replaces
-    flops = 2.0 * w.d * st["band_pairs"]
-    achieved = flops / (sm / 1e3) / 1e12
     effective = 2.0 * w.d * st["candidates"] / (sm / 1e3) / 1e12
     directed_surv = 2 * st["survivors"] - w.m if w.Q is None else st["survivors"]
-    if args.precision in ("bf16", "fp8"):
-        # tensor-bound scoring, timed inside a multi-kernel step: sustained
-        # peak (e4m3: the BF16 figure x 2, the nominal dense ratio)
-        f8 = args.precision == "fp8" and st["precision_used"] == 2
-        peak = float(peaks["bf16_tflops_sustained"]) * (2.0 if f8 else 1.0)
-        pipe = st["mma_flops_per_pair"] * st["band_pairs"] / (sm / 1e3) / 1e12
+    # the scoring kernel's roofline (kernel time from the events around its
+    # launch): the tensor pipe at high d, the per-pair epilogue on the FP32
+    # pipe at d <= 32 with the tensor fraction beside it
+    roofline = scorer_roofline(st, w.d, sm, st["precision_used"], peaks, src)
+    roofline["effective_tflops"] = effective
+    roofline["score_ms_source"] = "CUDA events around the scoring launch alone (stats.ms_score_kernel)"
+    if st["precision_used"] != 0:
         used = ["fp32", "bf16", "fp8"][st["precision_used"]]
         traffic = scorer_traffic(w.name, w.n, used) if w.Q is None else None
-        roofline = {"kernel": "k_score_tc", "bound": "tensor", "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                    "traffic_source": (f"{SCORER_TRAFFIC['profile']} (dram__bytes_read.sum + "
-                                       "dram__bytes_write.sum of one full-size launch)") if traffic else
-                                      "no full-size capture of this kernel build and workload",
-                    "peak_source": (f"MEASURED_PEAKS.json bf16_tflops_sustained x 2 (e4m3 nominal ratio; {src})"
-                                    if f8 else f"MEASURED_PEAKS.json bf16_tflops_sustained ({src})"),
-                    "algorithmic": "2d flop per scored pair (Eq. (4)); the symmetric self-join "
-                                   "scores each unordered pair once",
-                    "effective_tflops": effective, "score_ms": sm,
-                    "score_ms_source": "CUDA events around the scoring launch alone (stats.ms_score_kernel)",
-                    "executed_mma_tflops": pipe, "executed_frac": pipe / peak,
-                    "mma_flops_per_pair": st["mma_flops_per_pair"]}
-    else:
-        roofline = {"kernel": "k_score_fp32_single" if w.d <= 16 else "k_score_fp32_multi",
-                    "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                    "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)",
-                    "algorithmic": "2d flop per scored pair (Eq. (4)); the symmetric self-join "
-                                   "scores each unordered pair once",
-                    "effective_tflops": effective, "score_ms": sm}
+        roofline["traffic"] = traffic
+        roofline["traffic_source"] = (f"{SCORER_TRAFFIC['profile']} (dram__bytes_read.sum + "
+                                      "dram__bytes_write.sum of one full-size launch)") if traffic else \
+            "no full-size capture of this kernel build and workload"
     line = {
         "metric": "exact radius queries/s & pairs scored/s: BF16+FP64 recheck vs FP32, % roofline",
         "metric_detail": ("exact radius queries/s (16-bit or e4m3 tensor-core rejection, compensated FP32 "
@@ -544,10 +853,14 @@ def run_ours(args):
         "e2e": {"value": w.m / (e2e_pipe_ms / 1e3), "unit": "queries/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": e2e_pipe_ms,
-                "mode": f"{n_pipe} steps alternating between two streams, median of 3 passes",
+                "mode": f"{n_pipe} steps alternating between two streams, median of 5 passes",
                 "pass_ms_per_step": pipe_passes,
                 "serial": {"value": w.m / (np.median(e2e_ms) / 1e3), "ms_per_step": float(np.median(e2e_ms))}},
     }
+    if args.per_config and args.workload == "gmm_aniso" and world == 1:
+        # the other configurations of the benchmark, measured after the
+        # headline's timed region (rank 0 only)
+        line["per_config"] = per_config_block(args, snn, torch, flush, stream)
     if rank == 0:
         if args.cpu_baseline:
             csr_h = (last_out.offsets.cpu().numpy(), last_out.indices.cpu().numpy(),
@@ -983,17 +1296,18 @@ def run_peaks(args):
     lane count x clock); the rooflines themselves keep the denominators of
     MEASURED_PEAKS.json."""
     import torch
-    from paper_2212_07679_gb300 import snn
+    import bench_probes
+    from paper_2212_07679_gb300 import snn  # noqa: F401
     torch.cuda.set_device(0)
     iters = {"bf16_mma": 1 << 17, "e4m3_mma": 1 << 17, "fp32_fma": 1 << 18, "fp64_fma": 1 << 12}
     for k, it in iters.items():
         for _ in range(max(1, args.warmup)):
-            snn.measure_peak(k, it)
+            bench_probes.measure_peak(k, it)
     clk = ClockSampler(0)
     clk.start()
     res = {}
     for k, it in iters.items():
-        res[k] = max(snn.measure_peak(k, it) for _ in range(max(1, args.steps))) / 1e12
+        res[k] = max(bench_probes.measure_peak(k, it) for _ in range(max(1, args.steps))) / 1e12
     clocks = clk.stop()
     peaks, src = load_peaks()
     line = {"metric": "probe_peak_tflops", "value": res["e4m3_mma"], "unit": "TFLOP/s", "n_gpus": 1,
@@ -1018,6 +1332,12 @@ def main():
                     help="skip timing the other precision beside the headline one")
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-per-config", dest="per_config", action="store_false",
+                    help="skip the other configurations (default run: all of them after the headline)")
+    ap.add_argument("--parity-rows", type=int, default=2000,
+                    help="oracle rows sampled per configuration for the parity check")
+    ap.add_argument("--cfg-budget", type=float, default=3.0,
+                    help="seconds of oracle timing per configuration")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -7,6 +7,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "peaks.h"
 #include "tc_common.cuh"
 
 namespace snn {

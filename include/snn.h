@@ -433,27 +433,28 @@ const char *snn_version(void);
 
 /* Allocation-free sort of scores (the paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory).  Some
- * callers cannot call cudaMalloc or use a memory pool: code that runs while a
- * stream is being captured into a CUDA graph under an allocation ban, a
- * process whose device memory budget is fixed by someone else, or a latency-
- * critical loop that must never enter the allocator.  This call sorts n FP32
- * values ascending with a stable LSD radix sort -- the same sort and the same
- * result as the index build's sort of alpha (Algorithm 1) -- using
- * only a static device array compiled into the library (about 9 MB, held by
- * every GPU that loads the library until the process exits).
+ * callers cannot call cudaMalloc or use a memory pool: a process whose device
+ * memory budget is fixed by someone else (every byte already handed out), or
+ * a latency-critical loop that must never enter the allocator.  This call
+ * sorts n FP32 values ascending with a stable LSD radix sort -- the same
+ * kernels and the same result as the index build's sort of alpha (Algorithm
+ * 1) -- using only a static device array compiled into the library (about
+ * 9 MB, held by every GPU that loads the library until the process exits).
  *  alpha         device, n FP32 values (NaN/Inf rejected); may equal
  *                alpha_sorted (in place).
  *  n             0 <= n <= SNN_NOALLOC_SORT_MAX_N; larger n returns
  *                SNN_EINVAL with a message naming the limit.
- *  alpha_sorted  device, n FP32 outputs, ascending (caller-allocated).
+ *  alpha_sorted  device, n FP32 outputs, ascending in the order of the
+ *                values' order-preserving 32-bit keys (so -0.0 sorts before
+ *                +0.0); caller-allocated.
  *  order         device, n int32 outputs: order[r] is the input position of
- *                alpha_sorted[r]; equal values keep their input order.
- * The call allocates nothing and synchronises `stream` once (to check the
- * input for NaN/Inf).  The first call on a device looks up the device address
- * of the static array (make that first call before any stream capture).  All
- * calls share the one array and it keeps the last call's contents, so calls
- * whose device work overlaps (different streams, or different host threads on
- * one device) race: serialise them. */
+ *                alpha_sorted[r]; equal keys keep their input order.
+ * The call allocates nothing.  It copies a NaN/Inf flag to the host and
+ * synchronises `stream` once, before sorting.  The first call on a device
+ * looks up the device address of the static array (make that first call
+ * before any stream capture).  All calls share the one array and it keeps
+ * the last call's contents, so calls whose device work overlaps (different
+ * streams, or different host threads on one device) race: serialise them. */
 snn_status snn_sort_scores_noalloc(const float *alpha, int64_t n, float *alpha_sorted,
                                    int32_t *order, void *stream);
 
@@ -475,23 +476,6 @@ snn_status snn_sort_scores_noalloc(const float *alpha, int64_t n, float *alpha_s
 #define SNN_FAULT_SMALL_SURVIVOR_BUFFER 2
 #define SNN_FAULT_DEVICE_ALLOC 3
 snn_status snn_test_inject(int32_t fault);
-
-/* Throughput probe for roofline denominators (the paper has no counterpart).
- * Runs one kernel that keeps one arithmetic unit of every SM busy and returns
- * its rate in flop/s, timed with CUDA events on `stream`:
- *  kind 0  tcgen05.mma kind::f16, BF16 operands, FP32 accumulation,
- *          M = 128, N = 256, K = 16 per instruction, one CTA per SM;
- *  kind 1  tcgen05.mma kind::f8f6f4, e4m3 operands, same shape with K = 32;
- *  kind 2  FP32 fused multiply-add on every lane (8 warps x 8 CTAs per SM);
- *  kind 3  FP64 fused multiply-add, same launch.
- * An MMA of M x N x K counts 2MNK flop and an FMA 2.  `iters` (>= 64) is the
- * number of instructions per issuing thread (MMAs are issued in groups of 64,
- * so kinds 0 and 1 round it down to a multiple of 64).  The operands are
- * fixed finite values; the results are discarded.  Synchronises `stream`.
- * Errors: SNN_EINVAL for kind outside 0..3, iters < 64 or a NULL output;
- * SNN_ETIMEOUT if a bounded MMA completion wait (about 2 s) expired;
- * SNN_ENOMEM / SNN_ECUDA on device failures. */
-snn_status snn_measure_peak(int32_t kind, int64_t iters, void *stream, double *flops_per_s);
 
 /* Number of CUDA kernels this library has launched in this process so far
  * (diagnostics: the difference around a call is that call's launch count). */

@@ -173,6 +173,9 @@ def radius_rows(P: np.ndarray, Q: np.ndarray | None, rows: np.ndarray, R: float,
     P = _as_f32(P)
     Qs = _as_f32((P if Q is None else _as_f32(Q))[np.asarray(rows, dtype=np.int64)])
     n, d = P.shape
+    if d < 64:
+        # low d: the product costs more than the definition itself
+        return brute_radius(P, Qs, R)
     u = 2.0 ** -53
     if not margin >= 4.0 * (d + 2) * u / (1.0 - (d + 2) * u):
         raise ValueError("margin below the rounding bound of the matrix product")
@@ -198,6 +201,79 @@ def radius_rows(P: np.ndarray, Q: np.ndarray | None, rows: np.ndarray, R: float,
     offsets = np.zeros(m + 1, dtype=np.int64)
     np.cumsum(counts, out=offsets[1:])
     return CSR(offsets, pj[keep].astype(np.int32), S[keep].astype(np.float32))
+
+
+def radius_grid(P: np.ndarray, Q: np.ndarray | None, R: float, chunk: int = 8192) -> CSR:
+    """The definition of ``brute_radius`` for every query, for large sets in
+    low dimension (d <= 4): only pairs in the same or adjacent cells of a
+    uniform grid of side h = R (1 + 1e-6) (1 for R = 0) are evaluated, by the
+    definition itself (``snn_oracle_pairs``), and decided by S <= fl64(R*R).
+
+    No neighbour is missed: S <= fl64(R*R) implies an exact distance of at
+    most R (1 + 1e-15) (S is within gamma_{d+2} of it), hence every
+    coordinate difference is below h, and the cells floor(x_k / h), computed
+    in FP64 with |x_k / h| < 2^30, differ by at most one per axis."""
+    P = _as_f32(P)
+    Qa = P if Q is None else _as_f32(Q)
+    n, d = P.shape
+    m = Qa.shape[0]
+    if d > 4:
+        raise ValueError("radius_grid is for d <= 4")
+    R2 = float(np.float64(R) * np.float64(R))
+    # R = 0: only identical points (S = 0) are neighbours; any cell side works
+    h = float(R) * (1.0 + 1e-6) if R > 0 else 1.0
+    P64, Q64 = P.astype(np.float64), Qa.astype(np.float64)
+    if max(np.abs(P64).max(initial=0.0), np.abs(Q64).max(initial=0.0)) / h >= 2.0 ** 30:
+        raise ValueError("grid too fine for the coordinates")
+    cp = np.floor(P64 / h).astype(np.int64)
+    cq = np.floor(Q64 / h).astype(np.int64)
+    lo = np.minimum(cp.min(axis=0, initial=0), cq.min(axis=0, initial=0)) - 1
+    size = np.maximum(cp.max(axis=0, initial=0), cq.max(axis=0, initial=0)) - lo + 2
+    radix = np.ones(d, dtype=np.int64)
+    for k in range(1, d):
+        radix[k] = radix[k - 1] * size[k - 1]
+    if float(radix[-1]) * float(size[-1]) >= 2.0 ** 62:
+        raise ValueError("grid too large")
+    kp = ((cp - lo) * radix).sum(axis=1)
+    kq = ((cq - lo) * radix).sum(axis=1)
+    order = np.argsort(kp, kind="stable")
+    ks = kp[order]
+    shifts = np.array(np.meshgrid(*[[-1, 0, 1]] * d, indexing="ij")).reshape(d, -1).T
+    offs = (shifts * radix).sum(axis=1)
+    counts_all = np.zeros(m, dtype=np.int64)
+    ids_parts, d2_parts = [], []
+    for a in range(0, m, chunk):
+        qk = kq[a:a + chunk]
+        qis, pjs = [], []
+        for o in offs:
+            t = qk + o
+            l = np.searchsorted(ks, t, side="left")
+            r = np.searchsorted(ks, t, side="right")
+            c = r - l
+            tot = int(c.sum())
+            if tot == 0:
+                continue
+            qi = np.repeat(np.arange(len(qk), dtype=np.int64), c)
+            start = np.repeat(l - (np.cumsum(c) - c), c)
+            pjs.append(order[start + np.arange(tot, dtype=np.int64)])
+            qis.append(qi + a)
+        if not qis:
+            continue
+        qi = np.concatenate(qis)
+        pj = np.concatenate(pjs)
+        S = pair_dist2(P, Qa, qi, pj)
+        keep = S <= R2
+        qi, pj, S = qi[keep], pj[keep], S[keep]
+        srt = np.lexsort((pj, qi))
+        qi, pj, S = qi[srt], pj[srt], S[srt]
+        counts_all[a:a + chunk] = np.bincount(qi - a, minlength=len(qk))
+        ids_parts.append(pj.astype(np.int32))
+        d2_parts.append(S.astype(np.float32))
+    offsets = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(counts_all, out=offsets[1:])
+    ids = np.concatenate(ids_parts) if ids_parts else np.zeros(0, np.int32)
+    d2 = np.concatenate(d2_parts) if d2_parts else np.zeros(0, np.float32)
+    return CSR(offsets, ids, d2)
 
 
 def brute_row(P: np.ndarray, q: np.ndarray, R: float):

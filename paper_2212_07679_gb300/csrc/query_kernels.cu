@@ -507,6 +507,15 @@ __device__ __forceinline__ void decide_group_body(
     constexpr int GPW = 32 / G;   // groups per warp
     const int64_t nsurv = min((int64_t)*count, cap);
     const int lane = int(threadIdx.x % G);
+    // tier 0: a plain FP32 sum S0 of the squared (rounded) differences, each
+    // lane over at most h0 terms, then log2(G) additions; every term and sum
+    // is rounded at most h0 + log2(G) + 2 times, so S0 <= S (1 + u)^(h0 +
+    // log2 G + 2) for the exact sum S (underflow only lowers S0).  A pair
+    // with S0 above R^2 (1 + 1.01 (h + 3) u) + 2^-40 R^2 has S above R^2 by
+    // more than the FP64 definition's own rounding: not a neighbour.
+    const int h0 = 4 * int((dp / 4 + G - 1) / G) + (G == 32 ? 5 : 3) + 2;
+    const double f0 = 1.0 + 1.01 * (h0 + 3) * 0x1p-24 + 0x1p-40;
+    const float thr_uniform = fmaxf(__double2float_ru(R2 * f0), 0x1p-100f);
     const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t wstride = (int64_t(gridDim.x) * blockDim.x) >> 5;
     // the loop condition is the same for the whole warp; groups past the end
@@ -517,9 +526,28 @@ __device__ __forceinline__ void decide_group_body(
         const uint2 e = valid ? surv[s] : make_uint2(0u, 0u);
         const float4 *pq = reinterpret_cast<const float4 *>(qraw + int64_t(e.x) * dp);
         const float4 *pp = reinterpret_cast<const float4 *>(praw + int64_t(e.y) * dp);
+        float S0 = 0.f;
+        for (int k4 = lane; valid && k4 < dp / 4; k4 += G) {
+            const float4 a = pp[k4], b = pq[k4];
+            float t = __fsub_rn(a.x, b.x);
+            S0 = __fmaf_rn(t, t, S0);
+            t = __fsub_rn(a.y, b.y);
+            S0 = __fmaf_rn(t, t, S0);
+            t = __fsub_rn(a.z, b.z);
+            S0 = __fmaf_rn(t, t, S0);
+            t = __fsub_rn(a.w, b.w);
+            S0 = __fmaf_rn(t, t, S0);
+        }
+#pragma unroll
+        for (int o = G / 2; o; o >>= 1) S0 = __fadd_rn(S0, __shfl_xor_sync(0xffffffffu, S0, o, G));
+        const float thr0 =
+            R2q ? (valid ? fmaxf(__double2float_ru(R2q[e.x] * f0), 0x1p-100f) : 0.f) : thr_uniform;
+        // clearly outside: the compensated evaluation is skipped (the group
+        // still takes part in the warp's shuffles below)
+        const bool rej = valid && S0 > thr0;
         float H = 0.f, L = 0.f;
         bool nz = false;
-        for (int k4 = lane; valid && k4 < dp / 4; k4 += G) {
+        for (int k4 = lane; valid && !rej && k4 < dp / 4; k4 += G) {
             const float4 a = pp[k4], b = pq[k4];
             const float av[4] = {a.x, a.y, a.z, a.w};
             const float bv[4] = {b.x, b.y, b.z, b.w};
@@ -557,6 +585,12 @@ __device__ __forceinline__ void decide_group_body(
             nz = (b & gm) != 0u;
         }
         if (lane != 0 || !valid) continue;
+        if (rej) {
+            rec_d2[s] = 0.f;
+            rec_pos[s] = -1;
+            if (kSym) rec_pos[cap + s] = -1;
+            continue;
+        }
         const DecideConsts dc = dcq ? dcq[e.x] : dc0;
         const double R2e = R2q ? R2q[e.x] : R2;
         float d2 = 0.f;
@@ -611,6 +645,30 @@ __global__ void __launch_bounds__(256) k_decide_one_g32(SNN_DECIDE_ARGS) {
 }
 #undef SNN_DECIDE_PASS
 #undef SNN_DECIDE_ARGS
+
+// Survivors in query order for the decision of long rows: the query
+// position (key) and row position (value) of every buffer slot; slots past
+// the survivor count take the key m, so a stable sort by key puts them last.
+__global__ void k_surv_split(const uint2 *__restrict__ surv, const unsigned long long *__restrict__ count,
+                             int64_t cap, uint32_t m, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= cap) return;
+    const int64_t ns = min((int64_t)*count, cap);
+    if (i < ns) {
+        const uint2 e = surv[i];
+        keys[i] = e.x;
+        vals[i] = e.y;
+    } else {
+        keys[i] = m;
+        vals[i] = 0u;
+    }
+}
+
+__global__ void k_surv_join(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                            const unsigned long long *__restrict__ count, int64_t cap, uint2 *__restrict__ surv) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < min((int64_t)*count, cap)) surv[i] = make_uint2(keys[i], vals[i]);
+}
 
 __global__ void k_counts_to_i64(const int32_t *__restrict__ counts, int64_t m,
                                 int64_t *__restrict__ out) {

@@ -483,9 +483,9 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
 #pragma unroll 1
                 for (int g2 = 0; g2 < kGroups; g2 += 2) {
                     uint32_t rr[64];
-                    float mx;
+                    float mx[4];
                     const int cb0 = half * kGroups + g2;
-                    tmem_ld64_max(tbase + uint32_t(cb0 * 32), rr, mx);
+                    tmem_ld64_max4(tbase + uint32_t(cb0 * 32), rr, mx);
                     if (kGroups == 2) {
                         // this warp's only load of the chunk is complete: hand
                         // the accumulator back before the survivor processing
@@ -493,68 +493,56 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                         __syncwarp();
                         if (lane == 0) mbar_arrive(tempty_bar(b));
                     }
-                    // every accumulator of the 64 columns negative: all rejected
-                    // (an acceptable pair's accumulator is strictly positive)
-                    const bool any = !(mx < 0.f);
-                    if (!__any_sync(0xffffffffu, any)) continue;
+                    // a 16-column group whose accumulators are all negative
+                    // holds no survivor (an acceptable pair's accumulator is
+                    // strictly positive); only groups where some lane of the
+                    // warp may hold one are scanned
+                    bool anyg[4];
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int cb = cb0 + h;
-                        const uint32_t *rh = rr + 32 * h;
-                        uint32_t mask = 0;
-                        if (any) {
-                            // bit i = sign of column i: (mask << 1) | (x >> 31) per
-                            // column, one funnel shift each, highest column first
-                            uint32_t neg = 0;
+                    for (int g = 0; g < 4; ++g) anyg[g] = !(mx[g] < 0.f);
+                    if (!__any_sync(0xffffffffu, anyg[0] || anyg[1] || anyg[2] || anyg[3])) continue;
+                    // bit i of the mask = column cb0 * 32 + i is a survivor:
+                    // (mask << 1) | sign per column, highest column first, one
+                    // funnel shift each
+                    uint32_t neg[2] = {0xffffffffu, 0xffffffffu};
 #pragma unroll
-                            for (int i = 31; i >= 0; --i) neg = __funnelshift_l(rh[i], neg, 1);
-                            mask = qvalid ? ~neg : 0u;
-                            if (edge) {
-                                // validity near the band end and on the diagonal of
-                                // a symmetric self-join (rows >= query only)
-                                const int64_t jb = j0 + cb * 32;
-                                const int64_t lim = f.band_hi - jb;
-                                if (lim <= 0) mask = 0;
-                                else if (lim < 32) mask &= (1u << lim) - 1u;
-                                if (a.sym) {
-                                    const int64_t first = q - jb;
-                                    if (first >= 32) mask = 0;
-                                    else if (first > 0) mask &= ~((1u << first) - 1u);
-                                }
-                            }
+                    for (int g = 0; g < 4; ++g) {
+                        if (!__any_sync(0xffffffffu, anyg[g])) continue;
+                        uint32_t ng = 0;
+#pragma unroll
+                        for (int i = 15; i >= 0; --i) ng = __funnelshift_l(rr[16 * g + i], ng, 1);
+                        const int sh = 16 * (g & 1);
+                        neg[g >> 1] = (neg[g >> 1] & ~(0xffffu << sh)) | (ng << sh);
+                    }
+                    uint64_t mask = qvalid ? ~((uint64_t(neg[1]) << 32) | neg[0]) : 0ull;
+                    if (edge) {
+                        // validity near the band end and on the diagonal of a
+                        // symmetric self-join (rows >= query only)
+                        const int64_t jb = j0 + cb0 * 32;
+                        const int64_t lim = f.band_hi - jb;
+                        if (lim <= 0) mask = 0;
+                        else if (lim < 64) mask &= (1ull << lim) - 1ull;
+                        if (a.sym) {
+                            const int64_t first = q - jb;
+                            if (first >= 64) mask = 0;
+                            else if (first > 0) mask &= ~((1ull << first) - 1ull);
                         }
-                        const int cnt = __popc(mask);
-                        if (__any_sync(0xffffffffu, cnt != 0)) {
-                            int incl = cnt;
-                            for (int o = 1; o < 32; o <<= 1) {
-                                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                                if (lane >= o) incl += y;
-                            }
-                            const int wtot = __shfl_sync(0xffffffffu, incl, 31);
-                            if (scount + wtot > kStg) flush();
-                            if (wtot <= kStg) {
-                                int p = scount + incl - cnt;
-                                while (mask) {
-                                    const int i = __ffs(mask) - 1;
-                                    mask &= mask - 1;
-                                    stg[p++] = make_uint2(unsigned(q), unsigned(j0 + cb * 32 + i));
-                                }
-                                scount += wtot;
-                            } else {
-                                // more than a staging buffer at once: straight out
-                                unsigned long long pos = 0;
-                                if (lane == 31) pos = atomicAdd(a.count, (unsigned long long)wtot);
-                                pos = __shfl_sync(0xffffffffu, pos, 31) +
-                                      (unsigned long long)(incl - cnt);
-                                while (mask) {
-                                    const int i = __ffs(mask) - 1;
-                                    mask &= mask - 1;
-                                    if (pos < (unsigned long long)a.cap)
-                                        a.surv[pos] = make_uint2(unsigned(q), unsigned(j0 + cb * 32 + i));
-                                    ++pos;
-                                }
-                            }
+                    }
+                    // one survivor per lane per round: a ballot ranks them in
+                    // the warp's staging buffer
+                    const unsigned lt = lanemask_lt();
+                    const uint32_t jcol = unsigned(j0 + cb0 * 32);
+                    while (__any_sync(0xffffffffu, mask != 0)) {
+                        const bool has = mask != 0;
+                        const unsigned bal = __ballot_sync(0xffffffffu, has);
+                        const int nb = __popc(bal);
+                        if (scount + nb > kStg) flush();
+                        if (has) {
+                            const int i = __ffsll((long long)mask) - 1;
+                            mask &= mask - 1;
+                            stg[scount + __popc(bal & lt)] = make_uint2(unsigned(q), jcol + unsigned(i));
                         }
+                        scount += nb;
                     }
                 }
                 if (kGroups != 2) {

@@ -111,8 +111,6 @@ def _load():
     lib.snn_index_save.restype = ctypes.c_int
     lib.snn_index_load.argtypes = [ctypes.c_char_p, i64, vp, ctypes.POINTER(vp)]
     lib.snn_index_load.restype = ctypes.c_int
-    lib.snn_measure_peak.argtypes = [i32, i64, vp, ctypes.POINTER(f64)]
-    lib.snn_measure_peak.restype = ctypes.c_int
     lib.snn_index_build_batch.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(i64),
                                           ctypes.POINTER(i32), ctypes.POINTER(i64), vp,
                                           ctypes.POINTER(vp)]
@@ -630,14 +628,3 @@ def test_inject(fault: int) -> None:
 def launch_count() -> int:
     """Kernels launched by libsnn in this process so far."""
     return int(lib.snn_launch_count())
-
-
-PEAK_KINDS = {"bf16_mma": 0, "e4m3_mma": 1, "fp32_fma": 2, "fp64_fma": 3}
-
-
-def measure_peak(kind: str, iters: int, stream=None) -> float:
-    """Throughput probe (flop/s) of one arithmetic unit on every SM; see
-    snn_measure_peak in include/snn.h for the kernels and the flop counts."""
-    out = ctypes.c_double()
-    _check(lib.snn_measure_peak(PEAK_KINDS[kind], int(iters), _stream_ptr(stream), ctypes.byref(out)))
-    return out.value

@@ -396,6 +396,63 @@ def test_full_size_lowrank_img_sampled(snn, prec):
 
 
 @pytest.mark.slow
+def test_full_size_lowrank_img_whole_csr(snn):
+    """The 70,000 x 784 self-join at full size, every row: the rows' entries
+    at columns from their 4,096-row block onwards are compared with the
+    oracle's (oracle.radius_rows against the points from that block on), and
+    the whole CSR is symmetric, so every pair is checked once.  The default
+    16-bit scorer here keeps one FP16 part per row; the pairs nearest to R^2
+    that the oracle returns show the check reaches the boundary."""
+    w = wl.lowrank_img()
+    got = snn.Index(_dev(w.P)).query(None, w.R, precision="bf16", stats=True)
+    assert got.stats["split_used"] == snn.SNN_SPLIT_FP16X1
+    off = got.offsets.cpu().numpy()
+    idx = got.indices.cpu().numpy()
+    d2 = got.dist2.cpu().numpy()
+    n, R2 = w.n, float(np.float64(w.R) * np.float64(w.R))
+    step, checked, near = 4096, 0, 0
+    for a in range(0, n, step):
+        b = min(n, a + step)
+        ref = oracle.radius_rows(w.P[a:], w.P, np.arange(a, b), w.R)
+        for t, r in enumerate(range(a, b)):
+            ri, rd = ref.row(t)
+            lo, hi = off[r], off[r + 1]
+            sel = idx[lo:hi] >= a
+            assert np.array_equal(idx[lo:hi][sel], ri + a), r
+            assert np.array_equal(d2[lo:hi][sel].view(np.uint32), rd.view(np.uint32)), r
+            checked += len(ri)
+            near += int(np.count_nonzero(rd.astype(np.float64) >= R2 * (1.0 - 1e-6)))
+    rowid = np.repeat(np.arange(n, dtype=np.int64), np.diff(off))
+    ii = idx.astype(np.int64)
+    assert np.array_equal(np.sort(rowid * n + ii), np.sort(ii * n + rowid))
+    # every pair is compared at least once (pairs inside one block twice)
+    assert (got.nnz + n) // 2 <= checked <= got.nnz
+    assert near > 0
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", PRECS)
+def test_full_size_dbscan_labels(snn, prec):
+    """DBSCAN on the 500,000-point particle set (eps 0.4, minPts 10) at full
+    size: labels and core flags equal the oracle's DBSCAN element by element,
+    and the self-join under it equals the oracle's neighbour lists (every
+    pair in adjacent grid cells evaluated by the FP64 definition)."""
+    w = wl.blobs3d()
+    eps, min_pts = w.R, w.extra["min_pts"]
+    ref_csr = oracle.radius_grid(w.P, None, eps)
+    ref_lab, ref_core = oracle.dbscan(w.P, eps, min_pts, csr=ref_csr)
+    X = _dev(w.P)
+    labels, core = snn.dbscan(X, eps, min_pts, precision=prec)
+    lab = labels.cpu().numpy()
+    cr = core.cpu().numpy()
+    assert np.array_equal(cr, ref_core)
+    bad = np.nonzero(lab != ref_lab)[0]
+    assert bad.size == 0, f"{bad.size} labels differ, first at {bad[:5]}"
+    got = snn.Index(X).query(None, eps, precision=prec)
+    assert_csr_equal(got, ref_csr, f"blobs3d self-join {prec}")
+
+
+@pytest.mark.slow
 def test_full_size_dbscan_sampled(snn):
     w = wl.blobs3d()
     eps, min_pts = w.R, w.extra["min_pts"]

@@ -115,8 +115,12 @@ def test_normalize_rows_argument_validation_needs_no_gpu(libpath):
     assert lib.snn_normalize_rows(p, 0, 3, 3, p, 3, None) == 0         # nothing to do
 
 
-def test_peak_probe_validation_needs_no_gpu(libpath):
-    lib = ctypes.CDLL(libpath)
+def test_peak_probes_live_outside_the_search_library(libpath):
+    # the roofline probes are a bench-only library linked against libsnn.so;
+    # the search library itself does not export them
+    import bench_probes
+    assert not hasattr(ctypes.CDLL(libpath), "snn_measure_peak")
+    lib = ctypes.CDLL(bench_probes.build())
     lib.snn_measure_peak.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
                                      ctypes.POINTER(ctypes.c_double)]
     out = ctypes.c_double()

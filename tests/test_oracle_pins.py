@@ -252,3 +252,30 @@ def test_radius_rows_equals_brute_force():
         assert np.array_equal(got.dist2.view(np.uint32), ref.dist2.view(np.uint32))
     with pytest.raises(ValueError):
         oracle.radius_rows(P2, None, [0], 1.0, margin=1e-16)
+
+
+def test_radius_grid_equals_brute_force():
+    """The grid-cell evaluation of the definition returns exactly the full
+    brute force in d = 1..4: clusters, exact ties on an integer grid at R = 1
+    and R = 2, duplicates at R = 0, negative and offset coordinates, and
+    out-of-sample queries."""
+    rng = np.random.default_rng(92)
+    cases = []
+    for d in (1, 2, 3, 4):
+        P = (rng.standard_normal((2500, d)) + 8.0 * rng.standard_normal((4, d))[rng.integers(0, 4, 2500)])
+        cases.append((P.astype(np.float32), None, 0.35))
+        Q = (rng.standard_normal((400, d)) * 6.0 - 100.0 * (d == 2)).astype(np.float32)
+        cases.append(((P - 100.0 * (d == 2)).astype(np.float32), Q, 0.8))
+    g = np.stack(np.meshgrid(np.arange(10), np.arange(10), np.arange(10)), -1).reshape(-1, 3) - 5
+    cases.append((g.astype(np.float32), None, 1.0))
+    cases.append((g.astype(np.float32), None, 2.0))
+    dup = np.repeat(rng.standard_normal((50, 3)), 6, axis=0).astype(np.float32)
+    cases.append((dup, None, 0.0))
+    for P, Q, R in cases:
+        got = oracle.radius_grid(P, Q, R, chunk=777)
+        ref = oracle.brute_radius(P, Q, R)
+        assert np.array_equal(got.offsets, ref.offsets)
+        assert np.array_equal(got.ids, ref.ids)
+        assert np.array_equal(got.dist2.view(np.uint32), ref.dist2.view(np.uint32))
+    with pytest.raises(ValueError):
+        oracle.radius_grid(np.zeros((3, 5), np.float32), None, 1.0)
