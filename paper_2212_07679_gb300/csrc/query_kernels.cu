@@ -646,30 +646,6 @@ __global__ void __launch_bounds__(256) k_decide_one_g32(SNN_DECIDE_ARGS) {
 #undef SNN_DECIDE_PASS
 #undef SNN_DECIDE_ARGS
 
-// Survivors in query order for the decision of long rows: the query
-// position (key) and row position (value) of every buffer slot; slots past
-// the survivor count take the key m, so a stable sort by key puts them last.
-__global__ void k_surv_split(const uint2 *__restrict__ surv, const unsigned long long *__restrict__ count,
-                             int64_t cap, uint32_t m, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= cap) return;
-    const int64_t ns = min((int64_t)*count, cap);
-    if (i < ns) {
-        const uint2 e = surv[i];
-        keys[i] = e.x;
-        vals[i] = e.y;
-    } else {
-        keys[i] = m;
-        vals[i] = 0u;
-    }
-}
-
-__global__ void k_surv_join(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals,
-                            const unsigned long long *__restrict__ count, int64_t cap, uint2 *__restrict__ surv) {
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i < min((int64_t)*count, cap)) surv[i] = make_uint2(keys[i], vals[i]);
-}
-
 __global__ void k_counts_to_i64(const int32_t *__restrict__ counts, int64_t m,
                                 int64_t *__restrict__ out) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;

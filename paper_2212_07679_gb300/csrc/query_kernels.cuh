@@ -184,10 +184,6 @@ __device__ __forceinline__ int decide_df(float H, float L, bool nz, const Decide
                          const double *R2q, const DecideConsts *dcq,                         \
                          float *rec_d2, int32_t *rec_pos, uint2 *rec_rc, int32_t *counts,    \
                          unsigned long long *n_fp64)
-__global__ void k_surv_split(const uint2 *surv, const unsigned long long *count, int64_t cap, uint32_t m,
-                             uint32_t *keys, uint32_t *vals);
-__global__ void k_surv_join(const uint32_t *keys, const uint32_t *vals, const unsigned long long *count,
-                            int64_t cap, uint2 *surv);
 SNN_DECIDE_DECL(k_decide_sym);
 SNN_DECIDE_DECL(k_decide_one);
 SNN_DECIDE_DECL(k_decide_sym_g8);

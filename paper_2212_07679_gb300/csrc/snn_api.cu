@@ -1060,22 +1060,6 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         }
         if (st != SNN_OK) return fail(st);
         if (stats) cudaEventRecord(ev[2], s);
-        // long rows: the survivors in query order first (a stable sort by
-        // query position), so each query's raw row is reused from L1 and the
-        // rows of neighbouring queries, which share most of their survivors,
-        // from L2: the decision reads two raw rows per survivor, which do not
-        // fit L2 for large d and n
-        if (G > 1) {
-            uint32_t *sk;
-            TRY_Q(scr.alloc(&sk, size_t(4) * cap));
-            SNN_LAUNCH(k_surv_split, grid_for(cap, 256), 256, 0, s)(surv, ctr, cap, uint32_t(m), sk, sk + cap);
-            CUDA_Q(cudaGetLastError());
-            int bits = 1;
-            while ((uint64_t(1) << bits) <= uint64_t(m)) ++bits;
-            TRY_Q(radix_sort_pairs<uint32_t>(sk, sk + cap, sk + 2 * cap, sk + 3 * cap, cap, bits, s));
-            SNN_LAUNCH(k_surv_join, grid_for(cap, 256), 256, 0, s)(sk, sk + cap, ctr, cap, surv);
-            CUDA_Q(cudaGetLastError());
-        }
         // exact decision for every survivor (compensated FP32, FP64 where
         // needed), sized by the device-side survivor count
         CUDA_Q(cudaMemsetAsync(counts, 0, m * sizeof(int32_t), s));

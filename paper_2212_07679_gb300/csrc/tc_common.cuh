@@ -49,9 +49,12 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 }
 
 // Bounded wait; on timeout (or when another role already gave up) sets the
-// abort flags and returns false.
+// abort flags and returns false.  A phase that has already completed (the
+// common case of a deep pipeline) returns after one test, without reading the
+// clock.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
                                           int *err) {
+    if (mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try(bar, parity)) {
         if (*abort_flag) return false;
@@ -62,6 +65,19 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
         }
     }
     return true;
+}
+
+// Bounded wait that ignores the abort flag (draining copies before exit); on
+// timeout sets the error word.
+__device__ __forceinline__ void mbar_wait_drain(uint32_t bar, uint32_t parity, int *err) {
+    if (mbar_try(bar, parity)) return;
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity)) {
+        if (clock64() - t0 > kTcTimeoutCycles) {
+            atomicOr(err, 1);
+            return;
+        }
+    }
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,

@@ -90,7 +90,13 @@ constexpr int kTM = 128;            // queries per tile (MMA M)
 // MMA warps in front
 __host__ __device__ constexpr int tc_halves(int bn) { return bn >= 128 ? 2 : 1; }
 __host__ __device__ constexpr int tc_epi_warps(int mt, int bn) { return 4 * mt * tc_halves(bn); }
-__host__ __device__ constexpr int tc_threads(int mt, int bn) { return 64 + 32 * tc_epi_warps(mt, bn); }
+// warps: 0 TMA producer, 1 MMA issuer (and 2, a second issuer taking
+// alternate chunks, for the shapes with a resident query tile), then the
+// epilogue warps
+__host__ __device__ constexpr int tc_first_epi(bool ares) { return ares ? 3 : 2; }
+__host__ __device__ constexpr int tc_threads(int mt, int bn, bool ares) {
+    return 32 * tc_first_epi(ares) + 32 * tc_epi_warps(mt, bn);
+}
 // accumulator buffers in a CTA's share of the 512 TMEM columns (cps CTAs per
 // SM): four when they fit (the MMAs of three chunks then cover the hand-back
 // latency of the fourth), else two
@@ -144,7 +150,14 @@ struct TcShape {
     static constexpr int kRowBytesN = NW * 2;
     static constexpr uint32_t kTmemCols = tc_nbuf(MT, BN, CPS) * MT * BN;
     static constexpr int kEpiWarps = tc_epi_warps(MT, BN);
-    static constexpr int kThreads = tc_threads(MT, BN);
+    static constexpr int kThreads = tc_threads(MT, BN, ARES);
+    // two MMA issuers: a parity wait is only sound when the stage is at most
+    // one round behind the load it waits for, and an issuer waiting for the
+    // first k-block of its chunk has consumed the k-blocks up to its previous
+    // chunk, so the ring must hold more stages than a chunk has k-blocks: true
+    // for the resident-query-tile shapes (one k-block per chunk)
+    static constexpr bool kDual = ARES;
+    static constexpr int kFirstEpi = tc_first_epi(ARES);
     static constexpr int kNBuf = tc_nbuf(MT, BN, CPS);
     static constexpr size_t kSmem =
         size_t(kAResBytes) + size_t(kStages) * kStageBytes + kAlign + 512 + kStgBytes;
@@ -152,6 +165,8 @@ struct TcShape {
     static_assert(ARES || NW == BK, "narrow parts need a resident query tile");
     static_assert(MT == 1 || ARES, "several query tiles per item need a resident query tile");
     static_assert(kTmemCols * CPS <= 512, "accumulators exceed TMEM");
+    static_assert(kNBuf % 2 == 0, "two MMA issuers own alternate accumulator buffers");
+    static_assert(!ARES || kStagesRaw >= 2, "two issuers need two stages");
     static_assert(NW == 16 || NW == 32 || NW == 64, "unsupported part width");
     static_assert(!F8NP || ((BK == 16 || BK == 32) && NW == BK && !ARES && MT == 1), "FP8 shape");
     static_assert(!F8NP || (NSPLIT == 2 && (F8NP == 3 || F8NP == 4)) || (NSPLIT == 3 && F8NP == 6),
@@ -200,7 +215,7 @@ __device__ __forceinline__ ItemInfo item_info(const TcArgs &a, int64_t item) {
 }
 
 template <int NSPLIT, int BK, int BN, bool ARES, int CPS, int NW, int MT, int F8NP>
-__global__ void __launch_bounds__(tc_threads(MT, BN), CPS)
+__global__ void __launch_bounds__(tc_threads(MT, BN, ARES), CPS)
 k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUtensorMap qa1,
            const __grid_constant__ CUtensorMap qa2, const __grid_constant__ CUtensorMap xb0,
            const __grid_constant__ CUtensorMap xb1, const __grid_constant__ CUtensorMap xb2,
@@ -250,13 +265,16 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
     static_assert(8 * (2 * S + 2 * NB + 5) + 16 <= 512, "barrier area");
     volatile uint32_t *s_tmem = reinterpret_cast<volatile uint32_t *>(gmisc);
     volatile int *s_abort = reinterpret_cast<volatile int *>(gmisc + 4);
-    volatile int *s_consumed = reinterpret_cast<volatile int *>(gmisc + 8);
-    volatile int *s_aconsumed = reinterpret_cast<volatile int *>(gmisc + 12);
     // survivor staging: kStgEntries per epilogue warp, after the barriers
     uint2 *s_stg = reinterpret_cast<uint2 *>(gbase + (bar0 - base) + 512);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const CUtensorMap *qa[3] = {&qa0, &qa1, &qa2};
+    // Two MMA issuers (kDual, one per warp) take alternate chunks, each into
+    // its own accumulator buffers (NB is even), so one thread's barrier waits
+    // and commits overlap the other's MMAs; both walk the whole work list to
+    // keep the stage and buffer counters.
+    constexpr bool dual = Sh::kDual;
     const CUtensorMap *xb[3] = {&xb0, &xb1, &xb2};
 
     if (threadIdx.x == 0) {
@@ -270,12 +288,10 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
         }
         for (int k = 0; k < 2; ++k) {
             mbar_init(afull_bar(k), 1);
-            mbar_init(aempty_bar(k), 1);
+            mbar_init(aempty_bar(k), dual ? 2 : 1);   // one commit per MMA issuer
         }
-        mbar_init(done_bar, 1);
+        mbar_init(done_bar, dual ? 2 : 1);
         *s_abort = 0;
-        *s_consumed = 0;
-        *s_aconsumed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -336,8 +352,9 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                 }
             }
         }
-    } else if (warp == 1) {
-        // ------------------------------------------------- MMA issuer
+    } else if (warp >= 1 && warp < Sh::kFirstEpi) {
+        // ------------------------------------------------- MMA issuer(s)
+        const int me = warp - 1;
         if (lane == 0) {
             int it = 0, chunk = 0, itm = 0;
             bool ok = true;
@@ -347,10 +364,13 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                 if (ARES) {
                     if (!(ok = mbar_wait(afull_bar(aslot), uint32_t(itm >> 1) & 1u, s_abort, a.err)))
                         break;
-                    *s_aconsumed = itm + 1;
                     tmem_fence_after();
                 }
                 for (int64_t jr = f.c_first * kBR; jr < f.c_end * kBR && ok; jr += BN, ++chunk) {
+                    if (dual && (chunk & 1) != me) {
+                        it += a.nkb;
+                        continue;
+                    }
                     const int b = chunk % NB;
                     const uint32_t use = uint32_t(chunk / NB);
                     if (!(ok = mbar_wait(tempty_bar(b), (use & 1u) ^ 1u, s_abort, a.err))) break;
@@ -426,7 +446,6 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                             }
                         }
                         mma_commit(empty_bar(s));
-                        *s_consumed = it + 1;
                     }
                     if (ok) mma_commit(tfull_bar(b));
                 }
@@ -438,7 +457,7 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
         }
     } else {
         // ---------------------------------------------------- epilogue
-        const int ew = warp - 2;                   // 0 .. kEpiWarps-1
+        const int ew = warp - Sh::kFirstEpi;       // 0 .. kEpiWarps-1
         const int quad = warp & 3;                 // TMEM lanes 32*quad .. +31
         const int sub = ew >> 2;
         constexpr int kHalves = tc_halves(BN);
@@ -557,12 +576,16 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
         flush();
     }
     __syncthreads();
-    // drain TMA copies still in flight (only after an abort)
+    // every copy this CTA issued lands before its shared memory is released
+    // (after an abort some were never consumed): a load into a stage is issued
+    // only after the previous load into that stage was consumed, so waiting
+    // for the last load of each stage (the last S) and of each query-tile
+    // slot (the last two) covers all of them
     if (warp == 0 && lane == 0) {
-        for (int it = *s_consumed; it < issued; ++it)
-            mbar_wait(full_bar(it % S), uint32_t(it / S) & 1u, s_abort, a.err);
-        for (int itm = *s_aconsumed; itm < a_issued; ++itm)
-            mbar_wait(afull_bar(itm & 1), uint32_t(itm >> 1) & 1u, s_abort, a.err);
+        for (int it = issued > S ? issued - S : 0; it < issued; ++it)
+            mbar_wait_drain(full_bar(it % S), uint32_t(it / S) & 1u, a.err);
+        for (int itm = a_issued > 2 ? a_issued - 2 : 0; itm < a_issued; ++itm)
+            mbar_wait_drain(afull_bar(itm & 1), uint32_t(itm >> 1) & 1u, a.err);
     }
     tmem_fence_before();
     __syncthreads();
