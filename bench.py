@@ -37,10 +37,10 @@ HBM_PEAK_FALLBACK = 6800.0
 SCORER_SOURCES = ["tc_score.cu", "tc_score.cuh", "tc_common.cuh", "common.cuh", "index_struct.cuh",
                   "query_kernels.cuh"]
 SCORER_TRAFFIC = {
-    "sha": "42745175c21e5a17",
+    "sha": "743d81887150c9ea",
     "profile": "profiles/k_score_tc_dram_traffic_full_size.md",
-    ("gmm_aniso", 1000000, "bf16"): 192556288 + 171962368,
-    ("lowrank_img", 70000, "bf16"): 6992338688 + 9428992,
+    ("gmm_aniso", 1000000, "bf16"): 192621056 + 172989696,
+    ("lowrank_img", 70000, "bf16"): 255685888 + 8194560,
 }
 
 
