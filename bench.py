@@ -482,9 +482,9 @@ def per_config_ragged(args, snn, torch, flush, stream, steps=5, warmup=2):
     M = sum(q.shape[0] for q in Qs)
     N = sum(x.shape[0] for x in Xs)
 
-    def make_plan(idx):
-        plan = snn.BatchPlan(idx, [q.shape[0] for q in Qs], Rs, survivor_capacity=64 * M + (1 << 20),
-                             nnz_capacity=64 * M + (1 << 20))
+    def make_plan(idx, prec="bf16"):
+        plan = snn.BatchPlan(idx, [q.shape[0] for q in Qs], Rs, precision=prec,
+                             survivor_capacity=64 * M + (1 << 20), nnz_capacity=64 * M + (1 << 20))
         for t, q in enumerate(Qs):
             plan.queries(t).copy_(q)
         return plan
@@ -496,11 +496,12 @@ def per_config_ragged(args, snn, torch, flush, stream, steps=5, warmup=2):
         return plan.result(copy=False)
 
     ts, _ = _timed_steps(step, steps, warmup, flush, stream)
-    tsl, _ = _timed_steps(lambda: [snn.Index(x).query(q, r) for x, q, r in zip(Xs, Qs, Rs)], 3, 1, flush,
-                          stream)
+    tsl, _ = _timed_steps(lambda: [snn.Index(x).query(q, r, precision="bf16") for x, q, r in zip(Xs, Qs, Rs)],
+                          3, 1, flush, stream)
     idx = snn.build_batch(Xs)
     plan = make_plan(idx)
-    cpi, ctas, _ = plan.tune()
+    cpi, ctas, tune_ms = plan.tune()
+    tuned = plan.config()
 
     def graph_query():
         plan.launch_graph()
@@ -508,13 +509,26 @@ def per_config_ragged(args, snn, torch, flush, stream, steps=5, warmup=2):
     tsg, _ = _timed_steps(graph_query, steps, 2, flush, stream)
     plan.launch_graph()
     got = plan.result()
+    # the same query phase with the FP32 scorer only
+    plan32 = make_plan(idx, "fp32")
+    plan32.tune()
+
+    def graph_query32():
+        plan32.launch_graph()
+        return plan32.result(copy=False)
+    tsg32, _ = _timed_steps(graph_query32, steps, 2, flush, stream)
+    plan32.close()
     ms = float(np.median(ts))
     res = {"workload": "ragged_batch (256 mixtures, batched build + one batched query)", "sets": len(sets),
            "points": N, "queries": M, "value": M / (ms / 1e3), "unit": "queries/s", "ms_per_step": ms,
            "steps": steps, "per_set_calls": {"ms_per_step": float(np.median(tsl)),
                                             "value": M / (np.median(tsl) / 1e3)},
            "query_phase_graph_ms": float(np.median(tsg)),
-           "tuned": {"chunks_per_item": cpi, "ctas_per_sm": ctas}, "generation_s": gen_s}
+           "query_phase_graph_ms_fp32_scorer": float(np.median(tsg32)),
+           "precision": "bf16 (tensor-core groups for the out-of-sample sets of d <= 48)",
+           "tuned": {"chunks_per_item": cpi, "ctas_per_sm": ctas, "tc_groups": tuned["tc_groups"],
+                     "tc_mask": tuned["tc_mask"], "from_cache": tuned["from_cache"], "tune_ms": tune_ms},
+           "generation_s": gen_s}
     if args.cpu_baseline:
         import oracle
         rng = np.random.default_rng(33)
@@ -892,8 +906,8 @@ def run_ragged(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def make_plan(idx):
-        plan = snn.BatchPlan(idx, [q.shape[0] for q in Qs], Rs, survivor_capacity=64 * M + (1 << 20),
-                             nnz_capacity=64 * M + (1 << 20))
+        plan = snn.BatchPlan(idx, [q.shape[0] for q in Qs], Rs, precision=args.precision,
+                             survivor_capacity=64 * M + (1 << 20), nnz_capacity=64 * M + (1 << 20))
         for t, q in enumerate(Qs):
             plan.queries(t).copy_(q)
         return plan
@@ -906,7 +920,7 @@ def run_ragged(args):
         return idx, plan, out
 
     def per_set():
-        return [snn.Index(x).query(q, r) for x, q, r in zip(Xs, Qs, Rs)]
+        return [snn.Index(x).query(q, r, precision=args.precision) for x, q, r in zip(Xs, Qs, Rs)]
 
     def timed(fn, reps):
         ts = []
@@ -947,7 +961,7 @@ def run_ragged(args):
     pidx = [snn.Index(x) for x in Xs]
 
     def loop_query():
-        return [ix.query(q, r) for ix, q, r in zip(pidx, Qs, Rs)]
+        return [ix.query(q, r, precision=args.precision) for ix, q, r in zip(pidx, Qs, Rs)]
     ms_loop_query = timed(loop_query, max(3, min(args.steps, 5)))
     clk = clocks.stop()
     got = plan.result()
@@ -962,8 +976,8 @@ def run_ragged(args):
         t0 = time.perf_counter()
         xd = [x.to("cuda", non_blocking=True) for x in Xh]
         ex = snn.build_batch(xd)
-        ep = snn.BatchPlan(ex, [q.shape[0] for q in Qh], Rs, survivor_capacity=64 * M + (1 << 20),
-                           nnz_capacity=64 * M + (1 << 20))
+        ep = snn.BatchPlan(ex, [q.shape[0] for q in Qh], Rs, precision=args.precision,
+                           survivor_capacity=64 * M + (1 << 20), nnz_capacity=64 * M + (1 << 20))
         for t, q in enumerate(Qh):
             ep.queries(t).copy_(q, non_blocking=True)
         ep.run()
@@ -978,15 +992,16 @@ def run_ragged(args):
         "metric": "ragged batch exact radius queries/s (batched index build + one batched query)",
         "value": M / (ms_step / 1e3), "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f16+bf16+f32+f64" if args.precision != "fp32" else "f32+f64",
+        "data": "synthetic",
         "config": {"workload": "ragged_batch", "sets": len(sets), "points": N, "queries": M,
-                   "precision": "fp32", "parallelism": "replicas1",
+                   "precision": args.precision, "parallelism": "replicas1",
                    "l2": "flushed between steps (256 MiB write)"},
         "per_set_calls": {"ms_per_step": ms_loop, "value": M / (ms_loop / 1e3)},
         "query_phase": {"graph_ms": ms_graph, "graph_queries_per_s": M / (ms_graph / 1e3),
                         "per_set_calls_ms": ms_loop_query,
                         "per_set_calls_queries_per_s": M / (ms_loop_query / 1e3),
-                        "tuned": {"chunks_per_item": cpi, "ctas_per_sm": ctas}},
+                        "tuned": dict(plan.config(), chunks_per_item=cpi, ctas_per_sm=ctas)},
         "clocks": clk, "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
         "e2e": {"value": M / (np.median(e2e_ms) / 1e3), "unit": "queries/s",
                 "h2d_bytes_per_step": int(sum(x.numel() + q.numel() for x, q in zip(Xh, Qh)) * 4),

@@ -321,9 +321,14 @@ snn_status snn_dbscan(const float *X, int64_t n, int32_t d, int64_t ld, double e
  * paper has no counterpart) whose runs are pure stream-ordered device work:
  * every size is fixed at creation (queries per set, survivor and neighbour
  * capacities), so a run never synchronises and can be captured into a CUDA
- * graph and replayed with new query values.  One persistent scoring launch
- * covers every (set, query tile, band chunk group) item of the batch through a
- * device work counter; scoring is FP32 (exact results for any precision).
+ * graph and replayed with new query values.  One persistent FP32 scoring
+ * launch covers every (set, query tile, band chunk group) item of the batch
+ * through a device work counter.  With prec SNN_PREC_BF16 (or FP8, which
+ * takes the same path here) the out-of-sample sets of d <= 48 are scored on
+ * the tensor cores instead, one launch per group of sets with the same
+ * rounded width (d <= 16, <= 32, <= 48): two FP16 parts of each set's rows
+ * scaled by its own power of two, packed once at creation (Eq. (4) with the
+ * same rejection bound as snn_query_radius); results are exact either way.
  *  idx, m, R  host arrays of nsets entries: m[t] queries for set t (written
  *             into the plan's buffer, snn_batch_plan_queries) or m[t] < 0 for
  *             the self-join of idx[t].  The indices must outlive the plan.
@@ -356,12 +361,26 @@ snn_status snn_batch_plan_launch_graph(snn_batch_plan *plan, void *stream);
 snn_status snn_batch_plan_result(snn_batch_plan *plan, void *stream, snn_csr *out,
                                  int64_t *need_survivors, int64_t *need_nnz);
 
-/* Autotuner: runs the plan on its current queries with every work
- * granularity (band chunks per scoring item: 4, 8, 16, 32) and scoring grid
- * (1 or 2 CTAs per SM), keeps the fastest and reports it (nullable outputs).
- * Synchronises `stream`; drops a previously captured graph. */
+/* Autotuner: runs the plan on its current queries, the median of three timed
+ * runs per candidate: first every combination of tensor-core groups scoring
+ * their sets on the tensor cores or leaving them to the FP32 scorer, then
+ * every FP32 work granularity (band chunks per scoring item: 4, 8, 16, 32)
+ * and grid (1 or 2 CTAs per SM); keeps the fastest and reports the FP32 part
+ * (nullable outputs; snn_batch_plan_config reports the rest).  When the
+ * environment variable SNN_TUNE_CACHE names a file (JSON Lines: one object
+ * per plan key of row and query size buckets per group), a plan whose key is
+ * stored takes that choice without timing (ms = 0), and a tuned choice is
+ * stored.  Synchronises `stream`; drops a previously captured graph. */
 snn_status snn_batch_plan_tune(snn_batch_plan *plan, void *stream, int32_t *chunks_per_item,
                                int32_t *ctas_per_sm, float *ms);
+
+/* The plan's current scoring configuration (nullable outputs): FP32 work
+ * granularity and grid, the number of tensor-core groups and the mask of
+ * those that score on the tensor cores (bit k: group k), and whether the last
+ * snn_batch_plan_tune took its choice from the tuning cache. */
+snn_status snn_batch_plan_config(const snn_batch_plan *plan, int32_t *chunks_per_item,
+                                 int32_t *ctas_per_sm, int32_t *tc_groups, uint32_t *tc_mask,
+                                 int32_t *from_cache);
 
 /* Releases the plan (stream-ordered on `stream`; NULL is a no-op). */
 void snn_batch_plan_free(snn_batch_plan *plan, void *stream);

@@ -9,8 +9,13 @@
 #include <cstring>
 #include <vector>
 
+#include <cstdio>
+#include <mutex>
+#include <string>
+
 #include "index_struct.cuh"
 #include "query_kernels.cuh"
+#include "tc_score.cuh"
 
 namespace snn {
 
@@ -160,7 +165,8 @@ __global__ void k_b_band(const SetDesc *__restrict__ sets, const int32_t *__rest
     const int64_t hi = max(lo, ub_gt(sd.x_alpha, sd.n, hi_x));
     tile_lo[t] = lo;
     tile_hi[t] = hi;
-    items[t] = cdiv(cdiv(hi - lo, kBR), int64_t(cpi));
+    // sets of a tensor-core group are scored by that group's launch
+    items[t] = sd.tc ? 0 : cdiv(cdiv(hi - lo, kBR), int64_t(cpi));
 }
 
 __device__ __forceinline__ void two_sum_b(float a, float b, float &s, float &e) {
@@ -742,23 +748,26 @@ struct PlanStatus {
     int big;                   // rows longer than 4096 entries
     int skip;                  // the CSR build was skipped
     float qnorm;               // largest centred query norm
+    int tcerr;                 // tensor-core groups: 1 a bounded wait expired, 2 a query beyond FP16
 };
 
 __global__ void k_plan_guard(const unsigned long long *__restrict__ ctr,
                              const int64_t *__restrict__ nnz, unsigned *__restrict__ cls,
                              const int *__restrict__ bad, const float *__restrict__ qnmax,
-                             int64_t surv_cap, int64_t nnz_cap, PlanStatus *__restrict__ st) {
+                             const int *__restrict__ tcerr, int64_t surv_cap, int64_t nnz_cap,
+                             PlanStatus *__restrict__ st) {
     const unsigned long long sv = ctr[0];
     const long long nz = *nnz;
     const int big = cls[4] > 0;
     const int skip = sv > (unsigned long long)surv_cap || nz > nnz_cap || big || *bad ||
-                     !(*qnmax <= (float)kMaxCentredNorm);
+                     !(*qnmax <= (float)kMaxCentredNorm) || *tcerr;
     st->surv = sv;
     st->nnz = nz;
     st->bad = *bad;
     st->big = big;
     st->skip = skip;
     st->qnorm = *qnmax;
+    st->tcerr = *tcerr;
     if (skip)
         for (int k = 0; k < 8; ++k) cls[k] = 0;
 }
@@ -785,6 +794,13 @@ struct snn_batch_plan {
     int64_t surv_cap = 0, nnz_cap = 0;
     int cpi = snn::kChunksPerItem;   // tuned: band chunks per scoring item
     int ctas_per_sm = 2;             // tuned: persistent scoring grid
+    // tensor-core groups (16-bit precision): out-of-sample sets of d <= 48 by
+    // fold column; tc_mask bit k: group k scores its sets (else they go to
+    // the FP32 scorer)
+    std::vector<snn::TcBatchGroup *> tc_groups;
+    unsigned tc_mask = 0;
+    int *tc_err = nullptr;
+    int tuned_from_cache = 0;
     std::vector<void *> blocks;      // pool blocks owned by the plan
     // device arrays
     float *qbuf = nullptr;
@@ -841,6 +857,7 @@ snn_status plan_enqueue(snn_batch_plan *p, cudaStream_t s) {
     const int64_t M = p->M, ntiles = p->ntiles, Moos = p->Moos;
     SNN_CUDA(cudaMemsetAsync(p->bad, 0, sizeof(int), s));
     SNN_CUDA(cudaMemsetAsync(p->qnmax, 0, sizeof(float), s));
+    SNN_CUDA(cudaMemsetAsync(p->tc_err, 0, sizeof(int), s));
     if (p->noos > 0) {
         SNN_CUDA(cudaMemsetAsync(p->oeps, 0, p->noos * sizeof(float), s));
         SNN_LAUNCH(k_b_project, unsigned(cdiv(Moos, 256)), 256, 0, s)(p->d_od, p->d_ooff, p->noos, Moos,
@@ -885,6 +902,11 @@ snn_status plan_enqueue(snn_batch_plan *p, cudaStream_t s) {
         ba.work = p->ctr + 1;
         SNN_LAUNCH(k_score_fp32_batch, device_sm_count() * p->ctas_per_sm, 256, 0, s)(ba);
         SNN_LAUNCH_CHECK();
+        // tensor-core groups append their survivors after the FP32 scorer's
+        for (size_t k = 0; k < p->tc_groups.size(); ++k)
+            if (p->tc_mask & (1u << k))
+                SNN_TRY(tc_batch_enqueue(p->tc_groups[k], p->tile_lo, p->tile_hi, p->surv, p->surv_cap, p->ctr,
+                                         p->tc_err, s));
     }
     SNN_CUDA(cudaMemsetAsync(p->counts, 0, std::max<int64_t>(M, 1) * sizeof(int32_t), s));
     SNN_LAUNCH(k_b_decide, unsigned(4 * device_sm_count()), 256, 0, s)(
@@ -899,8 +921,8 @@ snn_status plan_enqueue(snn_batch_plan *p, cudaStream_t s) {
         SNN_LAUNCH(k_seg_classify, unsigned(cdiv(M, 256)), 256, 0, s)(p->goff, M, p->lists,
                                                                       p->big_list, p->big_len, p->cls);
     }
-    SNN_LAUNCH(k_plan_guard, 1, 1, 0, s)(p->ctr, p->goff + M, p->cls, p->bad, p->qnmax, p->surv_cap,
-                                         p->nnz_cap, p->status);
+    SNN_LAUNCH(k_plan_guard, 1, 1, 0, s)(p->ctr, p->goff + M, p->cls, p->bad, p->qnmax, p->tc_err,
+                                         p->surv_cap, p->nnz_cap, p->status);
     SNN_LAUNCH(k_b_scatter, unsigned(4 * device_sm_count()), 256, 0, s)(
         p->surv, p->ctr, p->surv_cap, p->d_sets, p->qset, p->rec_d2, p->rec_pos, p->goff, p->tmp,
         &p->status->skip);
@@ -933,6 +955,7 @@ snn_status plan_enqueue(snn_batch_plan *p, cudaStream_t s) {
 
 void plan_release(snn_batch_plan *p, cudaStream_t s) {
     if (!p) return;
+    for (TcBatchGroup *g : p->tc_groups) tc_batch_release(g, s);
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
     for (void *b : p->blocks) cudaFreeAsync(b, s);
@@ -1107,6 +1130,25 @@ snn_status plan_create(int32_t nsets, const snn_index *const *idx, const int64_t
     PTRY(plan_alloc(p, &p->d_offpos, nsets, s));
     PTRY(plan_alloc(p, &p->set_nnz, nsets + 1, s));
     PTRY(plan_alloc(p, &p->status, 1, s));
+    PTRY(plan_alloc(p, &p->tc_err, 1, s));
+    if (prec != SNN_PREC_FP32) {
+        // tensor-core groups: out-of-sample sets of d <= 48 by fold column
+        // (d rounded up to 16), two FP16 parts of each set's scaled rows
+        std::vector<int> grp[3];
+        for (int32_t t = 0; t < nsets; ++t) {
+            const SetDesc &d = p->sd[t];
+            if (d.sym || d.m <= 0 || d.d > 48) continue;
+            grp[d.d <= 16 ? 0 : (d.d <= 32 ? 1 : 2)].push_back(t);
+        }
+        for (int k = 0; k < 3; ++k) {
+            if (grp[k].empty()) continue;
+            TcBatchGroup *g = nullptr;
+            PTRY(tc_batch_create(idx, p->sd.data(), grp[k].data(), int(grp[k].size()), 16 * (k + 1), s, &g));
+            p->tc_mask |= 1u << p->tc_groups.size();
+            p->tc_groups.push_back(g);
+            for (int t : grp[k]) p->sd[t].tc = 1;
+        }
+    }
 #undef PTRY
     if ((p->noos > 0 &&
          (cudaMemcpyAsync(p->d_od, p->od.data(), p->noos * sizeof(OosDesc), cudaMemcpyHostToDevice,
@@ -1187,6 +1229,15 @@ snn_status plan_result(snn_batch_plan *p, cudaStream_t s, snn_csr *out, int64_t 
     if (need_surv) *need_surv = (int64_t)hs.surv;
     if (need_nnz) *need_nnz = hs.nnz;
     if (hs.bad) { set_error("a query set contains NaN or Inf"); return SNN_EINVAL; }
+    if (hs.tcerr & 1) {
+        set_error("tensor-core scoring: a bounded wait gave up (pipeline stalled)");
+        return SNN_ETIMEOUT;
+    }
+    if (hs.tcerr & 2) {
+        set_error("a query of a tensor-core set is too large for its set's FP16 scaling; create the plan "
+                  "with FP32 precision for such queries");
+        return SNN_ENOTSUP;
+    }
     if (!(hs.qnorm <= (float)kMaxCentredNorm)) {
         set_error("a centred query norm of %g exceeds %g", (double)hs.qnorm, kMaxCentredNorm);
         return SNN_ENOTSUP;
@@ -1211,31 +1262,163 @@ snn_status plan_result(snn_batch_plan *p, cudaStream_t s, snn_csr *out, int64_t 
     return SNN_OK;
 }
 
-// Autotuner: times the run with each work granularity (band chunks per
-// scoring item) and scoring grid (CTAs per SM) on the plan's current query
-// values and keeps the fastest (any previously captured graph is dropped).
+// Scoring choice of every tensor-core group (bit k of mask: group k scores
+// its sets on the tensor cores, else the FP32 scorer takes them): the set
+// descriptors' flags, copied to the device.
+static snn_status plan_apply_mask(snn_batch_plan *p, unsigned mask, cudaStream_t s) {
+    for (size_t k = 0; k < p->tc_groups.size(); ++k) {
+        int n = 0;
+        const int *sets = tc_batch_sets(p->tc_groups[k], &n);
+        for (int i = 0; i < n; ++i) p->sd[sets[i]].tc = (mask >> k) & 1u;
+    }
+    p->tc_mask = mask;
+    SNN_CUDA(cudaMemcpyAsync(p->d_sets, p->sd.data(), p->nsets * sizeof(SetDesc), cudaMemcpyHostToDevice, s));
+    return SNN_OK;
+}
+
+static void plan_drop_graph(snn_batch_plan *p) {
+    if (p->exec) {
+        cudaGraphExecDestroy(p->exec);
+        p->exec = nullptr;
+    }
+    if (p->graph) {
+        cudaGraphDestroy(p->graph);
+        p->graph = nullptr;
+    }
+}
+
+// Tuning cache key of a plan: log2 buckets of the rows and queries of each
+// tensor-core group (by fold column) and of the FP32-scored sets.
+static std::string plan_key(const snn_batch_plan *p) {
+    int64_t rows[4] = {0, 0, 0, 0}, qs[4] = {0, 0, 0, 0};
+    for (int32_t t = 0; t < p->nsets; ++t) {
+        const SetDesc &d = p->sd[t];
+        const int b = (d.sym || d.d > 48) ? 3 : (d.d <= 16 ? 0 : (d.d <= 32 ? 1 : 2));
+        rows[b] += d.n;
+        qs[b] += d.m;
+    }
+    auto lg = [](int64_t v) { return v > 0 ? 64 - __builtin_clzll(uint64_t(v)) : 0; };
+    char buf[160];
+    snprintf(buf, sizeof(buf), "d16:%d/%d,d32:%d/%d,d48:%d/%d,fp32:%d/%d,prec:%d", lg(rows[0]), lg(qs[0]),
+             lg(rows[1]), lg(qs[1]), lg(rows[2]), lg(qs[2]), lg(rows[3]), lg(qs[3]), int(p->prec));
+    return buf;
+}
+
+// The tuning cache (SNN_TUNE_CACHE): JSON Lines, one object per plan key
+// with the chosen "cpi", "ctas_per_sm", "tc_mask" and the measured "ms".
+static std::mutex g_tune_mu;
+
+static bool tune_cache_lookup(const std::string &key, int *cpi, int *ctas, unsigned *mask) {
+    const char *path = getenv("SNN_TUNE_CACHE");
+    if (!path || !*path) return false;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    char line[512];
+    bool hit = false;
+    const std::string want = "{\"key\": \"" + key + "\",";
+    while (fgets(line, sizeof(line), f)) {
+        if (strncmp(line, want.c_str(), want.size()) != 0) continue;
+        int c = 0, t = 0;
+        unsigned m = 0;
+        if (sscanf(line + want.size(), " \"cpi\": %d, \"ctas_per_sm\": %d, \"tc_mask\": %u", &c, &t, &m) == 3 &&
+            (c == 4 || c == 8 || c == 16 || c == 32) && (t == 1 || t == 2)) {
+            *cpi = c;
+            *ctas = t;
+            *mask = m;
+            hit = true;
+        }
+    }
+    fclose(f);
+    return hit;
+}
+
+static void tune_cache_store(const std::string &key, int cpi, int ctas, unsigned mask, float ms) {
+    const char *path = getenv("SNN_TUNE_CACHE");
+    if (!path || !*path) return;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    std::vector<std::string> keep;
+    const std::string want = "{\"key\": \"" + key + "\",";
+    if (FILE *f = fopen(path, "r")) {
+        char line[512];
+        while (fgets(line, sizeof(line), f))
+            if (strncmp(line, want.c_str(), want.size()) != 0) keep.push_back(line);
+        fclose(f);
+    }
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "w");
+    if (!f) return;
+    for (const std::string &l : keep) fputs(l.c_str(), f);
+    fprintf(f, "{\"key\": \"%s\", \"cpi\": %d, \"ctas_per_sm\": %d, \"tc_mask\": %u, \"ms\": %.4f}\n", key.c_str(), cpi,
+            ctas, mask, double(ms));
+    fclose(f);
+    rename(tmp.c_str(), path);
+}
+
+// Autotuner: the median of three timed runs (after one warm-up run) on the
+// plan's current query values for each candidate, keeping the fastest:
+// first the scoring of every tensor-core group (its sets on the tensor cores
+// or on the FP32 scorer, every combination), then, with that choice, the
+// FP32 scorer's work granularity (band chunks per item: 4, 8, 16, 32) and grid
+// (1 or 2 CTAs per SM).  With SNN_TUNE_CACHE naming a file, a plan whose key
+// (row and query buckets per group) is in it takes the stored choice without
+// timing, and a tuned choice is stored.  Any captured graph is dropped.
 snn_status plan_tune(snn_batch_plan *p, cudaStream_t s, int *best_cpi, int *best_ctas,
                      float *best_ms) {
-    const int cpis[4] = {4, 8, 16, 32};
-    const int ctas[2] = {1, 2};
+    const std::string key = plan_key(p);
+    const unsigned full = (1u << p->tc_groups.size()) - 1u;
+    int cc = 0, ct = 0;
+    unsigned cm = 0;
+    plan_drop_graph(p);
+    p->tuned_from_cache = 0;
+    if (tune_cache_lookup(key, &cc, &ct, &cm) && (cm & ~full) == 0) {
+        p->cpi = cc;
+        p->ctas_per_sm = ct;
+        SNN_TRY(plan_apply_mask(p, cm, s));
+        p->tuned_from_cache = 1;
+        if (best_cpi) *best_cpi = cc;
+        if (best_ctas) *best_ctas = ct;
+        if (best_ms) *best_ms = 0.f;
+        return SNN_OK;
+    }
     cudaEvent_t e0, e1;
     SNN_CUDA(cudaEventCreate(&e0));
     SNN_CUDA(cudaEventCreate(&e1));
-    float best = 1e30f;
-    int bc = p->cpi, bt = p->ctas_per_sm;
     snn_status st = SNN_OK;
+    auto time_run = [&](float *out) {
+        float t[3];
+        for (int rep = 0; rep < 4 && st == SNN_OK; ++rep) {   // the first run warms up
+            cudaEventRecord(e0, s);
+            st = plan_enqueue(p, s);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = SNN_ECUDA;
+            if (rep > 0) cudaEventElapsedTime(&t[rep - 1], e0, e1);
+        }
+        std::sort(t, t + 3);
+        *out = t[1];
+    };
+    float best = 1e30f;
+    unsigned bm = p->tc_mask;
+    for (unsigned m = 0; m <= full && st == SNN_OK; ++m) {
+        if ((st = plan_apply_mask(p, m, s)) != SNN_OK) break;
+        float ms = 0.f;
+        time_run(&ms);
+        if (st == SNN_OK && ms < best) {
+            best = ms;
+            bm = m;
+        }
+    }
+    if (st == SNN_OK) st = plan_apply_mask(p, bm, s);
+    const int cpis[4] = {4, 8, 16, 32};
+    const int ctas[2] = {1, 2};
+    int bc = p->cpi, bt = p->ctas_per_sm;
+    best = 1e30f;
     for (int a = 0; a < 4 && st == SNN_OK; ++a)
         for (int b = 0; b < 2 && st == SNN_OK; ++b) {
             p->cpi = cpis[a];
             p->ctas_per_sm = ctas[b];
             float ms = 0.f;
-            for (int rep = 0; rep < 2 && st == SNN_OK; ++rep) {   // first run warms up
-                cudaEventRecord(e0, s);
-                st = plan_enqueue(p, s);
-                cudaEventRecord(e1, s);
-                if (cudaEventSynchronize(e1) != cudaSuccess) st = SNN_ECUDA;
-                cudaEventElapsedTime(&ms, e0, e1);
-            }
+            time_run(&ms);
             if (st == SNN_OK && ms < best) {
                 best = ms;
                 bc = cpis[a];
@@ -1246,18 +1429,21 @@ snn_status plan_tune(snn_batch_plan *p, cudaStream_t s, int *best_cpi, int *best
     cudaEventDestroy(e1);
     p->cpi = bc;
     p->ctas_per_sm = bt;
-    if (p->exec) {
-        cudaGraphExecDestroy(p->exec);
-        p->exec = nullptr;
-    }
-    if (p->graph) {
-        cudaGraphDestroy(p->graph);
-        p->graph = nullptr;
-    }
+    if (st == SNN_OK) tune_cache_store(key, bc, bt, bm, best);
     if (best_cpi) *best_cpi = bc;
     if (best_ctas) *best_ctas = bt;
     if (best_ms) *best_ms = best;
     return st;
+}
+
+snn_status plan_config(const snn_batch_plan *p, int *cpi, int *ctas, int *ngroups, unsigned *mask,
+                       int *from_cache) {
+    if (cpi) *cpi = p->cpi;
+    if (ctas) *ctas = p->ctas_per_sm;
+    if (ngroups) *ngroups = int(p->tc_groups.size());
+    if (mask) *mask = p->tc_mask;
+    if (from_cache) *from_cache = p->tuned_from_cache;
+    return SNN_OK;
 }
 
 }  // namespace snn

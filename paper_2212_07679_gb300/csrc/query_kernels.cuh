@@ -84,6 +84,7 @@ struct SetDesc {
     const int32_t *x_order;
     const float *eps_d, *eps_q; // device scalars: score rounding bounds
     double Rx, e_data;          // radius slack and centring error bound
+    int tc;                     // scored by a tensor-core group (no FP32 items)
 };
 
 struct BatchScoreArgs {

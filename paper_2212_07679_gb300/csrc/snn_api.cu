@@ -1238,6 +1238,8 @@ snn_status plan_run(snn_batch_plan *p, cudaStream_t s);
 snn_status plan_launch_graph(snn_batch_plan *p, cudaStream_t s);
 snn_status plan_result(snn_batch_plan *p, cudaStream_t s, snn_csr *out, int64_t *need_surv,
                        int64_t *need_nnz);
+snn_status plan_config(const snn_batch_plan *p, int *cpi, int *ctas, int *ngroups, unsigned *mask,
+                       int *from_cache);
 snn_status plan_tune(snn_batch_plan *p, cudaStream_t s, int *best_cpi, int *best_ctas,
                      float *best_ms);
 snn_status batch_query(int32_t nsets, const snn_index *const *idx, const float *const *Q,
@@ -1502,6 +1504,21 @@ snn_status snn_batch_plan_tune(snn_batch_plan *plan, void *stream, int32_t *chun
     clear_error();
     if (!plan) { set_error("plan is NULL"); return SNN_EINVAL; }
     return plan_tune(plan, static_cast<cudaStream_t>(stream), chunks_per_item, ctas_per_sm, ms);
+}
+
+snn_status snn_batch_plan_config(const snn_batch_plan *plan, int32_t *chunks_per_item, int32_t *ctas_per_sm,
+                                 int32_t *tc_groups, uint32_t *tc_mask, int32_t *from_cache) {
+    clear_error();
+    if (!plan) { set_error("plan is NULL"); return SNN_EINVAL; }
+    int c = 0, t = 0, g = 0, fc = 0;
+    unsigned m = 0;
+    plan_config(plan, &c, &t, &g, &m, &fc);
+    if (chunks_per_item) *chunks_per_item = c;
+    if (ctas_per_sm) *ctas_per_sm = t;
+    if (tc_groups) *tc_groups = g;
+    if (tc_mask) *tc_mask = m;
+    if (from_cache) *from_cache = fc;
+    return SNN_OK;
 }
 
 void snn_batch_plan_free(snn_batch_plan *plan, void *stream) {

@@ -32,6 +32,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <vector>
 
 #include "index_struct.cuh"
 #include "tc_common.cuh"
@@ -1503,6 +1504,315 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
     // halves of the band chunk), 32-column k-blocks, four stages
     return nsplit == 2 ? launch_tc<2, 32, 256, false, 1, 32, 1>(ix, *op, sa, qp, K2, K2n, ts1, s, F)
                        : launch_tc<3, 32, 256, false, 1, 32, 1>(ix, *op, sa, qp, K2, K2n, ts1, s, 0);
+}
+
+
+// ------------------------------------------------ tensor-core groups of a batched query plan
+// One out-of-sample query set of a group: the plan's query arrays (sorted
+// order), where its rows sit in the group's arrays, and its operand constants
+// (as the single-index scorer derives them from the set's index).
+struct TcbSet {
+    const float *qxc, *qhx, *qnrm;
+    int64_t m, xoff, q0g, grp0, tile0, ntiles;
+    int d, dp;
+    float xscale;
+    double fs1, fs2, c, Rx, e_data, delta, abs_n, abs_q;
+};
+
+struct TcBatchGroup {
+    int fold_col = 16, MT = 2, K2 = 32, K2n = 16, BK = 32, NW = 16;
+    std::vector<int> plan_sets;
+    int64_t xrows = 0, ngroups = 0, qrows = 0, max_items = 0;
+    TcbSet *d_sets = nullptr;
+    int32_t *d_grp_set = nullptr;
+    uint16_t *x0 = nullptr, *x1 = nullptr, *q0 = nullptr, *q1 = nullptr;
+    int64_t *lo2 = nullptr, *hi2 = nullptr, *items2 = nullptr, *off2 = nullptr;
+    int32_t *it2 = nullptr;
+    unsigned long long *begin = nullptr;
+    CUtensorMap maps[8];
+    std::vector<void *> blocks;
+};
+
+namespace {
+
+// Query operand rows of a group, one thread per row: row r belongs to tile
+// group r / rpg; rows past the set's queries are padding whose folded A' is
+// -2^100, so their accumulators are negative and nothing survives.  Otherwise
+// the two FP16 parts of the scaled centred query and the query-side folded
+// columns, exactly as k_tc_query_consts and k_tc_pack compute them.  A
+// scaled coordinate outside the FP16 range sets bit 1 of err.
+__global__ void k_tcb_qpack(const TcbSet *__restrict__ sets, const int32_t *__restrict__ grp_set,
+                            int64_t qrows, int rpg, int K2, int K2n, int fold_col, uint16_t *__restrict__ q0,
+                            uint16_t *__restrict__ q1, int *__restrict__ err) {
+    const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (r >= qrows) return;
+    const int64_t g = r / rpg;
+    const TcbSet &S = sets[grp_set[g]];
+    const int64_t i = (g - S.grp0) * rpg + (r - g * rpg);
+    uint16_t *o0 = q0 + r * K2, *o1 = q1 + r * K2n;
+    for (int k = 0; k < K2; k += 4) *reinterpret_cast<uint2 *>(o0 + k) = make_uint2(0u, 0u);
+    for (int k = 0; k < K2n; k += 4) *reinterpret_cast<uint2 *>(o1 + k) = make_uint2(0u, 0u);
+    const uint16_t one = bf16_bits(__float2bfloat16_rn(1.0f));
+    uint16_t *f = o0 + fold_col;
+    uint16_t sp[3], sa[3];
+    if (i >= S.m) {
+        split3(-0x1p100, sa);
+        for (int t = 0; t < 3; ++t) {
+            f[t] = one;
+            f[6 + t] = sa[t];
+        }
+        return;
+    }
+    const int d = S.d;
+    const double qn = (double)S.qnrm[i], hy = (double)S.qhx[i];
+    const double ei = 1.0001 * (double)kU32 * qn;
+    const double rr = S.Rx + S.e_data + ei;
+    const double hy_low = hy * (1.0 - 1.05 * (d + 2) * (double)kU32);
+    double A = 0.5 * rr * rr - hy_low + (S.abs_n + S.abs_q * qn);
+    A += 4.0 * kU64 * (fabs(A) + 0.5 * rr * rr + hy);
+    A = A >= 0.0 ? A / (1.0 - S.delta) : A / (1.0 + S.delta);
+    A += 0x1p-22 * fabs(A) + 0x1p-100;
+    const float *x = S.qxc + i * S.dp;
+    bool bad = false;
+    for (int k = 0; k < d; ++k) {
+        const float v = x[k] * S.xscale;
+        bad |= !(fabsf(v) <= 60000.f);
+        float hf = __half2float(__float2half_rn(v));
+        if (fabsf(hf) < 0x1p-14f) hf = 0.f;
+        float lf = __half2float(__float2half_rn(v - hf));
+        if (fabsf(lf) < 0x1p-14f) lf = 0.f;
+        o0[k] = half_bits(hf);
+        o1[k] = half_bits(lf);
+    }
+    if (bad) atomicOr(err, 2);
+    split3(S.c * qn * S.fs1, sp);
+    split3(A * S.fs2, sa);
+    for (int t = 0; t < 3; ++t) {
+        f[t] = one;
+        f[3 + t] = sp[t];
+        f[6 + t] = sa[t];
+    }
+}
+
+// Band and work items of every tile group: the union of its plan tiles'
+// bands (set-local rows), moved to the group's concatenated rows.
+__global__ void k_tcb_groups(const TcbSet *__restrict__ sets, const int32_t *__restrict__ grp_set,
+                             int64_t ngroups, int MT, const int64_t *__restrict__ tile_lo,
+                             const int64_t *__restrict__ tile_hi, int64_t *__restrict__ lo2,
+                             int64_t *__restrict__ hi2, int64_t *__restrict__ items2) {
+    const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= ngroups) return;
+    const TcbSet &S = sets[grp_set[g]];
+    const int64_t t0 = S.tile0 + (g - S.grp0) * MT;
+    const int64_t t1 = min(S.tile0 + S.ntiles, t0 + MT);
+    int64_t lo = tile_lo[t0], hi = tile_hi[t0];
+    for (int64_t t = t0 + 1; t < t1; ++t) {
+        lo = min(lo, tile_lo[t]);
+        hi = max(hi, tile_hi[t]);
+    }
+    hi = max(hi, lo);
+    lo2[g] = lo + S.xoff;
+    hi2[g] = hi + S.xoff;
+    items2[g] = cdiv(cdiv(hi - lo, kBR), kChunksPerItem);
+}
+
+__global__ void k_tcb_begin(const unsigned long long *__restrict__ count, unsigned long long *__restrict__ begin) {
+    *begin = *count;
+}
+
+// The group's survivors (appended after *begin) rewritten from (query operand
+// row, concatenated row) to (global query number, row of the set's index).
+__global__ void k_tcb_convert(uint2 *__restrict__ surv, const unsigned long long *__restrict__ count,
+                              int64_t cap, const unsigned long long *__restrict__ begin,
+                              const TcbSet *__restrict__ sets, const int32_t *__restrict__ grp_set, int rpg) {
+    const int64_t end = min((int64_t)*count, cap);
+    for (int64_t k = int64_t(*begin) + int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < end;
+         k += int64_t(gridDim.x) * blockDim.x) {
+        const uint2 e = surv[k];
+        const int64_t g = int64_t(e.x) / rpg;
+        const TcbSet &S = sets[grp_set[g]];
+        const int64_t i = (g - S.grp0) * rpg + (int64_t(e.x) - g * rpg);
+        surv[k] = make_uint2(unsigned(S.q0g + i), unsigned(int64_t(e.y) - S.xoff));
+    }
+}
+
+template <typename T>
+snn_status tcb_alloc(TcBatchGroup *g, T **p, int64_t count, cudaStream_t s) {
+    void *q = nullptr;
+    const size_t bytes = (std::max<size_t>(size_t(count) * sizeof(T), 16) + 255) & ~size_t(255);
+    if (cudaMallocAsync(&q, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("tensor-core group allocation of %zu bytes failed", bytes);
+        return SNN_ENOMEM;
+    }
+    g->blocks.push_back(q);
+    *p = static_cast<T *>(q);
+    return SNN_OK;
+}
+
+}  // namespace
+
+void tc_batch_release(TcBatchGroup *g, cudaStream_t s) {
+    if (!g) return;
+    for (void *b : g->blocks) cudaFreeAsync(b, s);
+    delete g;
+}
+
+const int *tc_batch_sets(const TcBatchGroup *g, int *nsets) {
+    *nsets = int(g->plan_sets.size());
+    return g->plan_sets.data();
+}
+
+snn_status tc_batch_create(const snn_index *const *idx, const SetDesc *sd, const int *sets, int nsets,
+                           int fold_col, cudaStream_t s, TcBatchGroup **out) {
+    *out = nullptr;
+    if (fold_col != 16 && fold_col != 32 && fold_col != 48) {
+        set_error("tensor-core group: fold column %d is not 16, 32 or 48", fold_col);
+        return SNN_EINVAL;
+    }
+    TcBatchGroup *g = new (std::nothrow) TcBatchGroup();
+    if (!g) {
+        set_error("host allocation failed");
+        return SNN_ENOMEM;
+    }
+    auto fail = [&](snn_status st) {
+        tc_batch_release(g, s);
+        return st;
+    };
+    g->fold_col = fold_col;
+    g->MT = fold_col == 16 ? 2 : 1;
+    g->BK = fold_col == 16 ? 32 : 64;
+    g->K2 = g->BK;
+    g->NW = fold_col == 16 ? 16 : 64;
+    g->K2n = g->NW;
+    const int rpg = kTM * g->MT;
+    std::vector<TcbSet> hs(nsets);
+    std::vector<int32_t> grp_set;
+    for (int k = 0; k < nsets; ++k) {
+        const int t = sets[k];
+        const snn_index *ix = idx[t];
+        const SetDesc &d = sd[t];
+        TcbSet &S = hs[k];
+        S.qxc = d.q_xc;
+        S.qhx = d.q_hx;
+        S.qnrm = d.q_nrm;
+        S.m = d.m;
+        S.xoff = g->xrows;
+        S.q0g = d.q_glob;
+        S.tile0 = d.tile0;
+        S.ntiles = cdiv(d.m, int64_t(kBQ));
+        S.grp0 = g->ngroups;
+        S.d = ix->d;
+        S.dp = ix->dp;
+        const double Nd = (double)ix->nrm_max;
+        const int sigma = Nd > 0.0 ? std::min(120, std::max(-120, 13 - std::ilogb(Nd))) : 0;
+        S.fs1 = std::ldexp(1.0, sigma);
+        S.fs2 = std::ldexp(1.0, 2 * sigma);
+        S.xscale = float(S.fs1);
+        double u_k = 0.0;
+        S.c = tc_constant(2, ix->d, &u_k, true);
+        S.Rx = d.Rx;
+        S.e_data = d.e_data;
+        S.delta = 0x1p-23 + u_k;
+        S.abs_q = 1.001 * std::sqrt(double(ix->d)) * std::ldexp(1.0, -14 - sigma);
+        S.abs_n = S.abs_q * Nd + 2.0 * ix->d * std::ldexp(1.0, -28 - 2 * sigma);
+        const int64_t ng = cdiv(S.ntiles, int64_t(g->MT));
+        for (int64_t q = 0; q < ng; ++q) grp_set.push_back(k);
+        g->ngroups += ng;
+        g->xrows += ix->n;
+        g->max_items += ng * (cdiv(ix->n, int64_t(kBR) * kChunksPerItem) + 1);
+        g->plan_sets.push_back(t);
+    }
+    g->qrows = g->ngroups * rpg;
+#define GTRY(expr)                           \
+    do {                                     \
+        snn_status _st = (expr);             \
+        if (_st != SNN_OK) return fail(_st); \
+    } while (0)
+    GTRY(tcb_alloc(g, &g->x0, g->xrows * g->K2, s));
+    GTRY(tcb_alloc(g, &g->x1, g->xrows * g->K2n, s));
+    GTRY(tcb_alloc(g, &g->q0, std::max<int64_t>(g->qrows, 1) * g->K2, s));
+    GTRY(tcb_alloc(g, &g->q1, std::max<int64_t>(g->qrows, 1) * g->K2n, s));
+    GTRY(tcb_alloc(g, &g->d_sets, nsets, s));
+    GTRY(tcb_alloc(g, &g->d_grp_set, std::max<int64_t>(g->ngroups, 1), s));
+    GTRY(tcb_alloc(g, &g->lo2, std::max<int64_t>(g->ngroups, 1), s));
+    GTRY(tcb_alloc(g, &g->hi2, std::max<int64_t>(g->ngroups, 1), s));
+    GTRY(tcb_alloc(g, &g->items2, std::max<int64_t>(g->ngroups, 1), s));
+    GTRY(tcb_alloc(g, &g->off2, g->ngroups + 1, s));
+    GTRY(tcb_alloc(g, &g->it2, std::max<int64_t>(g->max_items, 1), s));
+    GTRY(tcb_alloc(g, &g->begin, 1, s));
+    if (cudaMemcpyAsync(g->d_sets, hs.data(), nsets * sizeof(TcbSet), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        (g->ngroups > 0 && cudaMemcpyAsync(g->d_grp_set, grp_set.data(), grp_set.size() * sizeof(int32_t),
+                                           cudaMemcpyHostToDevice, s) != cudaSuccess)) {
+        set_error("tensor-core group setup copy failed");
+        return fail(SNN_ECUDA);
+    }
+    // the data operands of every set, packed once into the group's rows
+    for (int k = 0; k < nsets; ++k) {
+        const snn_index *ix = idx[sets[k]];
+        const TcbSet &S = hs[k];
+        const TcPackMode pm{1, fold_col, S.xscale, S.fs1, S.fs2};
+        SNN_LAUNCH(k_tc_pack<2>, unsigned(cdiv(cdiv(ix->n, 32) * 32, 256)), 256, 0, s)(
+            ix->xc, ix->dp, ix->hx, ix->nrm, nullptr, ix->n, ix->d, g->K2, g->K2n, S.c, 0,
+            g->x0 + S.xoff * g->K2, g->x1 + S.xoff * g->K2n, nullptr, pm);
+        if (cudaGetLastError() != cudaSuccess) {
+            set_error("tensor-core group packing failed");
+            return fail(SNN_ECUDA);
+        }
+    }
+    GTRY(make_map(&g->maps[0], g->q0, std::max<int64_t>(g->qrows, 1), g->K2, g->BK, rpg));
+    GTRY(make_map(&g->maps[1], g->q1, std::max<int64_t>(g->qrows, 1), g->K2n, g->NW, rpg));
+    GTRY(make_map(&g->maps[3], g->x0, g->xrows, g->K2, g->BK, 128));
+    GTRY(make_map(&g->maps[4], g->x1, g->xrows, g->K2n, g->NW, 128));
+    g->maps[2] = g->maps[0];
+    g->maps[5] = g->maps[3];
+    g->maps[6] = g->maps[0];
+    g->maps[7] = g->maps[3];
+#undef GTRY
+    *out = g;
+    return SNN_OK;
+}
+
+snn_status tc_batch_enqueue(TcBatchGroup *g, const int64_t *tile_lo, const int64_t *tile_hi, uint2 *surv,
+                            int64_t cap, unsigned long long *count, int *err, cudaStream_t s) {
+    if (g->ngroups == 0) return SNN_OK;
+    const int rpg = kTM * g->MT;
+    SNN_LAUNCH(k_tcb_qpack, unsigned(cdiv(g->qrows, 128)), 128, 0, s)(
+        g->d_sets, g->d_grp_set, g->qrows, rpg, g->K2, g->K2n, g->fold_col, g->q0, g->q1, err);
+    SNN_LAUNCH(k_tcb_groups, unsigned(cdiv(g->ngroups, 128)), 128, 0, s)(
+        g->d_sets, g->d_grp_set, g->ngroups, g->MT, tile_lo, tile_hi, g->lo2, g->hi2, g->items2);
+    SNN_LAUNCH_CHECK();
+    SNN_TRY(scan_exclusive<int64_t>(g->items2, g->off2, g->ngroups, s));
+    SNN_LAUNCH(k_item_tiles, unsigned(cdiv(g->ngroups, 128)), 128, 0, s)(g->off2, int(g->ngroups), g->it2);
+    SNN_LAUNCH(k_tcb_begin, 1, 1, 0, s)(count, g->begin);
+    SNN_LAUNCH_CHECK();
+    TcArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.m = g->qrows;
+    a.n = g->xrows;
+    a.ksteps_data = g->fold_col / 16;
+    a.ksteps = a.ksteps_data + 1;
+    a.nkb = g->K2 / g->BK;
+    a.tile_lo = g->lo2;
+    a.tile_hi = g->hi2;
+    a.item_off = g->off2;
+    a.item_tile = g->it2;
+    a.ntiles = int(g->ngroups);
+    a.sym = 0;
+    a.surv = surv;
+    a.cap = cap;
+    a.count = count;
+    a.err = err;
+    a.stall = 0;
+    a.f16 = 1;
+    ScoreArgs sa;
+    snn_status st = g->fold_col == 16 ? run_tc<2, 32, 128, true, 1, 16, 2, 0>(g->maps, a, sa, s)
+                                      : run_tc<2, 64, 128, true, 1, 64, 1, 0>(g->maps, a, sa, s);
+    if (st != SNN_OK) return st;
+    SNN_LAUNCH(k_tcb_convert, unsigned(4 * device_sm_count()), 256, 0, s)(surv, count, cap, g->begin, g->d_sets,
+                                                                         g->d_grp_set, rpg);
+    SNN_LAUNCH_CHECK();
+    return SNN_OK;
 }
 
 }  // namespace snn

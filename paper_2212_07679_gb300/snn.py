@@ -131,6 +131,9 @@ def _load():
     lib.snn_batch_plan_tune.argtypes = [vp, vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                         ctypes.POINTER(ctypes.c_float)]
     lib.snn_batch_plan_tune.restype = ctypes.c_int
+    lib.snn_batch_plan_config.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                          ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(i32)]
+    lib.snn_batch_plan_config.restype = ctypes.c_int
     lib.snn_batch_plan_free.argtypes = [vp, vp]
     lib.snn_batch_plan_free.restype = None
     return lib
@@ -560,6 +563,17 @@ class BatchPlan:
             _check(lib.snn_batch_plan_tune(self._h, _stream_ptr(stream), ctypes.byref(c),
                                            ctypes.byref(t), ctypes.byref(ms)))
         return c.value, t.value, ms.value
+
+    def config(self) -> dict:
+        """Current scoring configuration: FP32 chunks per item and CTAs per SM,
+        tensor-core groups and the mask of those scoring on the tensor cores,
+        and whether the last tune() came from the tuning cache."""
+        c, t, g, fc = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        m = ctypes.c_uint32()
+        _check(lib.snn_batch_plan_config(self._h, ctypes.byref(c), ctypes.byref(t), ctypes.byref(g),
+                                         ctypes.byref(m), ctypes.byref(fc)))
+        return {"chunks_per_item": c.value, "ctas_per_sm": t.value, "tc_groups": g.value,
+                "tc_mask": m.value, "from_cache": bool(fc.value)}
 
     def result(self, stream=None, copy: bool = True) -> list:
         """Per-set results of the last run (copies unless copy=False: then

@@ -132,3 +132,80 @@ def test_plan_reports_overflow_and_nan(snn):
     plan.run()
     for s, got in zip(sets, plan.result()):
         _eq(got, oracle.brute_radius(s.P, s.Q, s.R), s.name)
+
+
+def _plan(snn, sets, prec, cap=1 << 22):
+    idx = snn.build_batch([_dev(s.P) for s in sets])
+    ms = [None if s.Q is None else s.Q.shape[0] for s in sets]
+    plan = snn.BatchPlan(idx, ms, [s.R for s in sets], precision=prec, survivor_capacity=cap,
+                         nnz_capacity=cap)
+    for t, s in enumerate(sets):
+        if s.Q is not None:
+            plan.queries(t).copy_(_dev(s.Q))
+    return idx, plan
+
+
+def test_plan_tensor_core_groups(snn, tmp_path, monkeypatch):
+    """With 16-bit precision the out-of-sample sets of d <= 48 are scored by
+    tensor-core groups (one per rounded width); sets of several query tiles
+    with odd tile counts (padded tile pairs), a self-join set and a d = 64
+    set left to the FP32 scorer.  Every group choice the tuner tries ends in
+    the oracle's result; a tuned choice is stored in the SNN_TUNE_CACHE file
+    and a second plan of the same shape takes it from there."""
+    rng = np.random.default_rng(41)
+    sets = []
+    for d, n, m in [(2, 3000, 700), (3, 2500, 300), (8, 4000, 390), (32, 3500, 520), (40, 2000, 260),
+                    (16, 1500, 129), (24, 1800, 1)]:
+        c = rng.uniform(-8, 8, size=(5, d))
+        P = (c[rng.integers(0, 5, n)] + rng.standard_normal((n, d))).astype(np.float32)
+        Q = (c[rng.integers(0, 5, m)] + rng.standard_normal((m, d))).astype(np.float32)
+        R = float(np.quantile(np.linalg.norm(P[:300, None] - P[None, :300], axis=2), 0.01))
+        sets.append(wl.Workload(f"d{d}", P, Q, R))
+    sets.append(wl.Workload("self", rng.standard_normal((900, 8)).astype(np.float32), None, 0.6))
+    sets.append(wl.Workload("d64", rng.standard_normal((600, 64)).astype(np.float32),
+                            rng.standard_normal((70, 64)).astype(np.float32), 9.0))
+    refs = [oracle.brute_radius(s.P, s.Q, s.R) for s in sets]
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("SNN_TUNE_CACHE", str(cache))
+    idx, plan = _plan(snn, sets, "bf16")
+    cfg = plan.config()
+    assert cfg["tc_groups"] == 3 and cfg["tc_mask"] == 7
+    plan.run()
+    for s, got, ref in zip(sets, plan.result(), refs):
+        _eq(got, ref, f"tc run {s.name}")
+    cpi, ctas, ms_best = plan.tune()
+    assert ms_best > 0 and not plan.config()["from_cache"]
+    plan.launch_graph()
+    for s, got, ref in zip(sets, plan.result(), refs):
+        _eq(got, ref, f"tuned {s.name}")
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and '"tc_mask"' in lines[0]
+    plan.close()
+    idx2, plan2 = _plan(snn, sets, "bf16")
+    cpi2, ctas2, ms2 = plan2.tune()
+    cfg2 = plan2.config()
+    assert cfg2["from_cache"] and ms2 == 0 and (cpi2, ctas2) == (cpi, ctas)
+    plan2.run()
+    for s, got, ref in zip(sets, plan2.result(), refs):
+        _eq(got, ref, f"cached {s.name}")
+    plan2.close()
+
+
+def test_plan_tensor_core_query_range(snn):
+    """A query far beyond the FP16 range of its set's scaled operands is
+    reported (SNN_ENOTSUP) instead of scored; the FP32 plan answers it."""
+    rng = np.random.default_rng(42)
+    P = rng.standard_normal((2000, 8)).astype(np.float32)
+    Q = rng.standard_normal((200, 8)).astype(np.float32)
+    Q[17] *= 1e4
+    sets = [wl.Workload("far", P, Q, 1.0)]
+    _, plan = _plan(snn, sets, "bf16")
+    plan.run()
+    with pytest.raises(snn.SNNError) as e:
+        plan.result()
+    assert e.value.status == snn.SNN_ENOTSUP
+    plan.close()
+    _, plan = _plan(snn, sets, "fp32")
+    plan.run()
+    _eq(plan.result()[0], oracle.brute_radius(P, Q, 1.0), "fp32 far")
+    plan.close()
