@@ -410,8 +410,10 @@ __device__ __forceinline__ double dist2_fp64(const float4 *pp, const float4 *pq,
 }
 
 // Survivor s of min(*count, cap) (grid-stride: the count is read on the
-// device); rec_pos[cap + s] holds the slot in the mirrored row.
-template <bool kSym>
+// device); rec_pos[cap + s] holds the slot in the mirrored row.  NQ bounds
+// the float4 columns of a row (dp / 4): every load of both rows is issued
+// before the arithmetic.
+template <bool kSym, int NQ>
 __device__ __forceinline__ void decide_one_survivor(
          int64_t s, const uint2 *__restrict__ surv, int64_t cap, const float *__restrict__ qraw,
          const int32_t *__restrict__ qorder, const float *__restrict__ praw,
@@ -424,10 +426,18 @@ __device__ __forceinline__ void decide_one_survivor(
     const double R2e = R2q ? R2q[e.x] : R2;
     const float4 *pq = reinterpret_cast<const float4 *>(qraw + int64_t(e.x) * dp);
     const float4 *pp = reinterpret_cast<const float4 *>(praw + int64_t(e.y) * dp);
+    float4 ra[NQ], rb[NQ];
+#pragma unroll
+    for (int k4 = 0; k4 < NQ; ++k4) {
+        const bool in = k4 < dp / 4;
+        ra[k4] = in ? pp[k4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        rb[k4] = in ? pq[k4] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     float H = 0.f, L = 0.f;
     bool nz = false;
-    for (int k4 = 0; k4 < dp / 4; ++k4) {
-        const float4 a = pp[k4], b = pq[k4];
+#pragma unroll
+    for (int k4 = 0; k4 < NQ; ++k4) {
+        const float4 a = ra[k4], b = rb[k4];
         const float av[4] = {a.x, a.y, a.z, a.w};
         const float bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
@@ -471,7 +481,7 @@ __device__ __forceinline__ void decide_one_survivor(
     if (kSym) rec_pos[cap + s] = p1;
 }
 
-template <bool kSym>
+template <bool kSym, int NQ>
 __device__ __forceinline__ void decide_body(
          const uint2 *__restrict__ surv, const unsigned long long *__restrict__ count, int64_t cap,
          const float *__restrict__ qraw, const int32_t *__restrict__ qorder,
@@ -483,8 +493,8 @@ __device__ __forceinline__ void decide_body(
     const int64_t nsurv = min((int64_t)*count, cap);
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < nsurv; s += stride)
-        decide_one_survivor<kSym>(s, surv, cap, qraw, qorder, praw, porder, d, dp, R2, dc, R2q, dcq,
-                                  rec_d2, rec_pos, rec_rc, counts, n_fp64);
+        decide_one_survivor<kSym, NQ>(s, surv, cap, qraw, qorder, praw, porder, d, dp, R2, dc, R2q, dcq,
+                                      rec_d2, rec_pos, rec_rc, counts, n_fp64);
 }
 
 // The same decision with G lanes per survivor for long rows: lane l
@@ -625,11 +635,18 @@ __device__ __forceinline__ void decide_group_body(
         unsigned long long *__restrict__ n_fp64
 #define SNN_DECIDE_PASS surv, count, cap, qraw, qorder, praw, porder, d, dp, R2, dc, R2q, dcq,  \
                         rec_d2, rec_pos, rec_rc, counts, n_fp64
+// one lane per survivor: rows of up to 16 floats (4 float4 columns) or 32
 __global__ void __launch_bounds__(256) k_decide_sym(SNN_DECIDE_ARGS) {
-    decide_body<true>(SNN_DECIDE_PASS);
+    decide_body<true, 4>(SNN_DECIDE_PASS);
 }
 __global__ void __launch_bounds__(256) k_decide_one(SNN_DECIDE_ARGS) {
-    decide_body<false>(SNN_DECIDE_PASS);
+    decide_body<false, 4>(SNN_DECIDE_PASS);
+}
+__global__ void __launch_bounds__(256) k_decide_sym_w(SNN_DECIDE_ARGS) {
+    decide_body<true, 8>(SNN_DECIDE_PASS);
+}
+__global__ void __launch_bounds__(256) k_decide_one_w(SNN_DECIDE_ARGS) {
+    decide_body<false, 8>(SNN_DECIDE_PASS);
 }
 __global__ void __launch_bounds__(256) k_decide_sym_g8(SNN_DECIDE_ARGS) {
     decide_group_body<true, 8>(SNN_DECIDE_PASS);
@@ -658,16 +675,32 @@ __global__ void k_counts_to_i64(const int32_t *__restrict__ counts, int64_t m,
 __global__ void k_scatter(const uint2 *__restrict__ rec_rc, const int32_t *__restrict__ rec_pos,
                           const float *__restrict__ rec_d2, int64_t nsurv, int64_t rstride, int sym,
                           const int64_t *__restrict__ offsets, uint64_t *__restrict__ tmp) {
-    const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (s >= nsurv) return;
-    const int32_t p0 = rec_pos[s];
-    if (p0 < 0) return;
-    const uint2 rc = rec_rc[s];
-    const uint64_t vb = __float_as_uint(rec_d2[s]);
-    tmp[offsets[rc.x] + p0] = (uint64_t(rc.y) << 32) | vb;
-    if (sym) {
-        const int32_t p1 = rec_pos[rstride + s];
-        if (p1 >= 0) tmp[offsets[rc.y] + p1] = (uint64_t(rc.x) << 32) | vb;
+    // four survivors per thread, every load independent of the others (the
+    // chain is rec arrays -> row offset -> store)
+    constexpr int U = 4;
+    const int64_t base = (int64_t(blockIdx.x) * blockDim.x) * U + threadIdx.x;
+    int32_t p0[U], p1[U];
+    uint2 rc[U];
+    uint32_t vb[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int64_t s = base + int64_t(u) * blockDim.x;
+        const bool in = s < nsurv;
+        p0[u] = in ? rec_pos[s] : -1;
+        p1[u] = (in && sym) ? rec_pos[rstride + s] : -1;
+        rc[u] = in ? rec_rc[s] : make_uint2(0u, 0u);
+        vb[u] = in ? __float_as_uint(rec_d2[s]) : 0u;
+    }
+    int64_t o0[U], o1[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        o0[u] = p0[u] >= 0 ? offsets[rc[u].x] : 0;
+        o1[u] = p1[u] >= 0 ? offsets[rc[u].y] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (p0[u] >= 0) tmp[o0[u] + p0[u]] = (uint64_t(rc[u].y) << 32) | vb[u];
+        if (p1[u] >= 0) tmp[o1[u] + p1[u]] = (uint64_t(rc[u].x) << 32) | vb[u];
     }
 }
 
@@ -679,25 +712,33 @@ __global__ void k_seg_classify(const int64_t *__restrict__ offsets, int64_t m,
                                int32_t *__restrict__ lists, int32_t *__restrict__ big_list,
                                int64_t *__restrict__ big_len, unsigned *__restrict__ counters) {
     const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (r >= m) return;
-    const int64_t len = offsets[r + 1] - offsets[r];
-    if (len == 0) return;
-    if (len <= kSegSmall) {
-        lists[atomicAdd(&counters[0], 1u)] = (int32_t)r;
-    } else if (len <= 2 * kSegSmall) {
-        lists[5 * m + atomicAdd(&counters[6], 1u)] = (int32_t)r;
-    } else if (len <= 4 * kSegSmall) {
-        lists[m + atomicAdd(&counters[1], 1u)] = (int32_t)r;
-    } else if (len <= 8 * kSegSmall) {
-        lists[4 * m + atomicAdd(&counters[5], 1u)] = (int32_t)r;
-    } else if (len <= 16 * kSegSmall) {
-        lists[2 * m + atomicAdd(&counters[2], 1u)] = (int32_t)r;
-    } else if (len <= kSegMid) {
-        lists[3 * m + atomicAdd(&counters[3], 1u)] = (int32_t)r;
+    const int64_t len = r < m ? offsets[r + 1] - offsets[r] : 0;
+    // class of the row (counter index; -1: empty), and its list slot
+    int c = -1, slot = 0;
+    if (len > 0) {
+        if (len <= kSegSmall) c = 0, slot = 0;
+        else if (len <= 2 * kSegSmall) c = 6, slot = 5;
+        else if (len <= 4 * kSegSmall) c = 1, slot = 1;
+        else if (len <= 8 * kSegSmall) c = 5, slot = 4;
+        else if (len <= 16 * kSegSmall) c = 2, slot = 2;
+        else if (len <= kSegMid) c = 3, slot = 3;
+        else c = 4;
+    }
+    // one atomic per class present in the warp: lanes of a class take
+    // consecutive positions after the leader's reservation
+    const unsigned peers = __match_any_sync(0xffffffffu, c);
+    const int leader = __ffs(peers) - 1;
+    const int lane = threadIdx.x & 31;
+    unsigned base = 0;
+    if (c >= 0 && lane == leader) base = atomicAdd(&counters[c], unsigned(__popc(peers)));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (c < 0) return;
+    const unsigned pos = base + __popc(peers & lanemask_lt());
+    if (c == 4) {
+        big_list[pos] = (int32_t)r;
+        big_len[pos] = len;
     } else {
-        const unsigned b = atomicAdd(&counters[4], 1u);
-        big_list[b] = (int32_t)r;
-        big_len[b] = len;
+        lists[int64_t(slot) * m + pos] = (int32_t)r;
     }
 }
 

@@ -187,6 +187,8 @@ __device__ __forceinline__ int decide_df(float H, float L, bool nz, const Decide
                          unsigned long long *n_fp64)
 SNN_DECIDE_DECL(k_decide_sym);
 SNN_DECIDE_DECL(k_decide_one);
+SNN_DECIDE_DECL(k_decide_sym_w);
+SNN_DECIDE_DECL(k_decide_one_w);
 SNN_DECIDE_DECL(k_decide_sym_g8);
 SNN_DECIDE_DECL(k_decide_one_g8);
 SNN_DECIDE_DECL(k_decide_sym_g32);

@@ -1015,7 +1015,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     // dimensions, 32 beyond (four lanes at d = 16 measured slower: 1.16
     // against 0.85 ms on the 10^6-point self-join)
     const int G = d <= 32 ? 1 : (d <= 128 ? 8 : 32);
-    auto dk = G == 1 ? (sym ? k_decide_sym : k_decide_one)
+    auto dk = G == 1 ? (dp <= 16 ? (sym ? k_decide_sym : k_decide_one) : (sym ? k_decide_sym_w : k_decide_one_w))
                      : (G == 8 ? (sym ? k_decide_sym_g8 : k_decide_one_g8)
                                : (sym ? k_decide_sym_g32 : k_decide_one_g32));
     // one host read-back per attempt (see Readback)
@@ -1137,7 +1137,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         TRY_Q(dev_alloc(&out->dist2, nnz, s));
         uint64_t *tmp;
         TRY_Q(scr.alloc(&tmp, nnz));
-        SNN_LAUNCH(k_scatter, grid_for(nsurv, 256), 256, 0, s)(rec_rc, rec_pos, rec_d2, nsurv, cap,
+        SNN_LAUNCH(k_scatter, grid_for(nsurv, 1024), 256, 0, s)(rec_rc, rec_pos, rec_d2, nsurv, cap,
                                                                sym, out->offsets, tmp);
         CUDA_Q(cudaGetLastError());
         // per-row ascending column ids, in place; classes with no rows are
