@@ -102,7 +102,7 @@ __host__ __device__ constexpr int tc_threads(int mt, int bn, bool ares) {
 // SM): four when they fit (the MMAs of three chunks then cover the hand-back
 // latency of the fourth), else two
 __host__ __device__ constexpr int tc_nbuf(int mt, int bn, int cps) {
-    return 4 * mt * bn <= 512 / cps ? 4 : 2;
+    return 4 * mt * bn <= 512 / cps ? 4 : (2 * mt * bn <= 512 / cps ? 2 : 1);
 }
 constexpr int kExtra = 9;           // folded columns
 // dynamic shared memory per CTA (minus base alignment and barriers) for 1
@@ -164,15 +164,16 @@ struct TcShape {
         size_t(kAResBytes) + size_t(kStages) * kStageBytes + kAlign + 512 + kStgBytes;
     static_assert(kStagesRaw >= 2, "shape does not fit shared memory");
     static_assert(ARES || NW == BK, "narrow parts need a resident query tile");
-    static_assert(MT == 1 || ARES, "several query tiles per item need a resident query tile");
+    static_assert(MT == 1 || ARES || NSPLIT == 1,
+                  "several streamed query tiles per item: one FP16 part only");
     static_assert(kTmemCols * CPS <= 512, "accumulators exceed TMEM");
-    static_assert(kNBuf % 2 == 0, "two MMA issuers own alternate accumulator buffers");
+    static_assert(!ARES || kNBuf % 2 == 0, "two MMA issuers own alternate accumulator buffers");
     static_assert(!ARES || kStagesRaw >= 2, "two issuers need two stages");
     static_assert(NW == 16 || NW == 32 || NW == 64, "unsupported part width");
     static_assert(!F8NP || ((BK == 16 || BK == 32) && NW == BK && !ARES && MT == 1), "FP8 shape");
     static_assert(!F8NP || (NSPLIT == 2 && (F8NP == 3 || F8NP == 4)) || (NSPLIT == 3 && F8NP == 6),
                   "FP8 products");
-    static_assert(NSPLIT != 1 || (!F8NP && !ARES && MT == 1 && NW == BK && BK == 32),
+    static_assert(NSPLIT != 1 || (!F8NP && !ARES && (MT == 1 || MT == 2) && NW == BK && BK == 32),
                   "one FP16 part: streamed shape with 32-column k-blocks");
 };
 
@@ -337,7 +338,7 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                         if (!mbar_wait(empty_bar(s), (round & 1u) ^ 1u, s_abort, a.err)) break;
                         if (Sh::kFoldBlock && kb == a.nkb - 1) {
                             // folded BF16 columns, 32 bytes per row, in part 1's slots
-                            mbar_expect_tx(full_bar(s), uint32_t((kTM + BN) * 32));
+                            mbar_expect_tx(full_bar(s), uint32_t((kTM * MT + BN) * 32));
                             tma_load_2d(a_tile(s, 0), &qf, 0, int(f.q0), full_bar(s));
                             tma_load_2d(b_tile(s, 0), &xf, 0, int(j0), full_bar(s));
                         } else {
@@ -383,19 +384,27 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                         if (!(ok = mbar_wait(full_bar(s), round & 1u, s_abort, a.err))) break;
                         tmem_fence_after();
                         if constexpr (NSPLIT == 1) {
+                            // query tile h of the item: 128 rows further into the A tile,
+                            // its own accumulator columns
                             if (kb == a.nkb - 1) {
                                 // the folded columns: one BF16 K = 16 step
-                                mma_bf16(dt0, smem_desc<32>(a_tile(s, 0)), smem_desc<32>(b_tile(s, 0)),
-                                         kIdesc, 1u);
+#pragma unroll
+                                for (int h = 0; h < MT; ++h)
+                                    mma_bf16(dt0 + uint32_t(h * BN), smem_desc<32>(a_tile(s, 0) + uint32_t(h * kTM * 32)),
+                                             smem_desc<32>(b_tile(s, 0)), kIdesc, 1u);
                             } else {
 #pragma unroll
                                 for (int ks = 0; ks < Sh::kKSteps; ++ks) {
                                     // FP16 data k steps; the last block may hold one
                                     const int kg = kb * Sh::kKSteps + ks;
                                     if (kg >= a.ksteps_data) break;
-                                    mma_bf16(dt0, smem_desc<Sh::kRowBytes>(a_tile(s, 0) + 32u * ks),
-                                             smem_desc<Sh::kRowBytes>(b_tile(s, 0) + 32u * ks), kIdescF16,
-                                             kg != 0 ? 1u : 0u);
+                                    const uint64_t bd = smem_desc<Sh::kRowBytes>(b_tile(s, 0) + 32u * ks);
+#pragma unroll
+                                    for (int h = 0; h < MT; ++h)
+                                        mma_bf16(dt0 + uint32_t(h * BN),
+                                                 smem_desc<Sh::kRowBytes>(a_tile(s, 0) +
+                                                                          uint32_t(h * kTM * Sh::kRowBytes) + 32u * ks),
+                                                 bd, kIdescF16, kg != 0 ? 1u : 0u);
                                 }
                             }
                         } else if constexpr (F8NP != 0) {
@@ -1357,18 +1366,43 @@ snn_status h1_score_launch(snn_index *ix, const ScoreArgs &sa, cudaStream_t s, d
     SNN_LAUNCH(k_h1_pack, pack_grid(m), pack_threads, 0, s)(sa.q.xc, ix->dp, nullptr, Aq, m, d, K2, ch, kacc,
                                                            1, qp, qfold);
     SNN_LAUNCH_CHECK();
+    // two query tiles per work item by default: each band k-block feeds four
+    // 128 x 256 MMAs (32 KB per k-block instead of 24 KB for two), the
+    // accumulators fill TMEM in one buffer (a chunk of ~26 k-blocks makes the
+    // hand-off a small fraction of its MMAs); SNN_H1_TILES=1 keeps one tile
+    const char *et = getenv("SNN_H1_TILES");
+    const int MTq = (et && et[0] == '1') ? 1 : 2;
     CUtensorMap maps[8];
-    SNN_TRY(make_map(&maps[0], qp, m, K2, 32, kTM));
+    SNN_TRY(make_map(&maps[0], qp, m, K2, 32, kTM * MTq));
     SNN_TRY(make_map(&maps[3], static_cast<const uint16_t *>(op->part[0]), ix->n, K2, 32, 256));
     maps[1] = maps[2] = maps[0];
     maps[4] = maps[5] = maps[3];
-    SNN_TRY(make_map(&maps[6], qfold, m, 16, 16, kTM));
+    SNN_TRY(make_map(&maps[6], qfold, m, 16, 16, kTM * MTq));
     SNN_TRY(make_map(&maps[7], op->fold, ix->n, 16, 16, 256));
     TileSet ts{sa.tile_lo, sa.tile_hi, sa.item_off, sa.item_tile, sa.ntiles};
+    if (MTq == 2) {
+        const int ng = int(cdiv(sa.ntiles, 2));
+        int64_t *lo2, *hi2, *items2, *off2;
+        int32_t *it2;
+        SNN_TRY(scr.alloc(&lo2, ng));
+        SNN_TRY(scr.alloc(&hi2, ng));
+        SNN_TRY(scr.alloc(&items2, ng));
+        SNN_TRY(scr.alloc(&off2, ng + 1));
+        SNN_LAUNCH(k_group_band, unsigned(cdiv(ng, 128)), 128, 0, s)(sa.tile_lo, sa.tile_hi, sa.ntiles, 2, lo2,
+                                                                     hi2, items2, ng);
+        SNN_LAUNCH_CHECK();
+        SNN_TRY(scan_exclusive<int64_t>(items2, off2, ng, s));
+        const int64_t max_items = int64_t(ng) * (cdiv(ix->n, int64_t(kBR) * kChunksPerItem) + 1);
+        SNN_TRY(scr.alloc(&it2, max_items));
+        SNN_LAUNCH(k_item_tiles, unsigned(cdiv(ng, 128)), 128, 0, s)(off2, ng, it2);
+        SNN_LAUNCH_CHECK();
+        ts = TileSet{lo2, hi2, off2, it2, ng};
+    }
     TcArgs a = tc_args(ix, sa, ts);
     a.ksteps_data = ksteps;
     a.nkb = int(cdiv(K2, 32)) + 1;
-    return run_tc<1, 32, 256, false, 1, 32, 1, 0>(maps, a, sa, s);
+    return MTq == 2 ? run_tc<1, 32, 256, false, 1, 32, 2, 0>(maps, a, sa, s)
+                    : run_tc<1, 32, 256, false, 1, 32, 1, 0>(maps, a, sa, s);
 }
 
 }  // namespace

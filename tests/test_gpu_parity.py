@@ -608,10 +608,14 @@ def test_fp16_single_part_scaling_and_small_values(snn, monkeypatch, d):
     assert_csr_equal(got, ref, f"d={d} large R")
 
 
-def test_lowrank_img_single_part_default(snn):
+@pytest.mark.parametrize("tiles", ["2", "1"])
+def test_lowrank_img_single_part_default(snn, monkeypatch, tiles):
     """On the image-like data the automatic choice is one FP16 part per row
     (one MMA per k step); the set equals the oracle's and the survivors stay
-    within a small multiple of the neighbour pairs."""
+    within a small multiple of the neighbour pairs, with two query tiles per
+    work item (the default, 47 tiles: the last group half empty) and with
+    one (SNN_H1_TILES=1)."""
+    monkeypatch.setenv("SNN_H1_TILES", tiles)
     w = wl.lowrank_img(n=6007, sub=2000)
     got = _run(snn, w.P, None, w.R, "bf16")
     assert got.stats["split_used"] == snn.SNN_SPLIT_FP16X1
