@@ -663,13 +663,14 @@ snn_status batch_query(int32_t nsets, const snn_index *const *idx, const float *
                                                                       big_len, cls);
         const unsigned wgrid = std::min<unsigned>(unsigned(cdiv(M * 32, 256)), 16384);
         const uint32_t ib = ids_bound(sd);
-        SNN_LAUNCH(k_seg_sort_w1, wgrid, 256, 0, s)(lists, cls, goff, tmp, gidx, gd2, ib);
-        SNN_LAUNCH(k_seg_sort_w2, wgrid, 256, 0, s)(lists + 5 * M, cls + 6, goff, tmp, gidx, gd2, ib);
-        SNN_LAUNCH(k_seg_sort_w4, wgrid, 256, 0, s)(lists + M, cls + 1, goff, tmp, gidx, gd2, ib);
-        SNN_LAUNCH(k_seg_sort_w8, wgrid, 256, 0, s)(lists + 4 * M, cls + 5, goff, tmp, gidx, gd2, ib);
-        SNN_LAUNCH(k_seg_sort_w16, wgrid, 256, 0, s)(lists + 2 * M, cls + 2, goff, tmp, gidx, gd2, ib);
+        const SegMap gm{goff, goff, nullptr};
+        SNN_LAUNCH(k_seg_sort_w1, wgrid, 256, 0, s)(lists, cls, gm, tmp, gidx, gd2, ib);
+        SNN_LAUNCH(k_seg_sort_w2, wgrid, 256, 0, s)(lists + 5 * M, cls + 6, gm, tmp, gidx, gd2, ib);
+        SNN_LAUNCH(k_seg_sort_w4, wgrid, 256, 0, s)(lists + M, cls + 1, gm, tmp, gidx, gd2, ib);
+        SNN_LAUNCH(k_seg_sort_w8, wgrid, 256, 0, s)(lists + 4 * M, cls + 5, gm, tmp, gidx, gd2, ib);
+        SNN_LAUNCH(k_seg_sort_w16, wgrid, 256, 0, s)(lists + 2 * M, cls + 2, gm, tmp, gidx, gd2, ib);
         SNN_LAUNCH(k_seg_sort_mid, std::min<unsigned>(unsigned(M), 4096), 256, 0, s)(
-            lists + 3 * M, cls + 3, goff, tmp, gidx, gd2, ib);
+            lists + 3 * M, cls + 3, gm, tmp, gidx, gd2, ib);
         unsigned hcls[8];
         if (cudaMemcpyAsync(hcls, cls, sizeof(hcls), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
@@ -692,14 +693,13 @@ snn_status batch_query(int32_t nsets, const snn_index *const *idx, const float *
             if (st == SNN_OK) st = scr.alloc(&bva, tot);
             if (st == SNN_OK) st = scr.alloc(&bd2, tot);
             if (st != SNN_OK) return fail(st);
-            SNN_LAUNCH(k_seg_big_gather, nbig, 256, 0, s)(big_list, nbig, goff, toff, tmp, bk, bv,
-                                                          bd2);
+            SNN_LAUNCH(k_seg_big_gather, nbig, 256, 0, s)(big_list, nbig, gm, toff, tmp, bk, bv, bd2);
             int bits = 32;
             while ((int64_t(1) << (bits - 32)) < nbig) ++bits;
             if ((st = radix_sort_pairs<uint64_t>(bk, bv, bka, bva, tot, bits, s)) != SNN_OK)
                 return fail(st);
             SNN_LAUNCH(k_seg_big_scatter, unsigned(cdiv(tot, 256)), 256, 0, s)(
-                bk, bv, tot, big_list, goff, toff, bd2, gidx, gd2);
+                bk, bv, tot, big_list, gm, toff, bd2, gidx, gd2);
         }
     }
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
@@ -929,17 +929,18 @@ snn_status plan_enqueue(snn_batch_plan *p, cudaStream_t s) {
     SNN_LAUNCH_CHECK();
     const unsigned wgrid = unsigned(std::min<int64_t>(cdiv(std::max<int64_t>(M, 1) * 32, 256), 16384));
     const uint32_t ib = ids_bound(p->sd);
-    SNN_LAUNCH(k_seg_sort_w1, wgrid, 256, 0, s)(p->lists, p->cls, p->goff, p->tmp, p->gidx, p->gd2, ib);
-    SNN_LAUNCH(k_seg_sort_w2, wgrid, 256, 0, s)(p->lists + 5 * M, p->cls + 6, p->goff, p->tmp, p->gidx,
+    const SegMap gm{p->goff, p->goff, nullptr};
+    SNN_LAUNCH(k_seg_sort_w1, wgrid, 256, 0, s)(p->lists, p->cls, gm, p->tmp, p->gidx, p->gd2, ib);
+    SNN_LAUNCH(k_seg_sort_w2, wgrid, 256, 0, s)(p->lists + 5 * M, p->cls + 6, gm, p->tmp, p->gidx,
                                                  p->gd2, ib);
-    SNN_LAUNCH(k_seg_sort_w4, wgrid, 256, 0, s)(p->lists + M, p->cls + 1, p->goff, p->tmp, p->gidx,
+    SNN_LAUNCH(k_seg_sort_w4, wgrid, 256, 0, s)(p->lists + M, p->cls + 1, gm, p->tmp, p->gidx,
                                                  p->gd2, ib);
-    SNN_LAUNCH(k_seg_sort_w8, wgrid, 256, 0, s)(p->lists + 4 * M, p->cls + 5, p->goff, p->tmp, p->gidx,
+    SNN_LAUNCH(k_seg_sort_w8, wgrid, 256, 0, s)(p->lists + 4 * M, p->cls + 5, gm, p->tmp, p->gidx,
                                                  p->gd2, ib);
-    SNN_LAUNCH(k_seg_sort_w16, wgrid, 256, 0, s)(p->lists + 2 * M, p->cls + 2, p->goff, p->tmp,
+    SNN_LAUNCH(k_seg_sort_w16, wgrid, 256, 0, s)(p->lists + 2 * M, p->cls + 2, gm, p->tmp,
                                                   p->gidx, p->gd2, ib);
     SNN_LAUNCH(k_seg_sort_mid, unsigned(std::min<int64_t>(std::max<int64_t>(M, 1), 4096)), 256, 0, s)(
-        p->lists + 3 * M, p->cls + 3, p->goff, p->tmp, p->gidx, p->gd2, ib);
+        p->lists + 3 * M, p->cls + 3, gm, p->tmp, p->gidx, p->gd2, ib);
     if (M > 0)
         SNN_LAUNCH(k_b_offsets, unsigned(cdiv(M, 256)), 256, 0, s)(p->goff, p->d_qglob, nsets, M,
                                                                    p->out_off, p->d_offpos);

@@ -416,11 +416,10 @@ __device__ __forceinline__ double dist2_fp64(const float4 *pp, const float4 *pq,
 template <bool kSym, int NQ>
 __device__ __forceinline__ void decide_one_survivor(
          int64_t s, const uint2 *__restrict__ surv, int64_t cap, const float *__restrict__ qraw,
-         const int32_t *__restrict__ qorder, const float *__restrict__ praw,
-         const int32_t *__restrict__ porder, int d, int dp, double R2, const DecideConsts &dc0,
+         const float *__restrict__ praw, int d, int dp, double R2, const DecideConsts &dc0,
          const double *__restrict__ R2q, const DecideConsts *__restrict__ dcq,
-         float *__restrict__ rec_d2, int32_t *__restrict__ rec_pos, uint2 *__restrict__ rec_rc,
-         int32_t *__restrict__ counts, unsigned long long *__restrict__ n_fp64) {
+         float *__restrict__ rec_d2, int32_t *__restrict__ rec_pos, int32_t *__restrict__ counts,
+         unsigned long long *__restrict__ n_fp64) {
     const uint2 e = surv[s];
     const DecideConsts dc = dcq ? dcq[e.x] : dc0;
     const double R2e = R2q ? R2q[e.x] : R2;
@@ -466,15 +465,15 @@ __device__ __forceinline__ void decide_one_survivor(
         atomicAdd(n_fp64, 1ull);
     }
     const bool accept = v == 1;
-    // record: dist2 and the slot of the pair within its row (from the
-    // counting atomic, so the scatter needs no atomics); -1 = not a neighbour.
-    // A symmetric self-join pair also takes a slot in the mirrored row.
+    // record: dist2 and the slot of the pair within its row of sorted
+    // positions (from the counting atomic, so the scatter needs no atomics);
+    // -1 = not a neighbour.  A symmetric self-join pair also takes a slot in
+    // the mirrored row.  Neighbouring survivors share rows (one query tile),
+    // so the atomics stay within a few cache lines.
     int32_t p0 = -1, p1 = -1;
     if (accept) {
-        const int32_t row = qorder[e.x], col = porder[e.y];
-        p0 = atomicAdd(&counts[row], 1);
-        if (kSym && e.x != e.y) p1 = atomicAdd(&counts[col], 1);
-        rec_rc[s] = make_uint2(uint32_t(row), uint32_t(col));
+        p0 = atomicAdd(&counts[e.x], 1);
+        if (kSym && e.x != e.y) p1 = atomicAdd(&counts[e.y], 1);
     }
     rec_d2[s] = d2;
     rec_pos[s] = p0;
@@ -484,17 +483,15 @@ __device__ __forceinline__ void decide_one_survivor(
 template <bool kSym, int NQ>
 __device__ __forceinline__ void decide_body(
          const uint2 *__restrict__ surv, const unsigned long long *__restrict__ count, int64_t cap,
-         const float *__restrict__ qraw, const int32_t *__restrict__ qorder,
-         const float *__restrict__ praw, const int32_t *__restrict__ porder, int d, int dp,
-         double R2, const DecideConsts &dc, const double *__restrict__ R2q,
-         const DecideConsts *__restrict__ dcq, float *__restrict__ rec_d2,
-         int32_t *__restrict__ rec_pos, uint2 *__restrict__ rec_rc, int32_t *__restrict__ counts,
+         const float *__restrict__ qraw, const float *__restrict__ praw, int d, int dp, double R2,
+         const DecideConsts &dc, const double *__restrict__ R2q, const DecideConsts *__restrict__ dcq,
+         float *__restrict__ rec_d2, int32_t *__restrict__ rec_pos, int32_t *__restrict__ counts,
          unsigned long long *__restrict__ n_fp64) {
     const int64_t nsurv = min((int64_t)*count, cap);
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < nsurv; s += stride)
-        decide_one_survivor<kSym, NQ>(s, surv, cap, qraw, qorder, praw, porder, d, dp, R2, dc, R2q, dcq,
-                                      rec_d2, rec_pos, rec_rc, counts, n_fp64);
+        decide_one_survivor<kSym, NQ>(s, surv, cap, qraw, praw, d, dp, R2, dc, R2q, dcq, rec_d2, rec_pos,
+                                      counts, n_fp64);
 }
 
 // The same decision with G lanes per survivor for long rows: lane l
@@ -508,11 +505,9 @@ __device__ __forceinline__ void decide_body(
 template <bool kSym, int G>
 __device__ __forceinline__ void decide_group_body(
          const uint2 *__restrict__ surv, const unsigned long long *__restrict__ count, int64_t cap,
-         const float *__restrict__ qraw, const int32_t *__restrict__ qorder,
-         const float *__restrict__ praw, const int32_t *__restrict__ porder, int d, int dp,
-         double R2, const DecideConsts &dc0, const double *__restrict__ R2q,
-         const DecideConsts *__restrict__ dcq, float *__restrict__ rec_d2,
-         int32_t *__restrict__ rec_pos, uint2 *__restrict__ rec_rc, int32_t *__restrict__ counts,
+         const float *__restrict__ qraw, const float *__restrict__ praw, int d, int dp, double R2,
+         const DecideConsts &dc0, const double *__restrict__ R2q, const DecideConsts *__restrict__ dcq,
+         float *__restrict__ rec_d2, int32_t *__restrict__ rec_pos, int32_t *__restrict__ counts,
          unsigned long long *__restrict__ n_fp64) {
     constexpr int GPW = 32 / G;   // groups per warp
     const int64_t nsurv = min((int64_t)*count, cap);
@@ -614,10 +609,8 @@ __device__ __forceinline__ void decide_group_body(
         const bool accept = v == 1;
         int32_t p0 = -1, p1 = -1;
         if (accept) {
-            const int32_t row = qorder[e.x], col = porder[e.y];
-            p0 = atomicAdd(&counts[row], 1);
-            if (kSym && e.x != e.y) p1 = atomicAdd(&counts[col], 1);
-            rec_rc[s] = make_uint2(uint32_t(row), uint32_t(col));
+            p0 = atomicAdd(&counts[e.x], 1);
+            if (kSym && e.x != e.y) p1 = atomicAdd(&counts[e.y], 1);
         }
         rec_d2[s] = d2;
         rec_pos[s] = p0;
@@ -627,14 +620,13 @@ __device__ __forceinline__ void decide_group_body(
 
 #define SNN_DECIDE_ARGS                                                                      \
     const uint2 *__restrict__ surv, const unsigned long long *__restrict__ count, int64_t cap, \
-        const float *__restrict__ qraw, const int32_t *__restrict__ qorder,                    \
-        const float *__restrict__ praw, const int32_t *__restrict__ porder, int d, int dp,     \
+        const float *__restrict__ qraw, const float *__restrict__ praw, int d, int dp,         \
         double R2, DecideConsts dc, const double *__restrict__ R2q,                            \
         const DecideConsts *__restrict__ dcq, float *__restrict__ rec_d2,                      \
-        int32_t *__restrict__ rec_pos, uint2 *__restrict__ rec_rc, int32_t *__restrict__ counts, \
+        int32_t *__restrict__ rec_pos, int32_t *__restrict__ counts,                           \
         unsigned long long *__restrict__ n_fp64
-#define SNN_DECIDE_PASS surv, count, cap, qraw, qorder, praw, porder, d, dp, R2, dc, R2q, dcq,  \
-                        rec_d2, rec_pos, rec_rc, counts, n_fp64
+#define SNN_DECIDE_PASS surv, count, cap, qraw, praw, d, dp, R2, dc, R2q, dcq, rec_d2, rec_pos, counts, \
+                        n_fp64
 // one lane per survivor: rows of up to 16 floats (4 float4 columns) or 32
 __global__ void __launch_bounds__(256) k_decide_sym(SNN_DECIDE_ARGS) {
     decide_body<true, 4>(SNN_DECIDE_PASS);
@@ -669,14 +661,24 @@ __global__ void k_counts_to_i64(const int32_t *__restrict__ counts, int64_t m,
     if (i < m) out[i] = counts[i];
 }
 
+__global__ void k_counts_by_id(const int32_t *__restrict__ counts, const int32_t *__restrict__ order,
+                               int64_t m, int64_t *__restrict__ out) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < m) out[order[i]] = counts[i];
+}
+
 // Writes each accepted pair at its row slot (and the mirrored pair of a
-// symmetric self-join) as one packed entry (id << 32 | dist2 bits) of the
-// row-grouped staging array; the per-row sort writes the output arrays.
-__global__ void k_scatter(const uint2 *__restrict__ rec_rc, const int32_t *__restrict__ rec_pos,
+// symmetric self-join) as one packed entry (column id << 32 | dist2 bits) of
+// the staging array, whose rows are sorted query positions: the rows of a
+// query tile and of its band are neighbours there, so the stores of one
+// stretch of survivors fall into a window of the array that stays in L2.
+// Column ids are the point ids porder[y] (mirrored: the query ids qorder[x]).
+__global__ void k_scatter(const uint2 *__restrict__ surv, const int32_t *__restrict__ rec_pos,
                           const float *__restrict__ rec_d2, int64_t nsurv, int64_t rstride, int sym,
-                          const int64_t *__restrict__ offsets, uint64_t *__restrict__ tmp) {
+                          const int64_t *__restrict__ offsets, const int32_t *__restrict__ qorder,
+                          const int32_t *__restrict__ porder, uint64_t *__restrict__ tmp) {
     // four survivors per thread, every load independent of the others (the
-    // chain is rec arrays -> row offset -> store)
+    // chain is rec arrays -> row offset and column id -> store)
     constexpr int U = 4;
     const int64_t base = (int64_t(blockIdx.x) * blockDim.x) * U + threadIdx.x;
     int32_t p0[U], p1[U];
@@ -688,19 +690,22 @@ __global__ void k_scatter(const uint2 *__restrict__ rec_rc, const int32_t *__res
         const bool in = s < nsurv;
         p0[u] = in ? rec_pos[s] : -1;
         p1[u] = (in && sym) ? rec_pos[rstride + s] : -1;
-        rc[u] = in ? rec_rc[s] : make_uint2(0u, 0u);
+        rc[u] = in ? surv[s] : make_uint2(0u, 0u);
         vb[u] = in ? __float_as_uint(rec_d2[s]) : 0u;
     }
     int64_t o0[U], o1[U];
+    uint32_t c0[U], c1[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         o0[u] = p0[u] >= 0 ? offsets[rc[u].x] : 0;
+        c0[u] = p0[u] >= 0 ? uint32_t(porder[rc[u].y]) : 0u;
         o1[u] = p1[u] >= 0 ? offsets[rc[u].y] : 0;
+        c1[u] = p1[u] >= 0 ? uint32_t(qorder[rc[u].x]) : 0u;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        if (p0[u] >= 0) tmp[o0[u] + p0[u]] = (uint64_t(rc[u].y) << 32) | vb[u];
-        if (p1[u] >= 0) tmp[o1[u] + p1[u]] = (uint64_t(rc[u].x) << 32) | vb[u];
+        if (p0[u] >= 0) tmp[o0[u] + p0[u]] = (uint64_t(c0[u]) << 32) | vb[u];
+        if (p1[u] >= 0) tmp[o1[u] + p1[u]] = (uint64_t(c1[u]) << 32) | vb[u];
     }
 }
 
@@ -807,8 +812,7 @@ __device__ __forceinline__ void bitonic_warp(T (&v)[E], int lane) {
 
 template <int E>
 __device__ __forceinline__ void seg_sort_warp(const int32_t *__restrict__ list, unsigned total,
-                                              const int64_t *__restrict__ offsets,
-                                              const uint64_t *__restrict__ tmp,
+                                              const SegMap &mp, const uint64_t *__restrict__ tmp,
                                               int32_t *__restrict__ idx, float *__restrict__ d2,
                                               uint32_t id_bound) {
     constexpr int N = 32 * E;
@@ -821,8 +825,9 @@ __device__ __forceinline__ void seg_sort_warp(const int32_t *__restrict__ list, 
     const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
     for (int64_t w = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); w < total; w += nw) {
         const int32_t r = list[w];
-        const int64_t o = offsets[r];
-        const int len = int(offsets[r + 1] - o);
+        const int64_t o = mp.src[r];
+        const int len = int(mp.src[r + 1] - o);
+        const int64_t od = mp.dst[mp.rmap ? mp.rmap[r] : r];
         if (k32) {
             uint32_t v[E];
 #pragma unroll
@@ -836,8 +841,8 @@ __device__ __forceinline__ void seg_sort_warp(const int32_t *__restrict__ list, 
                 const int i = lane * E + e;
                 if (i < len) {
                     const uint32_t src = v[e] & uint32_t(N - 1);
-                    idx[o + i] = int32_t(v[e] >> LB);
-                    d2[o + i] = __uint_as_float(w32[2 * (o + src)]);
+                    idx[od + i] = int32_t(v[e] >> LB);
+                    d2[od + i] = __uint_as_float(w32[2 * (o + src)]);
                 }
             }
         } else {
@@ -852,8 +857,8 @@ __device__ __forceinline__ void seg_sort_warp(const int32_t *__restrict__ list, 
             for (int e = 0; e < E; ++e) {
                 const int i = lane * E + e;
                 if (i < len) {
-                    idx[o + i] = int32_t(uint32_t(v[e] >> 32));
-                    d2[o + i] = __uint_as_float(uint32_t(v[e]));
+                    idx[od + i] = int32_t(uint32_t(v[e] >> 32));
+                    d2[od + i] = __uint_as_float(uint32_t(v[e]));
                 }
             }
         }
@@ -861,16 +866,13 @@ __device__ __forceinline__ void seg_sort_warp(const int32_t *__restrict__ list, 
 }
 
 #define SNN_SEG_ARGS                                                                            \
-    const int32_t *__restrict__ list, const unsigned *__restrict__ count,                       \
-        const int64_t *__restrict__ offsets, const uint64_t *__restrict__ tmp, int32_t *idx,   \
-        float *d2, uint32_t id_bound
-__global__ void k_seg_sort_w1(SNN_SEG_ARGS) { seg_sort_warp<1>(list, *count, offsets, tmp, idx, d2, id_bound); }
-__global__ void k_seg_sort_w2(SNN_SEG_ARGS) { seg_sort_warp<2>(list, *count, offsets, tmp, idx, d2, id_bound); }
-__global__ void k_seg_sort_w4(SNN_SEG_ARGS) { seg_sort_warp<4>(list, *count, offsets, tmp, idx, d2, id_bound); }
-__global__ void k_seg_sort_w8(SNN_SEG_ARGS) { seg_sort_warp<8>(list, *count, offsets, tmp, idx, d2, id_bound); }
-__global__ void k_seg_sort_w16(SNN_SEG_ARGS) {
-    seg_sort_warp<16>(list, *count, offsets, tmp, idx, d2, id_bound);
-}
+    const int32_t *__restrict__ list, const unsigned *__restrict__ count, SegMap mp,            \
+        const uint64_t *__restrict__ tmp, int32_t *idx, float *d2, uint32_t id_bound
+__global__ void k_seg_sort_w1(SNN_SEG_ARGS) { seg_sort_warp<1>(list, *count, mp, tmp, idx, d2, id_bound); }
+__global__ void k_seg_sort_w2(SNN_SEG_ARGS) { seg_sort_warp<2>(list, *count, mp, tmp, idx, d2, id_bound); }
+__global__ void k_seg_sort_w4(SNN_SEG_ARGS) { seg_sort_warp<4>(list, *count, mp, tmp, idx, d2, id_bound); }
+__global__ void k_seg_sort_w8(SNN_SEG_ARGS) { seg_sort_warp<8>(list, *count, mp, tmp, idx, d2, id_bound); }
+__global__ void k_seg_sort_w16(SNN_SEG_ARGS) { seg_sort_warp<16>(list, *count, mp, tmp, idx, d2, id_bound); }
 
 // One block per row of <= 4096 entries: bitonic sort in shared memory, of
 // 32-bit keys (id << 12 | position) when every id is below 2^20, else of the
@@ -902,8 +904,9 @@ __global__ void __launch_bounds__(256) k_seg_sort_mid(SNN_SEG_ARGS) {
     const unsigned total = *count;
     for (unsigned w = blockIdx.x; w < total; w += gridDim.x) {
         const int32_t r = list[w];
-        const int64_t o = offsets[r];
-        const int len = int(offsets[r + 1] - o);
+        const int64_t o = mp.src[r];
+        const int len = int(mp.src[r + 1] - o);
+        const int64_t od = mp.dst[mp.rmap ? mp.rmap[r] : r];
         int N = 64;
         while (N < len) N <<= 1;
         __syncthreads();
@@ -914,16 +917,16 @@ __global__ void __launch_bounds__(256) k_seg_sort_mid(SNN_SEG_ARGS) {
             block_bitonic(sk32, N);
             for (int i = threadIdx.x; i < len; i += blockDim.x) {
                 const uint32_t v = sk32[i];
-                idx[o + i] = int32_t(v >> 12);
-                d2[o + i] = __uint_as_float(w32[2 * (o + (v & 4095u))]);
+                idx[od + i] = int32_t(v >> 12);
+                d2[od + i] = __uint_as_float(w32[2 * (o + (v & 4095u))]);
             }
         } else {
             for (int i = threadIdx.x; i < N; i += blockDim.x) sk[i] = i < len ? tmp[o + i] : ~uint64_t(0);
             __syncthreads();
             block_bitonic(sk, N);
             for (int i = threadIdx.x; i < len; i += blockDim.x) {
-                idx[o + i] = int32_t(uint32_t(sk[i] >> 32));
-                d2[o + i] = __uint_as_float(uint32_t(sk[i]));
+                idx[od + i] = int32_t(uint32_t(sk[i] >> 32));
+                d2[od + i] = __uint_as_float(uint32_t(sk[i]));
             }
         }
     }
@@ -931,14 +934,14 @@ __global__ void __launch_bounds__(256) k_seg_sort_mid(SNN_SEG_ARGS) {
 #undef SNN_SEG_ARGS
 
 // Long rows: keys (big-row rank << 32 | column), values = source position.
-__global__ void k_seg_big_gather(const int32_t *__restrict__ big_list, int nbig,
-                                 const int64_t *__restrict__ offsets, const int64_t *__restrict__ toff,
-                                 const uint64_t *__restrict__ tmp, uint64_t *__restrict__ keys,
-                                 uint32_t *__restrict__ vals, float *__restrict__ gd2) {
+__global__ void k_seg_big_gather(const int32_t *__restrict__ big_list, int nbig, SegMap mp,
+                                 const int64_t *__restrict__ toff, const uint64_t *__restrict__ tmp,
+                                 uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                                 float *__restrict__ gd2) {
     const int b = blockIdx.x;
     if (b >= nbig) return;
     const int32_t r = big_list[b];
-    const int64_t o = offsets[r], len = offsets[r + 1] - o, t0 = toff[b];
+    const int64_t o = mp.src[r], len = mp.src[r + 1] - o, t0 = toff[b];
     for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
         const uint64_t v = tmp[o + i];
         keys[t0 + i] = (uint64_t(b) << 32) | (v >> 32);
@@ -948,15 +951,15 @@ __global__ void k_seg_big_gather(const int32_t *__restrict__ big_list, int nbig,
 }
 
 __global__ void k_seg_big_scatter(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
-                                  int64_t total, const int32_t *__restrict__ big_list,
-                                  const int64_t *__restrict__ offsets, const int64_t *__restrict__ toff,
-                                  const float *__restrict__ gd2, int32_t *__restrict__ idx,
-                                  float *__restrict__ d2) {
+                                  int64_t total, const int32_t *__restrict__ big_list, SegMap mp,
+                                  const int64_t *__restrict__ toff, const float *__restrict__ gd2,
+                                  int32_t *__restrict__ idx, float *__restrict__ d2) {
     const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (t >= total) return;
     const uint64_t k = keys[t];
     const int b = int(k >> 32);
-    const int64_t pos = offsets[big_list[b]] + (t - toff[b]);
+    const int32_t r = big_list[b];
+    const int64_t pos = mp.dst[mp.rmap ? mp.rmap[r] : r] + (t - toff[b]);
     idx[pos] = int32_t(uint32_t(k & 0xffffffffu));
     d2[pos] = gd2[vals[t]];
 }

@@ -177,13 +177,15 @@ __device__ __forceinline__ int decide_df(float H, float L, bool nz, const Decide
 // pair, _one emits the (query, point) orientation only; _g8 / _g32 use 8 or
 // 32 lanes per survivor (long rows).  R2q / dcq non-null: per-query fl64(R*R)
 // and decision constants (sorted query order) instead of R2 / dc.  The survivor count is read on the
-// device (min(*count, cap)); rec_pos[cap + s] is the mirrored slot.
+// device (min(*count, cap)).  Rows and columns are sorted positions: counts[x]
+// counts the neighbours of query position x (and of point position y for the
+// mirrored pairs of a self-join); rec_pos[s] is the pair's slot in its row,
+// rec_pos[cap + s] the mirrored slot, -1 for a pair that is not a neighbour.
 #define SNN_DECIDE_DECL(name)                                                                \
     __global__ void name(const uint2 *surv, const unsigned long long *count, int64_t cap,    \
-                         const float *qraw, const int32_t *qorder, const float *praw,        \
-                         const int32_t *porder, int d, int dp, double R2, DecideConsts dc,   \
-                         const double *R2q, const DecideConsts *dcq,                         \
-                         float *rec_d2, int32_t *rec_pos, uint2 *rec_rc, int32_t *counts,    \
+                         const float *qraw, const float *praw, int d, int dp, double R2,     \
+                         DecideConsts dc, const double *R2q, const DecideConsts *dcq,        \
+                         float *rec_d2, int32_t *rec_pos, int32_t *counts,                   \
                          unsigned long long *n_fp64)
 SNN_DECIDE_DECL(k_decide_sym);
 SNN_DECIDE_DECL(k_decide_one);
@@ -195,33 +197,41 @@ SNN_DECIDE_DECL(k_decide_sym_g32);
 SNN_DECIDE_DECL(k_decide_one_g32);
 #undef SNN_DECIDE_DECL
 __global__ void k_counts_to_i64(const int32_t *counts, int64_t m, int64_t *out);
-__global__ void k_scatter(const uint2 *rec_rc, const int32_t *rec_pos, const float *rec_d2,
+// out[order[i]] = counts[i]: per-position counts to per-id counts
+__global__ void k_counts_by_id(const int32_t *counts, const int32_t *order, int64_t m, int64_t *out);
+__global__ void k_scatter(const uint2 *surv, const int32_t *rec_pos, const float *rec_d2,
                           int64_t nsurv, int64_t rstride, int sym, const int64_t *offsets,
-                          uint64_t *tmp);
+                          const int32_t *qorder, const int32_t *porder, uint64_t *tmp);
 
 // Segmented sort of CSR rows by column id; id_bound is an exclusive upper
 // bound on the ids (it selects 32-bit sort keys where they fit).
 constexpr int kSegSmall = 32;
 constexpr int kSegMid = 4096;
+// Row placement of the per-row sort: row r is read from the staging array at
+// src[r] .. src[r + 1] and written to the output at dst[rmap ? rmap[r] : r].
+struct SegMap {
+    const int64_t *src;
+    const int64_t *dst;
+    const int32_t *rmap;
+};
 __global__ void k_seg_classify(const int64_t *offsets, int64_t m, int32_t *lists,
                                int32_t *big_list, int64_t *big_len, unsigned *counters);
-__global__ void k_seg_sort_w1(const int32_t *list, const unsigned *count, const int64_t *offsets,
-                          const uint64_t *tmp, int32_t *idx, float *d2, uint32_t id_bound);
-__global__ void k_seg_sort_w16(const int32_t *list, const unsigned *count, const int64_t *offsets,
-                          const uint64_t *tmp, int32_t *idx, float *d2, uint32_t id_bound);
-__global__ void k_seg_sort_w8(const int32_t *list, const unsigned *count, const int64_t *offsets,
-                          const uint64_t *tmp, int32_t *idx, float *d2, uint32_t id_bound);
-__global__ void k_seg_sort_w2(const int32_t *list, const unsigned *count, const int64_t *offsets,
-                          const uint64_t *tmp, int32_t *idx, float *d2, uint32_t id_bound);
-__global__ void k_seg_sort_w4(const int32_t *list, const unsigned *count, const int64_t *offsets,
-                          const uint64_t *tmp, int32_t *idx, float *d2, uint32_t id_bound);
-__global__ void k_seg_sort_mid(const int32_t *list, const unsigned *count, const int64_t *offsets,
-                          const uint64_t *tmp, int32_t *idx, float *d2, uint32_t id_bound);
-__global__ void k_seg_big_gather(const int32_t *big_list, int nbig, const int64_t *offsets,
-                                 const int64_t *toff, const uint64_t *tmp, uint64_t *keys,
-                                 uint32_t *vals, float *gd2);
+__global__ void k_seg_sort_w1(const int32_t *list, const unsigned *count, SegMap mp,
+                              const uint64_t *tmp, int32_t *idx, float *d2, uint32_t id_bound);
+__global__ void k_seg_sort_w16(const int32_t *list, const unsigned *count, SegMap mp,
+                              const uint64_t *tmp, int32_t *idx, float *d2, uint32_t id_bound);
+__global__ void k_seg_sort_w8(const int32_t *list, const unsigned *count, SegMap mp,
+                              const uint64_t *tmp, int32_t *idx, float *d2, uint32_t id_bound);
+__global__ void k_seg_sort_w2(const int32_t *list, const unsigned *count, SegMap mp,
+                              const uint64_t *tmp, int32_t *idx, float *d2, uint32_t id_bound);
+__global__ void k_seg_sort_w4(const int32_t *list, const unsigned *count, SegMap mp,
+                              const uint64_t *tmp, int32_t *idx, float *d2, uint32_t id_bound);
+__global__ void k_seg_sort_mid(const int32_t *list, const unsigned *count, SegMap mp,
+                              const uint64_t *tmp, int32_t *idx, float *d2, uint32_t id_bound);
+__global__ void k_seg_big_gather(const int32_t *big_list, int nbig, SegMap mp, const int64_t *toff,
+                                 const uint64_t *tmp, uint64_t *keys, uint32_t *vals, float *gd2);
 __global__ void k_seg_big_scatter(const uint64_t *keys, const uint32_t *vals, int64_t total,
-                                  const int32_t *big_list, const int64_t *offsets,
-                                  const int64_t *toff, const float *gd2, int32_t *idx, float *d2);
+                                  const int32_t *big_list, SegMap mp, const int64_t *toff,
+                                  const float *gd2, int32_t *idx, float *d2);
 
 }  // namespace snn

@@ -813,15 +813,14 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     out->dist2 = nullptr;
     ensure_pool();
     SNN_TRY(dev_alloc(&out->offsets, m + 1, s));
-    uint2 *surv = nullptr, *rec_rc = nullptr;
+    uint2 *surv = nullptr;
     float *rec_d2 = nullptr;
     int32_t *rec_pos = nullptr;
     auto fail = [&](snn_status st) {
-        void *tmp[] = {surv, rec_rc, rec_d2, rec_pos, out->offsets, out->indices, out->dist2};
+        void *tmp[] = {surv, rec_d2, rec_pos, out->offsets, out->indices, out->dist2};
         for (void *p : tmp)
             if (p) cudaFreeAsync(p, s);
         surv = nullptr;
-        rec_rc = nullptr;
         rec_d2 = nullptr;
         rec_pos = nullptr;
         out->offsets = nullptr;
@@ -1001,10 +1000,11 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         sa.ev_kernel[1] = ev[6];
     }
     int32_t *counts, *lists, *big_list;
-    int64_t *counts64, *big_len, *toff;
+    int64_t *counts64, *big_len, *toff, *soff;
     unsigned *cls;
     TRY_Q(scr.alloc(&counts, m));
     TRY_Q(scr.alloc(&counts64, m));
+    TRY_Q(scr.alloc(&soff, m + 1));
     TRY_Q(scr.alloc(&lists, 6 * m));
     TRY_Q(scr.alloc(&big_list, m));
     TRY_Q(scr.alloc(&big_len, m));
@@ -1033,7 +1033,6 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         CUDA_Q(cudaMallocAsync(&surv, size_t(cap) * sizeof(uint2), s));
         CUDA_Q(cudaMallocAsync(&rec_d2, size_t(cap) * sizeof(float), s));
         CUDA_Q(cudaMallocAsync(&rec_pos, size_t(sym ? 2 * cap : cap) * sizeof(int32_t), s));
-        CUDA_Q(cudaMallocAsync(&rec_rc, size_t(cap) * sizeof(uint2), s));
         sa.surv = surv;
         sa.cap = cap;
         if (stats) cudaEventRecord(ev[1], s);
@@ -1065,19 +1064,22 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         CUDA_Q(cudaMemsetAsync(counts, 0, m * sizeof(int32_t), s));
         const unsigned dgrid =
             std::min<unsigned>(grid_for(cap * G, 256), unsigned(16 * device_sm_count()));
-        SNN_LAUNCH(dk, dgrid, 256, 0, s)(surv, ctr, cap, qs.raw, qs.order, ds.raw, ds.order, d, dp,
-                                         R2, decide_consts(d, R2), R2s, dcs, rec_d2, rec_pos, rec_rc, counts,
-                                         ctr + 4);
+        SNN_LAUNCH(dk, dgrid, 256, 0, s)(surv, ctr, cap, qs.raw, ds.raw, d, dp, R2, decide_consts(d, R2),
+                                         R2s, dcs, rec_d2, rec_pos, counts, ctr + 4);
         CUDA_Q(cudaGetLastError());
         if (stats) cudaEventRecord(ev[3], s);
+        // row offsets twice: of the staging rows in sorted query positions
+        // (soff) and of the output rows by query id
         SNN_LAUNCH(k_counts_to_i64, grid_for(m, 256), 256, 0, s)(counts, m, counts64);
+        CUDA_Q(cudaGetLastError());
+        TRY_Q(scan_exclusive<int64_t>(counts64, soff, m, s));
+        SNN_LAUNCH(k_counts_by_id, grid_for(m, 256), 256, 0, s)(counts, qs.order, m, counts64);
         CUDA_Q(cudaGetLastError());
         TRY_Q(scan_exclusive<int64_t>(counts64, out->offsets, m, s));
         // rows by length class (per-row sort below); long rows' sizes scanned
         CUDA_Q(cudaMemsetAsync(cls, 0, 8 * sizeof(unsigned), s));
         CUDA_Q(cudaMemsetAsync(big_len, 0, m * sizeof(int64_t), s));
-        SNN_LAUNCH(k_seg_classify, grid_for(m, 256), 256, 0, s)(out->offsets, m, lists, big_list,
-                                                                big_len, cls);
+        SNN_LAUNCH(k_seg_classify, grid_for(m, 256), 256, 0, s)(soff, m, lists, big_list, big_len, cls);
         CUDA_Q(cudaGetLastError());
         TRY_Q(scan_exclusive<int64_t>(big_len, toff, m, s));
         SNN_LAUNCH(k_readback, 1, 32, 0, s)(ctr, bad, dev_err, out->offsets + m, cls, toff + m, dev_rb);
@@ -1102,11 +1104,9 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         cudaFreeAsync(surv, s);
         cudaFreeAsync(rec_d2, s);
         cudaFreeAsync(rec_pos, s);
-        cudaFreeAsync(rec_rc, s);
         surv = nullptr;
         rec_d2 = nullptr;
         rec_pos = nullptr;
-        rec_rc = nullptr;
         cap = (int64_t)hb->ctr[0] + 1024;
         CUDA_Q(cudaMemsetAsync(ctr, 0, 8 * sizeof(unsigned long long), s));
         if (stats) {
@@ -1137,18 +1137,19 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         TRY_Q(dev_alloc(&out->dist2, nnz, s));
         uint64_t *tmp;
         TRY_Q(scr.alloc(&tmp, nnz));
-        SNN_LAUNCH(k_scatter, grid_for(nsurv, 1024), 256, 0, s)(rec_rc, rec_pos, rec_d2, nsurv, cap,
-                                                               sym, out->offsets, tmp);
+        SNN_LAUNCH(k_scatter, grid_for(nsurv, 1024), 256, 0, s)(surv, rec_pos, rec_d2, nsurv, cap, sym,
+                                                               soff, qs.order, ds.order, tmp);
         CUDA_Q(cudaGetLastError());
-        // per-row ascending column ids, in place; classes with no rows are
-        // skipped and the grids sized by the class counts
+        // per-row ascending column ids: staging rows (sorted query positions)
+        // to output rows (query ids); classes with no rows are skipped and the
+        // grids sized by the class counts
         const unsigned *hc = hb->cls;
         auto wgrid = [&](unsigned rows) {
             return std::min<unsigned>(grid_for(int64_t(rows) * 32, 256), 16384);
         };
         int32_t *oi = out->indices;
         float *od = out->dist2;
-        const int64_t *oo = out->offsets;
+        const SegMap oo{soff, out->offsets, qs.order};
         // ids are point ids of the index; SNN_SORT_KEYS64=1 forces the
         // 64-bit sort keys (both widths give the same rows)
         const char *k64 = getenv("SNN_SORT_KEYS64");
@@ -1176,25 +1177,22 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
             TRY_Q(scr.alloc(&bv, tot));
             TRY_Q(scr.alloc(&bva, tot));
             TRY_Q(scr.alloc(&gd2, tot));
-            SNN_LAUNCH(k_seg_big_gather, nbig, 256, 0, s)(big_list, nbig, out->offsets, toff, tmp,
-                                                          bk, bv, gd2);
+            SNN_LAUNCH(k_seg_big_gather, nbig, 256, 0, s)(big_list, nbig, oo, toff, tmp, bk, bv, gd2);
             CUDA_Q(cudaGetLastError());
             int bits = 32;
             while ((int64_t(1) << (bits - 32)) < nbig) ++bits;
             TRY_Q(radix_sort_pairs<uint64_t>(bk, bv, bka, bva, tot, bits, s));
             SNN_LAUNCH(k_seg_big_scatter, grid_for(tot, 256), 256, 0, s)(
-                bk, bv, tot, big_list, out->offsets, toff, gd2, out->indices, out->dist2);
+                bk, bv, tot, big_list, oo, toff, gd2, out->indices, out->dist2);
             CUDA_Q(cudaGetLastError());
         }
     }
     cudaFreeAsync(surv, s);
     cudaFreeAsync(rec_d2, s);
     cudaFreeAsync(rec_pos, s);
-    cudaFreeAsync(rec_rc, s);
     surv = nullptr;
     rec_d2 = nullptr;
     rec_pos = nullptr;
-    rec_rc = nullptr;
     if (stats) {
         cudaEventRecord(ev[4], s);
         unsigned long long nf = 0;

@@ -197,6 +197,7 @@ struct TcArgs {
     int *err;
     int stall;                  // test fault: the producer issues no loads
     int f16;                    // data k steps hold FP16 parts (folded ones BF16)
+    int scan_rank;              // streamed shapes: branch-free survivor extraction
 };
 
 struct ItemInfo {
@@ -390,7 +391,8 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                                 // the folded columns: one BF16 K = 16 step
 #pragma unroll
                                 for (int h = 0; h < MT; ++h)
-                                    mma_bf16(dt0 + uint32_t(h * BN), smem_desc<32>(a_tile(s, 0) + uint32_t(h * kTM * 32)),
+                                    mma_bf16(dt0 + uint32_t(h * BN),
+                                             smem_desc<32>(a_tile(s, 0) + uint32_t(h * kTM * 32)),
                                              smem_desc<32>(b_tile(s, 0)), kIdesc, 1u);
                             } else {
 #pragma unroll
@@ -400,11 +402,12 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                                     if (kg >= a.ksteps_data) break;
                                     const uint64_t bd = smem_desc<Sh::kRowBytes>(b_tile(s, 0) + 32u * ks);
 #pragma unroll
-                                    for (int h = 0; h < MT; ++h)
-                                        mma_bf16(dt0 + uint32_t(h * BN),
-                                                 smem_desc<Sh::kRowBytes>(a_tile(s, 0) +
-                                                                          uint32_t(h * kTM * Sh::kRowBytes) + 32u * ks),
-                                                 bd, kIdescF16, kg != 0 ? 1u : 0u);
+                                    for (int h = 0; h < MT; ++h) {
+                                        const uint32_t aa =
+                                            a_tile(s, 0) + uint32_t(h * kTM * Sh::kRowBytes) + 32u * ks;
+                                        mma_bf16(dt0 + uint32_t(h * BN), smem_desc<Sh::kRowBytes>(aa), bd,
+                                                 kIdescF16, kg != 0 ? 1u : 0u);
+                                    }
                                 }
                             }
                         } else if constexpr (F8NP != 0) {
@@ -522,56 +525,132 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                         __syncwarp();
                         if (lane == 0) mbar_arrive(tempty_bar(b));
                     }
-                    // a 16-column group whose accumulators are all negative
-                    // holds no survivor (an acceptable pair's accumulator is
-                    // strictly positive); only groups where some lane of the
-                    // warp may hold one are scanned
-                    bool anyg[4];
-#pragma unroll
-                    for (int g = 0; g < 4; ++g) anyg[g] = !(mx[g] < 0.f);
-                    if (!__any_sync(0xffffffffu, anyg[0] || anyg[1] || anyg[2] || anyg[3])) continue;
-                    // bit i of the mask = column cb0 * 32 + i is a survivor:
-                    // (mask << 1) | sign per column, highest column first, one
-                    // funnel shift each
-                    uint32_t neg[2] = {0xffffffffu, 0xffffffffu};
-#pragma unroll
-                    for (int g = 0; g < 4; ++g) {
-                        if (!__any_sync(0xffffffffu, anyg[g])) continue;
-                        uint32_t ng = 0;
-#pragma unroll
-                        for (int i = 15; i >= 0; --i) ng = __funnelshift_l(rr[16 * g + i], ng, 1);
-                        const int sh = 16 * (g & 1);
-                        neg[g >> 1] = (neg[g >> 1] & ~(0xffffu << sh)) | (ng << sh);
-                    }
-                    uint64_t mask = qvalid ? ~((uint64_t(neg[1]) << 32) | neg[0]) : 0ull;
-                    if (edge) {
-                        // validity near the band end and on the diagonal of a
-                        // symmetric self-join (rows >= query only)
-                        const int64_t jb = j0 + cb0 * 32;
-                        const int64_t lim = f.band_hi - jb;
-                        if (lim <= 0) mask = 0;
-                        else if (lim < 64) mask &= (1ull << lim) - 1ull;
-                        if (a.sym) {
-                            const int64_t first = q - jb;
-                            if (first >= 64) mask = 0;
-                            else if (first > 0) mask &= ~((1ull << first) - 1ull);
+                    if (ARES || !a.scan_rank) {
+                        // chunks of few k-blocks (the resident-query-tile low-d
+                        // shapes and short streamed rows): the epilogue's ALU work
+                        // bounds the chunk rate, so only the 16-column groups that
+                        // may hold a survivor are scanned, and survivors are
+                        // ranked by ballot rounds (one round per survivor of the
+                        // lane with most)
+                        // a 16-column group whose accumulators are all negative
+                        // holds no survivor (an acceptable pair's accumulator is
+                        // strictly positive); only groups where some lane of the
+                        // warp may hold one are scanned
+                        bool anyg[4];
+    #pragma unroll
+                        for (int g = 0; g < 4; ++g) anyg[g] = !(mx[g] < 0.f);
+                        if (!__any_sync(0xffffffffu, anyg[0] || anyg[1] || anyg[2] || anyg[3])) continue;
+                        // bit i of the mask = column cb0 * 32 + i is a survivor:
+                        // (mask << 1) | sign per column, highest column first, one
+                        // funnel shift each
+                        uint32_t neg[2] = {0xffffffffu, 0xffffffffu};
+    #pragma unroll
+                        for (int g = 0; g < 4; ++g) {
+                            if (!__any_sync(0xffffffffu, anyg[g])) continue;
+                            uint32_t ng = 0;
+    #pragma unroll
+                            for (int i = 15; i >= 0; --i) ng = __funnelshift_l(rr[16 * g + i], ng, 1);
+                            const int sh = 16 * (g & 1);
+                            neg[g >> 1] = (neg[g >> 1] & ~(0xffffu << sh)) | (ng << sh);
                         }
-                    }
-                    // one survivor per lane per round: a ballot ranks them in
-                    // the warp's staging buffer
-                    const unsigned lt = lanemask_lt();
-                    const uint32_t jcol = unsigned(j0 + cb0 * 32);
-                    while (__any_sync(0xffffffffu, mask != 0)) {
-                        const bool has = mask != 0;
-                        const unsigned bal = __ballot_sync(0xffffffffu, has);
-                        const int nb = __popc(bal);
-                        if (scount + nb > kStg) flush();
-                        if (has) {
-                            const int i = __ffsll((long long)mask) - 1;
-                            mask &= mask - 1;
-                            stg[scount + __popc(bal & lt)] = make_uint2(unsigned(q), jcol + unsigned(i));
+                        uint64_t mask = qvalid ? ~((uint64_t(neg[1]) << 32) | neg[0]) : 0ull;
+                        if (edge) {
+                            // validity near the band end and on the diagonal of a
+                            // symmetric self-join (rows >= query only)
+                            const int64_t jb = j0 + cb0 * 32;
+                            const int64_t lim = f.band_hi - jb;
+                            if (lim <= 0) mask = 0;
+                            else if (lim < 64) mask &= (1ull << lim) - 1ull;
+                            if (a.sym) {
+                                const int64_t first = q - jb;
+                                if (first >= 64) mask = 0;
+                                else if (first > 0) mask &= ~((1ull << first) - 1ull);
+                            }
                         }
-                        scount += nb;
+                        // one survivor per lane per round: a ballot ranks them in
+                        // the warp's staging buffer
+                        const unsigned lt = lanemask_lt();
+                        const uint32_t jcol = unsigned(j0 + cb0 * 32);
+                        while (__any_sync(0xffffffffu, mask != 0)) {
+                            const bool has = mask != 0;
+                            const unsigned bal = __ballot_sync(0xffffffffu, has);
+                            const int nb = __popc(bal);
+                            if (scount + nb > kStg) flush();
+                            if (has) {
+                                const int i = __ffsll((long long)mask) - 1;
+                                mask &= mask - 1;
+                                stg[scount + __popc(bal & lt)] = make_uint2(unsigned(q), jcol + unsigned(i));
+                            }
+                            scount += nb;
+                        }
+                    } else {
+                        // chunks of many k-blocks (MMA-bound): branch-free sign
+                        // masks and one prefix sum for the ranks (shorter
+                        // dependency chains)
+                        // no survivor among the warp's 64 x 32 pairs unless some
+                        // 16-column maximum is non-negative (an acceptable pair's
+                        // accumulator is strictly positive)
+                        const bool anyl = !(mx[0] < 0.f) || !(mx[1] < 0.f) || !(mx[2] < 0.f) || !(mx[3] < 0.f);
+                        if (!__any_sync(0xffffffffu, anyl)) continue;
+                        // bit i of the mask = column cb0 * 32 + i is a survivor: the
+                        // sign bits of the 64 accumulators, gathered by four
+                        // independent funnel-shift chains (highest column first)
+                        uint32_t ng[4] = {0u, 0u, 0u, 0u};
+    #pragma unroll
+                        for (int i = 15; i >= 0; --i) {
+    #pragma unroll
+                            for (int g = 0; g < 4; ++g) ng[g] = __funnelshift_l(rr[16 * g + i], ng[g], 1);
+                        }
+                        const uint32_t neg0 = ng[0] | (ng[1] << 16), neg1 = ng[2] | (ng[3] << 16);
+                        uint64_t mask = qvalid ? ~((uint64_t(neg1) << 32) | neg0) : 0ull;
+                        if (edge) {
+                            // validity near the band end and on the diagonal of a
+                            // symmetric self-join (rows >= query only)
+                            const int64_t jb = j0 + cb0 * 32;
+                            const int64_t lim = f.band_hi - jb;
+                            if (lim <= 0) mask = 0;
+                            else if (lim < 64) mask &= (1ull << lim) - 1ull;
+                            if (a.sym) {
+                                const int64_t first = q - jb;
+                                if (first >= 64) mask = 0;
+                                else if (first > 0) mask &= ~((1ull << first) - 1ull);
+                            }
+                        }
+                        // the lanes' survivors in lane order: an exclusive prefix
+                        // sum of the per-lane counts places each lane's run
+                        const int cnt = __popcll(mask);
+                        int incl = cnt;
+    #pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                            if (lane >= o) incl += t;
+                        }
+                        const int total = __shfl_sync(0xffffffffu, incl, 31);
+                        if (total == 0) continue;
+                        const uint32_t jcol = unsigned(j0 + cb0 * 32);
+                        if (scount + total > kStg) flush();
+                        if (total <= kStg) {
+                            int pos = scount + incl - cnt;
+                            while (mask != 0) {
+                                const int i = __ffsll((long long)mask) - 1;
+                                mask &= mask - 1;
+                                stg[pos++] = make_uint2(unsigned(q), jcol + unsigned(i));
+                            }
+                            scount += total;
+                        } else {
+                            // more than the staging buffer holds: straight to the
+                            // global list
+                            unsigned long long base = 0;
+                            if (lane == 0) base = atomicAdd(a.count, (unsigned long long)total);
+                            base = __shfl_sync(0xffffffffu, base, 0) + unsigned(incl - cnt);
+                            while (mask != 0) {
+                                const int i = __ffsll((long long)mask) - 1;
+                                mask &= mask - 1;
+                                if (base < (unsigned long long)a.cap)
+                                    a.surv[base] = make_uint2(unsigned(q), jcol + unsigned(i));
+                                ++base;
+                            }
+                        }
                     }
                 }
                 if (kGroups != 2) {
@@ -1118,6 +1197,7 @@ TcArgs tc_args(const snn_index *ix, const ScoreArgs &sa, const TileSet &ts) {
     a.err = sa.err;
     a.stall = take_fault(SNN_FAULT_STALL_TC_PRODUCER) ? 1 : 0;
     a.f16 = 0;
+    a.scan_rank = 0;
     return a;
 }
 
@@ -1401,6 +1481,9 @@ snn_status h1_score_launch(snn_index *ix, const ScoreArgs &sa, cudaStream_t s, d
     TcArgs a = tc_args(ix, sa, ts);
     a.ksteps_data = ksteps;
     a.nkb = int(cdiv(K2, 32)) + 1;
+    // with 12 or more k-blocks per chunk the MMAs, not the epilogue, set the
+    // chunk rate (measured: 784 columns faster, 100 columns slower with it)
+    a.scan_rank = a.nkb >= 12 ? 1 : 0;
     return MTq == 2 ? run_tc<1, 32, 256, false, 1, 32, 2, 0>(maps, a, sa, s)
                     : run_tc<1, 32, 256, false, 1, 32, 1, 0>(maps, a, sa, s);
 }
