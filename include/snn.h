@@ -119,7 +119,11 @@ typedef struct {
  *              k-step (3, 4, 6);
  *  ms_*        device time of the phases (CUDA events on `stream`);
  *              ms_score covers the operand packing and the scoring launch,
- *              ms_score_kernel the scoring launch alone. */
+ *              ms_score_kernel the scoring launch alone;
+ *  flags       read on input (zero-initialise the struct): with
+ *              SNN_STATS_NO_CANDIDATES set the per-query candidate-range
+ *              sizes are not counted (one kernel of FP64 range arithmetic
+ *              fewer) and candidates is returned as -1. */
 typedef struct {
     int64_t candidates;
     int64_t band_pairs;
@@ -134,8 +138,10 @@ typedef struct {
     int32_t precision_used;
     int32_t split_used;
     float ms_score_kernel;
-    int32_t reserved;
+    int32_t flags;
 } snn_query_stats;
+
+#define SNN_STATS_NO_CANDIDATES 1
 
 #define SNN_SPLIT_NONE 0
 #define SNN_SPLIT_BF16X2 1

@@ -420,7 +420,9 @@ __device__ __forceinline__ void decide_one_survivor(
          const double *__restrict__ R2q, const DecideConsts *__restrict__ dcq,
          float *__restrict__ rec_d2, int32_t *__restrict__ rec_pos, int32_t *__restrict__ counts,
          unsigned long long *__restrict__ n_fp64) {
-    const uint2 e = surv[s];
+    // the survivor list and the records are read / written once: streaming
+    // accesses, so that they do not evict the data rows from L2
+    const uint2 e = __ldcs(surv + s);
     const DecideConsts dc = dcq ? dcq[e.x] : dc0;
     const double R2e = R2q ? R2q[e.x] : R2;
     const float4 *pq = reinterpret_cast<const float4 *>(qraw + int64_t(e.x) * dp);
@@ -475,9 +477,9 @@ __device__ __forceinline__ void decide_one_survivor(
         p0 = atomicAdd(&counts[e.x], 1);
         if (kSym && e.x != e.y) p1 = atomicAdd(&counts[e.y], 1);
     }
-    rec_d2[s] = d2;
-    rec_pos[s] = p0;
-    if (kSym) rec_pos[cap + s] = p1;
+    __stcs(rec_d2 + s, d2);
+    __stcs(rec_pos + s, p0);
+    if (kSym) __stcs(rec_pos + cap + s, p1);
 }
 
 template <bool kSym, int NQ>
@@ -688,10 +690,10 @@ __global__ void k_scatter(const uint2 *__restrict__ surv, const int32_t *__restr
     for (int u = 0; u < U; ++u) {
         const int64_t s = base + int64_t(u) * blockDim.x;
         const bool in = s < nsurv;
-        p0[u] = in ? rec_pos[s] : -1;
-        p1[u] = (in && sym) ? rec_pos[rstride + s] : -1;
-        rc[u] = in ? surv[s] : make_uint2(0u, 0u);
-        vb[u] = in ? __float_as_uint(rec_d2[s]) : 0u;
+        p0[u] = in ? __ldcs(rec_pos + s) : -1;
+        p1[u] = (in && sym) ? __ldcs(rec_pos + rstride + s) : -1;
+        rc[u] = in ? __ldcs(surv + s) : make_uint2(0u, 0u);
+        vb[u] = in ? __float_as_uint(__ldcs(rec_d2 + s)) : 0u;
     }
     int64_t o0[U], o1[U];
     uint32_t c0[U], c1[U];

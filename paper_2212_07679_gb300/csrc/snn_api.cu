@@ -927,10 +927,10 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         CUDA_Q(cudaGetLastError());
     }
 
+    // the FP32 scorer's per-query thresholds (computed below when that
+    // scorer runs)
     float *thrA;
     TRY_Q(scr.alloc(&thrA, m));
-    SNN_LAUNCH(k_query_consts, grid_for(m, 256), 256, 0, s)(qs.hx, qs.nrm, m, d, Rx, e_data, thrA, Rs);
-    CUDA_Q(cudaGetLastError());
 
     const int ntiles = (int)cdiv(m, kBQ);
     int64_t *tile_lo, *tile_hi, *items, *item_off;
@@ -947,7 +947,10 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
                                                       ix->dconst, eps_q, tile_lo, tile_hi, items,
                                                       ntiles, sym, stats ? ctr + 2 : nullptr, Rs, d);
     CUDA_Q(cudaGetLastError());
-    if (stats) {
+    // the candidate-range sizes are counted for the statistics only, unless
+    // the caller asked to skip them
+    const bool count_cand = stats && !(stats->flags & SNN_STATS_NO_CANDIDATES);
+    if (count_cand) {
         SNN_LAUNCH(k_query_windows, grid_for(m, 256), 256, 0, s)(qs.alpha, m, ix->alpha, ix->n, Wbase,
                                                          ix->dconst, eps_q, ctr + 3, Rs, d);
         CUDA_Q(cudaGetLastError());
@@ -1046,6 +1049,9 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
                                  &split_used);
         } else {
             const int grid = device_sm_count() * 2;
+            if (attempt == 0)
+                SNN_LAUNCH(k_query_consts, grid_for(m, 256), 256, 0, s)(qs.hx, qs.nrm, m, d, Rx, e_data, thrA,
+                                                                        Rs);
             if (stats) cudaEventRecord(ev[5], s);
             if (dp <= 16)
                 SNN_LAUNCH(k_score_fp32_single, grid, 256, 0, s)(sa);
@@ -1114,8 +1120,9 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
             SNN_LAUNCH(k_tile_band, grid_for(ntiles, 128), 128, 0, s)(
                 qs.alpha, m, ix->alpha, ix->n, Wbase, ix->dconst, eps_q, tile_lo, tile_hi, items,
                 ntiles, sym, ctr + 2, Rs, d);
-            SNN_LAUNCH(k_query_windows, grid_for(m, 256), 256, 0, s)(qs.alpha, m, ix->alpha, ix->n,
-                                                                     Wbase, ix->dconst, eps_q, ctr + 3, Rs, d);
+            if (count_cand)
+                SNN_LAUNCH(k_query_windows, grid_for(m, 256), 256, 0, s)(qs.alpha, m, ix->alpha, ix->n,
+                                                                         Wbase, ix->dconst, eps_q, ctr + 3, Rs, d);
             CUDA_Q(cudaGetLastError());
         }
     }
@@ -1204,7 +1211,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         stats->mma_flops_per_pair = mma_fpp;
         stats->precision_used = (int32_t)used;
         stats->split_used = (int32_t)split_used;
-        stats->candidates = (int64_t)hb->ctr[3];
+        stats->candidates = count_cand ? (int64_t)hb->ctr[3] : -1;
         stats->band_pairs = (int64_t)hb->ctr[2];
         stats->survivors = nsurv;
         stats->nnz = nnz;
@@ -1213,7 +1220,6 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         cudaEventElapsedTime(&stats->ms_recheck, ev[2], ev[3]);
         cudaEventElapsedTime(&stats->ms_csr, ev[3], ev[4]);
         cudaEventElapsedTime(&stats->ms_score_kernel, ev[5], ev[6]);
-        stats->reserved = 0;
         for (auto &e : ev) cudaEventDestroy(e);
     }
     // the caller owns the output arrays (released by snn_free)
@@ -1308,7 +1314,7 @@ static snn_status ip_search(const float *P, int64_t n, int d, int64_t ldp, const
     SNN_TRY(index_build(Pa, n, d + 1, d + 1, s, &ix));
     snn_csr cand;
     std::memset(&cand, 0, sizeof(cand));
-    snn_query_stats qst;
+    snn_query_stats qst{};
     snn_status rc = query_impl(ix, Qa, m, d + 1, Rmax, prec, s, &cand, st ? &qst : nullptr, Rq, Rmax);
     index_release(ix);
     if (rc != SNN_OK) return rc;

@@ -30,6 +30,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <vector>
@@ -537,18 +538,18 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                         // strictly positive); only groups where some lane of the
                         // warp may hold one are scanned
                         bool anyg[4];
-    #pragma unroll
+#pragma unroll
                         for (int g = 0; g < 4; ++g) anyg[g] = !(mx[g] < 0.f);
                         if (!__any_sync(0xffffffffu, anyg[0] || anyg[1] || anyg[2] || anyg[3])) continue;
                         // bit i of the mask = column cb0 * 32 + i is a survivor:
                         // (mask << 1) | sign per column, highest column first, one
                         // funnel shift each
                         uint32_t neg[2] = {0xffffffffu, 0xffffffffu};
-    #pragma unroll
+#pragma unroll
                         for (int g = 0; g < 4; ++g) {
                             if (!__any_sync(0xffffffffu, anyg[g])) continue;
                             uint32_t ng = 0;
-    #pragma unroll
+#pragma unroll
                             for (int i = 15; i >= 0; --i) ng = __funnelshift_l(rr[16 * g + i], ng, 1);
                             const int sh = 16 * (g & 1);
                             neg[g >> 1] = (neg[g >> 1] & ~(0xffffu << sh)) | (ng << sh);
@@ -596,9 +597,9 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                         // sign bits of the 64 accumulators, gathered by four
                         // independent funnel-shift chains (highest column first)
                         uint32_t ng[4] = {0u, 0u, 0u, 0u};
-    #pragma unroll
+#pragma unroll
                         for (int i = 15; i >= 0; --i) {
-    #pragma unroll
+#pragma unroll
                             for (int g = 0; g < 4; ++g) ng[g] = __funnelshift_l(rr[16 * g + i], ng[g], 1);
                         }
                         const uint32_t neg0 = ng[0] | (ng[1] << 16), neg1 = ng[2] | (ng[3] << 16);
@@ -620,7 +621,7 @@ k_score_tc(const __grid_constant__ CUtensorMap qa0, const __grid_constant__ CUte
                         // sum of the per-lane counts places each lane's run
                         const int cnt = __popcll(mask);
                         int incl = cnt;
-    #pragma unroll
+#pragma unroll
                         for (int o = 1; o < 32; o <<= 1) {
                             const int t = __shfl_up_sync(0xffffffffu, incl, o);
                             if (lane >= o) incl += t;
@@ -750,7 +751,7 @@ __device__ __forceinline__ uint16_t half_bits(float v) {
 // loads, 8-byte stores, coalesced in both arrays), then the folded columns
 // with one lane per row (their few FP64 operations then run on full warps).
 template <int NSPLIT>
-__global__ void k_tc_pack(const float *__restrict__ xc, int dp, const float *__restrict__ hx,
+__global__ void __launch_bounds__(256, 4) k_tc_pack(const float *__restrict__ xc, int dp, const float *__restrict__ hx,
                           const float *__restrict__ nrm, const double *__restrict__ Aq,
                           int64_t rows, int d, int K2, int K2n, double c, int query_side,
                           uint16_t *__restrict__ p0, uint16_t *__restrict__ p1,
@@ -763,7 +764,7 @@ __global__ void k_tc_pack(const float *__restrict__ xc, int dp, const float *__r
     // overwritten below (after __syncwarp)
     const int nq = K2 / 4;                 // quads per packed row
     const int total = nr * nq;
-    constexpr int U = 8;
+    constexpr int U = 4;
     for (int base = 0; base < total; base += 32 * U) {
         float4 xv[U];
 #pragma unroll
@@ -1136,11 +1137,21 @@ __global__ void k_h1_pack(const float *__restrict__ xc, int dp, const float *__r
     }
 }
 
+// 1 / (1 - delta) rounded up and 1 / (1 + delta) rounded down: multiplying by
+// them (product rounded up) bounds A / (1 -+ delta) from above for A >= 0 and
+// A < 0 alike, without an FP64 division per query.
+struct DeltaInv {
+    double inv_m, inv_p;
+};
+inline DeltaInv delta_inv(double delta) {
+    return DeltaInv{std::nextafter(1.0 / (1.0 - delta), INFINITY), std::nextafter(1.0 / (1.0 + delta), 0.0)};
+}
+
 // A'_i >= (Rx + e_data + e_i)^2/2 - ||y_i||^2/2, inflated so that its split
 // representation and the accumulation rounding (delta) keep the sign test
 // conservative, plus a margin that makes an acceptable pair's acc positive.
 __global__ void k_tc_query_consts(const float *__restrict__ hy, const float *__restrict__ qn,
-                                  int64_t m, int d, double Rx, double e_data, double delta,
+                                  int64_t m, int d, double Rx, double e_data, DeltaInv di,
                                   double margin, double *__restrict__ Aq, const double *__restrict__ Rq,
                                   double abs_n, double abs_q) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -1152,7 +1163,7 @@ __global__ void k_tc_query_consts(const float *__restrict__ hy, const float *__r
     // BF16 parts)
     double A = 0.5 * r * r - hy_low + (abs_n + abs_q * (double)qn[i]);
     A += 4.0 * kU64 * (fabs(A) + 0.5 * r * r + (double)hy[i]);
-    A = A >= 0.0 ? A / (1.0 - delta) : A / (1.0 + delta);
+    A = A >= 0.0 ? __dmul_ru(A, di.inv_m) : __dmul_ru(A, di.inv_p);
     A += 0x1p-22 * fabs(A) + margin;
     Aq[i] = A;
 }
@@ -1390,7 +1401,7 @@ snn_status f8_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
     SNN_TRY(scr.alloc(&qfold, size_t(m) * 16));
     // a margin of 2^-60 keeps A'_i 2^(s_x + s_y) a normal FP32 number
     SNN_LAUNCH(k_tc_query_consts, unsigned(cdiv(m, 256)), 256, 0, s)(
-        sa.q.hx, sa.q.nrm, m, d, Rx, e_data, 0x1p-23 + kacc, 0x1p-60, Aq, sa.Rq, 0.0, 0.0);
+        sa.q.hx, sa.q.nrm, m, d, Rx, e_data, delta_inv(0x1p-23 + kacc), 0x1p-60, Aq, sa.Rq, 0.0, 0.0);
     SNN_LAUNCH_CHECK();
     SNN_LAUNCH(packer, pack_grid(m), pack_threads, 0, s)(sa.q.xc, ix->dp, nullptr, Aq, m, d, K8, ch,
                                                         kacc, 1, qp[0], qp[1], qp[2], qfold);
@@ -1441,7 +1452,7 @@ snn_status h1_score_launch(snn_index *ix, const ScoreArgs &sa, cudaStream_t s, d
     SNN_TRY(scr.alloc(&qfold, size_t(m) * 16));
     // a margin of 2^-60 keeps A'_i 2^(s_x + s_y) a normal FP32 number
     SNN_LAUNCH(k_tc_query_consts, unsigned(cdiv(m, 256)), 256, 0, s)(
-        sa.q.hx, sa.q.nrm, m, d, Rx, e_data, 0x1p-23 + kacc, 0x1p-60, Aq, sa.Rq, 0.0, 0.0);
+        sa.q.hx, sa.q.nrm, m, d, Rx, e_data, delta_inv(0x1p-23 + kacc), 0x1p-60, Aq, sa.Rq, 0.0, 0.0);
     SNN_LAUNCH_CHECK();
     SNN_LAUNCH(k_h1_pack, pack_grid(m), pack_threads, 0, s)(sa.q.xc, ix->dp, nullptr, Aq, m, d, K2, ch, kacc,
                                                            1, qp, qfold);
@@ -1577,7 +1588,7 @@ snn_status tc_score_launch(const snn_index *ixc, const ScoreArgs &sa, cudaStream
     SNN_TRY(scr.alloc(&Aq, m));
     for (int p = 0; p < nsplit; ++p) SNN_TRY(scr.alloc(&qp[p], size_t(m) * (p == 0 ? K2 : K2n)));
     SNN_LAUNCH(k_tc_query_consts, unsigned(cdiv(m, 256)), 256, 0, s)(
-        sa.q.hx, sa.q.nrm, m, d, Rx, e_data, 0x1p-23 + u_k, 0x1p-100, Aq, sa.Rq, abs_n, abs_q);
+        sa.q.hx, sa.q.nrm, m, d, Rx, e_data, delta_inv(0x1p-23 + u_k), 0x1p-100, Aq, sa.Rq, abs_n, abs_q);
     SNN_LAUNCH_CHECK();
     auto packer = nsplit == 2 ? k_tc_pack<2> : k_tc_pack<3>;
     SNN_LAUNCH(packer, unsigned(cdiv(cdiv(m, 32) * 32, 256)), 256, 0, s)(sa.q.xc, ix->dp, sa.q.hx,
@@ -1633,7 +1644,8 @@ struct TcbSet {
     int64_t m, xoff, q0g, grp0, tile0, ntiles;
     int d, dp;
     float xscale;
-    double fs1, fs2, c, Rx, e_data, delta, abs_n, abs_q;
+    double fs1, fs2, c, Rx, e_data, abs_n, abs_q;
+    DeltaInv di;
 };
 
 struct TcBatchGroup {
@@ -1687,7 +1699,7 @@ __global__ void k_tcb_qpack(const TcbSet *__restrict__ sets, const int32_t *__re
     const double hy_low = hy * (1.0 - 1.05 * (d + 2) * (double)kU32);
     double A = 0.5 * rr * rr - hy_low + (S.abs_n + S.abs_q * qn);
     A += 4.0 * kU64 * (fabs(A) + 0.5 * rr * rr + hy);
-    A = A >= 0.0 ? A / (1.0 - S.delta) : A / (1.0 + S.delta);
+    A = A >= 0.0 ? __dmul_ru(A, S.di.inv_m) : __dmul_ru(A, S.di.inv_p);
     A += 0x1p-22 * fabs(A) + 0x1p-100;
     const float *x = S.qxc + i * S.dp;
     bool bad = false;
@@ -1830,7 +1842,7 @@ snn_status tc_batch_create(const snn_index *const *idx, const SetDesc *sd, const
         S.c = tc_constant(2, ix->d, &u_k, true);
         S.Rx = d.Rx;
         S.e_data = d.e_data;
-        S.delta = 0x1p-23 + u_k;
+        S.di = delta_inv(0x1p-23 + u_k);
         S.abs_q = 1.001 * std::sqrt(double(ix->d)) * std::ldexp(1.0, -14 - sigma);
         S.abs_n = S.abs_q * Nd + 2.0 * ix->d * std::ldexp(1.0, -28 - 2 * sigma);
         const int64_t ng = cdiv(S.ntiles, int64_t(g->MT));

@@ -39,7 +39,22 @@ class StatsStruct(ctypes.Structure):
                 ("ms_prep", ctypes.c_float), ("ms_score", ctypes.c_float),
                 ("ms_recheck", ctypes.c_float), ("ms_csr", ctypes.c_float),
                 ("precision_used", ctypes.c_int32), ("split_used", ctypes.c_int32),
-                ("ms_score_kernel", ctypes.c_float), ("reserved", ctypes.c_int32)]
+                ("ms_score_kernel", ctypes.c_float), ("flags", ctypes.c_int32)]
+
+SNN_STATS_NO_CANDIDATES = 1
+
+
+def _stats_struct(stats):
+    """stats: False (none), True (every counter) or "phases" (no candidate
+    count: SNN_STATS_NO_CANDIDATES, candidates = -1)."""
+    if not stats:
+        return None
+    if stats not in (True, "phases"):
+        raise ValueError("stats must be False, True or 'phases'")
+    st = StatsStruct()
+    if stats == "phases":
+        st.flags = SNN_STATS_NO_CANDIDATES
+    return st
 
 
 class IPStatsStruct(ctypes.Structure):
@@ -308,12 +323,13 @@ class Index:
         self.n = int(lib.snn_index_size(self._h))
 
     def query(self, Q: torch.Tensor | None = None, R: float = 0.0, precision: str = "fp32",
-              stats: bool = False, stream=None) -> CSR:
-        """Algorithm 2 for all rows of Q (None: self-join)."""
+              stats: bool | str = False, stream=None) -> CSR:
+        """Algorithm 2 for all rows of Q (None: self-join).  stats: False,
+        True (every counter) or "phases" (no candidate-range count)."""
         if self._h is None:
             raise RuntimeError("index was freed")
         cs = CSRStruct()
-        st = StatsStruct() if stats else None
+        st = _stats_struct(stats)
         if Q is None:
             qptr, m, ldq = None, 0, self.d
         else:
@@ -336,7 +352,7 @@ class Index:
             sd = {k: getattr(st, k) for k, _ in StatsStruct._fields_}
         return _csr_from(cs, self.device, sd)
 
-    def query_each(self, Q: torch.Tensor, R, precision: str = "fp32", stats: bool = False,
+    def query_each(self, Q: torch.Tensor, R, precision: str = "fp32", stats: bool | str = False,
                    stream=None) -> CSR:
         """Out-of-sample queries with one radius each (snn_query_radius_each);
         R: a float64 sequence or tensor of len(Q) radii."""
@@ -347,7 +363,7 @@ class Index:
         if Rt.numel() != Q.shape[0]:
             raise ValueError("one radius per query row")
         cs = CSRStruct()
-        st = StatsStruct() if stats else None
+        st = _stats_struct(stats)
         with torch.cuda.device(self.device):
             _check(lib.snn_query_radius_each(self._h, ctypes.c_void_p(Q.data_ptr()), Q.shape[0], ldq,
                                              ctypes.c_void_p(Rt.data_ptr()), PRECISIONS[precision],

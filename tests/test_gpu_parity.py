@@ -77,6 +77,24 @@ def test_gmm_iso_full_size(snn, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+def test_stats_without_candidate_count(snn, prec):
+    """stats="phases" (SNN_STATS_NO_CANDIDATES) skips the candidate-range
+    count only: the same CSR and counters, candidates = -1."""
+    w = wl.gmm_iso()
+    X = _dev(w.P)
+    Q = _dev(w.Q)
+    full = snn.Index(X).query(Q, w.R, precision=prec, stats=True)
+    light = snn.Index(X).query(Q, w.R, precision=prec, stats="phases")
+    assert light.stats["candidates"] == -1 and full.stats["candidates"] > 0
+    for k in ("band_pairs", "survivors", "nnz", "exact_fp64", "split_used", "precision_used"):
+        assert light.stats[k] == full.stats[k], k
+    assert torch.equal(light.offsets, full.offsets) and torch.equal(light.indices, full.indices)
+    assert torch.equal(light.dist2.view(torch.int32), full.dist2.view(torch.int32))
+    with pytest.raises(ValueError):
+        snn.Index(X).query(Q, w.R, precision=prec, stats="all")
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_gmm_aniso_self_join_small(snn, prec):
     w = wl.gmm_aniso(n=20011, sub=3000)
     got = _run(snn, w.P, None, w.R, prec)
