@@ -37,10 +37,10 @@ HBM_PEAK_FALLBACK = 6800.0
 SCORER_SOURCES = ["tc_score.cu", "tc_score.cuh", "tc_common.cuh", "common.cuh", "index_struct.cuh",
                   "query_kernels.cuh"]
 SCORER_TRAFFIC = {
-    "sha": "743d81887150c9ea",
+    "sha": "ebb13fbdbb08cd53",
     "profile": "profiles/k_score_tc_dram_traffic_full_size.md",
-    ("gmm_aniso", 1000000, "bf16"): 192621056 + 172989696,
-    ("lowrank_img", 70000, "bf16"): 255685888 + 8194560,
+    ("gmm_aniso", 1000000, "bf16"): 192618240 + 172335360,
+    ("lowrank_img", 70000, "bf16"): 292529408 + 7365632,
 }
 
 
