@@ -1,13 +1,17 @@
 // DBSCAN on the SNN self-join (Section 6.4: the neighbour search inside
-// DBSCAN is replaced by SNN).  From the CSR of eps-neighbourhoods (self
-// included): core flags, union-find over core-core neighbour pairs (hooking
-// the larger root under the smaller with atomicCAS, path halving), border
+// DBSCAN is replaced by SNN).  From the eps-neighbourhoods (self included) of
+// the points in sorted position p (rows unsorted, columns sorted positions;
+// order[p] is the point id): core flags, union-find over core-core neighbour
+// pairs (on point ids, hooking the larger root under the smaller with
+// atomicCAS, path halving: the ids are in the caller's order, where a
+// cluster is not one contiguous run as it is in sorted positions), border
 // points joined to the cluster of their smallest-id core neighbour, and
 // cluster labels canonicalised to the smallest member id.
 #include "dbscan_kernels.cuh"
 
 namespace snn {
 
+// core[p] by position; parent[] over ids
 __global__ void k_db_core(const int64_t *__restrict__ offsets, int64_t n, int32_t min_pts,
                           uint8_t *__restrict__ core, int32_t *__restrict__ parent) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -29,18 +33,22 @@ __device__ __forceinline__ int32_t uf_find(int32_t *parent, int32_t x) {
     return x;
 }
 
-// One warp per core point i: unions i with each core neighbour j < i.
+// One warp per core point (position i): unions its id with the id of each
+// core neighbour of smaller id (each pair once).
 __global__ void k_db_union(const int64_t *__restrict__ offsets, const int32_t *__restrict__ idx,
-                           int64_t n, const uint8_t *__restrict__ core,
+                           int64_t n, const uint8_t *__restrict__ core, const int32_t *__restrict__ order,
                            int32_t *__restrict__ parent) {
     const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= n || !core[i]) return;
+    const int32_t id = order[i];
     const int64_t o0 = offsets[i], o1 = offsets[i + 1];
     for (int64_t o = o0 + lane; o < o1; o += 32) {
         const int32_t j = idx[o];
-        if (j >= i || !core[j]) continue;
-        int32_t a = (int32_t)i, b = j;
+        if (!core[j]) continue;
+        const int32_t jd = order[j];
+        if (jd >= id) continue;
+        int32_t a = id, b = jd;
         for (;;) {
             a = uf_find(parent, a);
             b = uf_find(parent, b);
@@ -53,25 +61,29 @@ __global__ void k_db_union(const int64_t *__restrict__ offsets, const int32_t *_
     }
 }
 
-// root[i] for cores; for border points the root of the smallest-id core
-// neighbour (row ids are ascending); -1 for noise.  Also the label candidate.
+// The root (an id) of position p's cluster: its own for cores, that of the
+// core neighbour of smallest id for border points (a scan of the whole row:
+// rows are unsorted); -1 for noise.  The cluster's label candidate is the
+// smallest member id.
 __global__ void k_db_assign(const int64_t *__restrict__ offsets, const int32_t *__restrict__ idx,
-                            int64_t n, const uint8_t *__restrict__ core,
+                            int64_t n, const uint8_t *__restrict__ core, const int32_t *__restrict__ order,
                             int32_t *__restrict__ parent, int32_t *__restrict__ owner,
                             int32_t *__restrict__ minid) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int32_t r = -1;
     if (core[i]) {
-        r = uf_find(parent, (int32_t)i);
+        r = uf_find(parent, order[i]);
     } else {
+        int32_t best_id = INT32_MAX;
         for (int64_t o = offsets[i]; o < offsets[i + 1]; ++o) {
             const int32_t j = idx[o];
-            if (core[j]) { r = uf_find(parent, j); break; }
+            if (core[j]) best_id = min(best_id, order[j]);
         }
+        if (best_id != INT32_MAX) r = uf_find(parent, best_id);
     }
     owner[i] = r;
-    if (r >= 0) atomicMin(&minid[r], (int32_t)i);
+    if (r >= 0) atomicMin(&minid[r], order[i]);
 }
 
 __global__ void k_db_init_minid(int32_t *__restrict__ minid, int64_t n) {
@@ -79,12 +91,16 @@ __global__ void k_db_init_minid(int32_t *__restrict__ minid, int64_t n) {
     if (i < n) minid[i] = INT32_MAX;
 }
 
+// Results by point id: labels[order[p]], is_core[order[p]].
 __global__ void k_db_label(const int32_t *__restrict__ owner, const int32_t *__restrict__ minid,
-                           int64_t n, int32_t *__restrict__ labels) {
+                           const uint8_t *__restrict__ core, const int32_t *__restrict__ order, int64_t n,
+                           int32_t *__restrict__ labels, uint8_t *__restrict__ is_core) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int32_t r = owner[i];
-    labels[i] = r >= 0 ? minid[r] : -1;
+    const int32_t id = order[i];
+    labels[id] = r >= 0 ? minid[r] : -1;
+    is_core[id] = core[i];
 }
 
 }  // namespace snn

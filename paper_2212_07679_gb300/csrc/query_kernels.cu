@@ -711,6 +711,36 @@ __global__ void k_scatter(const uint2 *__restrict__ surv, const int32_t *__restr
     }
 }
 
+// The same placement for rows that stay in sorted positions (the internal
+// neighbourhoods of DBSCAN): column positions only, rows unsorted.
+__global__ void k_scatter_pos(const uint2 *__restrict__ surv, const int32_t *__restrict__ rec_pos,
+                              int64_t nsurv, int64_t rstride, int sym, const int64_t *__restrict__ offsets,
+                              int32_t *__restrict__ cols) {
+    constexpr int U = 4;
+    const int64_t base = (int64_t(blockIdx.x) * blockDim.x) * U + threadIdx.x;
+    int32_t p0[U], p1[U];
+    uint2 rc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int64_t s = base + int64_t(u) * blockDim.x;
+        const bool in = s < nsurv;
+        p0[u] = in ? __ldcs(rec_pos + s) : -1;
+        p1[u] = (in && sym) ? __ldcs(rec_pos + rstride + s) : -1;
+        rc[u] = in ? __ldcs(surv + s) : make_uint2(0u, 0u);
+    }
+    int64_t o0[U], o1[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        o0[u] = p0[u] >= 0 ? offsets[rc[u].x] : 0;
+        o1[u] = p1[u] >= 0 ? offsets[rc[u].y] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (p0[u] >= 0) cols[o0[u] + p0[u]] = int32_t(rc[u].y);
+        if (p1[u] >= 0) cols[o1[u] + p1[u]] = int32_t(rc[u].x);
+    }
+}
+
 // ------------------------------------------- per-row sort by column id
 // Rows by length: [0] <= 32, [6] <= 64, [1] <= 128, [5] <= 256, [2] <= 512
 // (one warp each), [3] <= 4096 (one block each), [4] longer (radix sort).

@@ -797,10 +797,13 @@ struct QueryScratch {
 // S >= D^2 (1 - gamma_{d+2}) and fl64(R*R) <= R^2 (1 + u).
 // R: the radius, or with per-query radii Rdev (device, m, query order; out-of-
 // sample queries only) the smallest of them, Rmax the largest (host choices:
-// the BF16 split, the FP8 availability).
+// the BF16 split, the FP8 availability).  pos_rows: the result stays in sorted
+// positions (row p = the query in sorted position p, columns point positions,
+// rows unsorted, no dist2): the internal neighbourhoods of DBSCAN.
 static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int64_t ldq,
                              double R, snn_precision prec, cudaStream_t s, snn_csr *out,
-                             snn_query_stats *stats, const double *Rdev = nullptr, double Rmax = 0.0) {
+                             snn_query_stats *stats, const double *Rdev = nullptr, double Rmax = 0.0,
+                             bool pos_rows = false) {
     NvtxPhase nvtx_("snn query: prepare");
     const bool self = (Q == nullptr);
     double q_nrm_max = self ? (double)ix->nrm_max : 0.0;   // largest centred query norm bound
@@ -1075,19 +1078,26 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         CUDA_Q(cudaGetLastError());
         if (stats) cudaEventRecord(ev[3], s);
         // row offsets twice: of the staging rows in sorted query positions
-        // (soff) and of the output rows by query id
+        // (soff) and of the output rows by query id (the same offsets when
+        // the result stays in positions)
         SNN_LAUNCH(k_counts_to_i64, grid_for(m, 256), 256, 0, s)(counts, m, counts64);
         CUDA_Q(cudaGetLastError());
-        TRY_Q(scan_exclusive<int64_t>(counts64, soff, m, s));
-        SNN_LAUNCH(k_counts_by_id, grid_for(m, 256), 256, 0, s)(counts, qs.order, m, counts64);
-        CUDA_Q(cudaGetLastError());
-        TRY_Q(scan_exclusive<int64_t>(counts64, out->offsets, m, s));
-        // rows by length class (per-row sort below); long rows' sizes scanned
         CUDA_Q(cudaMemsetAsync(cls, 0, 8 * sizeof(unsigned), s));
-        CUDA_Q(cudaMemsetAsync(big_len, 0, m * sizeof(int64_t), s));
-        SNN_LAUNCH(k_seg_classify, grid_for(m, 256), 256, 0, s)(soff, m, lists, big_list, big_len, cls);
-        CUDA_Q(cudaGetLastError());
-        TRY_Q(scan_exclusive<int64_t>(big_len, toff, m, s));
+        if (pos_rows) {
+            soff = out->offsets;
+            TRY_Q(scan_exclusive<int64_t>(counts64, soff, m, s));
+            CUDA_Q(cudaMemsetAsync(toff + m, 0, sizeof(int64_t), s));
+        } else {
+            TRY_Q(scan_exclusive<int64_t>(counts64, soff, m, s));
+            SNN_LAUNCH(k_counts_by_id, grid_for(m, 256), 256, 0, s)(counts, qs.order, m, counts64);
+            CUDA_Q(cudaGetLastError());
+            TRY_Q(scan_exclusive<int64_t>(counts64, out->offsets, m, s));
+            // rows by length class (per-row sort below); long rows' sizes scanned
+            CUDA_Q(cudaMemsetAsync(big_len, 0, m * sizeof(int64_t), s));
+            SNN_LAUNCH(k_seg_classify, grid_for(m, 256), 256, 0, s)(soff, m, lists, big_list, big_len, cls);
+            CUDA_Q(cudaGetLastError());
+            TRY_Q(scan_exclusive<int64_t>(big_len, toff, m, s));
+        }
         SNN_LAUNCH(k_readback, 1, 32, 0, s)(ctr, bad, dev_err, out->offsets + m, cls, toff + m, dev_rb);
         CUDA_Q(cudaGetLastError());
         {
@@ -1139,7 +1149,12 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     }
     out->nnz = nnz;
     nvtx_.next("snn query: CSR");
-    if (nnz > 0) {
+    if (nnz > 0 && pos_rows) {
+        TRY_Q(dev_alloc(&out->indices, nnz, s));
+        SNN_LAUNCH(k_scatter_pos, grid_for(nsurv, 1024), 256, 0, s)(surv, rec_pos, nsurv, cap, sym, soff,
+                                                                   out->indices);
+        CUDA_Q(cudaGetLastError());
+    } else if (nnz > 0) {
         TRY_Q(dev_alloc(&out->indices, nnz, s));
         TRY_Q(dev_alloc(&out->dist2, nnz, s));
         uint64_t *tmp;
@@ -1540,8 +1555,10 @@ snn_status snn_dbscan(const float *X, int64_t n, int32_t d, int64_t ld, double e
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     snn_index *ix = nullptr;
     SNN_TRY(index_build(X, n, d, ld, s, &ix));
+    // the eps-neighbourhoods in sorted positions (rows unsorted, no
+    // distances): the clustering needs neither ids nor order within a row
     snn_csr csr;
-    snn_status st = snn_query_radius(ix, nullptr, 0, 0, eps, prec, stream, &csr, nullptr);
+    snn_status st = query_impl(ix, nullptr, 0, 0, eps, prec, s, &csr, nullptr, nullptr, 0.0, true);
     if (st != SNN_OK) {
         index_release(ix);
         return st;
@@ -1549,17 +1566,20 @@ snn_status snn_dbscan(const float *X, int64_t n, int32_t d, int64_t ld, double e
     {
         Scratch scr(s);
         int32_t *parent = nullptr, *owner = nullptr, *minid = nullptr;
+        uint8_t *core = nullptr;
         st = scr.alloc(&parent, n);
         if (st == SNN_OK) st = scr.alloc(&owner, n);
         if (st == SNN_OK) st = scr.alloc(&minid, n);
+        if (st == SNN_OK) st = scr.alloc(&core, n);
         if (st == SNN_OK) {
-            SNN_LAUNCH(k_db_core, grid_for(n, 256), 256, 0, s)(csr.offsets, n, min_pts, is_core, parent);
-            SNN_LAUNCH(k_db_union, grid_for(n * 32, 256), 256, 0, s)(csr.offsets, csr.indices, n, is_core,
-                                                             parent);
+            SNN_LAUNCH(k_db_core, grid_for(n, 256), 256, 0, s)(csr.offsets, n, min_pts, core, parent);
+            SNN_LAUNCH(k_db_union, grid_for(n * 32, 256), 256, 0, s)(csr.offsets, csr.indices, n, core,
+                                                             ix->order, parent);
             SNN_LAUNCH(k_db_init_minid, grid_for(n, 256), 256, 0, s)(minid, n);
-            SNN_LAUNCH(k_db_assign, grid_for(n, 256), 256, 0, s)(csr.offsets, csr.indices, n, is_core,
+            SNN_LAUNCH(k_db_assign, grid_for(n, 256), 256, 0, s)(csr.offsets, csr.indices, n, core, ix->order,
                                                          parent, owner, minid);
-            SNN_LAUNCH(k_db_label, grid_for(n, 256), 256, 0, s)(owner, minid, n, labels);
+            SNN_LAUNCH(k_db_label, grid_for(n, 256), 256, 0, s)(owner, minid, core, ix->order, n, labels,
+                                                        is_core);
             cudaError_t e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) {

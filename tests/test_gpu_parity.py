@@ -269,6 +269,38 @@ def test_dbscan_small(snn):
     assert np.array_equal(labels.cpu().numpy(), ref_l)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_dbscan_border_points_between_clusters(snn, prec):
+    """Border points reachable from two clusters join the cluster of their
+    smallest-id core neighbour (the GPU scans unsorted neighbourhoods in
+    sorted positions); the hand case of two clusters sharing a border point,
+    under row permutations that reorder the ids against the projections, and
+    chains of points alternating between two clusters."""
+    base = np.array([[5, 0], [6, 0], [5.5, 0.5], [3, 0], [1, 0], [0, 0], [0.5, 0.5],
+                     [6, 0.5], [0, 0.5]], np.float32)
+    rng = np.random.default_rng(61)
+    for perm in [np.arange(len(base))] + [rng.permutation(len(base)) for _ in range(4)]:
+        P = np.ascontiguousarray(base[perm])
+        labels, core = snn.dbscan(_dev(P), 2.0, 4, precision=prec)
+        ref_l, ref_c = oracle.dbscan(P, 2.0, 4)
+        assert np.array_equal(core.cpu().numpy(), ref_c), perm
+        assert np.array_equal(labels.cpu().numpy(), ref_l), perm
+    # many border points: pairs of dense 1-D clusters with sparse bridges
+    pts = []
+    for k in range(40):
+        x0 = 10.0 * k
+        pts.append(np.stack([x0 + rng.uniform(0, 1.0, 30), rng.uniform(0, 0.3, 30)], 1))
+        pts.append(np.stack([x0 + 2.6 + rng.uniform(0, 1.0, 30), rng.uniform(0, 0.3, 30)], 1))
+        pts.append(np.stack([x0 + 1.8 + rng.uniform(-0.05, 0.05, 3), rng.uniform(0, 0.3, 3)], 1))
+    P = np.concatenate(pts).astype(np.float32)
+    P = P[rng.permutation(len(P))]
+    labels, core = snn.dbscan(_dev(P), 0.9, 8, precision=prec)
+    ref_l, ref_c = oracle.dbscan(P, 0.9, 8)
+    assert np.array_equal(core.cpu().numpy(), ref_c)
+    assert np.array_equal(labels.cpu().numpy(), ref_l)
+    assert (ref_c == 0).sum() > 0 and len(np.unique(ref_l[ref_l >= 0])) > 40
+
+
 # ------------------------------------------------------------ batches
 def test_batch_matches_oracle(snn):
     # one call, one persistent scoring launch for all sets: ragged n and d
