@@ -485,8 +485,7 @@ def per_config_ragged(args, snn, torch, flush, stream, steps=5, warmup=2):
     def make_plan(idx, prec="bf16"):
         plan = snn.BatchPlan(idx, [q.shape[0] for q in Qs], Rs, precision=prec,
                              survivor_capacity=64 * M + (1 << 20), nnz_capacity=64 * M + (1 << 20))
-        for t, q in enumerate(Qs):
-            plan.queries(t).copy_(q)
+        plan.set_queries(Qs)
         return plan
 
     def step():

@@ -351,6 +351,19 @@ snn_status snn_batch_plan_create(int32_t nsets, const snn_index *const *idx, con
  * every run; NULL for a self-join set or an invalid t. */
 float *snn_batch_plan_queries(snn_batch_plan *plan, int32_t set);
 
+/* Copies every out-of-sample set's queries into the plan's buffers in one
+ * launch on `stream` (instead of one copy per set).
+ *  Q    host array of nsets device pointers: Q[t] holds m[t] x d FP32 rows
+ *       with stride ldq[t] >= d; ignored (may be NULL) for self-join sets and
+ *       sets of no query.
+ *  ldq  host array of nsets row strides (elements).
+ * Errors: SNN_EINVAL for a NULL plan, Q or ldq, a NULL Q[t] or ldq[t] < d of
+ * an out-of-sample set with queries; SNN_ECUDA on a device failure.  No
+ * synchronisation; NaN or Inf values are reported by the next run's
+ * snn_batch_plan_result. */
+snn_status snn_batch_plan_set_queries(snn_batch_plan *plan, const float *const *Q, const int64_t *ldq,
+                                      void *stream);
+
 /* Enqueues one run on `stream` (no synchronisation). */
 snn_status snn_batch_plan_run(snn_batch_plan *plan, void *stream);
 

@@ -1173,6 +1173,55 @@ snn_status plan_create(int32_t nsets, const snn_index *const *idx, const int64_t
     return SNN_OK;
 }
 
+// All out-of-sample sets' query rows in one launch: element e of the
+// concatenated m_t x d_t blocks (prefix eoff) goes to the plan buffer.
+struct QCopyJob {
+    const float *src;
+    float *dst;
+    int64_t ld;
+    int d;
+};
+__global__ void k_plan_copy_queries(const QCopyJob *__restrict__ jobs, const int64_t *__restrict__ eoff, int njobs) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= eoff[njobs]) return;
+    int lo = 0, hi = njobs - 1;   // last job with eoff <= e
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (eoff[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    const QCopyJob &J = jobs[lo];
+    const int64_t k = e - eoff[lo], r = k / J.d, c = k - r * J.d;
+    J.dst[k] = J.src[r * J.ld + c];
+}
+
+snn_status plan_set_queries(snn_batch_plan *p, const float *const *Q, const int64_t *ldq, cudaStream_t s) {
+    std::vector<QCopyJob> jobs;
+    std::vector<int64_t> eoff(1, 0);
+    for (int32_t t = 0; t < p->nsets; ++t) {
+        if (p->qbuf_off[t] < 0 || p->sd[t].m == 0) continue;
+        const int d = p->sd[t].d;
+        if (!Q[t] || ldq[t] < d) {
+            set_error("set %d: queries NULL or ldq < d", t);
+            return SNN_EINVAL;
+        }
+        jobs.push_back(QCopyJob{Q[t], p->qbuf + p->qbuf_off[t], ldq[t], d});
+        eoff.push_back(eoff.back() + p->sd[t].m * d);
+    }
+    const int nj = int(jobs.size());
+    if (nj == 0) return SNN_OK;
+    Scratch scr(s);
+    QCopyJob *dj;
+    int64_t *de;
+    SNN_TRY(scr.alloc(&dj, nj));
+    SNN_TRY(scr.alloc(&de, nj + 1));
+    // (copies from pageable host memory have read their source on return)
+    SNN_CUDA(cudaMemcpyAsync(dj, jobs.data(), nj * sizeof(QCopyJob), cudaMemcpyHostToDevice, s));
+    SNN_CUDA(cudaMemcpyAsync(de, eoff.data(), (nj + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    SNN_LAUNCH(k_plan_copy_queries, unsigned(cdiv(eoff.back(), 256)), 256, 0, s)(dj, de, nj);
+    SNN_LAUNCH_CHECK();
+    return SNN_OK;
+}
+
 float *plan_queries(snn_batch_plan *p, int32_t t) {
     if (!p || t < 0 || t >= p->nsets || p->qbuf_off[t] < 0) return nullptr;
     return p->qbuf + p->qbuf_off[t];

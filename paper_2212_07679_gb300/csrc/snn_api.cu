@@ -1253,6 +1253,7 @@ snn_status plan_create(int32_t nsets, const snn_index *const *idx, const int64_t
                        cudaStream_t s, snn_batch_plan **out);
 void plan_release(snn_batch_plan *p, cudaStream_t s);
 float *plan_queries(snn_batch_plan *p, int32_t t);
+snn_status plan_set_queries(snn_batch_plan *p, const float *const *Q, const int64_t *ldq, cudaStream_t s);
 snn_status plan_run(snn_batch_plan *p, cudaStream_t s);
 snn_status plan_launch_graph(snn_batch_plan *p, cudaStream_t s);
 snn_status plan_result(snn_batch_plan *p, cudaStream_t s, snn_csr *out, int64_t *need_surv,
@@ -1498,6 +1499,16 @@ snn_status snn_batch_plan_create(int32_t nsets, const snn_index *const *idx, con
 }
 
 float *snn_batch_plan_queries(snn_batch_plan *plan, int32_t set) { return plan_queries(plan, set); }
+
+snn_status snn_batch_plan_set_queries(snn_batch_plan *plan, const float *const *Q, const int64_t *ldq,
+                                      void *stream) {
+    clear_error();
+    if (!plan || !Q || !ldq) {
+        set_error("plan, Q or ldq is NULL");
+        return SNN_EINVAL;
+    }
+    return plan_set_queries(plan, Q, ldq, static_cast<cudaStream_t>(stream));
+}
 
 snn_status snn_batch_plan_run(snn_batch_plan *plan, void *stream) {
     clear_error();

@@ -750,15 +750,14 @@ __device__ __forceinline__ uint16_t half_bits(float v) {
 // the lanes, eight loads in flight per lane before the conversions (float4
 // loads, 8-byte stores, coalesced in both arrays), then the folded columns
 // with one lane per row (their few FP64 operations then run on full warps).
+// The 32 rows r0 .. r0 + 31 of one warp.
 template <int NSPLIT>
-__global__ void __launch_bounds__(256, 4) k_tc_pack(const float *__restrict__ xc, int dp, const float *__restrict__ hx,
-                          const float *__restrict__ nrm, const double *__restrict__ Aq,
-                          int64_t rows, int d, int K2, int K2n, double c, int query_side,
-                          uint16_t *__restrict__ p0, uint16_t *__restrict__ p1,
-                          uint16_t *__restrict__ p2, TcPackMode pm) {
-    const int64_t r0 = ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * 32;
-    const int lane = threadIdx.x & 31;
-    if (r0 >= rows) return;   // whole warps leave together
+__device__ __forceinline__ void tc_pack_warp(int64_t r0, int lane, const float *__restrict__ xc, int dp,
+                                             const float *__restrict__ hx, const float *__restrict__ nrm,
+                                             const double *__restrict__ Aq, int64_t rows, int d, int K2,
+                                             int K2n, double c, int query_side, uint16_t *__restrict__ p0,
+                                             uint16_t *__restrict__ p1, uint16_t *__restrict__ p2,
+                                             const TcPackMode &pm) {
     const int nr = int(min(int64_t(32), rows - r0));
     // quads over the folded columns are written as zeros here and
     // overwritten below (after __syncwarp)
@@ -850,6 +849,43 @@ __global__ void __launch_bounds__(256, 4) k_tc_pack(const float *__restrict__ xc
             }
         }
     }
+}
+
+template <int NSPLIT>
+__global__ void __launch_bounds__(256, 4) k_tc_pack(const float *__restrict__ xc, int dp, const float *__restrict__ hx,
+                          const float *__restrict__ nrm, const double *__restrict__ Aq,
+                          int64_t rows, int d, int K2, int K2n, double c, int query_side,
+                          uint16_t *__restrict__ p0, uint16_t *__restrict__ p1,
+                          uint16_t *__restrict__ p2, TcPackMode pm) {
+    const int64_t r0 = ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * 32;
+    if (r0 >= rows) return;   // whole warps leave together
+    tc_pack_warp<NSPLIT>(r0, threadIdx.x & 31, xc, dp, hx, nrm, Aq, rows, d, K2, K2n, c, query_side, p0, p1, p2,
+                         pm);
+}
+
+// Data rows of every set of a batch group in one launch (two FP16 parts):
+// job t owns the warps warp0[t] .. warp0[t + 1] - 1, 32 rows each.
+struct TcPackJob {
+    const float *xc, *hx, *nrm;
+    uint16_t *p0, *p1;
+    int64_t rows;
+    int d, dp;
+    double c;
+    TcPackMode pm;
+};
+__global__ void __launch_bounds__(256, 2) k_tc_pack_jobs(const TcPackJob *__restrict__ jobs,
+                                                         const int64_t *__restrict__ warp0, int njobs, int K2,
+                                                         int K2n) {
+    const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    if (w >= warp0[njobs]) return;
+    int lo = 0, hi = njobs - 1;   // last job with warp0 <= w
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (warp0[mid] <= w) lo = mid; else hi = mid - 1;
+    }
+    const TcPackJob &J = jobs[lo];
+    tc_pack_warp<2>((w - warp0[lo]) * 32, threadIdx.x & 31, J.xc, J.dp, J.hx, J.nrm, nullptr, J.rows, J.d, K2, K2n,
+                    J.c, 0, J.p0, J.p1, nullptr, J.pm);
 }
 
 // ------------------------------------------------ FP8 operand packing
@@ -1876,18 +1912,37 @@ snn_status tc_batch_create(const snn_index *const *idx, const SetDesc *sd, const
         set_error("tensor-core group setup copy failed");
         return fail(SNN_ECUDA);
     }
-    // the data operands of every set, packed once into the group's rows
-    for (int k = 0; k < nsets; ++k) {
-        const snn_index *ix = idx[sets[k]];
-        const TcbSet &S = hs[k];
-        const TcPackMode pm{1, fold_col, S.xscale, S.fs1, S.fs2};
-        SNN_LAUNCH(k_tc_pack<2>, unsigned(cdiv(cdiv(ix->n, 32) * 32, 256)), 256, 0, s)(
-            ix->xc, ix->dp, ix->hx, ix->nrm, nullptr, ix->n, ix->d, g->K2, g->K2n, S.c, 0,
-            g->x0 + S.xoff * g->K2, g->x1 + S.xoff * g->K2n, nullptr, pm);
+    // the data operands of every set, packed once into the group's rows:
+    // one launch over all sets (a job per set, 32 rows per warp)
+    {
+        std::vector<TcPackJob> jobs(nsets);
+        std::vector<int64_t> warp0(nsets + 1, 0);
+        for (int k = 0; k < nsets; ++k) {
+            const snn_index *ix = idx[sets[k]];
+            const TcbSet &S = hs[k];
+            jobs[k] = TcPackJob{ix->xc, ix->hx, ix->nrm, g->x0 + S.xoff * g->K2, g->x1 + S.xoff * g->K2n, ix->n,
+                                ix->d, ix->dp, S.c, TcPackMode{1, fold_col, S.xscale, S.fs1, S.fs2}};
+            warp0[k + 1] = warp0[k] + cdiv(ix->n, 32);
+        }
+        TcPackJob *d_jobs = nullptr;
+        int64_t *d_warp0 = nullptr;
+        GTRY(tcb_alloc(g, &d_jobs, nsets, s));
+        GTRY(tcb_alloc(g, &d_warp0, nsets + 1, s));
+        if (cudaMemcpyAsync(d_jobs, jobs.data(), nsets * sizeof(TcPackJob), cudaMemcpyHostToDevice, s) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(d_warp0, warp0.data(), (nsets + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s) !=
+                cudaSuccess) {
+            set_error("tensor-core group setup copy failed");
+            return fail(SNN_ECUDA);
+        }
+        SNN_LAUNCH(k_tc_pack_jobs, unsigned(cdiv(warp0[nsets] * 32, 256)), 256, 0, s)(d_jobs, d_warp0, nsets,
+                                                                                   g->K2, g->K2n);
         if (cudaGetLastError() != cudaSuccess) {
             set_error("tensor-core group packing failed");
             return fail(SNN_ECUDA);
         }
+        // (copies from pageable host memory have read their source when
+        // they return, so the host arrays may go)
     }
     GTRY(make_map(&g->maps[0], g->q0, std::max<int64_t>(g->qrows, 1), g->K2, g->BK, rpg));
     GTRY(make_map(&g->maps[1], g->q1, std::max<int64_t>(g->qrows, 1), g->K2n, g->NW, rpg));

@@ -136,6 +136,8 @@ def _load():
     lib.snn_batch_plan_create.restype = ctypes.c_int
     lib.snn_batch_plan_queries.argtypes = [vp, i32]
     lib.snn_batch_plan_queries.restype = vp
+    lib.snn_batch_plan_set_queries.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(i64), vp]
+    lib.snn_batch_plan_set_queries.restype = ctypes.c_int
     lib.snn_batch_plan_run.argtypes = [vp, vp]
     lib.snn_batch_plan_run.restype = ctypes.c_int
     lib.snn_batch_plan_launch_graph.argtypes = [vp, vp]
@@ -564,6 +566,30 @@ class BatchPlan:
             return torch.empty((0, self.indices[t].d), dtype=torch.float32, device=self.device)
         m, d = self.ms[t], self.indices[t].d
         return torch.as_tensor(_Borrowed(p, m * d, "<f4"), device=self.device).view(m, d)
+
+    def set_queries(self, Qs: list, stream=None):
+        """Copies every out-of-sample set's queries (Qs[t]: m x d FP32 device
+        rows; None for self-join sets) into the plan in one launch
+        (snn_batch_plan_set_queries)."""
+        k = len(self.ms)
+        if len(Qs) != k:
+            raise ValueError("one query tensor (or None) per set")
+        ptrs, lds, keep = [], [], []
+        for t, q in enumerate(Qs):
+            if self.ms[t] <= 0 or q is None:
+                ptrs.append(None)
+                lds.append(0)
+                continue
+            q, ld = _points(q, "Q")
+            if q.shape != (self.ms[t], self.indices[t].d):
+                raise ValueError(f"set {t}: queries must be {self.ms[t]} x {self.indices[t].d}")
+            keep.append(q)
+            ptrs.append(q.data_ptr())
+            lds.append(ld)
+        qp = (ctypes.c_void_p * k)(*ptrs)
+        lp = (ctypes.c_int64 * k)(*lds)
+        with torch.cuda.device(self.device):
+            _check(lib.snn_batch_plan_set_queries(self._h, qp, lp, _stream_ptr(stream)))
 
     def run(self, stream=None):
         with torch.cuda.device(self.device):

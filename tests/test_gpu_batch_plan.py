@@ -134,6 +134,41 @@ def test_plan_reports_overflow_and_nan(snn):
         _eq(got, oracle.brute_radius(s.P, s.Q, s.R), s.name)
 
 
+def test_plan_set_queries_one_launch(snn):
+    """set_queries copies every out-of-sample set's rows (contiguous or with
+    a row stride) in one launch: the same result as per-set copies; a wrong
+    shape or a missing set is refused."""
+    sets = _sets()
+    idx = snn.build_batch([_dev(s.P) for s in sets])
+    ms = [None if s.Q is None else s.Q.shape[0] for s in sets]
+    plan = snn.BatchPlan(idx, ms, [s.R for s in sets], survivor_capacity=1 << 22, nnz_capacity=1 << 22)
+    qs = []
+    for s in sets:
+        if s.Q is None:
+            qs.append(None)
+            continue
+        wide = torch.zeros((s.Q.shape[0], s.Q.shape[1] + 5), dtype=torch.float32, device="cuda")
+        wide[:, :s.Q.shape[1]] = _dev(s.Q)
+        qs.append(wide[:, :s.Q.shape[1]])          # row stride d + 5
+    launches = snn.launch_count()
+    plan.set_queries(qs)
+    assert snn.launch_count() - launches == 1
+    for t, s in enumerate(sets):
+        if s.Q is not None:
+            assert torch.equal(plan.queries(t), _dev(s.Q)), t
+    plan.run()
+    for s, got in zip(sets, plan.result()):
+        _eq(got, oracle.brute_radius(s.P, s.Q, s.R), s.name)
+    t = next(t for t, s in enumerate(sets) if s.Q is not None)
+    bad = list(qs)
+    bad[t] = qs[t][:-1]
+    with pytest.raises(ValueError):
+        plan.set_queries(bad)
+    with pytest.raises(ValueError):
+        plan.set_queries(qs[:-1])
+    plan.close()
+
+
 def _plan(snn, sets, prec, cap=1 << 22):
     idx = snn.build_batch([_dev(s.P) for s in sets])
     ms = [None if s.Q is None else s.Q.shape[0] for s in sets]
