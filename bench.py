@@ -913,8 +913,7 @@ def run_ragged(args):
     def make_plan(idx):
         plan = snn.BatchPlan(idx, [q.shape[0] for q in Qs], Rs, precision=args.precision,
                              survivor_capacity=64 * M + (1 << 20), nnz_capacity=64 * M + (1 << 20))
-        for t, q in enumerate(Qs):
-            plan.queries(t).copy_(q)
+        plan.set_queries(Qs)
         return plan
 
     def step():

@@ -632,16 +632,30 @@ k_gather_batch(const BSet *__restrict__ sets, const uint64_t *__restrict__ skeys
         const int64_t r = p - st.p0;
         const int64_t i = int64_t(svals[p]) - st.p0;
         const int d = st.d, dp = st.dp;
+        // float4 rows out (dp = 4k); float4 rows in where every input row
+        // starts on a 16-byte boundary and d = dp
+        const bool vin = d == dp && (st.ld & 3) == 0 && (reinterpret_cast<uintptr_t>(st.X) & 15) == 0;
+        const float *xi = st.X + i * st.ld;
+        float4 *praw4 = reinterpret_cast<float4 *>(st.praw + r * dp);
+        float4 *xc4 = reinterpret_cast<float4 *>(st.xc + r * dp);
         float s = 0.f;
-        for (int k = 0; k < dp; ++k) {
-            float pv = 0.f, x = 0.f;
-            if (k < d) {
-                pv = st.X[i * st.ld + k];
-                x = pv - st.mu32[k];
+        for (int k4 = 0; k4 < dp / 4; ++k4) {
+            float pv[4], x[4];
+            if (vin) {
+                const float4 v = reinterpret_cast<const float4 *>(xi)[k4];
+                pv[0] = v.x, pv[1] = v.y, pv[2] = v.z, pv[3] = v.w;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) pv[e] = 4 * k4 + e < d ? xi[4 * k4 + e] : 0.f;
             }
-            st.praw[r * dp + k] = pv;
-            st.xc[r * dp + k] = x;
-            s = fmaf(x, x, s);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int k = 4 * k4 + e;
+                x[e] = k < d ? pv[e] - st.mu32[k] : 0.f;
+                s = fmaf(x[e], x[e], s);
+            }
+            praw4[k4] = make_float4(pv[0], pv[1], pv[2], pv[3]);
+            xc4[k4] = make_float4(x[0], x[1], x[2], x[3]);
         }
         st.alpha[r] = key_to_float(uint32_t(skeys[p] & 0xffffffffu));
         st.order[r] = int32_t(i);

@@ -537,6 +537,54 @@ def build_batch(Xs: list, stream=None) -> list:
     return out
 
 
+class _PlanViews:
+    """Per-set CSR views of a batch plan's result arrays: the sets' arrays are
+    slices of three plan arrays, each wrapped once as a tensor over its span
+    and narrowed per set on access."""
+
+    _ARRAYS = (("offsets", 8, "<i8", torch.int64), ("indices", 4, "<i4", torch.int32),
+               ("dist2", 4, "<f4", torch.float32))
+
+    def __init__(self, outs, device):
+        self._outs = outs
+        self._device = device
+        self._spans = {}
+        for key, size, typestr, dtype in self._ARRAYS:
+            ext = [(getattr(c, key), self._count(c, key)) for c in outs]
+            ext = [(p, n) for p, n in ext if p and n > 0]
+            if ext:
+                lo = min(p for p, _ in ext)
+                hi = max(p + n * size for p, n in ext)
+                self._spans[key] = (lo, size, torch.as_tensor(_Borrowed(lo, (hi - lo) // size, typestr),
+                                                              device=device))
+
+    @staticmethod
+    def _count(c, key):
+        return c.m + 1 if key == "offsets" else c.nnz
+
+    def __len__(self):
+        return len(self._outs)
+
+    def __getitem__(self, t):
+        if isinstance(t, slice):
+            return [self[i] for i in range(*t.indices(len(self)))]
+        if t < 0:
+            t += len(self)
+        c = self._outs[t]
+        arrs = []
+        for key, _, _, dtype in self._ARRAYS:
+            ptr, n = getattr(c, key), self._count(c, key)
+            if not ptr or n == 0:
+                arrs.append(torch.empty(0, dtype=dtype, device=self._device))
+            else:
+                lo, size, base = self._spans[key]
+                arrs.append(base.narrow(0, (ptr - lo) // size, n))
+        return CSR(*arrs)
+
+    def __iter__(self):
+        return (self[t] for t in range(len(self)))
+
+
 class BatchPlan:
     """A batched query with fixed sizes (snn_batch_plan_*): runs enqueue
     device work only, so they can be captured into a CUDA graph.  ms[t] is
@@ -617,28 +665,20 @@ class BatchPlan:
         return {"chunks_per_item": c.value, "ctas_per_sm": t.value, "tc_groups": g.value,
                 "tc_mask": m.value, "from_cache": bool(fc.value)}
 
-    def result(self, stream=None, copy: bool = True) -> list:
-        """Per-set results of the last run (copies unless copy=False: then
-        the tensors view the plan's arrays until the next run)."""
+    def result(self, stream=None, copy: bool = True):
+        """Per-set results of the last run: a list of copies, or with
+        copy=False a sequence of per-set views of the plan's arrays (made on
+        access; valid until the next run)."""
         k = len(self.indices)
         outs = (CSRStruct * k)()
         ns, nz = ctypes.c_int64(), ctypes.c_int64()
         with torch.cuda.device(self.device):
             _check(lib.snn_batch_plan_result(self._h, _stream_ptr(stream), outs, ctypes.byref(ns),
                                              ctypes.byref(nz)))
-        res = []
-        for t in range(k):
-            cs = outs[t]
-
-            def view(ptr, count, typestr, dtype):
-                if not ptr or count == 0:
-                    return torch.empty(0, dtype=dtype, device=self.device)
-                v = torch.as_tensor(_Borrowed(ptr, count, typestr), device=self.device)
-                return v.clone() if copy else v
-            res.append(CSR(view(cs.offsets, cs.m + 1, "<i8", torch.int64),
-                           view(cs.indices, cs.nnz, "<i4", torch.int32),
-                           view(cs.dist2, cs.nnz, "<f4", torch.float32)))
-        return res
+        views = _PlanViews(outs, self.device)
+        if not copy:
+            return views
+        return [CSR(v.offsets.clone(), v.indices.clone(), v.dist2.clone()) for v in views]
 
     def close(self, stream=None):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -157,8 +157,14 @@ def test_plan_set_queries_one_launch(snn):
         if s.Q is not None:
             assert torch.equal(plan.queries(t), _dev(s.Q)), t
     plan.run()
-    for s, got in zip(sets, plan.result()):
+    copies = plan.result()
+    views = plan.result(copy=False)              # per-set views, made on access
+    assert len(views) == len(sets)
+    for s, got, v in zip(sets, copies, views):
         _eq(got, oracle.brute_radius(s.P, s.Q, s.R), s.name)
+        assert torch.equal(v.offsets, got.offsets) and torch.equal(v.indices, got.indices), s.name
+        assert torch.equal(v.dist2, got.dist2), s.name
+    assert torch.equal(views[-1].indices, copies[-1].indices) and len(views[1:3]) == 2
     t = next(t for t, s in enumerate(sets) if s.Q is not None)
     bad = list(qs)
     bad[t] = qs[t][:-1]
