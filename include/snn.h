@@ -489,8 +489,8 @@ const char *snn_version(void);
  *                alpha_sorted[r]; equal keys keep their input order.
  * The call allocates nothing.  It copies a NaN/Inf flag to the host and
  * synchronises `stream` once, before sorting.  The first call on a device
- * looks up the device address of the static array (make that first call
- * before any stream capture).  All calls share the one array and it keeps
+ * looks up the device address of the static array.  All calls share the one
+ * array and it keeps
  * the last call's contents, so calls whose device work overlaps (different
  * streams, or different host threads on one device) race: serialise them. */
 snn_status snn_sort_scores_noalloc(const float *alpha, int64_t n, float *alpha_sorted,
