@@ -490,9 +490,9 @@ const char *snn_version(void);
  * The call allocates nothing.  It copies a NaN/Inf flag to the host and
  * synchronises `stream` once, before sorting.  The first call on a device
  * looks up the device address of the static array.  All calls share the one
- * array and it keeps
- * the last call's contents, so calls whose device work overlaps (different
- * streams, or different host threads on one device) race: serialise them. */
+ * array and it keeps the last call's contents, so calls whose device work
+ * overlaps (different streams, or different host threads on one device)
+ * race: serialise them. */
 snn_status snn_sort_scores_noalloc(const float *alpha, int64_t n, float *alpha_sorted,
                                    int32_t *order, void *stream);
 
