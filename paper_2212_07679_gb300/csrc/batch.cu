@@ -865,7 +865,8 @@ snn_status plan_enqueue(snn_batch_plan *p, cudaStream_t s) {
         SNN_LAUNCH_CHECK();
         int bits = 32;
         while ((int64_t(1) << (bits - 32)) < p->noos) ++bits;
-        SNN_TRY(radix_sort_pairs<uint64_t>(p->keys, p->vals, p->keys_alt, p->vals_alt, Moos, bits, s));
+        // (a bounded wait of the sort that gives up sets bit 0 of tc_err)
+        SNN_TRY(radix_sort_pairs<uint64_t>(p->keys, p->vals, p->keys_alt, p->vals_alt, Moos, bits, s, p->tc_err));
         SNN_LAUNCH(k_b_gather, unsigned(cdiv(Moos, 256)), 256, 0, s)(
             p->d_od, p->d_ooff, p->noos, Moos, p->keys, p->vals, p->q_alpha, p->q_order, p->q_raw,
             p->q_xc, p->q_hx, p->q_nrm);
@@ -1280,7 +1281,7 @@ snn_status plan_result(snn_batch_plan *p, cudaStream_t s, snn_csr *out, int64_t 
     if (need_nnz) *need_nnz = hs.nnz;
     if (hs.bad) { set_error("a query set contains NaN or Inf"); return SNN_EINVAL; }
     if (hs.tcerr & 1) {
-        set_error("tensor-core scoring: a bounded wait gave up (pipeline stalled)");
+        set_error("a bounded wait gave up (tensor-core scoring or the query sort)");
         return SNN_ETIMEOUT;
     }
     if (hs.tcerr & 2) {

@@ -157,7 +157,7 @@ snn_status index_build_batch(int32_t nsets, const float *const *X, const int64_t
             BTRY(scr.alloc(&keys_alt, N));
             BTRY(scr.alloc(&vals, N));
             BTRY(scr.alloc(&vals_alt, N));
-            BTRY(scr.alloc(&bad, 1));
+            BTRY(scr.alloc(&bad, 2));   // [0] NaN/Inf, [1] a bounded wait of the sort expired
             auto up = [&](void *dst, const void *src, size_t bytes) {
                 return bytes == 0 ? cudaSuccess
                                   : cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
@@ -168,7 +168,7 @@ snn_status index_build_batch(int32_t nsets, const float *const *X, const int64_t
                 up(dg32, bg32.data(), bg32.size() * sizeof(BBlk)) != cudaSuccess ||
                 up(dg64, bg64.data(), bg64.size() * sizeof(BBlk)) != cudaSuccess ||
                 up(dproj, bproj.data(), bproj.size() * sizeof(BBlk)) != cudaSuccess ||
-                cudaMemsetAsync(bad, 0, sizeof(int), s) != cudaSuccess ||
+                cudaMemsetAsync(bad, 0, 2 * sizeof(int), s) != cudaSuccess ||
                 cudaMemsetAsync(dconst, 0, size_t(nsets) * 16, s) != cudaSuccess) {
                 set_error("batched index build: table upload failed");
                 stt = SNN_ECUDA;
@@ -193,7 +193,7 @@ snn_status index_build_batch(int32_t nsets, const float *const *X, const int64_t
             // K5 one sort of all sets by (set, score); K6 gather
             int bits = 32;
             while ((int64_t(1) << (bits - 32)) < nsets) ++bits;
-            BTRY(radix_sort_pairs<uint64_t>(keys, vals, keys_alt, vals_alt, N, bits, s));
+            BTRY(radix_sort_pairs<uint64_t>(keys, vals, keys_alt, vals_alt, N, bits, s, bad + 1));
             SNN_LAUNCH(k_gather_batch, unsigned(cdiv(N, 256)), 256, 0, s)(dsets, keys, vals, N);
             if (cudaGetLastError() != cudaSuccess) {
                 set_error("batched index build: gather launch failed");
@@ -203,17 +203,20 @@ snn_status index_build_batch(int32_t nsets, const float *const *X, const int64_t
         } while (0);
 #undef BTRY
         std::vector<float> hc(size_t(nsets) * 4);
-        int hbad = 0;
+        int hbad[2] = {0, 0};
         if (stt == SNN_OK) {
             if (cudaMemcpyAsync(hc.data(), dconst, hc.size() * 4, cudaMemcpyDeviceToHost, s) !=
                     cudaSuccess ||
-                cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaMemcpyAsync(hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                 cudaStreamSynchronize(s) != cudaSuccess) {
                 set_error("batched index build failed: %s", cudaGetErrorString(cudaGetLastError()));
                 stt = SNN_ECUDA;
-            } else if (hbad) {
+            } else if (hbad[0]) {
                 set_error("a set contains NaN or Inf");
                 stt = SNN_EINVAL;
+            } else if (hbad[1]) {
+                set_error("batched index build: a bounded wait of the score sort expired");
+                stt = SNN_ETIMEOUT;
             }
         }
         for (int32_t t = 0; stt == SNN_OK && t < nsets; ++t)

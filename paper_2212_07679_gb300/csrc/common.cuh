@@ -151,9 +151,12 @@ snn_status scan_exclusive(const T *in, T *out, int64_t n, cudaStream_t s);
 
 // Stable LSD radix sort of (key, value) pairs by key bits [0, end_bit).
 // Result is left in (keys, vals); (keys_alt, vals_alt) are scratch of n.
+// With an error word (err, which the caller reads back) each 8-bit pass is
+// one launch with decoupled look-back, whose bounded waits set *err if they
+// give up; without one, three to four launches per pass and no waits.
 template <typename K>
 snn_status radix_sort_pairs(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt,
-                            int64_t n, int end_bit, cudaStream_t s);
+                            int64_t n, int end_bit, cudaStream_t s, int *err = nullptr);
 
 int device_sm_count();
 

@@ -379,7 +379,7 @@ static snn_status index_load(const void *buf, int64_t bytes, cudaStream_t s, snn
 // ---------------------------------------------------------- index build
 static snn_status project_sort_gather(const float *X, int64_t n, int d, int64_t ld, int dp,
                                       const float *cvec, const float *v32, cudaStream_t s,
-                                      Scratch &scr, float *eps_out, int *bad, float *alpha,
+                                      Scratch &scr, float *eps_out, int *bad, int *sort_err, float *alpha,
                                       int32_t *order, float *praw, float *xc, float *hx,
                                       float *nrm) {
     uint32_t *keys, *vals, *ka, *va;
@@ -393,7 +393,7 @@ static snn_status project_sort_gather(const float *X, int64_t n, int d, int64_t 
     SNN_LAUNCH(k_project, grid_for(pthreads, 256), 256, 0, s)(X, n, d, ld, cvec, v32, keys, vals,
                                                       eps_out, bad, vec);
     SNN_LAUNCH_CHECK();
-    SNN_TRY(radix_sort_pairs<uint32_t>(keys, vals, ka, va, n, 32, s));
+    SNN_TRY(radix_sort_pairs<uint32_t>(keys, vals, ka, va, n, 32, s, sort_err));
     SNN_LAUNCH(k_gather, grid_for(pthreads, 256), 256, 0, s)(keys, vals, X, n, d, ld, dp, cvec, alpha,
                                                      order, praw, xc, hx, nrm, vec);
     SNN_LAUNCH_CHECK();
@@ -459,7 +459,7 @@ static snn_status index_build(const float *X, int64_t n, int d, int64_t ld, cuda
     TRY_IX(dev_alloc(&ix->dconst, 4, s));
     {
         Scratch scr(s);
-        int *bad;   // [0] NaN/Inf seen, [1] a bounded tensor-core wait expired
+        int *bad;   // [0] NaN/Inf seen, [1] a bounded wait expired (tensor-core Gram or score sort)
         TRY_IX(scr.alloc(&bad, 2));
         if (cudaMemsetAsync(bad, 0, 2 * sizeof(int), s) != cudaSuccess ||
             cudaMemsetAsync(ix->dconst, 0, 4 * sizeof(float), s) != cudaSuccess) {
@@ -501,7 +501,7 @@ static snn_status index_build(const float *X, int64_t n, int d, int64_t ld, cuda
         // K3: first principal direction
         TRY_IX(first_direction(C, diagC, d, ix->v64, ix->v32, bad + 1, s, scr));
         // K4-K6: scores, sort, gather
-        TRY_IX(project_sort_gather(X, n, d, ld, dp, ix->mu32, ix->v32, s, scr, ix->dconst + 0, bad,
+        TRY_IX(project_sort_gather(X, n, d, ld, dp, ix->mu32, ix->v32, s, scr, ix->dconst + 0, bad, bad + 1,
                                    ix->alpha, ix->order, ix->praw, ix->xc, ix->hx, ix->nrm));
         SNN_LAUNCH(k_max_nonneg, std::min<unsigned>(grid_for(n, 256), 1024), 256, 0, s)(ix->nrm, n,
                                                                                 ix->dconst + 1);
@@ -517,7 +517,7 @@ static snn_status index_build(const float *X, int64_t n, int d, int64_t ld, cuda
             TRY_IX(SNN_EINVAL);
         }
         if (hbad[1]) {
-            set_error("index build: a bounded tensor-core wait expired");
+            set_error("index build: a bounded wait expired (tensor-core Gram or score sort)");
             TRY_IX(SNN_ETIMEOUT);
         }
         ix->alpha_err = hc[0];
@@ -628,11 +628,11 @@ static snn_status index_insert(snn_index *ix, const float *X, int64_t k, int64_t
     const int64_t n = ix->n;
     Scratch scr(s);
     PosArrays nw, out;
-    int *bad;
+    int *bad;     // [0] NaN/Inf seen, [1] a bounded wait of the score sort expired
     float *add;   // [0] score error bound of the new points, [1] their largest norm bound
-    SNN_TRY(scr.alloc(&bad, 1));
+    SNN_TRY(scr.alloc(&bad, 2));
     SNN_TRY(scr.alloc(&add, 2));
-    SNN_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    SNN_CUDA(cudaMemsetAsync(bad, 0, 2 * sizeof(int), s));
     SNN_CUDA(cudaMemsetAsync(add, 0, 2 * sizeof(float), s));
     SNN_TRY(scr.alloc(&nw.alpha, k));
     SNN_TRY(scr.alloc(&nw.order, k));
@@ -640,7 +640,7 @@ static snn_status index_insert(snn_index *ix, const float *X, int64_t k, int64_t
     SNN_TRY(scr.alloc(&nw.xc, size_t(k) * dp));
     SNN_TRY(scr.alloc(&nw.hx, k));
     SNN_TRY(scr.alloc(&nw.nrm, k));
-    SNN_TRY(project_sort_gather(X, k, d, ld, dp, ix->mu32, ix->v32, s, scr, add, bad, nw.alpha,
+    SNN_TRY(project_sort_gather(X, k, d, ld, dp, ix->mu32, ix->v32, s, scr, add, bad, bad + 1, nw.alpha,
                                 nw.order, nw.praw, nw.xc, nw.hx, nw.nrm));
     SNN_LAUNCH(k_max_nonneg, std::min<unsigned>(grid_for(k, 256), 1024), 256, 0, s)(nw.nrm, k, add + 1);
     SNN_LAUNCH_CHECK();
@@ -665,19 +665,24 @@ static snn_status index_insert(snn_index *ix, const float *X, int64_t k, int64_t
         return SNN_ECUDA;
     }
     float hadd[2];
-    int hbad = 0;
+    int hbad[2] = {0, 0};
     {
-        const HostRead rd[] = {{add, hadd, int(sizeof(hadd))}, {bad, &hbad, int(sizeof(int))}};
+        const HostRead rd[] = {{add, hadd, int(sizeof(hadd))}, {bad, hbad, int(sizeof(hbad))}};
         const snn_status st = read_to_host(rd, 2, s);
         if (st != SNN_OK) {
             out.release(s);
             return st;
         }
     }
-    if (hbad) {
+    if (hbad[0]) {
         set_error("X contains NaN or Inf");
         out.release(s);
         return SNN_EINVAL;
+    }
+    if (hbad[1]) {
+        set_error("insert: a bounded wait of the score sort expired");
+        out.release(s);
+        return SNN_ETIMEOUT;
     }
     if (!(hadd[1] <= kMaxCentredNorm)) {
         set_error("a centred point norm of %g exceeds %g", (double)hadd[1], kMaxCentredNorm);
@@ -861,9 +866,9 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     QuerySet qs;
     qs.m = m;
     float *eps_q = ix->dconst;   // self-join: the data's own bound
-    int *bad = nullptr;
-    TRY_Q(scr.alloc(&bad, 1));
-    CUDA_Q(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    int *bad = nullptr;   // [0] NaN/Inf in Q, [1] a bounded wait of the query sort expired
+    TRY_Q(scr.alloc(&bad, 2));
+    CUDA_Q(cudaMemsetAsync(bad, 0, 2 * sizeof(int), s));
     if (self) {
         qs.alpha = ix->alpha;
         qs.order = ix->order;
@@ -882,7 +887,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         TRY_Q(scr.alloc(&qnrm, m));
         TRY_Q(scr.alloc(&eps_q, 1));
         CUDA_Q(cudaMemsetAsync(eps_q, 0, sizeof(float), s));
-        TRY_Q(project_sort_gather(Q, m, d, ldq, dp, ix->mu32, ix->v32, s, scr, eps_q, bad, qa,
+        TRY_Q(project_sort_gather(Q, m, d, ldq, dp, ix->mu32, ix->v32, s, scr, eps_q, bad, bad + 1, qa,
                                   qorder, qraw, qxc, qhy, qnrm));
         // NaN/Inf and norm range of the queries, checked before any scoring
         float *qnmax;
@@ -891,14 +896,18 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         SNN_LAUNCH(k_max_nonneg, std::min<unsigned>(grid_for(m, 256), 1024), 256, 0, s)(qnrm, m, qnmax);
         CUDA_Q(cudaGetLastError());
         float hq = 0.f;
-        int hb = 0;
+        int hb[2] = {0, 0};
         {
-            const HostRead rd[] = {{qnmax, &hq, int(sizeof(float))}, {bad, &hb, int(sizeof(int))}};
+            const HostRead rd[] = {{qnmax, &hq, int(sizeof(float))}, {bad, hb, int(sizeof(hb))}};
             TRY_Q(read_to_host(rd, 2, s));
         }
-        if (hb) {
+        if (hb[0]) {
             set_error("Q contains NaN or Inf");
             return fail(SNN_EINVAL);
+        }
+        if (hb[1]) {
+            set_error("query: a bounded wait of the score sort expired");
+            return fail(SNN_ETIMEOUT);
         }
         if (!(hq <= kMaxCentredNorm)) {
             set_error("a centred query norm of %g exceeds %g: the FP32 and BF16 scores would "
