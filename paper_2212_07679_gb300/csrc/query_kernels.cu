@@ -712,9 +712,11 @@ __global__ void k_scatter(const uint2 *__restrict__ surv, const int32_t *__restr
 }
 
 // The same placement for rows that stay in sorted positions (the internal
-// neighbourhoods of DBSCAN): column positions only, rows unsorted.
+// neighbourhoods of DBSCAN): column ids only (porder[y]; mirrored: qorder[x]),
+// rows unsorted.
 __global__ void k_scatter_pos(const uint2 *__restrict__ surv, const int32_t *__restrict__ rec_pos,
                               int64_t nsurv, int64_t rstride, int sym, const int64_t *__restrict__ offsets,
+                              const int32_t *__restrict__ qorder, const int32_t *__restrict__ porder,
                               int32_t *__restrict__ cols) {
     constexpr int U = 4;
     const int64_t base = (int64_t(blockIdx.x) * blockDim.x) * U + threadIdx.x;
@@ -729,15 +731,18 @@ __global__ void k_scatter_pos(const uint2 *__restrict__ surv, const int32_t *__r
         rc[u] = in ? __ldcs(surv + s) : make_uint2(0u, 0u);
     }
     int64_t o0[U], o1[U];
+    int32_t c0[U], c1[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         o0[u] = p0[u] >= 0 ? offsets[rc[u].x] : 0;
+        c0[u] = p0[u] >= 0 ? porder[rc[u].y] : 0;
         o1[u] = p1[u] >= 0 ? offsets[rc[u].y] : 0;
+        c1[u] = p1[u] >= 0 ? qorder[rc[u].x] : 0;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        if (p0[u] >= 0) cols[o0[u] + p0[u]] = int32_t(rc[u].y);
-        if (p1[u] >= 0) cols[o1[u] + p1[u]] = int32_t(rc[u].x);
+        if (p0[u] >= 0) cols[o0[u] + p0[u]] = c0[u];
+        if (p1[u] >= 0) cols[o1[u] + p1[u]] = c1[u];
     }
 }
 

@@ -204,7 +204,8 @@ __global__ void k_scatter(const uint2 *surv, const int32_t *rec_pos, const float
                           const int32_t *qorder, const int32_t *porder, uint64_t *tmp);
 
 __global__ void k_scatter_pos(const uint2 *surv, const int32_t *rec_pos, int64_t nsurv, int64_t rstride,
-                              int sym, const int64_t *offsets, int32_t *cols);
+                              int sym, const int64_t *offsets, const int32_t *qorder, const int32_t *porder,
+                              int32_t *cols);
 
 // Segmented sort of CSR rows by column id; id_bound is an exclusive upper
 // bound on the ids (it selects 32-bit sort keys where they fit).

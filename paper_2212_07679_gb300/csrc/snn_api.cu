@@ -802,9 +802,9 @@ struct QueryScratch {
 // S >= D^2 (1 - gamma_{d+2}) and fl64(R*R) <= R^2 (1 + u).
 // R: the radius, or with per-query radii Rdev (device, m, query order; out-of-
 // sample queries only) the smallest of them, Rmax the largest (host choices:
-// the BF16 split, the FP8 availability).  pos_rows: the result stays in sorted
-// positions (row p = the query in sorted position p, columns point positions,
-// rows unsorted, no dist2): the internal neighbourhoods of DBSCAN.
+// the BF16 split, the FP8 availability).  pos_rows: the rows stay in sorted
+// positions (row p = the query in sorted position p; columns point ids, rows
+// unsorted, no dist2): the internal neighbourhoods of DBSCAN.
 static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int64_t ldq,
                              double R, snn_precision prec, cudaStream_t s, snn_csr *out,
                              snn_query_stats *stats, const double *Rdev = nullptr, double Rmax = 0.0,
@@ -1161,7 +1161,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     if (nnz > 0 && pos_rows) {
         TRY_Q(dev_alloc(&out->indices, nnz, s));
         SNN_LAUNCH(k_scatter_pos, grid_for(nsurv, 1024), 256, 0, s)(surv, rec_pos, nsurv, cap, sym, soff,
-                                                                   out->indices);
+                                                                   qs.order, ds.order, out->indices);
         CUDA_Q(cudaGetLastError());
     } else if (nnz > 0) {
         TRY_Q(dev_alloc(&out->indices, nnz, s));
@@ -1575,8 +1575,8 @@ snn_status snn_dbscan(const float *X, int64_t n, int32_t d, int64_t ld, double e
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     snn_index *ix = nullptr;
     SNN_TRY(index_build(X, n, d, ld, s, &ix));
-    // the eps-neighbourhoods in sorted positions (rows unsorted, no
-    // distances): the clustering needs neither ids nor order within a row
+    // the eps-neighbourhoods by sorted position (columns ids, rows unsorted,
+    // no distances): the clustering needs no order within a row
     snn_csr csr;
     snn_status st = query_impl(ix, nullptr, 0, 0, eps, prec, s, &csr, nullptr, nullptr, 0.0, true);
     if (st != SNN_OK) {
@@ -1586,20 +1586,19 @@ snn_status snn_dbscan(const float *X, int64_t n, int32_t d, int64_t ld, double e
     {
         Scratch scr(s);
         int32_t *parent = nullptr, *owner = nullptr, *minid = nullptr;
-        uint8_t *core = nullptr;
         st = scr.alloc(&parent, n);
         if (st == SNN_OK) st = scr.alloc(&owner, n);
         if (st == SNN_OK) st = scr.alloc(&minid, n);
-        if (st == SNN_OK) st = scr.alloc(&core, n);
         if (st == SNN_OK) {
-            SNN_LAUNCH(k_db_core, grid_for(n, 256), 256, 0, s)(csr.offsets, n, min_pts, core, parent);
-            SNN_LAUNCH(k_db_union, grid_for(n * 32, 256), 256, 0, s)(csr.offsets, csr.indices, n, core,
+            // core flags straight into is_core (by id)
+            SNN_LAUNCH(k_db_core, grid_for(n, 256), 256, 0, s)(csr.offsets, ix->order, n, min_pts, is_core,
+                                                       parent);
+            SNN_LAUNCH(k_db_union, grid_for(n * 32, 256), 256, 0, s)(csr.offsets, csr.indices, n, is_core,
                                                              ix->order, parent);
             SNN_LAUNCH(k_db_init_minid, grid_for(n, 256), 256, 0, s)(minid, n);
-            SNN_LAUNCH(k_db_assign, grid_for(n, 256), 256, 0, s)(csr.offsets, csr.indices, n, core, ix->order,
-                                                         parent, owner, minid);
-            SNN_LAUNCH(k_db_label, grid_for(n, 256), 256, 0, s)(owner, minid, core, ix->order, n, labels,
-                                                        is_core);
+            SNN_LAUNCH(k_db_assign, grid_for(n, 256), 256, 0, s)(csr.offsets, csr.indices, n, is_core,
+                                                         ix->order, parent, owner, minid);
+            SNN_LAUNCH(k_db_label, grid_for(n, 256), 256, 0, s)(owner, minid, ix->order, n, labels);
             cudaError_t e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) {
