@@ -664,9 +664,13 @@ __global__ void k_counts_to_i64(const int32_t *__restrict__ counts, int64_t m,
 }
 
 __global__ void k_counts_by_id(const int32_t *__restrict__ counts, const int32_t *__restrict__ order,
-                               int64_t m, int64_t *__restrict__ out) {
+                               int64_t m, int64_t *__restrict__ out, const int64_t *__restrict__ soff,
+                               uint2 *__restrict__ rinfo) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i < m) out[order[i]] = counts[i];
+    if (i >= m) return;
+    const int32_t id = order[i];
+    if (out) out[id] = counts[i];
+    if (rinfo) rinfo[i] = make_uint2(uint32_t(soff[i]), uint32_t(id));
 }
 
 // Writes each accepted pair at its row slot (and the mirrored pair of a
@@ -674,11 +678,14 @@ __global__ void k_counts_by_id(const int32_t *__restrict__ counts, const int32_t
 // the staging array, whose rows are sorted query positions: the rows of a
 // query tile and of its band are neighbours there, so the stores of one
 // stretch of survivors fall into a window of the array that stays in L2.
-// Column ids are the point ids porder[y] (mirrored: the query ids qorder[x]).
+// rinfo[x] = (staging offset of row x, query id qorder[x]); column ids are
+// the point ids porder[y] (mirrored: qorder[x]).  In a symmetric self-join
+// the points are the queries (porder = qorder), so rinfo[y] gives both the
+// mirrored row's offset and porder[y]: two random 8-byte loads per survivor.
 __global__ void k_scatter(const uint2 *__restrict__ surv, const int32_t *__restrict__ rec_pos,
                           const float *__restrict__ rec_d2, int64_t nsurv, int64_t rstride, int sym,
-                          const int64_t *__restrict__ offsets, const int32_t *__restrict__ qorder,
-                          const int32_t *__restrict__ porder, uint64_t *__restrict__ tmp) {
+                          const uint2 *__restrict__ rinfo, const int32_t *__restrict__ porder,
+                          uint64_t *__restrict__ tmp) {
     // four survivors per thread, every load independent of the others (the
     // chain is rec arrays -> row offset and column id -> store)
     constexpr int U = 4;
@@ -695,28 +702,26 @@ __global__ void k_scatter(const uint2 *__restrict__ surv, const int32_t *__restr
         rc[u] = in ? __ldcs(surv + s) : make_uint2(0u, 0u);
         vb[u] = in ? __float_as_uint(__ldcs(rec_d2 + s)) : 0u;
     }
-    int64_t o0[U], o1[U];
-    uint32_t c0[U], c1[U];
+    uint2 ix[U], iy[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        o0[u] = p0[u] >= 0 ? offsets[rc[u].x] : 0;
-        c0[u] = p0[u] >= 0 ? uint32_t(porder[rc[u].y]) : 0u;
-        o1[u] = p1[u] >= 0 ? offsets[rc[u].y] : 0;
-        c1[u] = p1[u] >= 0 ? uint32_t(qorder[rc[u].x]) : 0u;
+        ix[u] = p0[u] >= 0 ? rinfo[rc[u].x] : make_uint2(0u, 0u);
+        if (sym) iy[u] = p0[u] >= 0 ? rinfo[rc[u].y] : make_uint2(0u, 0u);
+        else iy[u] = make_uint2(0u, p0[u] >= 0 ? uint32_t(porder[rc[u].y]) : 0u);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        if (p0[u] >= 0) tmp[o0[u] + p0[u]] = (uint64_t(c0[u]) << 32) | vb[u];
-        if (p1[u] >= 0) tmp[o1[u] + p1[u]] = (uint64_t(c1[u]) << 32) | vb[u];
+        if (p0[u] >= 0) tmp[int64_t(ix[u].x) + p0[u]] = (uint64_t(iy[u].y) << 32) | vb[u];
+        if (p1[u] >= 0) tmp[int64_t(iy[u].x) + p1[u]] = (uint64_t(ix[u].y) << 32) | vb[u];
     }
 }
 
 // The same placement for rows that stay in sorted positions (the internal
-// neighbourhoods of DBSCAN): column ids only (porder[y]; mirrored: qorder[x]),
-// rows unsorted.
+// neighbourhoods of DBSCAN, a symmetric self-join): column ids only (rinfo[y]
+// = (offset of row y, point id); mirrored entries take the id of x), rows
+// unsorted.
 __global__ void k_scatter_pos(const uint2 *__restrict__ surv, const int32_t *__restrict__ rec_pos,
-                              int64_t nsurv, int64_t rstride, int sym, const int64_t *__restrict__ offsets,
-                              const int32_t *__restrict__ qorder, const int32_t *__restrict__ porder,
+                              int64_t nsurv, int64_t rstride, const uint2 *__restrict__ rinfo,
                               int32_t *__restrict__ cols) {
     constexpr int U = 4;
     const int64_t base = (int64_t(blockIdx.x) * blockDim.x) * U + threadIdx.x;
@@ -727,22 +732,19 @@ __global__ void k_scatter_pos(const uint2 *__restrict__ surv, const int32_t *__r
         const int64_t s = base + int64_t(u) * blockDim.x;
         const bool in = s < nsurv;
         p0[u] = in ? __ldcs(rec_pos + s) : -1;
-        p1[u] = (in && sym) ? __ldcs(rec_pos + rstride + s) : -1;
+        p1[u] = in ? __ldcs(rec_pos + rstride + s) : -1;
         rc[u] = in ? __ldcs(surv + s) : make_uint2(0u, 0u);
     }
-    int64_t o0[U], o1[U];
-    int32_t c0[U], c1[U];
+    uint2 ix[U], iy[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        o0[u] = p0[u] >= 0 ? offsets[rc[u].x] : 0;
-        c0[u] = p0[u] >= 0 ? porder[rc[u].y] : 0;
-        o1[u] = p1[u] >= 0 ? offsets[rc[u].y] : 0;
-        c1[u] = p1[u] >= 0 ? qorder[rc[u].x] : 0;
+        ix[u] = p0[u] >= 0 ? rinfo[rc[u].x] : make_uint2(0u, 0u);
+        iy[u] = p0[u] >= 0 ? rinfo[rc[u].y] : make_uint2(0u, 0u);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        if (p0[u] >= 0) cols[o0[u] + p0[u]] = c0[u];
-        if (p1[u] >= 0) cols[o1[u] + p1[u]] = c1[u];
+        if (p0[u] >= 0) cols[int64_t(ix[u].x) + p0[u]] = int32_t(iy[u].y);
+        if (p1[u] >= 0) cols[int64_t(iy[u].x) + p1[u]] = int32_t(ix[u].y);
     }
 }
 
@@ -792,7 +794,11 @@ __global__ void k_seg_classify(const int64_t *__restrict__ offsets, int64_t m,
 // When every id of the call is below 2^(32 - log2(32E)) the network runs on
 // 32-bit keys (id << log2(32E) | position in the row), which halves the
 // shuffles and replaces each 64-bit compare-and-select by a min and a max;
-// the distances are then fetched by position after the sort.
+// the distances are then fetched by position after the sort.  The 32-bit
+// keys are loaded striped (lane l takes entries l, l + 32, ...: the network
+// sorts whatever order it is given) and the sorted keys pass through shared
+// memory back to the striped layout, so that every load and store of a row
+// is a run of 32 consecutive words.
 __device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int m) {
     const uint32_t lo = __shfl_xor_sync(0xffffffffu, uint32_t(v), m);
     const uint32_t hi = __shfl_xor_sync(0xffffffffu, uint32_t(v >> 32), m);
@@ -847,6 +853,8 @@ __device__ __forceinline__ void bitonic_warp(T (&v)[E], int lane) {
     }
 }
 
+constexpr int kSegWarps = 8;   // warps per block of the per-row sorts
+
 template <int E>
 __device__ __forceinline__ void seg_sort_warp(const int32_t *__restrict__ list, unsigned total,
                                               const SegMap &mp, const uint64_t *__restrict__ tmp,
@@ -855,10 +863,16 @@ __device__ __forceinline__ void seg_sort_warp(const int32_t *__restrict__ list, 
     constexpr int N = 32 * E;
     constexpr int LB = E == 1 ? 5 : (E == 2 ? 6 : (E == 4 ? 7 : (E == 8 ? 8 : 9)));
     static_assert((1 << LB) == N, "position bits");
+    // transpose buffer: position p of a warp's sorted row at p + p / 32 (one
+    // padding word per 32, so that both the blocked writes and the striped
+    // reads hit 32 distinct banks)
+    constexpr int kTr = E > 1 ? N + N / 32 : 1;
+    __shared__ uint32_t s_tr[kSegWarps * kTr];
     const bool k32 = id_bound <= (1u << (32 - LB));
     // 32-bit words of the packed entries: [2i] = dist2 bits, [2i+1] = id
     const uint32_t *__restrict__ w32 = reinterpret_cast<const uint32_t *>(tmp);
     const int lane = threadIdx.x & 31;
+    uint32_t *tr = s_tr + (threadIdx.x >> 5) * kTr;
     const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
     for (int64_t w = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); w < total; w += nw) {
         const int32_t r = list[w];
@@ -869,13 +883,25 @@ __device__ __forceinline__ void seg_sort_warp(const int32_t *__restrict__ list, 
             uint32_t v[E];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                const int i = lane * E + e;
+                const int i = e * 32 + lane;
                 v[e] = i < len ? (w32[2 * (o + i) + 1] << LB) | uint32_t(i) : 0xffffffffu;
             }
             bitonic_warp<E>(v, lane);
+            // sorted: lane holds positions lane * E .. lane * E + E - 1
+            if constexpr (E > 1) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int p = lane * E + e;
+                    tr[p + (p >> 5)] = v[e];
+                }
+                __syncwarp();
+#pragma unroll
+                for (int e = 0; e < E; ++e) v[e] = tr[e * 33 + lane];
+                __syncwarp();
+            }
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                const int i = lane * E + e;
+                const int i = e * 32 + lane;
                 if (i < len) {
                     const uint32_t src = v[e] & uint32_t(N - 1);
                     idx[od + i] = int32_t(v[e] >> LB);
@@ -905,11 +931,22 @@ __device__ __forceinline__ void seg_sort_warp(const int32_t *__restrict__ list, 
 #define SNN_SEG_ARGS                                                                            \
     const int32_t *__restrict__ list, const unsigned *__restrict__ count, SegMap mp,            \
         const uint64_t *__restrict__ tmp, int32_t *idx, float *d2, uint32_t id_bound
-__global__ void k_seg_sort_w1(SNN_SEG_ARGS) { seg_sort_warp<1>(list, *count, mp, tmp, idx, d2, id_bound); }
-__global__ void k_seg_sort_w2(SNN_SEG_ARGS) { seg_sort_warp<2>(list, *count, mp, tmp, idx, d2, id_bound); }
-__global__ void k_seg_sort_w4(SNN_SEG_ARGS) { seg_sort_warp<4>(list, *count, mp, tmp, idx, d2, id_bound); }
-__global__ void k_seg_sort_w8(SNN_SEG_ARGS) { seg_sort_warp<8>(list, *count, mp, tmp, idx, d2, id_bound); }
-__global__ void k_seg_sort_w16(SNN_SEG_ARGS) { seg_sort_warp<16>(list, *count, mp, tmp, idx, d2, id_bound); }
+// blocks of kSegWarps warps (256 threads)
+__global__ void __launch_bounds__(256) k_seg_sort_w1(SNN_SEG_ARGS) {
+    seg_sort_warp<1>(list, *count, mp, tmp, idx, d2, id_bound);
+}
+__global__ void __launch_bounds__(256) k_seg_sort_w2(SNN_SEG_ARGS) {
+    seg_sort_warp<2>(list, *count, mp, tmp, idx, d2, id_bound);
+}
+__global__ void __launch_bounds__(256) k_seg_sort_w4(SNN_SEG_ARGS) {
+    seg_sort_warp<4>(list, *count, mp, tmp, idx, d2, id_bound);
+}
+__global__ void __launch_bounds__(256) k_seg_sort_w8(SNN_SEG_ARGS) {
+    seg_sort_warp<8>(list, *count, mp, tmp, idx, d2, id_bound);
+}
+__global__ void __launch_bounds__(256) k_seg_sort_w16(SNN_SEG_ARGS) {
+    seg_sort_warp<16>(list, *count, mp, tmp, idx, d2, id_bound);
+}
 
 // One block per row of <= 4096 entries: bitonic sort in shared memory, of
 // 32-bit keys (id << 12 | position) when every id is below 2^20, else of the

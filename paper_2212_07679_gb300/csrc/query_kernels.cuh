@@ -197,15 +197,16 @@ SNN_DECIDE_DECL(k_decide_sym_g32);
 SNN_DECIDE_DECL(k_decide_one_g32);
 #undef SNN_DECIDE_DECL
 __global__ void k_counts_to_i64(const int32_t *counts, int64_t m, int64_t *out);
-// out[order[i]] = counts[i]: per-position counts to per-id counts
-__global__ void k_counts_by_id(const int32_t *counts, const int32_t *order, int64_t m, int64_t *out);
+// out[order[i]] = counts[i] (out not null): per-position counts to per-id counts; with
+// rinfo set also rinfo[i] = (soff[i], order[i]) (offsets below 2^31)
+__global__ void k_counts_by_id(const int32_t *counts, const int32_t *order, int64_t m, int64_t *out,
+                               const int64_t *soff, uint2 *rinfo);
 __global__ void k_scatter(const uint2 *surv, const int32_t *rec_pos, const float *rec_d2,
-                          int64_t nsurv, int64_t rstride, int sym, const int64_t *offsets,
-                          const int32_t *qorder, const int32_t *porder, uint64_t *tmp);
+                          int64_t nsurv, int64_t rstride, int sym, const uint2 *rinfo,
+                          const int32_t *porder, uint64_t *tmp);
 
 __global__ void k_scatter_pos(const uint2 *surv, const int32_t *rec_pos, int64_t nsurv, int64_t rstride,
-                              int sym, const int64_t *offsets, const int32_t *qorder, const int32_t *porder,
-                              int32_t *cols);
+                              const uint2 *rinfo, int32_t *cols);
 
 // Segmented sort of CSR rows by column id; id_bound is an exclusive upper
 // bound on the ids (it selects 32-bit sort keys where they fit).

@@ -804,13 +804,18 @@ struct QueryScratch {
 // sample queries only) the smallest of them, Rmax the largest (host choices:
 // the BF16 split, the FP8 availability).  pos_rows: the rows stay in sorted
 // positions (row p = the query in sorted position p; columns point ids, rows
-// unsorted, no dist2): the internal neighbourhoods of DBSCAN.
+// unsorted, no dist2): the internal neighbourhoods of DBSCAN, a self-join
+// (Q null).
 static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int64_t ldq,
                              double R, snn_precision prec, cudaStream_t s, snn_csr *out,
                              snn_query_stats *stats, const double *Rdev = nullptr, double Rmax = 0.0,
                              bool pos_rows = false) {
     NvtxPhase nvtx_("snn query: prepare");
     const bool self = (Q == nullptr);
+    if (pos_rows && !self) {
+        set_error("internal: position rows need a self-join");
+        return SNN_EINVAL;
+    }
     double q_nrm_max = self ? (double)ix->nrm_max : 0.0;   // largest centred query norm bound
     if (self) m = ix->n;
     const int d = ix->d, dp = ix->dp;
@@ -1025,6 +1030,8 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     TRY_Q(scr.alloc(&big_len, m));
     TRY_Q(scr.alloc(&toff, m + 1));
     TRY_Q(scr.alloc(&cls, 8));
+    uint2 *rinfo;
+    TRY_Q(scr.alloc(&rinfo, m));
     const double R2 = R * R;
     // lanes per survivor in the decision: 1 for short rows, 8 up to 128
     // dimensions, 32 beyond (four lanes at d = 16 measured slower: 1.16
@@ -1095,10 +1102,14 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         if (pos_rows) {
             soff = out->offsets;
             TRY_Q(scan_exclusive<int64_t>(counts64, soff, m, s));
+            SNN_LAUNCH(k_counts_by_id, grid_for(m, 256), 256, 0, s)(counts, qs.order, m, nullptr, soff,
+                                                                    rinfo);
+            CUDA_Q(cudaGetLastError());
             CUDA_Q(cudaMemsetAsync(toff + m, 0, sizeof(int64_t), s));
         } else {
             TRY_Q(scan_exclusive<int64_t>(counts64, soff, m, s));
-            SNN_LAUNCH(k_counts_by_id, grid_for(m, 256), 256, 0, s)(counts, qs.order, m, counts64);
+            SNN_LAUNCH(k_counts_by_id, grid_for(m, 256), 256, 0, s)(counts, qs.order, m, counts64, soff,
+                                                                    rinfo);
             CUDA_Q(cudaGetLastError());
             TRY_Q(scan_exclusive<int64_t>(counts64, out->offsets, m, s));
             // rows by length class (per-row sort below); long rows' sizes scanned
@@ -1160,8 +1171,8 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
     nvtx_.next("snn query: CSR");
     if (nnz > 0 && pos_rows) {
         TRY_Q(dev_alloc(&out->indices, nnz, s));
-        SNN_LAUNCH(k_scatter_pos, grid_for(nsurv, 1024), 256, 0, s)(surv, rec_pos, nsurv, cap, sym, soff,
-                                                                   qs.order, ds.order, out->indices);
+        SNN_LAUNCH(k_scatter_pos, grid_for(nsurv, 1024), 256, 0, s)(surv, rec_pos, nsurv, cap, rinfo,
+                                                                   out->indices);
         CUDA_Q(cudaGetLastError());
     } else if (nnz > 0) {
         TRY_Q(dev_alloc(&out->indices, nnz, s));
@@ -1169,7 +1180,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         uint64_t *tmp;
         TRY_Q(scr.alloc(&tmp, nnz));
         SNN_LAUNCH(k_scatter, grid_for(nsurv, 1024), 256, 0, s)(surv, rec_pos, rec_d2, nsurv, cap, sym,
-                                                               soff, qs.order, ds.order, tmp);
+                                                               rinfo, ds.order, tmp);
         CUDA_Q(cudaGetLastError());
         // per-row ascending column ids: staging rows (sorted query positions)
         // to output rows (query ids); classes with no rows are skipped and the
