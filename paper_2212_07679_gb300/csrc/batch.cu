@@ -649,29 +649,22 @@ snn_status batch_query(int32_t nsets, const snn_index *const *idx, const float *
         SNN_LAUNCH(k_b_scatter, unsigned(cdiv(nsurv, 256)), 256, 0, s)(
             surv, ctr, nsurv, d_sets, qset, rec_d2, rec_pos, goff, tmp, nullptr);
         // per-row ascending ids over the global CSR (rows of every set)
-        int32_t *lists, *big_list;
+        ulonglong2 *lists;
+        int32_t *big_list;
         int64_t *big_len, *toff;
         unsigned *cls;
-        st = scr.alloc(&lists, 6 * M);
+        st = scr.alloc(&lists, int64_t(kSegSlotsFine) * M);
         if (st == SNN_OK) st = scr.alloc(&big_list, M);
         if (st == SNN_OK) st = scr.alloc(&big_len, M);
         if (st == SNN_OK) st = scr.alloc(&toff, M + 1);
-        if (st == SNN_OK) st = scr.alloc(&cls, 8);
+        if (st == SNN_OK) st = scr.alloc(&cls, kSegClasses);
         if (st != SNN_OK) return fail(st);
-        cudaMemsetAsync(cls, 0, 8 * sizeof(unsigned), s);
-        SNN_LAUNCH(k_seg_classify, unsigned(cdiv(M, 256)), 256, 0, s)(goff, M, lists, big_list,
-                                                                      big_len, cls);
-        const unsigned wgrid = std::min<unsigned>(unsigned(cdiv(M * 32, 256)), 16384);
-        const uint32_t ib = ids_bound(sd);
+        cudaMemsetAsync(cls, 0, kSegClasses * sizeof(unsigned), s);
         const SegMap gm{goff, goff, nullptr};
-        SNN_LAUNCH(k_seg_sort_w1, wgrid, 256, 0, s)(lists, cls, gm, tmp, gidx, gd2, ib);
-        SNN_LAUNCH(k_seg_sort_w2, wgrid, 256, 0, s)(lists + 5 * M, cls + 6, gm, tmp, gidx, gd2, ib);
-        SNN_LAUNCH(k_seg_sort_w4, wgrid, 256, 0, s)(lists + M, cls + 1, gm, tmp, gidx, gd2, ib);
-        SNN_LAUNCH(k_seg_sort_w8, wgrid, 256, 0, s)(lists + 4 * M, cls + 5, gm, tmp, gidx, gd2, ib);
-        SNN_LAUNCH(k_seg_sort_w16, wgrid, 256, 0, s)(lists + 2 * M, cls + 2, gm, tmp, gidx, gd2, ib);
-        SNN_LAUNCH(k_seg_sort_mid, std::min<unsigned>(unsigned(M), 4096), 256, 0, s)(
-            lists + 3 * M, cls + 3, gm, tmp, gidx, gd2, ib);
-        unsigned hcls[8];
+        SNN_LAUNCH(k_seg_classify, unsigned(cdiv(M, 256)), 256, 0, s)(gm, M, 1, lists, big_list, big_len,
+                                                                      cls);
+        seg_sort_launch(lists, cls, M, tmp, gidx, gd2, ids_bound(sd), s);
+        unsigned hcls[kSegClasses];
         if (cudaMemcpyAsync(hcls, cls, sizeof(hcls), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
             set_error("batched CSR build failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -769,7 +762,7 @@ __global__ void k_plan_guard(const unsigned long long *__restrict__ ctr,
     st->qnorm = *qnmax;
     st->tcerr = *tcerr;
     if (skip)
-        for (int k = 0; k < 8; ++k) cls[k] = 0;
+        for (int k = 0; k < kSegClasses; ++k) cls[k] = 0;
 }
 
 // set_nnz[t] = first global neighbour entry of set t (t <= nsets).
@@ -809,8 +802,8 @@ struct snn_batch_plan {
     float *oeps = nullptr, *q_alpha = nullptr, *q_raw = nullptr, *q_xc = nullptr, *q_hx = nullptr,
           *q_nrm = nullptr, *qnmax = nullptr, *thrA = nullptr, *rec_d2 = nullptr, *gd2 = nullptr;
     int32_t *q_order = nullptr, *qset = nullptr, *tile_set = nullptr, *item_tile = nullptr,
-            *rec_pos = nullptr, *counts = nullptr, *lists = nullptr, *big_list = nullptr,
-            *gidx = nullptr;
+            *rec_pos = nullptr, *counts = nullptr, *big_list = nullptr, *gidx = nullptr;
+    ulonglong2 *lists = nullptr;
     uint64_t *keys = nullptr, *keys_alt = nullptr, *tmp = nullptr;
     uint32_t *vals = nullptr, *vals_alt = nullptr;
     int *bad = nullptr;
@@ -916,11 +909,12 @@ snn_status plan_enqueue(snn_batch_plan *p, cudaStream_t s) {
         SNN_LAUNCH(k_counts_to_i64, unsigned(cdiv(M, 256)), 256, 0, s)(p->counts, M, p->counts64);
     SNN_LAUNCH_CHECK();
     SNN_TRY(scan_exclusive<int64_t>(p->counts64, p->goff, M, s));
-    SNN_CUDA(cudaMemsetAsync(p->cls, 0, 8 * sizeof(unsigned), s));
+    SNN_CUDA(cudaMemsetAsync(p->cls, 0, kSegClasses * sizeof(unsigned), s));
+    const SegMap gm{p->goff, p->goff, nullptr};
     if (M > 0) {
         SNN_CUDA(cudaMemsetAsync(p->big_len, 0, M * sizeof(int64_t), s));
-        SNN_LAUNCH(k_seg_classify, unsigned(cdiv(M, 256)), 256, 0, s)(p->goff, M, p->lists,
-                                                                      p->big_list, p->big_len, p->cls);
+        SNN_LAUNCH(k_seg_classify, unsigned(cdiv(M, 256)), 256, 0, s)(gm, M, 1, p->lists, p->big_list,
+                                                                      p->big_len, p->cls);
     }
     SNN_LAUNCH(k_plan_guard, 1, 1, 0, s)(p->ctr, p->goff + M, p->cls, p->bad, p->qnmax, p->tc_err,
                                          p->surv_cap, p->nnz_cap, p->status);
@@ -928,20 +922,7 @@ snn_status plan_enqueue(snn_batch_plan *p, cudaStream_t s) {
         p->surv, p->ctr, p->surv_cap, p->d_sets, p->qset, p->rec_d2, p->rec_pos, p->goff, p->tmp,
         &p->status->skip);
     SNN_LAUNCH_CHECK();
-    const unsigned wgrid = unsigned(std::min<int64_t>(cdiv(std::max<int64_t>(M, 1) * 32, 256), 16384));
-    const uint32_t ib = ids_bound(p->sd);
-    const SegMap gm{p->goff, p->goff, nullptr};
-    SNN_LAUNCH(k_seg_sort_w1, wgrid, 256, 0, s)(p->lists, p->cls, gm, p->tmp, p->gidx, p->gd2, ib);
-    SNN_LAUNCH(k_seg_sort_w2, wgrid, 256, 0, s)(p->lists + 5 * M, p->cls + 6, gm, p->tmp, p->gidx,
-                                                 p->gd2, ib);
-    SNN_LAUNCH(k_seg_sort_w4, wgrid, 256, 0, s)(p->lists + M, p->cls + 1, gm, p->tmp, p->gidx,
-                                                 p->gd2, ib);
-    SNN_LAUNCH(k_seg_sort_w8, wgrid, 256, 0, s)(p->lists + 4 * M, p->cls + 5, gm, p->tmp, p->gidx,
-                                                 p->gd2, ib);
-    SNN_LAUNCH(k_seg_sort_w16, wgrid, 256, 0, s)(p->lists + 2 * M, p->cls + 2, gm, p->tmp,
-                                                  p->gidx, p->gd2, ib);
-    SNN_LAUNCH(k_seg_sort_mid, unsigned(std::min<int64_t>(std::max<int64_t>(M, 1), 4096)), 256, 0, s)(
-        p->lists + 3 * M, p->cls + 3, gm, p->tmp, p->gidx, p->gd2, ib);
+    seg_sort_launch(p->lists, p->cls, M, p->tmp, p->gidx, p->gd2, ids_bound(p->sd), s);
     if (M > 0)
         SNN_LAUNCH(k_b_offsets, unsigned(cdiv(M, 256)), 256, 0, s)(p->goff, p->d_qglob, nsets, M,
                                                                    p->out_off, p->d_offpos);
@@ -1120,11 +1101,11 @@ snn_status plan_create(int32_t nsets, const snn_index *const *idx, const int64_t
     PTRY(plan_alloc(p, &p->counts, M, s));
     PTRY(plan_alloc(p, &p->counts64, M, s));
     PTRY(plan_alloc(p, &p->goff, M + 1, s));
-    PTRY(plan_alloc(p, &p->lists, 6 * std::max<int64_t>(M, 1), s));
+    PTRY(plan_alloc(p, &p->lists, int64_t(kSegSlotsFine) * std::max<int64_t>(M, 1), s));
     PTRY(plan_alloc(p, &p->big_list, M, s));
     PTRY(plan_alloc(p, &p->big_len, M, s));
     PTRY(plan_alloc(p, &p->toff, M + 1, s));
-    PTRY(plan_alloc(p, &p->cls, 8, s));
+    PTRY(plan_alloc(p, &p->cls, kSegClasses, s));
     PTRY(plan_alloc(p, &p->tmp, p->nnz_cap, s));
     PTRY(plan_alloc(p, &p->out_off, p->off_words, s));
     PTRY(plan_alloc(p, &p->gidx, p->nnz_cap, s));

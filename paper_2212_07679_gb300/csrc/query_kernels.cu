@@ -749,23 +749,30 @@ __global__ void k_scatter_pos(const uint2 *__restrict__ surv, const int32_t *__r
 }
 
 // ------------------------------------------- per-row sort by column id
-// Rows by length: [0] <= 32, [6] <= 64, [1] <= 128, [5] <= 256, [2] <= 512
-// (one warp each), [3] <= 4096 (one block each), [4] longer (radix sort).
-// lists holds 6 arrays of m entries (class 5 in slot 4, class 6 in slot 5).
-__global__ void k_seg_classify(const int64_t *__restrict__ offsets, int64_t m,
-                               int32_t *__restrict__ lists, int32_t *__restrict__ big_list,
-                               int64_t *__restrict__ big_len, unsigned *__restrict__ counters) {
+// Rows by length: [7] <= 8 and [8] <= 16 (fine classes only; else in [0]),
+// [0] <= 32, [6] <= 64, [1] <= 128, [5] <= 256, [2] <= 512 (warp sorts),
+// [3] <= 4096 (one block each), [4] longer (radix sort).  Each list entry is
+// the row's descriptor (staging offset | length << 48, output offset), so a
+// sort reads its row without further lookups; lists holds one array of m
+// entries per class, class c in slot seg_slot(c).
+__global__ void k_seg_classify(SegMap mp, int64_t m, int fine, ulonglong2 *__restrict__ lists,
+                               int32_t *__restrict__ big_list, int64_t *__restrict__ big_len,
+                               unsigned *__restrict__ counters) {
     const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const int64_t len = r < m ? offsets[r + 1] - offsets[r] : 0;
+    int64_t o = 0, len = 0;
+    if (r < m) {
+        o = mp.src[r];
+        len = mp.src[r + 1] - o;
+    }
     // class of the row (counter index; -1: empty), and its list slot
-    int c = -1, slot = 0;
+    int c = -1;
     if (len > 0) {
-        if (len <= kSegSmall) c = 0, slot = 0;
-        else if (len <= 2 * kSegSmall) c = 6, slot = 5;
-        else if (len <= 4 * kSegSmall) c = 1, slot = 1;
-        else if (len <= 8 * kSegSmall) c = 5, slot = 4;
-        else if (len <= 16 * kSegSmall) c = 2, slot = 2;
-        else if (len <= kSegMid) c = 3, slot = 3;
+        if (len <= kSegSmall) c = fine && len <= 8 ? 7 : (fine && len <= 16 ? 8 : 0);
+        else if (len <= 2 * kSegSmall) c = 6;
+        else if (len <= 4 * kSegSmall) c = 1;
+        else if (len <= 8 * kSegSmall) c = 5;
+        else if (len <= 16 * kSegSmall) c = 2;
+        else if (len <= kSegMid) c = 3;
         else c = 4;
     }
     // one atomic per class present in the warp: lanes of a class take
@@ -782,45 +789,49 @@ __global__ void k_seg_classify(const int64_t *__restrict__ offsets, int64_t m,
         big_list[pos] = (int32_t)r;
         big_len[pos] = len;
     } else {
-        lists[int64_t(slot) * m + pos] = (int32_t)r;
+        const int64_t od = mp.dst[mp.rmap ? mp.rmap[r] : r];
+        lists[int64_t(seg_slot(c)) * m + pos] =
+            make_ulonglong2(uint64_t(o) | (uint64_t(len) << 48), uint64_t(od));
     }
 }
 
-// One warp per row of <= 32*E packed entries (id << 32 | dist2 bits; ids are
-// unique in a row, so ordering the packed values orders the ids).  Bitonic
-// network over the blocked layout: lane l holds entries l*E .. l*E+E-1, so the
-// steps with distance < E are compare-exchanges inside a lane and only the
-// 15 steps with distance >= E cross lanes; every step is branch-free.
-// When every id of the call is below 2^(32 - log2(32E)) the network runs on
-// 32-bit keys (id << log2(32E) | position in the row), which halves the
-// shuffles and replaces each 64-bit compare-and-select by a min and a max;
-// the distances are then fetched by position after the sort.  The 32-bit
-// keys are loaded striped (lane l takes entries l, l + 32, ...: the network
-// sorts whatever order it is given) and the sorted keys pass through shared
-// memory back to the striped layout, so that every load and store of a row
-// is a run of 32 consecutive words.
+// S lanes per row of <= S*E packed entries (id << 32 | dist2 bits; ids are
+// unique in a row, so ordering the packed values orders the ids); S < 32
+// (rows of <= 8 or <= 16 entries, E = 1) puts 32/S rows in one warp.  Bitonic
+// network over the blocked layout: lane l of the row's group holds entries
+// l*E .. l*E+E-1, so the steps with distance < E are compare-exchanges inside
+// a lane and only the steps with distance >= E cross lanes (inside the
+// group); every step is branch-free.  When every id of the call is below
+// 2^(32 - log2(S*E)) the network runs on 32-bit keys (id << log2(S*E) |
+// position in the row), which halves the shuffles and replaces each 64-bit
+// compare-and-select by a min and a max; the distances are then fetched by
+// position after the sort.  The 32-bit keys are loaded striped (lane l takes
+// entries l, l + 32, ...: the network sorts whatever order it is given) and
+// the sorted keys pass through shared memory back to the striped layout, so
+// that every load and store of a row is a run of consecutive words.
 __device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int m) {
     const uint32_t lo = __shfl_xor_sync(0xffffffffu, uint32_t(v), m);
     const uint32_t hi = __shfl_xor_sync(0xffffffffu, uint32_t(v >> 32), m);
     return (uint64_t(hi) << 32) | lo;
 }
 
-template <int E, typename T>
+template <int E, int S, typename T>
 __device__ __forceinline__ void bitonic_warp(T (&v)[E], int lane) {
-    constexpr int N = 32 * E;
+    constexpr int N = S * E;
+    const int sl = lane & (S - 1);   // lane within the row's group
 #pragma unroll
     for (int k = 2; k <= N; k <<= 1) {
 #pragma unroll
         for (int j = k >> 1; j > 0; j >>= 1) {
             if (j >= E) {
                 const int lj = j / E;
-                const bool lower = (lane & lj) == 0;
+                const bool lower = (sl & lj) == 0;
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     T p;
                     if constexpr (sizeof(T) == 8) p = shfl_xor_u64(v[e], lj);
                     else p = __shfl_xor_sync(0xffffffffu, v[e], lj);
-                    const bool asc = ((lane * E + e) & k) == 0;
+                    const bool asc = ((sl * E + e) & k) == 0;
                     const bool keep_min = lower == asc;
                     if constexpr (sizeof(T) == 8) {
                         const bool pl = p < v[e];
@@ -835,7 +846,7 @@ __device__ __forceinline__ void bitonic_warp(T (&v)[E], int lane) {
                 for (int e = 0; e < E; ++e) {
                     const int pe = e ^ j;
                     if (pe > e) {
-                        const bool asc = ((lane * E + e) & k) == 0;
+                        const bool asc = ((sl * E + e) & k) == 0;
                         const T a = v[e], b = v[pe];
                         if constexpr (sizeof(T) == 8) {
                             const bool sw = (a > b) == asc;
@@ -855,14 +866,17 @@ __device__ __forceinline__ void bitonic_warp(T (&v)[E], int lane) {
 
 constexpr int kSegWarps = 8;   // warps per block of the per-row sorts
 
-template <int E>
-__device__ __forceinline__ void seg_sort_warp(const int32_t *__restrict__ list, unsigned total,
-                                              const SegMap &mp, const uint64_t *__restrict__ tmp,
-                                              int32_t *__restrict__ idx, float *__restrict__ d2,
-                                              uint32_t id_bound) {
-    constexpr int N = 32 * E;
-    constexpr int LB = E == 1 ? 5 : (E == 2 ? 6 : (E == 4 ? 7 : (E == 8 ? 8 : 9)));
+__host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x >> 1); }
+
+template <int E, int S>
+__device__ __forceinline__ void seg_sort_warp(const ulonglong2 *__restrict__ list, unsigned total,
+                                              const uint64_t *__restrict__ tmp, int32_t *__restrict__ idx,
+                                              float *__restrict__ d2, uint32_t id_bound) {
+    static_assert(S == 32 || E == 1, "groups of fewer than 32 lanes sort one entry per lane");
+    constexpr int N = S * E;
+    constexpr int LB = ilog2c(N);
     static_assert((1 << LB) == N, "position bits");
+    constexpr int RW = 32 / S;   // rows per warp
     // transpose buffer: position p of a warp's sorted row at p + p / 32 (one
     // padding word per 32, so that both the blocked writes and the striped
     // reads hit 32 distinct banks)
@@ -872,22 +886,27 @@ __device__ __forceinline__ void seg_sort_warp(const int32_t *__restrict__ list, 
     // 32-bit words of the packed entries: [2i] = dist2 bits, [2i+1] = id
     const uint32_t *__restrict__ w32 = reinterpret_cast<const uint32_t *>(tmp);
     const int lane = threadIdx.x & 31;
+    const int sl = lane & (S - 1);
     uint32_t *tr = s_tr + (threadIdx.x >> 5) * kTr;
     const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
-    for (int64_t w = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); w < total; w += nw) {
-        const int32_t r = list[w];
-        const int64_t o = mp.src[r];
-        const int len = int(mp.src[r + 1] - o);
-        const int64_t od = mp.dst[mp.rmap ? mp.rmap[r] : r];
+    // the loop runs alike on the whole warp (the shuffles need every lane);
+    // a group past the last row holds no entries
+    for (int64_t wb = (int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5)) * RW; wb < total;
+         wb += nw * RW) {
+        const int64_t w = wb + lane / S;
+        const ulonglong2 rd = w < total ? list[w] : make_ulonglong2(0ull, 0ull);
+        const int64_t o = int64_t(rd.x & ((1ull << 48) - 1ull));
+        const int len = int(rd.x >> 48);
+        const int64_t od = int64_t(rd.y);
         if (k32) {
             uint32_t v[E];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                const int i = e * 32 + lane;
+                const int i = e * S + sl;
                 v[e] = i < len ? (w32[2 * (o + i) + 1] << LB) | uint32_t(i) : 0xffffffffu;
             }
-            bitonic_warp<E>(v, lane);
-            // sorted: lane holds positions lane * E .. lane * E + E - 1
+            bitonic_warp<E, S>(v, lane);
+            // sorted: the group's lane l holds positions l * E .. l * E + E - 1
             if constexpr (E > 1) {
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
@@ -901,7 +920,7 @@ __device__ __forceinline__ void seg_sort_warp(const int32_t *__restrict__ list, 
             }
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                const int i = e * 32 + lane;
+                const int i = e * S + sl;
                 if (i < len) {
                     const uint32_t src = v[e] & uint32_t(N - 1);
                     idx[od + i] = int32_t(v[e] >> LB);
@@ -912,13 +931,13 @@ __device__ __forceinline__ void seg_sort_warp(const int32_t *__restrict__ list, 
             uint64_t v[E];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                const int i = lane * E + e;
+                const int i = sl * E + e;
                 v[e] = i < len ? tmp[o + i] : ~uint64_t(0);
             }
-            bitonic_warp<E>(v, lane);
+            bitonic_warp<E, S>(v, lane);
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                const int i = lane * E + e;
+                const int i = sl * E + e;
                 if (i < len) {
                     idx[od + i] = int32_t(uint32_t(v[e] >> 32));
                     d2[od + i] = __uint_as_float(uint32_t(v[e]));
@@ -928,24 +947,30 @@ __device__ __forceinline__ void seg_sort_warp(const int32_t *__restrict__ list, 
     }
 }
 
-#define SNN_SEG_ARGS                                                                            \
-    const int32_t *__restrict__ list, const unsigned *__restrict__ count, SegMap mp,            \
+#define SNN_SEG_ARGS                                                                        \
+    const ulonglong2 *__restrict__ list, const unsigned *__restrict__ count,                \
         const uint64_t *__restrict__ tmp, int32_t *idx, float *d2, uint32_t id_bound
 // blocks of kSegWarps warps (256 threads)
+__global__ void __launch_bounds__(256) k_seg_sort_s8(SNN_SEG_ARGS) {
+    seg_sort_warp<1, 8>(list, *count, tmp, idx, d2, id_bound);
+}
+__global__ void __launch_bounds__(256) k_seg_sort_s16(SNN_SEG_ARGS) {
+    seg_sort_warp<1, 16>(list, *count, tmp, idx, d2, id_bound);
+}
 __global__ void __launch_bounds__(256) k_seg_sort_w1(SNN_SEG_ARGS) {
-    seg_sort_warp<1>(list, *count, mp, tmp, idx, d2, id_bound);
+    seg_sort_warp<1, 32>(list, *count, tmp, idx, d2, id_bound);
 }
 __global__ void __launch_bounds__(256) k_seg_sort_w2(SNN_SEG_ARGS) {
-    seg_sort_warp<2>(list, *count, mp, tmp, idx, d2, id_bound);
+    seg_sort_warp<2, 32>(list, *count, tmp, idx, d2, id_bound);
 }
 __global__ void __launch_bounds__(256) k_seg_sort_w4(SNN_SEG_ARGS) {
-    seg_sort_warp<4>(list, *count, mp, tmp, idx, d2, id_bound);
+    seg_sort_warp<4, 32>(list, *count, tmp, idx, d2, id_bound);
 }
 __global__ void __launch_bounds__(256) k_seg_sort_w8(SNN_SEG_ARGS) {
-    seg_sort_warp<8>(list, *count, mp, tmp, idx, d2, id_bound);
+    seg_sort_warp<8, 32>(list, *count, tmp, idx, d2, id_bound);
 }
 __global__ void __launch_bounds__(256) k_seg_sort_w16(SNN_SEG_ARGS) {
-    seg_sort_warp<16>(list, *count, mp, tmp, idx, d2, id_bound);
+    seg_sort_warp<16, 32>(list, *count, tmp, idx, d2, id_bound);
 }
 
 // One block per row of <= 4096 entries: bitonic sort in shared memory, of
@@ -977,10 +1002,10 @@ __global__ void __launch_bounds__(256) k_seg_sort_mid(SNN_SEG_ARGS) {
     const bool k32 = id_bound <= (1u << 20);
     const unsigned total = *count;
     for (unsigned w = blockIdx.x; w < total; w += gridDim.x) {
-        const int32_t r = list[w];
-        const int64_t o = mp.src[r];
-        const int len = int(mp.src[r + 1] - o);
-        const int64_t od = mp.dst[mp.rmap ? mp.rmap[r] : r];
+        const ulonglong2 rd = list[w];
+        const int64_t o = int64_t(rd.x & ((1ull << 48) - 1ull));
+        const int len = int(rd.x >> 48);
+        const int64_t od = int64_t(rd.y);
         int N = 64;
         while (N < len) N <<= 1;
         __syncthreads();
@@ -1006,6 +1031,26 @@ __global__ void __launch_bounds__(256) k_seg_sort_mid(SNN_SEG_ARGS) {
     }
 }
 #undef SNN_SEG_ARGS
+
+snn_status seg_sort_launch(const ulonglong2 *lists, const unsigned *cls, int64_t m, const uint64_t *tmp,
+                           int32_t *idx, float *d2, uint32_t id_bound, cudaStream_t s) {
+    const int64_t mm = m > 0 ? m : 1;
+    auto wgrid = [&](int rpw) {
+        return unsigned(std::min<int64_t>(cdiv(cdiv(mm, rpw) * 32, 256), 16384));
+    };
+    auto lst = [&](int c) { return lists + int64_t(seg_slot(c)) * m; };
+    SNN_LAUNCH(k_seg_sort_s8, wgrid(4), 256, 0, s)(lst(7), cls + 7, tmp, idx, d2, id_bound);
+    SNN_LAUNCH(k_seg_sort_s16, wgrid(2), 256, 0, s)(lst(8), cls + 8, tmp, idx, d2, id_bound);
+    SNN_LAUNCH(k_seg_sort_w1, wgrid(1), 256, 0, s)(lst(0), cls, tmp, idx, d2, id_bound);
+    SNN_LAUNCH(k_seg_sort_w2, wgrid(1), 256, 0, s)(lst(6), cls + 6, tmp, idx, d2, id_bound);
+    SNN_LAUNCH(k_seg_sort_w4, wgrid(1), 256, 0, s)(lst(1), cls + 1, tmp, idx, d2, id_bound);
+    SNN_LAUNCH(k_seg_sort_w8, wgrid(1), 256, 0, s)(lst(5), cls + 5, tmp, idx, d2, id_bound);
+    SNN_LAUNCH(k_seg_sort_w16, wgrid(1), 256, 0, s)(lst(2), cls + 2, tmp, idx, d2, id_bound);
+    SNN_LAUNCH(k_seg_sort_mid, unsigned(std::min<int64_t>(mm, 4096)), 256, 0, s)(lst(3), cls + 3, tmp, idx, d2,
+                                                                             id_bound);
+    SNN_LAUNCH_CHECK();
+    return SNN_OK;
+}
 
 // Long rows: keys (big-row rank << 32 | column), values = source position.
 __global__ void k_seg_big_gather(const int32_t *__restrict__ big_list, int nbig, SegMap mp,

@@ -219,20 +219,37 @@ struct SegMap {
     const int64_t *dst;
     const int32_t *rmap;
 };
-__global__ void k_seg_classify(const int64_t *offsets, int64_t m, int32_t *lists,
-                               int32_t *big_list, int64_t *big_len, unsigned *counters);
-__global__ void k_seg_sort_w1(const int32_t *list, const unsigned *count, SegMap mp,
-                              const uint64_t *tmp, int32_t *idx, float *d2, uint32_t id_bound);
-__global__ void k_seg_sort_w16(const int32_t *list, const unsigned *count, SegMap mp,
-                              const uint64_t *tmp, int32_t *idx, float *d2, uint32_t id_bound);
-__global__ void k_seg_sort_w8(const int32_t *list, const unsigned *count, SegMap mp,
-                              const uint64_t *tmp, int32_t *idx, float *d2, uint32_t id_bound);
-__global__ void k_seg_sort_w2(const int32_t *list, const unsigned *count, SegMap mp,
-                              const uint64_t *tmp, int32_t *idx, float *d2, uint32_t id_bound);
-__global__ void k_seg_sort_w4(const int32_t *list, const unsigned *count, SegMap mp,
-                              const uint64_t *tmp, int32_t *idx, float *d2, uint32_t id_bound);
-__global__ void k_seg_sort_mid(const int32_t *list, const unsigned *count, SegMap mp,
-                              const uint64_t *tmp, int32_t *idx, float *d2, uint32_t id_bound);
+// Length classes (counter index c): 0 <= 32 entries (fine: 17-32), 6 <= 64,
+// 1 <= 128, 5 <= 256, 2 <= 512, 3 <= 4096, 4 longer, and with fine set
+// 7 <= 8 and 8 <= 16.  List slot of class c (class 4 has none: big_list).
+__host__ __device__ constexpr int seg_slot(int c) { return c < 4 ? c : c - 1; }
+constexpr int kSegSlotsCoarse = 6;   // list slots without the fine classes
+constexpr int kSegSlotsFine = 8;
+constexpr int kSegClasses = 9;       // counters
+// Classifies row r < m by length: appends its descriptor (src offset |
+// length << 48, output offset) to its class list (slot seg_slot(c), m
+// entries each), or for rows longer than kSegMid its index and length to
+// big_list / big_len.  counters[c] counts the rows of class c (zeroed first).
+__global__ void k_seg_classify(SegMap mp, int64_t m, int fine, ulonglong2 *lists, int32_t *big_list,
+                               int64_t *big_len, unsigned *counters);
+#define SNN_SEG_DECL(name)                                                                   \
+    __global__ void name(const ulonglong2 *list, const unsigned *count, const uint64_t *tmp, \
+                         int32_t *idx, float *d2, uint32_t id_bound)
+// launched with 256 threads per block
+SNN_SEG_DECL(k_seg_sort_s8);
+SNN_SEG_DECL(k_seg_sort_s16);
+SNN_SEG_DECL(k_seg_sort_w1);
+SNN_SEG_DECL(k_seg_sort_w2);
+SNN_SEG_DECL(k_seg_sort_w4);
+SNN_SEG_DECL(k_seg_sort_w8);
+SNN_SEG_DECL(k_seg_sort_w16);
+SNN_SEG_DECL(k_seg_sort_mid);
+#undef SNN_SEG_DECL
+// Every per-row sort of lists classified with the fine classes (m entries per
+// list slot), grids sized for m rows per class: the class counts are read on
+// the device, so the launches are the same whatever the row lengths.
+snn_status seg_sort_launch(const ulonglong2 *lists, const unsigned *cls, int64_t m, const uint64_t *tmp,
+                           int32_t *idx, float *d2, uint32_t id_bound, cudaStream_t s);
 __global__ void k_seg_big_gather(const int32_t *big_list, int nbig, SegMap mp, const int64_t *toff,
                                  const uint64_t *tmp, uint64_t *keys, uint32_t *vals, float *gd2);
 __global__ void k_seg_big_scatter(const uint64_t *keys, const uint32_t *vals, int64_t total,

@@ -771,7 +771,7 @@ struct Readback {
     unsigned long long ctr[4];   // survivors, work, band pairs, candidates
     int bad, err;                // NaN/Inf in the queries, expired wait
     int64_t nnz;
-    unsigned cls[8];             // rows per length class
+    unsigned cls[kSegClasses];   // rows per length class
     int64_t big_total;           // entries in rows longer than 4096
 };
 
@@ -781,7 +781,7 @@ __global__ void k_readback(const unsigned long long *__restrict__ ctr, const int
                            Readback *__restrict__ rb) {
     const int t = threadIdx.x;
     if (t < 4) rb->ctr[t] = ctr[t];
-    if (t < 8) rb->cls[t] = cls[t];
+    if (t < kSegClasses) rb->cls[t] = cls[t];
     if (t == 0) {
         rb->bad = *bad;
         rb->err = *err;
@@ -1019,17 +1019,18 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         sa.ev_kernel[0] = ev[5];
         sa.ev_kernel[1] = ev[6];
     }
-    int32_t *counts, *lists, *big_list;
+    int32_t *counts, *big_list;
+    ulonglong2 *lists;
     int64_t *counts64, *big_len, *toff, *soff;
     unsigned *cls;
     TRY_Q(scr.alloc(&counts, m));
     TRY_Q(scr.alloc(&counts64, m));
     TRY_Q(scr.alloc(&soff, m + 1));
-    TRY_Q(scr.alloc(&lists, 6 * m));
+    TRY_Q(scr.alloc(&lists, int64_t(kSegSlotsFine) * m));
     TRY_Q(scr.alloc(&big_list, m));
     TRY_Q(scr.alloc(&big_len, m));
     TRY_Q(scr.alloc(&toff, m + 1));
-    TRY_Q(scr.alloc(&cls, 8));
+    TRY_Q(scr.alloc(&cls, kSegClasses));
     uint2 *rinfo;
     TRY_Q(scr.alloc(&rinfo, m));
     const double R2 = R * R;
@@ -1098,7 +1099,7 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         // the result stays in positions)
         SNN_LAUNCH(k_counts_to_i64, grid_for(m, 256), 256, 0, s)(counts, m, counts64);
         CUDA_Q(cudaGetLastError());
-        CUDA_Q(cudaMemsetAsync(cls, 0, 8 * sizeof(unsigned), s));
+        CUDA_Q(cudaMemsetAsync(cls, 0, kSegClasses * sizeof(unsigned), s));
         if (pos_rows) {
             soff = out->offsets;
             TRY_Q(scan_exclusive<int64_t>(counts64, soff, m, s));
@@ -1114,7 +1115,8 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
             TRY_Q(scan_exclusive<int64_t>(counts64, out->offsets, m, s));
             // rows by length class (per-row sort below); long rows' sizes scanned
             CUDA_Q(cudaMemsetAsync(big_len, 0, m * sizeof(int64_t), s));
-            SNN_LAUNCH(k_seg_classify, grid_for(m, 256), 256, 0, s)(soff, m, lists, big_list, big_len, cls);
+            SNN_LAUNCH(k_seg_classify, grid_for(m, 256), 256, 0, s)(SegMap{soff, out->offsets, qs.order}, m, 1,
+                                                                     lists, big_list, big_len, cls);
             CUDA_Q(cudaGetLastError());
             TRY_Q(scan_exclusive<int64_t>(big_len, toff, m, s));
         }
@@ -1186,9 +1188,11 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         // to output rows (query ids); classes with no rows are skipped and the
         // grids sized by the class counts
         const unsigned *hc = hb->cls;
-        auto wgrid = [&](unsigned rows) {
-            return std::min<unsigned>(grid_for(int64_t(rows) * 32, 256), 16384);
+        // warps for the rows of a class (rpw rows per warp)
+        auto wgrid = [&](unsigned rows, int rpw) {
+            return std::min<unsigned>(grid_for(int64_t(cdiv(int64_t(rows), rpw)) * 32, 256), 16384);
         };
+        auto lst = [&](int c) { return lists + int64_t(seg_slot(c)) * m; };
         int32_t *oi = out->indices;
         float *od = out->dist2;
         const SegMap oo{soff, out->offsets, qs.order};
@@ -1196,17 +1200,15 @@ static snn_status query_impl(const snn_index *ix, const float *Q, int64_t m, int
         // 64-bit sort keys (both widths give the same rows)
         const char *k64 = getenv("SNN_SORT_KEYS64");
         const uint32_t ib = (k64 && k64[0] == '1') ? 0xffffffffu : uint32_t(ix->n);
-        if (hc[0]) SNN_LAUNCH(k_seg_sort_w1, wgrid(hc[0]), 256, 0, s)(lists, cls, oo, tmp, oi, od, ib);
-        if (hc[6]) SNN_LAUNCH(k_seg_sort_w2, wgrid(hc[6]), 256, 0, s)(lists + 5 * m, cls + 6, oo, tmp,
-                                                                     oi, od, ib);
-        if (hc[1]) SNN_LAUNCH(k_seg_sort_w4, wgrid(hc[1]), 256, 0, s)(lists + m, cls + 1, oo, tmp, oi,
-                                                                     od, ib);
-        if (hc[5]) SNN_LAUNCH(k_seg_sort_w8, wgrid(hc[5]), 256, 0, s)(lists + 4 * m, cls + 5, oo, tmp,
-                                                                     oi, od, ib);
-        if (hc[2]) SNN_LAUNCH(k_seg_sort_w16, wgrid(hc[2]), 256, 0, s)(lists + 2 * m, cls + 2, oo,
-                                                                      tmp, oi, od, ib);
-        if (hc[3]) SNN_LAUNCH(k_seg_sort_mid, std::min<unsigned>(hc[3], 4096), 256, 0, s)(
-            lists + 3 * m, cls + 3, oo, tmp, oi, od, ib);
+        if (hc[7]) SNN_LAUNCH(k_seg_sort_s8, wgrid(hc[7], 4), 256, 0, s)(lst(7), cls + 7, tmp, oi, od, ib);
+        if (hc[8]) SNN_LAUNCH(k_seg_sort_s16, wgrid(hc[8], 2), 256, 0, s)(lst(8), cls + 8, tmp, oi, od, ib);
+        if (hc[0]) SNN_LAUNCH(k_seg_sort_w1, wgrid(hc[0], 1), 256, 0, s)(lst(0), cls, tmp, oi, od, ib);
+        if (hc[6]) SNN_LAUNCH(k_seg_sort_w2, wgrid(hc[6], 1), 256, 0, s)(lst(6), cls + 6, tmp, oi, od, ib);
+        if (hc[1]) SNN_LAUNCH(k_seg_sort_w4, wgrid(hc[1], 1), 256, 0, s)(lst(1), cls + 1, tmp, oi, od, ib);
+        if (hc[5]) SNN_LAUNCH(k_seg_sort_w8, wgrid(hc[5], 1), 256, 0, s)(lst(5), cls + 5, tmp, oi, od, ib);
+        if (hc[2]) SNN_LAUNCH(k_seg_sort_w16, wgrid(hc[2], 1), 256, 0, s)(lst(2), cls + 2, tmp, oi, od, ib);
+        if (hc[3]) SNN_LAUNCH(k_seg_sort_mid, std::min<unsigned>(hc[3], 4096), 256, 0, s)(lst(3), cls + 3, tmp,
+                                                                                       oi, od, ib);
         CUDA_Q(cudaGetLastError());
         const int nbig = (int)hc[4];
         if (nbig > 0) {
