@@ -423,6 +423,13 @@ __device__ __forceinline__ void decide_one_survivor(
     // the survivor list and the records are read / written once: streaming
     // accesses, so that they do not evict the data rows from L2
     const uint2 e = __ldcs(surv + s);
+    if (kSym && e.x == e.y) {
+        // a point and itself: S = 0 <= fl64(R*R), dist2 0, one entry
+        __stcs(rec_d2 + s, 0.f);
+        __stcs(rec_pos + s, atomicAdd(&counts[e.x], 1));
+        __stcs(rec_pos + cap + s, -1);
+        return;
+    }
     const DecideConsts dc = dcq ? dcq[e.x] : dc0;
     const double R2e = R2q ? R2q[e.x] : R2;
     const float4 *pq = reinterpret_cast<const float4 *>(qraw + int64_t(e.x) * dp);
@@ -435,7 +442,6 @@ __device__ __forceinline__ void decide_one_survivor(
         rb[k4] = in ? pq[k4] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     float H = 0.f, L = 0.f;
-    bool nz = false;
 #pragma unroll
     for (int k4 = 0; k4 < NQ; ++k4) {
         const float4 a = ra[k4], b = rb[k4];
@@ -447,7 +453,6 @@ __device__ __forceinline__ void decide_one_survivor(
             // leaves (H, L) exactly unchanged
             float sd, ed;
             two_sum(av[c], -bv[c], sd, ed);
-            nz |= sd != 0.f;
             const float ph = __fmul_rn(sd, sd);
             const float pl = __fmaf_rn(sd, sd, -ph);
             const float cc = __fmaf_rn(__fadd_rn(sd, sd), ed, pl);
@@ -458,8 +463,10 @@ __device__ __forceinline__ void decide_one_survivor(
             L = __fsub_rn(t3, __fsub_rn(H, s1));
         }
     }
+    // H below 2^-100 goes to the FP64 loop (an underflow, or two equal
+    // points other than a point and itself)
     float d2 = 0.f;
-    int v = decide_df(H, L, nz, dc, &d2);
+    int v = decide_df(H, L, true, dc, &d2);
     if (v == 2) {
         const double S = dist2_fp64(pp, pq, d, dp);
         v = S <= R2e ? 1 : 0;
@@ -531,10 +538,12 @@ __device__ __forceinline__ void decide_group_body(
         const int64_t s = base + int((threadIdx.x & 31) / G);
         const bool valid = s < nsurv;
         const uint2 e = valid ? surv[s] : make_uint2(0u, 0u);
+        // a point and itself (S = 0, always a neighbour) skips the arithmetic
+        const bool self = kSym && valid && e.x == e.y;
         const float4 *pq = reinterpret_cast<const float4 *>(qraw + int64_t(e.x) * dp);
         const float4 *pp = reinterpret_cast<const float4 *>(praw + int64_t(e.y) * dp);
         float S0 = 0.f;
-        for (int k4 = lane; valid && k4 < dp / 4; k4 += G) {
+        for (int k4 = lane; valid && !self && k4 < dp / 4; k4 += G) {
             const float4 a = pp[k4], b = pq[k4];
             float t = __fsub_rn(a.x, b.x);
             S0 = __fmaf_rn(t, t, S0);
@@ -553,8 +562,7 @@ __device__ __forceinline__ void decide_group_body(
         // still takes part in the warp's shuffles below)
         const bool rej = valid && S0 > thr0;
         float H = 0.f, L = 0.f;
-        bool nz = false;
-        for (int k4 = lane; valid && !rej && k4 < dp / 4; k4 += G) {
+        for (int k4 = lane; valid && !rej && !self && k4 < dp / 4; k4 += G) {
             const float4 a = pp[k4], b = pq[k4];
             const float av[4] = {a.x, a.y, a.z, a.w};
             const float bv[4] = {b.x, b.y, b.z, b.w};
@@ -564,7 +572,6 @@ __device__ __forceinline__ void decide_group_body(
                 // leaves (H, L) exactly unchanged
                 float sd, ed;
                 two_sum(av[c], -bv[c], sd, ed);
-                nz |= sd != 0.f;
                 const float ph = __fmul_rn(sd, sd);
                 const float pl = __fmaf_rn(sd, sd, -ph);
                 const float cc = __fmaf_rn(__fadd_rn(sd, sd), ed, pl);
@@ -585,13 +592,13 @@ __device__ __forceinline__ void decide_group_body(
             H = __fadd_rn(s1, t3);
             L = __fsub_rn(t3, __fsub_rn(H, s1));
         }
-        if (G > 1) {
-            // any nonzero difference in this survivor's group of G lanes
-            const unsigned b = __ballot_sync(0xffffffffu, nz);
-            const unsigned gm = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1));
-            nz = (b & gm) != 0u;
-        }
         if (lane != 0 || !valid) continue;
+        if (self) {
+            rec_d2[s] = 0.f;
+            rec_pos[s] = atomicAdd(&counts[e.x], 1);
+            rec_pos[cap + s] = -1;
+            continue;
+        }
         if (rej) {
             rec_d2[s] = 0.f;
             rec_pos[s] = -1;
@@ -600,8 +607,10 @@ __device__ __forceinline__ void decide_group_body(
         }
         const DecideConsts dc = dcq ? dcq[e.x] : dc0;
         const double R2e = R2q ? R2q[e.x] : R2;
+        // H below 2^-100 goes to the FP64 loop (an underflow, or two equal
+        // points other than a point and itself)
         float d2 = 0.f;
-        int v = decide_df(H, L, nz, dc, &d2);
+        int v = decide_df(H, L, true, dc, &d2);
         if (v == 2) {
             const double S = dist2_fp64(pp, pq, d, dp);
             v = S <= R2e ? 1 : 0;

@@ -137,7 +137,8 @@ __global__ void k_score_fp32_multi(ScoreArgs a);
 // matters).  Returns 1 (accept, *d2 = (float)S), 0 (reject) or 2 (take the
 // FP64 loop: near-ties, values near a float rounding boundary, overflow,
 // underflow).  nz: some coordinate differs (H = 0 with nz may be an
-// underflow).
+// underflow); a caller that does not track it passes true, and then every H
+// below 2^-100, equal points included, takes the FP64 loop.
 
 
 // (computed on the host and passed to the kernels: FP64 is slow on this part)

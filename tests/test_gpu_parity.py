@@ -580,6 +580,28 @@ def test_row_sort_key_widths(snn, monkeypatch, keys64):
     assert_csr_equal(got, ref, f"keys64={keys64}")
 
 
+@pytest.mark.parametrize("keys64", ["0", "1"])
+@pytest.mark.parametrize("prec", PRECS)
+def test_row_lengths_at_sort_class_edges(snn, monkeypatch, keys64, prec):
+    """Rows whose lengths sit on both sides of every per-row sort class edge
+    (8, 16, 32, 64, 128, 256, 512): well separated tight clusters of k points
+    give k rows of exactly k entries; self-join and out-of-sample queries."""
+    monkeypatch.setenv("SNN_SORT_KEYS64", keys64)
+    rng = np.random.default_rng(47)
+    sizes = [1, 2, 7, 8, 9, 15, 16, 17, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257,
+             511, 512, 513]
+    centres = rng.permutation(len(sizes))[:, None] * np.array([[100.0, -50.0, 25.0]])
+    P = np.concatenate([c + rng.normal(0.0, 0.01, (k, 3)) for c, k in zip(centres, sizes)])
+    P = P[rng.permutation(len(P))].astype(np.float32)
+    got = _run(snn, P, None, 1.0, prec)
+    ref = oracle.brute_radius(P, None, 1.0)
+    assert sorted(set(np.diff(ref.offsets).tolist())) == sorted(sizes)
+    assert_csr_equal(got, ref, f"self-join keys64={keys64}")
+    Q = P[rng.permutation(len(P))[:700]] + np.float32(0.001)
+    got = _run(snn, P, Q, 1.0, prec)
+    assert_csr_equal(got, oracle.brute_radius(P, Q, 1.0), f"queries keys64={keys64}")
+
+
 @pytest.mark.parametrize("split", ["bf16x2", "bf16x3", "fp16x2", "fp16x1"])
 @pytest.mark.parametrize("d,spread", [(12, 40.0), (16, 3.0), (40, 10.0), (100, 2.0), (300, 6.0)])
 def test_tensor_core_shapes_forced_split(snn, monkeypatch, split, d, spread):
