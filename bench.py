@@ -37,10 +37,10 @@ HBM_PEAK_FALLBACK = 6800.0
 SCORER_SOURCES = ["tc_score.cu", "tc_score.cuh", "tc_common.cuh", "common.cuh", "index_struct.cuh",
                   "query_kernels.cuh"]
 SCORER_TRAFFIC = {
-    "sha": "3474f57d20ab8c3e",
+    "sha": "4adb7edb29bdea29",
     "profile": "profiles/k_score_tc_dram_traffic_full_size.md",
-    ("gmm_aniso", 1000000, "bf16"): 193428736 + 172581120,
-    ("lowrank_img", 70000, "bf16"): 295200768 + 7284224,
+    ("gmm_aniso", 1000000, "bf16"): 193561088 + 172464896,
+    ("lowrank_img", 70000, "bf16"): 299913472 + 7792384,
 }
 
 
