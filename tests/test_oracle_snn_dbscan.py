@@ -148,3 +148,35 @@ def test_dbscan_union_find_equals_bfs_random():
         b = oracle.dbscan_bfs(work.P, 0.4, 6)
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
         assert (a[0] >= 0).sum() > 100 and (a[0] < 0).sum() > 10
+
+
+def test_dbscan_matches_scikit_learn():
+    """Pin against an independent library: scikit-learn's DBSCAN (neighbourhoods
+    with dist <= eps counting the point itself, core iff at least min_samples
+    of them) gives the same core points, the same noise and the same
+    partition of the core points; a border point joins a cluster of one of
+    its core neighbours in both (which one is the method's choice: here the
+    smallest-id core neighbour's)."""
+    skc = pytest.importorskip("sklearn.cluster")
+    from scipy.spatial.distance import cdist
+    work = wl.blobs3d(n=3000, blobs=12, box=12.0, seed=1077)
+    P, eps, mp = work.P, 0.4, 6
+    D = cdist(P.astype(np.float64), P.astype(np.float64))
+    # no pair so close to eps that a different rounding order could flip it
+    assert np.abs(D - eps).min() > 1e-9 * eps
+    labels, core = oracle.dbscan(P, eps, mp)
+    sk = skc.DBSCAN(eps=eps, min_samples=mp, algorithm="brute").fit(P.astype(np.float64))
+    sk_core = np.zeros(len(P), dtype=bool)
+    sk_core[sk.core_sample_indices_] = True
+    assert np.array_equal(core.astype(bool), sk_core)
+    assert np.array_equal(labels < 0, sk.labels_ < 0)
+    c = core.astype(bool)
+    pairs = set(zip(labels[c].tolist(), sk.labels_[c].tolist()))
+    assert len(pairs) == len(set(labels[c].tolist())) == len(set(sk.labels_[c].tolist()))
+    to_sk = dict(pairs)
+    border = (~c) & (labels >= 0)
+    for i in np.nonzero(border)[0]:
+        nb_core = np.nonzero((D[i] <= eps) & c)[0]
+        assert labels[i] in set(labels[nb_core].tolist())
+        assert sk.labels_[i] in {to_sk[l] for l in labels[nb_core].tolist()}
+    assert border.sum() > 0 and (labels < 0).sum() > 10 and len(pairs) > 5
